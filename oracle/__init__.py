@@ -1,0 +1,137 @@
+"""FP64 CPU oracle for the ADI Cahn-Hilliard step and its batched cyclic solvers.
+
+TEST INFRASTRUCTURE ONLY: the tests, the package smoke check and the benchmark's
+CPU-baseline leg may import this; the library never does.  It shares no code
+with the CUDA path.  See ``oracle.c`` for the paper passages each function
+follows.  All arrays are float64 numpy arrays; layouts match the C ABI
+(row-major fields ``c[j, i]``, interleaved batches ``x[i * batch + s]``).
+
+Parity pins: every function is pinned by the ``-m "not gpu"`` tests in
+``tests/test_oracle_pins.py`` against dense solves, circulant FFT solves, closed
+forms of the discrete scheme, conservation laws and symmetries.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+_D = ctypes.POINTER(ctypes.c_double)
+
+ERRORS = {0: "ok", -1: "invalid argument", -2: "singular", -3: "out of memory"}
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        i, l, d = ctypes.c_int, ctypes.c_long, ctypes.c_double
+        L.oracle_penta_cyclic_solve.argtypes = [i, _D, _D, _D, _D, _D, l, _D, l, _D, l]
+        L.oracle_penta_cyclic_batch.argtypes = [i, i, i, _D, _D, _D, _D, _D, _D, _D]
+        L.oracle_tri_cyclic_solve.argtypes = [i, _D, _D, _D, l, _D, l, _D, l]
+        L.oracle_tri_cyclic_batch.argtypes = [i, i, i, _D, _D, _D, _D, _D]
+        L.oracle_stencil_apply_2d.argtypes = [_D, _D, i, i, i, _D, i, i, i, i, i, i]
+        L.oracle_ch_step.argtypes = [i, i, d, d, d, d, _D, _D]
+        L.oracle_ch_run.argtypes = [i, i, d, d, d, d, i, _D, _D]
+        L.oracle_ch_diagnostics.argtypes = [i, i, d, d, d, _D, _D, _D]
+        for fn in ("oracle_penta_cyclic_solve", "oracle_penta_cyclic_batch", "oracle_tri_cyclic_solve",
+                   "oracle_tri_cyclic_batch", "oracle_stencil_apply_2d", "oracle_ch_step",
+                   "oracle_ch_run", "oracle_ch_diagnostics"):
+            getattr(L, fn).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise OracleError(ERRORS.get(rc, str(rc)))
+
+
+def penta_cyclic_batch(a, b, c, d, e, f, batch: int):
+    """Solve ``batch`` cyclic pentadiagonal systems, interleaved ``f[i*batch + s]``.
+
+    Coefficients of length n are shared by all systems; of length n*batch they
+    are per system (interleaved like ``f``).
+    """
+    f = _f64(f).ravel()
+    n = f.size // batch
+    co = [_f64(v).ravel() for v in (a, b, c, d, e)]
+    mode = 1 if co[0].size == n * batch and batch > 1 else 0
+    x = np.empty_like(f)
+    _check(lib().oracle_penta_cyclic_batch(n, batch, mode, *[_p(v) for v in co], _p(f), _p(x)))
+    return x
+
+
+def penta_cyclic_solve(a, b, c, d, e, f):
+    """One cyclic pentadiagonal system (vectors of length n)."""
+    return penta_cyclic_batch(a, b, c, d, e, f, 1)
+
+
+def tri_cyclic_batch(a, b, c, f, batch: int):
+    """Solve ``batch`` cyclic tridiagonal systems, interleaved ``f[i*batch + s]``."""
+    f = _f64(f).ravel()
+    n = f.size // batch
+    co = [_f64(v).ravel() for v in (a, b, c)]
+    mode = 1 if co[0].size == n * batch and batch > 1 else 0
+    x = np.empty_like(f)
+    _check(lib().oracle_tri_cyclic_batch(n, batch, mode, *[_p(v) for v in co], _p(f), _p(x)))
+    return x
+
+
+def tri_cyclic_solve(a, b, c, f):
+    return tri_cyclic_batch(a, b, c, f, 1)
+
+
+def stencil_apply_2d(inp, w, left, right, top, bottom, premap=False, periodic=True, out=None):
+    """General box stencil on a (ny, nx) field; ``w`` is (top+bottom+1, left+right+1)."""
+    inp = _f64(inp)
+    ny, nx = inp.shape
+    w = _f64(w)
+    assert w.shape == (top + bottom + 1, left + right + 1)
+    out = np.zeros_like(inp) if out is None else _f64(out).copy()
+    _check(lib().oracle_stencil_apply_2d(_p(inp), _p(out), nx, ny, nx, _p(w), left, right, top, bottom,
+                                         int(bool(premap)), int(bool(periodic))))
+    return out
+
+
+def ch_run(c_now, c_prev, lx, ly, gamma, dt, nsteps=1):
+    """Advance ``nsteps`` ADI steps; returns (C^{n+nsteps}, C^{n+nsteps-1}) as new arrays."""
+    cn = _f64(c_now).copy()
+    cp = _f64(c_prev).copy()
+    ny, nx = cn.shape
+    _check(lib().oracle_ch_run(nx, ny, float(lx), float(ly), float(gamma), float(dt), int(nsteps),
+                               _p(cn), _p(cp)))
+    return cn, cp
+
+
+def ch_step(c_now, c_prev, lx, ly, gamma, dt):
+    return ch_run(c_now, c_prev, lx, ly, gamma, dt, 1)
+
+
+def ch_diagnostics(c, lx, ly, gamma):
+    """(mass, free energy) of a (ny, nx) field."""
+    c = _f64(c)
+    ny, nx = c.shape
+    m = ctypes.c_double()
+    e = ctypes.c_double()
+    _check(lib().oracle_ch_diagnostics(nx, ny, float(lx), float(ly), float(gamma), _p(c),
+                                       ctypes.byref(m), ctypes.byref(e)))
+    return m.value, e.value

@@ -1,0 +1,320 @@
+"""Pins for the CPU oracle: each check compares it with something other than itself.
+
+- cyclic band solves: dense LU with partial pivoting (numpy.linalg.solve, brute
+  force), circulant FFT solves for constant coefficients, residuals computed by
+  array shifts;
+- stencil: exactness on polynomials, the Fourier symbol on periodic modes,
+  an array-shift formulation on random asymmetric boxes;
+- ADI step (Eq. 3.1): the spectral form of the whole step, the closed-form
+  single-mode recurrence of the linearised scheme and its continuum limit
+  sigma(k) = k^2 - gamma k^4, mass conservation, odd symmetry (bit exact),
+  shift and transpose equivariance, constant states;
+- diagnostics: closed-form discrete sums.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import spectral
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+# --------------------------------------------------------------------------- penta
+@pytest.mark.parametrize("n", [5, 6, 7, 8, 13, 32, 64])
+def test_penta_matches_dense_lu(n):
+    batch = 3
+    a, b, c, d, e = synth.diag_dominant_penta(11 + n, n, batch)
+    f = synth.uniform(7 + n, n * batch, -1.0, 1.0)
+    x = oracle.penta_cyclic_batch(a, b, c, d, e, f, batch)
+    for s in range(batch):
+        co = [v.reshape(n, batch)[:, s] for v in (a, b, c, d, e)]
+        A = spectral.dense_cyclic_penta(*co)
+        ref = np.linalg.solve(A, f.reshape(n, batch)[:, s])
+        got = x.reshape(n, batch)[:, s]
+        assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_penta_shared_coefficients_dense():
+    n, batch = 24, 5
+    a, b, c, d, e = synth.diag_dominant_penta(3, n, 1)
+    f = synth.uniform(4, n * batch, -1.0, 1.0)
+    x = oracle.penta_cyclic_batch(a, b, c, d, e, f, batch)
+    A = spectral.dense_cyclic_penta(a, b, c, d, e)
+    ref = np.linalg.solve(A, f.reshape(n, batch))
+    assert np.max(np.abs(x.reshape(n, batch) - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("n,sigma", [(16, 0.3), (256, 18.4), (1024, 7.05e3), (512, 1.9e4)])
+def test_penta_constant_matches_circulant_fft(n, sigma):
+    # The ADI matrix (sigma, -4 sigma, 1 + 6 sigma, -4 sigma, sigma) (eq:1d_hyper_scheme).
+    batch = 4
+    co = [np.full(n, v) for v in (sigma, -4 * sigma, 1 + 6 * sigma, -4 * sigma, sigma)]
+    f = synth.uniform(5, n * batch, -1.0, 1.0)
+    x = oracle.penta_cyclic_batch(*co, f, batch).reshape(n, batch)
+    col = np.zeros(n)
+    col[0], col[1], col[2], col[-1], col[-2] = 1 + 6 * sigma, -4 * sigma, sigma, -4 * sigma, sigma
+    ref = spectral.circulant_solve(col, f.reshape(n, batch))
+    # forward error of an LU solve grows with cond(A) ~ 1 + 16 sigma
+    tol = 1e-15 * (1 + 16 * sigma) * 50
+    assert np.max(np.abs(x - ref)) <= tol * np.max(np.abs(ref))
+
+
+def test_penta_large_residual_per_system():
+    n, batch = 1024, 16
+    a, b, c, d, e = synth.diag_dominant_penta(2, n, batch)
+    f = synth.uniform(1, n * batch, -1.0, 1.0)
+    x = oracle.penta_cyclic_batch(a, b, c, d, e, f, batch)
+    res = spectral.penta_matvec_interleaved(a, b, c, d, e, x, batch) - f
+    assert np.max(np.abs(res)) <= 1e-14 * np.max(np.abs(f)) * 10
+
+
+def test_penta_detects_swapped_diagonals():
+    # a plausible slip (a <-> e) must change the answer on non-symmetric rows
+    n = 16
+    a, b, c, d, e = synth.diag_dominant_penta(9, n, 1)
+    f = synth.uniform(9, n, -1, 1)
+    x1 = oracle.penta_cyclic_solve(a, b, c, d, e, f)
+    x2 = oracle.penta_cyclic_solve(e, b, c, d, a, f)
+    assert np.max(np.abs(x1 - x2)) > 1e-3
+
+
+def test_penta_singular_reported():
+    n = 8
+    z = np.zeros(n)
+    with pytest.raises(oracle.OracleError):
+        oracle.penta_cyclic_solve(z, z, z, z, z, np.ones(n))
+
+
+# --------------------------------------------------------------------------- tri
+@pytest.mark.parametrize("n", [3, 4, 5, 9, 33, 64])
+def test_tri_matches_dense_lu(n):
+    batch = 3
+    a, b, c = synth.diag_dominant_tri(21 + n, n, batch)
+    f = synth.uniform(8 + n, n * batch, -1.0, 1.0)
+    x = oracle.tri_cyclic_batch(a, b, c, f, batch)
+    for s in range(batch):
+        co = [v.reshape(n, batch)[:, s] for v in (a, b, c)]
+        ref = np.linalg.solve(spectral.dense_cyclic_tri(*co), f.reshape(n, batch)[:, s])
+        got = x.reshape(n, batch)[:, s]
+        assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("n,sigma", [(64, 0.5), (1024, 8.5e3)])
+def test_tri_constant_matches_circulant_fft(n, sigma):
+    # periodic Crank-Nicolson diffusion matrix (-sigma, 1 + 2 sigma, -sigma) (eq5:1ddiffscheme)
+    batch = 3
+    f = synth.uniform(6, n * batch, -1.0, 1.0)
+    x = oracle.tri_cyclic_batch(np.full(n, -sigma), np.full(n, 1 + 2 * sigma), np.full(n, -sigma), f, batch)
+    col = np.zeros(n)
+    col[0], col[1], col[-1] = 1 + 2 * sigma, -sigma, -sigma
+    ref = spectral.circulant_solve(col, f.reshape(n, batch))
+    tol = 1e-15 * (1 + 4 * sigma) * 50
+    assert np.max(np.abs(x.reshape(n, batch) - ref)) <= tol * np.max(np.abs(ref))
+
+
+def test_tri_large_residual():
+    n, batch = 1024, 8
+    a, b, c = synth.diag_dominant_tri(4, n, batch)
+    f = synth.uniform(3, n * batch, -1.0, 1.0)
+    x = oracle.tri_cyclic_batch(a, b, c, f, batch)
+    res = spectral.tri_matvec_interleaved(a, b, c, x, batch) - f
+    assert np.max(np.abs(res)) <= 1e-14 * np.max(np.abs(f)) * 10
+
+
+# --------------------------------------------------------------------------- stencil
+def _lap5(h):
+    return np.array([[0, 1, 0], [1, -4, 1], [0, 1, 0]], dtype=float) / h**2
+
+
+def test_stencil_laplacian_exact_on_quadratics():
+    nx, ny, h = 20, 17, 0.1
+    y, x = np.meshgrid(np.arange(ny) * h, np.arange(nx) * h, indexing="ij")
+    f = 1.5 * x**2 + 3 * x * y - 2 * y**2 + x - 4 * y + 0.5
+    out = oracle.stencil_apply_2d(f, _lap5(h), 1, 1, 1, 1, periodic=False)
+    inner = out[1:-1, 1:-1]
+    assert np.allclose(inner, 3.0 - 4.0, atol=1e-9)
+    # the untouched border stays at the incoming value (zeros here)
+    assert np.all(out[0, :] == 0) and np.all(out[:, -1] == 0)
+
+
+def test_stencil_biharmonic_exact_on_quartics():
+    # 13-point biharmonic (dxxxx + 2 dxxyy + dyyyy) is exact on quartic polynomials
+    nx, ny, h = 16, 15, 0.5
+    w = np.zeros((5, 5))
+    w[2, :] += np.array([1, -4, 6, -4, 1])
+    w[:, 2] += np.array([1, -4, 6, -4, 1])
+    w[1:4, 1:4] += 2 * np.array([[1, -2, 1], [-2, 4, -2], [1, -2, 1]])
+    w /= h**4
+    y, x = np.meshgrid(np.arange(ny) * h, np.arange(nx) * h, indexing="ij")
+    f = x**4 + 2 * x**2 * y**2 - 3 * y**4 + x**3 * y + 5 * x * y
+    # d4/dx4 = 24, 2 d4/dx2dy2 = 2*8 = 16, d4/dy4 = -72
+    out = oracle.stencil_apply_2d(f, w, 2, 2, 2, 2, periodic=False)
+    assert np.allclose(out[2:-2, 2:-2], 24 + 16 - 72, rtol=0, atol=1e-8)
+
+
+@pytest.mark.parametrize("kx,ky", [(1, 0), (3, 2), (7, 5)])
+def test_stencil_periodic_fourier_symbol(kx, ky):
+    nx, ny = 32, 24
+    lx, ly = 2 * np.pi, 3.0
+    dx, dy = lx / nx, ly / ny
+    y, x = np.meshgrid(np.arange(ny) * dy, np.arange(nx) * dx, indexing="ij")
+    th = 2 * np.pi * (kx * x / lx + ky * y / ly)
+    f = np.cos(th)
+    w = np.array([[0, 1 / dy**2, 0], [1 / dx**2, -2 / dx**2 - 2 / dy**2, 1 / dx**2], [0, 1 / dy**2, 0]])
+    out = oracle.stencil_apply_2d(f, w, 1, 1, 1, 1)
+    sym = -4 * np.sin(np.pi * kx / nx) ** 2 / dx**2 - 4 * np.sin(np.pi * ky / ny) ** 2 / dy**2
+    assert np.max(np.abs(out - sym * f)) <= 1e-12 * max(1.0, abs(sym))
+
+
+def test_stencil_asymmetric_box_matches_shifts():
+    nx, ny = 19, 11
+    left, right, top, bottom = 3, 1, 0, 2
+    f = synth.field(5, ny, nx, -1, 1)
+    w = synth.uniform(6, (top + bottom + 1) * (left + right + 1), -1, 1).reshape(top + bottom + 1, -1)
+    for premap in (False, True):
+        out = oracle.stencil_apply_2d(f, w, left, right, top, bottom, premap=premap)
+        g = f**3 - f if premap else f
+        ref = np.zeros_like(f)
+        for dj in range(-top, bottom + 1):
+            for di in range(-left, right + 1):
+                ref += w[dj + top, di + left] * np.roll(np.roll(g, -dj, axis=0), -di, axis=1)
+        assert np.max(np.abs(out - ref)) <= 1e-14 * 20
+
+
+def test_stencil_premap_constant_field():
+    f = np.full((9, 10), 0.7)
+    w = np.arange(9, dtype=float).reshape(3, 3)
+    out = oracle.stencil_apply_2d(f, w, 1, 1, 1, 1, premap=True)
+    assert np.allclose(out, (0.7**3 - 0.7) * w.sum(), rtol=1e-14)
+
+
+# --------------------------------------------------------------------------- ch_step
+def test_ch_step_matches_spectral_form():
+    ny, nx = 24, 32
+    lx, ly, gamma, dt = 2 * np.pi, 1.7 * np.pi, 0.01, 1e-3
+    cn = synth.field(0, ny, nx, -0.1, 0.1)
+    cp = synth.field(1, ny, nx, -0.1, 0.1)
+    got, prev = oracle.ch_step(cn, cp, lx, ly, gamma, dt)
+    ref = spectral.ch_step_spectral(cn, cp, lx, ly, gamma, dt)
+    assert np.array_equal(prev, cn)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_ch_step_stiff_matches_spectral_form():
+    # large a' (stiff implicit part), non-square and anisotropic spacing
+    ny, nx = 40, 64
+    lx, ly, gamma, dt = 2 * np.pi, np.pi, 0.005, 5e-3
+    cn = synth.field(2, ny, nx, -0.6, 0.6)
+    cp = cn + 0.01 * synth.field(3, ny, nx, -1, 1)
+    got, _ = oracle.ch_step(cn, cp, lx, ly, gamma, dt)
+    ref = spectral.ch_step_spectral(cn, cp, lx, ly, gamma, dt)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def _amplification(kx, ky, nx, ny, lx, ly, gamma, dt):
+    dx, dy = lx / nx, ly / ny
+    px = 4 * np.sin(np.pi * kx / nx) ** 2 / dx**2
+    py = 4 * np.sin(np.pi * ky / ny) ** 2 / dy**2
+    lam = -(px + py)
+    g = (2 / 3) * gamma * dt
+    P = (1 + g * px**2) * (1 + g * py**2)
+    A = 2 + (-2 / 3 - 2 * g * lam**2 - (2 / 3) * dt * lam) / P
+    B = -1 + (2 / 3 + g * lam**2) / P
+    return A, B
+
+
+@pytest.mark.parametrize("kx,ky", [(0, 0), (1, 0), (2, 3), (5, 4), (9, 1)])
+def test_ch_step_linear_mode_closed_form(kx, ky):
+    # single small mode: the cubic term is O(eps^3), so amplitudes follow
+    # c^{n+1} = A c^n + B c^{n-1} with A, B from the symbols of the scheme
+    nx, ny, lx, ly, gamma, dt, eps = 32, 24, 2 * np.pi, 2 * np.pi, 0.01, 2e-3, 1e-8
+    y, x = np.meshgrid(np.arange(ny) * ly / ny, np.arange(nx) * lx / nx, indexing="ij")
+    mode = np.cos(kx * x * 2 * np.pi / lx + ky * y * 2 * np.pi / ly)
+    cn = eps * mode
+    cp = cn.copy()
+    A, B = _amplification(kx, ky, nx, ny, lx, ly, gamma, dt)
+    an, ap = eps, eps
+    for _ in range(25):
+        cn, cp = oracle.ch_step(cn, cp, lx, ly, gamma, dt)
+        an, ap = A * an + B * ap, an
+        assert np.max(np.abs(cn - an * mode)) <= 1e-11 * max(abs(an), eps)
+    if kx == 0 and ky == 0:
+        assert A == pytest.approx(4 / 3) and B == pytest.approx(-1 / 3)
+
+
+@pytest.mark.parametrize("k", [1, 3, 5, 7, 10])
+def test_linear_growth_rate_continuum_limit(k):
+    # dominant root of l^2 = A l + B approaches exp(sigma dt), sigma = k^2 - gamma k^4
+    nx = ny = 512
+    gamma, dt = 0.01, 1e-5
+    A, B = _amplification(k, 0, nx, ny, 2 * np.pi, 2 * np.pi, gamma, dt)
+    lam = (A + np.sqrt(A * A + 4 * B)) / 2
+    sigma = k**2 - gamma * k**4
+    # O(dx^2, dt) discretisation error, measured against the size of the terms (k^2)
+    assert abs(np.log(lam) / dt - sigma) <= 2e-3 * k**2
+
+
+def test_ch_mass_conserved_and_energy_decays():
+    ny = nx = 48
+    lx = ly = 2 * np.pi
+    gamma, dt = 0.01, 1e-3
+    c0 = synth.field(0, ny, nx, -0.1, 0.1) + 0.05
+    m0, e0 = oracle.ch_diagnostics(c0, lx, ly, gamma)
+    cn, cp = oracle.ch_run(c0, c0, lx, ly, gamma, dt, 200)
+    m1, e1 = oracle.ch_diagnostics(cn, lx, ly, gamma)
+    scale = np.sum(np.abs(c0)) * (lx / nx) * (ly / ny)
+    assert abs(m1 - m0) <= 1e-13 * scale * 10
+    assert e1 < e0
+
+
+def test_ch_odd_symmetry_bit_exact():
+    ny, nx = 16, 20
+    cn = synth.field(4, ny, nx, -0.5, 0.5)
+    cp = synth.field(5, ny, nx, -0.5, 0.5)
+    a, _ = oracle.ch_run(cn, cp, 2 * np.pi, 2 * np.pi, 0.01, 1e-3, 3)
+    b, _ = oracle.ch_run(-cn, -cp, 2 * np.pi, 2 * np.pi, 0.01, 1e-3, 3)
+    assert np.array_equal(a, -b)
+
+
+def test_ch_shift_and_transpose_equivariance():
+    n = 24
+    cn = synth.field(6, n, n, -0.5, 0.5)
+    cp = cn.copy()
+    args = (2 * np.pi, 2 * np.pi, 0.01, 1e-3)
+    base, _ = oracle.ch_run(cn, cp, *args, 4)
+    sh, _ = oracle.ch_run(np.roll(cn, (3, -5), (0, 1)), np.roll(cp, (3, -5), (0, 1)), *args, 4)
+    assert np.max(np.abs(np.roll(base, (3, -5), (0, 1)) - sh)) <= 1e-13
+    tr, _ = oracle.ch_run(cn.T.copy(), cp.T.copy(), *args, 4)
+    assert np.max(np.abs(base.T - tr)) <= 1e-13
+
+
+def test_ch_constant_state_is_fixed():
+    c = np.full((12, 10), 0.3)
+    got, _ = oracle.ch_run(c, c, 2 * np.pi, 2 * np.pi, 0.01, 1e-3, 5)
+    assert np.max(np.abs(got - 0.3)) <= 1e-15
+
+
+# --------------------------------------------------------------------------- diagnostics
+def test_diagnostics_closed_forms():
+    nx, ny, lx, ly, gamma = 64, 32, 2 * np.pi, 1.0, 0.02
+    dx, dy = lx / nx, ly / ny
+    m, e = oracle.ch_diagnostics(np.ones((ny, nx)), lx, ly, gamma)
+    assert m == pytest.approx(lx * ly, rel=1e-14) and e == 0.0
+    amp, k = 0.8, 3
+    th = 2 * np.pi * k * np.arange(nx) / nx
+    c = np.tile(amp * np.cos(th), (ny, 1))
+    m, e = oracle.ch_diagnostics(c, lx, ly, gamma)
+    assert abs(m) <= 1e-13
+    # sum cos^2 = n/2, sum cos^4 = 3n/8 (k not 0, n/4, n/2); sum (c_{i+1}-c_i)^2 = amp^2 n (1 - cos(2 pi k/n))
+    bulk = 0.25 * ny * (amp**4 * 3 * nx / 8 - 2 * amp**2 * nx / 2 + nx)
+    grad = 0.5 * gamma * ny * amp**2 * nx * (1 - np.cos(2 * np.pi * k / nx)) / dx**2
+    assert e == pytest.approx((bulk + grad) * dx * dy, rel=1e-12)
+
+
+def test_synth_torch_matches_numpy():
+    torch = pytest.importorskip("torch")
+    a = synth.uniform(123, 1000, -1, 1, offset=17)
+    b = synth.uniform_torch(123, 1000, -1, 1, device="cpu", offset=17).numpy()
+    assert np.array_equal(a, b)
