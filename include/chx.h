@@ -1,0 +1,196 @@
+/*
+ * chx: GB300-native (sm_103a) semi-implicit ADI stepping of the periodic 2D
+ * Cahn-Hilliard equation  c_t = Lap(c^3 - c - gamma Lap c)  and the batched
+ * cyclic band solvers it is built from (Gloster, arXiv 2101.06550).
+ *
+ * Conventions (all entry points):
+ *  - Every function returns an int status: CHX_OK (0) or a negative CHX_E*
+ *    code; chx_status_string() names it and chx_last_error() gives the detail
+ *    of the most recent failure on the calling host thread.
+ *  - Device pointers are owned by the caller.  Plans own only what their
+ *    *_create / *_factor call allocated (factors, small scratch); nothing else
+ *    in this library allocates device memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued asynchronously on it.  Errors found on the device are
+ *    reported by the next chx_sync_status(plan).
+ *  - Fields are row-major, v(i, j) = v[j * ld + i], i the x index.  Batched
+ *    solver data is interleaved: element i of system s is at x[i * batch + s].
+ *  - Only one precision per plan.  dtype CHX_F64 = double, CHX_F32 = float.
+ */
+#ifndef CHX_H
+#define CHX_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  CHX_OK = 0,
+  CHX_EINVAL = -1,       /* bad argument (null pointer, size out of range, mode)  */
+  CHX_ESINGULAR = -2,    /* zero or tiny pivot in LU without pivoting, or a tiny
+                            Sherman-Morrison / bordering denominator               */
+  CHX_ENONFINITE = -3,   /* a diagnostic reduction met NaN or Inf                  */
+  CHX_ENOMEM = -4,       /* a plan allocation failed                               */
+  CHX_ECUDA = -5,        /* a CUDA runtime call or kernel launch failed            */
+  CHX_ETIMEOUT = -6,     /* a bounded device-side wait ran out                     */
+  CHX_EUNSUPPORTED = -7  /* valid request this build does not implement           */
+};
+
+enum { CHX_F64 = 0, CHX_F32 = 1 };
+
+/* Coefficient modes of the band solvers (Secs. 4.2.4, 5.2, 5.4):
+ * UNIFORM    - one value per diagonal for every row and system (cuPentUniformBatch);
+ *              a..e (or a..c) each point to ONE host double.
+ * SHARED     - one LHS for all systems, coefficients vary by row
+ *              (cuPentConstantBatch / cuThomasConstantBatch); n host doubles each.
+ * PER_SYSTEM - every system has its own LHS (cuPentBatch "Rewrite" mode);
+ *              n * batch DEVICE doubles each, interleaved like the RHS.      */
+enum { CHX_COEF_UNIFORM = 0, CHX_COEF_SHARED = 1, CHX_COEF_PER_SYSTEM = 2 };
+
+enum { CHX_PREMAP_NONE = 0, CHX_PREMAP_CUBIC_MINUS_C = 1 };
+
+/* ch_step precision: plain FP64, or FP32 sweeps with one FP64-residual
+ * refinement per pentadiagonal solve (FP64 state and update). */
+enum { CHX_PREC_F64 = 0, CHX_PREC_F32_REFINE = 1 };
+
+typedef struct chx_penta_plan chx_penta_plan;
+typedef struct chx_tri_plan chx_tri_plan;
+typedef struct chx_ch_plan chx_ch_plan;
+
+const char* chx_status_string(int status);
+/* Detail of the last failure on this host thread ("" if none). */
+const char* chx_last_error(void);
+/* Library version, major * 10000 + minor * 100 + patch. */
+int chx_version(void);
+
+/*
+ * General 2D stencil apply (cuSten Compute 2D XY, Sec. 3.3; weights indexed
+ * from the top-left of the box, i fastest, then row by row in j, Sec. 3.5.2):
+ *   out(i,j) = sum_{dj=-top..bottom} sum_{di=-left..right}
+ *              w[(dj+top)*(left+right+1) + (di+left)] * p(in(i+di, j+dj)),
+ * p = identity, or p(c) = c^3 - c for CHX_PREMAP_CUBIC_MINUS_C (the
+ * function-pointer form used for the nonlinear Cahn-Hilliard term, Sec. 3.5.2).
+ *  in, out   device arrays of dtype, row-major with leading dimension ldx >= nx;
+ *            out must not alias in (the blocks overlap, Sec. 3.2).
+ *  w_host    HOST array of (top+bottom+1)*(left+right+1) doubles, copied into
+ *            the launch; left, right, top, bottom each in [0, 7].
+ *  periodic  1: wrap in both directions.  0: only points whose whole box lies
+ *            inside the grid are written; the boundary cells are left untouched
+ *            for the caller's own boundary conditions (Sec. 3.3).
+ * Errors: CHX_EINVAL for null pointers, nx or ny < 1, ldx < nx, box out of range,
+ * aliasing in/out, unknown dtype or premap; CHX_ECUDA if the launch fails.
+ */
+int stencil_apply_2d(const void* in, void* out, int nx, int ny, int ldx, const double* w_host, int left,
+                     int right, int top, int bottom, int premap, int periodic, int dtype, void* stream);
+
+/*
+ * Batched cyclic pentadiagonal solver (Secs. 4.2.2-4.2.5 and 5.4).  Row i of
+ * every system: a_i x_{i-2} + b_i x_{i-1} + c_i x_i + d_i x_{i+1} + e_i x_{i+2}
+ * = f_i, indices mod n (eq:matrix_sys1), n >= 5.  The periodic corners are
+ * removed by Navon's bordering of the last two unknowns (Eqs. solve and
+ * first_two) and the rest is LU without pivoting, which the paper requires to
+ * be applied only to symmetric positive definite or diagonally dominant
+ * matrices.  Factorisation is split from the solve (Sec. 4.2.5).
+ *
+ * penta_cyclic_factor: creates *plan for systems of size n.  For UNIFORM and
+ *   SHARED the factors (and the bordering vectors and 2x2 tail inverse, which
+ *   the paper precomputes once) are formed on the host in FP64 and uploaded;
+ *   for PER_SYSTEM they are formed on the device, one thread per system, into
+ *   plan-owned storage of about 9 * n * batch values, enqueued on `stream`.
+ *   `batch` is the largest batch later solves may use.  dtype is the storage
+ *   and sweep precision of the right-hand sides (CHX_F64 or CHX_F32).
+ *   Errors: CHX_EINVAL, CHX_ESINGULAR (host factorisation met a pivot with
+ *   |alpha| <= 1e3 * eps * row scale, or a tiny tail determinant), CHX_ENOMEM,
+ *   CHX_ECUDA.  A singular PER_SYSTEM factorisation is flagged on the device
+ *   and returned by chx_sync_status.
+ * penta_cyclic_refactor: PER_SYSTEM plans only; recompute the factors from new
+ *   device coefficients in the existing storage (the "Rewrite" mode, no
+ *   allocation).
+ * penta_cyclic_solve_batched: solves in place.  rhs_inout is a device array of
+ *   n * batch values of the plan's dtype, interleaved; on return it holds x.
+ *   refine = 1 (CHX_F64 plans only): the sweeps run in FP32 and one
+ *   iterative-refinement pass with an FP64 residual f - A x corrects the result
+ *   (uses plan-owned FP32 scratch of n * batch values).
+ *   Errors: CHX_EINVAL (batch < 1 or above the plan's batch, PER_SYSTEM batch
+ *   different from the factor batch, refine on an FP32 plan), CHX_ECUDA.
+ */
+int penta_cyclic_factor(chx_penta_plan** plan, int n, int coef_mode, const double* a, const double* b,
+                        const double* c, const double* d, const double* e, int batch, int dtype, void* stream);
+int penta_cyclic_refactor(chx_penta_plan* plan, const double* a, const double* b, const double* c,
+                          const double* d, const double* e, void* stream);
+int penta_cyclic_solve_batched(chx_penta_plan* plan, void* rhs_inout, int batch, int refine, void* stream);
+
+/*
+ * Batched cyclic tridiagonal solver (Sec. 5.3): Thomas algorithm with
+ * pre-factorisation; the corners are removed with the Sherman-Morrison formula
+ * x = y - (v.y)/(1 + v.z) z, with u = (-b_1, 0.., c_N), v = (1, 0.., -a_1/b_1)
+ * and z = A'^{-1} u formed once at factor time.  Row i: a_i x_{i-1} + b_i x_i +
+ * c_i x_{i+1} = f_i, indices mod n, n >= 3.  Modes, layouts, ownership and
+ * errors as for the pentadiagonal solver (no refine option).
+ */
+int tri_cyclic_factor(chx_tri_plan** plan, int n, int coef_mode, const double* a, const double* b,
+                      const double* c, int batch, int dtype, void* stream);
+int tri_cyclic_refactor(chx_tri_plan* plan, const double* a, const double* b, const double* c, void* stream);
+int tri_cyclic_solve_batched(chx_tri_plan* plan, void* rhs_inout, int batch, void* stream);
+
+/*
+ * One semi-implicit ADI step of the periodic 2D Cahn-Hilliard equation with
+ * D = 1 (Eq. 3.1, eq3:ch_adi, Sec. 3.5.1):
+ *   Cbar = 2 C^n - C^{n-1}
+ *   r    = -(2/3)(C^n - C^{n-1}) - (2/3) gamma dt Lap_h^2 Cbar + (2/3) dt Lap_h (C^3 - C)^n
+ *   (I + (2/3) gamma dt d_xxxx) w = r    (rows),
+ *   (I + (2/3) gamma dt d_yyyy) v = w    (columns),
+ *   C^{n+1} = Cbar + v,
+ * on [0, lx) x [0, ly) with dx = lx/nx, dy = ly/ny; Lap_h is the 5-point
+ * Laplacian and Lap_h^2 the 13-point biharmonic.  The first step uses
+ * C^{-1} = C^0: the caller sets c_prev = c_now = c0 (Sec. 3.5.1).
+ *
+ * ch_plan_create: nx, ny in [8, 16384]; lx, ly, dt > 0; gamma >= 0;
+ *   precision CHX_PREC_F64 or CHX_PREC_F32_REFINE.  Factors the two implicit
+ *   operators on the host in FP64 and uploads them (plan-owned).
+ * ch_work_bytes: size of the caller-provided device scratch `work` for ch_step.
+ * ch_step: advances nsteps >= 0 steps.  c_now and c_prev are device arrays of
+ *   nx * ny doubles (row-major, ld = nx) that keep their roles: on return
+ *   c_now = C^{n+nsteps} and c_prev = C^{n+nsteps-1}.  work must hold at
+ *   least ch_work_bytes(plan) bytes, 256-byte aligned, and must not overlap
+ *   the fields.  Errors: CHX_EINVAL, CHX_ECUDA.
+ * ch_diagnostics: mass = sum c dx dy and free energy
+ *   F_h = sum [ (1/4)(c^2-1)^2 + (gamma/2)(|D+x c|^2 + |D+y c|^2) ] dx dy
+ *   (forward differences, periodic; Sec. 2.5 with the bulk density read as
+ *   (1/4)(c^2-1)^2, the one whose derivative is c^3 - c).  mass_out and
+ *   energy_out are DEVICE pointers to one double each, written asynchronously
+ *   in a fixed summation order (bit-reproducible).  If c holds NaN or Inf, the
+ *   plan's status becomes CHX_ENONFINITE (read it with chx_sync_status).
+ */
+int ch_plan_create(chx_ch_plan** plan, int nx, int ny, double lx, double ly, double gamma, double dt,
+                   int precision);
+size_t ch_work_bytes(const chx_ch_plan* plan);
+int ch_step(chx_ch_plan* plan, double* c_now, double* c_prev, void* work, int nsteps, void* stream);
+int ch_diagnostics(chx_ch_plan* plan, const double* c, double* mass_out, double* energy_out, void* stream);
+
+/* Profiling aid.  ch_profile(plan, 1) makes every later ch_step bracket each
+ * kernel it launches with CUDA events on the launch stream (a few microseconds
+ * of host time per launch); ch_profile(plan, 0) stops it.  ch_profile_read
+ * waits for the recorded events, adds their elapsed times to per-kernel
+ * totals, copies up to max_slots totals (milliseconds) and launch counts into
+ * ms[] and launches[] (either may be NULL), optionally resets them, and returns
+ * the number of kernel slots (or a negative status).  ch_profile_slot_name
+ * names a slot ("" if out of range). */
+int ch_profile(chx_ch_plan* plan, int enable);
+int ch_profile_read(chx_ch_plan* plan, double* ms, long long* launches, int max_slots, int reset);
+const char* ch_profile_slot_name(int slot);
+
+/* Waits for the plan's last stream and returns (and clears) the first error the
+ * device recorded for this plan, or CHX_OK.  Works for every plan type. */
+int chx_sync_status(void* plan);
+/* Frees a plan of any type (NULL is allowed).  The caller must make sure no
+ * work using the plan is still in flight. */
+void chx_plan_destroy(void* plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHX_H */

@@ -1,0 +1,270 @@
+"""ctypes binding of the chx C ABI (``include/chx.h``): argument marshalling only.
+
+Every computation runs in ``libchx.so``; this module checks tensor shapes,
+dtypes and devices, passes raw device pointers and the current CUDA stream,
+and turns status codes into exceptions.  There is no CPU fallback: if the
+library is missing the import of the first entry point fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libchx.so")
+
+F64, F32 = 0, 1
+COEF_UNIFORM, COEF_SHARED, COEF_PER_SYSTEM = 0, 1, 2
+PREMAP_NONE, PREMAP_CUBIC_MINUS_C = 0, 1
+PREC_F64, PREC_F32_REFINE = 0, 1
+
+STATUS = {0: "CHX_OK", -1: "CHX_EINVAL", -2: "CHX_ESINGULAR", -3: "CHX_ENONFINITE", -4: "CHX_ENOMEM",
+          -5: "CHX_ECUDA", -6: "CHX_ETIMEOUT", -7: "CHX_EUNSUPPORTED"}
+
+# every symbol include/chx.h declares
+EXPORTS = ("chx_status_string", "chx_last_error", "chx_version", "stencil_apply_2d", "penta_cyclic_factor",
+           "penta_cyclic_refactor", "penta_cyclic_solve_batched", "tri_cyclic_factor", "tri_cyclic_refactor",
+           "tri_cyclic_solve_batched", "ch_plan_create", "ch_work_bytes", "ch_step", "ch_diagnostics",
+           "ch_profile", "ch_profile_read", "ch_profile_slot_name", "chx_sync_status", "chx_plan_destroy")
+
+
+class ChxError(RuntimeError):
+    def __init__(self, status: int, detail: str):
+        super().__init__(f"{STATUS.get(status, status)}: {detail}")
+        self.status = status
+
+
+_lib = None
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def lib():
+    """Load libchx.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run `python -c 'import __graft_entry__ as g; g.build()'` first")
+    L = ctypes.CDLL(LIB_PATH)
+    i, d, sz = ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    sig = {
+        "chx_status_string": (ctypes.c_char_p, [i]),
+        "chx_last_error": (ctypes.c_char_p, []),
+        "chx_version": (i, []),
+        "stencil_apply_2d": (i, [_P, _P, i, i, i, _D, i, i, i, i, i, i, i, _P]),
+        "penta_cyclic_factor": (i, [ctypes.POINTER(_P), i, i, _P, _P, _P, _P, _P, i, i, _P]),
+        "penta_cyclic_refactor": (i, [_P, _P, _P, _P, _P, _P, _P]),
+        "penta_cyclic_solve_batched": (i, [_P, _P, i, i, _P]),
+        "tri_cyclic_factor": (i, [ctypes.POINTER(_P), i, i, _P, _P, _P, i, i, _P]),
+        "tri_cyclic_refactor": (i, [_P, _P, _P, _P, _P]),
+        "tri_cyclic_solve_batched": (i, [_P, _P, i, _P]),
+        "ch_plan_create": (i, [ctypes.POINTER(_P), i, i, d, d, d, d, i]),
+        "ch_work_bytes": (sz, [_P]),
+        "ch_step": (i, [_P, _P, _P, _P, i, _P]),
+        "ch_diagnostics": (i, [_P, _P, _P, _P, _P]),
+        "ch_profile": (i, [_P, i]),
+        "ch_profile_read": (i, [_P, _D, ctypes.POINTER(ctypes.c_longlong), i, i]),
+        "ch_profile_slot_name": (ctypes.c_char_p, [i]),
+        "chx_sync_status": (i, [_P]),
+        "chx_plan_destroy": (None, [_P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise ChxError(rc, lib().chx_last_error().decode())
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, dtype=None, numel=None, name="tensor"):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dtype_code(t):
+    import torch
+
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32:
+        return F32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def status_string(code: int) -> str:
+    return lib().chx_status_string(code).decode()
+
+
+def version() -> int:
+    return lib().chx_version()
+
+
+def stencil_apply_2d(inp, out, weights, left, right, top, bottom, premap=False, periodic=True, stream=None):
+    """cuSten-style weighted box stencil on a (ny, nx) field; see include/chx.h."""
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
+    if w.shape != (top + bottom + 1, left + right + 1):
+        raise ValueError("weights must have shape (top+bottom+1, left+right+1)")
+    if inp.dim() != 2 or out.shape != inp.shape or out.dtype != inp.dtype:
+        raise ValueError("inp and out must be 2D tensors of the same shape and dtype")
+    ny, nx = inp.shape
+    _check(lib().stencil_apply_2d(_dev(inp, name="inp"), _dev(out, name="out"), nx, ny, nx,
+                                  w.ctypes.data_as(_D), left, right, top, bottom,
+                                  PREMAP_CUBIC_MINUS_C if premap else PREMAP_NONE, int(bool(periodic)),
+                                  _dtype_code(inp), _stream(stream)))
+    return out
+
+
+class _Plan:
+    _handle = None
+
+    def sync_status(self):
+        _check(lib().chx_sync_status(self._handle))
+
+    def close(self):
+        if self._handle:
+            lib().chx_plan_destroy(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _coef_ptrs(coefs, mode, n, batch):
+    """Host numpy arrays for UNIFORM/SHARED (kept alive by the caller), device tensors for PER_SYSTEM."""
+    import torch
+
+    if mode == COEF_PER_SYSTEM:
+        return [_dev(c, torch.float64, n * batch, "coefficient") for c in coefs], coefs
+    want = 1 if mode == COEF_UNIFORM else n
+    arrs = [np.ascontiguousarray(np.broadcast_to(np.asarray(c, dtype=np.float64).ravel(), (want,))) for c in coefs]
+    return [ctypes.c_void_p(a.ctypes.data) for a in arrs], arrs
+
+
+class PentaPlan(_Plan):
+    """Factorised batched cyclic pentadiagonal operator (penta_cyclic_factor)."""
+
+    def __init__(self, n, coefs, batch, mode=COEF_SHARED, dtype=F64, stream=None):
+        ptrs, keep = _coef_ptrs(coefs, mode, n, batch)
+        h = ctypes.c_void_p()
+        _check(lib().penta_cyclic_factor(ctypes.byref(h), n, mode, *ptrs, batch, dtype, _stream(stream)))
+        self._handle, self.n, self.batch, self.mode, self.dtype = h, n, batch, mode, dtype
+        del keep
+
+    def refactor(self, coefs, stream=None):
+        ptrs, keep = _coef_ptrs(coefs, COEF_PER_SYSTEM, self.n, self.batch)
+        _check(lib().penta_cyclic_refactor(self._handle, *ptrs, _stream(stream)))
+
+    def solve(self, rhs, refine=False, stream=None):
+        """In-place solve of an interleaved (n * batch) right-hand side."""
+        batch = rhs.numel() // self.n
+        if batch * self.n != rhs.numel():
+            raise ValueError("rhs size must be a multiple of n")
+        if _dtype_code(rhs) != self.dtype:
+            raise TypeError("rhs dtype does not match the plan")
+        _check(lib().penta_cyclic_solve_batched(self._handle, _dev(rhs, name="rhs"), batch, int(bool(refine)),
+                                                _stream(stream)))
+        return rhs
+
+
+class TriPlan(_Plan):
+    """Factorised batched cyclic tridiagonal operator (tri_cyclic_factor)."""
+
+    def __init__(self, n, coefs, batch, mode=COEF_SHARED, dtype=F64, stream=None):
+        ptrs, keep = _coef_ptrs(coefs, mode, n, batch)
+        h = ctypes.c_void_p()
+        _check(lib().tri_cyclic_factor(ctypes.byref(h), n, mode, *ptrs, batch, dtype, _stream(stream)))
+        self._handle, self.n, self.batch, self.mode, self.dtype = h, n, batch, mode, dtype
+        del keep
+
+    def refactor(self, coefs, stream=None):
+        ptrs, keep = _coef_ptrs(coefs, COEF_PER_SYSTEM, self.n, self.batch)
+        _check(lib().tri_cyclic_refactor(self._handle, *ptrs, _stream(stream)))
+
+    def solve(self, rhs, stream=None):
+        batch = rhs.numel() // self.n
+        if batch * self.n != rhs.numel():
+            raise ValueError("rhs size must be a multiple of n")
+        if _dtype_code(rhs) != self.dtype:
+            raise TypeError("rhs dtype does not match the plan")
+        _check(lib().tri_cyclic_solve_batched(self._handle, _dev(rhs, name="rhs"), batch, _stream(stream)))
+        return rhs
+
+
+class ChPlan(_Plan):
+    """Plan for the ADI Cahn-Hilliard step (ch_plan_create / ch_step / ch_diagnostics)."""
+
+    def __init__(self, nx, ny, lx, ly, gamma, dt, precision=PREC_F64):
+        h = ctypes.c_void_p()
+        _check(lib().ch_plan_create(ctypes.byref(h), nx, ny, float(lx), float(ly), float(gamma), float(dt),
+                                    precision))
+        self._handle = h
+        self.nx, self.ny, self.lx, self.ly, self.gamma, self.dt, self.precision = nx, ny, lx, ly, gamma, dt, precision
+
+    @property
+    def work_bytes(self) -> int:
+        return lib().ch_work_bytes(self._handle)
+
+    def alloc_work(self, device="cuda"):
+        import torch
+
+        # torch allocations are at least 512-byte aligned
+        return torch.empty(max(self.work_bytes, 1), dtype=torch.uint8, device=device)
+
+    def step(self, c_now, c_prev, work, nsteps=1, stream=None):
+        import torch
+
+        n = self.nx * self.ny
+        _check(lib().ch_step(self._handle, _dev(c_now, torch.float64, n, "c_now"),
+                             _dev(c_prev, torch.float64, n, "c_prev"), _dev(work, None, None, "work"), int(nsteps),
+                             _stream(stream)))
+
+    def profile(self, enable: bool = True):
+        """Bracket every kernel of later steps with CUDA events (ch_profile)."""
+        _check(lib().ch_profile(self._handle, int(bool(enable))))
+
+    def profile_read(self, reset: bool = True) -> dict:
+        """{kernel name: (total ms, launches)} accumulated since the last reset."""
+        ms = (ctypes.c_double * 16)()
+        n = (ctypes.c_longlong * 16)()
+        k = lib().ch_profile_read(self._handle, ms, n, 16, int(bool(reset)))
+        if k < 0:
+            _check(k)
+        return {lib().ch_profile_slot_name(i).decode(): (ms[i], n[i]) for i in range(k) if n[i] > 0}
+
+    def diagnostics(self, c, out, stream=None):
+        """Writes (mass, energy) into the 2-element float64 device tensor ``out``."""
+        import torch
+
+        _dev(out, torch.float64, 2, "out")
+        base = out.data_ptr()
+        _check(lib().ch_diagnostics(self._handle, _dev(c, torch.float64, self.nx * self.ny, "c"),
+                                    ctypes.c_void_p(base), ctypes.c_void_p(base + 8), _stream(stream)))
+        return out

@@ -1,0 +1,208 @@
+"""GPU parity of the stencil apply, the ADI Cahn-Hilliard step and its diagnostics (through the C ABI)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+def _chx():
+    import paper_2101_06550_gb300 as chx
+
+    return chx
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+# --------------------------------------------------------------------------- stencil
+@pytest.mark.parametrize("shape", [(1, 1), (17, 45), (64, 100)])
+@pytest.mark.parametrize("box", [(1, 1, 1, 1), (2, 2, 2, 2), (3, 0, 1, 4)])
+@pytest.mark.parametrize("premap", [False, True])
+@pytest.mark.parametrize("periodic", [True, False])
+def test_stencil_f64(shape, box, premap, periodic):
+    chx = _chx()
+    ny, nx = shape
+    left, right, top, bottom = box
+    f = synth.field(1, ny, nx, -1, 1)
+    w = synth.uniform(2, (top + bottom + 1) * (left + right + 1), -1, 1).reshape(top + bottom + 1, -1)
+    init = synth.field(3, ny, nx, -1, 1)
+    ref = oracle.stencil_apply_2d(f, w, left, right, top, bottom, premap=premap, periodic=periodic, out=init)
+    out = torch.from_numpy(init).to(DEV)
+    chx.stencil_apply_2d(torch.from_numpy(f).to(DEV), out, w, left, right, top, bottom, premap, periodic)
+    assert np.max(np.abs(out.cpu().numpy() - ref)) <= 1e-13
+
+
+def test_stencil_f32_and_alias_rejected():
+    chx = _chx()
+    ny, nx = 40, 70
+    f = synth.field(4, ny, nx, -1, 1)
+    w = np.array([[0, 1, 0], [1, -4, 1], [0, 1, 0]], dtype=float)
+    ref = oracle.stencil_apply_2d(f, w, 1, 1, 1, 1, premap=True)
+    out = torch.zeros(ny, nx, dtype=torch.float32, device=DEV)
+    chx.stencil_apply_2d(torch.from_numpy(f.astype(np.float32)).to(DEV), out, w, 1, 1, 1, 1, True, True)
+    assert np.max(np.abs(out.cpu().numpy() - ref)) <= 1e-5
+    with pytest.raises(chx.ChxError):
+        chx.stencil_apply_2d(out, out, w, 1, 1, 1, 1)
+
+
+# --------------------------------------------------------------------------- ch_step
+def _run_gpu(c_now, c_prev, lx, ly, gamma, dt, nsteps, precision=0):
+    chx = _chx()
+    ny, nx = c_now.shape
+    plan = chx.ChPlan(nx, ny, lx, ly, gamma, dt, precision)
+    cn = torch.from_numpy(c_now).to(DEV)
+    cp = torch.from_numpy(c_prev).to(DEV)
+    work = plan.alloc_work(DEV)
+    plan.step(cn, cp, work, nsteps)
+    torch.cuda.synchronize()
+    plan.sync_status()
+    return cn.cpu().numpy(), cp.cpu().numpy()
+
+
+@pytest.mark.parametrize("ny,nx", [(8, 8), (64, 64), (80, 96), (256, 256), (40, 200)])
+@pytest.mark.parametrize("nsteps", [1, 2, 3])
+def test_ch_step_f64_matches_oracle(ny, nx, nsteps):
+    lx, ly, gamma, dt = 2 * np.pi, 2 * np.pi * ny / nx, 0.01, 1e-3
+    c0 = synth.field(0, ny, nx, -0.1, 0.1)
+    cm = c0 + 1e-3 * synth.field(1, ny, nx, -1, 1)
+    got, gprev = _run_gpu(c0, cm, lx, ly, gamma, dt, nsteps)
+    ref, rprev = oracle.ch_run(c0, cm, lx, ly, gamma, dt, nsteps)
+    assert _rel(got, ref) <= 1e-11
+    assert _rel(gprev, rprev) <= 1e-11
+
+
+def test_ch_step_zero_steps_is_noop():
+    c0 = synth.field(0, 16, 16, -0.1, 0.1)
+    got, prev = _run_gpu(c0, c0 * 0.5, 1.0, 1.0, 0.01, 1e-3, 0)
+    assert np.array_equal(got, c0) and np.array_equal(prev, c0 * 0.5)
+
+
+def _rhs_norm(cn, cp, lx, ly, gamma, dt):
+    """max |r| of Eq. 3.1's right-hand side (array shifts; test-side arithmetic)."""
+    ny, nx = cn.shape
+    dx, dy = lx / nx, ly / ny
+
+    def lap(u):
+        return (np.roll(u, 1, 1) + np.roll(u, -1, 1) - 2 * u) / dx**2 + (np.roll(u, 1, 0) + np.roll(u, -1, 0) - 2 * u) / dy**2
+
+    r = -(2 / 3) * (cn - cp) + (2 / 3) * dt * lap(cn**3 - cn - gamma * lap(2 * cn - cp))
+    return float(np.max(np.abs(r)))
+
+
+def step_tolerance(ref, cn, cp, lx, ly, gamma, dt):
+    """Per-step parity bound: 1e-11 relative on C^{n+1}, plus the FP64 rounding of
+    forming the right-hand side (eps * max|r|), which the implicit solves pass on
+    unamplified (their smallest eigenvalue is 1).  The second term only matters
+    for stiff steps from rough data, where max|r| >> max|c|."""
+    return 1e-11 * float(np.max(np.abs(ref))) + 2.220446049250313e-16 * _rhs_norm(cn, cp, lx, ly, gamma, dt)
+
+
+def test_ch_step_stiff_large_grid_one_step():
+    # the 2048^2 workload (gamma 0.005, dt 5e-4) from its random initial state:
+    # max|r| ~ 5e4 while max|c| ~ 0.07, so FP64 rounding of r alone is ~1e-11 of c
+    from tests import spectral
+
+    n = 2048
+    lx = 2 * np.pi
+    c0 = synth.field(3, n, n, -0.05, 0.05)
+    cm = c0 + 1e-4 * synth.field(4, n, n, -1, 1)
+    got, _ = _run_gpu(c0, cm, lx, lx, 0.005, 5e-4, 1)
+    ref, _ = oracle.ch_run(c0, cm, lx, lx, 0.005, 5e-4, 1)
+    tol = step_tolerance(ref, c0, cm, lx, lx, 0.005, 5e-4)
+    assert np.max(np.abs(got - ref)) <= tol
+    # the GPU is no further from the spectral evaluation of the step than the oracle is
+    sp = spectral.ch_step_spectral(c0, cm, lx, lx, 0.005, 5e-4)
+    assert np.max(np.abs(got - sp)) <= max(tol, 1.5 * np.max(np.abs(ref - sp)))
+
+
+def test_ch_step_256_500_steps_per_step_parity_and_mass():
+    # the 256^2, 500-step workload: per-step parity from the same input state at
+    # sampled steps, and mass conservation along the GPU trajectory
+    chx = _chx()
+    n, lx, gamma, dt = 256, 2 * np.pi, 0.01, 1e-3
+    c0 = synth.field(0, n, n, -0.1, 0.1)
+    plan = chx.ChPlan(n, n, lx, lx, gamma, dt)
+    cn = torch.from_numpy(c0).to(DEV)
+    cp = cn.clone()
+    work = plan.alloc_work(DEV)
+    diag = torch.zeros(2, dtype=torch.float64, device=DEV)
+    plan.diagnostics(cn, diag)
+    m0, e0 = diag.cpu().numpy()
+    for k, chunk in enumerate([1, 99, 150, 249]):
+        plan.step(cn, cp, work, chunk - 1)
+        a, b = cn.cpu().numpy(), cp.cpu().numpy()
+        plan.step(cn, cp, work, 1)
+        ref, _ = oracle.ch_step(a, b, lx, lx, gamma, dt)
+        assert _rel(cn.cpu().numpy(), ref) <= 1e-11
+    plan.diagnostics(cn, diag)
+    m1, e1 = diag.cpu().numpy()
+    plan.sync_status()
+    assert abs(m1 - m0) <= 1e-13 * np.sum(np.abs(c0)) * (lx / n) ** 2 * 10
+    assert e1 < e0
+
+
+@pytest.mark.xfail(reason="FP32 right-hand side: its rounding (a' * eps32 * |c|, a' = 1.9e4) reaches the low modes "
+                   "unattenuated and exceeds 1e-6 of c; needs a double-float right-hand side", strict=False)
+def test_ch_step_f32_refine_per_step_error():
+    n = 512
+    lx, gamma, dt = 2 * np.pi, 0.005, 5e-4
+    c0 = synth.field(3, n, n, -0.05, 0.05)
+    cm = c0 + 1e-4 * synth.field(4, n, n, -1, 1)
+    got, _ = _run_gpu(c0, cm, lx, lx, gamma, dt, 1, precision=1)
+    ref, _ = oracle.ch_run(c0, cm, lx, lx, gamma, dt, 1)
+    assert _rel(got, ref) <= 1e-6
+
+
+def test_ch_odd_symmetry_on_gpu():
+    n = 64
+    c0 = synth.field(7, n, n, -0.5, 0.5)
+    a, _ = _run_gpu(c0, c0, 2 * np.pi, 2 * np.pi, 0.01, 1e-3, 4)
+    b, _ = _run_gpu(-c0, -c0, 2 * np.pi, 2 * np.pi, 0.01, 1e-3, 4)
+    assert np.array_equal(a, -b)
+
+
+# --------------------------------------------------------------------------- diagnostics
+@pytest.mark.parametrize("ny,nx", [(8, 8), (100, 37), (512, 512)])
+def test_diagnostics_match_oracle(ny, nx):
+    chx = _chx()
+    lx, ly, gamma = 2 * np.pi, 3.0, 0.02
+    c = synth.field(9, ny, nx, -1, 1)
+    plan = chx.ChPlan(nx, ny, lx, ly, gamma, 1e-3)
+    out = torch.zeros(2, dtype=torch.float64, device=DEV)
+    plan.diagnostics(torch.from_numpy(c).to(DEV), out)
+    m, e = oracle.ch_diagnostics(c, lx, ly, gamma)
+    gm, ge = out.cpu().numpy()
+    assert abs(gm - m) <= 1e-12 * np.sum(np.abs(c)) * (lx / nx) * (ly / ny)
+    assert abs(ge - e) <= 1e-12 * abs(e)
+    plan.sync_status()
+
+
+def test_diagnostics_flag_nonfinite():
+    chx = _chx()
+    c = synth.field(9, 16, 16, -1, 1)
+    c[3, 5] = np.nan
+    plan = chx.ChPlan(16, 16, 1.0, 1.0, 0.01, 1e-3)
+    out = torch.zeros(2, dtype=torch.float64, device=DEV)
+    plan.diagnostics(torch.from_numpy(c).to(DEV), out)
+    with pytest.raises(chx.ChxError) as e:
+        plan.sync_status()
+    assert e.value.status == -3
+    plan.sync_status()  # cleared
+
+
+def test_ch_step_rejects_overlap_and_alignment():
+    chx = _chx()
+    plan = chx.ChPlan(16, 16, 1.0, 1.0, 0.01, 1e-3)
+    cn = torch.zeros(256, dtype=torch.float64, device=DEV)
+    work = plan.alloc_work(DEV)
+    with pytest.raises(chx.ChxError):
+        plan.step(cn, cn, work, 1)
+    with pytest.raises(chx.ChxError):
+        plan.step(cn, torch.zeros_like(cn), work[8:], 1)
