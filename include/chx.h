@@ -170,6 +170,31 @@ size_t ch_work_bytes(const chx_ch_plan* plan);
 int ch_step(chx_ch_plan* plan, double* c_now, double* c_prev, void* work, int nsteps, void* stream);
 int ch_diagnostics(chx_ch_plan* plan, const double* c, double* mass_out, double* energy_out, void* stream);
 
+/*
+ * Allocation-free mass / free-energy reduction.  The paper has no counterpart;
+ * this entry point exists for callers that cannot call cudaMalloc (code running
+ * where the device allocator may not be used, or hosts that reserve all device
+ * memory up front), so it needs no plan and allocates nothing.  It computes the
+ * same two sums as ch_diagnostics (same definitions; the summation order
+ * differs, by rows), for a row-major nx x ny field c on [0,lx) x [0,ly).
+ *  c, mass_out, energy_out  device pointers (one double each for the outputs),
+ *                           written asynchronously on `stream`.
+ *  Scratch: one partial-sum triple per row in a fixed device array of 16384
+ *  rows (384 KiB) that every GPU loading this library holds until exit; ny above
+ *  16384 is rejected with CHX_EINVAL.  All calls share that array and it keeps
+ *  the last call's contents (each call overwrites every row it reads, so nothing
+ *  needs clearing); calls that overlap on the GPU (different streams, or
+ *  different host threads) race on it and must be serialised by the caller.
+ *  The first call on each device looks up the array's device address
+ *  (cudaGetSymbolAddress) with that device current; make that first call
+ *  before any stream capture.
+ *  A NaN or Inf in c makes both outputs NaN.
+ * Errors: CHX_EINVAL (null pointer, nx or ny < 1, ny > 16384, lx or ly <= 0,
+ * gamma < 0), CHX_ECUDA.
+ */
+int ch_diagnostics_noalloc(const double* c, int nx, int ny, double lx, double ly, double gamma, double* mass_out,
+                           double* energy_out, void* stream);
+
 /* Profiling aid.  ch_profile(plan, 1) makes every later ch_step bracket each
  * kernel it launches with CUDA events on the launch stream (a few microseconds
  * of host time per launch); ch_profile(plan, 0) stops it.  ch_profile_read

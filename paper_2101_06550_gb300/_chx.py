@@ -27,7 +27,8 @@ STATUS = {0: "CHX_OK", -1: "CHX_EINVAL", -2: "CHX_ESINGULAR", -3: "CHX_ENONFINIT
 EXPORTS = ("chx_status_string", "chx_last_error", "chx_version", "stencil_apply_2d", "penta_cyclic_factor",
            "penta_cyclic_refactor", "penta_cyclic_solve_batched", "tri_cyclic_factor", "tri_cyclic_refactor",
            "tri_cyclic_solve_batched", "ch_plan_create", "ch_work_bytes", "ch_step", "ch_diagnostics",
-           "ch_profile", "ch_profile_read", "ch_profile_slot_name", "chx_sync_status", "chx_plan_destroy")
+           "ch_diagnostics_noalloc", "ch_profile", "ch_profile_read", "ch_profile_slot_name", "chx_sync_status",
+           "chx_plan_destroy")
 
 
 class ChxError(RuntimeError):
@@ -65,6 +66,7 @@ def lib():
         "ch_work_bytes": (sz, [_P]),
         "ch_step": (i, [_P, _P, _P, _P, i, _P]),
         "ch_diagnostics": (i, [_P, _P, _P, _P, _P]),
+        "ch_diagnostics_noalloc": (i, [_P, i, i, d, d, d, _P, _P, _P]),
         "ch_profile": (i, [_P, i]),
         "ch_profile_read": (i, [_P, _D, ctypes.POINTER(ctypes.c_longlong), i, i]),
         "ch_profile_slot_name": (ctypes.c_char_p, [i]),
@@ -268,3 +270,18 @@ class ChPlan(_Plan):
         _check(lib().ch_diagnostics(self._handle, _dev(c, torch.float64, self.nx * self.ny, "c"),
                                     ctypes.c_void_p(base), ctypes.c_void_p(base + 8), _stream(stream)))
         return out
+
+
+def ch_diagnostics_noalloc(c, lx, ly, gamma, out, stream=None):
+    """(mass, energy) of a (ny, nx) float64 CUDA field into the 2-element device tensor ``out``,
+    through the allocation-free entry point (no plan, static device scratch)."""
+    import torch
+
+    if c.dim() != 2:
+        raise ValueError("c must be a 2D (ny, nx) tensor")
+    ny, nx = c.shape
+    _dev(out, torch.float64, 2, "out")
+    base = out.data_ptr()
+    _check(lib().ch_diagnostics_noalloc(_dev(c, torch.float64, None, "c"), nx, ny, float(lx), float(ly), float(gamma),
+                                        ctypes.c_void_p(base), ctypes.c_void_p(base + 8), _stream(stream)))
+    return out
