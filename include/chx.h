@@ -58,6 +58,7 @@ enum { CHX_PREC_F64 = 0, CHX_PREC_F32_REFINE = 1 };
 typedef struct chx_penta_plan chx_penta_plan;
 typedef struct chx_tri_plan chx_tri_plan;
 typedef struct chx_ch_plan chx_ch_plan;
+typedef struct chx_ens chx_ens;
 
 const char* chx_status_string(int status);
 /* Detail of the last failure on this host thread ("" if none). */
@@ -169,6 +170,48 @@ int ch_plan_create(chx_ch_plan** plan, int nx, int ny, double lx, double ly, dou
 size_t ch_work_bytes(const chx_ch_plan* plan);
 int ch_step(chx_ch_plan* plan, double* c_now, double* c_prev, void* work, int nsteps, void* stream);
 int ch_diagnostics(chx_ch_plan* plan, const double* c, double* mass_out, double* energy_out, void* stream);
+
+/*
+ * Ensemble runtime: many simulations of uneven sizes advanced together (the
+ * batches of 2D simulations per domain size behind the thesis's statistics,
+ * Sec. 7.2, and its note that batches of different sizes want one LHS per
+ * distinct matrix, Sec. 9).  Every simulation is the ADI step of ch_step with
+ * the ensemble's dt and precision on an n x n grid of side l.
+ *  - A group holds simulations with the same (n, l): packed device-resident
+ *    state (C^n, C^{n-1}) for `capacity` slots, per-slot LHS factors (so the
+ *    slots may have different gamma), and one set of batched launches per step.  Only ens_create and ens_group_create
+ *    allocate device memory; ens_group_create fails with CHX_ENOMEM when the
+ *    group would take the ensemble past hbm_budget_bytes (0 = no budget).
+ *  - Slots [0, active) of each group are stepped (ens_group_set_active); the
+ *    caller keeps active simulations packed with ens_slot_move.  A simulation's
+ *    arithmetic does not depend on which other slots are active.
+ *  - ens_step advances every active slot of every group by nsteps, replaying a
+ *    CUDA graph that holds two steps of all groups (one graph branch per
+ *    group); the graph is rebuilt after any change of groups or active counts.
+ *  - ens_slot_load sets C^n = c0 and C^{n-1} = cm1 (or c0 if cm1 is NULL) for a
+ *    slot and, if gamma >= 0 differs from the slot's, refactorises the slot's
+ *    operators for it (host FP64, synchronous); ens_slot_read copies C^n (and
+ *    optionally C^{n-1}) out.  ens_slot_move copies state and factors.  Pointers may
+ *    be host or device memory (cudaMemcpyDefault); n*n doubles each.
+ *  - ens_autotune times `trial` steps per candidate segment count of a group's
+ *    partitioned sweeps and keeps the fastest; the simulations' state is saved
+ *    and restored, so the call changes no result other than by rounding order.
+ * Destroy with chx_plan_destroy; chx_sync_status works on the ensemble too.
+ * Errors: CHX_EINVAL (bad ids, sizes, slots), CHX_ENOMEM, CHX_ECUDA.
+ */
+int ens_create(chx_ens** ens, int precision, double dt, size_t hbm_budget_bytes);
+int ens_group_create(chx_ens* ens, int n, double l, double gamma, int capacity, int* group_id);
+int ens_group_destroy(chx_ens* ens, int group_id);
+int ens_group_set_active(chx_ens* ens, int group_id, int active);
+int ens_slot_load(chx_ens* ens, int group_id, int slot, const double* c0, const double* cm1, double gamma,
+                  void* stream);
+int ens_slot_read(chx_ens* ens, int group_id, int slot, double* c_now, double* c_prev, void* stream);
+int ens_slot_move(chx_ens* ens, int group_id, int from, int to, void* stream);
+int ens_step(chx_ens* ens, int nsteps, void* stream);
+int ens_group_step(chx_ens* ens, int group_id, int nsteps, void* stream);
+int ens_autotune(chx_ens* ens, int group_id, int trial, int* px_out, int* py_out, void* stream);
+int ens_info(chx_ens* ens, int group_id, int* n, int* capacity, int* active, int* px, int* py, size_t* bytes);
+size_t ens_bytes_used(const chx_ens* ens);
 
 /*
  * Allocation-free mass / free-energy reduction.  The paper has no counterpart;

@@ -27,8 +27,10 @@ STATUS = {0: "CHX_OK", -1: "CHX_EINVAL", -2: "CHX_ESINGULAR", -3: "CHX_ENONFINIT
 EXPORTS = ("chx_status_string", "chx_last_error", "chx_version", "stencil_apply_2d", "penta_cyclic_factor",
            "penta_cyclic_refactor", "penta_cyclic_solve_batched", "tri_cyclic_factor", "tri_cyclic_refactor",
            "tri_cyclic_solve_batched", "ch_plan_create", "ch_work_bytes", "ch_step", "ch_diagnostics",
-           "ch_diagnostics_noalloc", "ch_profile", "ch_profile_read", "ch_profile_slot_name", "chx_sync_status",
-           "chx_plan_destroy")
+           "ch_diagnostics_noalloc", "ch_profile", "ch_profile_read", "ch_profile_slot_name", "ens_create",
+           "ens_group_create", "ens_group_destroy", "ens_group_set_active", "ens_slot_load", "ens_slot_read",
+           "ens_slot_move", "ens_step", "ens_group_step", "ens_autotune", "ens_info", "ens_bytes_used",
+           "chx_sync_status", "chx_plan_destroy")
 
 
 class ChxError(RuntimeError):
@@ -70,6 +72,19 @@ def lib():
         "ch_profile": (i, [_P, i]),
         "ch_profile_read": (i, [_P, _D, ctypes.POINTER(ctypes.c_longlong), i, i]),
         "ch_profile_slot_name": (ctypes.c_char_p, [i]),
+        "ens_create": (i, [ctypes.POINTER(_P), i, d, sz]),
+        "ens_group_create": (i, [_P, i, d, d, i, ctypes.POINTER(i)]),
+        "ens_group_destroy": (i, [_P, i]),
+        "ens_group_set_active": (i, [_P, i, i]),
+        "ens_slot_load": (i, [_P, i, i, _P, _P, d, _P]),
+        "ens_slot_read": (i, [_P, i, i, _P, _P, _P]),
+        "ens_slot_move": (i, [_P, i, i, i, _P]),
+        "ens_step": (i, [_P, i, _P]),
+        "ens_group_step": (i, [_P, i, i, _P]),
+        "ens_autotune": (i, [_P, i, i, ctypes.POINTER(i), ctypes.POINTER(i), _P]),
+        "ens_info": (i, [_P, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
+                         ctypes.POINTER(i), ctypes.POINTER(sz)]),
+        "ens_bytes_used": (sz, [_P]),
         "chx_sync_status": (i, [_P]),
         "chx_plan_destroy": (None, [_P]),
     }
@@ -285,3 +300,73 @@ def ch_diagnostics_noalloc(c, lx, ly, gamma, out, stream=None):
     _check(lib().ch_diagnostics_noalloc(_dev(c, torch.float64, None, "c"), nx, ny, float(lx), float(ly), float(gamma),
                                         ctypes.c_void_p(base), ctypes.c_void_p(base + 8), _stream(stream)))
     return out
+
+
+def _any_ptr(t, numel, name):
+    """Contiguous float64 tensor on the GPU or in (preferably pinned) host memory."""
+    import torch
+
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != numel:
+        raise ValueError(f"{name} must be a contiguous float64 tensor of {numel} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Ensemble(_Plan):
+    """Ensemble runtime (ens_*): groups of same-(n, L) simulations with per-slot gamma,
+    device-resident state, graph-captured batched steps."""
+
+    def __init__(self, dt, precision=PREC_F64, hbm_budget=0):
+        h = ctypes.c_void_p()
+        _check(lib().ens_create(ctypes.byref(h), precision, float(dt), int(hbm_budget)))
+        self._handle, self.dt, self.precision = h, dt, precision
+        self.groups = {}
+
+    def group_create(self, n, l, gamma, capacity):
+        gid = ctypes.c_int()
+        _check(lib().ens_group_create(self._handle, n, float(l), float(gamma), capacity, ctypes.byref(gid)))
+        self.groups[gid.value] = (n, l, capacity)
+        return gid.value
+
+    def group_destroy(self, gid):
+        _check(lib().ens_group_destroy(self._handle, gid))
+        self.groups.pop(gid, None)
+
+    def set_active(self, gid, active):
+        _check(lib().ens_group_set_active(self._handle, gid, active))
+
+    def load(self, gid, slot, c0, cm1=None, gamma=-1.0, stream=None):
+        n = self.groups[gid][0]
+        p1 = _any_ptr(c0, n * n, "c0")
+        p2 = _any_ptr(cm1, n * n, "cm1") if cm1 is not None else None
+        _check(lib().ens_slot_load(self._handle, gid, slot, p1, p2, float(gamma), _stream(stream)))
+
+    def read(self, gid, slot, c_now, c_prev=None, stream=None):
+        n = self.groups[gid][0]
+        p1 = _any_ptr(c_now, n * n, "c_now")
+        p2 = _any_ptr(c_prev, n * n, "c_prev") if c_prev is not None else None
+        _check(lib().ens_slot_read(self._handle, gid, slot, p1, p2, _stream(stream)))
+
+    def move(self, gid, src, dst, stream=None):
+        _check(lib().ens_slot_move(self._handle, gid, src, dst, _stream(stream)))
+
+    def step(self, nsteps=1, stream=None):
+        _check(lib().ens_step(self._handle, int(nsteps), _stream(stream)))
+
+    def group_step(self, gid, nsteps=1, stream=None):
+        _check(lib().ens_group_step(self._handle, gid, int(nsteps), _stream(stream)))
+
+    def autotune(self, gid, trial=3, stream=None):
+        px, py = ctypes.c_int(), ctypes.c_int()
+        _check(lib().ens_autotune(self._handle, gid, int(trial), ctypes.byref(px), ctypes.byref(py), _stream(stream)))
+        return px.value, py.value
+
+    def info(self, gid):
+        v = [ctypes.c_int() for _ in range(5)]
+        b = ctypes.c_size_t()
+        _check(lib().ens_info(self._handle, gid, *[ctypes.byref(x) for x in v], ctypes.byref(b)))
+        return {"n": v[0].value, "capacity": v[1].value, "active": v[2].value, "px": v[3].value, "py": v[4].value,
+                "bytes": b.value}
+
+    @property
+    def bytes_used(self):
+        return lib().ens_bytes_used(self._handle)

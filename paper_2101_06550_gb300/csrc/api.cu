@@ -278,6 +278,7 @@ int dense_inverse_host(int k, const double* A, double* Ainv) {
 void penta_plan_free(chx_penta_plan* p);
 void tri_plan_free(chx_tri_plan* p);
 void ch_plan_free(chx_ch_plan* p);
+void ens_free(chx_ens* e);
 
 }  // namespace chx
 
@@ -304,7 +305,7 @@ extern "C" int chx_version(void) { return 10000; }
 extern "C" int chx_sync_status(void* plan) {
   if (!plan) return fail(CHX_EINVAL, "chx_sync_status: null plan");
   PlanHdr* h = (PlanHdr*)plan;
-  if (h->magic != kMagicPenta && h->magic != kMagicTri && h->magic != kMagicCh)
+  if (h->magic != kMagicPenta && h->magic != kMagicTri && h->magic != kMagicCh && h->magic != kMagicEns)
     return fail(CHX_EINVAL, "chx_sync_status: not a chx plan");
   int rc = cuda_check(cudaStreamSynchronize(h->last_stream), "chx_sync_status: stream synchronize");
   if (rc) return rc;
@@ -325,6 +326,7 @@ extern "C" void chx_plan_destroy(void* plan) {
     case kMagicPenta: penta_plan_free((chx_penta_plan*)plan); break;
     case kMagicTri: tri_plan_free((chx_tri_plan*)plan); break;
     case kMagicCh: ch_plan_free((chx_ch_plan*)plan); break;
+    case kMagicEns: ens_free((chx_ens*)plan); break;
     default: break;
   }
 }

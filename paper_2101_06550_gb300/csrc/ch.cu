@@ -11,6 +11,9 @@
 //            systems of the x sweep become interleaved (coalesced).
 //   x sweep  (I + a_x d_xxxx) w = r along rows; y sweep (I + a_y d_yyyy) v = w
 //            along columns; update C^{n+1} = Cbar + v.
+// Several same-shape simulations run as one group: the stencil, update and y
+// sweep index the simulation by blockIdx.z, and the x sweep sees the row
+// systems of all of them as one interleaved batch.
 // Each sweep splits every cyclic system into P segments (a partitioned,
 // SPIKE-type solve) so a single grid gives n * P independent threads instead
 // of the paper's n: segment-local LU sweeps (the paper's factor/solve steps on
@@ -26,51 +29,24 @@
 #include <utility>
 #include <vector>
 
-#include "chx_internal.cuh"
+#include "chgroup.cuh"
 
 using namespace chx;
 
-namespace {
-
-struct SpikeDir {
-  int n = 0, P = 1, m = 0, nsys = 0;
-  double a = 0, b = 0, c = 0;   // LHS row (a, b, c, b, a)
-  double* d_lu = nullptr;       // 4*m: ralpha, beta, gam, del of the segment block
-  double* d_vw = nullptr;       // 4*m: V0, V1, W0, W1
-  double* d_rinv = nullptr;     // (4P)^2
-  float* d_lu32 = nullptr;
-  float* d_vw32 = nullptr;
-  float* d_rinv32 = nullptr;
-};
-
-}  // namespace
-
-struct chx_ch_plan {
-  PlanHdr hdr;
-  int nx, ny, precision;
-  double lx, ly, gamma, dt, dx, dy;
-  double rho, kap, gl, k1, k2;  // stencil constants
-  SpikeDir X, Y;
-  double* d_partials;
-  int npart;
-  // work layout (byte offsets into the caller's work buffer)
-  size_t off_f, off_w, off_y1, off_y2, off_ybx, off_tx, off_ybx2, off_tx2, off_yby, off_ty, off_yby2, off_ty2;
-  size_t work_bytes;
-  // optional per-kernel event timing (ch_profile)
-  int prof_on;
-  std::vector<cudaEvent_t>* ev_pool;
-  std::vector<int>* pend_slot;                      // slot of each pending pair
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* pend;
-  double prof_ms[16];
-  long long prof_n[16];
-};
-
-namespace {
-
-enum Slot { kRhs, kLocX, kRedX, kRefX, kRed2X, kFinX, kLocY, kRedY, kRefY, kRed2Y, kUpd, kSlots };
+namespace chx {
 const char* const kSlotName[kSlots] = {"ch_rhs",         "spike_local_x", "spike_reduced_x", "spike_refine_x",
                                        "spike_reduced2_x", "ch_xfinish",   "spike_local_y",   "spike_reduced_y",
                                        "spike_refine_y", "spike_reduced2_y", "ch_update"};
+}  // namespace chx
+
+struct chx_ch_plan {
+  PlanHdr hdr;
+  ChGroup g;
+  double* d_partials;
+  Prof* prof;
+};
+
+namespace {
 
 constexpr int kT = 32;      // tile edge of the transposing kernels
 constexpr int kBY = 8;      // tile threads in y
@@ -82,16 +58,21 @@ __device__ __forceinline__ int wrapi(int i, int n) {
 }
 
 // ---------------------------------------------------------------------------
-// RHS stencil pass.  Tile of 32 (i) x 32 (j) outputs, Cn/Cbar staged with a
-// 2-point halo, M with a 1-point halo.  TC: arithmetic type, TO: output type.
+// RHS stencil pass.  Tile of 32 (i) x 32 (j) outputs of simulation blockIdx.z,
+// Cn/Cbar staged with a 2-point halo, M with a 1-point halo.  Output element
+// (i, j) of simulation z goes to rT[i * (G*ny) + z*ny + j].  gls[z] = gamma/dx^2.
 template <typename TC, typename TO>
 __global__ void __launch_bounds__(kT* kBY) ch_rhs_kernel(const double* __restrict__ cn, const double* __restrict__ cp,
-                                                         TO* __restrict__ rT, int nx, int ny, TC rho, TC kap, TC gl,
-                                                         TC k1, TC k2) {
+                                                         TO* __restrict__ rT, int nx, int ny, int G, TC rho, TC kap,
+                                                         const TC* __restrict__ gls, TC k1, TC k2) {
   __shared__ TC s_cn[kT + 4][kT + 5];
   __shared__ TC s_cb[kT + 4][kT + 5];
   __shared__ TC s_m[kT + 2][kT + 3];
   __shared__ TO s_o[kT][kT + 1];
+  const int z = blockIdx.z;
+  const TC gl = gls[z];
+  cn += (size_t)z * nx * ny;
+  cp += (size_t)z * nx * ny;
   const int i0 = blockIdx.x * kT, j0 = blockIdx.y * kT;
   const int tid = threadIdx.y * kT + threadIdx.x;
   for (int idx = tid; idx < (kT + 4) * (kT + 4); idx += kT * kBY) {
@@ -123,29 +104,37 @@ __global__ void __launch_bounds__(kT* kBY) ch_rhs_kernel(const double* __restric
     s_o[lx - 1][ly - 1] = (TO)fma(k2, l, -(k1 * diff));
   }
   __syncthreads();
+  const size_t ldo = (size_t)G * ny;
 #pragma unroll
   for (int k = 0; k < kT / kBY; ++k) {
     const int li = threadIdx.y + k * kBY, lj = threadIdx.x;
     const int gi = i0 + li, gj = j0 + lj;
-    if (gi < nx && gj < ny) rT[(size_t)gi * ny + gj] = s_o[li][lj];
+    if (gi < nx && gj < ny) rT[(size_t)gi * ldo + (size_t)z * ny + gj] = s_o[li][lj];
   }
 }
 
 // ---------------------------------------------------------------------------
 // Segment-local LU sweeps on interleaved data: element r of segment s of
-// system j at [(s*m + r)*ld + j].  Writes y = A_seg^{-1} f and the four
-// boundary values (y_0, y_1, y_{m-2}, y_{m-1}) of every segment.
-template <typename TIn, typename TC>
-__global__ void __launch_bounds__(kSolveThreads) spike_local_kernel(const TIn* f, TC* y, int ld, int nsys, int m,
-                                                                    TC a, const TC* __restrict__ lu, TC* __restrict__ yb) {
+// system j at [(s*m + r)*ld + j] (+ blockIdx.z * fz for batched y sweeps).
+// Writes y = A_seg^{-1} f and the four boundary values (y_0, y_1, y_{m-2},
+// y_{m-1}) of every segment (+ blockIdx.z * ybz).  Loads run U rows ahead.
+template <typename TIn, typename TC, int U = (sizeof(TC) == 8 ? 8 : 32)>
+__global__ void __launch_bounds__(kSolveThreads) spike_local_kernel(const TIn* f, TC* y, int ld, int nsys,
+                                                                    DirView<TC> D, TC* __restrict__ yb, size_t fz,
+                                                                    size_t ybz) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nsys) return;
-  const int s = blockIdx.y;
+  const int s = blockIdx.y, m = D.m;
+  const int slot = blockIdx.z + j / D.spp;
+  const TC a = D.a[slot];
+  const TC* lu = D.lu + (size_t)slot * 4 * m;
+  f += blockIdx.z * fz;
+  y += blockIdx.z * fz;
+  yb += blockIdx.z * ybz;
   const size_t L = (size_t)ld;
   const TIn* pf = f + (size_t)s * m * L + j;
   TC* py = y + (size_t)s * m * L + j;
   const TC *ra = lu, *be = lu + m, *ga = lu + 2 * m, *de = lu + 3 * m;
-  constexpr int U = 8;
   TC g1 = 0, g2 = 0;
   TC buf[U];
 #pragma unroll
@@ -208,21 +197,38 @@ __global__ void __launch_bounds__(kSolveThreads) spike_local_kernel(const TIn* f
   yb[(size_t)(4 * s + 3) * S + j] = ylast;
 }
 
-// Reduced system: tau = Rinv * yb for every system (4P unknowns each).
+// Reduced system: tau = Rinv * yb for every system (4P unknowns each), one
+// output per thread; the 4P loads of the system's boundary values are issued
+// 8 at a time so their latencies overlap.
 template <typename TC>
-__global__ void __launch_bounds__(kSolveThreads) spike_reduced_kernel(const TC* __restrict__ yb,
-                                                                      const TC* __restrict__ rinv,
-                                                                      TC* __restrict__ tau, int nsys, int k) {
+__global__ void __launch_bounds__(kSolveThreads) spike_reduced_kernel(const TC* __restrict__ yb, DirView<TC> D,
+                                                                      TC* __restrict__ tau, int nsys, size_t ybz) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nsys) return;
+  const int k = 4 * D.P;
+  const int slot = blockIdx.z + j / D.spp;
+  yb += blockIdx.z * ybz;
+  tau += blockIdx.z * ybz;
   const int q = blockIdx.y;
-  const TC* row = rinv + (size_t)q * k;
-  TC acc = 0;
-  for (int p = 0; p < k; ++p) acc = fma(__ldg(&row[p]), yb[(size_t)p * nsys + j], acc);
-  tau[(size_t)q * nsys + j] = acc;
+  const TC* row = D.rinv + (size_t)slot * k * k + (size_t)q * k;
+  TC acc0 = 0, acc1 = 0;
+  int p = 0;
+  for (; p + 8 <= k; p += 8) {
+    TC v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = yb[(size_t)(p + u) * nsys + j];
+#pragma unroll
+    for (int u = 0; u < 8; u += 2) {
+      acc0 = fma(__ldg(&row[p + u]), v[u], acc0);
+      acc1 = fma(__ldg(&row[p + u + 1]), v[u + 1], acc1);
+    }
+  }
+  for (; p < k; ++p) acc0 = fma(__ldg(&row[p]), yb[(size_t)p * nsys + j], acc0);
+  tau[(size_t)q * nsys + j] = acc0 + acc1;
 }
 
-// Spike correction of element (row r of segment s) of system j.
+// Spike correction of element (row r of segment s) of system j; vw is the
+// slot's spike block.
 template <typename TC>
 __device__ __forceinline__ TC spike_corr(const TC* __restrict__ vw, const TC* __restrict__ tau, int m, int P,
                                          int nsys, int s, int r, int j) {
@@ -235,28 +241,28 @@ __device__ __forceinline__ TC spike_corr(const TC* __restrict__ vw, const TC* __
   return c;
 }
 
-// x-sweep correction + transpose back: yT (element i of row-system j at
-// yT[i*ny + j]) -> w[j*nx + i].  With two (y, tau) pairs the results add
-// (first solution + refinement correction).
-template <typename TC, typename TO, bool kTwo>
+// x-sweep correction + transpose back: y (element i of row-system (z, j) at
+// y[i*(G*ny) + z*ny + j]) -> w[z*nx*ny + j*nx + i].
+template <typename TC, typename TO>
 __global__ void __launch_bounds__(kT* kBY) ch_xfinish_kernel(const TC* __restrict__ y1, const TC* __restrict__ t1,
-                                                             const TC* __restrict__ y2, const TC* __restrict__ t2,
-                                                             const TC* __restrict__ vw, TO* __restrict__ w, int nx,
-                                                             int ny, int m, int P) {
+                                                             DirView<TC> D, TO* __restrict__ w, int nx, int ny, int G) {
   __shared__ TO s_t[kT][kT + 1];
+  const int z = blockIdx.z, m = D.m, P = D.P;
+  const TC* vw = D.vw + (size_t)z * 4 * m;
   const int i0 = blockIdx.x * kT, j0 = blockIdx.y * kT;
   const int j = j0 + threadIdx.x;
+  const size_t ld = (size_t)G * ny;
+  const int sys = z * ny + j;
 #pragma unroll
   for (int k = 0; k < kT / kBY; ++k) {
     const int li = threadIdx.y + k * kBY, i = i0 + li;
     if (i < nx && j < ny) {
       const int s = i / m, r = i - s * m;
-      TC v = y1[(size_t)i * ny + j] - spike_corr(vw, t1, m, P, ny, s, r, j);
-      if (kTwo) v += y2[(size_t)i * ny + j] - spike_corr(vw, t2, m, P, ny, s, r, j);
-      s_t[li][threadIdx.x] = (TO)v;
+      s_t[li][threadIdx.x] = (TO)(y1[(size_t)i * ld + sys] - spike_corr(vw, t1, m, P, G * ny, s, r, sys));
     }
   }
   __syncthreads();
+  w += (size_t)z * nx * ny;
 #pragma unroll
   for (int k = 0; k < kT / kBY; ++k) {
     const int lj = threadIdx.y + k * kBY, li = threadIdx.x;
@@ -265,21 +271,20 @@ __global__ void __launch_bounds__(kT* kBY) ch_xfinish_kernel(const TC* __restric
   }
 }
 
-// y-sweep correction + update C^{n+1} = 2C^n - C^{n-1} + v.  keep_roles = 1
-// writes C^n into c_prev and C^{n+1} into c_now; otherwise C^{n+1} goes into
-// c_prev (the caller swaps the pointers).
-template <typename TC, bool kTwo>
+// y-sweep correction + update C^{n+1} = 2C^n - C^{n-1} + v for simulation z.
+// keep_roles = 1 writes C^n into c_prev and C^{n+1} into c_now; otherwise
+// C^{n+1} goes into c_prev (the caller swaps the pointers).
+template <typename TC>
 __global__ void __launch_bounds__(kSolveThreads) ch_update_kernel(const TC* __restrict__ y1, const TC* __restrict__ t1,
-                                                                  const TC* __restrict__ y2, const TC* __restrict__ t2,
-                                                                  const TC* __restrict__ vw, double* cn, double* cp,
-                                                                  int nx, int ny, int m, int P, int keep_roles) {
+                                                                  DirView<TC> D, double* cn, double* cp, int nx,
+                                                                  int ny, int keep_roles) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y;
+  const int j = blockIdx.y, z = blockIdx.z, m = D.m, P = D.P;
   if (i >= nx) return;
   const int s = j / m, r = j - s * m;
-  const size_t p = (size_t)j * nx + i;
-  TC v = y1[p] - spike_corr(vw, t1, m, P, nx, s, r, i);
-  if (kTwo) v += y2[p] - spike_corr(vw, t2, m, P, nx, s, r, i);
+  const size_t p = (size_t)z * nx * ny + (size_t)j * nx + i;
+  t1 += (size_t)z * 4 * P * nx;
+  const TC v = y1[p] - spike_corr(D.vw + (size_t)z * 4 * m, t1, m, P, nx, s, r, i);
   const double a = cn[p], b = cp[p];
   const double nxt = fma(2.0, a, -b) + (double)v;
   if (keep_roles) {
@@ -288,65 +293,6 @@ __global__ void __launch_bounds__(kSolveThreads) ch_update_kernel(const TC* __re
   } else {
     cp[p] = nxt;
   }
-}
-
-// FP32 refinement sweep: residual rho = f - A x0 in FP64 with x0 the corrected
-// first FP32 solution (from y1, tau1), then the segment-local FP32 LU sweeps on
-// rho into y2, plus the boundary values for the second reduced solve.
-__device__ __forceinline__ double x0_at(const float* __restrict__ y1, const float* __restrict__ t1,
-                                        const float* __restrict__ vw, int n, int m, int P, int ld, int nsys, int i,
-                                        int j) {
-  i = wrapi(i, n);
-  const int s = i / m, r = i - s * m;
-  return (double)(y1[(size_t)i * ld + j] - spike_corr(vw, t1, m, P, nsys, s, r, j));
-}
-
-__global__ void __launch_bounds__(kSolveThreads) spike_refine_kernel(
-    const float* __restrict__ f, const float* __restrict__ y1, const float* __restrict__ t1, float* __restrict__ y2,
-    float* __restrict__ yb, int ld, int nsys, int n, int m, int P, double ca, double cb, double cc, float a32,
-    const float* __restrict__ lu, const float* __restrict__ vw) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= nsys) return;
-  const int s = blockIdx.y;
-  const int base = s * m;
-  const size_t L = (size_t)ld;
-  const float *ra = lu, *be = lu + m, *ga = lu + 2 * m, *de = lu + 3 * m;
-  double w0 = x0_at(y1, t1, vw, n, m, P, ld, nsys, base - 2, j);
-  double w1 = x0_at(y1, t1, vw, n, m, P, ld, nsys, base - 1, j);
-  double w2 = x0_at(y1, t1, vw, n, m, P, ld, nsys, base, j);
-  double w3 = x0_at(y1, t1, vw, n, m, P, ld, nsys, base + 1, j);
-  double w4 = x0_at(y1, t1, vw, n, m, P, ld, nsys, base + 2, j);
-  float g1 = 0.f, g2 = 0.f;
-  for (int r = 0; r < m; ++r) {
-    const int i = base + r;
-    double ax = cc * w2;
-    ax = fma(cb, w1 + w3, ax);
-    ax = fma(ca, w0 + w4, ax);
-    const float res = (float)((double)f[(size_t)i * L + j] - ax);
-    float g = fmaf(-a32, g2, res);
-    g = fmaf(-__ldg(&be[r]), g1, g) * __ldg(&ra[r]);
-    y2[(size_t)i * L + j] = g;
-    g2 = g1;
-    g1 = g;
-    w0 = w1; w1 = w2; w2 = w3; w3 = w4;
-    w4 = x0_at(y1, t1, vw, n, m, P, ld, nsys, i + 3, j);
-  }
-  float x1 = 0.f, x2 = 0.f, ylast = 0.f, ylast2 = 0.f;
-  for (int r = m - 1; r >= 0; --r) {
-    const size_t p = (size_t)(base + r) * L + j;
-    float v = fmaf(-__ldg(&ga[r]), x1, y2[p]);
-    v = fmaf(-__ldg(&de[r]), x2, v);
-    y2[p] = v;
-    if (r == m - 1) ylast = v;
-    if (r == m - 2) ylast2 = v;
-    x2 = x1;
-    x1 = v;
-  }
-  const size_t S = (size_t)nsys;
-  yb[(size_t)(4 * s + 0) * S + j] = x1;
-  yb[(size_t)(4 * s + 1) * S + j] = x2;
-  yb[(size_t)(4 * s + 2) * S + j] = ylast2;
-  yb[(size_t)(4 * s + 3) * S + j] = ylast;
 }
 
 // ---------------------------------------------------------------------------
@@ -402,8 +348,10 @@ __global__ void ch_diag_final_kernel(const double* __restrict__ part, int nb, do
 }
 
 // ---------------------------------------------------------------------------
-// Host: segment count and precomputation for one sweep direction.
-int choose_segments(int n, int nsys) {
+// Host helpers.
+int default_segments(int n, int nsys) {
+  // The dense reduced solve costs 16 P^2 / n operations per point, so P stays
+  // near sqrt(n / 8) while aiming at about 32k independent sweeps.
   int pmax = (int)floor(sqrt(n / 8.0));
   if (pmax < 1) pmax = 1;
   int want = (32768 + nsys - 1) / nsys;
@@ -414,30 +362,18 @@ int choose_segments(int n, int nsys) {
   return 1;
 }
 
-template <typename T>
-int dev_upload(T** dst, const std::vector<double>& src) {
-  std::vector<T> h(src.size());
-  for (size_t i = 0; i < src.size(); ++i) h[i] = (T)src[i];
-  if (cudaMalloc(dst, h.size() * sizeof(T)) != cudaSuccess) {
-    cudaGetLastError();
-    *dst = nullptr;
-    return fail(CHX_ENOMEM, "ch_plan_create: allocation of %zu values", h.size());
-  }
-  return cuda_check(cudaMemcpy(*dst, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice), "ch_plan_create: upload");
-}
-
-int setup_dir(SpikeDir* D, int n, int nsys, double acoef) {
-  D->n = n;
-  D->nsys = nsys;
-  D->a = acoef;
-  D->b = -4.0 * acoef;
-  D->c = 1.0 + 6.0 * acoef;
-  D->P = choose_segments(n, nsys);
-  D->m = n / D->P;
-  const int m = D->m, P = D->P, k = 4 * P;
-  std::vector<double> lu(4 * (size_t)m), vw(4 * (size_t)m), R((size_t)k * k, 0.0), Rinv((size_t)k * k);
+// Host FP64 factors of the segment block for one value of a: LU (4m), spikes
+// V, W (4m) and the reduced-system inverse ((4P)^2).
+int dir_factors_host(int n, int P, double a, std::vector<double>& lu, std::vector<double>& vw,
+                     std::vector<double>& rinv) {
+  const int m = n / P, k = 4 * P;
+  const double b = -4.0 * a, c = 1.0 + 6.0 * a;
+  lu.assign(4 * (size_t)m, 0.0);
+  vw.assign(4 * (size_t)m, 0.0);
+  rinv.assign((size_t)k * k, 0.0);
+  std::vector<double> R((size_t)k * k, 0.0);
   double *ra = &lu[0], *be = &lu[m], *ga = &lu[2 * (size_t)m], *de = &lu[3 * (size_t)m];
-  int rc = band_factor_host(m, D->a, D->b, D->c, D->b, D->a, ra, be, ga, de);
+  int rc = band_factor_host(m, a, b, c, b, a, ra, be, ga, de);
   if (rc) return rc;
   // V = A_seg^{-1} [e at row m-2; d, e at row m-1] (couples t_{s+1}),
   // W = A_seg^{-1} [a, b at row 0; 0, a at row 1] (couples b_{s-1}).
@@ -445,13 +381,13 @@ int setup_dir(SpikeDir* D, int n, int nsys, double acoef) {
   for (int q = 0; q < 4; ++q) {
     std::fill(rhs.begin(), rhs.end(), 0.0);
     if (q < 2) {
-      rhs[m - 2] += q == 0 ? D->a : 0.0;   // e = a
-      rhs[m - 1] += q == 0 ? D->b : D->a;  // d = b, e = a
+      rhs[m - 2] += q == 0 ? a : 0.0;  // e = a
+      rhs[m - 1] += q == 0 ? b : a;    // d = b, e = a
     } else {
-      rhs[0] += q == 2 ? D->a : D->b;      // a, b
-      rhs[1] += q == 2 ? 0.0 : D->a;       // 0, a
+      rhs[0] += q == 2 ? a : b;        // a, b
+      rhs[1] += q == 2 ? 0.0 : a;      // 0, a
     }
-    band_solve_host(m, D->a, ra, be, ga, de, rhs.data(), col.data());
+    band_solve_host(m, a, ra, be, ga, de, rhs.data(), col.data());
     for (int r = 0; r < m; ++r) vw[(size_t)q * m + r] = col[r];
   }
   const int rows[4] = {0, 1, m - 2, m - 1};
@@ -466,112 +402,120 @@ int setup_dir(SpikeDir* D, int n, int nsys, double acoef) {
       R[(size_t)row * k + 4 * sp + 3] += vw[3 * (size_t)m + r];
     }
   }
-  rc = dense_inverse_host(k, R.data(), Rinv.data());
-  if (rc) return rc;
-  if ((rc = dev_upload(&D->d_lu, lu)) || (rc = dev_upload(&D->d_vw, vw)) || (rc = dev_upload(&D->d_rinv, Rinv)) ||
-      (rc = dev_upload(&D->d_lu32, lu)) || (rc = dev_upload(&D->d_vw32, vw)) || (rc = dev_upload(&D->d_rinv32, Rinv)))
+  return dense_inverse_host(k, R.data(), rinv.data());
+}
+
+template <typename T>
+int dev_alloc(T** p, size_t cnt) {
+  if (cudaMalloc(p, cnt * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(CHX_ENOMEM, "ch: allocation of %zu values", cnt);
+  }
+  return CHX_OK;
+}
+
+template <typename T>
+int put(T* dst, const std::vector<double>& src) {
+  std::vector<T> h(src.size());
+  for (size_t i = 0; i < src.size(); ++i) h[i] = (T)src[i];
+  return cuda_check(cudaMemcpy(dst, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice), "ch: upload");
+}
+
+int dir_alloc(SpikeDir* D, int n, int P, int slots) {
+  D->n = n;
+  D->P = P;
+  D->m = n / P;
+  D->slots = slots;
+  const size_t m4 = 4 * (size_t)D->m * slots, kk = (size_t)16 * P * P * slots;
+  int rc;
+  if ((rc = dev_alloc(&D->d_a, slots)) || (rc = dev_alloc(&D->d_lu, m4)) || (rc = dev_alloc(&D->d_vw, m4)) ||
+      (rc = dev_alloc(&D->d_rinv, kk)) || (rc = dev_alloc(&D->d_a32, slots)) || (rc = dev_alloc(&D->d_aff, slots)) ||
+      (rc = dev_alloc(&D->d_lu32, m4)) || (rc = dev_alloc(&D->d_vw32, m4)) || (rc = dev_alloc(&D->d_rinv32, kk)))
     return rc;
   return CHX_OK;
 }
 
+// Factorises for `a` and uploads into slot z.
+int dir_set(SpikeDir* D, int z, double a) {
+  std::vector<double> lu, vw, rinv;
+  int rc = dir_factors_host(D->n, D->P, a, lu, vw, rinv);
+  if (rc) return rc;
+  const size_t m4 = 4 * (size_t)D->m, kk = (size_t)16 * D->P * D->P;
+  const std::vector<double> av(1, a);
+  const float2 aff = split_ff(a);
+  if ((rc = put(D->d_a + z, av)) || (rc = put(D->d_lu + z * m4, lu)) || (rc = put(D->d_vw + z * m4, vw)) ||
+      (rc = put(D->d_rinv + z * kk, rinv)) || (rc = put(D->d_a32 + z, av)) || (rc = put(D->d_lu32 + z * m4, lu)) ||
+      (rc = put(D->d_vw32 + z * m4, vw)) || (rc = put(D->d_rinv32 + z * kk, rinv)))
+    return rc;
+  return cuda_check(cudaMemcpy(D->d_aff + z, &aff, sizeof(float2), cudaMemcpyHostToDevice), "ch: upload");
+}
+
+// Copies every slot from slot 0 (device to device).
+int dir_replicate(SpikeDir* D) {
+  const size_t m4 = 4 * (size_t)D->m, kk = (size_t)16 * D->P * D->P;
+  int rc = CHX_OK;
+  for (int z = 1; z < D->slots && !rc; ++z) {
+    rc = cuda_check(cudaMemcpy(D->d_a + z, D->d_a, sizeof(double), cudaMemcpyDeviceToDevice), "ch: replicate");
+    if (!rc) rc = cuda_check(cudaMemcpy(D->d_lu + z * m4, D->d_lu, m4 * 8, cudaMemcpyDeviceToDevice), "ch: replicate");
+    if (!rc) rc = cuda_check(cudaMemcpy(D->d_vw + z * m4, D->d_vw, m4 * 8, cudaMemcpyDeviceToDevice), "ch: replicate");
+    if (!rc) rc = cuda_check(cudaMemcpy(D->d_rinv + z * kk, D->d_rinv, kk * 8, cudaMemcpyDeviceToDevice), "ch: replicate");
+    if (!rc) rc = cuda_check(cudaMemcpy(D->d_a32 + z, D->d_a32, 4, cudaMemcpyDeviceToDevice), "ch: replicate");
+    if (!rc) rc = cuda_check(cudaMemcpy(D->d_aff + z, D->d_aff, 8, cudaMemcpyDeviceToDevice), "ch: replicate");
+    if (!rc) rc = cuda_check(cudaMemcpy(D->d_lu32 + z * m4, D->d_lu32, m4 * 4, cudaMemcpyDeviceToDevice), "ch: replicate");
+    if (!rc) rc = cuda_check(cudaMemcpy(D->d_vw32 + z * m4, D->d_vw32, m4 * 4, cudaMemcpyDeviceToDevice), "ch: replicate");
+    if (!rc) rc = cuda_check(cudaMemcpy(D->d_rinv32 + z * kk, D->d_rinv32, kk * 4, cudaMemcpyDeviceToDevice), "ch: replicate");
+  }
+  return rc;
+}
+
+int dir_move(SpikeDir* D, int from, int to, cudaStream_t st) {
+  const size_t m4 = 4 * (size_t)D->m, kk = (size_t)16 * D->P * D->P;
+  struct { void* base; size_t esz, per; } a[9] = {
+      {D->d_a, 8, 1}, {D->d_lu, 8, m4}, {D->d_vw, 8, m4}, {D->d_rinv, 8, kk}, {D->d_a32, 4, 1},
+      {D->d_aff, 8, 1}, {D->d_lu32, 4, m4}, {D->d_vw32, 4, m4}, {D->d_rinv32, 4, kk}};
+  for (auto& x : a) {
+    const size_t b = x.esz * x.per;
+    int rc = cuda_check(cudaMemcpyAsync((char*)x.base + to * b, (char*)x.base + from * b, b, cudaMemcpyDeviceToDevice, st),
+                        "ch: move parameters");
+    if (rc) return rc;
+  }
+  return CHX_OK;
+}
+
 void free_dir(SpikeDir* D) {
-  cudaFree(D->d_lu); cudaFree(D->d_vw); cudaFree(D->d_rinv);
-  cudaFree(D->d_lu32); cudaFree(D->d_vw32); cudaFree(D->d_rinv32);
+  cudaFree(D->d_a); cudaFree(D->d_lu); cudaFree(D->d_vw); cudaFree(D->d_rinv);
+  cudaFree(D->d_a32); cudaFree(D->d_aff); cudaFree(D->d_lu32); cudaFree(D->d_vw32); cudaFree(D->d_rinv32);
+  *D = SpikeDir();
+}
+
+template <typename T>
+DirView<T> view(const SpikeDir& D, int spp);
+template <>
+DirView<double> view<double>(const SpikeDir& D, int spp) {
+  return DirView<double>{D.d_a, D.d_lu, D.d_vw, D.d_rinv, D.m, D.P, spp};
+}
+template <>
+DirView<float> view<float>(const SpikeDir& D, int spp) {
+  return DirView<float>{D.d_a32, D.d_lu32, D.d_vw32, D.d_rinv32, D.m, D.P, spp};
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+template <typename T>
+T* wptr(void* work, size_t off) {
+  return (T*)((char*)work + off);
+}
+
 }  // namespace
 
+// ---------------------------------------------------------------------------
 namespace chx {
-void ch_plan_free(chx_ch_plan* p) {
-  if (!p) return;
-  free_dir(&p->X);
-  free_dir(&p->Y);
-  if (p->d_partials) cudaFree(p->d_partials);
-  if (p->pend) {
-    for (auto& e : *p->pend) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
-    delete p->pend;
-  }
-  if (p->ev_pool) {
-    for (auto e : *p->ev_pool) cudaEventDestroy(e);
-    delete p->ev_pool;
-  }
-  delete p->pend_slot;
-  hdr_free(&p->hdr);
-  free(p);
-}
-}  // namespace chx
 
-extern "C" int ch_plan_create(chx_ch_plan** plan, int nx, int ny, double lx, double ly, double gamma, double dt,
-                              int precision) {
-  if (!plan) return fail(CHX_EINVAL, "ch_plan_create: null plan pointer");
-  *plan = nullptr;
-  if (nx < 8 || ny < 8 || nx > 16384 || ny > 16384)
-    return fail(CHX_EINVAL, "ch_plan_create: nx %d, ny %d outside [8, 16384]", nx, ny);
-  if (!(lx > 0) || !(ly > 0) || !(dt > 0) || !(gamma >= 0) || !isfinite(lx) || !isfinite(ly) || !isfinite(dt) ||
-      !isfinite(gamma))
-    return fail(CHX_EINVAL, "ch_plan_create: lx %g, ly %g, dt %g, gamma %g", lx, ly, dt, gamma);
-  if (precision != CHX_PREC_F64 && precision != CHX_PREC_F32_REFINE)
-    return fail(CHX_EINVAL, "ch_plan_create: precision %d", precision);
-  chx_ch_plan* p = (chx_ch_plan*)calloc(1, sizeof(chx_ch_plan));
-  if (!p) return fail(CHX_ENOMEM, "ch_plan_create: plan allocation");
-  new (&p->X) SpikeDir();
-  new (&p->Y) SpikeDir();
-  p->ev_pool = new std::vector<cudaEvent_t>();
-  p->pend = new std::vector<std::pair<cudaEvent_t, cudaEvent_t>>();
-  p->pend_slot = new std::vector<int>();
-  int rc = hdr_init(&p->hdr, kMagicCh);
-  if (rc) { ch_plan_free(p); return rc; }
-  p->nx = nx; p->ny = ny; p->precision = precision;
-  p->lx = lx; p->ly = ly; p->gamma = gamma; p->dt = dt;
-  p->dx = lx / nx; p->dy = ly / ny;
-  const double sx = 1.0 / (p->dx * p->dx);
-  p->rho = (p->dx * p->dx) / (p->dy * p->dy);
-  p->kap = -2.0 * (1.0 + p->rho);
-  p->gl = gamma * sx;
-  p->k1 = 2.0 / 3.0;
-  p->k2 = (2.0 / 3.0) * dt * sx;
-  const double ax = (2.0 / 3.0) * gamma * dt / (p->dx * p->dx * p->dx * p->dx);
-  const double ay = (2.0 / 3.0) * gamma * dt / (p->dy * p->dy * p->dy * p->dy);
-  if ((rc = setup_dir(&p->X, nx, ny, ax)) || (rc = setup_dir(&p->Y, ny, nx, ay))) { ch_plan_free(p); return rc; }
-  p->npart = kDiagBlocks;
-  if (cudaMalloc(&p->d_partials, 3 * (size_t)kDiagBlocks * sizeof(double)) != cudaSuccess) {
-    cudaGetLastError();
-    p->d_partials = nullptr;
-    ch_plan_free(p);
-    return fail(CHX_ENOMEM, "ch_plan_create: diagnostics scratch");
-  }
-  const size_t N = (size_t)nx * ny;
-  const size_t esz = precision == CHX_PREC_F64 ? 8 : 4;
-  size_t off = 0;
-  p->off_f = off; off = align256(off + N * esz);
-  p->off_w = off; off = align256(off + N * esz);
-  p->off_y1 = off; off = align256(off + (precision == CHX_PREC_F64 ? 0 : N * esz));
-  p->off_y2 = off; off = align256(off + (precision == CHX_PREC_F64 ? 0 : N * esz));
-  const size_t kx = 4 * (size_t)p->X.P * ny, ky = 4 * (size_t)p->Y.P * nx;
-  p->off_ybx = off; off = align256(off + kx * esz);
-  p->off_tx = off; off = align256(off + kx * esz);
-  p->off_ybx2 = off; off = align256(off + kx * esz);
-  p->off_tx2 = off; off = align256(off + kx * esz);
-  p->off_yby = off; off = align256(off + ky * esz);
-  p->off_ty = off; off = align256(off + ky * esz);
-  p->off_yby2 = off; off = align256(off + ky * esz);
-  p->off_ty2 = off; off = align256(off + ky * esz);
-  p->work_bytes = off;
-  *plan = p;
-  return CHX_OK;
-}
-
-extern "C" size_t ch_work_bytes(const chx_ch_plan* p) {
-  if (!p || p->hdr.magic != kMagicCh) return 0;
-  return p->work_bytes;
-}
-
-static cudaEvent_t prof_event(chx_ch_plan* p) {
-  if (!p->ev_pool->empty()) {
-    cudaEvent_t e = p->ev_pool->back();
-    p->ev_pool->pop_back();
+cudaEvent_t Prof::get() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
     return e;
   }
   cudaEvent_t e = nullptr;
@@ -579,83 +523,266 @@ static cudaEvent_t prof_event(chx_ch_plan* p) {
   return e;
 }
 
-// Brackets one kernel launch with events when profiling is on.
-struct ProfScope {
-  chx_ch_plan* p;
-  int slot;
-  cudaStream_t st;
-  cudaEvent_t e0 = nullptr;
-  ProfScope(chx_ch_plan* p_, int slot_, cudaStream_t st_) : p(p_), slot(slot_), st(st_) {
-    if (p->prof_on) {
-      e0 = prof_event(p);
-      cudaEventRecord(e0, st);
-    }
-  }
-  ~ProfScope() {
-    if (e0) {
-      cudaEvent_t e1 = prof_event(p);
-      cudaEventRecord(e1, st);
-      p->pend->push_back({e0, e1});
-      p->pend_slot->push_back(slot);
-    }
-  }
-};
-#define PROF(slot) ProfScope prof_scope_##slot(p, slot, st)
-
-template <typename T>
-static T* wptr(void* work, size_t off) {
-  return (T*)((char*)work + off);
+void Prof::release_all() {
+  for (auto& e : pend) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+  for (auto e : pool) cudaEventDestroy(e);
+  pend.clear();
+  pool.clear();
+  slot.clear();
 }
 
-static void step_f64(chx_ch_plan* p, double* cur, double* prev, void* work, int keep_roles, cudaStream_t st) {
-  const int nx = p->nx, ny = p->ny;
-  double* f = wptr<double>(work, p->off_f);
-  double* w = wptr<double>(work, p->off_w);
-  double *ybx = wptr<double>(work, p->off_ybx), *tx = wptr<double>(work, p->off_tx);
-  double *yby = wptr<double>(work, p->off_yby), *ty = wptr<double>(work, p->off_ty);
-  const dim3 tgrid(ceil_div(nx, kT), ceil_div(ny, kT)), tblock(kT, kBY);
-  const SpikeDir &X = p->X, &Y = p->Y;
-  const dim3 gx(ceil_div(ny, kSolveThreads), X.P), gy(ceil_div(nx, kSolveThreads), Y.P);
-  { PROF(kRhs); ch_rhs_kernel<double, double><<<tgrid, tblock, 0, st>>>(cur, prev, f, nx, ny, p->rho, p->kap, p->gl, p->k1, p->k2); }
-  { PROF(kLocX); spike_local_kernel<double, double><<<gx, kSolveThreads, 0, st>>>(f, f, ny, ny, X.m, X.a, X.d_lu, ybx); }
-  { PROF(kRedX); spike_reduced_kernel<double><<<dim3(gx.x, 4 * X.P), kSolveThreads, 0, st>>>(ybx, X.d_rinv, tx, ny, 4 * X.P); }
-  { PROF(kFinX); ch_xfinish_kernel<double, double, false><<<tgrid, tblock, 0, st>>>(f, tx, nullptr, nullptr, X.d_vw, w, nx, ny, X.m, X.P); }
-  { PROF(kLocY); spike_local_kernel<double, double><<<gy, kSolveThreads, 0, st>>>(w, w, nx, nx, Y.m, Y.a, Y.d_lu, yby); }
-  { PROF(kRedY); spike_reduced_kernel<double><<<dim3(gy.x, 4 * Y.P), kSolveThreads, 0, st>>>(yby, Y.d_rinv, ty, nx, 4 * Y.P); }
-  { PROF(kUpd); ch_update_kernel<double, false><<<dim3(ceil_div(nx, kSolveThreads), ny), kSolveThreads, 0, st>>>(
-        w, ty, nullptr, nullptr, Y.d_vw, cur, prev, nx, ny, Y.m, Y.P, keep_roles); }
+int Prof::read(double* ms_out, long long* n_out, int max_slots, int reset) {
+  for (size_t k = 0; k < pend.size(); ++k) {
+    int rc = cuda_check(cudaEventSynchronize(pend[k].second), "ch_profile_read: event synchronize");
+    if (rc) return rc;
+    float t = 0.f;
+    cudaEventElapsedTime(&t, pend[k].first, pend[k].second);
+    ms[slot[k]] += t;
+    n[slot[k]] += 1;
+    pool.push_back(pend[k].first);
+    pool.push_back(pend[k].second);
+  }
+  pend.clear();
+  slot.clear();
+  for (int k = 0; k < max_slots && k < kSlots; ++k) {
+    if (ms_out) ms_out[k] = ms[k];
+    if (n_out) n_out[k] = n[k];
+  }
+  if (reset)
+    for (int k = 0; k < kSlots; ++k) { ms[k] = 0.0; n[k] = 0; }
+  return kSlots;
 }
 
-static void step_f32r(chx_ch_plan* p, double* cur, double* prev, void* work, int keep_roles, cudaStream_t st) {
-  const int nx = p->nx, ny = p->ny;
-  float* f = wptr<float>(work, p->off_f);
-  float* w = wptr<float>(work, p->off_w);
-  float* y1 = wptr<float>(work, p->off_y1);
-  float* y2 = wptr<float>(work, p->off_y2);
-  float *ybx = wptr<float>(work, p->off_ybx), *tx = wptr<float>(work, p->off_tx);
-  float *ybx2 = wptr<float>(work, p->off_ybx2), *tx2 = wptr<float>(work, p->off_tx2);
-  float *yby = wptr<float>(work, p->off_yby), *ty = wptr<float>(work, p->off_ty);
-  float *yby2 = wptr<float>(work, p->off_yby2), *ty2 = wptr<float>(work, p->off_ty2);
-  const dim3 tgrid(ceil_div(nx, kT), ceil_div(ny, kT)), tblock(kT, kBY);
-  const SpikeDir &X = p->X, &Y = p->Y;
-  const dim3 gx(ceil_div(ny, kSolveThreads), X.P), gy(ceil_div(nx, kSolveThreads), Y.P);
-  { PROF(kRhs); ch_rhs_kernel<float, float><<<tgrid, tblock, 0, st>>>(cur, prev, f, nx, ny, (float)p->rho, (float)p->kap,
-                                                        (float)p->gl, (float)p->k1, (float)p->k2); }
-  // x: first FP32 solve, FP64-residual refinement, combine + transpose.
-  { PROF(kLocX); spike_local_kernel<float, float><<<gx, kSolveThreads, 0, st>>>(f, y1, ny, ny, X.m, (float)X.a, X.d_lu32, ybx); }
-  { PROF(kRedX); spike_reduced_kernel<float><<<dim3(gx.x, 4 * X.P), kSolveThreads, 0, st>>>(ybx, X.d_rinv32, tx, ny, 4 * X.P); }
-  { PROF(kRefX); spike_refine_kernel<<<gx, kSolveThreads, 0, st>>>(f, y1, tx, y2, ybx2, ny, ny, nx, X.m, X.P, X.a, X.b, X.c,
-                                                    (float)X.a, X.d_lu32, X.d_vw32); }
-  { PROF(kRed2X); spike_reduced_kernel<float><<<dim3(gx.x, 4 * X.P), kSolveThreads, 0, st>>>(ybx2, X.d_rinv32, tx2, ny, 4 * X.P); }
-  { PROF(kFinX); ch_xfinish_kernel<float, float, true><<<tgrid, tblock, 0, st>>>(y1, tx, y2, tx2, X.d_vw32, w, nx, ny, X.m, X.P); }
+ProfScope::ProfScope(Prof* p_, int slot_, cudaStream_t st_) : p(p_), slot(slot_), st(st_) {
+  if (p && p->on) {
+    e0 = p->get();
+    cudaEventRecord(e0, st);
+  }
+}
+
+ProfScope::~ProfScope() {
+  if (e0) {
+    cudaEvent_t e1 = p->get();
+    cudaEventRecord(e1, st);
+    p->pend.push_back({e0, e1});
+    p->slot.push_back(slot);
+  }
+}
+#define PROF(slot) ProfScope prof_scope_##slot(prof, slot, st)
+
+std::vector<int> segment_candidates(int n, int nsys, int precision) {
+  (void)precision;
+  std::vector<int> out;
+  const int d = default_segments(n, nsys);
+  out.push_back(d);
+  for (int P = 1; P <= n / 8 && P <= 64; ++P)
+    if (n % P == 0 && P != d && (P == d / 2 || P == 2 * d || P == d / 4 || P == 4 * d)) out.push_back(P);
+  return out;
+}
+
+static int group_move_params_gl(ChGroup* g, int from, int to) {
+  int rc = cuda_check(cudaMemcpy(g->d_gl + to, g->d_gl + from, 8, cudaMemcpyDeviceToDevice), "ch: replicate");
+  if (!rc) rc = cuda_check(cudaMemcpy(g->d_glff + to, g->d_glff + from, 8, cudaMemcpyDeviceToDevice), "ch: replicate");
+  return rc;
+}
+
+int group_init(ChGroup* g, int nx, int ny, double lx, double ly, double gamma, double dt, int precision, int G,
+               int px, int py) {
+  if (nx < 8 || ny < 8 || nx > 16384 || ny > 16384)
+    return fail(CHX_EINVAL, "ch: nx %d, ny %d outside [8, 16384]", nx, ny);
+  if (!(lx > 0) || !(ly > 0) || !(dt > 0) || !(gamma >= 0) || !isfinite(lx) || !isfinite(ly) || !isfinite(dt) ||
+      !isfinite(gamma))
+    return fail(CHX_EINVAL, "ch: lx %g, ly %g, dt %g, gamma %g", lx, ly, dt, gamma);
+  if (precision != CHX_PREC_F64 && precision != CHX_PREC_F32_REFINE)
+    return fail(CHX_EINVAL, "ch: precision %d", precision);
+  if (G < 1 || G > 65535) return fail(CHX_EINVAL, "ch: group size %d", G);
+  if ((px && (nx % px || nx / px < 8)) || (py && (ny % py || ny / py < 8)))
+    return fail(CHX_EINVAL, "ch: segment counts %d, %d must divide nx, ny with >= 8 points each", px, py);
+  g->nx = nx; g->ny = ny; g->G = G; g->precision = precision;
+  g->lx = lx; g->ly = ly; g->gamma = gamma; g->dt = dt;
+  g->dx = lx / nx; g->dy = ly / ny;
+  const double sx = 1.0 / (g->dx * g->dx);
+  g->rho = (g->dx * g->dx) / (g->dy * g->dy);
+  g->kap = -2.0 * (1.0 + g->rho);
+  g->k1 = 2.0 / 3.0;
+  g->k2 = (2.0 / 3.0) * dt * sx;
+  g->kff.rho = split_ff(g->rho);
+  g->kff.kap = split_ff(g->kap);
+  g->kff.gl = split_ff(0.0);
+  g->kff.k1 = split_ff(g->k1);
+  g->kff.k2 = split_ff(g->k2);
+  int rc;
+  if ((rc = dir_alloc(&g->X, nx, px ? px : default_segments(nx, G * ny), G)) ||
+      (rc = dir_alloc(&g->Y, ny, py ? py : default_segments(ny, nx * G), G)) || (rc = dev_alloc(&g->d_gl, G)) ||
+      (rc = dev_alloc(&g->d_glff, G)) || (rc = group_set_gamma(g, 0, gamma)) || (rc = dir_replicate(&g->X)) ||
+      (rc = dir_replicate(&g->Y))) {
+    group_free(g);
+    return rc;
+  }
+  for (int z = 1; z < G && !rc; ++z) rc = group_move_params_gl(g, 0, z);
+  if (rc) {
+    group_free(g);
+    return rc;
+  }
+  const size_t N = (size_t)nx * ny * G;
+  const int f64 = precision == CHX_PREC_F64;
+  const size_t esz = f64 ? 8 : 4;
+  const size_t mix = f64 ? 0 : N * esz;
+  size_t off = 0;
+  g->off_f = off; off = align256(off + N * esz);
+  g->off_flo = off; off = align256(off + mix);
+  g->off_w = off; off = align256(off + N * esz);
+  g->off_wlo = off; off = align256(off + mix);
+  g->off_y1 = off; off = align256(off + mix);
+  g->off_y2 = off; off = align256(off + mix);
+  const size_t kx = 4 * (size_t)g->X.P * ny * G, ky = 4 * (size_t)g->Y.P * nx * G;
+  g->off_ybx = off; off = align256(off + kx * esz);
+  g->off_tx = off; off = align256(off + kx * esz);
+  g->off_ybx2 = off; off = align256(off + (f64 ? 0 : kx * esz));
+  g->off_tx2 = off; off = align256(off + (f64 ? 0 : kx * esz));
+  g->off_yby = off; off = align256(off + ky * esz);
+  g->off_ty = off; off = align256(off + ky * esz);
+  g->off_yby2 = off; off = align256(off + (f64 ? 0 : ky * esz));
+  g->off_ty2 = off; off = align256(off + (f64 ? 0 : ky * esz));
+  g->work_bytes = off;
+  return CHX_OK;
+}
+
+int group_set_gamma(ChGroup* g, int z, double gamma) {
+  if (z < 0 || z >= g->G || !(gamma >= 0) || !isfinite(gamma)) return fail(CHX_EINVAL, "ch: slot %d gamma %g", z, gamma);
+  const double ax = (2.0 / 3.0) * gamma * g->dt / (g->dx * g->dx * g->dx * g->dx);
+  const double ay = (2.0 / 3.0) * gamma * g->dt / (g->dy * g->dy * g->dy * g->dy);
+  int rc;
+  if ((rc = dir_set(&g->X, z, ax)) || (rc = dir_set(&g->Y, z, ay))) return rc;
+  const double gl = gamma / (g->dx * g->dx);
+  const float2 glff = split_ff(gl);
+  if ((rc = cuda_check(cudaMemcpy(g->d_gl + z, &gl, sizeof(double), cudaMemcpyHostToDevice), "ch: gamma upload")))
+    return rc;
+  if (z == 0) g->gamma = gamma;
+  return cuda_check(cudaMemcpy(g->d_glff + z, &glff, sizeof(float2), cudaMemcpyHostToDevice), "ch: gamma upload");
+}
+
+int group_move_params(ChGroup* g, int from, int to, cudaStream_t st) {
+  if (from == to) return CHX_OK;
+  int rc;
+  if ((rc = dir_move(&g->X, from, to, st)) || (rc = dir_move(&g->Y, from, to, st))) return rc;
+  if ((rc = cuda_check(cudaMemcpyAsync(g->d_gl + to, g->d_gl + from, 8, cudaMemcpyDeviceToDevice, st), "ch: move")))
+    return rc;
+  return cuda_check(cudaMemcpyAsync(g->d_glff + to, g->d_glff + from, 8, cudaMemcpyDeviceToDevice, st), "ch: move");
+}
+
+void group_free(ChGroup* g) {
+  free_dir(&g->X);
+  free_dir(&g->Y);
+  cudaFree(g->d_gl);
+  cudaFree(g->d_glff);
+  g->d_gl = nullptr;
+  g->d_glff = nullptr;
+}
+
+static void step_f64(ChGroup* g, int G, double* cur, double* prev, void* work, int keep_roles, cudaStream_t st,
+                     Prof* prof) {
+  const int nx = g->nx, ny = g->ny;
+  const size_t N = (size_t)nx * ny;
+  double* f = wptr<double>(work, g->off_f);
+  double* w = wptr<double>(work, g->off_w);
+  double *ybx = wptr<double>(work, g->off_ybx), *tx = wptr<double>(work, g->off_tx);
+  double *yby = wptr<double>(work, g->off_yby), *ty = wptr<double>(work, g->off_ty);
+  const dim3 tgrid(ceil_div(nx, kT), ceil_div(ny, kT), G), tblock(kT, kBY);
+  const int nsx = G * ny;  // the x sweep: all row systems of the group, interleaved
+  const DirView<double> X = view<double>(g->X, ny), Y = view<double>(g->Y, nx);
+  const dim3 gx(ceil_div(nsx, kSolveThreads), X.P), gy(ceil_div(nx, kSolveThreads), Y.P, G);
+  const size_t kyz = 4 * (size_t)Y.P * nx;
+  { PROF(kRhs); ch_rhs_kernel<double, double><<<tgrid, tblock, 0, st>>>(cur, prev, f, nx, ny, G, g->rho, g->kap, g->d_gl, g->k1, g->k2); }
+  { PROF(kLocX); spike_local_kernel<double, double><<<gx, kSolveThreads, 0, st>>>(f, f, nsx, nsx, X, ybx, 0, 0); }
+  { PROF(kRedX); spike_reduced_kernel<double><<<dim3(gx.x, 4 * X.P), kSolveThreads, 0, st>>>(ybx, X, tx, nsx, 0); }
+  { PROF(kFinX); ch_xfinish_kernel<double, double><<<tgrid, tblock, 0, st>>>(f, tx, X, w, nx, ny, G); }
+  { PROF(kLocY); spike_local_kernel<double, double><<<gy, kSolveThreads, 0, st>>>(w, w, nx, nx, Y, yby, N, kyz); }
+  { PROF(kRedY); spike_reduced_kernel<double><<<dim3(gy.x, 4 * Y.P, G), kSolveThreads, 0, st>>>(yby, Y, ty, nx, kyz); }
+  { PROF(kUpd); ch_update_kernel<double><<<dim3(ceil_div(nx, kSolveThreads), ny, G), kSolveThreads, 0, st>>>(
+        w, ty, Y, cur, prev, nx, ny, keep_roles); }
+}
+
+static void step_f32r(ChGroup* g, int G, double* cur, double* prev, void* work, int keep_roles, cudaStream_t st,
+                      Prof* prof) {
+  const int nx = g->nx, ny = g->ny;
+  const size_t N = (size_t)nx * ny;
+  float *fhi = wptr<float>(work, g->off_f), *flo = wptr<float>(work, g->off_flo);
+  float *whi = wptr<float>(work, g->off_w), *wlo = wptr<float>(work, g->off_wlo);
+  float* y1 = wptr<float>(work, g->off_y1);
+  float* y2 = wptr<float>(work, g->off_y2);
+  float *ybx = wptr<float>(work, g->off_ybx), *tx = wptr<float>(work, g->off_tx);
+  float *ybx2 = wptr<float>(work, g->off_ybx2), *tx2 = wptr<float>(work, g->off_tx2);
+  float *yby = wptr<float>(work, g->off_yby), *ty = wptr<float>(work, g->off_ty);
+  float *yby2 = wptr<float>(work, g->off_yby2), *ty2 = wptr<float>(work, g->off_ty2);
+  const int nsx = G * ny;
+  const DirView<float> X = view<float>(g->X, ny), Y = view<float>(g->Y, nx);
+  const dim3 gx(ceil_div(nsx, kSolveThreads), X.P), gy(ceil_div(nx, kSolveThreads), Y.P, G);
+  const size_t kyz = 4 * (size_t)Y.P * nx;
+  // right-hand side in double-float
+  { PROF(kRhs); launch_ch_rhs_ff(cur, prev, fhi, flo, nx, ny, G, g->kff, g->d_glff, st); }
+  // x: FP32 solve of the high part, double-float residual, FP32 correction solve
+  { PROF(kLocX); spike_local_kernel<float, float><<<gx, kSolveThreads, 0, st>>>(fhi, y1, nsx, nsx, X, ybx, 0, 0); }
+  { PROF(kRedX); spike_reduced_kernel<float><<<dim3(gx.x, 4 * X.P), kSolveThreads, 0, st>>>(ybx, X, tx, nsx, 0); }
+  { PROF(kRefX); launch_spike_refine_ff(fhi, flo, y1, tx, y2, ybx2, nsx, nsx, nx, X, g->X.d_aff, 1, 0, 0, st); }
+  { PROF(kRed2X); spike_reduced_kernel<float><<<dim3(gx.x, 4 * X.P), kSolveThreads, 0, st>>>(ybx2, X, tx2, nsx, 0); }
+  { PROF(kFinX); launch_ch_xfinish_ff(y1, tx, y2, tx2, X, whi, wlo, nx, ny, G, st); }
   // y
-  { PROF(kLocY); spike_local_kernel<float, float><<<gy, kSolveThreads, 0, st>>>(w, y1, nx, nx, Y.m, (float)Y.a, Y.d_lu32, yby); }
-  { PROF(kRedY); spike_reduced_kernel<float><<<dim3(gy.x, 4 * Y.P), kSolveThreads, 0, st>>>(yby, Y.d_rinv32, ty, nx, 4 * Y.P); }
-  { PROF(kRefY); spike_refine_kernel<<<gy, kSolveThreads, 0, st>>>(w, y1, ty, y2, yby2, nx, nx, ny, Y.m, Y.P, Y.a, Y.b, Y.c,
-                                                    (float)Y.a, Y.d_lu32, Y.d_vw32); }
-  { PROF(kRed2Y); spike_reduced_kernel<float><<<dim3(gy.x, 4 * Y.P), kSolveThreads, 0, st>>>(yby2, Y.d_rinv32, ty2, nx, 4 * Y.P); }
-  { PROF(kUpd); ch_update_kernel<float, true><<<dim3(ceil_div(nx, kSolveThreads), ny), kSolveThreads, 0, st>>>(
-        y1, ty, y2, ty2, Y.d_vw32, cur, prev, nx, ny, Y.m, Y.P, keep_roles); }
+  { PROF(kLocY); spike_local_kernel<float, float><<<gy, kSolveThreads, 0, st>>>(whi, y1, nx, nx, Y, yby, N, kyz); }
+  { PROF(kRedY); spike_reduced_kernel<float><<<dim3(gy.x, 4 * Y.P, G), kSolveThreads, 0, st>>>(yby, Y, ty, nx, kyz); }
+  { PROF(kRefY); launch_spike_refine_ff(whi, wlo, y1, ty, y2, yby2, nx, nx, ny, Y, g->Y.d_aff, G, N, kyz, st); }
+  { PROF(kRed2Y); spike_reduced_kernel<float><<<dim3(gy.x, 4 * Y.P, G), kSolveThreads, 0, st>>>(yby2, Y, ty2, nx, kyz); }
+  { PROF(kUpd); launch_ch_update_ff(y1, ty, y2, ty2, Y, cur, prev, nx, ny, G, keep_roles, st); }
+}
+
+void group_step(ChGroup* g, int gact, double* cur, double* prev, void* work, int keep_roles, cudaStream_t st,
+                Prof* prof) {
+  if (g->precision == CHX_PREC_F64) step_f64(g, gact, cur, prev, work, keep_roles, st, prof);
+  else step_f32r(g, gact, cur, prev, work, keep_roles, st, prof);
+}
+
+void ch_plan_free(chx_ch_plan* p) {
+  if (!p) return;
+  group_free(&p->g);
+  if (p->d_partials) cudaFree(p->d_partials);
+  if (p->prof) {
+    p->prof->release_all();
+    delete p->prof;
+  }
+  hdr_free(&p->hdr);
+  p->g.~ChGroup();
+  free(p);
+}
+
+}  // namespace chx
+
+// ---------------------------------------------------------------------------
+extern "C" int ch_plan_create(chx_ch_plan** plan, int nx, int ny, double lx, double ly, double gamma, double dt,
+                              int precision) {
+  if (!plan) return fail(CHX_EINVAL, "ch_plan_create: null plan pointer");
+  *plan = nullptr;
+  if (nx < 8 || ny < 8 || nx > 16384 || ny > 16384)
+    return fail(CHX_EINVAL, "ch_plan_create: nx %d, ny %d outside [8, 16384]", nx, ny);
+  chx_ch_plan* p = (chx_ch_plan*)calloc(1, sizeof(chx_ch_plan));
+  if (!p) return fail(CHX_ENOMEM, "ch_plan_create: plan allocation");
+  new (&p->g) ChGroup();
+  p->prof = new Prof();
+  int rc = hdr_init(&p->hdr, kMagicCh);
+  if (!rc) rc = group_init(&p->g, nx, ny, lx, ly, gamma, dt, precision, 1);
+  if (rc) { ch_plan_free(p); return rc; }
+  if (cudaMalloc(&p->d_partials, 3 * (size_t)kDiagBlocks * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    p->d_partials = nullptr;
+    ch_plan_free(p);
+    return fail(CHX_ENOMEM, "ch_plan_create: diagnostics scratch");
+  }
+  *plan = p;
+  return CHX_OK;
+}
+
+extern "C" size_t ch_work_bytes(const chx_ch_plan* p) {
+  if (!p || p->hdr.magic != kMagicCh) return 0;
+  return p->g.work_bytes;
 }
 
 extern "C" int ch_step(chx_ch_plan* p, double* c_now, double* c_prev, void* work, int nsteps, void* stream) {
@@ -663,17 +790,17 @@ extern "C" int ch_step(chx_ch_plan* p, double* c_now, double* c_prev, void* work
   if (!c_now || !c_prev || !work) return fail(CHX_EINVAL, "ch_step: null pointer");
   if (nsteps < 0) return fail(CHX_EINVAL, "ch_step: nsteps %d < 0", nsteps);
   if (((uintptr_t)work & 255) != 0) return fail(CHX_EINVAL, "ch_step: work must be 256-byte aligned");
-  const size_t fb = (size_t)p->nx * p->ny * sizeof(double);
+  const size_t fb = (size_t)p->g.nx * p->g.ny * sizeof(double);
   const char *a = (const char*)c_now, *b = (const char*)c_prev, *w = (const char*)work;
-  if ((a < b + fb && b < a + fb) || (a < w + p->work_bytes && w < a + fb) || (b < w + p->work_bytes && w < b + fb))
+  const size_t wb = p->g.work_bytes;
+  if ((a < b + fb && b < a + fb) || (a < w + wb && w < a + fb) || (b < w + wb && w < b + fb))
     return fail(CHX_EINVAL, "ch_step: c_now, c_prev and work must not overlap");
   cudaStream_t st = (cudaStream_t)stream;
   double *cur = c_now, *prev = c_prev;
   for (int s = 0; s < nsteps; ++s) {
     const int last = s == nsteps - 1;
     const int keep = last && cur == c_now;
-    if (p->precision == CHX_PREC_F64) step_f64(p, cur, prev, work, keep, st);
-    else step_f32r(p, cur, prev, work, keep, st);
+    group_step(&p->g, 1, cur, prev, work, keep, st, p->prof);
     if (!keep) {
       double* t = cur;
       cur = prev;
@@ -690,9 +817,10 @@ extern "C" int ch_diagnostics(chx_ch_plan* p, const double* c, double* mass_out,
   if (!p || p->hdr.magic != kMagicCh) return fail(CHX_EINVAL, "ch_diagnostics: bad plan");
   if (!c || !mass_out || !energy_out) return fail(CHX_EINVAL, "ch_diagnostics: null pointer");
   cudaStream_t st = (cudaStream_t)stream;
-  const double hx = 0.5 * p->gamma / (p->dx * p->dx), hy = 0.5 * p->gamma / (p->dy * p->dy);
-  ch_diag_partial_kernel<<<kDiagBlocks, kDiagThreads, 0, st>>>(c, p->nx, p->ny, hx, hy, p->d_partials);
-  ch_diag_final_kernel<<<1, 32, 0, st>>>(p->d_partials, kDiagBlocks, p->dx * p->dy, mass_out, energy_out,
+  const ChGroup& g = p->g;
+  const double hx = 0.5 * g.gamma / (g.dx * g.dx), hy = 0.5 * g.gamma / (g.dy * g.dy);
+  ch_diag_partial_kernel<<<kDiagBlocks, kDiagThreads, 0, st>>>(c, g.nx, g.ny, hx, hy, p->d_partials);
+  ch_diag_final_kernel<<<1, 32, 0, st>>>(p->d_partials, kDiagBlocks, g.dx * g.dy, mass_out, energy_out,
                                          p->hdr.d_status);
   p->hdr.last_stream = st;
   return launch_check("ch_diagnostics");
@@ -700,33 +828,13 @@ extern "C" int ch_diagnostics(chx_ch_plan* p, const double* c, double* mass_out,
 
 extern "C" int ch_profile(chx_ch_plan* p, int enable) {
   if (!p || p->hdr.magic != kMagicCh) return fail(CHX_EINVAL, "ch_profile: bad plan");
-  p->prof_on = enable ? 1 : 0;
+  p->prof->on = enable ? 1 : 0;
   return CHX_OK;
 }
 
 extern "C" int ch_profile_read(chx_ch_plan* p, double* ms, long long* launches, int max_slots, int reset) {
   if (!p || p->hdr.magic != kMagicCh) return fail(CHX_EINVAL, "ch_profile_read: bad plan");
-  for (size_t k = 0; k < p->pend->size(); ++k) {
-    auto& e = (*p->pend)[k];
-    int rc = cuda_check(cudaEventSynchronize(e.second), "ch_profile_read: event synchronize");
-    if (rc) return rc;
-    float t = 0.f;
-    cudaEventElapsedTime(&t, e.first, e.second);
-    const int slot = (*p->pend_slot)[k];
-    p->prof_ms[slot] += t;
-    p->prof_n[slot] += 1;
-    p->ev_pool->push_back(e.first);
-    p->ev_pool->push_back(e.second);
-  }
-  p->pend->clear();
-  p->pend_slot->clear();
-  for (int k = 0; k < max_slots && k < kSlots; ++k) {
-    if (ms) ms[k] = p->prof_ms[k];
-    if (launches) launches[k] = p->prof_n[k];
-  }
-  if (reset)
-    for (int k = 0; k < kSlots; ++k) { p->prof_ms[k] = 0.0; p->prof_n[k] = 0; }
-  return kSlots;
+  return p->prof->read(ms, launches, max_slots, reset);
 }
 
 extern "C" const char* ch_profile_slot_name(int slot) {

@@ -1,0 +1,101 @@
+// A group of same-shape Cahn-Hilliard simulations advanced together by one set
+// of batched launches (the ADI step of Eq. 3.1 for G fields at once).  The
+// single-simulation plan (ch_plan_*) is a group of one; the ensemble runtime
+// (ens.cu) keeps one group per distinct (n, gamma, L, dt).
+#pragma once
+
+#include <utility>
+#include <vector>
+
+#include "chx_internal.cuh"
+#include "mixed.cuh"
+
+namespace chx {
+
+// Partitioned (SPIKE-type) factors of the constant cyclic operator
+// I + a delta^4 along one direction.  Every simulation slot of a group has its
+// own block (its own gamma, hence its own a): slot z's factors start at
+// z * 4m (lu, vw) and z * (4P)^2 (rinv).
+struct SpikeDir {
+  int n = 0, P = 1, m = 0, slots = 0;
+  double* d_a = nullptr;        // slots: a = (2/3) gamma dt / h^4
+  double* d_lu = nullptr;       // slots x 4m: ralpha, beta, gam, del of the segment block
+  double* d_vw = nullptr;       // slots x 4m: spikes V0, V1, W0, W1
+  double* d_rinv = nullptr;     // slots x (4P)^2 reduced-system inverse
+  float* d_a32 = nullptr;
+  float2* d_aff = nullptr;      // a as a double-float pair
+  float* d_lu32 = nullptr;
+  float* d_vw32 = nullptr;
+  float* d_rinv32 = nullptr;
+};
+
+// Per-direction view handed to the kernels: slot of system j = blockIdx.z + j / spp.
+template <typename T>
+struct DirView {
+  const T* a;
+  const T* lu;
+  const T* vw;
+  const T* rinv;
+  int m, P, spp;
+};
+
+// Per-kernel CUDA-event timing (ch_profile).
+enum ProfSlot { kRhs, kLocX, kRedX, kRefX, kRed2X, kFinX, kLocY, kRedY, kRefY, kRed2Y, kUpd, kSlots };
+extern const char* const kSlotName[kSlots];
+
+struct Prof {
+  int on = 0;
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pend;
+  std::vector<int> slot;
+  double ms[kSlots] = {0};
+  long long n[kSlots] = {0};
+  cudaEvent_t get();
+  void release_all();
+  int read(double* ms_out, long long* n_out, int max_slots, int reset);
+};
+
+struct ProfScope {
+  Prof* p;
+  int slot;
+  cudaStream_t st;
+  cudaEvent_t e0 = nullptr;
+  ProfScope(Prof* p_, int slot_, cudaStream_t st_);
+  ~ProfScope();
+};
+
+struct ChGroup {
+  int nx = 0, ny = 0, G = 0, precision = 0;
+  double lx = 0, ly = 0, gamma = 0, dt = 0, dx = 0, dy = 0;
+  double rho = 0, kap = 0, k1 = 0, k2 = 0;  // right-hand side constants shared by the slots
+  FFConst kff;                               // the same as double-float pairs (gl unused there)
+  double* d_gl = nullptr;                    // slots: gamma / dx^2
+  float2* d_glff = nullptr;
+  SpikeDir X, Y;
+  // work layout (byte offsets), for G fields
+  size_t off_f = 0, off_flo = 0, off_w = 0, off_wlo = 0, off_y1 = 0, off_y2 = 0;
+  size_t off_ybx = 0, off_tx = 0, off_ybx2 = 0, off_tx2 = 0, off_yby = 0, off_ty = 0, off_yby2 = 0, off_ty2 = 0;
+  size_t work_bytes = 0;
+};
+
+// Validates, factorises both directions on the host (FP64) for `gamma` and
+// uploads them into every slot.  px / py > 0 force the segment counts (the
+// ensemble autotuner); 0 = default.
+int group_init(ChGroup* g, int nx, int ny, double lx, double ly, double gamma, double dt, int precision, int G,
+               int px = 0, int py = 0);
+// Refactorises slot z of the group for a new gamma (host FP64, synchronous upload).
+int group_set_gamma(ChGroup* g, int z, double gamma);
+// Copies slot `from`'s parameters onto slot `to` (device to device, on st).
+int group_move_params(ChGroup* g, int from, int to, cudaStream_t st);
+void group_free(ChGroup* g);
+// Candidate segment counts for n points and nsys systems (divisors of n with
+// at least 8 points per segment), default first.
+std::vector<int> segment_candidates(int n, int nsys, int precision);
+// One step for the first `gact` fields of the group: cur / prev point to
+// gact contiguous fields of nx*ny doubles (C^n, C^{n-1}).  keep_roles = 0
+// writes C^{n+1} over prev (caller swaps); 1 writes C^n into prev and C^{n+1}
+// into cur.
+void group_step(ChGroup* g, int gact, double* cur, double* prev, void* work, int keep_roles, cudaStream_t st,
+                Prof* prof);
+
+}  // namespace chx

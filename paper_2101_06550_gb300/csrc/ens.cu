@@ -1,0 +1,396 @@
+// Ensemble runtime: many Cahn-Hilliard simulations of uneven sizes advanced
+// together (the batched pattern the thesis's 2D statistics rest on, Sec. 7.2:
+// batches of simulations per domain size, run concurrently).
+//
+// Simulations that share (n, L) form a group: one ChGroup (one set of batched
+// launches per step) with packed device-resident state, C^n and C^{n-1} for
+// `capacity` slots, and per-slot LHS factors, so a group mixes any gammas
+// (one LHS per distinct matrix, as the thesis proposes for uneven batches).  Slots [0, active) of a group
+// are stepped; the host keeps them packed (ens_slot_move).  ens_step replays a
+// CUDA graph holding two steps of every group, each group on its own branch so
+// small groups overlap large ones; an odd leftover step runs eagerly.  The two
+// state buffers of a group swap roles each step (no copy).
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "chgroup.cuh"
+
+using namespace chx;
+
+namespace {
+
+
+struct EnsGroup {
+  ChGroup g;
+  int n = 0, capacity = 0, active = 0;
+  double l = 0, gamma = 0;
+  double* d_state[2] = {nullptr, nullptr};  // each capacity * n * n doubles
+  int cur = 0;                              // index of the buffer holding C^n
+  void* d_work = nullptr;
+  size_t work_bytes = 0, bytes = 0;
+  cudaStream_t stream = nullptr;            // branch stream used during capture
+  cudaEvent_t done = nullptr;
+  std::vector<double> slot_gamma;           // gamma each slot is factorised for
+  bool live = false;
+};
+
+}  // namespace
+
+struct chx_ens {
+  PlanHdr hdr;
+  int precision;
+  double dt;
+  size_t budget, used;
+  std::vector<EnsGroup*>* groups;
+  cudaGraphExec_t exec;
+  bool dirty;  // active counts or groups changed since the graph was built
+  cudaEvent_t fork;
+  cudaStream_t cap;  // private stream the graph is captured on (never the legacy stream)
+};
+
+namespace {
+
+size_t state_bytes(int n, int cap) { return 2 * (size_t)cap * n * n * sizeof(double); }
+
+void free_group(EnsGroup* G) {
+  if (!G) return;
+  group_free(&G->g);
+  cudaFree(G->d_state[0]);
+  cudaFree(G->d_state[1]);
+  cudaFree(G->d_work);
+  if (G->stream) cudaStreamDestroy(G->stream);
+  if (G->done) cudaEventDestroy(G->done);
+  delete G;
+}
+
+EnsGroup* get_group(chx_ens* e, int id) {
+  if (!e || e->hdr.magic != kMagicEns || id < 0 || id >= (int)e->groups->size()) return nullptr;
+  EnsGroup* G = (*e->groups)[id];
+  return (G && G->live) ? G : nullptr;
+}
+
+void drop_graph(chx_ens* e) {
+  if (e->exec) cudaGraphExecDestroy(e->exec);
+  e->exec = nullptr;
+  e->dirty = true;
+}
+
+void step_group(EnsGroup* G, cudaStream_t st) {
+  if (G->active < 1) return;
+  const size_t N = (size_t)G->n * G->n;
+  (void)N;
+  group_step(&G->g, G->active, G->d_state[G->cur], G->d_state[1 - G->cur], G->d_work, 0, st, nullptr);
+  G->cur = 1 - G->cur;
+}
+
+// Two steps of every active group, each group on its own branch.  Captured on
+// the ensemble's private stream; the instantiated graph can launch on any stream.
+int build_graph(chx_ens* e) {
+  drop_graph(e);
+  cudaGraph_t graph = nullptr;
+  cudaStream_t st = e->cap;
+  int rc = cuda_check(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "ens: begin capture");
+  if (rc) return rc;
+  cudaEventRecord(e->fork, st);
+  std::vector<int> saved;
+  for (EnsGroup* G : *e->groups) {
+    saved.push_back(G && G->live ? G->cur : 0);
+    if (!G || !G->live || G->active < 1) continue;
+    cudaStreamWaitEvent(G->stream, e->fork, 0);
+    step_group(G, G->stream);
+    step_group(G, G->stream);
+    cudaEventRecord(G->done, G->stream);
+    cudaStreamWaitEvent(st, G->done, 0);
+  }
+  cudaError_t ce = cudaStreamEndCapture(st, &graph);
+  // capture does not execute: put the role flags back (two flips cancel anyway)
+  for (size_t k = 0; k < e->groups->size(); ++k)
+    if ((*e->groups)[k] && (*e->groups)[k]->live) (*e->groups)[k]->cur = saved[k];
+  rc = cuda_check(ce, "ens: end capture");
+  if (!rc) rc = cuda_check(cudaGraphInstantiate(&e->exec, graph, 0), "ens: graph instantiate");
+  if (graph) cudaGraphDestroy(graph);
+  if (rc) {
+    e->exec = nullptr;
+    return rc;
+  }
+  e->dirty = false;
+  return CHX_OK;
+}
+
+}  // namespace
+
+namespace chx {
+void ens_free(chx_ens* e) {
+  if (!e) return;
+  drop_graph(e);
+  if (e->groups) {
+    for (EnsGroup* G : *e->groups) free_group(G);
+    delete e->groups;
+  }
+  if (e->fork) cudaEventDestroy(e->fork);
+  if (e->cap) cudaStreamDestroy(e->cap);
+  hdr_free(&e->hdr);
+  free(e);
+}
+}  // namespace chx
+
+extern "C" int ens_create(chx_ens** out, int precision, double dt, size_t hbm_budget_bytes) {
+  if (!out) return fail(CHX_EINVAL, "ens_create: null pointer");
+  *out = nullptr;
+  if (precision != CHX_PREC_F64 && precision != CHX_PREC_F32_REFINE)
+    return fail(CHX_EINVAL, "ens_create: precision %d", precision);
+  if (!(dt > 0) || !isfinite(dt)) return fail(CHX_EINVAL, "ens_create: dt %g", dt);
+  chx_ens* e = (chx_ens*)calloc(1, sizeof(chx_ens));
+  if (!e) return fail(CHX_ENOMEM, "ens_create: allocation");
+  int rc = hdr_init(&e->hdr, kMagicEns);
+  e->precision = precision;
+  e->dt = dt;
+  e->budget = hbm_budget_bytes;
+  e->groups = new std::vector<EnsGroup*>();
+  e->dirty = true;
+  if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming), "ens_create: event");
+  if (!rc) rc = cuda_check(cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking), "ens_create: stream");
+  if (rc) { ens_free(e); return rc; }
+  *out = e;
+  return CHX_OK;
+}
+
+extern "C" int ens_group_create(chx_ens* e, int n, double l, double gamma, int capacity, int* group_id) {
+  if (!e || e->hdr.magic != kMagicEns || !group_id) return fail(CHX_EINVAL, "ens_group_create: bad argument");
+  if (capacity < 1 || capacity > 65535) return fail(CHX_EINVAL, "ens_group_create: capacity %d", capacity);
+  EnsGroup* G = new (std::nothrow) EnsGroup();
+  if (!G) return fail(CHX_ENOMEM, "ens_group_create: host allocation");
+  int rc = group_init(&G->g, n, n, l, l, gamma, e->dt, e->precision, capacity);
+  if (rc) { free_group(G); return rc; }
+  G->n = n; G->l = l; G->gamma = gamma; G->capacity = capacity;
+  G->slot_gamma.assign(capacity, gamma);
+  // room for the autotuner's larger segment counts (their boundary arrays grow with P)
+  G->work_bytes = G->g.work_bytes + G->g.work_bytes / 4 + (1 << 20);
+  G->bytes = state_bytes(n, capacity) + G->work_bytes;
+  if (e->budget && e->used + G->bytes > e->budget) {
+    free_group(G);
+    return fail(CHX_ENOMEM, "ens_group_create: %zu bytes over the HBM budget (%zu of %zu used)", G->bytes, e->used,
+                e->budget);
+  }
+  const size_t sb = (size_t)capacity * n * n * sizeof(double);
+  if (cudaMalloc(&G->d_state[0], sb) != cudaSuccess || cudaMalloc(&G->d_state[1], sb) != cudaSuccess ||
+      cudaMalloc(&G->d_work, G->work_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    free_group(G);
+    return fail(CHX_ENOMEM, "ens_group_create: device allocation of %zu bytes", G->bytes);
+  }
+  if ((rc = cuda_check(cudaStreamCreateWithFlags(&G->stream, cudaStreamNonBlocking), "ens: stream")) ||
+      (rc = cuda_check(cudaEventCreateWithFlags(&G->done, cudaEventDisableTiming), "ens: event"))) {
+    free_group(G);
+    return rc;
+  }
+  G->live = true;
+  e->used += G->bytes;
+  e->groups->push_back(G);
+  *group_id = (int)e->groups->size() - 1;
+  drop_graph(e);
+  return CHX_OK;
+}
+
+extern "C" int ens_group_destroy(chx_ens* e, int group_id) {
+  EnsGroup* G = get_group(e, group_id);
+  if (!G) return fail(CHX_EINVAL, "ens_group_destroy: bad group %d", group_id);
+  cudaDeviceSynchronize();
+  e->used -= G->bytes;
+  free_group(G);
+  (*e->groups)[group_id] = nullptr;
+  drop_graph(e);
+  return CHX_OK;
+}
+
+extern "C" int ens_slot_load(chx_ens* e, int group_id, int slot, const double* c0, const double* cm1,
+                             double gamma, void* stream) {
+  EnsGroup* G = get_group(e, group_id);
+  if (!G || !c0 || slot < 0 || slot >= G->capacity) return fail(CHX_EINVAL, "ens_slot_load: bad argument");
+  const size_t nb = (size_t)G->n * G->n * sizeof(double);
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = CHX_OK;
+  if (gamma >= 0 && gamma != G->slot_gamma[slot]) {
+    // the refactorisation uploads synchronously; wait for earlier work on the slot first
+    rc = cuda_check(cudaStreamSynchronize(st), "ens_slot_load: synchronize");
+    if (!rc) rc = group_set_gamma(&G->g, slot, gamma);
+    if (rc) return rc;
+    G->slot_gamma[slot] = gamma;
+  }
+  rc = cuda_check(cudaMemcpyAsync((char*)G->d_state[G->cur] + slot * nb, c0, nb, cudaMemcpyDefault, st),
+                      "ens_slot_load: C^n");
+  if (!rc)
+    rc = cuda_check(cudaMemcpyAsync((char*)G->d_state[1 - G->cur] + slot * nb, cm1 ? cm1 : c0, nb, cudaMemcpyDefault,
+                                    st),
+                    "ens_slot_load: C^{n-1}");
+  e->hdr.last_stream = st;
+  return rc;
+}
+
+extern "C" int ens_slot_read(chx_ens* e, int group_id, int slot, double* c_now, double* c_prev, void* stream) {
+  EnsGroup* G = get_group(e, group_id);
+  if (!G || !c_now || slot < 0 || slot >= G->capacity) return fail(CHX_EINVAL, "ens_slot_read: bad argument");
+  const size_t nb = (size_t)G->n * G->n * sizeof(double);
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = cuda_check(cudaMemcpyAsync(c_now, (char*)G->d_state[G->cur] + slot * nb, nb, cudaMemcpyDefault, st),
+                      "ens_slot_read");
+  if (!rc && c_prev)
+    rc = cuda_check(cudaMemcpyAsync(c_prev, (char*)G->d_state[1 - G->cur] + slot * nb, nb, cudaMemcpyDefault, st),
+                    "ens_slot_read");
+  e->hdr.last_stream = st;
+  return rc;
+}
+
+extern "C" int ens_slot_move(chx_ens* e, int group_id, int from, int to, void* stream) {
+  EnsGroup* G = get_group(e, group_id);
+  if (!G || from < 0 || to < 0 || from >= G->capacity || to >= G->capacity)
+    return fail(CHX_EINVAL, "ens_slot_move: bad argument");
+  if (from == to) return CHX_OK;
+  const size_t nb = (size_t)G->n * G->n * sizeof(double);
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = CHX_OK;
+  for (int b = 0; b < 2 && !rc; ++b)
+    rc = cuda_check(cudaMemcpyAsync((char*)G->d_state[b] + to * nb, (char*)G->d_state[b] + from * nb, nb,
+                                    cudaMemcpyDeviceToDevice, st),
+                    "ens_slot_move");
+  if (!rc) rc = group_move_params(&G->g, from, to, st);
+  if (!rc) G->slot_gamma[to] = G->slot_gamma[from];
+  e->hdr.last_stream = st;
+  return rc;
+}
+
+extern "C" int ens_group_set_active(chx_ens* e, int group_id, int active) {
+  EnsGroup* G = get_group(e, group_id);
+  if (!G || active < 0 || active > G->capacity) return fail(CHX_EINVAL, "ens_group_set_active: bad argument");
+  if (G->active != active) {
+    G->active = active;
+    e->dirty = true;
+  }
+  return CHX_OK;
+}
+
+extern "C" int ens_step(chx_ens* e, int nsteps, void* stream) {
+  if (!e || e->hdr.magic != kMagicEns || nsteps < 0) return fail(CHX_EINVAL, "ens_step: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = CHX_OK;
+  if (nsteps >= 2 && (e->dirty || !e->exec)) {
+    rc = build_graph(e);
+    if (rc) return rc;
+  }
+  for (int k = 0; k + 2 <= nsteps; k += 2) {
+    rc = cuda_check(cudaGraphLaunch(e->exec, st), "ens_step: graph launch");
+    if (rc) return rc;
+  }
+  if (nsteps & 1) {
+    for (EnsGroup* G : *e->groups)
+      if (G && G->live) step_group(G, st);
+    e->dirty = true;  // the captured pair starts from the other buffer now
+  }
+  e->hdr.last_stream = st;
+  return launch_check("ens_step");
+}
+
+extern "C" int ens_group_step(chx_ens* e, int group_id, int nsteps, void* stream) {
+  EnsGroup* G = get_group(e, group_id);
+  if (!G || nsteps < 0) return fail(CHX_EINVAL, "ens_group_step: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int k = 0; k < nsteps; ++k) step_group(G, st);
+  if (nsteps & 1) e->dirty = true;
+  e->hdr.last_stream = st;
+  return launch_check("ens_group_step");
+}
+
+// Times `trial` steps of the group for each candidate pair of segment counts
+// and keeps the fastest.  The state of the active slots is saved and restored
+// around the trials, so the call changes no simulation.
+extern "C" int ens_autotune(chx_ens* e, int group_id, int trial, int* px_out, int* py_out, void* stream) {
+  EnsGroup* G = get_group(e, group_id);
+  if (!G || trial < 1) return fail(CHX_EINVAL, "ens_autotune: bad argument");
+  if (G->active < 1) return fail(CHX_EINVAL, "ens_autotune: group %d has no active slots", group_id);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = G->n;
+  const size_t sb = (size_t)G->active * n * n * sizeof(double);
+  std::vector<int> cx = segment_candidates(n, G->capacity * n, e->precision);
+  double best = 1e300;
+  int bx = G->g.X.P, by = G->g.Y.P;
+  void* save = nullptr;
+  if (cudaMalloc(&save, 2 * sb) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(CHX_ENOMEM, "ens_autotune: scratch for the saved state");
+  }
+  cudaMemcpyAsync(save, G->d_state[0], sb, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync((char*)save + sb, G->d_state[1], sb, cudaMemcpyDeviceToDevice, st);
+  const int cur0 = G->cur;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  int rc = CHX_OK;
+  for (int P : cx) {
+    ChGroup trialg;
+    rc = group_init(&trialg, n, n, G->l, G->l, G->gamma, e->dt, e->precision, G->capacity, P, P);
+    for (int z = 0; z < G->active && !rc; ++z)
+      if (G->slot_gamma[z] != G->gamma) rc = group_set_gamma(&trialg, z, G->slot_gamma[z]);
+    if (rc) break;
+    if (trialg.work_bytes > G->work_bytes) {  // candidate needs more scratch than the group holds
+      group_free(&trialg);
+      continue;
+    }
+    group_step(&trialg, G->active, G->d_state[G->cur], G->d_state[1 - G->cur], G->d_work, 0, st, nullptr);
+    G->cur = 1 - G->cur;
+    cudaEventRecord(a, st);
+    for (int k = 0; k < trial; ++k) {
+      group_step(&trialg, G->active, G->d_state[G->cur], G->d_state[1 - G->cur], G->d_work, 0, st, nullptr);
+      G->cur = 1 - G->cur;
+    }
+    cudaEventRecord(b, st);
+    rc = cuda_check(cudaEventSynchronize(b), "ens_autotune: trial");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    group_free(&trialg);
+    if (rc) break;
+    if (ms < best) { best = ms; bx = P; by = P; }
+  }
+  cudaMemcpyAsync(G->d_state[0], save, sb, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(G->d_state[1], (char*)save + sb, sb, cudaMemcpyDeviceToDevice, st);
+  G->cur = cur0;
+  cudaStreamSynchronize(st);
+  cudaFree(save);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc) return rc;
+  if (bx != G->g.X.P || by != G->g.Y.P) {
+    ChGroup ng;
+    rc = group_init(&ng, n, n, G->l, G->l, G->gamma, e->dt, e->precision, G->capacity, bx, by);
+    for (int z = 0; z < G->capacity && !rc; ++z)
+      if (G->slot_gamma[z] != G->gamma) rc = group_set_gamma(&ng, z, G->slot_gamma[z]);
+    if (rc) {
+      group_free(&ng);
+      return rc;
+    }
+    group_free(&G->g);
+    G->g = ng;
+    drop_graph(e);
+  }
+  if (px_out) *px_out = G->g.X.P;
+  if (py_out) *py_out = G->g.Y.P;
+  return CHX_OK;
+}
+
+extern "C" int ens_info(chx_ens* e, int group_id, int* n, int* capacity, int* active, int* px, int* py,
+                        size_t* bytes) {
+  EnsGroup* G = get_group(e, group_id);
+  if (!G) return fail(CHX_EINVAL, "ens_info: bad group %d", group_id);
+  if (n) *n = G->n;
+  if (capacity) *capacity = G->capacity;
+  if (active) *active = G->active;
+  if (px) *px = G->g.X.P;
+  if (py) *py = G->g.Y.P;
+  if (bytes) *bytes = G->bytes;
+  return CHX_OK;
+}
+
+extern "C" size_t ens_bytes_used(const chx_ens* e) { return (e && e->hdr.magic == kMagicEns) ? e->used : 0; }

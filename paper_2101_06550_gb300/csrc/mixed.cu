@@ -1,0 +1,452 @@
+// Mixed-precision kernels: FP32 sweeps with one refinement whose residual is
+// formed in double-float arithmetic on the FP32 pipes (ff.cuh), for the ADI
+// step (CHX_PREC_F32_REFINE) and the batched pentadiagonal solver (refine = 1).
+//
+// Compiled with --fmad=false: the error-free transformations need every sum
+// and product rounded as written; every intended fused multiply-add is an
+// explicit fmaf().
+//
+// Why the residual is not formed with FP64 instructions: on GB300 one FP64
+// instruction costs as much issue bandwidth as ~64 FP32 ones, and an FP64
+// residual plus the FP64<->FP32 conversions around it would cost as much as the
+// FP64 sweeps it is meant to replace.  The double-float residual is accurate to
+// ~2^-46 of its terms, which is what one refinement step of an FP32 solve needs.
+#include "chgroup.cuh"
+#include "ff.cuh"
+
+namespace chx {
+namespace {
+
+constexpr int kT = 32, kBY = 8, kSolveThreads = 128;
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+  int r = i % n;
+  return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ ff ffc(float2 c) { return ff{c.x, c.y}; }
+
+// L'(u) = (E + W) + rho (N + S) + kap C on shared-memory ff tiles.
+template <int LD>
+__device__ __forceinline__ ff lap_ff(const ff (*t)[LD], int y, int x, ff rho, ff kap) {
+  ff a = ff_add(t[y][x - 1], t[y][x + 1]);
+  ff b = ff_add(t[y - 1][x], t[y + 1][x]);
+  a = ff_add(a, ff_mul(rho, b));
+  return ff_add(a, ff_mul(kap, t[y][x]));
+}
+
+// Right-hand side of Eq. 3.1 in double-float: r = k2 L'(M) - k1 (C^n - C^{n-1}),
+// M = C^3 - C - gl L'(Cbar).  Same tiling as the FP64 kernel; r written transposed.
+__global__ void __launch_bounds__(kT* kBY) ch_rhs_ff_kernel(const double* __restrict__ cn,
+                                                            const double* __restrict__ cp, float* __restrict__ rhi,
+                                                            float* __restrict__ rlo, int nx, int ny, int G, float2 rho2,
+                                                            float2 kap2, const float2* __restrict__ glff, float2 k12,
+                                                            float2 k22) {
+  __shared__ ff s_cn[kT + 4][kT + 5];
+  __shared__ ff s_cb[kT + 4][kT + 5];
+  __shared__ ff s_m[kT + 2][kT + 3];
+  __shared__ ff s_o[kT][kT + 1];
+  const int z = blockIdx.z;
+  const ff rho = ffc(rho2), kap = ffc(kap2), gl = ffc(glff[z]), k1 = ffc(k12), k2 = ffc(k22);
+  cn += (size_t)z * nx * ny;
+  cp += (size_t)z * nx * ny;
+  const int i0 = blockIdx.x * kT, j0 = blockIdx.y * kT;
+  const int tid = threadIdx.y * kT + threadIdx.x;
+  for (int idx = tid; idx < (kT + 4) * (kT + 4); idx += kT * kBY) {
+    const int ly = idx / (kT + 4), lx = idx % (kT + 4);
+    const int gi = wrapi(i0 - 2 + lx, nx), gj = wrapi(j0 - 2 + ly, ny);
+    const size_t p = (size_t)gj * nx + gi;
+    const ff a = d2ff(cn[p]), b = d2ff(cp[p]);
+    s_cn[ly][lx] = a;
+    s_cb[ly][lx] = ff_sub(ff_scale2(a, 2.f), b);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < (kT + 2) * (kT + 2); idx += kT * kBY) {
+    const int ly = idx / (kT + 2) + 1, lx = idx % (kT + 2) + 1;
+    const ff l = lap_ff<kT + 5>(s_cb, ly, lx, rho, kap);
+    const ff c = s_cn[ly][lx];
+    const ff nl = ff_mul(c, ff_add_f(ff_mul(c, c), -1.f));
+    s_m[ly - 1][lx - 1] = ff_sub(nl, ff_mul(gl, l));
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kT / kBY; ++k) {
+    const int ly = threadIdx.y + k * kBY + 1, lx = threadIdx.x + 1;
+    const ff l = lap_ff<kT + 3>(s_m, ly, lx, rho, kap);
+    const ff diff = ff_sub(s_cb[ly + 1][lx + 1], s_cn[ly + 1][lx + 1]);  // C^n - C^{n-1}
+    s_o[lx - 1][ly - 1] = ff_sub(ff_mul(k2, l), ff_mul(k1, diff));
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kT / kBY; ++k) {
+    const int li = threadIdx.y + k * kBY, lj = threadIdx.x;
+    const int gi = i0 + li, gj = j0 + lj;
+    if (gi < nx && gj < ny) {
+      const ff v = s_o[li][lj];
+      const size_t q = (size_t)gi * G * ny + (size_t)z * ny + gj;
+      rhi[q] = v.hi;
+      rlo[q] = v.lo;
+    }
+  }
+}
+
+__device__ __forceinline__ float corr32(const float* __restrict__ vw, const float* __restrict__ tau, int m, int P,
+                                        int nsys, int s, int r, int j) {
+  const int sn = s + 1 == P ? 0 : s + 1, sp = s == 0 ? P - 1 : s - 1;
+  const size_t S = (size_t)nsys;
+  float c = __ldg(&vw[r]) * tau[(size_t)(4 * sn + 0) * S + j];
+  c = fmaf(__ldg(&vw[m + r]), tau[(size_t)(4 * sn + 1) * S + j], c);
+  c = fmaf(__ldg(&vw[2 * m + r]), tau[(size_t)(4 * sp + 2) * S + j], c);
+  c = fmaf(__ldg(&vw[3 * m + r]), tau[(size_t)(4 * sp + 3) * S + j], c);
+  return c;
+}
+
+// First FP32 solution at global row i (wrapped) of system j.
+__device__ __forceinline__ float x0_at(const float* __restrict__ y1, const float* __restrict__ t1,
+                                       const float* __restrict__ vw, int n, int m, int P, int ld, int nsys, int i,
+                                       int j) {
+  i = wrapi(i, n);
+  const int s = i / m, r = i - s * m;
+  return y1[(size_t)i * ld + j] - corr32(vw, t1, m, P, nsys, s, r, j);
+}
+
+// A x0 for the ADI row (a, -4a, 1 + 6a, -4a, a): x0 + a * delta^4 x0, the fourth
+// difference formed with error-free sums.
+__device__ __forceinline__ ff adi_apply_ff(float w0, float w1, float w2, float w3, float w4, ff a) {
+  const ff s2 = two_sum(w0, w4);
+  const ff s1 = two_sum(w1, w3);
+  ff d = ff_sub(s2, ff_scale2(s1, 4.f));
+  d = ff_add(d, two_prod(6.f, w2));
+  return ff_add_f(ff_mul(a, d), w2);
+}
+
+// Refinement sweep: rho = f - A x0 in double-float, then the segment-local FP32
+// LU sweeps on rho into y2 and its boundary values.  The reduced-system values
+// of the thread's own segment are loaded once; only the two halo rows on each
+// side need the neighbouring segments' values.  Loads run U rows ahead.
+template <int U>
+__global__ void __launch_bounds__(kSolveThreads) spike_refine_ff_kernel(
+    const float* __restrict__ fhi, const float* __restrict__ flo, const float* __restrict__ y1,
+    const float* __restrict__ t1, float* __restrict__ y2, float* __restrict__ yb, int ld, int nsys, int n,
+    DirView<float> D, const float2* __restrict__ aff, size_t fz, size_t ybz) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nsys) return;
+  const int s = blockIdx.y, m = D.m, P = D.P;
+  const int slot = blockIdx.z + j / D.spp;
+  const float2 a2 = aff[slot];
+  const float* lu = D.lu + (size_t)slot * 4 * m;
+  const float* vw = D.vw + (size_t)slot * 4 * m;
+  fhi += blockIdx.z * fz;
+  flo += blockIdx.z * fz;
+  y1 += blockIdx.z * fz;
+  y2 += blockIdx.z * fz;
+  t1 += blockIdx.z * ybz;
+  yb += blockIdx.z * ybz;
+  const int base = s * m;
+  const size_t L = (size_t)ld, S = (size_t)nsys;
+  const ff a = ffc(a2);
+  const float a32 = a2.x;
+  const float *ra = lu, *be = lu + m, *ga = lu + 2 * m, *de = lu + 3 * m;
+  const float *V0 = vw, *V1 = vw + m, *W0 = vw + 2 * m, *W1 = vw + 3 * m;
+  const int sn = s + 1 == P ? 0 : s + 1, sp = s == 0 ? P - 1 : s - 1;
+  const float T0 = t1[(size_t)(4 * sn) * S + j], T1 = t1[(size_t)(4 * sn + 1) * S + j];
+  const float B0 = t1[(size_t)(4 * sp + 2) * S + j], B1 = t1[(size_t)(4 * sp + 3) * S + j];
+  auto corr = [&](int r) {
+    float c = __ldg(&V0[r]) * T0;
+    c = fmaf(__ldg(&V1[r]), T1, c);
+    c = fmaf(__ldg(&W0[r]), B0, c);
+    return fmaf(__ldg(&W1[r]), B1, c);
+  };
+  const float* py = y1 + (size_t)base * L + j;
+  const float* pfh = fhi + (size_t)base * L + j;
+  const float* pfl = flo + (size_t)base * L + j;
+  float* p2 = y2 + (size_t)base * L + j;
+  float w0 = x0_at(y1, t1, vw, n, m, P, ld, nsys, base - 2, j);
+  float w1 = x0_at(y1, t1, vw, n, m, P, ld, nsys, base - 1, j);
+  float w2 = py[0] - corr(0);
+  float w3 = py[L] - corr(1);
+  float w4;
+  // chunk buffers: f rows r0..r0+U-1 and y1 rows r0+2..r0+U+1
+  float qy[U], qh[U], ql[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    qy[u] = (u + 2 < m) ? py[(size_t)(u + 2) * L] : 0.f;
+    qh[u] = (u < m) ? pfh[(size_t)u * L] : 0.f;
+    ql[u] = (u < m) ? pfl[(size_t)u * L] : 0.f;
+  }
+  float g1 = 0.f, g2 = 0.f;
+  for (int r0 = 0; r0 < m; r0 += U) {
+    float ny_[U], nh[U], nl[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 + U + u;
+      ny_[u] = (r + 2 < m) ? py[(size_t)(r + 2) * L] : 0.f;
+      nh[u] = (r < m) ? pfh[(size_t)r * L] : 0.f;
+      nl[u] = (r < m) ? pfl[(size_t)r * L] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 + u;
+      if (r < m) {
+        w4 = (r + 2 < m) ? qy[u] - corr(r + 2) : x0_at(y1, t1, vw, n, m, P, ld, nsys, base + r + 2, j);
+        const ff ax = adi_apply_ff(w0, w1, w2, w3, w4, a);
+        const float res = ff_sub(ff{qh[u], ql[u]}, ax).hi;
+        float g = fmaf(-a32, g2, res);
+        g = fmaf(-__ldg(&be[r]), g1, g) * __ldg(&ra[r]);
+        p2[(size_t)r * L] = g;
+        g2 = g1;
+        g1 = g;
+        w0 = w1; w1 = w2; w2 = w3; w3 = w4;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) { qy[u] = ny_[u]; qh[u] = nh[u]; ql[u] = nl[u]; }
+  }
+  float x1 = 0.f, x2 = 0.f, ylast = 0.f, ylast2 = 0.f;
+  float buf[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int r = m - 1 - u;
+    buf[u] = (r >= 0) ? p2[(size_t)r * L] : 0.f;
+  }
+  for (int r0 = m - 1; r0 >= 0; r0 -= U) {
+    float nxt[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 - U - u;
+      nxt[u] = (r >= 0) ? p2[(size_t)r * L] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 - u;
+      if (r >= 0) {
+        float v = fmaf(-__ldg(&ga[r]), x1, buf[u]);
+        v = fmaf(-__ldg(&de[r]), x2, v);
+        p2[(size_t)r * L] = v;
+        if (r == m - 1) ylast = v;
+        if (r == m - 2) ylast2 = v;
+        x2 = x1;
+        x1 = v;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) buf[u] = nxt[u];
+  }
+  yb[(size_t)(4 * s + 0) * S + j] = x1;
+  yb[(size_t)(4 * s + 1) * S + j] = x2;
+  yb[(size_t)(4 * s + 2) * S + j] = ylast2;
+  yb[(size_t)(4 * s + 3) * S + j] = ylast;
+}
+
+// x sweep result w = x0 + delta as an exact double-float pair, transposed back
+// to row-major (w[j*nx + i]).
+__global__ void __launch_bounds__(kT* kBY) ch_xfinish_ff_kernel(const float* __restrict__ y1,
+                                                                const float* __restrict__ t1,
+                                                                const float* __restrict__ y2,
+                                                                const float* __restrict__ t2, DirView<float> D,
+                                                                float* __restrict__ whi, float* __restrict__ wlo,
+                                                                int nx, int ny, int G) {
+  __shared__ ff s_t[kT][kT + 1];
+  const int z = blockIdx.z, m = D.m, P = D.P;
+  const float* vw = D.vw + (size_t)z * 4 * m;
+  const int i0 = blockIdx.x * kT, j0 = blockIdx.y * kT;
+  const int j = j0 + threadIdx.x;
+  const size_t ld = (size_t)G * ny;
+  const int sys = z * ny + j;
+#pragma unroll
+  for (int k = 0; k < kT / kBY; ++k) {
+    const int li = threadIdx.y + k * kBY, i = i0 + li;
+    if (i < nx && j < ny) {
+      const int s = i / m, r = i - s * m;
+      const float x0 = y1[(size_t)i * ld + sys] - corr32(vw, t1, m, P, G * ny, s, r, sys);
+      const float dl = y2[(size_t)i * ld + sys] - corr32(vw, t2, m, P, G * ny, s, r, sys);
+      s_t[li][threadIdx.x] = two_sum(x0, dl);
+    }
+  }
+  __syncthreads();
+  whi += (size_t)z * nx * ny;
+  wlo += (size_t)z * nx * ny;
+#pragma unroll
+  for (int k = 0; k < kT / kBY; ++k) {
+    const int lj = threadIdx.y + k * kBY, li = threadIdx.x;
+    const int gi = i0 + li, gj = j0 + lj;
+    if (gi < nx && gj < ny) {
+      const ff v = s_t[li][lj];
+      whi[(size_t)gj * nx + gi] = v.hi;
+      wlo[(size_t)gj * nx + gi] = v.lo;
+    }
+  }
+}
+
+// C^{n+1} = 2 C^n - C^{n-1} + v with v = x0 + delta (exact pair, added in FP64).
+__global__ void __launch_bounds__(kSolveThreads) ch_update_ff_kernel(const float* __restrict__ y1,
+                                                                     const float* __restrict__ t1,
+                                                                     const float* __restrict__ y2,
+                                                                     const float* __restrict__ t2, DirView<float> D,
+                                                                     double* cn, double* cp, int nx, int ny,
+                                                                     int keep_roles) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y, z = blockIdx.z, m = D.m, P = D.P;
+  const float* vw = D.vw + (size_t)z * 4 * m;
+  if (i >= nx) return;
+  const int s = j / m, r = j - s * m;
+  const size_t p = (size_t)z * nx * ny + (size_t)j * nx + i;
+  t1 += (size_t)z * 4 * P * nx;
+  t2 += (size_t)z * 4 * P * nx;
+  const float x0 = y1[p] - corr32(vw, t1, m, P, nx, s, r, i);
+  const float dl = y2[p] - corr32(vw, t2, m, P, nx, s, r, i);
+  const ff v = two_sum(x0, dl);
+  const double a = cn[p], b = cp[p];
+  const double nxt = fma(2.0, a, -b) + ff2d(v);
+  if (keep_roles) {
+    cp[p] = a;
+    cn[p] = nxt;
+  } else {
+    cp[p] = nxt;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Batched pentadiagonal refinement (SHARED / UNIFORM coefficients): residual
+// r = f - A x0 in double-float (rows of A as double-float constants, f split
+// from FP64 by bits), FP32 sweeps for delta, x = x0 + delta added in FP64.
+// The forward intermediate is kept as a float in the low half of f's slot.
+__global__ void __launch_bounds__(kSolveThreads) penta_refine_ff_kernel(double* x, const float* __restrict__ x0,
+                                                                        int n, int batch,
+                                                                        const float* __restrict__ fac,
+                                                                        const float2* __restrict__ coef, float s00,
+                                                                        float s01, float s10, float s11) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= batch) return;
+  const int m = n - 2;
+  const size_t B = (size_t)batch;
+#define FAC(k, r) __ldg(&fac[(size_t)(k) * m + (r)])
+  double* px = x + s;
+  const float* p0 = x0 + s;
+  float w0 = p0[(size_t)(n - 2) * B], w1 = p0[(size_t)(n - 1) * B];
+  float w2 = p0[0], w3 = p0[B], w4 = p0[2 * B];
+  float g1 = 0.f, g2 = 0.f, t0 = 0.f, t1 = 0.f, rt0 = 0.f, rt1 = 0.f;
+  for (int r = 0; r < n; ++r) {
+    const float2 ca = __ldg(&coef[r]), cb = __ldg(&coef[n + r]), cc = __ldg(&coef[2 * n + r]);
+    const float2 cd = __ldg(&coef[3 * n + r]), ce = __ldg(&coef[4 * n + r]);
+    ff ax = ff_mul_f(ffc(cc), w2);
+    ax = ff_add(ax, ff_mul_f(ffc(cb), w1));
+    ax = ff_add(ax, ff_mul_f(ffc(cd), w3));
+    ax = ff_add(ax, ff_mul_f(ffc(ca), w0));
+    ax = ff_add(ax, ff_mul_f(ffc(ce), w4));
+    const float res = ff_sub(d2ff(px[(size_t)r * B]), ax).hi;
+    if (r < m) {
+      float g = fmaf(-FAC(2, r), g2, res);
+      g = fmaf(-FAC(1, r), g1, g) * FAC(0, r);
+      t0 = fmaf(FAC(5, r), res, t0);
+      t1 = fmaf(FAC(6, r), res, t1);
+      reinterpret_cast<float*>(px + (size_t)r * B)[0] = g;
+      g2 = g1;
+      g1 = g;
+    } else if (r == m) {
+      rt0 = res;
+    } else {
+      rt1 = res;
+    }
+    w0 = w1; w1 = w2; w2 = w3; w3 = w4;
+    const int nx = (r + 3 < n) ? r + 3 : r + 3 - n;
+    w4 = p0[(size_t)nx * B];
+  }
+  const float a0 = rt0 - t0, a1 = rt1 - t1;
+  const float xt0 = fmaf(s00, a0, s01 * a1), xt1 = fmaf(s10, a0, s11 * a1);
+  px[(size_t)m * B] = f2d_exact(p0[(size_t)m * B]) + f2d_exact(xt0);
+  px[(size_t)(m + 1) * B] = f2d_exact(p0[(size_t)(m + 1) * B]) + f2d_exact(xt1);
+  float d1 = 0.f, d2 = 0.f;
+  for (int r = m - 1; r >= 0; --r) {
+    const float g = reinterpret_cast<const float*>(px + (size_t)r * B)[0];
+    float v = fmaf(-FAC(7, r), xt0, g);
+    v = fmaf(-FAC(8, r), xt1, v);
+    v = fmaf(-FAC(3, r), d1, v);
+    v = fmaf(-FAC(4, r), d2, v);
+    px[(size_t)r * B] = f2d_exact(p0[(size_t)r * B]) + f2d_exact(v);
+    d2 = d1;
+    d1 = v;
+  }
+#undef FAC
+}
+
+// First FP32 solve of the refinement path: reads the FP64 right-hand side by
+// its high part (bits, no FP64 instruction), writes x0 (float) into work.
+__global__ void __launch_bounds__(kSolveThreads) penta_solve_f32_from_f64_kernel(const double* __restrict__ in,
+                                                                                 float* __restrict__ work, int n,
+                                                                                 int batch,
+                                                                                 const float* __restrict__ fac,
+                                                                                 float s00, float s01, float s10,
+                                                                                 float s11) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= batch) return;
+  const int m = n - 2;
+  const size_t B = (size_t)batch;
+#define FAC(k, r) __ldg(&fac[(size_t)(k) * m + (r)])
+  const double* pin = in + s;
+  float* pw = work + s;
+  float g1 = 0.f, g2 = 0.f, t0 = 0.f, t1 = 0.f;
+  for (int r = 0; r < m; ++r) {
+    const float f = d2ff(pin[(size_t)r * B]).hi;
+    float g = fmaf(-FAC(2, r), g2, f);
+    g = fmaf(-FAC(1, r), g1, g) * FAC(0, r);
+    t0 = fmaf(FAC(5, r), f, t0);
+    t1 = fmaf(FAC(6, r), f, t1);
+    pw[(size_t)r * B] = g;
+    g2 = g1;
+    g1 = g;
+  }
+  const float r0 = d2ff(pin[(size_t)m * B]).hi - t0, r1 = d2ff(pin[(size_t)(m + 1) * B]).hi - t1;
+  const float xt0 = fmaf(s00, r0, s01 * r1), xt1 = fmaf(s10, r0, s11 * r1);
+  pw[(size_t)m * B] = xt0;
+  pw[(size_t)(m + 1) * B] = xt1;
+  float x1 = 0.f, x2 = 0.f;
+  for (int r = m - 1; r >= 0; --r) {
+    float v = fmaf(-FAC(7, r), xt0, pw[(size_t)r * B]);
+    v = fmaf(-FAC(8, r), xt1, v);
+    v = fmaf(-FAC(3, r), x1, v);
+    v = fmaf(-FAC(4, r), x2, v);
+    pw[(size_t)r * B] = v;
+    x2 = x1;
+    x1 = v;
+  }
+#undef FAC
+}
+
+}  // namespace
+
+void launch_ch_rhs_ff(const double* cn, const double* cp, float* rhi, float* rlo, int nx, int ny, int G,
+                      const FFConst& k, const float2* glff, cudaStream_t st) {
+  const dim3 grid(ceil_div(nx, kT), ceil_div(ny, kT), G), block(kT, kBY);
+  ch_rhs_ff_kernel<<<grid, block, 0, st>>>(cn, cp, rhi, rlo, nx, ny, G, k.rho, k.kap, glff, k.k1, k.k2);
+}
+
+void launch_spike_refine_ff(const float* fhi, const float* flo, const float* y1, const float* t1, float* y2, float* yb,
+                            int ld, int nsys, int n, const DirView<float>& D, const float2* aff, int Z, size_t fz,
+                            size_t ybz, cudaStream_t st) {
+  spike_refine_ff_kernel<16><<<dim3(ceil_div(nsys, kSolveThreads), D.P, Z), kSolveThreads, 0, st>>>(
+      fhi, flo, y1, t1, y2, yb, ld, nsys, n, D, aff, fz, ybz);
+}
+
+void launch_ch_xfinish_ff(const float* y1, const float* t1, const float* y2, const float* t2, const DirView<float>& D,
+                          float* whi, float* wlo, int nx, int ny, int G, cudaStream_t st) {
+  const dim3 grid(ceil_div(nx, kT), ceil_div(ny, kT), G), block(kT, kBY);
+  ch_xfinish_ff_kernel<<<grid, block, 0, st>>>(y1, t1, y2, t2, D, whi, wlo, nx, ny, G);
+}
+
+void launch_ch_update_ff(const float* y1, const float* t1, const float* y2, const float* t2, const DirView<float>& D,
+                         double* cn, double* cp, int nx, int ny, int G, int keep_roles, cudaStream_t st) {
+  ch_update_ff_kernel<<<dim3(ceil_div(nx, kSolveThreads), ny, G), kSolveThreads, 0, st>>>(y1, t1, y2, t2, D, cn, cp,
+                                                                                         nx, ny, keep_roles);
+}
+
+void launch_penta_refine_ff(double* x, float* work, int n, int batch, const float* fac32, const float2* coef_ff,
+                            const float* s32, cudaStream_t st) {
+  const unsigned grid = ceil_div(batch, kSolveThreads);
+  penta_solve_f32_from_f64_kernel<<<grid, kSolveThreads, 0, st>>>(x, work, n, batch, fac32, s32[0], s32[1], s32[2],
+                                                                   s32[3]);
+  penta_refine_ff_kernel<<<grid, kSolveThreads, 0, st>>>(x, work, n, batch, fac32, coef_ff, s32[0], s32[1], s32[2],
+                                                         s32[3]);
+}
+
+}  // namespace chx

@@ -1,0 +1,38 @@
+// Launchers of the mixed-precision kernels (mixed.cu, compiled with --fmad=false).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "chx_internal.cuh"
+
+namespace chx {
+
+// Double-float constants of the right-hand side stencil: (hi, lo) pairs.
+struct FFConst {
+  float2 rho, kap, gl, k1, k2;
+};
+
+// Splits a double into a (hi, lo) float pair on the host.
+inline float2 split_ff(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+
+template <typename T>
+struct DirView;
+
+// All launchers take G / Z simulations of the group (blockIdx.z); see chgroup.cuh for layouts.
+// glff[z] = gamma_z / dx^2 and aff[z] = a_z as double-float pairs, per slot.
+void launch_ch_rhs_ff(const double* cn, const double* cp, float* rhi, float* rlo, int nx, int ny, int G,
+                      const FFConst& k, const float2* glff, cudaStream_t st);
+void launch_spike_refine_ff(const float* fhi, const float* flo, const float* y1, const float* t1, float* y2, float* yb,
+                            int ld, int nsys, int n, const DirView<float>& D, const float2* aff, int Z, size_t fz,
+                            size_t ybz, cudaStream_t st);
+void launch_ch_xfinish_ff(const float* y1, const float* t1, const float* y2, const float* t2, const DirView<float>& D,
+                          float* whi, float* wlo, int nx, int ny, int G, cudaStream_t st);
+void launch_ch_update_ff(const float* y1, const float* t1, const float* y2, const float* t2, const DirView<float>& D,
+                         double* cn, double* cp, int nx, int ny, int G, int keep_roles, cudaStream_t st);
+void launch_penta_refine_ff(double* x, float* work, int n, int batch, const float* fac32, const float2* coef_ff,
+                            const float* s32, cudaStream_t st);
+
+}  // namespace chx

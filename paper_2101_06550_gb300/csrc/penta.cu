@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "chx_internal.cuh"
+#include "mixed.cuh"
 
 using namespace chx;
 
@@ -26,9 +27,9 @@ struct chx_penta_plan {
   int n, m, batch, mode, dtype;
   void* d_fac;        // SHARED/UNIFORM: 9*m values; PER_SYSTEM: (9*m + 4) * batch values (dtype)
   double sinv[4];     // SHARED/UNIFORM tail inverse
-  // FP32-sweep + FP64-residual refinement (SHARED/UNIFORM FP64 plans)
+  // FP32 sweeps + double-float residual refinement (SHARED/UNIFORM FP64 plans)
   float* d_fac32;     // 9*m floats
-  double* d_coef;     // 5*n doubles: the rows of A for the residual
+  float2* d_coef;     // 5*n double-float pairs: the rows of A for the residual
   float* d_work32;    // n*batch floats
   float sinv32[4];
 };
@@ -130,69 +131,6 @@ __global__ void __launch_bounds__(kThreads) penta_solve_kernel(const TIn* in, TW
     for (int u = 0; u < kUnroll; ++u) buf[u] = nxt[u];
   }
 #undef FAC
-}
-
-// ---------------------------------------------------------------------------
-// Refinement pass: r = f - A x0 in FP64 (x0 = first FP32 solution in work32),
-// delta = A^{-1} r with FP32 sweeps, x = x0 + delta written over f in FP64.
-// The forward intermediate is kept as a float in the low half of f's slot.
-__global__ void __launch_bounds__(kThreads) penta_refine_kernel(double* x, const float* __restrict__ x0, int n,
-                                                                int batch, const float* __restrict__ fac,
-                                                                const double* __restrict__ coef, float s00,
-                                                                float s01, float s10, float s11) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= batch) return;
-  const int m = n - 2;
-  const size_t B = (size_t)batch;
-#define FAC(k, r) __ldg(&fac[(size_t)(k) * m + (r)])
-#define COEF(k, r) __ldg(&coef[(size_t)(k) * n + (r)])
-  double* px = x + s;
-  const float* p0 = x0 + s;
-  // window w[o + 2] = x0[(r + o) mod n]
-  double w0 = (double)p0[(size_t)(n - 2) * B], w1 = (double)p0[(size_t)(n - 1) * B];
-  double w2 = (double)p0[0], w3 = (double)p0[B], w4 = (double)p0[2 * B];
-  float g1 = 0.f, g2 = 0.f, t0 = 0.f, t1 = 0.f;
-  float rt0 = 0.f, rt1 = 0.f;
-  for (int r = 0; r < n; ++r) {
-    double ax = COEF(2, r) * w2;
-    ax = fma(COEF(1, r), w1, ax);
-    ax = fma(COEF(3, r), w3, ax);
-    ax = fma(COEF(0, r), w0, ax);
-    ax = fma(COEF(4, r), w4, ax);
-    const float res = (float)(px[(size_t)r * B] - ax);
-    if (r < m) {
-      const float g = (res - FAC(2, r) * g2 - FAC(1, r) * g1) * FAC(0, r);
-      t0 = fmaf(FAC(5, r), res, t0);
-      t1 = fmaf(FAC(6, r), res, t1);
-      reinterpret_cast<float*>(px + (size_t)r * B)[0] = g;
-      g2 = g1;
-      g1 = g;
-    } else if (r == m) {
-      rt0 = res;
-    } else {
-      rt1 = res;
-    }
-    w0 = w1; w1 = w2; w2 = w3; w3 = w4;
-    const int nx = (r + 3 < n) ? r + 3 : r + 3 - n;
-    w4 = (double)p0[(size_t)nx * B];
-  }
-  const float a0 = rt0 - t0, a1 = rt1 - t1;
-  const float xt0 = s00 * a0 + s01 * a1, xt1 = s10 * a0 + s11 * a1;
-  px[(size_t)m * B] = (double)p0[(size_t)m * B] + (double)xt0;
-  px[(size_t)(m + 1) * B] = (double)p0[(size_t)(m + 1) * B] + (double)xt1;
-  float d1 = 0.f, d2 = 0.f;
-  for (int r = m - 1; r >= 0; --r) {
-    const float g = reinterpret_cast<const float*>(px + (size_t)r * B)[0];
-    float v = fmaf(-FAC(7, r), xt0, g);
-    v = fmaf(-FAC(8, r), xt1, v);
-    v = fmaf(-FAC(3, r), d1, v);
-    v = fmaf(-FAC(4, r), d2, v);
-    px[(size_t)r * B] = (double)p0[(size_t)r * B] + (double)v;
-    d2 = d1;
-    d1 = v;
-  }
-#undef FAC
-#undef COEF
 }
 
 // ---------------------------------------------------------------------------
@@ -377,12 +315,14 @@ extern "C" int penta_cyclic_factor(chx_penta_plan** plan, int n, int coef_mode, 
     rc = upload_factors<float>(pf, &f32);
     p->d_fac32 = (float*)f32;
     if (!rc) {
-      if (cudaMalloc(&p->d_coef, co.size() * sizeof(double)) != cudaSuccess ||
+      std::vector<float2> cff(co.size());
+      for (size_t k = 0; k < co.size(); ++k) cff[k] = split_ff(co[k]);
+      if (cudaMalloc(&p->d_coef, cff.size() * sizeof(float2)) != cudaSuccess ||
           cudaMalloc(&p->d_work32, (size_t)n * batch * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         rc = fail(CHX_ENOMEM, "penta_cyclic_factor: refinement storage");
       } else {
-        rc = cuda_check(cudaMemcpy(p->d_coef, co.data(), co.size() * sizeof(double), cudaMemcpyHostToDevice),
+        rc = cuda_check(cudaMemcpy(p->d_coef, cff.data(), cff.size() * sizeof(float2), cudaMemcpyHostToDevice),
                         "penta: coefficient upload");
       }
     }
@@ -417,10 +357,7 @@ extern "C" int penta_cyclic_solve_batched(chx_penta_plan* p, void* rhs, int batc
   const double* S = p->sinv;
   const float* S32 = p->sinv32;
   if (refine) {
-    penta_solve_kernel<double, float, float, false><<<grid, kThreads, 0, st>>>(
-        (const double*)rhs, p->d_work32, p->n, batch, p->d_fac32, S32[0], S32[1], S32[2], S32[3]);
-    penta_refine_kernel<<<grid, kThreads, 0, st>>>((double*)rhs, p->d_work32, p->n, batch, p->d_fac32, p->d_coef,
-                                                   S32[0], S32[1], S32[2], S32[3]);
+    launch_penta_refine_ff((double*)rhs, p->d_work32, p->n, batch, p->d_fac32, p->d_coef, S32, st);
   } else if (p->dtype == CHX_F64) {
     double* x = (double*)rhs;
     if (p->mode == CHX_COEF_PER_SYSTEM)

@@ -1,0 +1,149 @@
+"""GPU tests of the ensemble runtime and the continuous-batching server."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+DX = 2 * np.pi / 64  # fixed spacing: L = n * DX
+
+
+def _chx():
+    import paper_2101_06550_gb300 as chx
+
+    return chx
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _ic(seed, n):
+    return synth.field(seed, n, n, -0.1, 0.1)
+
+
+def _alone(n, gamma, dt, seed, steps, precision=0):
+    chx = _chx()
+    plan = chx.ChPlan(n, n, n * DX, n * DX, gamma, dt, precision)
+    c = torch.from_numpy(_ic(seed, n)).to(DEV)
+    p = c.clone()
+    plan.step(c, p, plan.alloc_work(DEV), steps)
+    return c.cpu().numpy()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("steps", [1, 6, 7])
+def test_ensemble_matches_single_plans(precision, steps):
+    chx = _chx()
+    dt = 1e-3
+    ens = chx.Ensemble(dt, precision)
+    sims = [(64, 0.01, 1), (64, 0.02, 2), (96, 0.005, 3), (64, 0.01, 4), (128, 0.015, 5)]
+    gids, slots = {}, []
+    for n, g, s in sims:
+        if n not in gids:
+            gids[n] = ens.group_create(n, n * DX, 0.01, 4)
+        gid = gids[n]
+        slot = sum(1 for x in slots if x[0] == gid)
+        ens.load(gid, slot, torch.from_numpy(_ic(s, n)).to(DEV), None, g)
+        slots.append((gid, slot, n, g, s))
+    for n, gid in gids.items():
+        ens.set_active(gid, sum(1 for x in slots if x[0] == gid))
+    ens.step(steps)
+    tol = 1e-11 if precision == 0 else 1e-6
+    for gid, slot, n, g, s in slots:
+        out = torch.empty(n * n, dtype=torch.float64, device=DEV)
+        ens.read(gid, slot, out)
+        ref = _alone(n, g, dt, s, steps, precision)
+        assert _rel(out.cpu().numpy().reshape(n, n), ref) <= tol, (n, g, s)
+    ens.sync_status()
+
+
+def test_ensemble_result_independent_of_the_mix_bit_exact():
+    chx = _chx()
+    n, dt, steps = 64, 1e-3, 9
+    target = torch.from_numpy(_ic(11, n)).to(DEV)
+    ens1 = chx.Ensemble(dt)
+    g1 = ens1.group_create(n, n * DX, 0.01, 8)
+    ens1.load(g1, 0, target, None, 0.013)
+    ens1.set_active(g1, 1)
+    ens1.step(steps)
+    a = torch.empty(n * n, dtype=torch.float64, device=DEV)
+    ens1.read(g1, 0, a)
+    ens2 = chx.Ensemble(dt)
+    g2 = ens2.group_create(n, n * DX, 0.01, 8)
+    for s in range(6):
+        if s == 3:
+            ens2.load(g2, s, target, None, 0.013)
+        else:
+            ens2.load(g2, s, torch.from_numpy(_ic(50 + s, n)).to(DEV), None, 0.005 + 0.003 * s)
+    ens2.set_active(g2, 6)
+    ens2.step(steps)
+    b = torch.empty(n * n, dtype=torch.float64, device=DEV)
+    ens2.read(g2, 3, b)
+    assert torch.equal(a, b)
+
+
+def test_ensemble_matches_oracle_and_slot_move():
+    chx = _chx()
+    n, dt, g = 48, 1e-3, 0.01
+    ens = chx.Ensemble(dt)
+    gid = ens.group_create(n, n * DX, g, 3)
+    c0, c1 = _ic(7, n), _ic(8, n)
+    ens.load(gid, 0, torch.from_numpy(c0).to(DEV))
+    ens.load(gid, 1, torch.from_numpy(c1).to(DEV))
+    ens.set_active(gid, 2)
+    ens.step(4)
+    ens.move(gid, 1, 0)  # slot 1's simulation continues from slot 0
+    ens.set_active(gid, 1)
+    ens.step(3)
+    out = torch.empty(n * n, dtype=torch.float64, device=DEV)
+    ens.read(gid, 0, out)
+    ref, _ = oracle.ch_run(c1, c1, n * DX, n * DX, g, dt, 7)
+    assert _rel(out.cpu().numpy().reshape(n, n), ref) <= 1e-11
+
+
+def test_ensemble_autotune_keeps_state_and_budget_admission():
+    chx = _chx()
+    n, dt = 128, 1e-3
+    ens = chx.Ensemble(dt, hbm_budget=64 << 20)
+    gid = ens.group_create(n, n * DX, 0.01, 4)
+    for s in range(4):
+        ens.load(gid, s, torch.from_numpy(_ic(20 + s, n)).to(DEV))
+    ens.set_active(gid, 4)
+    px, py = ens.autotune(gid, 2)
+    assert n % px == 0 and n % py == 0
+    ens.step(5)
+    out = torch.empty(n * n, dtype=torch.float64, device=DEV)
+    ens.read(gid, 2, out)
+    ref = _alone(n, 0.01, dt, 22, 5)
+    assert _rel(out.cpu().numpy().reshape(n, n), ref) <= 1e-11
+    with pytest.raises(chx.ChxError) as e:
+        ens.group_create(1024, 1024 * DX, 0.01, 16)  # far over the 64 MiB budget
+    assert e.value.status == -4
+    assert ens.bytes_used <= 64 << 20
+
+
+def test_server_continuous_batching_results_match_alone():
+    from paper_2101_06550_gb300 import serving
+
+    dt = 1e-3
+    reqs = serving.poisson_requests(12, rate=400.0, seed=3, n_min=32, n_max=128, steps_lo=10, steps_hi=60)
+    srv = serving.Server(dt, DX, capacity=4, chunk=16, make_ic=lambda r: torch.from_numpy(_ic(r.seed, r.n)).to(DEV))
+    stats = serving.serve(reqs, srv, time_limit=120)
+    assert stats["completed"] == len(reqs)
+    assert stats["p50_s"] <= stats["p99_s"]
+    # requests overlapped on the device: more requests than ticks would allow one at a time
+    assert srv.ticks < sum(-(-r.steps // 16) for r in reqs)
+    for r in reqs:
+        got = r.result.numpy().reshape(r.n, r.n)
+        assert _rel(got, _alone(r.n, r.gamma, dt, r.seed, r.steps)) <= 1e-11, r
+    # the same request alone in a fresh server gives the same bits as in the mix
+    r0 = reqs[5]
+    solo = serving.Request(rid=0, n=r0.n, steps=r0.steps, gamma=r0.gamma, seed=r0.seed, arrival=0.0)
+    srv2 = serving.Server(dt, DX, capacity=4, chunk=16, make_ic=lambda r: torch.from_numpy(_ic(r.seed, r.n)).to(DEV))
+    serving.serve([solo], srv2)
+    assert torch.equal(solo.result, r0.result)
