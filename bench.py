@@ -179,8 +179,8 @@ def run_chx(args, rank, world, local_rank):
         plan.sync_status()
         return ms, prof, plan, cn, cp, work
 
-    with ClockSampler(local_rank) as clk:
-        ms64, prof64, plan64, cn64, cp64, work64 = measure(chx.PREC_F64)
+    clk = ClockSampler(local_rank).__enter__()
+    ms64, prof64, plan64, cn64, cp64, work64 = measure(chx.PREC_F64)
     ms32, prof32, plan32, _, _, _ = measure(chx.PREC_F32_REFINE)
     launches_per_step = sum(n for _, n in prof64.values()) / max(1, args.steps)
 
@@ -207,6 +207,7 @@ def run_chx(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms64, ms32, e2e_ms = t.tolist()
     if rank != 0:
+        clk.__exit__(None, None, None)
         if dist:
             dist.destroy_process_group()
         return
@@ -227,6 +228,15 @@ def run_chx(args, rank, world, local_rank):
     else:
         roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": fp64_peak_gops, "unit": "G fp64-op/s",
                 "frac": None, "traffic": None, "ms_per_launch": per_launch_ms}
+    extras = {}
+    if not args.no_extras:
+        extras["solvers"] = bench_solvers(dev)
+        torch.cuda.empty_cache()
+        extras["ensemble"] = bench_ensemble(dev, chx.PREC_F32_REFINE, args.ens_steps, 3)
+        torch.cuda.empty_cache()
+        extras["serving"] = bench_serving(dev, args.serve_requests, args.serve_rate, chx.PREC_F32_REFINE)
+        torch.cuda.empty_cache()
+    clk.__exit__(None, None, None)
     cb_v, cb_t = cpu_baseline_oracle(max(1, args.cpu_steps))
     line = {
         "metric": "grid-pt-steps/s", "value": value, "unit": "grid-pt-steps/s", "n_gpus": world,
@@ -247,18 +257,170 @@ def run_chx(args, rank, world, local_rank):
         "clocks": clk.summary(),
         "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
     }
+    line.update(extras)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
+def bench_solvers(dev, reps=5):
+    """Standalone batched solvers, N = 1024, batch 65536, interleaved (one solve = one call)."""
+    import torch
+
+    import paper_2101_06550_gb300 as chx
+
+    n, batch = 1024, 65536
+    sig = 0.01 * 1e-3 / (2 * np.pi / n) ** 4  # a = gamma dt / dx^4
+    co = [sig, -4 * sig, 1 + 6 * sig, -4 * sig, sig]
+    f = synth.uniform_torch(1, n * batch, -1, 1, device=dev)
+    x = torch.empty_like(f)
+    out = {}
+
+    def timeit(fn, k=reps):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = 0.0
+        for _ in range(k):
+            x.copy_(f)  # 512 MiB copy also flushes L2
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(b)
+        return ms / k
+
+    unknowns = n * batch
+    p = chx.PentaPlan(n, co, batch, mode=chx.COEF_UNIFORM)
+    ms = timeit(lambda: p.solve(x))
+    out["penta_uniform_f64"] = {"ms": ms, "unknowns_per_s": unknowns / (ms * 1e-3),
+                                "hbm_gbs_algorithmic": 16 * unknowns / (ms * 1e-3) / 1e9,
+                                "fp64_gops": 9 * unknowns / (ms * 1e-3) / 1e9}
+    ms = timeit(lambda: p.solve(x, refine=True))
+    out["penta_uniform_f32_refine"] = {"ms": ms, "unknowns_per_s": unknowns / (ms * 1e-3)}
+    p.close()
+    # variable diagonally dominant coefficients, factor + solve each call ("Rewrite")
+    # the same streams as synth.diag_dominant_penta(2, n, batch), drawn on the device
+    a_, b_, d_, e_ = [synth.uniform_torch(2, unknowns, -1, 1, device=dev, offset=k * unknowns) for k in range(4)]
+    u = synth.uniform_torch(2, unknowns, 0, 1, device=dev, offset=4 * unknowns)
+    c_ = (1.5 + 0.5 * u) * (a_.abs() + b_.abs() + d_.abs() + e_.abs())
+    del u
+    pp = chx.PentaPlan(n, [a_, b_, c_, d_, e_], batch, mode=chx.COEF_PER_SYSTEM)
+    ms_f = timeit(lambda: pp.refactor([a_, b_, c_, d_, e_]))
+    ms_s = timeit(lambda: pp.solve(x))
+    out["penta_per_system_f64"] = {"ms_factor": ms_f, "ms_solve": ms_s,
+                                   "unknowns_per_s_rewrite": unknowns / ((ms_f + ms_s) * 1e-3)}
+    pp.close()
+    del a_, b_, c_, d_, e_
+    sig_t = 1e-3 / (2 * (2 * np.pi / n) ** 2)
+    tp = chx.TriPlan(n, [-sig_t, 1 + 2 * sig_t, -sig_t], batch, mode=chx.COEF_UNIFORM)
+    ms = timeit(lambda: tp.solve(x))
+    out["tri_uniform_f64"] = {"ms": ms, "unknowns_per_s": unknowns / (ms * 1e-3),
+                              "hbm_gbs_algorithmic": 16 * unknowns / (ms * 1e-3) / 1e9}
+    tp.close()
+    return out
+
+
+def ensemble_sims(count=512, seed=11):
+    """Uneven ensemble: n uniform in {128, 256, 512, 1024}, gamma in {0.005, 0.01, 0.02}."""
+    u = synth.uniform(seed, 2 * count, 0.0, 1.0).reshape(2, count)
+    sizes = np.array([128, 256, 512, 1024])[np.minimum((u[0] * 4).astype(int), 3)]
+    gammas = np.array([0.005, 0.01, 0.02])[np.minimum((u[1] * 3).astype(int), 2)]
+    return [(int(sizes[k]), float(gammas[k]), 1000 + k) for k in range(count)]
+
+
+def bench_ensemble(dev, precision, steps, warmup, count=512):
+    """One ensemble step advances all simulations; grid-pt-steps/s over `steps` steps."""
+    import torch
+
+    import paper_2101_06550_gb300 as chx
+
+    dx, dt = 2 * np.pi / 256, 1e-3
+    sims = ensemble_sims(count)
+    ens = chx.Ensemble(dt, precision)
+    by_n = {}
+    for n, g, sd in sims:
+        by_n.setdefault(n, []).append((g, sd))
+    gids = {}
+    for n, lst in sorted(by_n.items()):
+        gid = ens.group_create(n, n * dx, lst[0][0], len(lst))
+        gids[n] = gid
+        for slot, (g, sd) in enumerate(lst):
+            c0 = synth.uniform_torch(sd, n * n, -0.1, 0.1, device=dev)
+            ens.load(gid, slot, c0, None, g)
+        ens.set_active(gid, len(lst))
+    tuned = {n: ens.autotune(gid, 2) for n, gid in gids.items()}
+    ens.step(max(2, warmup))
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    ens.step(steps)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    ens.sync_status()
+    pts = sum(n * n for n, _, _ in sims)
+    res = {"sims": count, "grid_pts": pts, "steps": steps, "ms_per_ensemble_step": ms / steps,
+           "value": pts * steps / (ms * 1e-3), "unit": "grid-pt-steps/s", "segments": tuned,
+           "hbm_bytes": ens.bytes_used}
+    ens.close()
+    return res
+
+
+def bench_serving(dev, count, rate, precision):
+    import torch
+
+    import paper_2101_06550_gb300 as chx
+    from paper_2101_06550_gb300 import serving
+
+    dx, dt = 2 * np.pi / 256, 1e-3
+    reqs = serving.poisson_requests(count, rate, seed=7)
+    srv = serving.Server(dt, dx, precision=precision, hbm_budget=96 << 30, capacity=16, chunk=100,
+                         keep_results=False)
+    stats = serving.serve(reqs, srv, time_limit=900)
+    offered = sum(r.n * r.n * r.steps for r in reqs) / max(reqs[-1].arrival, 1e-9)
+    stats["offered_grid_pt_steps_per_s"] = offered
+    stats["precision"] = "f32+f64-residual" if precision == chx.PREC_F32_REFINE else "f64"
+    # serial per-request FP64 baseline on the same GPU: measured FP64 step time per
+    # grid size, a FIFO single-server queue over the same arrivals
+    t_step = {}
+    for n in sorted({r.n for r in reqs}):
+        plan = chx.ChPlan(n, n, n * dx, n * dx, 0.01, dt)
+        c = synth.uniform_torch(1, n * n, -0.1, 0.1, device=dev)
+        pc = c.clone()
+        w = plan.alloc_work(dev)
+        plan.step(c, pc, w, 3)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        plan.step(c, pc, w, 20)
+        b.record()
+        torch.cuda.synchronize()
+        t_step[n] = a.elapsed_time(b) / 20e3
+        plan.close()
+    t, lat = 0.0, []
+    for r in sorted(reqs, key=lambda r: r.arrival):
+        t = max(t, r.arrival) + r.steps * t_step[r.n]
+        lat.append(t - r.arrival)
+    lat = np.array(lat)
+    stats["serial_fp64_baseline"] = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                                     "makespan_s": t,
+                                     "grid_pt_steps_per_s": sum(r.n * r.n * r.steps for r in reqs) / t,
+                                     "kind": "FIFO queue over measured per-size FP64 ch_step times"}
+    return stats
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="chx", choices=["chx", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=12)
+    ap.add_argument("--no-extras", action="store_true", help="skip the solver / ensemble / serving sub-benchmarks")
+    ap.add_argument("--ens-steps", type=int, default=20)
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
