@@ -57,6 +57,15 @@ __device__ __forceinline__ int wrapi(int i, int n) {
   return r < 0 ? r + n : r;
 }
 
+// Wrap for indices within a few periods of [0, n): two compares instead of a
+// division on the common path.
+__device__ __forceinline__ int wrap_near(int i, int n) {
+  if (i >= 0 && i < n) return i;
+  if (i < 0 && i >= -n) return i + n;
+  if (i >= n && i < 2 * n) return i - n;
+  return wrapi(i, n);
+}
+
 // ---------------------------------------------------------------------------
 // RHS stencil pass.  Tile of 32 (i) x 32 (j) outputs of simulation blockIdx.z,
 // Cn/Cbar staged with a 2-point halo, M with a 1-point halo.  Output element
@@ -77,7 +86,7 @@ __global__ void __launch_bounds__(kT* kBY) ch_rhs_kernel(const double* __restric
   const int tid = threadIdx.y * kT + threadIdx.x;
   for (int idx = tid; idx < (kT + 4) * (kT + 4); idx += kT * kBY) {
     const int ly = idx / (kT + 4), lx = idx % (kT + 4);
-    const int gi = wrapi(i0 - 2 + lx, nx), gj = wrapi(j0 - 2 + ly, ny);
+    const int gi = wrap_near(i0 - 2 + lx, nx), gj = wrap_near(j0 - 2 + ly, ny);
     const size_t p = (size_t)gj * nx + gi;
     const TC a = (TC)cn[p], b = (TC)cp[p];
     s_cn[ly][lx] = a;
@@ -198,47 +207,56 @@ __global__ void __launch_bounds__(kSolveThreads) spike_local_kernel(const TIn* f
 }
 
 // Reduced system: tau = Rinv * yb for every system (4P unknowns each), one
-// output per thread; the 4P loads of the system's boundary values are issued
-// 8 at a time so their latencies overlap.
+// output per thread.  Rinv's 4x4 blocks decay with the circular distance
+// between segments; only distances <= D.band are kept (the dropped blocks are
+// below 1e-17 of the largest, set at plan time), so output q reads the boundary
+// values of segments s_q - band .. s_q + band, 8 loads at a time.
 template <typename TC>
 __global__ void __launch_bounds__(kSolveThreads) spike_reduced_kernel(const TC* __restrict__ yb, DirView<TC> D,
                                                                       TC* __restrict__ tau, int nsys, size_t ybz) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nsys) return;
-  const int k = 4 * D.P;
+  const int P = D.P, k = 4 * P;
   const int slot = blockIdx.z + j / D.spp;
   yb += blockIdx.z * ybz;
   tau += blockIdx.z * ybz;
   const int q = blockIdx.y;
   const TC* row = D.rinv + (size_t)slot * k * k + (size_t)q * k;
+  const int sq = q >> 2, nb = 2 * D.band + 1 < P ? 2 * D.band + 1 : P;
+  const int s0 = nb == P ? 0 : sq - D.band;
   TC acc0 = 0, acc1 = 0;
-  int p = 0;
-  for (; p + 8 <= k; p += 8) {
+  for (int bb = 0; bb < nb; bb += 2) {
     TC v[8];
+    int pc[2];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = yb[(size_t)(p + u) * nsys + j];
+    for (int h = 0; h < 2; ++h) {
+      int sb = s0 + bb + h;
+      sb = sb < 0 ? sb + P : (sb >= P ? sb - P : sb);
+      pc[h] = 4 * sb;
 #pragma unroll
-    for (int u = 0; u < 8; u += 2) {
-      acc0 = fma(__ldg(&row[p + u]), v[u], acc0);
-      acc1 = fma(__ldg(&row[p + u + 1]), v[u + 1], acc1);
+      for (int u = 0; u < 4; ++u) v[4 * h + u] = (bb + h < nb) ? yb[(size_t)(pc[h] + u) * nsys + j] : TC(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc0 = fma(__ldg(&row[pc[0] + u]), v[u], acc0);
+    if (bb + 1 < nb) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc1 = fma(__ldg(&row[pc[1] + u]), v[4 + u], acc1);
     }
   }
-  for (; p < k; ++p) acc0 = fma(__ldg(&row[p]), yb[(size_t)p * nsys + j], acc0);
   tau[(size_t)q * nsys + j] = acc0 + acc1;
 }
 
-// Spike correction of element (row r of segment s) of system j; vw is the
-// slot's spike block.
+// Spike correction of element (row r of segment s) of system j, applied to y
+// as an FMA chain: y - V0 t0 - V1 t1 - W0 b0 - W1 b1 (vw: the slot's spikes).
 template <typename TC>
-__device__ __forceinline__ TC spike_corr(const TC* __restrict__ vw, const TC* __restrict__ tau, int m, int P,
-                                         int nsys, int s, int r, int j) {
+__device__ __forceinline__ TC spike_apply(TC y, const TC* __restrict__ vw, const TC* __restrict__ tau, int m, int P,
+                                          int nsys, int s, int r, int j) {
   const int sn = s + 1 == P ? 0 : s + 1, sp = s == 0 ? P - 1 : s - 1;
   const size_t S = (size_t)nsys;
-  TC c = __ldg(&vw[r]) * tau[(size_t)(4 * sn + 0) * S + j];
-  c = fma(__ldg(&vw[m + r]), tau[(size_t)(4 * sn + 1) * S + j], c);
-  c = fma(__ldg(&vw[2 * m + r]), tau[(size_t)(4 * sp + 2) * S + j], c);
-  c = fma(__ldg(&vw[3 * m + r]), tau[(size_t)(4 * sp + 3) * S + j], c);
-  return c;
+  y = fma(-__ldg(&vw[r]), tau[(size_t)(4 * sn + 0) * S + j], y);
+  y = fma(-__ldg(&vw[m + r]), tau[(size_t)(4 * sn + 1) * S + j], y);
+  y = fma(-__ldg(&vw[2 * m + r]), tau[(size_t)(4 * sp + 2) * S + j], y);
+  return fma(-__ldg(&vw[3 * m + r]), tau[(size_t)(4 * sp + 3) * S + j], y);
 }
 
 // x-sweep correction + transpose back: y (element i of row-system (z, j) at
@@ -258,7 +276,7 @@ __global__ void __launch_bounds__(kT* kBY) ch_xfinish_kernel(const TC* __restric
     const int li = threadIdx.y + k * kBY, i = i0 + li;
     if (i < nx && j < ny) {
       const int s = i / m, r = i - s * m;
-      s_t[li][threadIdx.x] = (TO)(y1[(size_t)i * ld + sys] - spike_corr(vw, t1, m, P, G * ny, s, r, sys));
+      s_t[li][threadIdx.x] = (TO)spike_apply(y1[(size_t)i * ld + sys], vw, t1, m, P, G * ny, s, r, sys);
     }
   }
   __syncthreads();
@@ -284,9 +302,10 @@ __global__ void __launch_bounds__(kSolveThreads) ch_update_kernel(const TC* __re
   const int s = j / m, r = j - s * m;
   const size_t p = (size_t)z * nx * ny + (size_t)j * nx + i;
   t1 += (size_t)z * 4 * P * nx;
-  const TC v = y1[p] - spike_corr(D.vw + (size_t)z * 4 * m, t1, m, P, nx, s, r, i);
   const double a = cn[p], b = cp[p];
-  const double nxt = fma(2.0, a, -b) + (double)v;
+  // C^{n+1} = 2a - b + y - corr: (y - b), then + 2a, then the four spike terms
+  const double nxt = (double)spike_apply((TC)fma(2.0, a, (double)y1[p] - b), D.vw + (size_t)z * 4 * m, t1, m, P, nx,
+                                         s, r, i);
   if (keep_roles) {
     cp[p] = a;
     cn[p] = nxt;
@@ -405,6 +424,26 @@ int dir_factors_host(int n, int P, double a, std::vector<double>& lu, std::vecto
   return dense_inverse_host(k, R.data(), rinv.data());
 }
 
+// Largest circular segment distance whose Rinv block is not below 1e-17 of the
+// largest block entry.
+int rinv_band(const std::vector<double>& rinv, int P) {
+  const int k = 4 * P;
+  std::vector<double> mx(P / 2 + 1, 0.0);
+  double all = 0.0;
+  for (int q = 0; q < k; ++q)
+    for (int p = 0; p < k; ++p) {
+      int d = (p / 4 - q / 4 + P) % P;
+      if (d > P / 2) d = P - d;
+      const double v = fabs(rinv[(size_t)q * k + p]);
+      if (v > mx[d]) mx[d] = v;
+      if (v > all) all = v;
+    }
+  int band = 0;
+  for (int d = 0; d <= P / 2; ++d)
+    if (mx[d] > 1e-17 * all) band = d;
+  return band;
+}
+
 template <typename T>
 int dev_alloc(T** p, size_t cnt) {
   if (cudaMalloc(p, cnt * sizeof(T)) != cudaSuccess) {
@@ -441,6 +480,9 @@ int dir_set(SpikeDir* D, int z, double a) {
   std::vector<double> lu, vw, rinv;
   int rc = dir_factors_host(D->n, D->P, a, lu, vw, rinv);
   if (rc) return rc;
+  // the band is shared by the slots: keep the widest any slot has needed
+  const int band = rinv_band(rinv, D->P);
+  if (band > D->band) D->band = band;
   const size_t m4 = 4 * (size_t)D->m, kk = (size_t)16 * D->P * D->P;
   const std::vector<double> av(1, a);
   const float2 aff = split_ff(a);
@@ -493,11 +535,11 @@ template <typename T>
 DirView<T> view(const SpikeDir& D, int spp);
 template <>
 DirView<double> view<double>(const SpikeDir& D, int spp) {
-  return DirView<double>{D.d_a, D.d_lu, D.d_vw, D.d_rinv, D.m, D.P, spp};
+  return DirView<double>{D.d_a, D.d_lu, D.d_vw, D.d_rinv, D.m, D.P, spp, D.band};
 }
 template <>
 DirView<float> view<float>(const SpikeDir& D, int spp) {
-  return DirView<float>{D.d_a32, D.d_lu32, D.d_vw32, D.d_rinv32, D.m, D.P, spp};
+  return DirView<float>{D.d_a32, D.d_lu32, D.d_vw32, D.d_rinv32, D.m, D.P, spp, D.band};
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }

@@ -18,6 +18,7 @@ namespace chx {
 // z * 4m (lu, vw) and z * (4P)^2 (rinv).
 struct SpikeDir {
   int n = 0, P = 1, m = 0, slots = 0;
+  int band = 0;                 // reduced inverse kept for segment distances <= band (all slots)
   double* d_a = nullptr;        // slots: a = (2/3) gamma dt / h^4
   double* d_lu = nullptr;       // slots x 4m: ralpha, beta, gam, del of the segment block
   double* d_vw = nullptr;       // slots x 4m: spikes V0, V1, W0, W1
@@ -36,7 +37,7 @@ struct DirView {
   const T* lu;
   const T* vw;
   const T* rinv;
-  int m, P, spp;
+  int m, P, spp, band;
 };
 
 // Per-kernel CUDA-event timing (ch_profile).

@@ -220,6 +220,7 @@ extern "C" int ens_slot_load(chx_ens* e, int group_id, int slot, const double* c
     if (!rc) rc = group_set_gamma(&G->g, slot, gamma);
     if (rc) return rc;
     G->slot_gamma[slot] = gamma;
+    e->dirty = true;  // the reduced-solve band captured in the graph may have grown
   }
   rc = cuda_check(cudaMemcpyAsync((char*)G->d_state[G->cur] + slot * nb, c0, nb, cudaMemcpyDefault, st),
                       "ens_slot_load: C^n");

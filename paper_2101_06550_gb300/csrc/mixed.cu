@@ -24,19 +24,31 @@ __device__ __forceinline__ int wrapi(int i, int n) {
   return r < 0 ? r + n : r;
 }
 
+// Wrap for indices within a few periods of [0, n): two compares instead of a
+// division on the common path.
+__device__ __forceinline__ int wrap_near(int i, int n) {
+  if (i >= 0 && i < n) return i;
+  if (i < 0 && i >= -n) return i + n;
+  if (i >= n && i < 2 * n) return i - n;
+  return wrapi(i, n);
+}
+
 __device__ __forceinline__ ff ffc(float2 c) { return ff{c.x, c.y}; }
 
-// L'(u) = (E + W) + rho (N + S) + kap C on shared-memory ff tiles.
-template <int LD>
+// L'(u) = (E + W) + rho (N + S) + kap C on shared-memory ff tiles; for a
+// square cell (rho = 1, kap = -4) the scalings are exact and skipped.
+template <int LD, bool kIso>
 __device__ __forceinline__ ff lap_ff(const ff (*t)[LD], int y, int x, ff rho, ff kap) {
   ff a = ff_add(t[y][x - 1], t[y][x + 1]);
-  ff b = ff_add(t[y - 1][x], t[y + 1][x]);
+  const ff b = ff_add(t[y - 1][x], t[y + 1][x]);
+  if (kIso) return ff_add(ff_add(a, b), ff_scale2(t[y][x], -4.f));
   a = ff_add(a, ff_mul(rho, b));
   return ff_add(a, ff_mul(kap, t[y][x]));
 }
 
 // Right-hand side of Eq. 3.1 in double-float: r = k2 L'(M) - k1 (C^n - C^{n-1}),
 // M = C^3 - C - gl L'(Cbar).  Same tiling as the FP64 kernel; r written transposed.
+template <bool kIso>
 __global__ void __launch_bounds__(kT* kBY) ch_rhs_ff_kernel(const double* __restrict__ cn,
                                                             const double* __restrict__ cp, float* __restrict__ rhi,
                                                             float* __restrict__ rlo, int nx, int ny, int G, float2 rho2,
@@ -54,7 +66,7 @@ __global__ void __launch_bounds__(kT* kBY) ch_rhs_ff_kernel(const double* __rest
   const int tid = threadIdx.y * kT + threadIdx.x;
   for (int idx = tid; idx < (kT + 4) * (kT + 4); idx += kT * kBY) {
     const int ly = idx / (kT + 4), lx = idx % (kT + 4);
-    const int gi = wrapi(i0 - 2 + lx, nx), gj = wrapi(j0 - 2 + ly, ny);
+    const int gi = wrap_near(i0 - 2 + lx, nx), gj = wrap_near(j0 - 2 + ly, ny);
     const size_t p = (size_t)gj * nx + gi;
     const ff a = d2ff(cn[p]), b = d2ff(cp[p]);
     s_cn[ly][lx] = a;
@@ -63,7 +75,7 @@ __global__ void __launch_bounds__(kT* kBY) ch_rhs_ff_kernel(const double* __rest
   __syncthreads();
   for (int idx = tid; idx < (kT + 2) * (kT + 2); idx += kT * kBY) {
     const int ly = idx / (kT + 2) + 1, lx = idx % (kT + 2) + 1;
-    const ff l = lap_ff<kT + 5>(s_cb, ly, lx, rho, kap);
+    const ff l = lap_ff<kT + 5, kIso>(s_cb, ly, lx, rho, kap);
     const ff c = s_cn[ly][lx];
     const ff nl = ff_mul(c, ff_add_f(ff_mul(c, c), -1.f));
     s_m[ly - 1][lx - 1] = ff_sub(nl, ff_mul(gl, l));
@@ -72,7 +84,7 @@ __global__ void __launch_bounds__(kT* kBY) ch_rhs_ff_kernel(const double* __rest
 #pragma unroll
   for (int k = 0; k < kT / kBY; ++k) {
     const int ly = threadIdx.y + k * kBY + 1, lx = threadIdx.x + 1;
-    const ff l = lap_ff<kT + 3>(s_m, ly, lx, rho, kap);
+    const ff l = lap_ff<kT + 3, kIso>(s_m, ly, lx, rho, kap);
     const ff diff = ff_sub(s_cb[ly + 1][lx + 1], s_cn[ly + 1][lx + 1]);  // C^n - C^{n-1}
     s_o[lx - 1][ly - 1] = ff_sub(ff_mul(k2, l), ff_mul(k1, diff));
   }
@@ -311,6 +323,9 @@ __global__ void __launch_bounds__(kSolveThreads) ch_update_ff_kernel(const float
 // r = f - A x0 in double-float (rows of A as double-float constants, f split
 // from FP64 by bits), FP32 sweeps for delta, x = x0 + delta added in FP64.
 // The forward intermediate is kept as a float in the low half of f's slot.
+// Loads of f and x0 run U rows ahead of the sweep.
+constexpr int kPU = 8;
+
 __global__ void __launch_bounds__(kSolveThreads) penta_refine_ff_kernel(double* x, const float* __restrict__ x0,
                                                                         int n, int batch,
                                                                         const float* __restrict__ fac,
@@ -323,49 +338,95 @@ __global__ void __launch_bounds__(kSolveThreads) penta_refine_ff_kernel(double* 
 #define FAC(k, r) __ldg(&fac[(size_t)(k) * m + (r)])
   double* px = x + s;
   const float* p0 = x0 + s;
+  // window of x0 at rows r-2..r+2; rows ahead come from the prefetch buffers
   float w0 = p0[(size_t)(n - 2) * B], w1 = p0[(size_t)(n - 1) * B];
-  float w2 = p0[0], w3 = p0[B], w4 = p0[2 * B];
+  float w2 = p0[0], w3 = p0[B];
   float g1 = 0.f, g2 = 0.f, t0 = 0.f, t1 = 0.f, rt0 = 0.f, rt1 = 0.f;
-  for (int r = 0; r < n; ++r) {
-    const float2 ca = __ldg(&coef[r]), cb = __ldg(&coef[n + r]), cc = __ldg(&coef[2 * n + r]);
-    const float2 cd = __ldg(&coef[3 * n + r]), ce = __ldg(&coef[4 * n + r]);
-    ff ax = ff_mul_f(ffc(cc), w2);
-    ax = ff_add(ax, ff_mul_f(ffc(cb), w1));
-    ax = ff_add(ax, ff_mul_f(ffc(cd), w3));
-    ax = ff_add(ax, ff_mul_f(ffc(ca), w0));
-    ax = ff_add(ax, ff_mul_f(ffc(ce), w4));
-    const float res = ff_sub(d2ff(px[(size_t)r * B]), ax).hi;
-    if (r < m) {
-      float g = fmaf(-FAC(2, r), g2, res);
-      g = fmaf(-FAC(1, r), g1, g) * FAC(0, r);
-      t0 = fmaf(FAC(5, r), res, t0);
-      t1 = fmaf(FAC(6, r), res, t1);
-      reinterpret_cast<float*>(px + (size_t)r * B)[0] = g;
-      g2 = g1;
-      g1 = g;
-    } else if (r == m) {
-      rt0 = res;
-    } else {
-      rt1 = res;
+  double fb[kPU];
+  float xb[kPU];  // x0 at rows r+2
+#pragma unroll
+  for (int u = 0; u < kPU; ++u) {
+    fb[u] = (u < n) ? px[(size_t)u * B] : 0.0;
+    const int q = u + 2 < n ? u + 2 : u + 2 - n;
+    xb[u] = (u < n) ? p0[(size_t)q * B] : 0.f;
+  }
+  for (int r0 = 0; r0 < n; r0 += kPU) {
+    double fn[kPU];
+    float xn[kPU];
+#pragma unroll
+    for (int u = 0; u < kPU; ++u) {
+      const int r = r0 + kPU + u;
+      fn[u] = (r < n) ? px[(size_t)r * B] : 0.0;
+      const int q = r + 2 < n ? r + 2 : r + 2 - n;
+      xn[u] = (r < n) ? p0[(size_t)q * B] : 0.f;
     }
-    w0 = w1; w1 = w2; w2 = w3; w3 = w4;
-    const int nx = (r + 3 < n) ? r + 3 : r + 3 - n;
-    w4 = p0[(size_t)nx * B];
+#pragma unroll
+    for (int u = 0; u < kPU; ++u) {
+      const int r = r0 + u;
+      if (r < n) {
+        const float w4 = xb[u];
+        const float2 ca = __ldg(&coef[r]), cb = __ldg(&coef[n + r]), cc = __ldg(&coef[2 * n + r]);
+        const float2 cd = __ldg(&coef[3 * n + r]), ce = __ldg(&coef[4 * n + r]);
+        ff ax = ff_mul_f(ffc(cc), w2);
+        ax = ff_add(ax, ff_mul_f(ffc(cb), w1));
+        ax = ff_add(ax, ff_mul_f(ffc(cd), w3));
+        ax = ff_add(ax, ff_mul_f(ffc(ca), w0));
+        ax = ff_add(ax, ff_mul_f(ffc(ce), w4));
+        const float res = ff_sub(d2ff(fb[u]), ax).hi;
+        if (r < m) {
+          float g = fmaf(-FAC(2, r), g2, res);
+          g = fmaf(-FAC(1, r), g1, g) * FAC(0, r);
+          t0 = fmaf(FAC(5, r), res, t0);
+          t1 = fmaf(FAC(6, r), res, t1);
+          reinterpret_cast<float*>(px + (size_t)r * B)[0] = g;
+          g2 = g1;
+          g1 = g;
+        } else if (r == m) {
+          rt0 = res;
+        } else {
+          rt1 = res;
+        }
+        w0 = w1; w1 = w2; w2 = w3; w3 = w4;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kPU; ++u) { fb[u] = fn[u]; xb[u] = xn[u]; }
   }
   const float a0 = rt0 - t0, a1 = rt1 - t1;
   const float xt0 = fmaf(s00, a0, s01 * a1), xt1 = fmaf(s10, a0, s11 * a1);
   px[(size_t)m * B] = f2d_exact(p0[(size_t)m * B]) + f2d_exact(xt0);
   px[(size_t)(m + 1) * B] = f2d_exact(p0[(size_t)(m + 1) * B]) + f2d_exact(xt1);
   float d1 = 0.f, d2 = 0.f;
-  for (int r = m - 1; r >= 0; --r) {
-    const float g = reinterpret_cast<const float*>(px + (size_t)r * B)[0];
-    float v = fmaf(-FAC(7, r), xt0, g);
-    v = fmaf(-FAC(8, r), xt1, v);
-    v = fmaf(-FAC(3, r), d1, v);
-    v = fmaf(-FAC(4, r), d2, v);
-    px[(size_t)r * B] = f2d_exact(p0[(size_t)r * B]) + f2d_exact(v);
-    d2 = d1;
-    d1 = v;
+  float gb[kPU], zb[kPU];
+#pragma unroll
+  for (int u = 0; u < kPU; ++u) {
+    const int r = m - 1 - u;
+    gb[u] = (r >= 0) ? reinterpret_cast<const float*>(px + (size_t)r * B)[0] : 0.f;
+    zb[u] = (r >= 0) ? p0[(size_t)r * B] : 0.f;
+  }
+  for (int r0 = m - 1; r0 >= 0; r0 -= kPU) {
+    float gn[kPU], zn[kPU];
+#pragma unroll
+    for (int u = 0; u < kPU; ++u) {
+      const int r = r0 - kPU - u;
+      gn[u] = (r >= 0) ? reinterpret_cast<const float*>(px + (size_t)r * B)[0] : 0.f;
+      zn[u] = (r >= 0) ? p0[(size_t)r * B] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kPU; ++u) {
+      const int r = r0 - u;
+      if (r >= 0) {
+        float v = fmaf(-FAC(7, r), xt0, gb[u]);
+        v = fmaf(-FAC(8, r), xt1, v);
+        v = fmaf(-FAC(3, r), d1, v);
+        v = fmaf(-FAC(4, r), d2, v);
+        px[(size_t)r * B] = f2d_exact(zb[u]) + f2d_exact(v);
+        d2 = d1;
+        d1 = v;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kPU; ++u) { gb[u] = gn[u]; zb[u] = zn[u]; }
   }
 #undef FAC
 }
@@ -386,29 +447,66 @@ __global__ void __launch_bounds__(kSolveThreads) penta_solve_f32_from_f64_kernel
   const double* pin = in + s;
   float* pw = work + s;
   float g1 = 0.f, g2 = 0.f, t0 = 0.f, t1 = 0.f;
-  for (int r = 0; r < m; ++r) {
-    const float f = d2ff(pin[(size_t)r * B]).hi;
-    float g = fmaf(-FAC(2, r), g2, f);
-    g = fmaf(-FAC(1, r), g1, g) * FAC(0, r);
-    t0 = fmaf(FAC(5, r), f, t0);
-    t1 = fmaf(FAC(6, r), f, t1);
-    pw[(size_t)r * B] = g;
-    g2 = g1;
-    g1 = g;
+  double fb[kPU];
+#pragma unroll
+  for (int u = 0; u < kPU; ++u) fb[u] = (u < m) ? pin[(size_t)u * B] : 0.0;
+  for (int r0 = 0; r0 < m; r0 += kPU) {
+    double fn[kPU];
+#pragma unroll
+    for (int u = 0; u < kPU; ++u) {
+      const int r = r0 + kPU + u;
+      fn[u] = (r < m) ? pin[(size_t)r * B] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kPU; ++u) {
+      const int r = r0 + u;
+      if (r < m) {
+        const float f = d2ff(fb[u]).hi;
+        float g = fmaf(-FAC(2, r), g2, f);
+        g = fmaf(-FAC(1, r), g1, g) * FAC(0, r);
+        t0 = fmaf(FAC(5, r), f, t0);
+        t1 = fmaf(FAC(6, r), f, t1);
+        pw[(size_t)r * B] = g;
+        g2 = g1;
+        g1 = g;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kPU; ++u) fb[u] = fn[u];
   }
-  const float r0 = d2ff(pin[(size_t)m * B]).hi - t0, r1 = d2ff(pin[(size_t)(m + 1) * B]).hi - t1;
-  const float xt0 = fmaf(s00, r0, s01 * r1), xt1 = fmaf(s10, r0, s11 * r1);
+  const float r0v = d2ff(pin[(size_t)m * B]).hi - t0, r1v = d2ff(pin[(size_t)(m + 1) * B]).hi - t1;
+  const float xt0 = fmaf(s00, r0v, s01 * r1v), xt1 = fmaf(s10, r0v, s11 * r1v);
   pw[(size_t)m * B] = xt0;
   pw[(size_t)(m + 1) * B] = xt1;
   float x1 = 0.f, x2 = 0.f;
-  for (int r = m - 1; r >= 0; --r) {
-    float v = fmaf(-FAC(7, r), xt0, pw[(size_t)r * B]);
-    v = fmaf(-FAC(8, r), xt1, v);
-    v = fmaf(-FAC(3, r), x1, v);
-    v = fmaf(-FAC(4, r), x2, v);
-    pw[(size_t)r * B] = v;
-    x2 = x1;
-    x1 = v;
+  float gb[kPU];
+#pragma unroll
+  for (int u = 0; u < kPU; ++u) {
+    const int r = m - 1 - u;
+    gb[u] = (r >= 0) ? pw[(size_t)r * B] : 0.f;
+  }
+  for (int r0 = m - 1; r0 >= 0; r0 -= kPU) {
+    float gn[kPU];
+#pragma unroll
+    for (int u = 0; u < kPU; ++u) {
+      const int r = r0 - kPU - u;
+      gn[u] = (r >= 0) ? pw[(size_t)r * B] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kPU; ++u) {
+      const int r = r0 - u;
+      if (r >= 0) {
+        float v = fmaf(-FAC(7, r), xt0, gb[u]);
+        v = fmaf(-FAC(8, r), xt1, v);
+        v = fmaf(-FAC(3, r), x1, v);
+        v = fmaf(-FAC(4, r), x2, v);
+        pw[(size_t)r * B] = v;
+        x2 = x1;
+        x1 = v;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kPU; ++u) gb[u] = gn[u];
   }
 #undef FAC
 }
@@ -418,7 +516,10 @@ __global__ void __launch_bounds__(kSolveThreads) penta_solve_f32_from_f64_kernel
 void launch_ch_rhs_ff(const double* cn, const double* cp, float* rhi, float* rlo, int nx, int ny, int G,
                       const FFConst& k, const float2* glff, cudaStream_t st) {
   const dim3 grid(ceil_div(nx, kT), ceil_div(ny, kT), G), block(kT, kBY);
-  ch_rhs_ff_kernel<<<grid, block, 0, st>>>(cn, cp, rhi, rlo, nx, ny, G, k.rho, k.kap, glff, k.k1, k.k2);
+  if (k.rho.x == 1.f && k.rho.y == 0.f)
+    ch_rhs_ff_kernel<true><<<grid, block, 0, st>>>(cn, cp, rhi, rlo, nx, ny, G, k.rho, k.kap, glff, k.k1, k.k2);
+  else
+    ch_rhs_ff_kernel<false><<<grid, block, 0, st>>>(cn, cp, rhi, rlo, nx, ny, G, k.rho, k.kap, glff, k.k1, k.k2);
 }
 
 void launch_spike_refine_ff(const float* fhi, const float* flo, const float* y1, const float* t1, float* y2, float* yb,
