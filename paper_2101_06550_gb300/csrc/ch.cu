@@ -26,9 +26,11 @@
 #include <string.h>
 
 #include <new>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
+#include "bulk.cuh"
 #include "chgroup.cuh"
 
 using namespace chx;
@@ -202,6 +204,63 @@ __global__ void __launch_bounds__(kSolveThreads) spike_local_kernel(const TIn* f
   const size_t S = (size_t)nsys;
   yb[(size_t)(4 * s + 0) * S + j] = x1;  // y_0
   yb[(size_t)(4 * s + 1) * S + j] = x2;  // y_1
+  yb[(size_t)(4 * s + 2) * S + j] = ylast2;
+  yb[(size_t)(4 * s + 3) * S + j] = ylast;
+}
+
+// The same sweeps with the segment tile staged in shared memory: one thread
+// issues bulk asynchronous copies of the m rows (32 systems each) onto an
+// mbarrier, so the whole tile is in flight at once, and the forward
+// intermediate stays on chip instead of making a round trip through HBM.
+// Requires nsys % 32 == 0 and 16-byte aligned rows (checked by the host).
+template <typename TC>
+__global__ void __launch_bounds__(32) spike_local_staged_kernel(const TC* f, TC* y, int ld, int nsys, DirView<TC> D,
+                                                                TC* __restrict__ yb, size_t fz, size_t ybz,
+                                                                int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t bar;
+  TC* tile = reinterpret_cast<TC*>(smem_raw);
+  const int t = threadIdx.x, s = blockIdx.y, m = D.m;
+  const int j0 = blockIdx.x * 32, j = j0 + t;
+  f += blockIdx.z * fz;
+  y += blockIdx.z * fz;
+  yb += blockIdx.z * ybz;
+  const size_t L = (size_t)ld;
+  if (t == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (t == 0) bulk_tile_load(tile, (const char*)(f + (size_t)s * m * L + j0), L * sizeof(TC), 32 * sizeof(TC), m, &bar);
+  if (!mbar_wait_bounded(&bar, 0, status)) {
+    mbar_wait_bounded(&bar, 0, status);  // let copies still in flight land before the CTA exits
+    return;
+  }
+  const int slot = blockIdx.z + j / D.spp;
+  const TC a = D.a[slot];
+  const TC* lu = D.lu + (size_t)slot * 4 * m;
+  const TC *ra = lu, *be = lu + m, *ga = lu + 2 * m, *de = lu + 3 * m;
+  TC g1 = 0, g2 = 0;
+#pragma unroll 8
+  for (int r = 0; r < m; ++r) {
+    TC g = fma(-a, g2, tile[r * 32 + t]);
+    g = fma(-__ldg(&be[r]), g1, g) * __ldg(&ra[r]);
+    tile[r * 32 + t] = g;
+    g2 = g1;
+    g1 = g;
+  }
+  TC x1 = 0, x2 = 0, ylast = 0, ylast2 = 0;
+  TC* py = y + (size_t)s * m * L + j;
+#pragma unroll 8
+  for (int r = m - 1; r >= 0; --r) {
+    TC v = fma(-__ldg(&ga[r]), x1, tile[r * 32 + t]);
+    v = fma(-__ldg(&de[r]), x2, v);
+    py[(size_t)r * L] = v;
+    if (r == m - 1) ylast = v;
+    if (r == m - 2) ylast2 = v;
+    x2 = x1;
+    x1 = v;
+  }
+  const size_t S = (size_t)nsys;
+  yb[(size_t)(4 * s + 0) * S + j] = x1;
+  yb[(size_t)(4 * s + 1) * S + j] = x2;
   yb[(size_t)(4 * s + 2) * S + j] = ylast2;
   yb[(size_t)(4 * s + 3) * S + j] = ylast;
 }
@@ -722,8 +781,34 @@ void group_free(ChGroup* g) {
   g->d_glff = nullptr;
 }
 
+// Segment-local sweeps.  FP32: the shared-memory staged kernel when the tile
+// rows are 16-byte aligned and the systems fill whole warps (measured 20 us vs
+// 24 us at 2048^2).  FP64: the register-prefetch kernel, which keeps the FP64
+// pipe busier (51 us vs 82 us staged: the serial chain per system, not load
+// latency, limits these sweeps).
+template <typename TIn, typename TC>
+static void launch_local(const TIn* f, TC* y, int ld, int nsys, const DirView<TC>& D, TC* yb, size_t fz, size_t ybz,
+                         int Z, int* status, cudaStream_t st) {
+  const size_t tile = (size_t)D.m * 32 * sizeof(TC);
+  const bool aligned = std::is_same<TIn, TC>::value && sizeof(TC) == 4 && nsys % 32 == 0 &&
+                       ((size_t)ld * sizeof(TC)) % 16 == 0 &&
+                       (fz * sizeof(TC)) % 16 == 0 && ((uintptr_t)f & 15) == 0 && tile <= 200 * 1024;
+  if (aligned) {
+    static bool attr_set = false;  // one opt-in per instantiation
+    if (!attr_set) {
+      cudaFuncSetAttribute(spike_local_staged_kernel<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr_set = true;
+    }
+    spike_local_staged_kernel<TC><<<dim3(nsys / 32, D.P, Z), 32, tile, st>>>((const TC*)f, y, ld, nsys, D, yb, fz, ybz,
+                                                                           status);
+  } else {
+    spike_local_kernel<TIn, TC><<<dim3(ceil_div(nsys, kSolveThreads), D.P, Z), kSolveThreads, 0, st>>>(f, y, ld, nsys, D,
+                                                                                                    yb, fz, ybz);
+  }
+}
+
 static void step_f64(ChGroup* g, int G, double* cur, double* prev, void* work, int keep_roles, cudaStream_t st,
-                     Prof* prof) {
+                     Prof* prof, int* status) {
   const int nx = g->nx, ny = g->ny;
   const size_t N = (size_t)nx * ny;
   double* f = wptr<double>(work, g->off_f);
@@ -736,17 +821,17 @@ static void step_f64(ChGroup* g, int G, double* cur, double* prev, void* work, i
   const dim3 gx(ceil_div(nsx, kSolveThreads), X.P), gy(ceil_div(nx, kSolveThreads), Y.P, G);
   const size_t kyz = 4 * (size_t)Y.P * nx;
   { PROF(kRhs); ch_rhs_kernel<double, double><<<tgrid, tblock, 0, st>>>(cur, prev, f, nx, ny, G, g->rho, g->kap, g->d_gl, g->k1, g->k2); }
-  { PROF(kLocX); spike_local_kernel<double, double><<<gx, kSolveThreads, 0, st>>>(f, f, nsx, nsx, X, ybx, 0, 0); }
+  { PROF(kLocX); launch_local<double, double>(f, f, nsx, nsx, X, ybx, 0, 0, 1, status, st); }
   { PROF(kRedX); spike_reduced_kernel<double><<<dim3(gx.x, 4 * X.P), kSolveThreads, 0, st>>>(ybx, X, tx, nsx, 0); }
   { PROF(kFinX); ch_xfinish_kernel<double, double><<<tgrid, tblock, 0, st>>>(f, tx, X, w, nx, ny, G); }
-  { PROF(kLocY); spike_local_kernel<double, double><<<gy, kSolveThreads, 0, st>>>(w, w, nx, nx, Y, yby, N, kyz); }
+  { PROF(kLocY); launch_local<double, double>(w, w, nx, nx, Y, yby, N, kyz, G, status, st); }
   { PROF(kRedY); spike_reduced_kernel<double><<<dim3(gy.x, 4 * Y.P, G), kSolveThreads, 0, st>>>(yby, Y, ty, nx, kyz); }
   { PROF(kUpd); ch_update_kernel<double><<<dim3(ceil_div(nx, kSolveThreads), ny, G), kSolveThreads, 0, st>>>(
         w, ty, Y, cur, prev, nx, ny, keep_roles); }
 }
 
 static void step_f32r(ChGroup* g, int G, double* cur, double* prev, void* work, int keep_roles, cudaStream_t st,
-                      Prof* prof) {
+                      Prof* prof, int* status) {
   const int nx = g->nx, ny = g->ny;
   const size_t N = (size_t)nx * ny;
   float *fhi = wptr<float>(work, g->off_f), *flo = wptr<float>(work, g->off_flo);
@@ -764,23 +849,23 @@ static void step_f32r(ChGroup* g, int G, double* cur, double* prev, void* work, 
   // right-hand side in double-float
   { PROF(kRhs); launch_ch_rhs_ff(cur, prev, fhi, flo, nx, ny, G, g->kff, g->d_glff, st); }
   // x: FP32 solve of the high part, double-float residual, FP32 correction solve
-  { PROF(kLocX); spike_local_kernel<float, float><<<gx, kSolveThreads, 0, st>>>(fhi, y1, nsx, nsx, X, ybx, 0, 0); }
+  { PROF(kLocX); launch_local<float, float>(fhi, y1, nsx, nsx, X, ybx, 0, 0, 1, status, st); }
   { PROF(kRedX); spike_reduced_kernel<float><<<dim3(gx.x, 4 * X.P), kSolveThreads, 0, st>>>(ybx, X, tx, nsx, 0); }
-  { PROF(kRefX); launch_spike_refine_ff(fhi, flo, y1, tx, y2, ybx2, nsx, nsx, nx, X, g->X.d_aff, 1, 0, 0, st); }
+  { PROF(kRefX); launch_spike_refine_ff(fhi, flo, y1, tx, y2, ybx2, nsx, nsx, nx, X, g->X.d_aff, 1, 0, 0, status, st); }
   { PROF(kRed2X); spike_reduced_kernel<float><<<dim3(gx.x, 4 * X.P), kSolveThreads, 0, st>>>(ybx2, X, tx2, nsx, 0); }
   { PROF(kFinX); launch_ch_xfinish_ff(y1, tx, y2, tx2, X, whi, wlo, nx, ny, G, st); }
   // y
-  { PROF(kLocY); spike_local_kernel<float, float><<<gy, kSolveThreads, 0, st>>>(whi, y1, nx, nx, Y, yby, N, kyz); }
+  { PROF(kLocY); launch_local<float, float>(whi, y1, nx, nx, Y, yby, N, kyz, G, status, st); }
   { PROF(kRedY); spike_reduced_kernel<float><<<dim3(gy.x, 4 * Y.P, G), kSolveThreads, 0, st>>>(yby, Y, ty, nx, kyz); }
-  { PROF(kRefY); launch_spike_refine_ff(whi, wlo, y1, ty, y2, yby2, nx, nx, ny, Y, g->Y.d_aff, G, N, kyz, st); }
+  { PROF(kRefY); launch_spike_refine_ff(whi, wlo, y1, ty, y2, yby2, nx, nx, ny, Y, g->Y.d_aff, G, N, kyz, status, st); }
   { PROF(kRed2Y); spike_reduced_kernel<float><<<dim3(gy.x, 4 * Y.P, G), kSolveThreads, 0, st>>>(yby2, Y, ty2, nx, kyz); }
   { PROF(kUpd); launch_ch_update_ff(y1, ty, y2, ty2, Y, cur, prev, nx, ny, G, keep_roles, st); }
 }
 
 void group_step(ChGroup* g, int gact, double* cur, double* prev, void* work, int keep_roles, cudaStream_t st,
-                Prof* prof) {
-  if (g->precision == CHX_PREC_F64) step_f64(g, gact, cur, prev, work, keep_roles, st, prof);
-  else step_f32r(g, gact, cur, prev, work, keep_roles, st, prof);
+                Prof* prof, int* status) {
+  if (g->precision == CHX_PREC_F64) step_f64(g, gact, cur, prev, work, keep_roles, st, prof, status);
+  else step_f32r(g, gact, cur, prev, work, keep_roles, st, prof, status);
 }
 
 void ch_plan_free(chx_ch_plan* p) {
@@ -842,7 +927,7 @@ extern "C" int ch_step(chx_ch_plan* p, double* c_now, double* c_prev, void* work
   for (int s = 0; s < nsteps; ++s) {
     const int last = s == nsteps - 1;
     const int keep = last && cur == c_now;
-    group_step(&p->g, 1, cur, prev, work, keep, st, p->prof);
+    group_step(&p->g, 1, cur, prev, work, keep, st, p->prof, p->hdr.d_status);
     if (!keep) {
       double* t = cur;
       cur = prev;

@@ -96,7 +96,8 @@ std::vector<int> segment_candidates(int n, int nsys, int precision);
 // gact contiguous fields of nx*ny doubles (C^n, C^{n-1}).  keep_roles = 0
 // writes C^{n+1} over prev (caller swaps); 1 writes C^n into prev and C^{n+1}
 // into cur.
+// status: device word for bounded-wait timeouts (CHX_ETIMEOUT), may be null.
 void group_step(ChGroup* g, int gact, double* cur, double* prev, void* work, int keep_roles, cudaStream_t st,
-                Prof* prof);
+                Prof* prof, int* status);
 
 }  // namespace chx

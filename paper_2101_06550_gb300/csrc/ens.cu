@@ -35,6 +35,7 @@ struct EnsGroup {
   cudaStream_t stream = nullptr;            // branch stream used during capture
   cudaEvent_t done = nullptr;
   std::vector<double> slot_gamma;           // gamma each slot is factorised for
+  int* status = nullptr;                    // the ensemble's device status word
   bool live = false;
 };
 
@@ -83,7 +84,7 @@ void step_group(EnsGroup* G, cudaStream_t st) {
   if (G->active < 1) return;
   const size_t N = (size_t)G->n * G->n;
   (void)N;
-  group_step(&G->g, G->active, G->d_state[G->cur], G->d_state[1 - G->cur], G->d_work, 0, st, nullptr);
+  group_step(&G->g, G->active, G->d_state[G->cur], G->d_state[1 - G->cur], G->d_work, 0, st, nullptr, G->status);
   G->cur = 1 - G->cur;
 }
 
@@ -188,6 +189,7 @@ extern "C" int ens_group_create(chx_ens* e, int n, double l, double gamma, int c
     free_group(G);
     return rc;
   }
+  G->status = e->hdr.d_status;
   G->live = true;
   e->used += G->bytes;
   e->groups->push_back(G);
@@ -340,11 +342,11 @@ extern "C" int ens_autotune(chx_ens* e, int group_id, int trial, int* px_out, in
       group_free(&trialg);
       continue;
     }
-    group_step(&trialg, G->active, G->d_state[G->cur], G->d_state[1 - G->cur], G->d_work, 0, st, nullptr);
+    group_step(&trialg, G->active, G->d_state[G->cur], G->d_state[1 - G->cur], G->d_work, 0, st, nullptr, G->status);
     G->cur = 1 - G->cur;
     cudaEventRecord(a, st);
     for (int k = 0; k < trial; ++k) {
-      group_step(&trialg, G->active, G->d_state[G->cur], G->d_state[1 - G->cur], G->d_work, 0, st, nullptr);
+      group_step(&trialg, G->active, G->d_state[G->cur], G->d_state[1 - G->cur], G->d_work, 0, st, nullptr, G->status);
       G->cur = 1 - G->cur;
     }
     cudaEventRecord(b, st);

@@ -524,7 +524,8 @@ void launch_ch_rhs_ff(const double* cn, const double* cp, float* rhi, float* rlo
 
 void launch_spike_refine_ff(const float* fhi, const float* flo, const float* y1, const float* t1, float* y2, float* yb,
                             int ld, int nsys, int n, const DirView<float>& D, const float2* aff, int Z, size_t fz,
-                            size_t ybz, cudaStream_t st) {
+                            size_t ybz, int* status, cudaStream_t st) {
+  (void)status;
   spike_refine_ff_kernel<16><<<dim3(ceil_div(nsys, kSolveThreads), D.P, Z), kSolveThreads, 0, st>>>(
       fhi, flo, y1, t1, y2, yb, ld, nsys, n, D, aff, fz, ybz);
 }
