@@ -98,6 +98,46 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(values, dist, device):
+    """Element-wise max of per-rank timings (ms) over all ranks; identity without a process group."""
+    import torch
+
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def fp32_accuracy(dev, warm=100):
+    """Config-3 accuracy of the FP32+refine step: per-step error against the CPU oracle
+    from the state the FP64 path reaches after `warm` steps, and the FP32 trajectory's
+    error and mass drift against the FP64 trajectory over the same steps."""
+    import torch
+
+    import oracle
+    import paper_2101_06550_gb300 as chx
+
+    c0 = torch.from_numpy(synth.field(SEED, N, N, -0.05, 0.05)).to(dev)
+    p64 = chx.ChPlan(N, N, LX, LX, GAMMA, DT, chx.PREC_F64)
+    p32 = chx.ChPlan(N, N, LX, LX, GAMMA, DT, chx.PREC_F32_REFINE)
+    a, b, c, d = c0.clone(), c0.clone(), c0.clone(), c0.clone()
+    p64.step(a, b, p64.alloc_work(dev), warm)
+    w32 = p32.alloc_work(dev)
+    p32.step(c, d, w32, warm)
+    torch.cuda.synchronize()
+    traj = float((a - c).abs().max() / a.abs().max())
+    cell = (LX / N) ** 2
+    drift = float(abs(c.sum() - c0.sum()) / c0.abs().sum())
+    an, bn = a.cpu().numpy(), b.cpu().numpy()
+    e, f = a.clone(), b.clone()
+    p32.step(e, f, w32, 1)
+    ref, _ = oracle.ch_step(an, bn, LX, LX, GAMMA, DT)
+    step_err = float(np.max(np.abs(e.cpu().numpy() - ref)) / np.max(np.abs(ref)))
+    return {"per_step_rel_err_vs_oracle_at_step": step_err, "step": warm + 1,
+            "trajectory_rel_err_vs_fp64_gpu": traj, "mass_drift_rel_to_sum_abs_c": drift,
+            "cell_area": cell}
+
+
 def cpu_baseline_oracle(steps: int):
     """The CPU oracle, as it stands (plain C, FP64, single thread), on `steps` full steps."""
     import oracle
@@ -202,10 +242,7 @@ def run_chx(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
 
-    t = torch.tensor([ms64, ms32, e2e_ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms64, ms32, e2e_ms = t.tolist()
+    ms64, ms32, e2e_ms = max_over_ranks([ms64, ms32, e2e_ms], dist, dev)
     if rank != 0:
         clk.__exit__(None, None, None)
         if dist:
@@ -230,6 +267,8 @@ def run_chx(args, rank, world, local_rank):
                 "frac": None, "traffic": None, "ms_per_launch": per_launch_ms}
     extras = {}
     if not args.no_extras:
+        extras["fp32_refine_accuracy"] = fp32_accuracy(dev)
+        torch.cuda.empty_cache()
         extras["solvers"] = bench_solvers(dev)
         torch.cuda.empty_cache()
         extras["ensemble"] = bench_ensemble(dev, chx.PREC_F32_REFINE, args.ens_steps, 3)

@@ -36,9 +36,10 @@
 using namespace chx;
 
 namespace chx {
-const char* const kSlotName[kSlots] = {"ch_rhs",         "spike_local_x", "spike_reduced_x", "spike_refine_x",
-                                       "spike_reduced2_x", "ch_xfinish",   "spike_local_y",   "spike_reduced_y",
-                                       "spike_refine_y", "spike_reduced2_y", "ch_update"};
+const char* const kSlotName[kSlots] = {"ch_rhs",           "spike_local_x",   "spike_reduced_x",  "ch_resid_x",
+                                       "spike_local2_x",   "spike_reduced2_x", "ch_xfinish",       "spike_local_y",
+                                       "spike_reduced_y",  "ch_resid_y",       "spike_local2_y",   "spike_reduced2_y",
+                                       "ch_update"};
 }  // namespace chx
 
 struct chx_ch_plan {
@@ -736,6 +737,7 @@ int group_init(ChGroup* g, int nx, int ny, double lx, double ly, double gamma, d
   g->off_wlo = off; off = align256(off + mix);
   g->off_y1 = off; off = align256(off + mix);
   g->off_y2 = off; off = align256(off + mix);
+  g->off_x0 = off; off = align256(off + mix);
   const size_t kx = 4 * (size_t)g->X.P * ny * G, ky = 4 * (size_t)g->Y.P * nx * G;
   g->off_ybx = off; off = align256(off + kx * esz);
   g->off_tx = off; off = align256(off + kx * esz);
@@ -838,6 +840,7 @@ static void step_f32r(ChGroup* g, int G, double* cur, double* prev, void* work, 
   float *whi = wptr<float>(work, g->off_w), *wlo = wptr<float>(work, g->off_wlo);
   float* y1 = wptr<float>(work, g->off_y1);
   float* y2 = wptr<float>(work, g->off_y2);
+  float* x0 = wptr<float>(work, g->off_x0);
   float *ybx = wptr<float>(work, g->off_ybx), *tx = wptr<float>(work, g->off_tx);
   float *ybx2 = wptr<float>(work, g->off_ybx2), *tx2 = wptr<float>(work, g->off_tx2);
   float *yby = wptr<float>(work, g->off_yby), *ty = wptr<float>(work, g->off_ty);
@@ -851,15 +854,17 @@ static void step_f32r(ChGroup* g, int G, double* cur, double* prev, void* work, 
   // x: FP32 solve of the high part, double-float residual, FP32 correction solve
   { PROF(kLocX); launch_local<float, float>(fhi, y1, nsx, nsx, X, ybx, 0, 0, 1, status, st); }
   { PROF(kRedX); spike_reduced_kernel<float><<<dim3(gx.x, 4 * X.P), kSolveThreads, 0, st>>>(ybx, X, tx, nsx, 0); }
-  { PROF(kRefX); launch_spike_refine_ff(fhi, flo, y1, tx, y2, ybx2, nsx, nsx, nx, X, g->X.d_aff, 1, 0, 0, status, st); }
+  { PROF(kRefX); launch_resid_ff(fhi, flo, y1, tx, x0, y2, nsx, nsx, nx, X, g->X.d_aff, 1, 0, 0, st); }
+  { PROF(kLoc2X); launch_local<float, float>(y2, y2, nsx, nsx, X, ybx2, 0, 0, 1, status, st); }
   { PROF(kRed2X); spike_reduced_kernel<float><<<dim3(gx.x, 4 * X.P), kSolveThreads, 0, st>>>(ybx2, X, tx2, nsx, 0); }
-  { PROF(kFinX); launch_ch_xfinish_ff(y1, tx, y2, tx2, X, whi, wlo, nx, ny, G, st); }
+  { PROF(kFinX); launch_ch_xfinish_ff(x0, tx, y2, tx2, X, whi, wlo, nx, ny, G, st); }
   // y
   { PROF(kLocY); launch_local<float, float>(whi, y1, nx, nx, Y, yby, N, kyz, G, status, st); }
   { PROF(kRedY); spike_reduced_kernel<float><<<dim3(gy.x, 4 * Y.P, G), kSolveThreads, 0, st>>>(yby, Y, ty, nx, kyz); }
-  { PROF(kRefY); launch_spike_refine_ff(whi, wlo, y1, ty, y2, yby2, nx, nx, ny, Y, g->Y.d_aff, G, N, kyz, status, st); }
+  { PROF(kRefY); launch_resid_ff(whi, wlo, y1, ty, x0, y2, nx, nx, ny, Y, g->Y.d_aff, G, N, kyz, st); }
+  { PROF(kLoc2Y); launch_local<float, float>(y2, y2, nx, nx, Y, yby2, N, kyz, G, status, st); }
   { PROF(kRed2Y); spike_reduced_kernel<float><<<dim3(gy.x, 4 * Y.P, G), kSolveThreads, 0, st>>>(yby2, Y, ty2, nx, kyz); }
-  { PROF(kUpd); launch_ch_update_ff(y1, ty, y2, ty2, Y, cur, prev, nx, ny, G, keep_roles, st); }
+  { PROF(kUpd); launch_ch_update_ff(x0, ty, y2, ty2, Y, cur, prev, nx, ny, G, keep_roles, st); }
 }
 
 void group_step(ChGroup* g, int gact, double* cur, double* prev, void* work, int keep_roles, cudaStream_t st,

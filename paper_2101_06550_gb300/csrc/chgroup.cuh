@@ -41,7 +41,7 @@ struct DirView {
 };
 
 // Per-kernel CUDA-event timing (ch_profile).
-enum ProfSlot { kRhs, kLocX, kRedX, kRefX, kRed2X, kFinX, kLocY, kRedY, kRefY, kRed2Y, kUpd, kSlots };
+enum ProfSlot { kRhs, kLocX, kRedX, kRefX, kLoc2X, kRed2X, kFinX, kLocY, kRedY, kRefY, kLoc2Y, kRed2Y, kUpd, kSlots };
 extern const char* const kSlotName[kSlots];
 
 struct Prof {
@@ -74,7 +74,7 @@ struct ChGroup {
   float2* d_glff = nullptr;
   SpikeDir X, Y;
   // work layout (byte offsets), for G fields
-  size_t off_f = 0, off_flo = 0, off_w = 0, off_wlo = 0, off_y1 = 0, off_y2 = 0;
+  size_t off_f = 0, off_flo = 0, off_w = 0, off_wlo = 0, off_y1 = 0, off_y2 = 0, off_x0 = 0;
   size_t off_ybx = 0, off_tx = 0, off_ybx2 = 0, off_tx2 = 0, off_yby = 0, off_ty = 0, off_yby2 = 0, off_ty2 = 0;
   size_t work_bytes = 0;
 };

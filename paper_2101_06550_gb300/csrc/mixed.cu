@@ -132,122 +132,59 @@ __device__ __forceinline__ ff adi_apply_ff(float w0, float w1, float w2, float w
   return ff_add_f(ff_mul(a, d), w2);
 }
 
-// Refinement sweep: rho = f - A x0 in double-float, then the segment-local FP32
-// LU sweeps on rho into y2 and its boundary values.  The reduced-system values
-// of the thread's own segment are loaded once; only the two halo rows on each
-// side need the neighbouring segments' values.  Loads run U rows ahead.
-template <int U>
-__global__ void __launch_bounds__(kSolveThreads) spike_refine_ff_kernel(
+// Refinement residual on tiles of 32 rows x 32 systems: the first FP32
+// solution x0 = y1 - spike correction is formed once per element of the tile
+// and its 2-row halo and staged in shared memory; then rho = f - A x0 in
+// double-float for the tile's points.  Writes rho's high part (the right-hand
+// side of the FP32 correction solve) and x0.  Element (row i, system j) at
+// [i*ld + j] (+ blockIdx.z * fz); grid (systems / 32, n / 32, Z), block 32 x 8.
+__global__ void __launch_bounds__(kT* kBY) ch_resid_ff_kernel(
     const float* __restrict__ fhi, const float* __restrict__ flo, const float* __restrict__ y1,
-    const float* __restrict__ t1, float* __restrict__ y2, float* __restrict__ yb, int ld, int nsys, int n,
+    const float* __restrict__ t1, float* __restrict__ x0out, float* __restrict__ rho, int ld, int nsys, int n,
     DirView<float> D, const float2* __restrict__ aff, size_t fz, size_t ybz) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= nsys) return;
-  const int s = blockIdx.y, m = D.m, P = D.P;
-  const int slot = blockIdx.z + j / D.spp;
-  const float2 a2 = aff[slot];
-  const float* lu = D.lu + (size_t)slot * 4 * m;
-  const float* vw = D.vw + (size_t)slot * 4 * m;
-  fhi += blockIdx.z * fz;
-  flo += blockIdx.z * fz;
-  y1 += blockIdx.z * fz;
-  y2 += blockIdx.z * fz;
+  __shared__ float sx[kT + 4][kT + 1];
+  const int m = D.m, P = D.P;
+  const int j = blockIdx.x * kT + threadIdx.x;
+  const int i0 = blockIdx.y * kT;
+  const size_t off = blockIdx.z * fz;
+  fhi += off;
+  flo += off;
+  y1 += off;
+  x0out += off;
+  rho += off;
   t1 += blockIdx.z * ybz;
-  yb += blockIdx.z * ybz;
-  const int base = s * m;
-  const size_t L = (size_t)ld, S = (size_t)nsys;
-  const ff a = ffc(a2);
-  const float a32 = a2.x;
-  const float *ra = lu, *be = lu + m, *ga = lu + 2 * m, *de = lu + 3 * m;
-  const float *V0 = vw, *V1 = vw + m, *W0 = vw + 2 * m, *W1 = vw + 3 * m;
-  const int sn = s + 1 == P ? 0 : s + 1, sp = s == 0 ? P - 1 : s - 1;
-  const float T0 = t1[(size_t)(4 * sn) * S + j], T1 = t1[(size_t)(4 * sn + 1) * S + j];
-  const float B0 = t1[(size_t)(4 * sp + 2) * S + j], B1 = t1[(size_t)(4 * sp + 3) * S + j];
-  auto corr = [&](int r) {
-    float c = __ldg(&V0[r]) * T0;
-    c = fmaf(__ldg(&V1[r]), T1, c);
-    c = fmaf(__ldg(&W0[r]), B0, c);
-    return fmaf(__ldg(&W1[r]), B1, c);
-  };
-  const float* py = y1 + (size_t)base * L + j;
-  const float* pfh = fhi + (size_t)base * L + j;
-  const float* pfl = flo + (size_t)base * L + j;
-  float* p2 = y2 + (size_t)base * L + j;
-  float w0 = x0_at(y1, t1, vw, n, m, P, ld, nsys, base - 2, j);
-  float w1 = x0_at(y1, t1, vw, n, m, P, ld, nsys, base - 1, j);
-  float w2 = py[0] - corr(0);
-  float w3 = py[L] - corr(1);
-  float w4;
-  // chunk buffers: f rows r0..r0+U-1 and y1 rows r0+2..r0+U+1
-  float qy[U], qh[U], ql[U];
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    qy[u] = (u + 2 < m) ? py[(size_t)(u + 2) * L] : 0.f;
-    qh[u] = (u < m) ? pfh[(size_t)u * L] : 0.f;
-    ql[u] = (u < m) ? pfl[(size_t)u * L] : 0.f;
-  }
-  float g1 = 0.f, g2 = 0.f;
-  for (int r0 = 0; r0 < m; r0 += U) {
-    float ny_[U], nh[U], nl[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int r = r0 + U + u;
-      ny_[u] = (r + 2 < m) ? py[(size_t)(r + 2) * L] : 0.f;
-      nh[u] = (r < m) ? pfh[(size_t)r * L] : 0.f;
-      nl[u] = (r < m) ? pfl[(size_t)r * L] : 0.f;
+  const bool live = j < nsys;
+  const int slot = blockIdx.z + (live ? j : 0) / D.spp;
+  const float* vw = D.vw + (size_t)slot * 4 * m;
+  const size_t S = (size_t)nsys;
+  for (int ly = threadIdx.y; ly < kT + 4; ly += kBY) {
+    float v = 0.f;
+    if (live) {
+      int i = i0 - 2 + ly;
+      i = i < 0 ? i + n : (i >= n ? i - n : i);
+      const int s = i / m, r = i - s * m;
+      const int sn = s + 1 == P ? 0 : s + 1, sp = s == 0 ? P - 1 : s - 1;
+      float c = __ldg(&vw[r]) * t1[(size_t)(4 * sn) * S + j];
+      c = fmaf(__ldg(&vw[m + r]), t1[(size_t)(4 * sn + 1) * S + j], c);
+      c = fmaf(__ldg(&vw[2 * m + r]), t1[(size_t)(4 * sp + 2) * S + j], c);
+      c = fmaf(__ldg(&vw[3 * m + r]), t1[(size_t)(4 * sp + 3) * S + j], c);
+      v = y1[(size_t)i * ld + j] - c;
     }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int r = r0 + u;
-      if (r < m) {
-        w4 = (r + 2 < m) ? qy[u] - corr(r + 2) : x0_at(y1, t1, vw, n, m, P, ld, nsys, base + r + 2, j);
-        const ff ax = adi_apply_ff(w0, w1, w2, w3, w4, a);
-        const float res = ff_sub(ff{qh[u], ql[u]}, ax).hi;
-        float g = fmaf(-a32, g2, res);
-        g = fmaf(-__ldg(&be[r]), g1, g) * __ldg(&ra[r]);
-        p2[(size_t)r * L] = g;
-        g2 = g1;
-        g1 = g;
-        w0 = w1; w1 = w2; w2 = w3; w3 = w4;
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) { qy[u] = ny_[u]; qh[u] = nh[u]; ql[u] = nl[u]; }
+    sx[ly][threadIdx.x] = v;
   }
-  float x1 = 0.f, x2 = 0.f, ylast = 0.f, ylast2 = 0.f;
-  float buf[U];
+  __syncthreads();
+  if (!live) return;
+  const ff a = ffc(aff[slot]);
 #pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int r = m - 1 - u;
-    buf[u] = (r >= 0) ? p2[(size_t)r * L] : 0.f;
+  for (int k = 0; k < kT / kBY; ++k) {
+    const int ly = threadIdx.y + k * kBY, i = i0 + ly;
+    if (i >= n) break;
+    const float* col = &sx[ly][threadIdx.x];
+    const ff ax = adi_apply_ff(col[0], col[kT + 1], col[2 * (kT + 1)], col[3 * (kT + 1)], col[4 * (kT + 1)], a);
+    const size_t p = (size_t)i * ld + j;
+    rho[p] = ff_sub(ff{fhi[p], flo[p]}, ax).hi;
+    x0out[p] = col[2 * (kT + 1)];
   }
-  for (int r0 = m - 1; r0 >= 0; r0 -= U) {
-    float nxt[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int r = r0 - U - u;
-      nxt[u] = (r >= 0) ? p2[(size_t)r * L] : 0.f;
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int r = r0 - u;
-      if (r >= 0) {
-        float v = fmaf(-__ldg(&ga[r]), x1, buf[u]);
-        v = fmaf(-__ldg(&de[r]), x2, v);
-        p2[(size_t)r * L] = v;
-        if (r == m - 1) ylast = v;
-        if (r == m - 2) ylast2 = v;
-        x2 = x1;
-        x1 = v;
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) buf[u] = nxt[u];
-  }
-  yb[(size_t)(4 * s + 0) * S + j] = x1;
-  yb[(size_t)(4 * s + 1) * S + j] = x2;
-  yb[(size_t)(4 * s + 2) * S + j] = ylast2;
-  yb[(size_t)(4 * s + 3) * S + j] = ylast;
 }
 
 // x sweep result w = x0 + delta as an exact double-float pair, transposed back
@@ -270,7 +207,7 @@ __global__ void __launch_bounds__(kT* kBY) ch_xfinish_ff_kernel(const float* __r
     const int li = threadIdx.y + k * kBY, i = i0 + li;
     if (i < nx && j < ny) {
       const int s = i / m, r = i - s * m;
-      const float x0 = y1[(size_t)i * ld + sys] - corr32(vw, t1, m, P, G * ny, s, r, sys);
+      const float x0 = y1[(size_t)i * ld + sys];  // corrected first solution
       const float dl = y2[(size_t)i * ld + sys] - corr32(vw, t2, m, P, G * ny, s, r, sys);
       s_t[li][threadIdx.x] = two_sum(x0, dl);
     }
@@ -305,7 +242,7 @@ __global__ void __launch_bounds__(kSolveThreads) ch_update_ff_kernel(const float
   const size_t p = (size_t)z * nx * ny + (size_t)j * nx + i;
   t1 += (size_t)z * 4 * P * nx;
   t2 += (size_t)z * 4 * P * nx;
-  const float x0 = y1[p] - corr32(vw, t1, m, P, nx, s, r, i);
+  const float x0 = y1[p];  // corrected first solution
   const float dl = y2[p] - corr32(vw, t2, m, P, nx, s, r, i);
   const ff v = two_sum(x0, dl);
   const double a = cn[p], b = cp[p];
@@ -522,12 +459,11 @@ void launch_ch_rhs_ff(const double* cn, const double* cp, float* rhi, float* rlo
     ch_rhs_ff_kernel<false><<<grid, block, 0, st>>>(cn, cp, rhi, rlo, nx, ny, G, k.rho, k.kap, glff, k.k1, k.k2);
 }
 
-void launch_spike_refine_ff(const float* fhi, const float* flo, const float* y1, const float* t1, float* y2, float* yb,
-                            int ld, int nsys, int n, const DirView<float>& D, const float2* aff, int Z, size_t fz,
-                            size_t ybz, int* status, cudaStream_t st) {
-  (void)status;
-  spike_refine_ff_kernel<16><<<dim3(ceil_div(nsys, kSolveThreads), D.P, Z), kSolveThreads, 0, st>>>(
-      fhi, flo, y1, t1, y2, yb, ld, nsys, n, D, aff, fz, ybz);
+void launch_resid_ff(const float* fhi, const float* flo, const float* y1, const float* t1, float* x0, float* rho,
+                     int ld, int nsys, int n, const DirView<float>& D, const float2* aff, int Z, size_t fz, size_t ybz,
+                     cudaStream_t st) {
+  ch_resid_ff_kernel<<<dim3(ceil_div(nsys, kT), ceil_div(n, kT), Z), dim3(kT, kBY), 0, st>>>(fhi, flo, y1, t1, x0, rho,
+                                                                                           ld, nsys, n, D, aff, fz, ybz);
 }
 
 void launch_ch_xfinish_ff(const float* y1, const float* t1, const float* y2, const float* t2, const DirView<float>& D,

@@ -25,9 +25,10 @@ struct DirView;
 // glff[z] = gamma_z / dx^2 and aff[z] = a_z as double-float pairs, per slot.
 void launch_ch_rhs_ff(const double* cn, const double* cp, float* rhi, float* rlo, int nx, int ny, int G,
                       const FFConst& k, const float2* glff, cudaStream_t st);
-void launch_spike_refine_ff(const float* fhi, const float* flo, const float* y1, const float* t1, float* y2, float* yb,
-                            int ld, int nsys, int n, const DirView<float>& D, const float2* aff, int Z, size_t fz,
-                            size_t ybz, int* status, cudaStream_t st);
+void launch_resid_ff(const float* fhi, const float* flo, const float* y1, const float* t1, float* x0, float* rho,
+                     int ld, int nsys, int n, const DirView<float>& D, const float2* aff, int Z, size_t fz, size_t ybz,
+                     cudaStream_t st);
+// xfinish / update: y1 is the corrected first solution x0, (y2, t2) the correction solve.
 void launch_ch_xfinish_ff(const float* y1, const float* t1, const float* y2, const float* t2, const DirView<float>& D,
                           float* whi, float* wlo, int nx, int ny, int G, cudaStream_t st);
 void launch_ch_update_ff(const float* y1, const float* t1, const float* y2, const float* t2, const DirView<float>& D,
