@@ -34,6 +34,10 @@ LX = 2 * np.pi
 GAMMA, DT = 0.005, 5e-4
 SEED = 3
 WORKLOAD = "ch2d_periodic_2048sq_gamma0.005_dt5e-4"
+# DRAM bytes (read + write) per launch of the FP64 right-hand-side kernel on this
+# workload, from an ncu capture of the current kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum, mean of 3 launches; the written field partly stays in L2)
+RHS_TRAFFIC_BYTES = 67.22e6 + 4.67e6
 
 
 def _peaks():
@@ -260,7 +264,8 @@ def run_chx(args, rank, world, local_rank):
     if dom in dp_ops:
         ach = dp_ops[dom] * pts / (per_launch_ms * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp64_peak_gops, "unit": "G fp64-op/s",
-                "frac": ach / fp64_peak_gops, "traffic": None, "ms_per_launch": per_launch_ms,
+                "frac": ach / fp64_peak_gops, "traffic": RHS_TRAFFIC_BYTES if dom == "ch_rhs" else None,
+                "traffic_unit": "bytes per launch", "algorithmic_bytes": 24 * pts, "ms_per_launch": per_launch_ms,
                 "peak_source": "measured DFMA microbenchmark 1.90/clk/SM x 152 SMs x 2070 MHz"}
     else:
         roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": fp64_peak_gops, "unit": "G fp64-op/s",

@@ -47,6 +47,10 @@ struct chx_ch_plan {
   ChGroup g;
   double* d_partials;
   Prof* prof;
+  // two captured steps for multi-step calls, valid for these pointers
+  cudaGraphExec_t pair;
+  const void *pair_now, *pair_prev, *pair_work;
+  cudaStream_t cap;
 };
 
 namespace {
@@ -688,8 +692,23 @@ static int group_move_params_gl(ChGroup* g, int from, int to) {
   return rc;
 }
 
+// One-time opt-in of the staged kernels to large dynamic shared memory (kept out
+// of launch paths, which may be inside a stream capture).
+static int prepare_kernels() {
+  static bool done[64] = {false};  // per device
+  int dev = 0;
+  int rc = cuda_check(cudaGetDevice(&dev), "ch: cudaGetDevice");
+  if (rc || dev < 0 || dev >= 64 || done[dev]) return rc;
+  rc = cuda_check(cudaFuncSetAttribute(spike_local_staged_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024),
+                  "ch: shared-memory opt-in");
+  if (!rc) done[dev] = true;
+  return rc;
+}
+
 int group_init(ChGroup* g, int nx, int ny, double lx, double ly, double gamma, double dt, int precision, int G,
                int px, int py) {
+  if (int rc0 = prepare_kernels()) return rc0;
   if (nx < 8 || ny < 8 || nx > 16384 || ny > 16384)
     return fail(CHX_EINVAL, "ch: nx %d, ny %d outside [8, 16384]", nx, ny);
   if (!(lx > 0) || !(ly > 0) || !(dt > 0) || !(gamma >= 0) || !isfinite(lx) || !isfinite(ly) || !isfinite(dt) ||
@@ -796,11 +815,6 @@ static void launch_local(const TIn* f, TC* y, int ld, int nsys, const DirView<TC
                        ((size_t)ld * sizeof(TC)) % 16 == 0 &&
                        (fz * sizeof(TC)) % 16 == 0 && ((uintptr_t)f & 15) == 0 && tile <= 200 * 1024;
   if (aligned) {
-    static bool attr_set = false;  // one opt-in per instantiation
-    if (!attr_set) {
-      cudaFuncSetAttribute(spike_local_staged_kernel<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr_set = true;
-    }
     spike_local_staged_kernel<TC><<<dim3(nsys / 32, D.P, Z), 32, tile, st>>>((const TC*)f, y, ld, nsys, D, yb, fz, ybz,
                                                                            status);
   } else {
@@ -875,6 +889,8 @@ void group_step(ChGroup* g, int gact, double* cur, double* prev, void* work, int
 
 void ch_plan_free(chx_ch_plan* p) {
   if (!p) return;
+  if (p->pair) cudaGraphExecDestroy(p->pair);
+  if (p->cap) cudaStreamDestroy(p->cap);
   group_free(&p->g);
   if (p->d_partials) cudaFree(p->d_partials);
   if (p->prof) {
@@ -929,6 +945,37 @@ extern "C" int ch_step(chx_ch_plan* p, double* c_now, double* c_prev, void* work
     return fail(CHX_EINVAL, "ch_step: c_now, c_prev and work must not overlap");
   cudaStream_t st = (cudaStream_t)stream;
   double *cur = c_now, *prev = c_prev;
+  if (nsteps >= 4 && !p->prof->on) {
+    // Pairs of steps from a CUDA graph: a pair starts and ends with C^n in c_now.
+    int rc = CHX_OK;
+    if (!p->pair || p->pair_now != c_now || p->pair_prev != c_prev || p->pair_work != work) {
+      if (p->pair) cudaGraphExecDestroy(p->pair);
+      p->pair = nullptr;
+      if (!p->cap) rc = cuda_check(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking), "ch_step: stream");
+      cudaGraph_t graph = nullptr;
+      if (!rc) rc = cuda_check(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal), "ch_step: capture");
+      if (!rc) {
+        group_step(&p->g, 1, c_now, c_prev, work, 0, p->cap, nullptr, p->hdr.d_status);
+        group_step(&p->g, 1, c_prev, c_now, work, 0, p->cap, nullptr, p->hdr.d_status);
+        rc = cuda_check(cudaStreamEndCapture(p->cap, &graph), "ch_step: end capture");
+      }
+      if (!rc) rc = cuda_check(cudaGraphInstantiate(&p->pair, graph, 0), "ch_step: instantiate");
+      if (graph) cudaGraphDestroy(graph);
+      if (rc) {
+        p->pair = nullptr;
+        return rc;
+      }
+      p->pair_now = c_now;
+      p->pair_prev = c_prev;
+      p->pair_work = work;
+    }
+    const int pairs = nsteps / 2;
+    for (int k = 0; k < pairs && !rc; ++k) rc = cuda_check(cudaGraphLaunch(p->pair, st), "ch_step: graph launch");
+    if (rc) return rc;
+    if (nsteps & 1) group_step(&p->g, 1, c_now, c_prev, work, 1, st, p->prof, p->hdr.d_status);
+    p->hdr.last_stream = st;
+    return launch_check("ch_step");
+  }
   for (int s = 0; s < nsteps; ++s) {
     const int last = s == nsteps - 1;
     const int keep = last && cur == c_now;

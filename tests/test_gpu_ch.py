@@ -237,3 +237,25 @@ def test_ch_step_rejects_overlap_and_alignment():
         plan.step(cn, cn, work, 1)
     with pytest.raises(chx.ChxError):
         plan.step(cn, torch.zeros_like(cn), work[8:], 1)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ch_step_graph_pairs_match_single_steps(precision):
+    # nsteps >= 4 replays a captured two-step graph; it must give the same bits
+    # as single-step calls, for even and odd counts and after a pointer change
+    chx = _chx()
+    n = 96
+    c0 = synth.field(12, n, n, -0.1, 0.1)
+    plan = chx.ChPlan(n, n, 2 * np.pi, 2 * np.pi, 0.01, 1e-3, precision)
+    work = plan.alloc_work(DEV)
+    for nsteps in (4, 5, 9):
+        a = torch.from_numpy(c0).to(DEV)
+        b = a.clone()
+        plan.step(a, b, work, nsteps)
+        c = torch.from_numpy(c0).to(DEV)
+        d = c.clone()
+        for _ in range(nsteps):
+            plan.step(c, d, work, 1)
+        torch.cuda.synchronize()
+        assert torch.equal(a, c) and torch.equal(b, d), nsteps
+    plan.sync_status()
