@@ -43,9 +43,10 @@ def lib():
         L.oracle_ch_step.argtypes = [i, i, d, d, d, d, _D, _D]
         L.oracle_ch_run.argtypes = [i, i, d, d, d, d, i, _D, _D]
         L.oracle_ch_diagnostics.argtypes = [i, i, d, d, d, _D, _D, _D]
+        L.oracle_ch1d_run.argtypes = [i, i, d, d, d, i, _D]
         for fn in ("oracle_penta_cyclic_solve", "oracle_penta_cyclic_batch", "oracle_tri_cyclic_solve",
                    "oracle_tri_cyclic_batch", "oracle_stencil_apply_2d", "oracle_ch_step",
-                   "oracle_ch_run", "oracle_ch_diagnostics"):
+                   "oracle_ch_run", "oracle_ch_diagnostics", "oracle_ch1d_run"):
             getattr(L, fn).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -135,3 +136,11 @@ def ch_diagnostics(c, lx, ly, gamma):
     _check(lib().oracle_ch_diagnostics(nx, ny, float(lx), float(ly), float(gamma), _p(c),
                                        ctypes.byref(m), ctypes.byref(e)))
     return m.value, e.value
+
+
+def ch1d_run(c, l, gamma, dt, nsteps=1, batch=1):
+    """Batched 1D Cahn-Hilliard steps (Sec. 6.2.2) on an interleaved (n * batch) array; returns a new array."""
+    c = _f64(c).ravel().copy()
+    n = c.size // batch
+    _check(lib().oracle_ch1d_run(n, batch, float(l), float(gamma), float(dt), int(nsteps), _p(c)))
+    return c

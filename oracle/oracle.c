@@ -414,3 +414,45 @@ int oracle_ch_diagnostics(int nx, int ny, double lx, double ly, double gamma, co
   *energy = e * dx * dy;
   return ORC_OK;
 }
+
+/* ---------------------------------------------------------------------------
+ * Batched 1D Cahn-Hilliard step (Sec. 6.2.2, eq6:1Dnumerical): on [0, l) with
+ * dx = l/n, for every system s of the interleaved batch c[i*batch + s],
+ *   (I + sigma delta^4) C^{n+1} = C^n + alpha delta^2 (C^3 - C)^n,
+ *   sigma = gamma dt / dx^4, alpha = dt / dx^2, periodic in i.
+ * Reading: the printed right-hand side f_i omits C_i^n; eq6:1Dnumerical has it.
+ * ------------------------------------------------------------------------- */
+int oracle_ch1d_step(int n, int batch, double l, double gamma, double dt, double* c) {
+  if (n < 5 || batch < 1 || !(l > 0) || !(dt > 0) || !(gamma >= 0)) return ORC_EINVAL;
+  double dx = l / n, sigma = gamma * dt / (dx * dx * dx * dx), alpha = dt / (dx * dx);
+  double *f = malloc(n * sizeof(double)), *x = malloc(n * sizeof(double)), *nl = malloc(n * sizeof(double));
+  double *co = malloc(5 * n * sizeof(double));
+  int rc = ORC_OK;
+  if (!f || !x || !nl || !co) { rc = ORC_ENOMEM; goto done1; }
+  for (int i = 0; i < n; ++i) {
+    co[i] = sigma; co[n + i] = -4.0 * sigma; co[2 * n + i] = 1.0 + 6.0 * sigma;
+    co[3 * n + i] = -4.0 * sigma; co[4 * n + i] = sigma;
+  }
+  for (int s = 0; s < batch; ++s) {
+    for (int i = 0; i < n; ++i) {
+      double v = c[(long)i * batch + s];
+      nl[i] = v * v * v - v;
+    }
+    for (int i = 0; i < n; ++i)
+      f[i] = c[(long)i * batch + s] + alpha * (nl[wrap(i - 1, n)] - 2.0 * nl[i] + nl[wrap(i + 1, n)]);
+    rc = oracle_penta_cyclic_solve(n, co, co + n, co + 2 * n, co + 3 * n, co + 4 * n, 1, f, 1, x, 1);
+    if (rc) goto done1;
+    for (int i = 0; i < n; ++i) c[(long)i * batch + s] = x[i];
+  }
+done1:
+  free(f); free(x); free(nl); free(co);
+  return rc;
+}
+
+int oracle_ch1d_run(int n, int batch, double l, double gamma, double dt, int nsteps, double* c) {
+  for (int k = 0; k < nsteps; ++k) {
+    int rc = oracle_ch1d_step(n, batch, l, gamma, dt, c);
+    if (rc) return rc;
+  }
+  return ORC_OK;
+}

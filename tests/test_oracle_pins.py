@@ -318,3 +318,43 @@ def test_synth_torch_matches_numpy():
     a = synth.uniform(123, 1000, -1, 1, offset=17)
     b = synth.uniform_torch(123, 1000, -1, 1, device="cpu", offset=17).numpy()
     assert np.array_equal(a, b)
+
+
+# --------------------------------------------------------------------------- 1D Cahn-Hilliard (Sec. 6.2.2)
+def test_ch1d_linear_mode_closed_form():
+    # small single mode: N(c) ~ -c, so each step multiplies the mode by
+    # G = (1 + dt p) / (1 + gamma dt p^2), p = 4 sin^2(k dx / 2) / dx^2
+    n, l, gamma, dt, eps, k = 64, 2 * np.pi, 0.01, 1e-3, 1e-8, 5
+    x = np.arange(n) * l / n
+    batch = 3
+    c = np.repeat((eps * np.cos(k * x))[:, None], batch, axis=1).ravel()
+    dx = l / n
+    p = 4 * np.sin(k * dx / 2) ** 2 / dx**2
+    G = (1 + dt * p) / (1 + gamma * dt * p**2)
+    got = oracle.ch1d_run(c, l, gamma, dt, 20, batch).reshape(n, batch)
+    ref = eps * G**20 * np.cos(k * x)
+    for s in range(batch):
+        assert np.max(np.abs(got[:, s] - ref)) <= 1e-11 * eps * G**20
+
+
+def test_ch1d_spatial_order_two_against_continuum():
+    # linear regime, tiny dt: error against eps e^{sigma t} cos(kx), sigma = k^2 - gamma k^4,
+    # falls as N^-2 (the O(dx^2) differencing of the scheme)
+    l, gamma, eps, k, T, dt = 2 * np.pi, 0.01, 1e-8, 3, 0.02, 1e-5
+    sig = k**2 - gamma * k**4
+    errs = []
+    for n in (32, 64, 128):
+        x = np.arange(n) * l / n
+        got = oracle.ch1d_run(eps * np.cos(k * x), l, gamma, dt, int(round(T / dt)))
+        errs.append(np.max(np.abs(got - eps * np.exp(sig * T) * np.cos(k * x))) / eps)
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(orders - 2.0) < 0.1), orders
+
+
+def test_ch1d_mass_conservation():
+    n, batch = 48, 4
+    c = synth.uniform(3, n * batch, -0.1, 0.1) + 0.02
+    got = oracle.ch1d_run(c, 2 * np.pi, 0.01, 2e-3, 100, batch)
+    m0 = c.reshape(n, batch).sum(0)
+    m1 = got.reshape(n, batch).sum(0)
+    assert np.max(np.abs(m1 - m0)) <= 1e-13 * np.abs(c).reshape(n, batch).sum(0).max()
