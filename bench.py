@@ -276,6 +276,8 @@ def run_chx(args, rank, world, local_rank):
         torch.cuda.empty_cache()
         extras["solvers"] = bench_solvers(dev)
         torch.cuda.empty_cache()
+        extras["ch1d"] = bench_ch1d(dev)
+        torch.cuda.empty_cache()
         extras["ensemble"] = bench_ensemble(dev, chx.PREC_F32_REFINE, args.ens_steps, 3)
         torch.cuda.empty_cache()
         extras["serving"] = bench_serving(dev, args.serve_requests, args.serve_rate, chx.PREC_F32_REFINE)
@@ -363,6 +365,30 @@ def bench_solvers(dev, reps=5):
                               "hbm_gbs_algorithmic": 16 * unknowns / (ms * 1e-3) / 1e9}
     tp.close()
     return out
+
+
+def bench_ch1d(dev, steps=20):
+    """Batched 1D Cahn-Hilliard (Sec. 6.2.4): 2^20 simulations of N = 256, dt = 0.1 dx, FP64."""
+    import torch
+
+    import paper_2101_06550_gb300 as chx
+
+    n, batch, l, gamma = 256, 1 << 20, 2 * np.pi, 0.01
+    dt = 0.1 * l / n
+    c = synth.uniform_torch(5, n * batch, -0.1, 0.1, device=dev)
+    plan = chx.Ch1DPlan(n, batch, l, gamma, dt)
+    plan.step(c, 3)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    plan.step(c, steps)  # 2 GiB of state per step: larger than L2
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    plan.sync_status()
+    pts = n * batch
+    return {"sims": batch, "n": n, "ms_per_step": ms, "value": pts / (ms * 1e-3), "unit": "grid-pt-steps/s",
+            "fp64_gops": 14 * pts / (ms * 1e-3) / 1e9, "hbm_gbs_algorithmic": 16 * pts / (ms * 1e-3) / 1e9}
 
 
 def ensemble_sims(count=512, seed=11):

@@ -59,6 +59,7 @@ typedef struct chx_penta_plan chx_penta_plan;
 typedef struct chx_tri_plan chx_tri_plan;
 typedef struct chx_ch_plan chx_ch_plan;
 typedef struct chx_ens chx_ens;
+typedef struct chx_ch1d_plan chx_ch1d_plan;
 
 const char* chx_status_string(int status);
 /* Detail of the last failure on this host thread ("" if none). */
@@ -170,6 +171,22 @@ int ch_plan_create(chx_ch_plan** plan, int nx, int ny, double lx, double ly, dou
 size_t ch_work_bytes(const chx_ch_plan* plan);
 int ch_step(chx_ch_plan* plan, double* c_now, double* c_prev, void* work, int nsteps, void* stream);
 int ch_diagnostics(chx_ch_plan* plan, const double* c, double* mass_out, double* energy_out, void* stream);
+
+/*
+ * Batched 1D Cahn-Hilliard (Sec. 6.2.2, eq6:1Dnumerical): for every simulation s
+ * of an interleaved batch c[i * batch + s] (i = 0..n-1, periodic on [0, l)),
+ *   (I + sigma delta^4) C^{n+1} = C^n + alpha delta^2 (C^3 - C)^n,
+ *   sigma = gamma dt / dx^4, alpha = dt / dx^2, dx = l / n
+ * (the printed f_i lacks C_i^n; eq6:1Dnumerical has it).  The cyclic
+ * pentadiagonal operator is factorised once on the host (FP64, Navon bordering
+ * + LU without pivoting) by ch1d_plan_create (n >= 8, batch >= 1, l, dt > 0,
+ * gamma >= 0; the plan owns about 9 n doubles of device memory).  ch1d_step
+ * advances nsteps >= 0 steps in place on the device array c (n * batch
+ * doubles, caller-owned, FP64); it needs no scratch.  Errors: CHX_EINVAL,
+ * CHX_ESINGULAR (factorisation), CHX_ENOMEM, CHX_ECUDA.
+ */
+int ch1d_plan_create(chx_ch1d_plan** plan, int n, int batch, double l, double gamma, double dt);
+int ch1d_step(chx_ch1d_plan* plan, double* c, int nsteps, void* stream);
 
 /*
  * Ensemble runtime: many simulations of uneven sizes advanced together (the

@@ -27,7 +27,7 @@ STATUS = {0: "CHX_OK", -1: "CHX_EINVAL", -2: "CHX_ESINGULAR", -3: "CHX_ENONFINIT
 EXPORTS = ("chx_status_string", "chx_last_error", "chx_version", "stencil_apply_2d", "penta_cyclic_factor",
            "penta_cyclic_refactor", "penta_cyclic_solve_batched", "tri_cyclic_factor", "tri_cyclic_refactor",
            "tri_cyclic_solve_batched", "ch_plan_create", "ch_work_bytes", "ch_step", "ch_diagnostics",
-           "ch_diagnostics_noalloc", "ch_profile", "ch_profile_read", "ch_profile_slot_name", "ens_create",
+           "ch_diagnostics_noalloc", "ch1d_plan_create", "ch1d_step", "ch_profile", "ch_profile_read", "ch_profile_slot_name", "ens_create",
            "ens_group_create", "ens_group_destroy", "ens_group_set_active", "ens_slot_load", "ens_slot_read",
            "ens_slot_move", "ens_step", "ens_group_step", "ens_autotune", "ens_info", "ens_bytes_used",
            "chx_sync_status", "chx_plan_destroy")
@@ -69,6 +69,8 @@ def lib():
         "ch_step": (i, [_P, _P, _P, _P, i, _P]),
         "ch_diagnostics": (i, [_P, _P, _P, _P, _P]),
         "ch_diagnostics_noalloc": (i, [_P, i, i, d, d, d, _P, _P, _P]),
+        "ch1d_plan_create": (i, [ctypes.POINTER(_P), i, i, d, d, d]),
+        "ch1d_step": (i, [_P, _P, i, _P]),
         "ch_profile": (i, [_P, i]),
         "ch_profile_read": (i, [_P, _D, ctypes.POINTER(ctypes.c_longlong), i, i]),
         "ch_profile_slot_name": (ctypes.c_char_p, [i]),
@@ -309,6 +311,22 @@ def _any_ptr(t, numel, name):
     if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != numel:
         raise ValueError(f"{name} must be a contiguous float64 tensor of {numel} elements")
     return ctypes.c_void_p(t.data_ptr())
+
+
+class Ch1DPlan(_Plan):
+    """Batched 1D Cahn-Hilliard (ch1d_plan_create / ch1d_step), interleaved c[i*batch + s]."""
+
+    def __init__(self, n, batch, l, gamma, dt):
+        h = ctypes.c_void_p()
+        _check(lib().ch1d_plan_create(ctypes.byref(h), n, batch, float(l), float(gamma), float(dt)))
+        self._handle, self.n, self.batch = h, n, batch
+
+    def step(self, c, nsteps=1, stream=None):
+        import torch
+
+        _check(lib().ch1d_step(self._handle, _dev(c, torch.float64, self.n * self.batch, "c"), int(nsteps),
+                               _stream(stream)))
+        return c
 
 
 class Ensemble(_Plan):

@@ -279,6 +279,7 @@ void penta_plan_free(chx_penta_plan* p);
 void tri_plan_free(chx_tri_plan* p);
 void ch_plan_free(chx_ch_plan* p);
 void ens_free(chx_ens* e);
+void ch1d_plan_free(chx_ch1d_plan* p);
 
 }  // namespace chx
 
@@ -305,7 +306,8 @@ extern "C" int chx_version(void) { return 10000; }
 extern "C" int chx_sync_status(void* plan) {
   if (!plan) return fail(CHX_EINVAL, "chx_sync_status: null plan");
   PlanHdr* h = (PlanHdr*)plan;
-  if (h->magic != kMagicPenta && h->magic != kMagicTri && h->magic != kMagicCh && h->magic != kMagicEns)
+  if (h->magic != kMagicPenta && h->magic != kMagicTri && h->magic != kMagicCh && h->magic != kMagicEns &&
+      h->magic != kMagicCh1d)
     return fail(CHX_EINVAL, "chx_sync_status: not a chx plan");
   int rc = cuda_check(cudaStreamSynchronize(h->last_stream), "chx_sync_status: stream synchronize");
   if (rc) return rc;
@@ -327,6 +329,7 @@ extern "C" void chx_plan_destroy(void* plan) {
     case kMagicTri: tri_plan_free((chx_tri_plan*)plan); break;
     case kMagicCh: ch_plan_free((chx_ch_plan*)plan); break;
     case kMagicEns: ens_free((chx_ens*)plan); break;
+    case kMagicCh1d: ch1d_plan_free((chx_ch1d_plan*)plan); break;
     default: break;
   }
 }

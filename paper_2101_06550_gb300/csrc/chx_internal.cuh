@@ -11,7 +11,8 @@ namespace chx {
 
 // Every plan starts with this header so chx_sync_status / chx_plan_destroy can
 // take any plan type.
-enum : uint32_t { kMagicPenta = 0x70656e74u, kMagicTri = 0x74726964u, kMagicCh = 0x63686164u, kMagicEns = 0x656e7362u };
+enum : uint32_t { kMagicPenta = 0x70656e74u, kMagicTri = 0x74726964u, kMagicCh = 0x63686164u, kMagicEns = 0x656e7362u,
+                  kMagicCh1d = 0x63683164u };
 
 struct PlanHdr {
   uint32_t magic;
