@@ -44,9 +44,11 @@ def lib():
         L.oracle_ch_run.argtypes = [i, i, d, d, d, d, i, _D, _D]
         L.oracle_ch_diagnostics.argtypes = [i, i, d, d, d, _D, _D, _D]
         L.oracle_ch1d_run.argtypes = [i, i, d, d, d, i, _D]
+        L.oracle_cn1d_run.argtypes = [i, i, i, d, d, d, i, _D]
         for fn in ("oracle_penta_cyclic_solve", "oracle_penta_cyclic_batch", "oracle_tri_cyclic_solve",
                    "oracle_tri_cyclic_batch", "oracle_stencil_apply_2d", "oracle_ch_step",
-                   "oracle_ch_run", "oracle_ch_diagnostics", "oracle_ch1d_run"):
+                   "oracle_ch_run", "oracle_ch_diagnostics", "oracle_ch1d_run",
+                   "oracle_cn1d_run"):
             getattr(L, fn).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -143,4 +145,12 @@ def ch1d_run(c, l, gamma, dt, nsteps=1, batch=1):
     c = _f64(c).ravel().copy()
     n = c.size // batch
     _check(lib().oracle_ch1d_run(n, batch, float(l), float(gamma), float(dt), int(nsteps), _p(c)))
+    return c
+
+
+def cn1d_run(order, c, l, kappa, dt, nsteps=1, batch=1):
+    """Crank-Nicolson hyperdiffusion (order 4) or diffusion (order 2) steps (Secs. 4.2.1, 5.3.2)."""
+    c = _f64(c).ravel().copy()
+    n = c.size // batch
+    _check(lib().oracle_cn1d_run(int(order), n, batch, float(l), float(kappa), float(dt), int(nsteps), _p(c)))
     return c

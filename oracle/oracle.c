@@ -456,3 +456,53 @@ int oracle_ch1d_run(int n, int batch, double l, double gamma, double dt, int nst
   }
   return ORC_OK;
 }
+
+/* ---------------------------------------------------------------------------
+ * Crank-Nicolson benchmark steps on a batch of periodic 1D problems,
+ * interleaved c[i*batch + s], dx = l/n:
+ *  order 4, hyperdiffusion C_t = -kappa C_xxxx (Sec. 4.2.1, eq:1d_hyper_scheme):
+ *    sigma = kappa dt / (2 dx^4),
+ *    (sigma, -4 sigma, 1 + 6 sigma, -4 sigma, sigma) C^{n+1}
+ *      = (-sigma, 4 sigma, 1 - 6 sigma, 4 sigma, -sigma) C^n;
+ *  order 2, diffusion C_t = kappa C_xx (Sec. 5.3.2, eq5:1ddiffscheme):
+ *    sigma = kappa dt / (2 dx^2),
+ *    (-sigma, 1 + 2 sigma, -sigma) C^{n+1} = (sigma, 1 - 2 sigma, sigma) C^n.
+ * ------------------------------------------------------------------------- */
+int oracle_cn1d_run(int order, int n, int batch, double l, double kappa, double dt, int nsteps, double* c) {
+  if ((order != 2 && order != 4) || n < 5 || batch < 1 || !(l > 0) || !(dt > 0) || !(kappa >= 0)) return ORC_EINVAL;
+  double dx = l / n;
+  double sigma = order == 4 ? kappa * dt / (2.0 * dx * dx * dx * dx) : kappa * dt / (2.0 * dx * dx);
+  double *f = malloc(n * sizeof(double)), *x = malloc(n * sizeof(double)), *co = malloc(5 * n * sizeof(double));
+  int rc = ORC_OK;
+  if (!f || !x || !co) { rc = ORC_ENOMEM; goto done2; }
+  for (int i = 0; i < n; ++i) {
+    if (order == 4) {
+      co[i] = sigma; co[n + i] = -4.0 * sigma; co[2 * n + i] = 1.0 + 6.0 * sigma;
+      co[3 * n + i] = -4.0 * sigma; co[4 * n + i] = sigma;
+    } else {
+      co[i] = -sigma; co[n + i] = 1.0 + 2.0 * sigma; co[2 * n + i] = -sigma;
+    }
+  }
+  for (int k = 0; k < nsteps; ++k) {
+    for (int s = 0; s < batch; ++s) {
+      for (int i = 0; i < n; ++i) {
+#define CC(j) c[(long)wrap((j), n) * batch + s]
+        if (order == 4)
+          f[i] = -sigma * CC(i - 2) + 4.0 * sigma * CC(i - 1) + (1.0 - 6.0 * sigma) * CC(i) + 4.0 * sigma * CC(i + 1) -
+                 sigma * CC(i + 2);
+        else
+          f[i] = sigma * CC(i - 1) + (1.0 - 2.0 * sigma) * CC(i) + sigma * CC(i + 1);
+#undef CC
+      }
+      if (order == 4)
+        rc = oracle_penta_cyclic_solve(n, co, co + n, co + 2 * n, co + 3 * n, co + 4 * n, 1, f, 1, x, 1);
+      else
+        rc = oracle_tri_cyclic_solve(n, co, co + n, co + 2 * n, 1, f, 1, x, 1);
+      if (rc) goto done2;
+      for (int i = 0; i < n; ++i) c[(long)i * batch + s] = x[i];
+    }
+  }
+done2:
+  free(f); free(x); free(co);
+  return rc;
+}

@@ -358,3 +358,56 @@ def test_ch1d_mass_conservation():
     m0 = c.reshape(n, batch).sum(0)
     m1 = got.reshape(n, batch).sum(0)
     assert np.max(np.abs(m1 - m0)) <= 1e-13 * np.abs(c).reshape(n, batch).sum(0).max()
+
+
+# --------------------------------------------------------------------------- CN benchmarks (Secs. 4.2, 5.3)
+def _golden(name):
+    import os
+
+    vals = {}
+    for ln in open(os.path.join(os.path.dirname(__file__), "golden", name)):
+        if ln.strip() and not ln.startswith("#"):
+            k, v = ln.split()
+            vals[k] = float(v)
+    return vals
+
+
+def test_cn_hyperdiffusion_exact_solution_slope():
+    # the paper's validation (Eq. exact, Eq. myerr): slope of the L2 error vs N
+    g = _golden("hyperdiffusion_slope.txt")
+    T, dt, wave = g["T"], g["dt"], int(g["wave"])
+    k = 2 * np.pi * wave
+    steps = int(round(T / dt))
+    errs, ns = [], [16, 32, 64]
+    for n in ns:
+        x = np.arange(n) / n
+        got = oracle.cn1d_run(4, np.cos(k * x), 1.0, 1.0, dt, steps)
+        exact = np.exp(-k**4 * T) * np.cos(k * x)
+        errs.append(np.sqrt(np.mean((got - exact) ** 2)))
+    slope = np.polyfit(np.log(ns), np.log(errs), 1)[0]
+    assert abs(slope - g["slope"]) < 0.05, slope
+
+
+def test_cn_diffusion_exact_solution_order_two():
+    k, T, dt = 2 * np.pi * 3, 1e-3, 1e-6
+    errs = []
+    for n in (32, 64, 128):
+        x = np.arange(n) / n
+        got = oracle.cn1d_run(2, np.cos(k * x), 1.0, 1.0, dt, int(round(T / dt)))
+        errs.append(np.max(np.abs(got - np.exp(-k**2 * T) * np.cos(k * x))))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(orders - 2.0) < 0.05), orders
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_cn_mode_amplification_closed_form(order):
+    # CN multiplies a Fourier mode by (1 - s)/(1 + s), s = sigma * symbol
+    n, l, kappa, dt, kk = 40, 1.0, 0.7, 2e-4, 3
+    x = np.arange(n) / n
+    dx = l / n
+    th = 2 * np.pi * kk / n
+    sym = (2 - 2 * np.cos(th)) ** (order // 2)
+    sig = kappa * dt / (2 * dx**order)
+    G = (1 - sig * sym) / (1 + sig * sym)
+    got = oracle.cn1d_run(order, np.cos(2 * np.pi * kk * x), l, kappa, dt, 10)
+    assert np.max(np.abs(got - G**10 * np.cos(2 * np.pi * kk * x))) <= 1e-12
