@@ -277,6 +277,7 @@ def run_chx(args, rank, world, local_rank):
         extras["solvers"] = bench_solvers(dev)
         torch.cuda.empty_cache()
         extras["ch1d"] = bench_ch1d(dev)
+        extras["cn1d"] = bench_cn1d(dev)
         torch.cuda.empty_cache()
         extras["ensemble"] = bench_ensemble(dev, chx.PREC_F32_REFINE, args.ens_steps, 3)
         torch.cuda.empty_cache()
@@ -389,6 +390,48 @@ def bench_ch1d(dev, steps=20):
     pts = n * batch
     return {"sims": batch, "n": n, "ms_per_step": ms, "value": pts / (ms * 1e-3), "unit": "grid-pt-steps/s",
             "fp64_gops": 14 * pts / (ms * 1e-3) / 1e9, "hbm_gbs_algorithmic": 16 * pts / (ms * 1e-3) / 1e9}
+
+
+def bench_cn1d(dev, steps=100, rewrite_steps=20):
+    """The paper's batched solver benchmarks (Sec. 4.3, Sec. 5.3): Crank-Nicolson
+    hyperdiffusion (pentadiagonal) and diffusion (tridiagonal) on 65536 identical-shape
+    systems of 1024 unknowns, L = kappa = 1, in the Constant (factor once) and Rewrite
+    (reset + refactorise every system every step) variants, FP64."""
+    import torch
+
+    import paper_2101_06550_gb300 as chx
+
+    n, batch = 1024, 1 << 16
+    # FP64 operations per unknown and step: explicit half + forward + backward sweep
+    ops = {4: 5 + 5 + 4, 2: 3 + 3 + 2}
+    out = {"n": n, "systems": batch, "unit": "unknown-steps/s"}
+    for order, name, dt in ((4, "hyperdiffusion_penta", 1e-8), (2, "diffusion_tri", 1e-5)):
+        x = np.arange(n) / n
+        c = torch.from_numpy(np.cos(4 * np.pi * x)).to(dev)[:, None].repeat(1, batch).reshape(-1).contiguous()
+        res = {"dt": dt}
+        for rewrite in (False, True):
+            plan = chx.CN1DPlan(order, n, batch, 1.0, 1.0, dt, rewrite)
+            k = rewrite_steps if rewrite else steps
+            plan.step(c, 3)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            plan.step(c, k)  # 512 MiB of state per step: larger than L2
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / k
+            plan.sync_status()
+            plan.close()
+            pts = n * batch
+            r = {"ms_per_step": ms, "value": pts / (ms * 1e-3)}
+            if not rewrite:
+                r["fp64_gops"] = ops[order] * pts / (ms * 1e-3) / 1e9
+            res["rewrite" if rewrite else "constant"] = r
+        res["rewrite_over_constant_time"] = res["rewrite"]["ms_per_step"] / res["constant"]["ms_per_step"]
+        out[name] = res
+        del c
+        torch.cuda.empty_cache()
+    return out
 
 
 def ensemble_sims(count=512, seed=11):

@@ -60,6 +60,7 @@ typedef struct chx_tri_plan chx_tri_plan;
 typedef struct chx_ch_plan chx_ch_plan;
 typedef struct chx_ens chx_ens;
 typedef struct chx_ch1d_plan chx_ch1d_plan;
+typedef struct chx_cn1d_plan chx_cn1d_plan;
 
 const char* chx_status_string(int status);
 /* Detail of the last failure on this host thread ("" if none). */
@@ -187,6 +188,37 @@ int ch_diagnostics(chx_ch_plan* plan, const double* c, double* mass_out, double*
  */
 int ch1d_plan_create(chx_ch1d_plan** plan, int n, int batch, double l, double gamma, double dt);
 int ch1d_step(chx_ch1d_plan* plan, double* c, int nsteps, void* stream);
+
+/*
+ * Batched Crank-Nicolson steps of the paper's two 1D periodic benchmark
+ * problems, for every system s of an interleaved batch c[i * batch + s]
+ * (i = 0..n-1, dx = l / n):
+ *  order 4, hyperdiffusion C_t = -kappa C_xxxx (Sec. 4.2.1, eq:1d_hyper_scheme;
+ *    kappa = gamma D), sigma = kappa dt / (2 dx^4):
+ *    (sigma, -4 sigma, 1 + 6 sigma, -4 sigma, sigma) C^{n+1}
+ *      = (-sigma, 4 sigma, 1 - 6 sigma, 4 sigma, -sigma) C^n;
+ *  order 2, diffusion C_t = kappa C_xx (Sec. 5.3.2, eq5:1ddiffscheme),
+ *    sigma = kappa dt / (2 dx^2):
+ *    (-sigma, 1 + 2 sigma, -sigma) C^{n+1} = (sigma, 1 - 2 sigma, sigma) C^n.
+ * The right-hand side is formed inside the forward sweep of the cyclic
+ * pentadiagonal (Navon bordering + LU) or tridiagonal (Thomas + Sherman-Morrison)
+ * solve.  cn1d_plan_create: order 2 or 4; n >= 6 (order 4) or >= 3 (order 2);
+ * batch >= 1; l, dt > 0; kappa >= 0.  rewrite selects the paper's benchmark
+ * variant (Sec. 4.3):
+ *   0 (Constant)  the matrix is factorised once on the host in FP64; the plan
+ *                 owns about 9 n doubles of device memory;
+ *   1 (Rewrite)   the plan owns (order + 1) * n * batch doubles of per-system
+ *                 matrix entries plus a PER_SYSTEM solver plan (about 9 n batch
+ *                 doubles of factors), and every step resets the entries and
+ *                 refactorises every system on the device before the sweep.
+ * cn1d_step advances nsteps >= 0 steps in place on the caller-owned device
+ * array c (n * batch doubles); it needs no scratch.  Errors: CHX_EINVAL,
+ * CHX_ESINGULAR (host factorisation; a Rewrite plan's device factorisation
+ * reports it through chx_sync_status), CHX_ENOMEM, CHX_ECUDA.
+ */
+int cn1d_plan_create(chx_cn1d_plan** plan, int order, int n, int batch, double l, double kappa, double dt,
+                     int rewrite);
+int cn1d_step(chx_cn1d_plan* plan, double* c, int nsteps, void* stream);
 
 /*
  * Ensemble runtime: many simulations of uneven sizes advanced together (the

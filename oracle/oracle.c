@@ -469,7 +469,7 @@ int oracle_ch1d_run(int n, int batch, double l, double gamma, double dt, int nst
  *    (-sigma, 1 + 2 sigma, -sigma) C^{n+1} = (sigma, 1 - 2 sigma, sigma) C^n.
  * ------------------------------------------------------------------------- */
 int oracle_cn1d_run(int order, int n, int batch, double l, double kappa, double dt, int nsteps, double* c) {
-  if ((order != 2 && order != 4) || n < 5 || batch < 1 || !(l > 0) || !(dt > 0) || !(kappa >= 0)) return ORC_EINVAL;
+  if ((order != 2 && order != 4) || n < (order == 4 ? 5 : 3) || batch < 1 || !(l > 0) || !(dt > 0) || !(kappa >= 0)) return ORC_EINVAL;
   double dx = l / n;
   double sigma = order == 4 ? kappa * dt / (2.0 * dx * dx * dx * dx) : kappa * dt / (2.0 * dx * dx);
   double *f = malloc(n * sizeof(double)), *x = malloc(n * sizeof(double)), *co = malloc(5 * n * sizeof(double));

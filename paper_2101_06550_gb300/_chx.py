@@ -27,7 +27,7 @@ STATUS = {0: "CHX_OK", -1: "CHX_EINVAL", -2: "CHX_ESINGULAR", -3: "CHX_ENONFINIT
 EXPORTS = ("chx_status_string", "chx_last_error", "chx_version", "stencil_apply_2d", "penta_cyclic_factor",
            "penta_cyclic_refactor", "penta_cyclic_solve_batched", "tri_cyclic_factor", "tri_cyclic_refactor",
            "tri_cyclic_solve_batched", "ch_plan_create", "ch_work_bytes", "ch_step", "ch_diagnostics",
-           "ch_diagnostics_noalloc", "ch1d_plan_create", "ch1d_step", "ch_profile", "ch_profile_read", "ch_profile_slot_name", "ens_create",
+           "ch_diagnostics_noalloc", "ch1d_plan_create", "ch1d_step", "cn1d_plan_create", "cn1d_step", "ch_profile", "ch_profile_read", "ch_profile_slot_name", "ens_create",
            "ens_group_create", "ens_group_destroy", "ens_group_set_active", "ens_slot_load", "ens_slot_read",
            "ens_slot_move", "ens_step", "ens_group_step", "ens_autotune", "ens_info", "ens_bytes_used",
            "chx_sync_status", "chx_plan_destroy")
@@ -71,6 +71,8 @@ def lib():
         "ch_diagnostics_noalloc": (i, [_P, i, i, d, d, d, _P, _P, _P]),
         "ch1d_plan_create": (i, [ctypes.POINTER(_P), i, i, d, d, d]),
         "ch1d_step": (i, [_P, _P, i, _P]),
+        "cn1d_plan_create": (i, [ctypes.POINTER(_P), i, i, i, d, d, d, i]),
+        "cn1d_step": (i, [_P, _P, i, _P]),
         "ch_profile": (i, [_P, i]),
         "ch_profile_read": (i, [_P, _D, ctypes.POINTER(ctypes.c_longlong), i, i]),
         "ch_profile_slot_name": (ctypes.c_char_p, [i]),
@@ -325,6 +327,25 @@ class Ch1DPlan(_Plan):
         import torch
 
         _check(lib().ch1d_step(self._handle, _dev(c, torch.float64, self.n * self.batch, "c"), int(nsteps),
+                               _stream(stream)))
+        return c
+
+
+class CN1DPlan(_Plan):
+    """Batched Crank-Nicolson hyperdiffusion (order 4) or diffusion (order 2) steps
+    (cn1d_plan_create / cn1d_step), interleaved c[i*batch + s]; rewrite=True resets
+    and refactorises every system's matrix each step."""
+
+    def __init__(self, order, n, batch, l, kappa, dt, rewrite=False):
+        h = ctypes.c_void_p()
+        _check(lib().cn1d_plan_create(ctypes.byref(h), int(order), n, batch, float(l), float(kappa), float(dt),
+                                      1 if rewrite else 0))
+        self._handle, self.order, self.n, self.batch, self.rewrite = h, order, n, batch, bool(rewrite)
+
+    def step(self, c, nsteps=1, stream=None):
+        import torch
+
+        _check(lib().cn1d_step(self._handle, _dev(c, torch.float64, self.n * self.batch, "c"), int(nsteps),
                                _stream(stream)))
         return c
 

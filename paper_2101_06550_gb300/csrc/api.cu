@@ -280,6 +280,8 @@ void tri_plan_free(chx_tri_plan* p);
 void ch_plan_free(chx_ch_plan* p);
 void ens_free(chx_ens* e);
 void ch1d_plan_free(chx_ch1d_plan* p);
+void cn1d_plan_free(chx_cn1d_plan* p);
+void* cn1d_inner_plan(chx_cn1d_plan* p);
 
 }  // namespace chx
 
@@ -307,8 +309,15 @@ extern "C" int chx_sync_status(void* plan) {
   if (!plan) return fail(CHX_EINVAL, "chx_sync_status: null plan");
   PlanHdr* h = (PlanHdr*)plan;
   if (h->magic != kMagicPenta && h->magic != kMagicTri && h->magic != kMagicCh && h->magic != kMagicEns &&
-      h->magic != kMagicCh1d)
+      h->magic != kMagicCh1d && h->magic != kMagicCn1d)
     return fail(CHX_EINVAL, "chx_sync_status: not a chx plan");
+  if (h->magic == kMagicCn1d) {  // a Rewrite plan's per-system factorisation flags its own solver plan
+    void* inner = cn1d_inner_plan((chx_cn1d_plan*)plan);
+    if (inner) {
+      int rc = chx_sync_status(inner);
+      if (rc) return rc;
+    }
+  }
   int rc = cuda_check(cudaStreamSynchronize(h->last_stream), "chx_sync_status: stream synchronize");
   if (rc) return rc;
   int st = 0;
@@ -330,6 +339,7 @@ extern "C" void chx_plan_destroy(void* plan) {
     case kMagicCh: ch_plan_free((chx_ch_plan*)plan); break;
     case kMagicEns: ens_free((chx_ens*)plan); break;
     case kMagicCh1d: ch1d_plan_free((chx_ch1d_plan*)plan); break;
+    case kMagicCn1d: cn1d_plan_free((chx_cn1d_plan*)plan); break;
     default: break;
   }
 }

@@ -12,7 +12,7 @@ namespace chx {
 // Every plan starts with this header so chx_sync_status / chx_plan_destroy can
 // take any plan type.
 enum : uint32_t { kMagicPenta = 0x70656e74u, kMagicTri = 0x74726964u, kMagicCh = 0x63686164u, kMagicEns = 0x656e7362u,
-                  kMagicCh1d = 0x63683164u };
+                  kMagicCh1d = 0x63683164u, kMagicCn1d = 0x636e3164u };
 
 struct PlanHdr {
   uint32_t magic;
@@ -59,6 +59,11 @@ struct TriFactors {
   double* arr = nullptr;  // 5 * n doubles: rden, a, chat, z, omega
 };
 int tri_factor_host(int n, const double* a, const double* b, const double* c, size_t cs, TriFactors* out);
+
+// Device factor storage of an FP64 plan (PER_SYSTEM: interleaved per system,
+// followed for the pentadiagonal plan by the 4 tail-inverse entries per system).
+const double* penta_plan_factors(const chx_penta_plan* p);
+const double* tri_plan_factors(const chx_tri_plan* p);
 
 // Plain non-cyclic pentadiagonal LU (paper factor steps) of the m x m Toeplitz
 // band (a, b, c, d, e); ralpha, beta, gam, del of length m.

@@ -245,6 +245,8 @@ int upload_factors(const PentaFactors& pf, void** dst) {
 }  // namespace
 
 namespace chx {
+const double* penta_plan_factors(const chx_penta_plan* p) { return (const double*)p->d_fac; }
+
 void penta_plan_free(chx_penta_plan* p) {
   if (!p) return;
   if (p->d_fac) cudaFree(p->d_fac);

@@ -148,6 +148,8 @@ __global__ void __launch_bounds__(kThreads) tri_factor_kernel(const double* __re
 }  // namespace
 
 namespace chx {
+const double* tri_plan_factors(const chx_tri_plan* p) { return (const double*)p->d_fac; }
+
 void tri_plan_free(chx_tri_plan* p) {
   if (!p) return;
   if (p->d_fac) cudaFree(p->d_fac);
