@@ -45,10 +45,18 @@ def lib():
         L.oracle_ch_diagnostics.argtypes = [i, i, d, d, d, _D, _D, _D]
         L.oracle_ch1d_run.argtypes = [i, i, d, d, d, i, _D]
         L.oracle_cn1d_run.argtypes = [i, i, i, d, d, d, i, _D]
+        u64, U64 = ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)
+        L.oracle_philox4x64.argtypes = [U64, U64, U64]
+        L.oracle_philox4x64.restype = None
+        L.oracle_noise_normals.argtypes = [i, i, u64, u64, u64, _D]
+        L.oracle_cook_forcing.argtypes = [i, i, d, d, d, d, _D, _D]
+        L.oracle_ch_cook_step.argtypes = [i, i, d, d, d, d, d, _D, _D, _D]
+        L.oracle_ch_cook_run.argtypes = [i, i, d, d, d, d, d, u64, u64, u64, i, _D, _D]
         for fn in ("oracle_penta_cyclic_solve", "oracle_penta_cyclic_batch", "oracle_tri_cyclic_solve",
                    "oracle_tri_cyclic_batch", "oracle_stencil_apply_2d", "oracle_ch_step",
                    "oracle_ch_run", "oracle_ch_diagnostics", "oracle_ch1d_run",
-                   "oracle_cn1d_run"):
+                   "oracle_cn1d_run", "oracle_noise_normals", "oracle_cook_forcing", "oracle_ch_cook_step",
+                   "oracle_ch_cook_run"):
             getattr(L, fn).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -154,3 +162,45 @@ def cn1d_run(order, c, l, kappa, dt, nsteps=1, batch=1):
     n = c.size // batch
     _check(lib().oracle_cn1d_run(int(order), n, batch, float(l), float(kappa), float(dt), int(nsteps), _p(c)))
     return c
+
+
+def philox4x64(ctr, key):
+    """Philox4x64-10 block (Salmon et al., SC 2011): four 64-bit words."""
+    U = ctypes.c_uint64
+    c, k, o = (U * 4)(*[int(v) for v in ctr]), (U * 2)(*[int(v) for v in key]), (U * 4)()
+    lib().oracle_philox4x64(c, k, o)
+    return [int(v) for v in o]
+
+
+def noise_normals(nx, ny, seed, sim, step):
+    """Box-Muller deviates (rho^x, rho^y) of one Cahn-Hilliard-Cook step, shape (2, ny, nx)."""
+    rho = np.empty(2 * nx * ny)
+    _check(lib().oracle_noise_normals(nx, ny, int(seed), int(sim), int(step), _p(rho)))
+    return rho.reshape(2, ny, nx)
+
+
+def cook_forcing(rho, lx, ly, dt, sigma):
+    """eta = sqrt(sigma / (dx dy dt)) div_h rho for rho of shape (2, ny, nx) (Sec. 7.6)."""
+    rho = _f64(rho)
+    _, ny, nx = rho.shape
+    eta = np.empty((ny, nx))
+    _check(lib().oracle_cook_forcing(nx, ny, float(lx), float(ly), float(dt), float(sigma), _p(rho), _p(eta)))
+    return eta
+
+
+def ch_cook_step(c_now, c_prev, rho, lx, ly, gamma, dt, sigma):
+    """One Cahn-Hilliard-Cook ADI step with the given deviates; returns (C^{n+1}, C^n)."""
+    cn, cp, rho = _f64(c_now).copy(), _f64(c_prev).copy(), _f64(rho)
+    ny, nx = cn.shape
+    _check(lib().oracle_ch_cook_step(nx, ny, float(lx), float(ly), float(gamma), float(dt), float(sigma), _p(rho),
+                                     _p(cn), _p(cp)))
+    return cn, cp
+
+
+def ch_cook_run(c_now, c_prev, lx, ly, gamma, dt, sigma, seed, sim, step0, nsteps):
+    """nsteps Cahn-Hilliard-Cook steps drawing the deviates of steps step0.. ; returns (C, C_prev)."""
+    cn, cp = _f64(c_now).copy(), _f64(c_prev).copy()
+    ny, nx = cn.shape
+    _check(lib().oracle_ch_cook_run(nx, ny, float(lx), float(ly), float(gamma), float(dt), float(sigma), int(seed),
+                                    int(sim), int(step0), int(nsteps), _p(cn), _p(cp)))
+    return cn, cp

@@ -22,6 +22,7 @@
  * Readings of garbled or silent passages are listed where they are used.
  */
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -314,8 +315,10 @@ int oracle_stencil_apply_2d(const double* in, double* out, int nx, int ny, int l
  * eq:1d_hyper_scheme and the cross stencil [1,-2,1;-2,4,-2;1,-2,1]/(dx^2 dy^2)
  * of fig3:stencil.  On return c_prev holds C^n and c_now C^{n+1}.
  * ------------------------------------------------------------------------- */
-int oracle_ch_step(int nx, int ny, double lx, double ly, double gamma, double dt,
-                   double* c_now, double* c_prev) {
+/* eta: NULL, or an nx*ny forcing field added to the PDE's right-hand side; in
+ * the two-level scheme it enters r with the weight (2/3) dt of the explicit terms. */
+static int ch_step_forced(int nx, int ny, double lx, double ly, double gamma, double dt,
+                          double* c_now, double* c_prev, const double* eta) {
   if (nx < 5 || ny < 5 || !(lx > 0) || !(ly > 0) || !(dt > 0) || !(gamma >= 0)) return ORC_EINVAL;
   long np = (long)nx * ny;
   double dx = lx / nx, dy = ly / ny;
@@ -346,6 +349,7 @@ int oracle_ch_step(int nx, int ny, double lx, double ly, double gamma, double dt
       long p = (long)j * nx + i;
       r[p] = -(2.0 / 3.0) * (c_now[p] - c_prev[p]) - (2.0 / 3.0) * gamma * dt * bih +
              (2.0 / 3.0) * dt * lapN;
+      if (eta) r[p] += (2.0 / 3.0) * dt * eta[p];
     }
   }
 #undef AT
@@ -379,6 +383,11 @@ int oracle_ch_step(int nx, int ny, double lx, double ly, double gamma, double dt
 done:
   free(cb); free(r); free(nl); free(w); free(ca);
   return rc;
+}
+
+int oracle_ch_step(int nx, int ny, double lx, double ly, double gamma, double dt,
+                   double* c_now, double* c_prev) {
+  return ch_step_forced(nx, ny, lx, ly, gamma, dt, c_now, c_prev, NULL);
 }
 
 int oracle_ch_run(int nx, int ny, double lx, double ly, double gamma, double dt, int nsteps,
@@ -504,5 +513,103 @@ int oracle_cn1d_run(int order, int n, int batch, double l, double kappa, double 
   }
 done2:
   free(f); free(x); free(co);
+  return rc;
+}
+
+/* ---------------------------------------------------------------------------
+ * Cahn-Hilliard-Cook forcing (Sec. 7.6): C_t = D Lap(C^3 - C - gamma Lap C) + eta,
+ * eta_ij = sqrt(sigma / (dx dy dt)) div_h rho_ij, rho a 2-vector field of N(0,1)
+ * deviates drawn afresh every step by the Box-Muller transform of uniforms.
+ * Readings: div_h is the backward difference
+ *   (rho^x_ij - rho^x_{i-1,j}) / dx + (rho^y_ij - rho^y_{i,j-1}) / dy
+ * (periodic), whose covariance is sigma/(dx dy dt) times minus the 5-point
+ * Laplacian of a Kronecker delta, the discrete form of the stated correlation;
+ * dx^2 of the prefactor is dx dy for unequal spacings.
+ *
+ * Uniforms come from the counter-based generator Philox4x64-10 (Salmon, Moraes,
+ * Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC 2011):
+ * 10 rounds, each (hi0, lo0) = M0 * x0, (hi1, lo1) = M1 * x2 (128-bit products),
+ * x <- (hi1 ^ x1 ^ k0, lo1, hi0 ^ x3 ^ k1, lo0), with the key bumped by the
+ * Weyl constants W0, W1 between rounds.
+ * ------------------------------------------------------------------------- */
+void oracle_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+  uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3], k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) { k0 += W0; k1 += W1; }
+    unsigned __int128 p0 = (unsigned __int128)M0 * x0, p1 = (unsigned __int128)M1 * x2;
+    uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+    uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+    uint64_t y0 = hi1 ^ x1 ^ k0, y1 = lo1, y2 = hi0 ^ x3 ^ k1, y3 = lo0;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* Normal deviates of step `step` for an nx*ny grid: rho[0 .. np-1] = rho^x,
+ * rho[np .. 2np-1] = rho^y (row-major).  Points 2b and 2b+1 take the four words
+ * of Philox(counter = (b, step, 0, 0), key = (seed, sim)); word w gives the
+ * uniform u = (floor(w / 2^41) + 1/2) 2^-23 in (0, 1), and the pairs (u0, u1),
+ * (u2, u3) give (rho^x, rho^y) of the two points by Box-Muller:
+ *   rho^x = sqrt(-2 ln u_a) cos(2 pi u_b), rho^y = sqrt(-2 ln u_a) sin(2 pi u_b). */
+int oracle_noise_normals(int nx, int ny, uint64_t seed, uint64_t sim, uint64_t step, double* rho) {
+  if (nx < 1 || ny < 1) return ORC_EINVAL;
+  long np = (long)nx * ny;
+  const uint64_t key[2] = {seed, sim};
+  for (long b = 0; 2 * b < np; ++b) {
+    uint64_t ctr[4] = {(uint64_t)b, step, 0, 0}, w[4];
+    oracle_philox4x64(ctr, key, w);
+    for (int h = 0; h < 2; ++h) {
+      long p = 2 * b + h;
+      if (p >= np) break;
+      double ua = ((double)(w[2 * h] >> 41) + 0.5) * 0x1p-23;
+      double ub = ((double)(w[2 * h + 1] >> 41) + 0.5) * 0x1p-23;
+      double rad = sqrt(-2.0 * log(ua));
+      rho[p] = rad * cos(6.283185307179586 * ub); /* 2 pi */
+      rho[np + p] = rad * sin(6.283185307179586 * ub);
+    }
+  }
+  return ORC_OK;
+}
+
+/* eta = sqrt(sigma / (dx dy dt)) div_h rho (reading above). */
+int oracle_cook_forcing(int nx, int ny, double lx, double ly, double dt, double sigma, const double* rho,
+                        double* eta) {
+  if (nx < 2 || ny < 2 || !(lx > 0) || !(ly > 0) || !(dt > 0) || !(sigma >= 0)) return ORC_EINVAL;
+  long np = (long)nx * ny;
+  double dx = lx / nx, dy = ly / ny, amp = sqrt(sigma / (dx * dy * dt));
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      long p = (long)j * nx + i;
+      double div = (rho[p] - rho[(long)j * nx + wrap(i - 1, nx)]) / dx +
+                   (rho[np + p] - rho[np + (long)wrap(j - 1, ny) * nx + i]) / dy;
+      eta[p] = amp * div;
+    }
+  return ORC_OK;
+}
+
+/* One Cahn-Hilliard-Cook step with the given deviates rho (2 nx ny values). */
+int oracle_ch_cook_step(int nx, int ny, double lx, double ly, double gamma, double dt, double sigma,
+                        const double* rho, double* c_now, double* c_prev) {
+  double* eta = malloc((size_t)nx * ny * sizeof(double));
+  if (!eta) return ORC_ENOMEM;
+  int rc = oracle_cook_forcing(nx, ny, lx, ly, dt, sigma, rho, eta);
+  if (!rc) rc = ch_step_forced(nx, ny, lx, ly, gamma, dt, c_now, c_prev, eta);
+  free(eta);
+  return rc;
+}
+
+/* nsteps steps, the deviates of step k (k = step0 ..) drawn by oracle_noise_normals. */
+int oracle_ch_cook_run(int nx, int ny, double lx, double ly, double gamma, double dt, double sigma, uint64_t seed,
+                       uint64_t sim, uint64_t step0, int nsteps, double* c_now, double* c_prev) {
+  double* rho = malloc(2 * (size_t)nx * ny * sizeof(double));
+  if (!rho) return ORC_ENOMEM;
+  int rc = ORC_OK;
+  for (int k = 0; k < nsteps && !rc; ++k) {
+    rc = oracle_noise_normals(nx, ny, seed, sim, step0 + (uint64_t)k, rho);
+    if (!rc) rc = oracle_ch_cook_step(nx, ny, lx, ly, gamma, dt, sigma, rho, c_now, c_prev);
+  }
+  free(rho);
   return rc;
 }

@@ -411,3 +411,102 @@ def test_cn_mode_amplification_closed_form(order):
     G = (1 - sig * sym) / (1 + sig * sym)
     got = oracle.cn1d_run(order, np.cos(2 * np.pi * kk * x), l, kappa, dt, 10)
     assert np.max(np.abs(got - G**10 * np.cos(2 * np.pi * kk * x))) <= 1e-12
+
+
+# --------------------------------------------------------------------------- Cahn-Hilliard-Cook (Sec. 7.6)
+@pytest.mark.parametrize("key,ctr", [((5, 7), (0, 0, 0, 0)), ((0, 0), (41, 3, 0, 0)),
+                                     ((2**64 - 1, 12345), (2**64 - 1, 5, 9, 0))])
+def test_philox4x64_matches_numpy(key, ctr):
+    # numpy's Philox bit generator is Philox4x64-10; it advances its 256-bit
+    # counter by one before producing each block of four words
+    bg = np.random.Philox(key=np.array(key, dtype=np.uint64), counter=np.array(ctr, dtype=np.uint64))
+    ref = [int(v) for v in bg.random_raw(12)]
+    c = list(ctr)
+    for blk in range(3):
+        c[0] += 1
+        for w in range(3):  # carry into the next word
+            if c[w] == 2**64:
+                c[w] = 0
+                c[w + 1] += 1
+        assert oracle.philox4x64(c, key) == ref[4 * blk:4 * blk + 4]
+
+
+def test_noise_normals_are_standard_normal():
+    from scipy import stats
+
+    nx = ny = 256
+    z = np.concatenate([oracle.noise_normals(nx, ny, 2021, 3, step).reshape(2, -1) for step in range(4)], axis=1)
+    n = z.shape[1]
+    for comp in z:
+        assert abs(comp.mean()) < 5 / np.sqrt(n)
+        assert abs(comp.var() - 1.0) < 5 * np.sqrt(2.0 / n)
+        assert stats.kstest(comp, "norm").pvalue > 1e-3
+    assert abs(np.corrcoef(z[0], z[1])[0, 1]) < 5 / np.sqrt(n)
+    # different steps, simulations and seeds give unrelated deviates
+    a = oracle.noise_normals(64, 64, 1, 0, 0).ravel()
+    for other in (oracle.noise_normals(64, 64, 1, 0, 1), oracle.noise_normals(64, 64, 1, 1, 0),
+                  oracle.noise_normals(64, 64, 2, 0, 0)):
+        assert abs(np.corrcoef(a, other.ravel())[0, 1]) < 5 / np.sqrt(a.size)
+    # odd point count: the last pair is half used; the rest is unchanged
+    odd = oracle.noise_normals(7, 5, 9, 0, 0).reshape(2, -1)
+    full = oracle.noise_normals(6, 6, 9, 0, 0).reshape(2, -1)
+    assert np.array_equal(odd[:, :35], full[:, :35])
+
+
+def test_cook_forcing_conserves_mass_and_has_laplacian_covariance():
+    nx, ny, lx, ly, dt, sigma = 96, 64, 2 * np.pi, 1.5 * np.pi, 1e-3, 1e-14
+    dx, dy = lx / nx, ly / ny
+    amp2 = sigma / (dx * dy * dt)
+    etas = np.stack([oracle.cook_forcing(oracle.noise_normals(nx, ny, 77, 0, s), lx, ly, dt, sigma)
+                     for s in range(40)])
+    scale = np.sqrt(amp2) / min(dx, dy)
+    assert np.max(np.abs(etas.sum(axis=(1, 2)))) <= 1e-12 * scale * nx * ny
+    var = np.mean(etas**2)
+    cx = np.mean(etas * np.roll(etas, -1, axis=2))
+    cy = np.mean(etas * np.roll(etas, -1, axis=1))
+    cd = np.mean(etas * np.roll(np.roll(etas, -1, axis=2), -1, axis=1))
+    # <eta eta'> = -sigma/(dx dy dt) * (5-point Laplacian of the Kronecker delta)
+    assert var == pytest.approx(amp2 * (2 / dx**2 + 2 / dy**2), rel=0.03)
+    assert cx == pytest.approx(-amp2 / dx**2, rel=0.06)
+    assert cy == pytest.approx(-amp2 / dy**2, rel=0.06)
+    assert abs(cd) < 0.03 * var
+    # a unit deviate at one point is a dipole along its own axis
+    rho = np.zeros((2, ny, nx))
+    rho[0, 5, 9] = 1.0
+    eta = oracle.cook_forcing(rho, lx, ly, dt, sigma)
+    want = np.zeros((ny, nx))
+    want[5, 9], want[5, 10] = np.sqrt(amp2) / dx, -np.sqrt(amp2) / dx
+    assert np.allclose(eta, want, rtol=1e-15, atol=0)
+
+
+def test_cook_step_from_rest_matches_fourier_solution():
+    # from C = 0 the nonlinear and biharmonic terms vanish: the step is
+    # C^1 = (I + a dxxxx)^{-1} (I + a dyyyy)^{-1} (2/3) dt eta, evaluated here with
+    # the backward-difference divergence written as a Fourier multiplier
+    nx, ny, lx, ly, gamma, dt, sigma = 48, 40, 2 * np.pi, 2.5, 0.01, 2e-3, 1e-6
+    dx, dy = lx / nx, ly / ny
+    rho = oracle.noise_normals(nx, ny, 5, 1, 0)
+    zero = np.zeros((ny, nx))
+    got, prev = oracle.ch_cook_step(zero, zero, rho, lx, ly, gamma, dt, sigma)
+    assert np.array_equal(prev, zero)
+    tx = 2 * np.pi * np.fft.fftfreq(nx)[None, :]
+    ty = 2 * np.pi * np.fft.fftfreq(ny)[:, None]
+    amp = np.sqrt(sigma / (dx * dy * dt))
+    eta_h = amp * ((1 - np.exp(-1j * tx)) / dx * np.fft.fft2(rho[0]) + (1 - np.exp(-1j * ty)) / dy * np.fft.fft2(rho[1]))
+    px = spectral.second_diff_symbol(nx, dx)[None, :]
+    py = spectral.second_diff_symbol(ny, dy)[:, None]
+    a = (2.0 / 3.0) * gamma * dt
+    want = np.real(np.fft.ifft2((2.0 / 3.0) * dt * eta_h / ((1 + a * px**2) * (1 + a * py**2))))
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+
+
+def test_cook_step_without_noise_is_the_plain_step_and_conserves_mass():
+    n, l, gamma, dt = 32, 2 * np.pi, 0.02, 1e-3
+    c0 = synth.field(4, n, n, -0.1, 0.1)
+    rho = oracle.noise_normals(n, n, 1, 0, 0)
+    a, _ = oracle.ch_cook_step(c0, c0, rho, l, l, gamma, dt, 0.0)
+    b, _ = oracle.ch_run(c0, c0, l, l, gamma, dt, 1)
+    assert np.array_equal(a, b)
+    c, cp = oracle.ch_cook_run(c0, c0, l, l, gamma, dt, 1e-6, 8, 0, 0, 6)
+    assert abs(c.sum() - c0.sum()) <= 1e-13 * np.abs(c0).sum()
+    assert np.max(np.abs(c - c0)) > 1e-6  # the forcing acted
