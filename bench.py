@@ -279,6 +279,8 @@ def run_chx(args, rank, world, local_rank):
         extras["ch1d"] = bench_ch1d(dev)
         extras["cn1d"] = bench_cn1d(dev)
         torch.cuda.empty_cache()
+        extras["cook"] = bench_cook(dev)
+        torch.cuda.empty_cache()
         extras["ensemble"] = bench_ensemble(dev, chx.PREC_F32_REFINE, args.ens_steps, 3)
         torch.cuda.empty_cache()
         extras["serving"] = bench_serving(dev, args.serve_requests, args.serve_rate, chx.PREC_F32_REFINE)
@@ -432,6 +434,39 @@ def bench_cn1d(dev, steps=100, rewrite_steps=20):
         del c
         torch.cuda.empty_cache()
     return out
+
+
+def bench_cook(dev, steps=50):
+    """Cahn-Hilliard-Cook runs (Sec. 7.6) on the 2048^2 workload: C = 0 initially,
+    sigma = 1e-14, fresh Philox + Box-Muller deviates every step, FP64 step."""
+    import torch
+
+    import paper_2101_06550_gb300 as chx
+
+    n, l, gamma, dt = 2048, 2 * np.pi, 0.005, 5e-4
+    plan = chx.ChPlan(n, n, l, l, gamma, dt)
+    cn = torch.zeros(n * n, dtype=torch.float64, device=dev)
+    cp = torch.zeros_like(cn)
+    work = plan.alloc_work(dev)
+    rho = torch.empty(2 * n * n, dtype=torch.float64, device=dev)
+    plan.cook_run(cn, cp, work, rho, 3, 1e-14, seed=7)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    plan.cook_run(cn, cp, work, rho, steps, 1e-14, seed=7, step0=3)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    a.record()
+    for k in range(steps):
+        chx.noise_normals(rho, n, n, 7, 0, k)
+    b.record()
+    torch.cuda.synchronize()
+    ms_dev = a.elapsed_time(b) / steps
+    plan.sync_status()
+    pts = n * n
+    return {"n": n, "sigma": 1e-14, "ms_per_step": ms, "value": pts / (ms * 1e-3), "unit": "grid-pt-steps/s",
+            "deviates_ms_per_step": ms_dev, "max_abs_c": float(cn.abs().max())}
 
 
 def ensemble_sims(count=512, seed=11):

@@ -21,6 +21,7 @@
 #define CHX_H
 
 #include <stddef.h>
+#include <stdint.h>
 
 #ifdef __cplusplus
 extern "C" {
@@ -172,6 +173,37 @@ int ch_plan_create(chx_ch_plan** plan, int nx, int ny, double lx, double ly, dou
 size_t ch_work_bytes(const chx_ch_plan* plan);
 int ch_step(chx_ch_plan* plan, double* c_now, double* c_prev, void* work, int nsteps, void* stream);
 int ch_diagnostics(chx_ch_plan* plan, const double* c, double* mass_out, double* energy_out, void* stream);
+
+/*
+ * Cahn-Hilliard-Cook equation (Sec. 7.6): the Cahn-Hilliard equation with the
+ * conserved thermal forcing eta, C_t = Lap(C^3 - C - gamma Lap C) + eta, with
+ *   eta_ij = sqrt(sigma / (dx dy dt)) div_h rho_ij,
+ *   div_h rho_ij = (rho^x_ij - rho^x_{i-1,j}) / dx + (rho^y_ij - rho^y_{i,j-1}) / dy
+ * (periodic; the backward difference makes <eta eta'> = sigma/(dx dy dt) times
+ * minus the 5-point Laplacian of a Kronecker delta, the discrete form of the
+ * paper's correlation), rho a 2-vector field of N(0, 1) deviates drawn afresh
+ * every step.  In the ADI step of ch_step eta enters r with the weight (2/3) dt
+ * of the explicit terms.  FP64 plans only (CHX_EUNSUPPORTED otherwise).
+ *
+ * ch_noise_normals: writes the deviates of step `step` of simulation `sim`
+ *   into the device array rho (2 nx ny doubles: rho^x then rho^y, row-major,
+ *   ld = nx).  Points 2b and 2b+1 take the four words of Philox4x64-10 (Salmon
+ *   et al., SC 2011) with counter (b, step, 0, 0) and key (seed, sim); word w
+ *   gives u = (floor(w / 2^41) + 1/2) 2^-23 and the pairs (u0, u1), (u2, u3)
+ *   give (rho^x, rho^y) = sqrt(-2 ln ua) (cos 2 pi ub, sin 2 pi ub) (Box-Muller,
+ *   evaluated in FP32 and stored as FP64).  Errors: CHX_EINVAL, CHX_ECUDA.
+ * ch_step_noise: one step with caller-given deviates rho (device, 2 nx ny
+ *   doubles, layout as above); c_now/c_prev keep their roles as in ch_step.
+ * ch_cook_run: nsteps steps, step k drawing the deviates of step step0 + k into
+ *   the caller's device scratch rho (2 nx ny doubles) before stepping.
+ * sigma >= 0 (the paper uses 1e-14 with C = 0 initially).  rho must not overlap
+ * c_now, c_prev or work.  Errors: CHX_EINVAL, CHX_EUNSUPPORTED, CHX_ECUDA.
+ */
+int ch_noise_normals(double* rho, int nx, int ny, uint64_t seed, uint64_t sim, uint64_t step, void* stream);
+int ch_step_noise(chx_ch_plan* plan, double* c_now, double* c_prev, void* work, const double* rho, double sigma,
+                  void* stream);
+int ch_cook_run(chx_ch_plan* plan, double* c_now, double* c_prev, void* work, double* rho, int nsteps,
+                double sigma, uint64_t seed, uint64_t sim, uint64_t step0, void* stream);
 
 /*
  * Batched 1D Cahn-Hilliard (Sec. 6.2.2, eq6:1Dnumerical): for every simulation s

@@ -27,7 +27,7 @@ STATUS = {0: "CHX_OK", -1: "CHX_EINVAL", -2: "CHX_ESINGULAR", -3: "CHX_ENONFINIT
 EXPORTS = ("chx_status_string", "chx_last_error", "chx_version", "stencil_apply_2d", "penta_cyclic_factor",
            "penta_cyclic_refactor", "penta_cyclic_solve_batched", "tri_cyclic_factor", "tri_cyclic_refactor",
            "tri_cyclic_solve_batched", "ch_plan_create", "ch_work_bytes", "ch_step", "ch_diagnostics",
-           "ch_diagnostics_noalloc", "ch1d_plan_create", "ch1d_step", "cn1d_plan_create", "cn1d_step", "ch_profile", "ch_profile_read", "ch_profile_slot_name", "ens_create",
+           "ch_diagnostics_noalloc", "ch1d_plan_create", "ch1d_step", "cn1d_plan_create", "cn1d_step", "ch_noise_normals", "ch_step_noise", "ch_cook_run", "ch_profile", "ch_profile_read", "ch_profile_slot_name", "ens_create",
            "ens_group_create", "ens_group_destroy", "ens_group_set_active", "ens_slot_load", "ens_slot_read",
            "ens_slot_move", "ens_step", "ens_group_step", "ens_autotune", "ens_info", "ens_bytes_used",
            "chx_sync_status", "chx_plan_destroy")
@@ -73,6 +73,9 @@ def lib():
         "ch1d_step": (i, [_P, _P, i, _P]),
         "cn1d_plan_create": (i, [ctypes.POINTER(_P), i, i, i, d, d, d, i]),
         "cn1d_step": (i, [_P, _P, i, _P]),
+        "ch_noise_normals": (i, [_P, i, i, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _P]),
+        "ch_step_noise": (i, [_P, _P, _P, _P, _P, d, _P]),
+        "ch_cook_run": (i, [_P, _P, _P, _P, _P, i, d, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _P]),
         "ch_profile": (i, [_P, i]),
         "ch_profile_read": (i, [_P, _D, ctypes.POINTER(ctypes.c_longlong), i, i]),
         "ch_profile_slot_name": (ctypes.c_char_p, [i]),
@@ -267,6 +270,25 @@ class ChPlan(_Plan):
                              _dev(c_prev, torch.float64, n, "c_prev"), _dev(work, None, None, "work"), int(nsteps),
                              _stream(stream)))
 
+    def step_noise(self, c_now, c_prev, work, rho, sigma, stream=None):
+        """One Cahn-Hilliard-Cook step with given deviates rho (2*nx*ny float64, device)."""
+        import torch
+
+        n = self.nx * self.ny
+        _check(lib().ch_step_noise(self._handle, _dev(c_now, torch.float64, n, "c_now"),
+                                   _dev(c_prev, torch.float64, n, "c_prev"), _dev(work, None, None, "work"),
+                                   _dev(rho, torch.float64, 2 * n, "rho"), float(sigma), _stream(stream)))
+
+    def cook_run(self, c_now, c_prev, work, rho, nsteps, sigma, seed, sim=0, step0=0, stream=None):
+        """nsteps Cahn-Hilliard-Cook steps drawing deviates into the scratch rho (2*nx*ny float64)."""
+        import torch
+
+        n = self.nx * self.ny
+        _check(lib().ch_cook_run(self._handle, _dev(c_now, torch.float64, n, "c_now"),
+                                 _dev(c_prev, torch.float64, n, "c_prev"), _dev(work, None, None, "work"),
+                                 _dev(rho, torch.float64, 2 * n, "rho"), int(nsteps), float(sigma), int(seed),
+                                 int(sim), int(step0), _stream(stream)))
+
     def profile(self, enable: bool = True):
         """Bracket every kernel of later steps with CUDA events (ch_profile)."""
         _check(lib().ch_profile(self._handle, int(bool(enable))))
@@ -289,6 +311,15 @@ class ChPlan(_Plan):
         _check(lib().ch_diagnostics(self._handle, _dev(c, torch.float64, self.nx * self.ny, "c"),
                                     ctypes.c_void_p(base), ctypes.c_void_p(base + 8), _stream(stream)))
         return out
+
+
+def noise_normals(rho, nx, ny, seed, sim, step, stream=None):
+    """Cahn-Hilliard-Cook deviates (ch_noise_normals) into rho (2*nx*ny float64, device)."""
+    import torch
+
+    _check(lib().ch_noise_normals(_dev(rho, torch.float64, 2 * nx * ny, "rho"), int(nx), int(ny), int(seed), int(sim),
+                                  int(step), _stream(stream)))
+    return rho
 
 
 def ch_diagnostics_noalloc(c, lx, ly, gamma, out, stream=None):

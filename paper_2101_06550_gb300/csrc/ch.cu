@@ -77,10 +77,17 @@ __device__ __forceinline__ int wrap_near(int i, int n) {
 // RHS stencil pass.  Tile of 32 (i) x 32 (j) outputs of simulation blockIdx.z,
 // Cn/Cbar staged with a 2-point halo, M with a 1-point halo.  Output element
 // (i, j) of simulation z goes to rT[i * (G*ny) + z*ny + j].  gls[z] = gamma/dx^2.
-template <typename TC, typename TO>
+//
+// NOISE (Cahn-Hilliard-Cook, Sec. 7.6): adds (2/3) dt eta with
+// eta = sqrt(sigma / (dx dy dt)) div_h rho, the backward-difference divergence
+// of the deviates rho (planes rho^x, rho^y of nx*ny per simulation):
+// nkx (rho^x_ij - rho^x_{i-1,j}) + nky (rho^y_ij - rho^y_{i,j-1}).
+template <typename TC, typename TO, bool NOISE = false>
 __global__ void __launch_bounds__(kT* kBY) ch_rhs_kernel(const double* __restrict__ cn, const double* __restrict__ cp,
                                                          TO* __restrict__ rT, int nx, int ny, int G, TC rho, TC kap,
-                                                         const TC* __restrict__ gls, TC k1, TC k2) {
+                                                         const TC* __restrict__ gls, TC k1, TC k2,
+                                                         const double* __restrict__ dev = nullptr, double nkx = 0,
+                                                         double nky = 0) {
   __shared__ TC s_cn[kT + 4][kT + 5];
   __shared__ TC s_cb[kT + 4][kT + 5];
   __shared__ TC s_m[kT + 2][kT + 3];
@@ -117,7 +124,20 @@ __global__ void __launch_bounds__(kT* kBY) ch_rhs_kernel(const double* __restric
     l = fma(rho, s_m[ly - 1][lx] + s_m[ly + 1][lx], l);
     l = fma(kap, s_m[ly][lx], l);
     const TC diff = s_cb[ly + 1][lx + 1] - s_cn[ly + 1][lx + 1];  // C^n - C^{n-1}
-    s_o[lx - 1][ly - 1] = (TO)fma(k2, l, -(k1 * diff));
+    TC o = fma(k2, l, -(k1 * diff));
+    if (NOISE) {
+      const int gi = i0 + lx - 1, gj = j0 + ly - 1;
+      if (gi < nx && gj < ny) {
+        const size_t N = (size_t)nx * ny;
+        const double* rx = dev + (size_t)z * 2 * N;
+        const double* ry = rx + N;
+        const size_t p = (size_t)gj * nx + gi;
+        const size_t pw = (size_t)gj * nx + (gi == 0 ? nx - 1 : gi - 1);
+        const size_t ps = (size_t)(gj == 0 ? ny - 1 : gj - 1) * nx + gi;
+        o += (TC)fma(nkx, rx[p] - rx[pw], nky * (ry[p] - ry[ps]));
+      }
+    }
+    s_o[lx - 1][ly - 1] = (TO)o;
   }
   __syncthreads();
   const size_t ldo = (size_t)G * ny;
@@ -836,7 +856,15 @@ static void step_f64(ChGroup* g, int G, double* cur, double* prev, void* work, i
   const DirView<double> X = view<double>(g->X, ny), Y = view<double>(g->Y, nx);
   const dim3 gx(ceil_div(nsx, kSolveThreads), X.P), gy(ceil_div(nx, kSolveThreads), Y.P, G);
   const size_t kyz = 4 * (size_t)Y.P * nx;
-  { PROF(kRhs); ch_rhs_kernel<double, double><<<tgrid, tblock, 0, st>>>(cur, prev, f, nx, ny, G, g->rho, g->kap, g->d_gl, g->k1, g->k2); }
+  if (g->noise) {
+    PROF(kRhs);
+    ch_rhs_kernel<double, double, true><<<tgrid, tblock, 0, st>>>(cur, prev, f, nx, ny, G, g->rho, g->kap, g->d_gl,
+                                                                  g->k1, g->k2, g->noise, g->nkx, g->nky);
+  } else {
+    PROF(kRhs);
+    ch_rhs_kernel<double, double><<<tgrid, tblock, 0, st>>>(cur, prev, f, nx, ny, G, g->rho, g->kap, g->d_gl, g->k1,
+                                                            g->k2);
+  }
   { PROF(kLocX); launch_local<double, double>(f, f, nsx, nsx, X, ybx, 0, 0, 1, status, st); }
   { PROF(kRedX); spike_reduced_kernel<double><<<dim3(gx.x, 4 * X.P), kSolveThreads, 0, st>>>(ybx, X, tx, nsx, 0); }
   { PROF(kFinX); ch_xfinish_kernel<double, double><<<tgrid, tblock, 0, st>>>(f, tx, X, w, nx, ny, G); }
@@ -986,6 +1014,70 @@ extern "C" int ch_step(chx_ch_plan* p, double* c_now, double* c_prev, void* work
       prev = t;
     }
     int rc = launch_check("ch_step");
+    if (rc) return rc;
+  }
+  p->hdr.last_stream = st;
+  return CHX_OK;
+}
+
+static bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const char *x = (const char*)a, *y = (const char*)b;
+  return x < y + nb && y < x + na;
+}
+
+// Validation shared by the Cahn-Hilliard-Cook entry points; sets the forcing
+// weights (2/3) dt sqrt(sigma / (dx dy dt)) / dx and / dy.
+static int cook_prepare(chx_ch_plan* p, double* c_now, double* c_prev, void* work, const double* rho, double sigma,
+                        const char* name) {
+  if (!p || p->hdr.magic != kMagicCh) return fail(CHX_EINVAL, "%s: bad plan", name);
+  if (p->g.precision != CHX_PREC_F64)
+    return fail(CHX_EUNSUPPORTED, "%s: the forcing is implemented for CHX_PREC_F64 plans", name);
+  if (!c_now || !c_prev || !work || !rho) return fail(CHX_EINVAL, "%s: null pointer", name);
+  if (((uintptr_t)work & 255) != 0) return fail(CHX_EINVAL, "%s: work must be 256-byte aligned", name);
+  if (!(sigma >= 0) || !isfinite(sigma)) return fail(CHX_EINVAL, "%s: sigma %g", name, sigma);
+  const size_t fb = (size_t)p->g.nx * p->g.ny * sizeof(double), wb = p->g.work_bytes;
+  if (overlaps(c_now, fb, c_prev, fb) || overlaps(c_now, fb, work, wb) || overlaps(c_prev, fb, work, wb) ||
+      overlaps(rho, 2 * fb, c_now, fb) || overlaps(rho, 2 * fb, c_prev, fb) || overlaps(rho, 2 * fb, work, wb))
+    return fail(CHX_EINVAL, "%s: c_now, c_prev, work and rho must not overlap", name);
+  const ChGroup& g = p->g;
+  const double amp = sqrt(sigma / (g.dx * g.dy * g.dt));
+  p->g.nkx = (2.0 / 3.0) * g.dt * amp / g.dx;
+  p->g.nky = (2.0 / 3.0) * g.dt * amp / g.dy;
+  return CHX_OK;
+}
+
+extern "C" int ch_step_noise(chx_ch_plan* p, double* c_now, double* c_prev, void* work, const double* rho,
+                             double sigma, void* stream) {
+  int rc = cook_prepare(p, c_now, c_prev, work, rho, sigma, "ch_step_noise");
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  p->g.noise = rho;
+  group_step(&p->g, 1, c_now, c_prev, work, 1, st, p->prof, p->hdr.d_status);
+  p->g.noise = nullptr;
+  p->hdr.last_stream = st;
+  return launch_check("ch_step_noise");
+}
+
+extern "C" int ch_cook_run(chx_ch_plan* p, double* c_now, double* c_prev, void* work, double* rho, int nsteps,
+                           double sigma, uint64_t seed, uint64_t sim, uint64_t step0, void* stream) {
+  int rc = cook_prepare(p, c_now, c_prev, work, rho, sigma, "ch_cook_run");
+  if (rc) return rc;
+  if (nsteps < 0) return fail(CHX_EINVAL, "ch_cook_run: nsteps %d < 0", nsteps);
+  cudaStream_t st = (cudaStream_t)stream;
+  double *cur = c_now, *prev = c_prev;
+  for (int s = 0; s < nsteps; ++s) {
+    const int keep = s == nsteps - 1 && cur == c_now;
+    rc = launch_noise_normals(rho, p->g.nx, p->g.ny, 1, seed, sim, step0 + (uint64_t)s, st);
+    if (rc) return rc;
+    p->g.noise = rho;
+    group_step(&p->g, 1, cur, prev, work, keep, st, p->prof, p->hdr.d_status);
+    p->g.noise = nullptr;
+    if (!keep) {
+      double* t = cur;
+      cur = prev;
+      prev = t;
+    }
+    rc = launch_check("ch_cook_run");
     if (rc) return rc;
   }
   p->hdr.last_stream = st;

@@ -71,6 +71,10 @@ struct ChGroup {
   double rho = 0, kap = 0, k1 = 0, k2 = 0;  // right-hand side constants shared by the slots
   FFConst kff;                               // the same as double-float pairs (gl unused there)
   double* d_gl = nullptr;                    // slots: gamma / dx^2
+  // Cahn-Hilliard-Cook deviates for the next step (FP64 only; nullptr: none),
+  // 2 nx ny doubles per slot, and the forcing weights (2/3) dt amp / dx, / dy
+  const double* noise = nullptr;
+  double nkx = 0, nky = 0;
   float2* d_glff = nullptr;
   SpikeDir X, Y;
   // work layout (byte offsets), for G fields

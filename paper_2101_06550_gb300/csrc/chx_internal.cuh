@@ -65,6 +65,10 @@ int tri_factor_host(int n, const double* a, const double* b, const double* c, si
 const double* penta_plan_factors(const chx_penta_plan* p);
 const double* tri_plan_factors(const chx_tri_plan* p);
 
+// Cahn-Hilliard-Cook deviates for G consecutive simulations sim0.. (noise.cu).
+int launch_noise_normals(double* rho, int nx, int ny, int G, uint64_t seed, uint64_t sim0, uint64_t step,
+                         cudaStream_t st);
+
 // Plain non-cyclic pentadiagonal LU (paper factor steps) of the m x m Toeplitz
 // band (a, b, c, d, e); ralpha, beta, gam, del of length m.
 int band_factor_host(int m, double a, double b, double c, double d, double e, double* ralpha, double* beta,

@@ -1,0 +1,127 @@
+"""GPU parity of the Cahn-Hilliard-Cook forcing (Sec. 7.6): the Philox4x64-10 +
+Box-Muller deviates, the forced ADI step with given deviates, and whole runs."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.test_gpu_ch import _rhs_norm, step_tolerance
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+def _chx():
+    import paper_2101_06550_gb300 as chx
+
+    return chx
+
+
+def _forced_rhs_norm(cn, cp, rho, lx, ly, gamma, dt, sigma):
+    return _rhs_norm(cn, cp, lx, ly, gamma, dt) + (2.0 / 3.0) * dt * float(
+        np.max(np.abs(oracle.cook_forcing(rho, lx, ly, dt, sigma))))
+
+
+@pytest.mark.parametrize("nx,ny,seed,sim,step", [(64, 64, 7, 0, 0), (37, 23, 2**63 + 5, 3, 12345),
+                                                 (1, 1, 1, 1, 1), (512, 384, 2021, 11, 2**40)])
+def test_noise_normals_match_oracle(nx, ny, seed, sim, step):
+    chx = _chx()
+    rho = torch.empty(2 * nx * ny, dtype=torch.float64, device=DEV)
+    chx.noise_normals(rho, nx, ny, seed, sim, step)
+    got = rho.cpu().numpy().reshape(2, ny, nx)
+    want = oracle.noise_normals(nx, ny, seed, sim, step)
+    # same uniforms (integer work); the transform runs in FP32 on the device and
+    # in FP64 in the oracle: a few FP32 ulps of the radius sqrt(-2 ln u)
+    rad = np.sqrt(want[0] ** 2 + want[1] ** 2)
+    assert np.all(np.abs(got - want) <= 5e-7 * rad + 1e-300)
+    if nx * ny > 1000:
+        z = got.ravel()
+        assert abs(z.mean()) < 5 / np.sqrt(z.size) and abs(z.var() - 1) < 5 * np.sqrt(2 / z.size)
+
+
+@pytest.mark.parametrize("ny,nx,sigma,rest", [(64, 64, 1e-14, True), (80, 96, 1e-6, False), (48, 40, 1e-3, False)])
+def test_step_noise_matches_oracle(ny, nx, sigma, rest):
+    chx = _chx()
+    lx, ly, gamma, dt = 2 * np.pi, 2 * np.pi * ny / nx, 0.01, 1e-3
+    if rest:
+        c0 = np.zeros((ny, nx))
+        cm = c0.copy()
+    else:
+        c0 = synth.field(31, ny, nx, -0.3, 0.3)
+        cm = c0 + 1e-3 * synth.field(32, ny, nx, -1, 1)
+    rho = synth.field(33, 2 * ny, nx, -2.0, 2.0).reshape(2, ny, nx)  # any deviates: the step is linear in rho
+    plan = chx.ChPlan(nx, ny, lx, ly, gamma, dt)
+    cn = torch.from_numpy(c0).to(DEV)
+    cp = torch.from_numpy(cm).to(DEV)
+    plan.step_noise(cn, cp, plan.alloc_work(DEV), torch.from_numpy(rho.ravel()).to(DEV), sigma)
+    plan.sync_status()
+    want, want_prev = oracle.ch_cook_step(c0, cm, rho, lx, ly, gamma, dt, sigma)
+    assert np.array_equal(cp.cpu().numpy(), want_prev)
+    tol = 1e-11 * float(np.max(np.abs(want))) + 4 * 2.220446049250313e-16 * _forced_rhs_norm(
+        c0, cm, rho, lx, ly, gamma, dt, sigma)
+    assert np.max(np.abs(cn.cpu().numpy() - want)) <= tol
+
+
+def test_step_noise_full_size_one_step():
+    # the 2048^2 workload (gamma 0.005, dt 5e-4) with the paper's sigma = 1e-14
+    chx = _chx()
+    n, l, gamma, dt, sigma = 2048, 2 * np.pi, 0.005, 5e-4, 1e-14
+    c0 = synth.field(3, n, n, -0.05, 0.05)
+    cm = c0 + 1e-4 * synth.field(4, n, n, -1, 1)
+    rho = oracle.noise_normals(n, n, 99, 0, 0)
+    plan = chx.ChPlan(n, n, l, l, gamma, dt)
+    cn = torch.from_numpy(c0).to(DEV)
+    cp = torch.from_numpy(cm).to(DEV)
+    plan.step_noise(cn, cp, plan.alloc_work(DEV), torch.from_numpy(rho.ravel()).to(DEV), sigma)
+    want, _ = oracle.ch_cook_step(c0, cm, rho, l, l, gamma, dt, sigma)
+    tol = step_tolerance(want, c0, cm, l, l, gamma, dt) + 4 * 2.220446049250313e-16 * (2 / 3) * dt * float(
+        np.max(np.abs(oracle.cook_forcing(rho, l, l, dt, sigma))))
+    assert np.max(np.abs(cn.cpu().numpy() - want)) <= tol
+
+
+@pytest.mark.parametrize("nsteps", [1, 6, 7])
+def test_cook_run_matches_oracle_from_rest(nsteps):
+    chx = _chx()
+    n, l, gamma, dt, sigma = 64, 2 * np.pi, 0.01, 0.1 * 2 * np.pi / 64, 1e-8
+    zero = np.zeros((n, n))
+    plan = chx.ChPlan(n, n, l, l, gamma, dt)
+    cn = torch.zeros(n * n, dtype=torch.float64, device=DEV)
+    cp = torch.zeros_like(cn)
+    rho = torch.empty(2 * n * n, dtype=torch.float64, device=DEV)
+    plan.cook_run(cn, cp, plan.alloc_work(DEV), rho, nsteps, sigma, seed=42, sim=3, step0=10)
+    plan.sync_status()
+    want, want_prev = oracle.ch_cook_run(zero, zero, l, l, gamma, dt, sigma, 42, 3, 10, nsteps)
+    got = cn.cpu().numpy().reshape(n, n)
+    # the run is driven by the deviates alone (C = 0 at the start), and the
+    # device's deviates carry FP32 rounding (5e-7 relative, test above); the
+    # response is linear in them at this amplitude
+    assert np.max(np.abs(got - want)) <= 1e-6 * np.max(np.abs(want))
+    assert np.max(np.abs(cp.cpu().numpy().reshape(n, n) - want_prev)) <= 1e-6 * np.max(np.abs(want_prev)) + 1e-300
+    # mass stays zero to rounding
+    assert abs(got.sum()) <= 1e-12 * np.abs(got).sum()
+    # the last deviates are those of step step0 + nsteps - 1
+    last = oracle.noise_normals(n, n, 42, 3, 10 + nsteps - 1)
+    assert np.all(np.abs(rho.cpu().numpy().reshape(2, n, n) - last) <= 5e-7 * np.sqrt(last[0]**2 + last[1]**2))
+
+
+def test_cook_rejects_bad_arguments():
+    chx = _chx()
+    n = 32
+    plan = chx.ChPlan(n, n, 1.0, 1.0, 0.01, 1e-3)
+    cn = torch.zeros(n * n, dtype=torch.float64, device=DEV)
+    cp = torch.zeros_like(cn)
+    work = plan.alloc_work(DEV)
+    rho = torch.zeros(2 * n * n, dtype=torch.float64, device=DEV)
+    with pytest.raises(chx.ChxError) as e:
+        plan.step_noise(cn, cp, work, rho, -1.0)
+    assert e.value.status == -1
+    both = torch.zeros(3 * n * n, dtype=torch.float64, device=DEV)
+    with pytest.raises(chx.ChxError) as e:  # rho overlapping c_now
+        plan.step_noise(both[:n * n], cp, work, both[n * n // 2:n * n // 2 + 2 * n * n], 1e-6)
+    assert e.value.status == -1
+    p32 = chx.ChPlan(n, n, 1.0, 1.0, 0.01, 1e-3, chx.PREC_F32_REFINE)
+    with pytest.raises(chx.ChxError) as e:
+        p32.step_noise(cn, cp, p32.alloc_work(DEV), rho, 1e-6)
+    assert e.value.status == -7
