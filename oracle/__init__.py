@@ -204,3 +204,57 @@ def ch_cook_run(c_now, c_prev, lx, ly, gamma, dt, sigma, seed, sim, step0, nstep
     _check(lib().oracle_ch_cook_run(nx, ny, float(lx), float(ly), float(gamma), float(dt), float(sigma), int(seed),
                                     int(sim), int(step0), int(nsteps), _p(cn), _p(cp)))
     return cn, cp
+
+
+# --------------------------------------------------------------------------- coarsening observables
+def simpson_mean(v):
+    """Spatial average of a periodic (ny, nx) field by the composite Simpson rule
+    (Sec. 3.6) in each direction.  Closing the periodic interval [0, L] with
+    f(L) = f(0), the rule's weights h/3 (1, 4, 2, ..., 4, 1) fold onto the grid as
+    h/3 (2, 4, 2, 4, ...).  Reading: it needs an even number of intervals; for an
+    odd count the trapezoid rule (all weights h) is used in that direction."""
+    v = _f64(v)
+
+    def weights(n):
+        if n % 2:
+            return np.ones(n)
+        w = np.full(n, 2.0 / 3.0)
+        w[1::2] = 4.0 / 3.0
+        return w
+
+    ny, nx = v.shape
+    return float(np.sum(weights(ny)[:, None] * weights(nx)[None, :] * v) / (nx * ny))
+
+
+def s_of_t(c):
+    """s = 1 / (1 - <C^2>) with <.> the Simpson average (Sec. 3.6)."""
+    return 1.0 / (1.0 - simpson_mean(_f64(c) ** 2))
+
+
+def k1_of_t(c, lx, ly):
+    """k1 = sum |C^(k)|^2 / sum |k|^-1 |C^(k)|^2 over the discrete Fourier modes (Sec. 3.6),
+    k = (2 pi mx / lx, 2 pi my / ly).  Reading: the k = 0 mode (the mean, with no
+    length scale and an infinite weight |k|^-1) is left out of both sums."""
+    c = _f64(c)
+    ny, nx = c.shape
+    ch = np.fft.fft2(c)
+    kx = 2 * np.pi * np.fft.fftfreq(nx, d=lx / nx)[None, :]
+    ky = 2 * np.pi * np.fft.fftfreq(ny, d=ly / ny)[:, None]
+    kk = np.sqrt(kx**2 + ky**2)
+    p = np.abs(ch) ** 2
+    mask = kk > 0
+    return float(np.sum(p[mask]) / np.sum(p[mask] / kk[mask]))
+
+
+def observables(c, lx, ly, gamma):
+    """(mass, free energy F_h, s, k1) of a (ny, nx) field."""
+    m, e = ch_diagnostics(c, lx, ly, gamma)
+    return m, e, s_of_t(c), k1_of_t(c, lx, ly)
+
+
+def coarsening_rate(t, F):
+    """beta = -(t / F) dF/dt along a sampled series (Eq. eq7:betaN, Sec. 7.2), dF/dt
+    from second-order finite differences on the (possibly uneven) sample times:
+    three-point central differences inside, three-point one-sided at the ends."""
+    t, F = _f64(t), _f64(F)
+    return -(t / F) * np.gradient(F, t, edge_order=2)

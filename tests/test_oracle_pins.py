@@ -510,3 +510,62 @@ def test_cook_step_without_noise_is_the_plain_step_and_conserves_mass():
     c, cp = oracle.ch_cook_run(c0, c0, l, l, gamma, dt, 1e-6, 8, 0, 0, 6)
     assert abs(c.sum() - c0.sum()) <= 1e-13 * np.abs(c0).sum()
     assert np.max(np.abs(c - c0)) > 1e-6  # the forcing acted
+
+
+# --------------------------------------------------------------------------- coarsening observables (Secs. 3.6, 7.2)
+def test_simpson_mean_is_scipy_simpson_on_the_closed_interval():
+    from scipy.integrate import simpson
+
+    ny, nx, lx, ly = 24, 40, 2.0, 3.0
+    v = synth.field(8, ny, nx, -1, 1)
+    closed = np.concatenate([v, v[:1]], axis=0)
+    closed = np.concatenate([closed, closed[:, :1]], axis=1)
+    x = np.linspace(0, lx, nx + 1)
+    y = np.linspace(0, ly, ny + 1)
+    want = simpson(simpson(closed, x=x, axis=1), x=y) / (lx * ly)
+    assert oracle.simpson_mean(v) == pytest.approx(want, rel=1e-14, abs=1e-15)
+    # odd counts fall back to the trapezoid rule: the plain mean
+    w = synth.field(9, 15, 9, -1, 1)
+    assert oracle.simpson_mean(w) == pytest.approx(w.mean(), rel=1e-14)
+
+
+def test_s_of_t_closed_forms():
+    n = 64
+    x = np.arange(n) * 2 * np.pi / n
+    c = 0.8 * np.cos(3 * x)[None, :] * np.ones((n, 1))
+    assert oracle.s_of_t(c) == pytest.approx(1.0 / (1.0 - 0.32), rel=1e-14)  # <C^2> = A^2 / 2
+    assert oracle.s_of_t(np.zeros((8, 8))) == 1.0
+    tanh = np.tanh(5 * np.sin(x))[None, :] * np.ones((4, 1))  # sharp interfaces: <C^2> -> 1, s grows
+    assert oracle.s_of_t(tanh) > 5
+
+
+def test_k1_closed_forms():
+    ny, nx, lx, ly = 48, 64, 2 * np.pi, 3.0
+    x = np.arange(nx) * lx / nx
+    y = np.arange(ny) * ly / ny
+    X, Y = np.meshgrid(x, y)
+    k = 5.0
+    assert oracle.k1_of_t(0.3 + np.cos(k * X), lx, ly) == pytest.approx(k, rel=1e-13)  # the mean is left out
+    ky = 2 * np.pi * 4 / ly
+    kk = np.hypot(2.0, ky)
+    assert oracle.k1_of_t(np.sin(2 * X + ky * Y), lx, ly) == pytest.approx(kk, rel=1e-13)
+    a, b, ka, kb = 1.0, 0.5, 3.0, 7.0
+    c = a * np.cos(ka * X) + b * np.sin(kb * X)
+    assert oracle.k1_of_t(c, lx, ly) == pytest.approx((a * a + b * b) / (a * a / ka + b * b / kb), rel=1e-13)
+
+
+def test_coarsening_rate_closed_forms():
+    # F ~ t^-1/3 (the LSW law) has beta = 1/3; the error falls as h^2 inside and at the ends
+    errs = []
+    for m in (91, 181, 361):
+        t = np.linspace(10, 100, m)
+        errs.append(np.abs(oracle.coarsening_rate(t, 3.0 * t ** (-1 / 3)) - 1 / 3)[[0, m // 2, -1]])
+    errs = np.array(errs)
+    assert np.all(errs[0] < 4e-3)
+    assert np.all(np.abs(np.log2(errs[1:-1] / errs[2:]) - 2) < 0.1)  # asymptotic by the finest pair
+    t = np.linspace(10, 100, 181)
+    assert np.allclose(oracle.coarsening_rate(t, np.exp(-0.01 * t)), 0.01 * t, rtol=1e-4)
+    # uneven sampling: second order, exact on quadratics
+    tu = np.sort(synth.uniform(4, 40, 1.0, 2.0))
+    F = 5 + tu - 0.5 * tu**2
+    assert np.allclose(oracle.coarsening_rate(tu, F), -(tu / F) * (1 - tu), rtol=1e-9)
