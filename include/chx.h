@@ -206,6 +206,38 @@ int ch_cook_run(chx_ch_plan* plan, double* c_now, double* c_prev, void* work, do
                 double sigma, uint64_t seed, uint64_t sim, uint64_t step0, void* stream);
 
 /*
+ * Coarsening observables (Secs. 2.5, 3.6, 7.2).  For a field C:
+ *   out[0] mass = sum C dx dy,
+ *   out[1] F_h  (as ch_diagnostics),
+ *   out[2] s    = 1 / (1 - <C^2>), <.> the composite Simpson average with the
+ *               periodic closure f(L) = f(0) (weights (2, 4, 2, 4, ...)/3 per
+ *               direction for an even point count; the trapezoid rule, i.e. the
+ *               plain mean, for an odd one),
+ *   out[3] k1   = sum |C^(k)|^2 / sum |k|^-1 |C^(k)|^2 over the discrete Fourier
+ *               modes k = (2 pi mx / lx, 2 pi my / ly) != 0 (the mean mode has no
+ *               length scale and is left out of both sums).
+ * ch_observables: one field of the plan's grid; out is a DEVICE array of 4
+ *   doubles written asynchronously on `stream`.  The first call allocates
+ *   plan-owned scratch (a cuFFT real-to-complex plan and ny (nx/2+1) complex
+ *   values); later calls allocate nothing.
+ * ens_group_observables: every active slot of a group at once, out = DEVICE
+ *   array of 4 * active doubles (slot-major); k1 is not formed (NaN).  The
+ *   first call allocates a small partial-sum buffer.
+ * Both flag NaN/Inf in the field as CHX_ENONFINITE (read with chx_sync_status).
+ * Errors: CHX_EINVAL, CHX_ENOMEM, CHX_ECUDA.
+ *
+ * chx_coarsening_rate: HOST arrays.  beta_k = -(t_k / F_k) dF/dt(t_k) (Eq.
+ *   eq7:betaN; the thesis extracts dF/dt numerically, Sec. 7.2) for a sampled
+ *   series, dF/dt from the derivative of the quadratic through three
+ *   neighbouring samples: centred inside, one-sided at the ends (second order
+ *   on uneven spacing).  count >= 3, t strictly increasing, F finite and
+ *   non-zero, else CHX_EINVAL.
+ */
+int ch_observables(chx_ch_plan* plan, const double* c, double* out, void* stream);
+int ens_group_observables(chx_ens* ens, int group_id, double* out, void* stream);
+int chx_coarsening_rate(const double* t, const double* F, int count, double* beta);
+
+/*
  * Batched 1D Cahn-Hilliard (Sec. 6.2.2, eq6:1Dnumerical): for every simulation s
  * of an interleaved batch c[i * batch + s] (i = 0..n-1, periodic on [0, l)),
  *   (I + sigma delta^4) C^{n+1} = C^n + alpha delta^2 (C^3 - C)^n,

@@ -27,7 +27,7 @@ STATUS = {0: "CHX_OK", -1: "CHX_EINVAL", -2: "CHX_ESINGULAR", -3: "CHX_ENONFINIT
 EXPORTS = ("chx_status_string", "chx_last_error", "chx_version", "stencil_apply_2d", "penta_cyclic_factor",
            "penta_cyclic_refactor", "penta_cyclic_solve_batched", "tri_cyclic_factor", "tri_cyclic_refactor",
            "tri_cyclic_solve_batched", "ch_plan_create", "ch_work_bytes", "ch_step", "ch_diagnostics",
-           "ch_diagnostics_noalloc", "ch1d_plan_create", "ch1d_step", "cn1d_plan_create", "cn1d_step", "ch_noise_normals", "ch_step_noise", "ch_cook_run", "ch_profile", "ch_profile_read", "ch_profile_slot_name", "ens_create",
+           "ch_diagnostics_noalloc", "ch1d_plan_create", "ch1d_step", "cn1d_plan_create", "cn1d_step", "ch_noise_normals", "ch_step_noise", "ch_cook_run", "ch_observables", "ens_group_observables", "chx_coarsening_rate", "ch_profile", "ch_profile_read", "ch_profile_slot_name", "ens_create",
            "ens_group_create", "ens_group_destroy", "ens_group_set_active", "ens_slot_load", "ens_slot_read",
            "ens_slot_move", "ens_step", "ens_group_step", "ens_autotune", "ens_info", "ens_bytes_used",
            "chx_sync_status", "chx_plan_destroy")
@@ -73,6 +73,9 @@ def lib():
         "ch1d_step": (i, [_P, _P, i, _P]),
         "cn1d_plan_create": (i, [ctypes.POINTER(_P), i, i, i, d, d, d, i]),
         "cn1d_step": (i, [_P, _P, i, _P]),
+        "ch_observables": (i, [_P, _P, _P, _P]),
+        "ens_group_observables": (i, [_P, i, _P, _P]),
+        "chx_coarsening_rate": (i, [ctypes.POINTER(d), ctypes.POINTER(d), i, ctypes.POINTER(d)]),
         "ch_noise_normals": (i, [_P, i, i, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _P]),
         "ch_step_noise": (i, [_P, _P, _P, _P, _P, d, _P]),
         "ch_cook_run": (i, [_P, _P, _P, _P, _P, i, d, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _P]),
@@ -289,6 +292,14 @@ class ChPlan(_Plan):
                                  _dev(rho, torch.float64, 2 * n, "rho"), int(nsteps), float(sigma), int(seed),
                                  int(sim), int(step0), _stream(stream)))
 
+    def observables(self, c, out, stream=None):
+        """[mass, F_h, s, k1] of field c into the 4-element float64 device tensor ``out``."""
+        import torch
+
+        _check(lib().ch_observables(self._handle, _dev(c, torch.float64, self.nx * self.ny, "c"),
+                                    _dev(out, torch.float64, 4, "out"), _stream(stream)))
+        return out
+
     def profile(self, enable: bool = True):
         """Bracket every kernel of later steps with CUDA events (ch_profile)."""
         _check(lib().ch_profile(self._handle, int(bool(enable))))
@@ -320,6 +331,20 @@ def noise_normals(rho, nx, ny, seed, sim, step, stream=None):
     _check(lib().ch_noise_normals(_dev(rho, torch.float64, 2 * nx * ny, "rho"), int(nx), int(ny), int(seed), int(sim),
                                   int(step), _stream(stream)))
     return rho
+
+
+def coarsening_rate(t, F):
+    """beta = -(t/F) dF/dt along a sampled series (chx_coarsening_rate, host arrays)."""
+    import numpy as np
+
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    if t.shape != F.shape:
+        raise ValueError("t and F must have the same length")
+    beta = np.empty_like(t)
+    P = ctypes.POINTER(ctypes.c_double)
+    _check(lib().chx_coarsening_rate(t.ctypes.data_as(P), F.ctypes.data_as(P), int(t.size), beta.ctypes.data_as(P)))
+    return beta
 
 
 def ch_diagnostics_noalloc(c, lx, ly, gamma, out, stream=None):
@@ -418,6 +443,15 @@ class Ensemble(_Plan):
 
     def move(self, gid, src, dst, stream=None):
         _check(lib().ens_slot_move(self._handle, gid, src, dst, _stream(stream)))
+
+    def observables(self, gid, out, stream=None):
+        """[mass, F_h, s, NaN] of every active slot of group gid into the float64 device tensor
+        ``out`` (4 * active values, slot-major)."""
+        import torch
+
+        _check(lib().ens_group_observables(self._handle, int(gid), _dev(out, torch.float64, None, "out"),
+                                           _stream(stream)))
+        return out
 
     def step(self, nsteps=1, stream=None):
         _check(lib().ens_step(self._handle, int(nsteps), _stream(stream)))

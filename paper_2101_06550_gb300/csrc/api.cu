@@ -305,6 +305,30 @@ extern "C" const char* chx_last_error(void) { return g_last_error; }
 
 extern "C" int chx_version(void) { return 10000; }
 
+extern "C" int chx_coarsening_rate(const double* t, const double* F, int count, double* beta) {
+  if (!t || !F || !beta || count < 3) return fail(CHX_EINVAL, "chx_coarsening_rate: null pointer or count %d < 3", count);
+  for (int k = 1; k < count; ++k)
+    if (!(t[k] > t[k - 1])) return fail(CHX_EINVAL, "chx_coarsening_rate: times not increasing at %d", k);
+  for (int k = 0; k < count; ++k)
+    if (!(F[k] != 0.0) || !isfinite(F[k])) return fail(CHX_EINVAL, "chx_coarsening_rate: F[%d] = %g", k, F[k]);
+  // derivative of the quadratic through three neighbouring samples: centred
+  // inside, one-sided at the two ends (second order on uneven spacing)
+  for (int k = 0; k < count; ++k) {
+    const int c = k == 0 ? 1 : (k == count - 1 ? count - 2 : k);
+    const double h1 = t[c] - t[c - 1], h2 = t[c + 1] - t[c];
+    const double f0 = F[c - 1], f1 = F[c], f2 = F[c + 1];
+    double d;
+    if (k == 0)
+      d = -(2 * h1 + h2) / (h1 * (h1 + h2)) * f0 + (h1 + h2) / (h1 * h2) * f1 - h1 / (h2 * (h1 + h2)) * f2;
+    else if (k == count - 1)
+      d = h2 / (h1 * (h1 + h2)) * f0 - (h1 + h2) / (h1 * h2) * f1 + (2 * h2 + h1) / (h2 * (h1 + h2)) * f2;
+    else
+      d = (h1 * h1 * f2 - h2 * h2 * f0 + (h2 * h2 - h1 * h1) * f1) / (h1 * h2 * (h1 + h2));
+    beta[k] = -(t[k] / F[k]) * d;
+  }
+  return CHX_OK;
+}
+
 extern "C" int chx_sync_status(void* plan) {
   if (!plan) return fail(CHX_EINVAL, "chx_sync_status: null plan");
   PlanHdr* h = (PlanHdr*)plan;

@@ -814,6 +814,8 @@ int group_move_params(ChGroup* g, int from, int to, cudaStream_t st) {
 }
 
 void group_free(ChGroup* g) {
+  obs_free(g->obs);
+  g->obs = nullptr;
   free_dir(&g->X);
   free_dir(&g->Y);
   cudaFree(g->d_gl);
@@ -1095,6 +1097,15 @@ extern "C" int ch_diagnostics(chx_ch_plan* p, const double* c, double* mass_out,
                                          p->hdr.d_status);
   p->hdr.last_stream = st;
   return launch_check("ch_diagnostics");
+}
+
+extern "C" int ch_observables(chx_ch_plan* p, const double* c, double* out, void* stream) {
+  if (!p || p->hdr.magic != kMagicCh) return fail(CHX_EINVAL, "ch_observables: bad plan");
+  if (!c || !out) return fail(CHX_EINVAL, "ch_observables: null pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int rc = group_observables(&p->g, 1, c, out, 1, p->hdr.d_status, st);
+  p->hdr.last_stream = st;
+  return rc;
 }
 
 extern "C" int ch_profile(chx_ch_plan* p, int enable) {

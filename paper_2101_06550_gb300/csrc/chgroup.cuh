@@ -65,6 +65,8 @@ struct ProfScope {
   ~ProfScope();
 };
 
+struct ObsState;
+
 struct ChGroup {
   int nx = 0, ny = 0, G = 0, precision = 0;
   double lx = 0, ly = 0, gamma = 0, dt = 0, dx = 0, dy = 0;
@@ -75,6 +77,7 @@ struct ChGroup {
   // 2 nx ny doubles per slot, and the forcing weights (2/3) dt amp / dx, / dy
   const double* noise = nullptr;
   double nkx = 0, nky = 0;
+  struct ObsState* obs = nullptr;  // observables scratch, made on first use (obs.cu)
   float2* d_glff = nullptr;
   SpikeDir X, Y;
   // work layout (byte offsets), for G fields
@@ -101,6 +104,11 @@ std::vector<int> segment_candidates(int n, int nsys, int precision);
 // writes C^{n+1} over prev (caller swaps); 1 writes C^n into prev and C^{n+1}
 // into cur.
 // status: device word for bounded-wait timeouts (CHX_ETIMEOUT), may be null.
+// Coarsening observables [mass, F_h, s, k1] of the first gact fields into the
+// device array out (4 per field; k1 only with with_k1 and gact == 1, else NaN).
+int group_observables(ChGroup* g, int gact, const double* fields, double* out, int with_k1, int* status,
+                      cudaStream_t st);
+void obs_free(ObsState* o);
 void group_step(ChGroup* g, int gact, double* cur, double* prev, void* work, int keep_roles, cudaStream_t st,
                 Prof* prof, int* status);
 

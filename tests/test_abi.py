@@ -47,3 +47,25 @@ def test_plan_create_rejects_bad_args_without_gpu():
     assert e.value.status == -1
     with pytest.raises(chx.ChxError):
         chx.ChPlan(64, 64, 1.0, 1.0, 0.01, -1.0)
+
+
+def test_coarsening_rate_host_entry_point_matches_oracle():
+    # chx_coarsening_rate works on host arrays: no device is involved
+    import numpy as np
+
+    import oracle
+    import synth
+
+    chx = pytest.importorskip("paper_2101_06550_gb300")
+    t = np.sort(synth.uniform(4, 40, 1.0, 2.0))
+    F = np.exp(-t) + 2 + np.sin(3 * t)
+    got = chx.coarsening_rate(t, F)
+    want = oracle.coarsening_rate(t, F)
+    # both take the quadratic-interpolant derivative; they differ only in rounding,
+    # bounded by eps times the size of the three-point weights times |F|
+    h = np.min(np.diff(t))
+    bound = 64 * np.finfo(float).eps * (t / np.abs(F)) * (6 / h) * np.max(np.abs(F))
+    assert np.all(np.abs(got - want) <= bound)
+    for bad_t, bad_F in ((t[:2], F[:2]), (t[::-1].copy(), F), (t, np.where(np.arange(t.size) == 3, 0.0, F))):
+        with pytest.raises(chx.ChxError):
+            chx.coarsening_rate(bad_t, bad_F)
