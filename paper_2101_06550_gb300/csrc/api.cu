@@ -29,6 +29,18 @@ int cuda_check(cudaError_t e, const char* what) {
 
 int launch_check(const char* what) { return cuda_check(cudaGetLastError(), what); }
 
+unsigned balanced_block(size_t threads) {
+  static int sms[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int& n = sms[dev & 63];
+  if (n == 0 && cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    n = 152;
+  }
+  return threads < (size_t)128 * 16 * n ? 32u : 128u;
+}
+
 int hdr_init(PlanHdr* h, uint32_t magic) {
   h->magic = magic;
   h->d_status = nullptr;

@@ -77,11 +77,16 @@ __device__ __forceinline__ int wrap_near(int i, int n) {
 // RHS stencil pass.  Tile of 32 (i) x 32 (j) outputs of simulation blockIdx.z,
 // Cn/Cbar staged with a 2-point halo, M with a 1-point halo.  Output element
 // (i, j) of simulation z goes to rT[i * (G*ny) + z*ny + j].  gls[z] = gamma/dx^2.
+// The last phase maps j along the warp: its column reads of the shared tiles
+// (odd row pitches) are free of bank conflicts and its transposed stores are
+// coalesced, so the output needs no staging tile (31 KB of shared memory per
+// block: 7 blocks per SM).
 //
 // NOISE (Cahn-Hilliard-Cook, Sec. 7.6): adds (2/3) dt eta with
 // eta = sqrt(sigma / (dx dy dt)) div_h rho, the backward-difference divergence
 // of the deviates rho (planes rho^x, rho^y of nx*ny per simulation):
-// nkx (rho^x_ij - rho^x_{i-1,j}) + nky (rho^y_ij - rho^y_{i,j-1}).
+// nkx (rho^x_ij - rho^x_{i-1,j}) + nky (rho^y_ij - rho^y_{i,j-1}), formed with
+// coalesced row reads into a shared tile first.
 template <typename TC, typename TO, bool NOISE = false>
 __global__ void __launch_bounds__(kT* kBY) ch_rhs_kernel(const double* __restrict__ cn, const double* __restrict__ cp,
                                                          TO* __restrict__ rT, int nx, int ny, int G, TC rho, TC kap,
@@ -91,7 +96,7 @@ __global__ void __launch_bounds__(kT* kBY) ch_rhs_kernel(const double* __restric
   __shared__ TC s_cn[kT + 4][kT + 5];
   __shared__ TC s_cb[kT + 4][kT + 5];
   __shared__ TC s_m[kT + 2][kT + 3];
-  __shared__ TO s_o[kT][kT + 1];
+  __shared__ TC s_nz[NOISE ? kT : 1][kT + 1];
   const int z = blockIdx.z;
   const TC gl = gls[z];
   cn += (size_t)z * nx * ny;
@@ -106,6 +111,23 @@ __global__ void __launch_bounds__(kT* kBY) ch_rhs_kernel(const double* __restric
     s_cn[ly][lx] = a;
     s_cb[ly][lx] = fma(TC(2), a, -b);
   }
+  if (NOISE) {
+    const size_t N = (size_t)nx * ny;
+    const double* rx = dev + (size_t)z * 2 * N;
+    const double* ry = rx + N;
+    for (int idx = tid; idx < kT * kT; idx += kT * kBY) {
+      const int lj = idx / kT, li = idx % kT;
+      const int gi = i0 + li, gj = j0 + lj;
+      TC v = 0;
+      if (gi < nx && gj < ny) {
+        const size_t q = (size_t)gj * nx + gi;
+        const size_t qw = (size_t)gj * nx + (gi == 0 ? nx - 1 : gi - 1);
+        const size_t qs = (size_t)(gj == 0 ? ny - 1 : gj - 1) * nx + gi;
+        v = (TC)fma(nkx, rx[q] - rx[qw], nky * (ry[q] - ry[qs]));
+      }
+      s_nz[lj][li] = v;
+    }
+  }
   __syncthreads();
   for (int idx = tid; idx < (kT + 2) * (kT + 2); idx += kT * kBY) {
     const int ly = idx / (kT + 2) + 1, lx = idx % (kT + 2) + 1;
@@ -117,35 +139,19 @@ __global__ void __launch_bounds__(kT* kBY) ch_rhs_kernel(const double* __restric
     s_m[ly - 1][lx - 1] = fma(-gl, l, nl);
   }
   __syncthreads();
+  const size_t ldo = (size_t)G * ny;
 #pragma unroll
   for (int k = 0; k < kT / kBY; ++k) {
-    const int ly = threadIdx.y + k * kBY + 1, lx = threadIdx.x + 1;
+    const int li = threadIdx.y + k * kBY, lj = threadIdx.x;  // output (i0 + li, j0 + lj)
+    const int ly = lj + 1, lx = li + 1;
     TC l = s_m[ly][lx - 1] + s_m[ly][lx + 1];
     l = fma(rho, s_m[ly - 1][lx] + s_m[ly + 1][lx], l);
     l = fma(kap, s_m[ly][lx], l);
     const TC diff = s_cb[ly + 1][lx + 1] - s_cn[ly + 1][lx + 1];  // C^n - C^{n-1}
     TC o = fma(k2, l, -(k1 * diff));
-    if (NOISE) {
-      const int gi = i0 + lx - 1, gj = j0 + ly - 1;
-      if (gi < nx && gj < ny) {
-        const size_t N = (size_t)nx * ny;
-        const double* rx = dev + (size_t)z * 2 * N;
-        const double* ry = rx + N;
-        const size_t p = (size_t)gj * nx + gi;
-        const size_t pw = (size_t)gj * nx + (gi == 0 ? nx - 1 : gi - 1);
-        const size_t ps = (size_t)(gj == 0 ? ny - 1 : gj - 1) * nx + gi;
-        o += (TC)fma(nkx, rx[p] - rx[pw], nky * (ry[p] - ry[ps]));
-      }
-    }
-    s_o[lx - 1][ly - 1] = (TO)o;
-  }
-  __syncthreads();
-  const size_t ldo = (size_t)G * ny;
-#pragma unroll
-  for (int k = 0; k < kT / kBY; ++k) {
-    const int li = threadIdx.y + k * kBY, lj = threadIdx.x;
+    if (NOISE) o += s_nz[lj][li];
     const int gi = i0 + li, gj = j0 + lj;
-    if (gi < nx && gj < ny) rT[(size_t)gi * ldo + (size_t)z * ny + gj] = s_o[li][lj];
+    if (gi < nx && gj < ny) rT[(size_t)gi * ldo + (size_t)z * ny + gj] = (TO)o;
   }
 }
 
@@ -719,6 +725,7 @@ static int prepare_kernels() {
   int dev = 0;
   int rc = cuda_check(cudaGetDevice(&dev), "ch: cudaGetDevice");
   if (rc || dev < 0 || dev >= 64 || done[dev]) return rc;
+  balanced_block(0);  // reads the SM count now, outside any stream capture
   rc = cuda_check(cudaFuncSetAttribute(spike_local_staged_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024),
                   "ch: shared-memory opt-in");
@@ -840,8 +847,8 @@ static void launch_local(const TIn* f, TC* y, int ld, int nsys, const DirView<TC
     spike_local_staged_kernel<TC><<<dim3(nsys / 32, D.P, Z), 32, tile, st>>>((const TC*)f, y, ld, nsys, D, yb, fz, ybz,
                                                                            status);
   } else {
-    spike_local_kernel<TIn, TC><<<dim3(ceil_div(nsys, kSolveThreads), D.P, Z), kSolveThreads, 0, st>>>(f, y, ld, nsys, D,
-                                                                                                    yb, fz, ybz);
+    const unsigned blk = balanced_block((size_t)nsys * D.P * Z);
+    spike_local_kernel<TIn, TC><<<dim3(ceil_div(nsys, blk), D.P, Z), blk, 0, st>>>(f, y, ld, nsys, D, yb, fz, ybz);
   }
 }
 

@@ -174,9 +174,9 @@ extern "C" int ch1d_step(chx_ch1d_plan* p, double* c, int nsteps, void* stream) 
   if (!p || p->hdr.magic != kMagicCh1d) return fail(CHX_EINVAL, "ch1d_step: bad plan");
   if (!c || nsteps < 0) return fail(CHX_EINVAL, "ch1d_step: null field or nsteps %d < 0", nsteps);
   cudaStream_t st = (cudaStream_t)stream;
-  const unsigned grid = ceil_div(p->batch, kThreads);
+  const unsigned blk = balanced_block(p->batch), grid = ceil_div(p->batch, blk);
   for (int k = 0; k < nsteps; ++k)
-    ch1d_step_kernel<<<grid, kThreads, 0, st>>>(c, p->n, p->batch, p->alpha, p->d_fac, p->sinv[0], p->sinv[1],
+    ch1d_step_kernel<<<grid, blk, 0, st>>>(c, p->n, p->batch, p->alpha, p->d_fac, p->sinv[0], p->sinv[1],
                                                 p->sinv[2], p->sinv[3]);
   p->hdr.last_stream = st;
   return launch_check("ch1d_step");

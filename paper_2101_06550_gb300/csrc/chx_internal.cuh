@@ -37,6 +37,13 @@ __device__ __forceinline__ void set_status(int* st, int code) {
 
 inline unsigned ceil_div(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
 
+// Threads per block for one-thread-per-system kernels, whose time is set by the
+// busiest SM.  With few blocks per SM, 128-thread blocks leave some SMs a whole
+// block ahead of the rest (65536 threads = 512 blocks on 152 SMs: 4 on some,
+// 3 on others, 84% balance); single-warp blocks spread the warps to within one
+// of each other (96%).  Many blocks balance by themselves and keep 128.
+unsigned balanced_block(size_t threads);
+
 // ---------------------------------------------------------------------------
 // Host FP64 factorisation of one cyclic pentadiagonal system (Secs. 4.2.2-4.2.3).
 // Output arrays (each m = n-2 long): ralpha = 1/alpha, beta, eps (= a on rows

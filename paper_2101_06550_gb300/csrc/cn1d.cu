@@ -358,22 +358,22 @@ extern "C" int cn1d_step(chx_cn1d_plan* p, double* c, int nsteps, void* stream) 
   if (!p || p->hdr.magic != kMagicCn1d) return fail(CHX_EINVAL, "cn1d_step: bad plan");
   if (!c || nsteps < 0) return fail(CHX_EINVAL, "cn1d_step: null field or nsteps %d < 0", nsteps);
   cudaStream_t st = (cudaStream_t)stream;
-  const unsigned grid = ceil_div(p->batch, kThreads);
+  const unsigned blk = balanced_block(p->batch), grid = ceil_div(p->batch, blk);
   for (int k = 0; k < nsteps; ++k) {
     if (p->rewrite) {
       int rc = cn1d_reset_and_factor(p, st);
       if (rc) return rc;
       // the refactor records the inner plan's stream; the sweep follows on `st`
       if (p->order == 4)
-        cn_penta_kernel<true><<<grid, kThreads, 0, st>>>(c, p->n, p->batch, p->sigma, penta_plan_factors(p->penta), 0,
+        cn_penta_kernel<true><<<grid, blk, 0, st>>>(c, p->n, p->batch, p->sigma, penta_plan_factors(p->penta), 0,
                                                          0, 0, 0);
       else
-        cn_tri_kernel<true><<<grid, kThreads, 0, st>>>(c, p->n, p->batch, p->sigma, tri_plan_factors(p->tri));
+        cn_tri_kernel<true><<<grid, blk, 0, st>>>(c, p->n, p->batch, p->sigma, tri_plan_factors(p->tri));
     } else if (p->order == 4) {
-      cn_penta_kernel<false><<<grid, kThreads, 0, st>>>(c, p->n, p->batch, p->sigma, p->d_fac, p->sinv[0],
+      cn_penta_kernel<false><<<grid, blk, 0, st>>>(c, p->n, p->batch, p->sigma, p->d_fac, p->sinv[0],
                                                         p->sinv[1], p->sinv[2], p->sinv[3]);
     } else {
-      cn_tri_kernel<false><<<grid, kThreads, 0, st>>>(c, p->n, p->batch, p->sigma, p->d_fac);
+      cn_tri_kernel<false><<<grid, blk, 0, st>>>(c, p->n, p->batch, p->sigma, p->d_fac);
     }
   }
   p->hdr.last_stream = st;

@@ -480,10 +480,10 @@ void launch_ch_update_ff(const float* y1, const float* t1, const float* y2, cons
 
 void launch_penta_refine_ff(double* x, float* work, int n, int batch, const float* fac32, const float2* coef_ff,
                             const float* s32, cudaStream_t st) {
-  const unsigned grid = ceil_div(batch, kSolveThreads);
-  penta_solve_f32_from_f64_kernel<<<grid, kSolveThreads, 0, st>>>(x, work, n, batch, fac32, s32[0], s32[1], s32[2],
+  const unsigned blk = balanced_block(batch), grid = ceil_div(batch, blk);
+  penta_solve_f32_from_f64_kernel<<<grid, blk, 0, st>>>(x, work, n, batch, fac32, s32[0], s32[1], s32[2],
                                                                    s32[3]);
-  penta_refine_ff_kernel<<<grid, kSolveThreads, 0, st>>>(x, work, n, batch, fac32, coef_ff, s32[0], s32[1], s32[2],
+  penta_refine_ff_kernel<<<grid, blk, 0, st>>>(x, work, n, batch, fac32, coef_ff, s32[0], s32[1], s32[2],
                                                          s32[3]);
 }
 

@@ -260,12 +260,12 @@ void penta_plan_free(chx_penta_plan* p) {
 
 static int launch_per_system_factor(chx_penta_plan* p, const double* a, const double* b, const double* c,
                                     const double* d, const double* e, cudaStream_t st) {
-  const unsigned grid = ceil_div(p->batch, kThreads);
+  const unsigned blk = balanced_block(p->batch), grid = ceil_div(p->batch, blk);
   if (p->dtype == CHX_F64)
-    penta_factor_kernel<double><<<grid, kThreads, 0, st>>>(a, b, c, d, e, p->n, p->batch, (double*)p->d_fac,
+    penta_factor_kernel<double><<<grid, blk, 0, st>>>(a, b, c, d, e, p->n, p->batch, (double*)p->d_fac,
                                                             p->hdr.d_status);
   else
-    penta_factor_kernel<float><<<grid, kThreads, 0, st>>>(a, b, c, d, e, p->n, p->batch, (float*)p->d_fac,
+    penta_factor_kernel<float><<<grid, blk, 0, st>>>(a, b, c, d, e, p->n, p->batch, (float*)p->d_fac,
                                                            p->hdr.d_status);
   p->hdr.last_stream = st;
   return launch_check("penta_factor_kernel");
@@ -355,7 +355,7 @@ extern "C" int penta_cyclic_solve_batched(chx_penta_plan* p, void* rhs, int batc
   if (refine && p->mode == CHX_COEF_PER_SYSTEM)
     return fail(CHX_EUNSUPPORTED, "penta_cyclic_solve_batched: refine with PER_SYSTEM coefficients");
   cudaStream_t st = (cudaStream_t)stream;
-  const unsigned grid = ceil_div(batch, kThreads);
+  const unsigned blk = balanced_block(batch), grid = ceil_div(batch, blk);
   const double* S = p->sinv;
   const float* S32 = p->sinv32;
   if (refine) {
@@ -363,18 +363,18 @@ extern "C" int penta_cyclic_solve_batched(chx_penta_plan* p, void* rhs, int batc
   } else if (p->dtype == CHX_F64) {
     double* x = (double*)rhs;
     if (p->mode == CHX_COEF_PER_SYSTEM)
-      penta_solve_kernel<double, double, double, true><<<grid, kThreads, 0, st>>>(x, x, p->n, batch,
+      penta_solve_kernel<double, double, double, true><<<grid, blk, 0, st>>>(x, x, p->n, batch,
                                                                                  (const double*)p->d_fac, 0, 0, 0, 0);
     else
-      penta_solve_kernel<double, double, double, false><<<grid, kThreads, 0, st>>>(
+      penta_solve_kernel<double, double, double, false><<<grid, blk, 0, st>>>(
           x, x, p->n, batch, (const double*)p->d_fac, S[0], S[1], S[2], S[3]);
   } else {
     float* x = (float*)rhs;
     if (p->mode == CHX_COEF_PER_SYSTEM)
-      penta_solve_kernel<float, float, float, true><<<grid, kThreads, 0, st>>>(x, x, p->n, batch,
+      penta_solve_kernel<float, float, float, true><<<grid, blk, 0, st>>>(x, x, p->n, batch,
                                                                               (const float*)p->d_fac, 0, 0, 0, 0);
     else
-      penta_solve_kernel<float, float, float, false><<<grid, kThreads, 0, st>>>(
+      penta_solve_kernel<float, float, float, false><<<grid, blk, 0, st>>>(
           x, x, p->n, batch, (const float*)p->d_fac, S32[0], S32[1], S32[2], S32[3]);
   }
   p->hdr.last_stream = st;

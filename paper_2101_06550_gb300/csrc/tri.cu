@@ -160,12 +160,12 @@ void tri_plan_free(chx_tri_plan* p) {
 
 static int launch_tri_factor(chx_tri_plan* p, const double* a, const double* b, const double* c,
                              cudaStream_t st) {
-  const unsigned grid = ceil_div(p->batch, kThreads);
+  const unsigned blk = balanced_block(p->batch), grid = ceil_div(p->batch, blk);
   if (p->dtype == CHX_F64)
-    tri_factor_kernel<double><<<grid, kThreads, 0, st>>>(a, b, c, p->n, p->batch, (double*)p->d_fac,
+    tri_factor_kernel<double><<<grid, blk, 0, st>>>(a, b, c, p->n, p->batch, (double*)p->d_fac,
                                                           p->hdr.d_status);
   else
-    tri_factor_kernel<float><<<grid, kThreads, 0, st>>>(a, b, c, p->n, p->batch, (float*)p->d_fac,
+    tri_factor_kernel<float><<<grid, blk, 0, st>>>(a, b, c, p->n, p->batch, (float*)p->d_fac,
                                                          p->hdr.d_status);
   p->hdr.last_stream = st;
   return launch_check("tri_factor_kernel");
@@ -245,17 +245,17 @@ extern "C" int tri_cyclic_solve_batched(chx_tri_plan* p, void* rhs, int batch, v
   if (p->mode == CHX_COEF_PER_SYSTEM && batch != p->batch)
     return fail(CHX_EINVAL, "tri_cyclic_solve_batched: PER_SYSTEM batch must equal the factor batch %d", p->batch);
   cudaStream_t st = (cudaStream_t)stream;
-  const unsigned grid = ceil_div(batch, kThreads);
+  const unsigned blk = balanced_block(batch), grid = ceil_div(batch, blk);
   if (p->dtype == CHX_F64) {
     if (p->mode == CHX_COEF_PER_SYSTEM)
-      tri_solve_kernel<double, true><<<grid, kThreads, 0, st>>>((double*)rhs, p->n, batch, (const double*)p->d_fac);
+      tri_solve_kernel<double, true><<<grid, blk, 0, st>>>((double*)rhs, p->n, batch, (const double*)p->d_fac);
     else
-      tri_solve_kernel<double, false><<<grid, kThreads, 0, st>>>((double*)rhs, p->n, batch, (const double*)p->d_fac);
+      tri_solve_kernel<double, false><<<grid, blk, 0, st>>>((double*)rhs, p->n, batch, (const double*)p->d_fac);
   } else {
     if (p->mode == CHX_COEF_PER_SYSTEM)
-      tri_solve_kernel<float, true><<<grid, kThreads, 0, st>>>((float*)rhs, p->n, batch, (const float*)p->d_fac);
+      tri_solve_kernel<float, true><<<grid, blk, 0, st>>>((float*)rhs, p->n, batch, (const float*)p->d_fac);
     else
-      tri_solve_kernel<float, false><<<grid, kThreads, 0, st>>>((float*)rhs, p->n, batch, (const float*)p->d_fac);
+      tri_solve_kernel<float, false><<<grid, blk, 0, st>>>((float*)rhs, p->n, batch, (const float*)p->d_fac);
   }
   p->hdr.last_stream = st;
   return launch_check("tri_cyclic_solve_batched");
