@@ -47,9 +47,11 @@ struct chx_ch_plan {
   ChGroup g;
   double* d_partials;
   Prof* prof;
-  // two captured steps for multi-step calls, valid for these pointers
-  cudaGraphExec_t pair;
-  const void *pair_now, *pair_prev, *pair_work;
+  // Captured steps, valid for the pointers they were captured with: `pair`
+  // (two steps that leave C^n in c_now) and `one` (one role-keeping step).
+  cudaGraphExec_t pair, one;
+  const void *graph_now, *graph_prev, *graph_work;
+  const void *seen_now, *seen_prev, *seen_work;  // the previous call's pointers
   cudaStream_t cap;
 };
 
@@ -927,6 +929,7 @@ void group_step(ChGroup* g, int gact, double* cur, double* prev, void* work, int
 void ch_plan_free(chx_ch_plan* p) {
   if (!p) return;
   if (p->pair) cudaGraphExecDestroy(p->pair);
+  if (p->one) cudaGraphExecDestroy(p->one);
   if (p->cap) cudaStreamDestroy(p->cap);
   group_free(&p->g);
   if (p->d_partials) cudaFree(p->d_partials);
@@ -982,34 +985,48 @@ extern "C" int ch_step(chx_ch_plan* p, double* c_now, double* c_prev, void* work
     return fail(CHX_EINVAL, "ch_step: c_now, c_prev and work must not overlap");
   cudaStream_t st = (cudaStream_t)stream;
   double *cur = c_now, *prev = c_prev;
-  if (nsteps >= 4 && !p->prof->on) {
-    // Pairs of steps from a CUDA graph: a pair starts and ends with C^n in c_now.
+  // Graphs replace the per-kernel launches when the call repeats the previous
+  // call's pointers (a loop of single steps) or runs four or more steps; a
+  // one-off call with new pointers launches eagerly instead of capturing.
+  const bool same = p->seen_now == c_now && p->seen_prev == c_prev && p->seen_work == work;
+  p->seen_now = c_now;
+  p->seen_prev = c_prev;
+  p->seen_work = work;
+  if (nsteps >= 1 && !p->prof->on && (same || nsteps >= 4)) {
     int rc = CHX_OK;
-    if (!p->pair || p->pair_now != c_now || p->pair_prev != c_prev || p->pair_work != work) {
+    if (p->graph_now != c_now || p->graph_prev != c_prev || p->graph_work != work) {
       if (p->pair) cudaGraphExecDestroy(p->pair);
-      p->pair = nullptr;
-      if (!p->cap) rc = cuda_check(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking), "ch_step: stream");
-      cudaGraph_t graph = nullptr;
-      if (!rc) rc = cuda_check(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal), "ch_step: capture");
-      if (!rc) {
-        group_step(&p->g, 1, c_now, c_prev, work, 0, p->cap, nullptr, p->hdr.d_status);
-        group_step(&p->g, 1, c_prev, c_now, work, 0, p->cap, nullptr, p->hdr.d_status);
-        rc = cuda_check(cudaStreamEndCapture(p->cap, &graph), "ch_step: end capture");
-      }
-      if (!rc) rc = cuda_check(cudaGraphInstantiate(&p->pair, graph, 0), "ch_step: instantiate");
-      if (graph) cudaGraphDestroy(graph);
-      if (rc) {
-        p->pair = nullptr;
-        return rc;
-      }
-      p->pair_now = c_now;
-      p->pair_prev = c_prev;
-      p->pair_work = work;
+      if (p->one) cudaGraphExecDestroy(p->one);
+      p->pair = p->one = nullptr;
+      p->graph_now = c_now;
+      p->graph_prev = c_prev;
+      p->graph_work = work;
     }
+    auto capture = [&](cudaGraphExec_t* exec, int two) -> int {
+      int r = CHX_OK;
+      if (!p->cap) r = cuda_check(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking), "ch_step: stream");
+      cudaGraph_t graph = nullptr;
+      if (!r) r = cuda_check(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal), "ch_step: capture");
+      if (!r) {
+        if (two) {
+          group_step(&p->g, 1, c_now, c_prev, work, 0, p->cap, nullptr, p->hdr.d_status);
+          group_step(&p->g, 1, c_prev, c_now, work, 0, p->cap, nullptr, p->hdr.d_status);
+        } else {
+          group_step(&p->g, 1, c_now, c_prev, work, 1, p->cap, nullptr, p->hdr.d_status);
+        }
+        r = cuda_check(cudaStreamEndCapture(p->cap, &graph), "ch_step: end capture");
+      }
+      if (!r) r = cuda_check(cudaGraphInstantiate(exec, graph, 0), "ch_step: instantiate");
+      if (graph) cudaGraphDestroy(graph);
+      if (r) *exec = nullptr;
+      return r;
+    };
     const int pairs = nsteps / 2;
+    if (pairs && !p->pair) rc = capture(&p->pair, 1);
+    if (!rc && (nsteps & 1) && !p->one) rc = capture(&p->one, 0);
     for (int k = 0; k < pairs && !rc; ++k) rc = cuda_check(cudaGraphLaunch(p->pair, st), "ch_step: graph launch");
+    if (!rc && (nsteps & 1)) rc = cuda_check(cudaGraphLaunch(p->one, st), "ch_step: graph launch");
     if (rc) return rc;
-    if (nsteps & 1) group_step(&p->g, 1, c_now, c_prev, work, 1, st, p->prof, p->hdr.d_status);
     p->hdr.last_stream = st;
     return launch_check("ch_step");
   }

@@ -241,21 +241,40 @@ def test_ch_step_rejects_overlap_and_alignment():
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_ch_step_graph_pairs_match_single_steps(precision):
-    # nsteps >= 4 replays a captured two-step graph; it must give the same bits
-    # as single-step calls, for even and odd counts and after a pointer change
+    # Repeated pointers or nsteps >= 4 replay captured graphs (two-step pairs and
+    # a role-keeping single step); they must give the same bits as the eager
+    # launches (profiling on forces those), for even and odd counts, for loops
+    # of single steps, and after a pointer change.
     chx = _chx()
     n = 96
     c0 = synth.field(12, n, n, -0.1, 0.1)
     plan = chx.ChPlan(n, n, 2 * np.pi, 2 * np.pi, 0.01, 1e-3, precision)
     work = plan.alloc_work(DEV)
-    for nsteps in (4, 5, 9):
+
+    def eager(nsteps):
+        c = torch.from_numpy(c0).to(DEV)
+        d = c.clone()
+        plan.profile(True)
+        for _ in range(nsteps):
+            plan.step(c, d, work, 1)
+        plan.profile(False)
+        plan.profile_read(reset=True)
+        return c, d
+
+    for nsteps in (1, 2, 3, 4, 5, 9):
         a = torch.from_numpy(c0).to(DEV)
         b = a.clone()
         plan.step(a, b, work, nsteps)
-        c = torch.from_numpy(c0).to(DEV)
-        d = c.clone()
-        for _ in range(nsteps):
-            plan.step(c, d, work, 1)
+        c, d = eager(nsteps)
         torch.cuda.synchronize()
         assert torch.equal(a, c) and torch.equal(b, d), nsteps
+        e = torch.from_numpy(c0).to(DEV)  # a loop of single steps on the same pointers
+        f = e.clone()
+        for _ in range(nsteps):
+            plan.step(e, f, work, 1)
+        assert torch.equal(e, c) and torch.equal(f, d), nsteps
+        if nsteps in (2, 3):  # short multi-step calls that repeat the previous pointers
+            plan.step(e, f, work, nsteps)
+            g, h = eager(2 * nsteps)
+            assert torch.equal(e, g) and torch.equal(f, h), nsteps
     plan.sync_status()
