@@ -105,14 +105,17 @@ __global__ void __launch_bounds__(kT* kBY) ch_rhs_kernel(const double* __restric
   cp += (size_t)z * nx * ny;
   const int i0 = blockIdx.x * kT, j0 = blockIdx.y * kT;
   const int tid = threadIdx.y * kT + threadIdx.x;
-  for (int idx = tid; idx < (kT + 4) * (kT + 4); idx += kT * kBY) {
-    const int ly = idx / (kT + 4), lx = idx % (kT + 4);
+  // Phases 1 and 2 give each warp whole 32-column rows (bank-conflict free),
+  // then sweep the few columns past 32 with the first threads.
+  auto stage = [&](int ly, int lx) {
     const int gi = wrap_near(i0 - 2 + lx, nx), gj = wrap_near(j0 - 2 + ly, ny);
     const size_t p = (size_t)gj * nx + gi;
     const TC a = (TC)cn[p], b = (TC)cp[p];
     s_cn[ly][lx] = a;
     s_cb[ly][lx] = fma(TC(2), a, -b);
-  }
+  };
+  for (int ly = threadIdx.y; ly < kT + 4; ly += kBY) stage(ly, threadIdx.x);
+  if (tid < 4 * (kT + 4)) stage(tid >> 2, kT + (tid & 3));
   if (NOISE) {
     const size_t N = (size_t)nx * ny;
     const double* rx = dev + (size_t)z * 2 * N;
@@ -131,15 +134,16 @@ __global__ void __launch_bounds__(kT* kBY) ch_rhs_kernel(const double* __restric
     }
   }
   __syncthreads();
-  for (int idx = tid; idx < (kT + 2) * (kT + 2); idx += kT * kBY) {
-    const int ly = idx / (kT + 2) + 1, lx = idx % (kT + 2) + 1;
+  auto mstage = [&](int ly, int lx) {  // M = C^3 - C - gamma Lap Cbar on the tile plus one halo ring
     TC l = s_cb[ly][lx - 1] + s_cb[ly][lx + 1];
     l = fma(rho, s_cb[ly - 1][lx] + s_cb[ly + 1][lx], l);
     l = fma(kap, s_cb[ly][lx], l);
     const TC c = s_cn[ly][lx];
     const TC nl = c * fma(c, c, TC(-1));
     s_m[ly - 1][lx - 1] = fma(-gl, l, nl);
-  }
+  };
+  for (int ly = 1 + threadIdx.y; ly <= kT + 2; ly += kBY) mstage(ly, 1 + threadIdx.x);
+  if (tid < 2 * (kT + 2)) mstage(1 + (tid >> 1), kT + 1 + (tid & 1));
   __syncthreads();
   const size_t ldo = (size_t)G * ny;
 #pragma unroll
