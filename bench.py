@@ -37,7 +37,7 @@ WORKLOAD = "ch2d_periodic_2048sq_gamma0.005_dt5e-4"
 # DRAM bytes (read + write) per launch of the FP64 right-hand-side kernel on this
 # workload, from an ncu capture of the current kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum, mean of 3 launches; the written field partly stays in L2)
-RHS_TRAFFIC_BYTES = 67.22e6 + 4.67e6
+RHS_TRAFFIC_BYTES = 67.21e6 + 4.01e6  # ncu: dram__bytes_read + write per ch_rhs launch (mean of 3)
 
 
 def _peaks():
