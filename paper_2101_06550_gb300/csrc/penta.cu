@@ -137,6 +137,9 @@ __global__ void __launch_bounds__(kThreads) penta_solve_kernel(const TIn* in, TW
 // PER_SYSTEM factorisation, one thread per system; coefficients interleaved.
 // Forward pass: LU of E (paper factor steps), G = L^{-1} k and y = R^{-T} h in
 // registers; backward pass: q = L^{-T} y, S = D - q^T k; tail inverse.
+// Only rows 0, 1, m-2 and m-1 of E touch the periodic corners (the k columns,
+// the h entries and the wrapped band entries); the rows between take a
+// straight-line path with k = h = 0.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) penta_factor_kernel(const double* __restrict__ a,
                                                                 const double* __restrict__ b,
@@ -156,30 +159,19 @@ __global__ void __launch_bounds__(kThreads) penta_factor_kernel(const double* __
   double G01 = 0, G02 = 0, G11 = 0, G12 = 0;  // G rows r-1, r-2
   double y01 = 0, y02 = 0, y11 = 0, y12 = 0;  // y rows r-1, r-2
   bool bad = false;
-  for (int r = 0; r < m; ++r) {
-    double band[5] = {0, 0, 0, 0, 0}, k0 = 0, k1 = 0;
-    for (int o = -2; o <= 2; ++o) {
-      const double v = co[o + 2][(size_t)r * B];
-      const int cc = r + o;
-      if (cc >= 0 && cc < m) band[o + 2] = v;
-      else if (col_of(r, o, n) == m) k0 += v;
-      else k1 += v;
-    }
-    const double ar = band[0];
-    const double br = band[1] - ar * ga2;
-    const double al = band[2] - ar * de2 - br * ga1;
-    const double scale = fabs(band[0]) + fabs(band[1]) + fabs(band[2]) + fabs(band[3]) + fabs(band[4]);
+  // one forward row; b0..b4 the row's entries on E-columns r-2..r+2 (0 off E)
+  auto fwd = [&](int r, double b0, double b1, double b2, double b3, double b4, double k0, double k1, double h0,
+                 double h1) {
+    const double ar = b0;
+    const double br = b1 - ar * ga2;
+    const double al = b2 - ar * de2 - br * ga1;
+    const double scale = fabs(b0) + fabs(b1) + fabs(b2) + fabs(b3) + fabs(b4);
     if (!(fabs(al) > tol * scale)) bad = true;
     const double ra = 1.0 / al;
-    const double ga = (band[3] - br * de1) * ra;
-    const double de = band[4] * ra;
+    const double ga = (b3 - br * de1) * ra;
+    const double de = b4 * ra;
     const double G0 = (k0 - ar * G02 - br * G01) * ra;
     const double G1 = (k1 - ar * G12 - br * G11) * ra;
-    // h column entries of the last two rows on E-column r
-    double h0 = 0, h1 = 0;
-    for (int q = 0; q < 2; ++q)
-      for (int o = -2; o <= 2; ++o)
-        if (col_of(m + q, o, n) == r) (q ? h1 : h0) += co[o + 2][(size_t)(m + q) * B];
     const double y0 = h0 - ga1 * y01 - de2 * y02;
     const double y1 = h1 - ga1 * y11 - de2 * y12;
     FST(0, r) = (T)ra; FST(1, r) = (T)br; FST(2, r) = (T)ar; FST(3, r) = (T)ga; FST(4, r) = (T)de;
@@ -187,37 +179,76 @@ __global__ void __launch_bounds__(kThreads) penta_factor_kernel(const double* __
     ga2 = ga1; ga1 = ga; de2 = de1; de1 = de;
     G02 = G01; G01 = G0; G12 = G11; G11 = G1;
     y02 = y01; y01 = y0; y12 = y11; y11 = y1;
+  };
+  // a corner row: entries whose column wraps or falls on the tail go to k0/k1
+  auto fwd_corner = [&](int r) {
+    double bnd[5], k0 = 0, k1 = 0, h0 = 0, h1 = 0;
+#pragma unroll
+    for (int o = -2; o <= 2; ++o) {
+      const double v = co[o + 2][(size_t)r * B];
+      const int cc = r + o;
+      const bool in = cc >= 0 && cc < m;
+      bnd[o + 2] = in ? v : 0.0;
+      if (!in) {
+        if (col_of(r, o, n) == m) k0 += v;
+        else k1 += v;
+      }
+    }
+    // h: entries of the last two rows (m, m + 1) on E-column r
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int o = -2; o <= 2; ++o)
+        if (col_of(m + q, o, n) == r) (q ? h1 : h0) += co[o + 2][(size_t)(m + q) * B];
+    fwd(r, bnd[0], bnd[1], bnd[2], bnd[3], bnd[4], k0, k1, h0, h1);
+  };
+  const int lo = m < 2 ? m : 2, hi = m - 2 > lo ? m - 2 : lo;  // interior rows [lo, hi)
+  for (int r = 0; r < lo; ++r) fwd_corner(r);
+  for (int r = lo; r < hi; ++r) {
+    const size_t o = (size_t)r * B;
+    fwd(r, co[0][o], co[1][o], co[2][o], co[3][o], co[4][o], 0.0, 0.0, 0.0, 0.0);
   }
+  for (int r = hi; r < m; ++r) fwd_corner(r);
   double q01 = 0, q02 = 0, q11 = 0, q12 = 0;  // q rows r+1, r+2
   double be1 = 0, ep2 = 0, ep1 = 0;           // beta_{r+1}, eps_{r+2}, eps_{r+1}
   double S00 = 0, S01 = 0, S10 = 0, S11 = 0;  // accumulates q^T k
-  for (int r = m - 1; r >= 0; --r) {
+  auto bwd = [&](int r, bool corner) {
     const double ra = (double)FST(0, r);
     const double q0 = ((double)FST(5, r) - be1 * q01 - ep2 * q02) * ra;
     const double q1 = ((double)FST(6, r) - be1 * q11 - ep2 * q12) * ra;
     FST(5, r) = (T)q0;
     FST(6, r) = (T)q1;
-    double k0 = 0, k1 = 0;
-    for (int o = -2; o <= 2; ++o) {
-      const int cc = r + o;
-      if (cc >= 0 && cc < m) continue;
-      const double v = co[o + 2][(size_t)r * B];
-      if (col_of(r, o, n) == m) k0 += v;
-      else k1 += v;
+    if (corner) {
+      double k0 = 0, k1 = 0;
+#pragma unroll
+      for (int o = -2; o <= 2; ++o) {
+        const int cc = r + o;
+        if (cc >= 0 && cc < m) continue;
+        const double v = co[o + 2][(size_t)r * B];
+        if (col_of(r, o, n) == m) k0 += v;
+        else k1 += v;
+      }
+      S00 += q0 * k0; S01 += q0 * k1; S10 += q1 * k0; S11 += q1 * k1;
     }
-    S00 += q0 * k0; S01 += q0 * k1; S10 += q1 * k0; S11 += q1 * k1;
     q02 = q01; q01 = q0; q12 = q11; q11 = q1;
     ep2 = ep1;
     ep1 = (double)FST(2, r);
     be1 = (double)FST(1, r);
-  }
-  double D[2][2] = {{0, 0}, {0, 0}};
+  };
+  for (int r = m - 1; r >= hi; --r) bwd(r, true);
+  for (int r = hi - 1; r >= lo; --r) bwd(r, false);
+  for (int r = lo - 1; r >= 0; --r) bwd(r, true);
+  double D00 = 0, D01 = 0, D10 = 0, D11 = 0;
+#pragma unroll
   for (int q = 0; q < 2; ++q)
+#pragma unroll
     for (int o = -2; o <= 2; ++o) {
       const int cc = col_of(m + q, o, n);
-      if (cc >= m) D[q][cc - m] += co[o + 2][(size_t)(m + q) * B];
+      const double v = cc >= m ? co[o + 2][(size_t)(m + q) * B] : 0.0;
+      if (cc == m) (q ? D10 : D00) += v;
+      else if (cc == m + 1) (q ? D11 : D01) += v;
     }
-  const double A00 = D[0][0] - S00, A01 = D[0][1] - S01, A10 = D[1][0] - S10, A11 = D[1][1] - S11;
+  const double A00 = D00 - S00, A01 = D01 - S01, A10 = D10 - S10, A11 = D11 - S11;
   const double det = A00 * A11 - A01 * A10;
   if (!(fabs(det) > tol * (fabs(A00 * A11) + fabs(A01 * A10)))) bad = true;
   const size_t base = (size_t)9 * m * B;

@@ -134,10 +134,11 @@ __global__ void __launch_bounds__(kThreads) tri_factor_kernel(const double* __re
   const double vz = zfirst - rb * zlast;
   const double den = 1.0 + vz;
   if (!(fabs(den) > tol * (1.0 + fabs(vz)))) bad = true;
+  const double rden = 1.0 / den;  // one division, not one per row
   double w = 1.0;
   for (int k = 0; k < n; ++k) {
-    double om = w / den;
-    if (k == n - 1) om -= rb / den;
+    double om = w * rden;
+    if (k == n - 1) om -= rb * rden;
     FST(4, k) = (T)om;
     w = -(double)FST(2, k) * w;
   }
