@@ -292,8 +292,9 @@ int cn1d_step(chx_cn1d_plan* plan, double* c, int nsteps, void* stream);
  * the ensemble's dt and precision on an n x n grid of side l.
  *  - A group holds simulations with the same (n, l): packed device-resident
  *    state (C^n, C^{n-1}) for `capacity` slots, per-slot LHS factors (so the
- *    slots may have different gamma), and one set of batched launches per step.  Only ens_create and ens_group_create
- *    allocate device memory; ens_group_create fails with CHX_ENOMEM when the
+ *    slots may have different gamma), and one set of batched launches per step.
+ *    Device memory is allocated only by ens_create, ens_group_create and the
+ *    first ens_group_set_cook / ens_group_observables of a group; ens_group_create fails with CHX_ENOMEM when the
  *    group would take the ensemble past hbm_budget_bytes (0 = no budget).
  *  - Slots [0, active) of each group are stepped (ens_group_set_active); the
  *    caller keeps active simulations packed with ens_slot_move.  A simulation's
@@ -309,13 +310,23 @@ int cn1d_step(chx_cn1d_plan* plan, double* c, int nsteps, void* stream);
  *  - ens_autotune times `trial` steps per candidate segment count of a group's
  *    partitioned sweeps and keeps the fastest; the simulations' state is saved
  *    and restored, so the call changes no result other than by rounding order.
+ *  - ens_group_set_cook turns on the Cahn-Hilliard-Cook forcing of ch_cook_run
+ *    (Sec. 7.6) for every slot of a group (CHX_PREC_F64 ensembles only, else
+ *    CHX_EUNSUPPORTED): each later step of the group first draws the deviates
+ *    of slot s with simulation id s, key seed, at the group's step counter
+ *    (starting at step0 and advanced on the device, so graph replays draw
+ *    fresh deviates), then takes the forced step.  It allocates the group's
+ *    deviate scratch (2 capacity n^2 doubles, counted against the budget) on
+ *    first use and synchronises the device; sigma = 0 turns the forcing off
+ *    and frees the scratch.
  * Destroy with chx_plan_destroy; chx_sync_status works on the ensemble too.
- * Errors: CHX_EINVAL (bad ids, sizes, slots), CHX_ENOMEM, CHX_ECUDA.
+ * Errors: CHX_EINVAL (bad ids, sizes, slots), CHX_ENOMEM, CHX_EUNSUPPORTED, CHX_ECUDA.
  */
 int ens_create(chx_ens** ens, int precision, double dt, size_t hbm_budget_bytes);
 int ens_group_create(chx_ens* ens, int n, double l, double gamma, int capacity, int* group_id);
 int ens_group_destroy(chx_ens* ens, int group_id);
 int ens_group_set_active(chx_ens* ens, int group_id, int active);
+int ens_group_set_cook(chx_ens* ens, int group_id, double sigma, uint64_t seed, uint64_t step0);
 int ens_slot_load(chx_ens* ens, int group_id, int slot, const double* c0, const double* cm1, double gamma,
                   void* stream);
 int ens_slot_read(chx_ens* ens, int group_id, int slot, double* c_now, double* c_prev, void* stream);

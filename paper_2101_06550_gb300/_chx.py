@@ -28,7 +28,7 @@ EXPORTS = ("chx_status_string", "chx_last_error", "chx_version", "stencil_apply_
            "penta_cyclic_refactor", "penta_cyclic_solve_batched", "tri_cyclic_factor", "tri_cyclic_refactor",
            "tri_cyclic_solve_batched", "ch_plan_create", "ch_work_bytes", "ch_step", "ch_diagnostics",
            "ch_diagnostics_noalloc", "ch1d_plan_create", "ch1d_step", "cn1d_plan_create", "cn1d_step", "ch_noise_normals", "ch_step_noise", "ch_cook_run", "ch_observables", "ens_group_observables", "chx_coarsening_rate", "ch_profile", "ch_profile_read", "ch_profile_slot_name", "ens_create",
-           "ens_group_create", "ens_group_destroy", "ens_group_set_active", "ens_slot_load", "ens_slot_read",
+           "ens_group_create", "ens_group_destroy", "ens_group_set_active", "ens_group_set_cook", "ens_slot_load", "ens_slot_read",
            "ens_slot_move", "ens_step", "ens_group_step", "ens_autotune", "ens_info", "ens_bytes_used",
            "chx_sync_status", "chx_plan_destroy")
 
@@ -86,6 +86,7 @@ def lib():
         "ens_group_create": (i, [_P, i, d, d, i, ctypes.POINTER(i)]),
         "ens_group_destroy": (i, [_P, i]),
         "ens_group_set_active": (i, [_P, i, i]),
+        "ens_group_set_cook": (i, [_P, i, d, ctypes.c_uint64, ctypes.c_uint64]),
         "ens_slot_load": (i, [_P, i, i, _P, _P, d, _P]),
         "ens_slot_read": (i, [_P, i, i, _P, _P, _P]),
         "ens_slot_move": (i, [_P, i, i, i, _P]),
@@ -428,6 +429,10 @@ class Ensemble(_Plan):
 
     def set_active(self, gid, active):
         _check(lib().ens_group_set_active(self._handle, gid, active))
+
+    def set_cook(self, gid, sigma, seed=0, step0=0):
+        """Cahn-Hilliard-Cook forcing for every slot of group gid (slot s draws with simulation id s)."""
+        _check(lib().ens_group_set_cook(self._handle, int(gid), float(sigma), int(seed), int(step0)))
 
     def load(self, gid, slot, c0, cm1=None, gamma=-1.0, stream=None):
         n = self.groups[gid][0]

@@ -1097,7 +1097,7 @@ extern "C" int ch_cook_run(chx_ch_plan* p, double* c_now, double* c_prev, void* 
   double *cur = c_now, *prev = c_prev;
   for (int s = 0; s < nsteps; ++s) {
     const int keep = s == nsteps - 1 && cur == c_now;
-    rc = launch_noise_normals(rho, p->g.nx, p->g.ny, 1, seed, sim, step0 + (uint64_t)s, st);
+    rc = launch_noise_normals(rho, p->g.nx, p->g.ny, 1, seed, sim, step0 + (uint64_t)s, nullptr, st);
     if (rc) return rc;
     p->g.noise = rho;
     group_step(&p->g, 1, cur, prev, work, keep, st, p->prof, p->hdr.d_status);

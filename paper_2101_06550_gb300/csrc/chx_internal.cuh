@@ -72,9 +72,12 @@ int tri_factor_host(int n, const double* a, const double* b, const double* c, si
 const double* penta_plan_factors(const chx_penta_plan* p);
 const double* tri_plan_factors(const chx_tri_plan* p);
 
-// Cahn-Hilliard-Cook deviates for G consecutive simulations sim0.. (noise.cu).
+// Cahn-Hilliard-Cook deviates for G consecutive simulations sim0.. (noise.cu);
+// the step index comes from *d_step when d_step is not null.
 int launch_noise_normals(double* rho, int nx, int ny, int G, uint64_t seed, uint64_t sim0, uint64_t step,
-                         cudaStream_t st);
+                         const uint64_t* d_step, cudaStream_t st);
+// *d_step += 1 on the stream.
+int launch_step_advance(uint64_t* d_step, cudaStream_t st);
 
 // Plain non-cyclic pentadiagonal LU (paper factor steps) of the m x m Toeplitz
 // band (a, b, c, d, e); ralpha, beta, gam, del of length m.

@@ -37,6 +37,13 @@ struct EnsGroup {
   std::vector<double> slot_gamma;           // gamma each slot is factorised for
   int* status = nullptr;                    // the ensemble's device status word
   bool live = false;
+  // Cahn-Hilliard-Cook forcing (ens_group_set_cook): deviates of every slot,
+  // drawn each step with the device step counter, then the forced step
+  double sigma = 0;
+  uint64_t seed = 0;
+  double* d_rho = nullptr;                  // capacity * 2 * n * n doubles
+  uint64_t* d_step = nullptr;
+  size_t cook_bytes = 0;
 };
 
 }  // namespace
@@ -63,6 +70,8 @@ void free_group(EnsGroup* G) {
   cudaFree(G->d_state[0]);
   cudaFree(G->d_state[1]);
   cudaFree(G->d_work);
+  cudaFree(G->d_rho);
+  cudaFree(G->d_step);
   if (G->stream) cudaStreamDestroy(G->stream);
   if (G->done) cudaEventDestroy(G->done);
   delete G;
@@ -82,9 +91,9 @@ void drop_graph(chx_ens* e) {
 
 void step_group(EnsGroup* G, cudaStream_t st) {
   if (G->active < 1) return;
-  const size_t N = (size_t)G->n * G->n;
-  (void)N;
+  if (G->sigma > 0) launch_noise_normals(G->d_rho, G->n, G->n, G->active, G->seed, 0, 0, G->d_step, st);
   group_step(&G->g, G->active, G->d_state[G->cur], G->d_state[1 - G->cur], G->d_work, 0, st, nullptr, G->status);
+  if (G->sigma > 0) launch_step_advance(G->d_step, st);
   G->cur = 1 - G->cur;
 }
 
@@ -276,6 +285,51 @@ extern "C" int ens_slot_move(chx_ens* e, int group_id, int from, int to, void* s
   return rc;
 }
 
+extern "C" int ens_group_set_cook(chx_ens* e, int group_id, double sigma, uint64_t seed, uint64_t step0) {
+  EnsGroup* G = get_group(e, group_id);
+  if (!G || !(sigma >= 0) || !isfinite(sigma)) return fail(CHX_EINVAL, "ens_group_set_cook: bad argument");
+  if (e->precision != CHX_PREC_F64)
+    return fail(CHX_EUNSUPPORTED, "ens_group_set_cook: the forcing is implemented for CHX_PREC_F64 ensembles");
+  int rc = cuda_check(cudaDeviceSynchronize(), "ens_group_set_cook: synchronize");
+  if (rc) return rc;
+  if (sigma == 0) {
+    cudaFree(G->d_rho);
+    cudaFree(G->d_step);
+    G->d_rho = nullptr;
+    G->d_step = nullptr;
+    e->used -= G->cook_bytes;
+    G->cook_bytes = 0;
+    G->sigma = 0;
+    G->g.noise = nullptr;
+    drop_graph(e);
+    return CHX_OK;
+  }
+  if (!G->d_rho) {
+    const size_t bytes = 2 * (size_t)G->capacity * G->n * G->n * sizeof(double) + 256;
+    if (e->budget && e->used + bytes > e->budget)
+      return fail(CHX_ENOMEM, "ens_group_set_cook: %zu bytes of deviates over the HBM budget", bytes);
+    if (cudaMalloc(&G->d_rho, bytes - 256) != cudaSuccess || cudaMalloc(&G->d_step, sizeof(uint64_t)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(G->d_rho);
+      G->d_rho = nullptr;
+      G->d_step = nullptr;
+      return fail(CHX_ENOMEM, "ens_group_set_cook: device allocation of %zu bytes", bytes);
+    }
+    G->cook_bytes = bytes;
+    e->used += bytes;
+  }
+  rc = cuda_check(cudaMemcpy(G->d_step, &step0, sizeof(uint64_t), cudaMemcpyHostToDevice), "ens_group_set_cook");
+  if (rc) return rc;
+  G->sigma = sigma;
+  G->seed = seed;
+  const double amp = sqrt(sigma / (G->g.dx * G->g.dy * G->g.dt));
+  G->g.noise = G->d_rho;
+  G->g.nkx = (2.0 / 3.0) * G->g.dt * amp / G->g.dx;
+  G->g.nky = (2.0 / 3.0) * G->g.dt * amp / G->g.dy;
+  drop_graph(e);
+  return CHX_OK;
+}
+
 extern "C" int ens_group_set_active(chx_ens* e, int group_id, int active) {
   EnsGroup* G = get_group(e, group_id);
   if (!G || active < 0 || active > G->capacity) return fail(CHX_EINVAL, "ens_group_set_active: bad argument");
@@ -384,8 +438,13 @@ extern "C" int ens_autotune(chx_ens* e, int group_id, int trial, int* px_out, in
       group_free(&ng);
       return rc;
     }
+    const double* noise = G->g.noise;
+    const double nkx = G->g.nkx, nky = G->g.nky;
     group_free(&G->g);
     G->g = ng;
+    G->g.noise = noise;  // the group's forcing carries over to the new factors
+    G->g.nkx = nkx;
+    G->g.nky = nky;
     drop_graph(e);
   }
   if (px_out) *px_out = G->g.X.P;

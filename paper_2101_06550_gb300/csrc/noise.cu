@@ -52,8 +52,12 @@ __device__ __forceinline__ void box_muller(uint64_t wa, uint64_t wb, double* zx,
 }
 
 // rho: G fields of [rho^x (nx*ny), rho^y (nx*ny)]; field z uses key (seed, sim0 + z).
+// The step index is `step`, or *d_step when d_step is given (a device counter
+// that captured graphs advance with step_advance_kernel).
 __global__ void __launch_bounds__(kThreads) noise_normals_kernel(double* __restrict__ rho, size_t np, uint64_t seed,
-                                                                 uint64_t sim0, uint64_t step) {
+                                                                 uint64_t sim0, uint64_t step,
+                                                                 const uint64_t* __restrict__ d_step) {
+  if (d_step) step = *d_step;
   const size_t pairs = (np + 1) / 2;
   const int z = blockIdx.y;
   double* rx = rho + (size_t)z * 2 * np;
@@ -73,23 +77,30 @@ __global__ void __launch_bounds__(kThreads) noise_normals_kernel(double* __restr
   }
 }
 
+__global__ void step_advance_kernel(uint64_t* d_step) { *d_step += 1; }
+
 }  // namespace
 
 namespace chx {
+int launch_step_advance(uint64_t* d_step, cudaStream_t st) {
+  step_advance_kernel<<<1, 1, 0, st>>>(d_step);
+  return launch_check("noise step counter");
+}
+
 int launch_noise_normals(double* rho, int nx, int ny, int G, uint64_t seed, uint64_t sim0, uint64_t step,
-                         cudaStream_t st) {
+                         const uint64_t* d_step, cudaStream_t st) {
   const size_t np = (size_t)nx * ny, pairs = (np + 1) / 2;
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const size_t want = ceil_div(pairs, (size_t)kThreads), cap = (size_t)sms * 8;
   const dim3 grid((unsigned)(want < cap ? want : cap), (unsigned)G);
-  noise_normals_kernel<<<grid, kThreads, 0, st>>>(rho, np, seed, sim0, step);
+  noise_normals_kernel<<<grid, kThreads, 0, st>>>(rho, np, seed, sim0, step, d_step);
   return launch_check("noise_normals");
 }
 }  // namespace chx
 
 extern "C" int ch_noise_normals(double* rho, int nx, int ny, uint64_t seed, uint64_t sim, uint64_t step, void* stream) {
   if (!rho || nx < 1 || ny < 1) return fail(CHX_EINVAL, "ch_noise_normals: rho %p, nx %d, ny %d", (void*)rho, nx, ny);
-  return launch_noise_normals(rho, nx, ny, 1, seed, sim, step, (cudaStream_t)stream);
+  return launch_noise_normals(rho, nx, ny, 1, seed, sim, step, nullptr, (cudaStream_t)stream);
 }

@@ -125,3 +125,51 @@ def test_cook_rejects_bad_arguments():
     with pytest.raises(chx.ChxError) as e:
         p32.step_noise(cn, cp, p32.alloc_work(DEV), rho, 1e-6)
     assert e.value.status == -7
+
+
+def test_ensemble_cook_matches_single_plan_runs():
+    # every slot of a forced ensemble group follows ch_cook_run with simulation
+    # id = slot, through eager single steps and graph-replayed pairs alike
+    chx = _chx()
+    n, dx, dt, sigma, seed, step0 = 64, 2 * np.pi / 64, 1e-3, 1e-8, 9, 5
+    gammas = [0.01, 0.02, 0.005]
+    ics = [np.zeros((n, n)), synth.field(61, n, n, -0.1, 0.1), synth.field(62, n, n, -0.3, 0.3)]
+    ens = chx.Ensemble(dt)
+    gid = ens.group_create(n, n * dx, 0.01, 4)
+    for s, (c0, g) in enumerate(zip(ics, gammas)):
+        ens.load(gid, s, torch.from_numpy(c0).to(DEV), None, g)
+    ens.set_active(gid, 3)
+    ens.set_cook(gid, sigma, seed=seed, step0=step0)
+    ens.step(1)  # eager
+    ens.step(6)  # three graph pairs
+    ens.sync_status()
+    for s, (c0, g) in enumerate(zip(ics, gammas)):
+        plan = chx.ChPlan(n, n, n * dx, n * dx, g, dt)
+        cn = torch.from_numpy(c0).to(DEV)
+        cp = cn.clone()
+        rho = torch.empty(2 * n * n, dtype=torch.float64, device=DEV)
+        plan.cook_run(cn, cp, plan.alloc_work(DEV), rho, 7, sigma, seed=seed, sim=s, step0=step0)
+        got = torch.empty(n * n, dtype=torch.float64, device=DEV)
+        ens.read(gid, s, got)
+        want = cn.cpu().numpy().ravel()
+        assert np.max(np.abs(got.cpu().numpy() - want)) <= 1e-11 * np.max(np.abs(want)), s
+    # forcing off: the next steps are the plain ADI steps
+    ens.set_cook(gid, 0.0)
+    before = torch.empty((n, n), dtype=torch.float64, device=DEV)
+    prev = torch.empty_like(before)
+    ens.read(gid, 1, before, prev)
+    ens.step(2)
+    after = torch.empty((n, n), dtype=torch.float64, device=DEV)
+    ens.read(gid, 1, after)
+    plan = chx.ChPlan(n, n, n * dx, n * dx, gammas[1], dt)
+    plan.step(before, prev, plan.alloc_work(DEV), 2)
+    assert np.max(np.abs(after.cpu().numpy() - before.cpu().numpy())) <= 1e-11 * float(before.abs().max())
+
+
+def test_ensemble_cook_rejects_mixed_precision():
+    chx = _chx()
+    ens = chx.Ensemble(1e-3, chx.PREC_F32_REFINE)
+    gid = ens.group_create(32, 1.0, 0.01, 2)
+    with pytest.raises(chx.ChxError) as e:
+        ens.set_cook(gid, 1e-8)
+    assert e.value.status == -7
