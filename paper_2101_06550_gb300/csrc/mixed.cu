@@ -47,7 +47,9 @@ __device__ __forceinline__ ff lap_ff(const ff (*t)[LD], int y, int x, ff rho, ff
 }
 
 // Right-hand side of Eq. 3.1 in double-float: r = k2 L'(M) - k1 (C^n - C^{n-1}),
-// M = C^3 - C - gl L'(Cbar).  Same tiling as the FP64 kernel; r written transposed.
+// M = C^3 - C - gl L'(Cbar).  Same tiling as the FP64 kernel: whole 32-column
+// rows per warp while staging, j along the warp for the output, whose
+// transposed stores are then coalesced without a staging tile.
 template <bool kIso>
 __global__ void __launch_bounds__(kT* kBY) ch_rhs_ff_kernel(const double* __restrict__ cn,
                                                             const double* __restrict__ cp, float* __restrict__ rhi,
@@ -57,44 +59,40 @@ __global__ void __launch_bounds__(kT* kBY) ch_rhs_ff_kernel(const double* __rest
   __shared__ ff s_cn[kT + 4][kT + 5];
   __shared__ ff s_cb[kT + 4][kT + 5];
   __shared__ ff s_m[kT + 2][kT + 3];
-  __shared__ ff s_o[kT][kT + 1];
   const int z = blockIdx.z;
   const ff rho = ffc(rho2), kap = ffc(kap2), gl = ffc(glff[z]), k1 = ffc(k12), k2 = ffc(k22);
   cn += (size_t)z * nx * ny;
   cp += (size_t)z * nx * ny;
   const int i0 = blockIdx.x * kT, j0 = blockIdx.y * kT;
   const int tid = threadIdx.y * kT + threadIdx.x;
-  for (int idx = tid; idx < (kT + 4) * (kT + 4); idx += kT * kBY) {
-    const int ly = idx / (kT + 4), lx = idx % (kT + 4);
+  auto stage = [&](int ly, int lx) {
     const int gi = wrap_near(i0 - 2 + lx, nx), gj = wrap_near(j0 - 2 + ly, ny);
     const size_t p = (size_t)gj * nx + gi;
     const ff a = d2ff(cn[p]), b = d2ff(cp[p]);
     s_cn[ly][lx] = a;
     s_cb[ly][lx] = ff_sub(ff_scale2(a, 2.f), b);
-  }
+  };
+  for (int ly = threadIdx.y; ly < kT + 4; ly += kBY) stage(ly, threadIdx.x);
+  if (tid < 4 * (kT + 4)) stage(tid >> 2, kT + (tid & 3));
   __syncthreads();
-  for (int idx = tid; idx < (kT + 2) * (kT + 2); idx += kT * kBY) {
-    const int ly = idx / (kT + 2) + 1, lx = idx % (kT + 2) + 1;
+  auto mstage = [&](int ly, int lx) {
     const ff l = lap_ff<kT + 5, kIso>(s_cb, ly, lx, rho, kap);
     const ff c = s_cn[ly][lx];
     const ff nl = ff_mul(c, ff_add_f(ff_mul(c, c), -1.f));
     s_m[ly - 1][lx - 1] = ff_sub(nl, ff_mul(gl, l));
-  }
+  };
+  for (int ly = 1 + threadIdx.y; ly <= kT + 2; ly += kBY) mstage(ly, 1 + threadIdx.x);
+  if (tid < 2 * (kT + 2)) mstage(1 + (tid >> 1), kT + 1 + (tid & 1));
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < kT / kBY; ++k) {
-    const int ly = threadIdx.y + k * kBY + 1, lx = threadIdx.x + 1;
+    const int li = threadIdx.y + k * kBY, lj = threadIdx.x;  // output (i0 + li, j0 + lj)
+    const int ly = lj + 1, lx = li + 1;
     const ff l = lap_ff<kT + 3, kIso>(s_m, ly, lx, rho, kap);
     const ff diff = ff_sub(s_cb[ly + 1][lx + 1], s_cn[ly + 1][lx + 1]);  // C^n - C^{n-1}
-    s_o[lx - 1][ly - 1] = ff_sub(ff_mul(k2, l), ff_mul(k1, diff));
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < kT / kBY; ++k) {
-    const int li = threadIdx.y + k * kBY, lj = threadIdx.x;
+    const ff v = ff_sub(ff_mul(k2, l), ff_mul(k1, diff));
     const int gi = i0 + li, gj = j0 + lj;
     if (gi < nx && gj < ny) {
-      const ff v = s_o[li][lj];
       const size_t q = (size_t)gi * G * ny + (size_t)z * ny + gj;
       rhi[q] = v.hi;
       rlo[q] = v.lo;
