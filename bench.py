@@ -311,6 +311,8 @@ def run_chx(args, rank, world, local_rank):
         torch.cuda.empty_cache()
         extras["ensemble"] = bench_ensemble(dev, chx.PREC_F32_REFINE, args.ens_steps, 3)
         torch.cuda.empty_cache()
+        extras["coarsening_stats"] = bench_coarsening_stats(dev)
+        torch.cuda.empty_cache()
         extras["serving"] = bench_serving(dev, args.serve_requests, args.serve_rate, chx.PREC_F32_REFINE)
         torch.cuda.empty_cache()
     clk.__exit__(None, None, None)
@@ -542,6 +544,48 @@ def bench_ensemble(dev, precision, steps, warmup, count=512):
     res = {"sims": count, "grid_pts": pts, "steps": steps, "ms_per_ensemble_step": ms / steps,
            "value": pts * steps / (ms * 1e-3), "unit": "grid-pt-steps/s", "segments": tuned,
            "hbm_bytes": ens.bytes_used}
+    ens.close()
+    return res
+
+
+def bench_coarsening_stats(dev, sims=1024, samples=20, every=10):
+    """The statistics workload of Sec. 7.2: a batch of 1024 simulations on the
+    2 pi x 2 pi domain (256^2, gamma = 0.01, dt = 0.1 dx, symmetric U[-0.1, 0.1]
+    mixtures, FP64), the free energy of every simulation sampled every `every`
+    steps on the device and beta = -(t/F) dF/dt formed per simulation at the end."""
+    import torch
+
+    import paper_2101_06550_gb300 as chx
+
+    n, l, gamma = 256, 2 * np.pi, 0.01
+    dt = 0.1 * l / n
+    ens = chx.Ensemble(dt, chx.PREC_F64)
+    gid = ens.group_create(n, l, gamma, sims)
+    for s in range(sims):
+        ens.load(gid, s, synth.uniform_torch(5000 + s, n * n, -0.1, 0.1, device=dev))
+    ens.set_active(gid, sims)
+    obs = torch.empty(samples, sims, 4, dtype=torch.float64, device=dev)
+    ens.step(2)
+    ens.observables(gid, obs[0])
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for k in range(samples):
+        ens.step(every)
+        ens.observables(gid, obs[k])
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    ens.sync_status()
+    t = (2 + every * (1 + np.arange(samples))) * dt
+    F = obs[:, :, 1].cpu().numpy()
+    beta = np.stack([chx.coarsening_rate(t, F[:, s]) for s in range(sims)], axis=1)
+    steps = samples * every
+    pts = sims * n * n
+    res = {"sims": sims, "n": n, "steps": steps, "samples": samples, "ms_per_ensemble_step": ms / steps,
+           "value": pts * steps / (ms * 1e-3), "unit": "grid-pt-steps/s", "t_end": float(t[-1]),
+           "beta_median_last": float(np.median(beta[-1])), "mass_drift_max": float(np.max(np.abs(
+               obs[-1, :, 0].cpu().numpy() - obs[0, :, 0].cpu().numpy())))}
     ens.close()
     return res
 
