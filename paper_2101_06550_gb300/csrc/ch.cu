@@ -245,6 +245,98 @@ __global__ void __launch_bounds__(kSolveThreads) spike_local_kernel(const TIn* f
   yb[(size_t)(4 * s + 3) * S + j] = ylast;
 }
 
+// The same sweeps for segments of a multiple of 2U rows (FP64): two prefetch
+// buffers used alternately, so there are no per-row bounds tests and no
+// register copies between blocks of rows.  Fewer non-FP64 instructions per
+// row is what counts here: a single grid gives these sweeps only a few warps
+// per SM, and each warp's issue rate bounds how often the FP64 unit is fed.
+template <typename TC, int U = 8>
+__global__ void __launch_bounds__(kSolveThreads) spike_local_even_kernel(const TC* f, TC* y, int ld, int nsys,
+                                                                         DirView<TC> D, TC* __restrict__ yb,
+                                                                         size_t fz, size_t ybz) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nsys) return;
+  const int s = blockIdx.y, m = D.m;
+  const int slot = blockIdx.z + j / D.spp;
+  const TC a = D.a[slot];
+  const TC* lu = D.lu + (size_t)slot * 4 * m;
+  f += blockIdx.z * fz;
+  y += blockIdx.z * fz;
+  yb += blockIdx.z * ybz;
+  const size_t L = (size_t)ld;
+  const TC* pf = f + (size_t)s * m * L + j;
+  TC* py = y + (size_t)s * m * L + j;
+  const TC *ra = lu, *be = lu + m, *ga = lu + 2 * m, *de = lu + 3 * m;
+  TC g1 = 0, g2 = 0;
+  TC b0[U], b1[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) b0[u] = pf[(size_t)u * L];
+  for (int r0 = 0; r0 < m; r0 += 2 * U) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) b1[u] = pf[(size_t)(r0 + U + u) * L];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 + u;
+      TC g = fma(-a, g2, b0[u]);
+      g = fma(-__ldg(&be[r]), g1, g) * __ldg(&ra[r]);
+      py[(size_t)r * L] = g;
+      g2 = g1;
+      g1 = g;
+    }
+    if (r0 + 2 * U < m) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) b0[u] = pf[(size_t)(r0 + 2 * U + u) * L];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 + U + u;
+      TC g = fma(-a, g2, b1[u]);
+      g = fma(-__ldg(&be[r]), g1, g) * __ldg(&ra[r]);
+      py[(size_t)r * L] = g;
+      g2 = g1;
+      g1 = g;
+    }
+  }
+  // back substitution, rows m-1 .. 0
+  TC x1 = 0, x2 = 0;
+#pragma unroll
+  for (int u = 0; u < U; ++u) b0[u] = py[(size_t)(m - 1 - u) * L];
+  TC ylast = 0, ylast2 = 0;
+  for (int r0 = m - 1; r0 >= 0; r0 -= 2 * U) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) b1[u] = py[(size_t)(r0 - U - u) * L];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 - u;
+      TC v = fma(-__ldg(&ga[r]), x1, b0[u]);
+      v = fma(-__ldg(&de[r]), x2, v);
+      py[(size_t)r * L] = v;
+      if (u == 0 && r0 == m - 1) ylast = v;
+      if (u == 1 && r0 == m - 1) ylast2 = v;
+      x2 = x1;
+      x1 = v;
+    }
+    if (r0 - 2 * U >= 0) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) b0[u] = py[(size_t)(r0 - 2 * U - u) * L];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 - U - u;
+      TC v = fma(-__ldg(&ga[r]), x1, b1[u]);
+      v = fma(-__ldg(&de[r]), x2, v);
+      py[(size_t)r * L] = v;
+      x2 = x1;
+      x1 = v;
+    }
+  }
+  const size_t S = (size_t)nsys;
+  yb[(size_t)(4 * s + 0) * S + j] = x1;  // y_0
+  yb[(size_t)(4 * s + 1) * S + j] = x2;  // y_1
+  yb[(size_t)(4 * s + 2) * S + j] = ylast2;
+  yb[(size_t)(4 * s + 3) * S + j] = ylast;
+}
+
 // The same sweeps with the segment tile staged in shared memory: one thread
 // issues bulk asynchronous copies of the m rows (32 systems each) onto an
 // mbarrier, so the whole tile is in flight at once, and the forward
@@ -854,7 +946,11 @@ static void launch_local(const TIn* f, TC* y, int ld, int nsys, const DirView<TC
                                                                            status);
   } else {
     const unsigned blk = balanced_block((size_t)nsys * D.P * Z);
-    spike_local_kernel<TIn, TC><<<dim3(ceil_div(nsys, blk), D.P, Z), blk, 0, st>>>(f, y, ld, nsys, D, yb, fz, ybz);
+    const dim3 grid(ceil_div(nsys, blk), D.P, Z);
+    if (std::is_same<TIn, TC>::value && sizeof(TC) == 8 && D.m % 16 == 0)
+      spike_local_even_kernel<TC><<<grid, blk, 0, st>>>((const TC*)f, y, ld, nsys, D, yb, fz, ybz);
+    else
+      spike_local_kernel<TIn, TC><<<grid, blk, 0, st>>>(f, y, ld, nsys, D, yb, fz, ybz);
   }
 }
 
