@@ -90,9 +90,10 @@ __device__ __forceinline__ int wrap_near(int i, int n) {
 // nkx (rho^x_ij - rho^x_{i-1,j}) + nky (rho^y_ij - rho^y_{i,j-1}), formed with
 // coalesced row reads into a shared tile first.
 template <typename TC, typename TO, bool NOISE = false>
-__global__ void __launch_bounds__(kT* kBY) ch_rhs_kernel(const double* __restrict__ cn, const double* __restrict__ cp,
+__global__ void __launch_bounds__(kT* kBY, 7) ch_rhs_kernel(const double* __restrict__ cn, const double* __restrict__ cp,
                                                          TO* __restrict__ rT, int nx, int ny, int G, TC rho, TC kap,
                                                          const TC* __restrict__ gls, TC k1, TC k2,
+                                                         double* __restrict__ cbar,
                                                          const double* __restrict__ dev = nullptr, double nkx = 0,
                                                          double nky = 0) {
   __shared__ TC s_cn[kT + 4][kT + 5];
@@ -134,6 +135,7 @@ __global__ void __launch_bounds__(kT* kBY) ch_rhs_kernel(const double* __restric
     }
   }
   __syncthreads();
+  double* cbz = cbar + (size_t)z * nx * ny;
   auto mstage = [&](int ly, int lx) {  // M = C^3 - C - gamma Lap Cbar on the tile plus one halo ring
     TC l = s_cb[ly][lx - 1] + s_cb[ly][lx + 1];
     l = fma(rho, s_cb[ly - 1][lx] + s_cb[ly + 1][lx], l);
@@ -141,6 +143,10 @@ __global__ void __launch_bounds__(kT* kBY) ch_rhs_kernel(const double* __restric
     const TC c = s_cn[ly][lx];
     const TC nl = c * fma(c, c, TC(-1));
     s_m[ly - 1][lx - 1] = fma(-gl, l, nl);
+    // the tile's own Cbar goes out for the update (C^{n+1} = Cbar + v)
+    const int gi = i0 - 2 + lx, gj = j0 - 2 + ly;
+    if (ly >= 2 && ly < kT + 2 && lx >= 2 && lx < kT + 2 && gi < nx && gj < ny)
+      cbz[(size_t)gj * nx + gi] = (double)s_cb[ly][lx];
   };
   for (int ly = 1 + threadIdx.y; ly <= kT + 2; ly += kBY) mstage(ly, 1 + threadIdx.x);
   if (tid < 2 * (kT + 2)) mstage(1 + (tid >> 1), kT + 1 + (tid & 1));
@@ -482,20 +488,20 @@ __global__ void __launch_bounds__(kT* kBY) ch_xfinish_kernel(const TC* __restric
 // C^{n+1} goes into c_prev (the caller swaps the pointers).
 template <typename TC>
 __global__ void __launch_bounds__(kSolveThreads) ch_update_kernel(const TC* __restrict__ y1, const TC* __restrict__ t1,
-                                                                  DirView<TC> D, double* cn, double* cp, int nx,
-                                                                  int ny, int keep_roles) {
+                                                                  DirView<TC> D, const double* __restrict__ cbar,
+                                                                  double* cn, double* cp, int nx, int ny,
+                                                                  int keep_roles) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y, z = blockIdx.z, m = D.m, P = D.P;
   if (i >= nx) return;
   const int s = j / m, r = j - s * m;
   const size_t p = (size_t)z * nx * ny + (size_t)j * nx + i;
   t1 += (size_t)z * 4 * P * nx;
-  const double a = cn[p], b = cp[p];
-  // C^{n+1} = 2a - b + y - corr: (y - b), then + 2a, then the four spike terms
-  const double nxt = (double)spike_apply((TC)fma(2.0, a, (double)y1[p] - b), D.vw + (size_t)z * 4 * m, t1, m, P, nx,
-                                         s, r, i);
+  // C^{n+1} = Cbar + y - corr: one add, then the four spike terms
+  const double nxt = (double)spike_apply((TC)(cbar[p] + (double)y1[p]), D.vw + (size_t)z * 4 * m, t1, m, P, nx, s, r,
+                                         i);
   if (keep_roles) {
-    cp[p] = a;
+    cp[p] = cn[p];
     cn[p] = nxt;
   } else {
     cp[p] = nxt;
@@ -882,6 +888,7 @@ int group_init(ChGroup* g, int nx, int ny, double lx, double ly, double gamma, d
   g->off_y1 = off; off = align256(off + mix);
   g->off_y2 = off; off = align256(off + mix);
   g->off_x0 = off; off = align256(off + mix);
+  g->off_cb = off; off = align256(off + (f64 ? N * esz : 0));  // Cbar, formed by the RHS pass for the update
   const size_t kx = 4 * (size_t)g->X.P * ny * G, ky = 4 * (size_t)g->Y.P * nx * G;
   g->off_ybx = off; off = align256(off + kx * esz);
   g->off_tx = off; off = align256(off + kx * esz);
@@ -962,6 +969,7 @@ static void step_f64(ChGroup* g, int G, double* cur, double* prev, void* work, i
   double* w = wptr<double>(work, g->off_w);
   double *ybx = wptr<double>(work, g->off_ybx), *tx = wptr<double>(work, g->off_tx);
   double *yby = wptr<double>(work, g->off_yby), *ty = wptr<double>(work, g->off_ty);
+  double* cbar = wptr<double>(work, g->off_cb);
   const dim3 tgrid(ceil_div(nx, kT), ceil_div(ny, kT), G), tblock(kT, kBY);
   const int nsx = G * ny;  // the x sweep: all row systems of the group, interleaved
   const DirView<double> X = view<double>(g->X, ny), Y = view<double>(g->Y, nx);
@@ -970,11 +978,11 @@ static void step_f64(ChGroup* g, int G, double* cur, double* prev, void* work, i
   if (g->noise) {
     PROF(kRhs);
     ch_rhs_kernel<double, double, true><<<tgrid, tblock, 0, st>>>(cur, prev, f, nx, ny, G, g->rho, g->kap, g->d_gl,
-                                                                  g->k1, g->k2, g->noise, g->nkx, g->nky);
+                                                                  g->k1, g->k2, cbar, g->noise, g->nkx, g->nky);
   } else {
     PROF(kRhs);
     ch_rhs_kernel<double, double><<<tgrid, tblock, 0, st>>>(cur, prev, f, nx, ny, G, g->rho, g->kap, g->d_gl, g->k1,
-                                                            g->k2);
+                                                            g->k2, cbar);
   }
   { PROF(kLocX); launch_local<double, double>(f, f, nsx, nsx, X, ybx, 0, 0, 1, status, st); }
   { PROF(kRedX); spike_reduced_kernel<double><<<dim3(gx.x, 4 * X.P), kSolveThreads, 0, st>>>(ybx, X, tx, nsx, 0); }
@@ -982,7 +990,7 @@ static void step_f64(ChGroup* g, int G, double* cur, double* prev, void* work, i
   { PROF(kLocY); launch_local<double, double>(w, w, nx, nx, Y, yby, N, kyz, G, status, st); }
   { PROF(kRedY); spike_reduced_kernel<double><<<dim3(gy.x, 4 * Y.P, G), kSolveThreads, 0, st>>>(yby, Y, ty, nx, kyz); }
   { PROF(kUpd); ch_update_kernel<double><<<dim3(ceil_div(nx, kSolveThreads), ny, G), kSolveThreads, 0, st>>>(
-        w, ty, Y, cur, prev, nx, ny, keep_roles); }
+        w, ty, Y, cbar, cur, prev, nx, ny, keep_roles); }
 }
 
 static void step_f32r(ChGroup* g, int G, double* cur, double* prev, void* work, int keep_roles, cudaStream_t st,
