@@ -183,7 +183,8 @@ int ch_diagnostics(chx_ch_plan* plan, const double* c, double* mass_out, double*
  * minus the 5-point Laplacian of a Kronecker delta, the discrete form of the
  * paper's correlation), rho a 2-vector field of N(0, 1) deviates drawn afresh
  * every step.  In the ADI step of ch_step eta enters r with the weight (2/3) dt
- * of the explicit terms.  FP64 plans only (CHX_EUNSUPPORTED otherwise).
+ * of the explicit terms.  Both precisions: CHX_PREC_F32_REFINE plans form
+ * the forcing term in FP64 and add it to their double-float right-hand side.
  *
  * ch_noise_normals: writes the deviates of step `step` of simulation `sim`
  *   into the device array rho (2 nx ny doubles: rho^x then rho^y, row-major,
@@ -197,7 +198,7 @@ int ch_diagnostics(chx_ch_plan* plan, const double* c, double* mass_out, double*
  * ch_cook_run: nsteps steps, step k drawing the deviates of step step0 + k into
  *   the caller's device scratch rho (2 nx ny doubles) before stepping.
  * sigma >= 0 (the paper uses 1e-14 with C = 0 initially).  rho must not overlap
- * c_now, c_prev or work.  Errors: CHX_EINVAL, CHX_EUNSUPPORTED, CHX_ECUDA.
+ * c_now, c_prev or work.  Errors: CHX_EINVAL, CHX_ECUDA.
  */
 int ch_noise_normals(double* rho, int nx, int ny, uint64_t seed, uint64_t sim, uint64_t step, void* stream);
 int ch_step_noise(chx_ch_plan* plan, double* c_now, double* c_prev, void* work, const double* rho, double sigma,
@@ -311,16 +312,16 @@ int cn1d_step(chx_cn1d_plan* plan, double* c, int nsteps, void* stream);
  *    partitioned sweeps and keeps the fastest; the simulations' state is saved
  *    and restored, so the call changes no result other than by rounding order.
  *  - ens_group_set_cook turns on the Cahn-Hilliard-Cook forcing of ch_cook_run
- *    (Sec. 7.6) for every slot of a group (CHX_PREC_F64 ensembles only, else
- *    CHX_EUNSUPPORTED): each later step of the group first draws the deviates
- *    of slot s with simulation id s, key seed, at the group's step counter
+ *    (Sec. 7.6) for every slot of a group (either precision): each later step
+ *    of the group first draws the deviates of slot s with simulation id s, key
+ *    seed, at the group's step counter
  *    (starting at step0 and advanced on the device, so graph replays draw
  *    fresh deviates), then takes the forced step.  It allocates the group's
  *    deviate scratch (2 capacity n^2 doubles, counted against the budget) on
  *    first use and synchronises the device; sigma = 0 turns the forcing off
  *    and frees the scratch.
  * Destroy with chx_plan_destroy; chx_sync_status works on the ensemble too.
- * Errors: CHX_EINVAL (bad ids, sizes, slots), CHX_ENOMEM, CHX_EUNSUPPORTED, CHX_ECUDA.
+ * Errors: CHX_EINVAL (bad ids, sizes, slots), CHX_ENOMEM, CHX_ECUDA.
  */
 int ens_create(chx_ens** ens, int precision, double dt, size_t hbm_budget_bytes);
 int ens_group_create(chx_ens* ens, int n, double l, double gamma, int capacity, int* group_id);

@@ -1051,7 +1051,7 @@ static void step_f32r(ChGroup* g, int G, double* cur, double* prev, void* work, 
   const dim3 gx(ceil_div(nsx, kSolveThreads), X.P), gy(ceil_div(nx, kSolveThreads), Y.P, G);
   const size_t kyz = 4 * (size_t)Y.P * nx;
   // right-hand side in double-float
-  { PROF(kRhs); launch_ch_rhs_ff(cur, prev, fhi, flo, nx, ny, G, g->kff, g->d_glff, st); }
+  { PROF(kRhs); launch_ch_rhs_ff(cur, prev, fhi, flo, nx, ny, G, g->kff, g->d_glff, g->noise, g->nkx, g->nky, st); }
   // x: FP32 solve of the high part, double-float residual, FP32 correction solve
   { PROF(kLocX); launch_local<float, float>(fhi, y1, nsx, nsx, X, ybx, 0, 0, 1, status, st); }
   { PROF(kRedX); spike_reduced_kernel<float><<<dim3(gx.x, 4 * X.P), kSolveThreads, 0, st>>>(ybx, X, tx, nsx, 0); }
@@ -1204,8 +1204,6 @@ static bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
 static int cook_prepare(chx_ch_plan* p, double* c_now, double* c_prev, void* work, const double* rho, double sigma,
                         const char* name) {
   if (!p || p->hdr.magic != kMagicCh) return fail(CHX_EINVAL, "%s: bad plan", name);
-  if (p->g.precision != CHX_PREC_F64)
-    return fail(CHX_EUNSUPPORTED, "%s: the forcing is implemented for CHX_PREC_F64 plans", name);
   if (!c_now || !c_prev || !work || !rho) return fail(CHX_EINVAL, "%s: null pointer", name);
   if (((uintptr_t)work & 255) != 0) return fail(CHX_EINVAL, "%s: work must be 256-byte aligned", name);
   if (!(sigma >= 0) || !isfinite(sigma)) return fail(CHX_EINVAL, "%s: sigma %g", name, sigma);

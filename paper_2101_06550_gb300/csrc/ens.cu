@@ -288,8 +288,6 @@ extern "C" int ens_slot_move(chx_ens* e, int group_id, int from, int to, void* s
 extern "C" int ens_group_set_cook(chx_ens* e, int group_id, double sigma, uint64_t seed, uint64_t step0) {
   EnsGroup* G = get_group(e, group_id);
   if (!G || !(sigma >= 0) || !isfinite(sigma)) return fail(CHX_EINVAL, "ens_group_set_cook: bad argument");
-  if (e->precision != CHX_PREC_F64)
-    return fail(CHX_EUNSUPPORTED, "ens_group_set_cook: the forcing is implemented for CHX_PREC_F64 ensembles");
   int rc = cuda_check(cudaDeviceSynchronize(), "ens_group_set_cook: synchronize");
   if (rc) return rc;
   if (sigma == 0) {

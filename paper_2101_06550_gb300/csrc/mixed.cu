@@ -50,15 +50,21 @@ __device__ __forceinline__ ff lap_ff(const ff (*t)[LD], int y, int x, ff rho, ff
 // M = C^3 - C - gl L'(Cbar).  Same tiling as the FP64 kernel: whole 32-column
 // rows per warp while staging, j along the warp for the output, whose
 // transposed stores are then coalesced without a staging tile.
-template <bool kIso>
+//
+// NOISE (Cahn-Hilliard-Cook, Sec. 7.6): the forcing term (2/3) dt eta is
+// formed in FP64 on the otherwise idle FP64 unit (one subtraction and one FMA
+// per direction), as in the FP64 kernel, and added as a double-float pair.
+template <bool kIso, bool NOISE = false>
 __global__ void __launch_bounds__(kT* kBY) ch_rhs_ff_kernel(const double* __restrict__ cn,
                                                             const double* __restrict__ cp, float* __restrict__ rhi,
                                                             float* __restrict__ rlo, int nx, int ny, int G, float2 rho2,
                                                             float2 kap2, const float2* __restrict__ glff, float2 k12,
-                                                            float2 k22) {
+                                                            float2 k22, const double* __restrict__ dev = nullptr,
+                                                            double nkx = 0, double nky = 0) {
   __shared__ ff s_cn[kT + 4][kT + 5];
   __shared__ ff s_cb[kT + 4][kT + 5];
   __shared__ ff s_m[kT + 2][kT + 3];
+  __shared__ ff s_nz[NOISE ? kT : 1][kT + 1];
   const int z = blockIdx.z;
   const ff rho = ffc(rho2), kap = ffc(kap2), gl = ffc(glff[z]), k1 = ffc(k12), k2 = ffc(k22);
   cn += (size_t)z * nx * ny;
@@ -74,6 +80,22 @@ __global__ void __launch_bounds__(kT* kBY) ch_rhs_ff_kernel(const double* __rest
   };
   for (int ly = threadIdx.y; ly < kT + 4; ly += kBY) stage(ly, threadIdx.x);
   if (tid < 4 * (kT + 4)) stage(tid >> 2, kT + (tid & 3));
+  if (NOISE) {
+    const size_t N = (size_t)nx * ny;
+    const double* rx = dev + (size_t)z * 2 * N;
+    const double* ry = rx + N;
+    for (int lj = threadIdx.y; lj < kT; lj += kBY) {
+      const int li = threadIdx.x, gi = i0 + li, gj = j0 + lj;
+      double v = 0;
+      if (gi < nx && gj < ny) {
+        const size_t q = (size_t)gj * nx + gi;
+        const size_t qw = (size_t)gj * nx + (gi == 0 ? nx - 1 : gi - 1);
+        const size_t qs = (size_t)(gj == 0 ? ny - 1 : gj - 1) * nx + gi;
+        v = fma(nkx, rx[q] - rx[qw], nky * (ry[q] - ry[qs]));
+      }
+      s_nz[lj][li] = d2ff(v);
+    }
+  }
   __syncthreads();
   auto mstage = [&](int ly, int lx) {
     const ff l = lap_ff<kT + 5, kIso>(s_cb, ly, lx, rho, kap);
@@ -90,7 +112,8 @@ __global__ void __launch_bounds__(kT* kBY) ch_rhs_ff_kernel(const double* __rest
     const int ly = lj + 1, lx = li + 1;
     const ff l = lap_ff<kT + 3, kIso>(s_m, ly, lx, rho, kap);
     const ff diff = ff_sub(s_cb[ly + 1][lx + 1], s_cn[ly + 1][lx + 1]);  // C^n - C^{n-1}
-    const ff v = ff_sub(ff_mul(k2, l), ff_mul(k1, diff));
+    ff v = ff_sub(ff_mul(k2, l), ff_mul(k1, diff));
+    if (NOISE) v = ff_add(v, s_nz[lj][li]);
     const int gi = i0 + li, gj = j0 + lj;
     if (gi < nx && gj < ny) {
       const size_t q = (size_t)gi * G * ny + (size_t)z * ny + gj;
@@ -449,9 +472,17 @@ __global__ void __launch_bounds__(kSolveThreads) penta_solve_f32_from_f64_kernel
 }  // namespace
 
 void launch_ch_rhs_ff(const double* cn, const double* cp, float* rhi, float* rlo, int nx, int ny, int G,
-                      const FFConst& k, const float2* glff, cudaStream_t st) {
+                      const FFConst& k, const float2* glff, const double* noise, double nkx, double nky,
+                      cudaStream_t st) {
   const dim3 grid(ceil_div(nx, kT), ceil_div(ny, kT), G), block(kT, kBY);
-  if (k.rho.x == 1.f && k.rho.y == 0.f)
+  const bool iso = k.rho.x == 1.f && k.rho.y == 0.f;
+  if (noise && iso)
+    ch_rhs_ff_kernel<true, true><<<grid, block, 0, st>>>(cn, cp, rhi, rlo, nx, ny, G, k.rho, k.kap, glff, k.k1, k.k2,
+                                                         noise, nkx, nky);
+  else if (noise)
+    ch_rhs_ff_kernel<false, true><<<grid, block, 0, st>>>(cn, cp, rhi, rlo, nx, ny, G, k.rho, k.kap, glff, k.k1, k.k2,
+                                                          noise, nkx, nky);
+  else if (iso)
     ch_rhs_ff_kernel<true><<<grid, block, 0, st>>>(cn, cp, rhi, rlo, nx, ny, G, k.rho, k.kap, glff, k.k1, k.k2);
   else
     ch_rhs_ff_kernel<false><<<grid, block, 0, st>>>(cn, cp, rhi, rlo, nx, ny, G, k.rho, k.kap, glff, k.k1, k.k2);

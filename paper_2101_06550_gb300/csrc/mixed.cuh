@@ -24,7 +24,8 @@ struct DirView;
 // All launchers take G / Z simulations of the group (blockIdx.z); see chgroup.cuh for layouts.
 // glff[z] = gamma_z / dx^2 and aff[z] = a_z as double-float pairs, per slot.
 void launch_ch_rhs_ff(const double* cn, const double* cp, float* rhi, float* rlo, int nx, int ny, int G,
-                      const FFConst& k, const float2* glff, cudaStream_t st);
+                      const FFConst& k, const float2* glff, const double* noise, double nkx, double nky,
+                      cudaStream_t st);
 void launch_resid_ff(const float* fhi, const float* flo, const float* y1, const float* t1, float* x0, float* rho,
                      int ld, int nsys, int n, const DirView<float>& D, const float2* aff, int Z, size_t fz, size_t ybz,
                      cudaStream_t st);
