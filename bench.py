@@ -557,8 +557,9 @@ def bench_ensemble(dev, precision, steps, warmup, count=512):
 def bench_coarsening_stats(dev, sims=1024, samples=20, every=10):
     """The statistics workload of Sec. 7.2: a batch of 1024 simulations on the
     2 pi x 2 pi domain (256^2, gamma = 0.01, dt = 0.1 dx, symmetric U[-0.1, 0.1]
-    mixtures, FP64), the free energy of every simulation sampled every `every`
-    steps on the device and beta = -(t/F) dF/dt formed per simulation at the end."""
+    mixtures, FP64), the observables (mass, F, s, k1) of every simulation sampled
+    every `every` steps on the device and beta = -(t/F) dF/dt formed per
+    simulation at the end."""
     import torch
 
     import paper_2101_06550_gb300 as chx
@@ -572,13 +573,13 @@ def bench_coarsening_stats(dev, sims=1024, samples=20, every=10):
     ens.set_active(gid, sims)
     obs = torch.empty(samples, sims, 4, dtype=torch.float64, device=dev)
     ens.step(2)
-    ens.observables(gid, obs[0])
+    ens.observables(gid, obs[0], with_k1=True)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
     for k in range(samples):
         ens.step(every)
-        ens.observables(gid, obs[k])
+        ens.observables(gid, obs[k], with_k1=True)
     b.record()
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
@@ -590,7 +591,10 @@ def bench_coarsening_stats(dev, sims=1024, samples=20, every=10):
     pts = sims * n * n
     res = {"sims": sims, "n": n, "steps": steps, "samples": samples, "ms_per_ensemble_step": ms / steps,
            "value": pts * steps / (ms * 1e-3), "unit": "grid-pt-steps/s", "t_end": float(t[-1]),
-           "beta_median_last": float(np.median(beta[-1])), "mass_drift_max": float(np.max(np.abs(
+           "beta_median_last": float(np.median(beta[-1])),
+           "s_median_last": float(np.median(obs[-1, :, 2].cpu().numpy())),
+           "k1_median_last": float(np.median(obs[-1, :, 3].cpu().numpy())),
+           "mass_drift_max": float(np.max(np.abs(
                obs[-1, :, 0].cpu().numpy() - obs[0, :, 0].cpu().numpy())))}
     ens.close()
     return res

@@ -222,8 +222,12 @@ int ch_cook_run(chx_ch_plan* plan, double* c_now, double* c_prev, void* work, do
  *   plan-owned scratch (a cuFFT real-to-complex plan and ny (nx/2+1) complex
  *   values); later calls allocate nothing.
  * ens_group_observables: every active slot of a group at once, out = DEVICE
- *   array of 4 * active doubles (slot-major); k1 is not formed (NaN).  The
- *   first call allocates a small partial-sum buffer.
+ *   array of 4 * active doubles (slot-major).  with_k1 = 0 leaves out[4s+3]
+ *   NaN and needs only a small partial-sum buffer; with_k1 = 1 forms k1 with
+ *   one batched real-to-complex cuFFT plan over the active slots, whose
+ *   spectra (active * ny (nx/2+1) complex values) and cuFFT work area are
+ *   allocated on the first such call and again when the active count changes
+ *   (not counted against the ensemble's budget).
  * Both flag NaN/Inf in the field as CHX_ENONFINITE (read with chx_sync_status).
  * Errors: CHX_EINVAL, CHX_ENOMEM, CHX_ECUDA.
  *
@@ -235,7 +239,7 @@ int ch_cook_run(chx_ch_plan* plan, double* c_now, double* c_prev, void* work, do
  *   non-zero, else CHX_EINVAL.
  */
 int ch_observables(chx_ch_plan* plan, const double* c, double* out, void* stream);
-int ens_group_observables(chx_ens* ens, int group_id, double* out, void* stream);
+int ens_group_observables(chx_ens* ens, int group_id, int with_k1, double* out, void* stream);
 int chx_coarsening_rate(const double* t, const double* F, int count, double* beta);
 
 /*

@@ -74,7 +74,7 @@ def lib():
         "cn1d_plan_create": (i, [ctypes.POINTER(_P), i, i, i, d, d, d, i]),
         "cn1d_step": (i, [_P, _P, i, _P]),
         "ch_observables": (i, [_P, _P, _P, _P]),
-        "ens_group_observables": (i, [_P, i, _P, _P]),
+        "ens_group_observables": (i, [_P, i, i, _P, _P]),
         "chx_coarsening_rate": (i, [ctypes.POINTER(d), ctypes.POINTER(d), i, ctypes.POINTER(d)]),
         "ch_noise_normals": (i, [_P, i, i, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _P]),
         "ch_step_noise": (i, [_P, _P, _P, _P, _P, d, _P]),
@@ -449,13 +449,13 @@ class Ensemble(_Plan):
     def move(self, gid, src, dst, stream=None):
         _check(lib().ens_slot_move(self._handle, gid, src, dst, _stream(stream)))
 
-    def observables(self, gid, out, stream=None):
-        """[mass, F_h, s, NaN] of every active slot of group gid into the float64 device tensor
-        ``out`` (4 * active values, slot-major)."""
+    def observables(self, gid, out, with_k1=False, stream=None):
+        """[mass, F_h, s, k1] of every active slot of group gid into the float64 device tensor
+        ``out`` (4 * active values, slot-major); k1 is NaN unless with_k1."""
         import torch
 
-        _check(lib().ens_group_observables(self._handle, int(gid), _dev(out, torch.float64, None, "out"),
-                                           _stream(stream)))
+        _check(lib().ens_group_observables(self._handle, int(gid), 1 if with_k1 else 0,
+                                           _dev(out, torch.float64, None, "out"), _stream(stream)))
         return out
 
     def step(self, nsteps=1, stream=None):

@@ -257,12 +257,12 @@ extern "C" int ens_slot_read(chx_ens* e, int group_id, int slot, double* c_now, 
   return rc;
 }
 
-extern "C" int ens_group_observables(chx_ens* e, int group_id, double* out, void* stream) {
+extern "C" int ens_group_observables(chx_ens* e, int group_id, int with_k1, double* out, void* stream) {
   EnsGroup* G = get_group(e, group_id);
   if (!G || !out) return fail(CHX_EINVAL, "ens_group_observables: bad argument");
   if (G->active < 1) return CHX_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  const int rc = group_observables(&G->g, G->active, G->d_state[G->cur], out, 0, e->hdr.d_status, st);
+  const int rc = group_observables(&G->g, G->active, G->d_state[G->cur], out, with_k1 ? 1 : 0, e->hdr.d_status, st);
   e->hdr.last_stream = st;
   return rc;
 }

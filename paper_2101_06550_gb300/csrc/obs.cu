@@ -21,7 +21,8 @@ struct ObsState {
   size_t part_cap = 0;  // doubles
   cufftHandle fft = 0;
   bool fft_ok = false;
-  double2* spec = nullptr;  // ny * (nx/2 + 1) complex values
+  int fft_batch = 0;        // fields the cuFFT plan transforms at once
+  double2* spec = nullptr;  // fft_batch * ny * (nx/2 + 1) complex values
 };
 
 void obs_free(ObsState* o) {
@@ -118,6 +119,8 @@ __global__ void __launch_bounds__(kThreads) k1_partial_kernel(const double2* __r
                                                               double kx0, double ky0, double* __restrict__ part) {
   const int nh = nx / 2 + 1;
   const size_t total = (size_t)ny * nh;
+  spec += (size_t)blockIdx.y * total;  // field z = blockIdx.y
+  part += (size_t)blockIdx.y * gridDim.x * 2;
   double v2[2] = {0, 0};
   for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
     const int j = (int)(q / nh), mx = (int)(q - (size_t)j * nh);
@@ -133,14 +136,16 @@ __global__ void __launch_bounds__(kThreads) k1_partial_kernel(const double2* __r
   block_sums<2>(v2, part + (size_t)blockIdx.x * 2);
 }
 
-__global__ void k1_final_kernel(const double* __restrict__ part, int nb, double* __restrict__ k1) {
-  if (threadIdx.x != 0) return;
+// One thread per field: out[4 z + 3] = k1 of field z.
+__global__ void k1_final_kernel(const double* __restrict__ part, int nb, int G, double* __restrict__ out) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= G) return;
   double num = 0, den = 0;
   for (int b = 0; b < nb; ++b) {
-    num += part[2 * b];
-    den += part[2 * b + 1];
+    num += part[((size_t)z * nb + b) * 2];
+    den += part[((size_t)z * nb + b) * 2 + 1];
   }
-  *k1 = num / den;
+  out[4 * z + 3] = num / den;
 }
 
 int blocks_per_slot(size_t N, int G) {
@@ -175,21 +180,31 @@ int group_observables(ChGroup* g, int gact, const double* fields, double* out, i
   const int nx = g->nx, ny = g->ny;
   const size_t N = (size_t)nx * ny;
   const int nb = blocks_per_slot(N, gact);
-  int rc = ensure_part(o, (size_t)gact * nb * 4 > (size_t)kMaxBlocks * 2 ? (size_t)gact * nb * 4 : kMaxBlocks * 2);
+  const int kb = blocks_per_slot((size_t)ny * (nx / 2 + 1), gact);
+  // one partial-sum buffer, sized before any launch that uses it
+  const size_t need_obs = (size_t)gact * nb * 4, need_k1 = with_k1 ? (size_t)gact * kb * 2 : 0;
+  int rc = ensure_part(o, need_obs > need_k1 ? need_obs : need_k1);
   if (rc) return rc;
   obs_partial_kernel<<<dim3(nb, gact), kThreads, 0, st>>>(fields, nx, ny, g->d_gl, g->rho, o->part);
   obs_final_kernel<<<ceil_div(gact, 128), 128, 0, st>>>(o->part, nb, gact, g->dx * g->dy, 1.0 / (double)N, out,
                                                         status);
   rc = launch_check("observables");
   if (rc || !with_k1) return rc;
-  if (gact != 1) return fail(CHX_EINVAL, "observables: k1 is formed for one field at a time");
-  if (!o->fft_ok) {
-    if (cufftPlan2d(&o->fft, ny, nx, CUFFT_D2Z) != CUFFT_SUCCESS)
-      return fail(CHX_ENOMEM, "observables: cuFFT plan %d x %d", ny, nx);
+  if (!o->fft_ok || o->fft_batch != gact) {
+    if (o->fft_ok) cufftDestroy(o->fft);
+    o->fft_ok = false;
+    if (o->spec) cudaFree(o->spec);
+    o->spec = nullptr;
+    int dims[2] = {ny, nx};
+    if (cufftPlanMany(&o->fft, 2, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_D2Z, gact) != CUFFT_SUCCESS)
+      return fail(CHX_ENOMEM, "observables: cuFFT plan %d x %d x %d", gact, ny, nx);
     o->fft_ok = true;
-    if (cudaMalloc(&o->spec, (size_t)ny * (nx / 2 + 1) * sizeof(double2)) != cudaSuccess) {
+    o->fft_batch = gact;
+    if (cudaMalloc(&o->spec, (size_t)gact * ny * (nx / 2 + 1) * sizeof(double2)) != cudaSuccess) {
       cudaGetLastError();
       o->spec = nullptr;
+      cufftDestroy(o->fft);
+      o->fft_ok = false;
       return fail(CHX_ENOMEM, "observables: spectrum buffer");
     }
   }
@@ -197,9 +212,9 @@ int group_observables(ChGroup* g, int gact, const double* fields, double* out, i
       cufftExecD2Z(o->fft, const_cast<double*>(fields), reinterpret_cast<cufftDoubleComplex*>(o->spec)) !=
           CUFFT_SUCCESS)
     return fail(CHX_ECUDA, "observables: cuFFT transform");
-  const int kb = blocks_per_slot((size_t)ny * (nx / 2 + 1), 1);
-  k1_partial_kernel<<<kb, kThreads, 0, st>>>(o->spec, nx, ny, 2.0 * M_PI / g->lx, 2.0 * M_PI / g->ly, o->part);
-  k1_final_kernel<<<1, 32, 0, st>>>(o->part, kb, out + 3);
+  k1_partial_kernel<<<dim3(kb, gact), kThreads, 0, st>>>(o->spec, nx, ny, 2.0 * M_PI / g->lx, 2.0 * M_PI / g->ly,
+                                                         o->part);
+  k1_final_kernel<<<ceil_div(gact, 128), 128, 0, st>>>(o->part, kb, gact, out);
   return launch_check("observables: k1");
 }
 

@@ -76,6 +76,13 @@ def test_ensemble_observables_per_slot():
         assert got[s, 1] == pytest.approx(e, rel=n * n * EPS)
         assert got[s, 2] == pytest.approx(sv, rel=n * n * EPS)
         assert np.isnan(got[s, 3])
+    # with k1: one batched transform over the active slots
+    ens.observables(gid, out, with_k1=True)
+    got = out.cpu().numpy().reshape(5, 4)
+    for s in range(5):
+        m, e, sv, k1 = oracle.observables(fields[s], n * dx, n * dx, gammas[s])
+        assert got[s, 3] == pytest.approx(k1, rel=1e-12)
+        assert got[s, 1] == pytest.approx(e, rel=n * n * EPS)
     # after steps the observables follow the slots' state
     ens.step(3)
     ens.observables(gid, out)
