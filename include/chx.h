@@ -7,9 +7,14 @@
  *  - Every function returns an int status: CHX_OK (0) or a negative CHX_E*
  *    code; chx_status_string() names it and chx_last_error() gives the detail
  *    of the most recent failure on the calling host thread.
- *  - Device pointers are owned by the caller.  Plans own only what their
- *    *_create / *_factor call allocated (factors, small scratch); nothing else
- *    in this library allocates device memory.
+ *  - Device pointers are owned by the caller.  Plans own what their
+ *    *_create / *_factor call allocated (factors, small scratch) and the few
+ *    lazily made buffers a function's comment names (observables scratch, an
+ *    ensemble group's deviates); nothing else in this library allocates device
+ *    memory.
+ *  - A plan (and an ensemble) is used by one host thread at a time: calls on
+ *    the same plan from several threads must be serialised by the caller.
+ *    Different plans are independent.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    Work is enqueued asynchronously on it.  Errors found on the device are
  *    reported by the next chx_sync_status(plan).
