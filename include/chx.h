@@ -201,7 +201,10 @@ int ch_diagnostics(chx_ch_plan* plan, const double* c, double* mass_out, double*
  * ch_step_noise: one step with caller-given deviates rho (device, 2 nx ny
  *   doubles, layout as above); c_now/c_prev keep their roles as in ch_step.
  * ch_cook_run: nsteps steps, step k drawing the deviates of step step0 + k into
- *   the caller's device scratch rho (2 nx ny doubles) before stepping.
+ *   the caller's device scratch rho (2 nx ny doubles) before stepping.  Pairs
+ *   of steps replay a captured graph whose deviates read their step index
+ *   from a device counter; the first such call allocates that 8-byte counter
+ *   and captures the graph (again when the pointers, sigma, seed or sim change).
  * sigma >= 0 (the paper uses 1e-14 with C = 0 initially).  rho must not overlap
  * c_now, c_prev or work.  Errors: CHX_EINVAL, CHX_ECUDA.
  */

@@ -53,6 +53,14 @@ struct chx_ch_plan {
   const void *graph_now, *graph_prev, *graph_work;
   const void *seen_now, *seen_prev, *seen_work;  // the previous call's pointers
   cudaStream_t cap;
+  // Cahn-Hilliard-Cook pairs (ch_cook_run): two forced steps whose deviates take
+  // their step index from the device counter d_cook_step, valid for these
+  // pointers and parameters
+  cudaGraphExec_t cook_pair;
+  const void *cook_now, *cook_prev, *cook_work, *cook_rho;
+  double cook_sigma;
+  uint64_t cook_seed, cook_sim;
+  uint64_t* d_cook_step;
 };
 
 namespace {
@@ -1078,6 +1086,8 @@ void ch_plan_free(chx_ch_plan* p) {
   if (!p) return;
   if (p->pair) cudaGraphExecDestroy(p->pair);
   if (p->one) cudaGraphExecDestroy(p->one);
+  if (p->cook_pair) cudaGraphExecDestroy(p->cook_pair);
+  if (p->d_cook_step) cudaFree(p->d_cook_step);
   if (p->cap) cudaStreamDestroy(p->cap);
   group_free(&p->g);
   if (p->d_partials) cudaFree(p->d_partials);
@@ -1236,8 +1246,54 @@ extern "C" int ch_cook_run(chx_ch_plan* p, double* c_now, double* c_prev, void* 
   if (rc) return rc;
   if (nsteps < 0) return fail(CHX_EINVAL, "ch_cook_run: nsteps %d < 0", nsteps);
   cudaStream_t st = (cudaStream_t)stream;
+  int done = 0;
+  if (nsteps >= 2 && !p->prof->on) {
+    // pairs of forced steps from a captured graph; the deviates' step index
+    // lives on the device (set here, advanced inside the graph)
+    if (!p->d_cook_step && cudaMalloc(&p->d_cook_step, sizeof(uint64_t)) != cudaSuccess) {
+      cudaGetLastError();
+      p->d_cook_step = nullptr;
+      return fail(CHX_ENOMEM, "ch_cook_run: step counter");
+    }
+    if (!p->cook_pair || p->cook_now != c_now || p->cook_prev != c_prev || p->cook_work != work ||
+        p->cook_rho != rho || p->cook_sigma != sigma || p->cook_seed != seed || p->cook_sim != sim) {
+      if (p->cook_pair) cudaGraphExecDestroy(p->cook_pair);
+      p->cook_pair = nullptr;
+      if (!p->cap) rc = cuda_check(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking), "ch_cook_run: stream");
+      cudaGraph_t graph = nullptr;
+      if (!rc) rc = cuda_check(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal), "ch_cook_run: capture");
+      if (!rc) {
+        p->g.noise = rho;
+        for (int h = 0; h < 2; ++h) {
+          launch_noise_normals(rho, p->g.nx, p->g.ny, 1, seed, sim, 0, p->d_cook_step, p->cap);
+          group_step(&p->g, 1, h ? c_prev : c_now, h ? c_now : c_prev, work, 0, p->cap, nullptr, p->hdr.d_status);
+          launch_step_advance(p->d_cook_step, p->cap);
+        }
+        p->g.noise = nullptr;
+        rc = cuda_check(cudaStreamEndCapture(p->cap, &graph), "ch_cook_run: end capture");
+      }
+      if (!rc) rc = cuda_check(cudaGraphInstantiate(&p->cook_pair, graph, 0), "ch_cook_run: instantiate");
+      if (graph) cudaGraphDestroy(graph);
+      if (rc) {
+        p->cook_pair = nullptr;
+        return rc;
+      }
+      p->cook_now = c_now;
+      p->cook_prev = c_prev;
+      p->cook_work = work;
+      p->cook_rho = rho;
+      p->cook_sigma = sigma;
+      p->cook_seed = seed;
+      p->cook_sim = sim;
+    }
+    rc = launch_step_set(p->d_cook_step, step0, st);
+    for (int k = 0; k + 2 <= nsteps && !rc; k += 2)
+      rc = cuda_check(cudaGraphLaunch(p->cook_pair, st), "ch_cook_run: graph launch");
+    if (rc) return rc;
+    done = nsteps & ~1;  // pairs leave C^n in c_now
+  }
   double *cur = c_now, *prev = c_prev;
-  for (int s = 0; s < nsteps; ++s) {
+  for (int s = done; s < nsteps; ++s) {
     const int keep = s == nsteps - 1 && cur == c_now;
     rc = launch_noise_normals(rho, p->g.nx, p->g.ny, 1, seed, sim, step0 + (uint64_t)s, nullptr, st);
     if (rc) return rc;
@@ -1253,7 +1309,7 @@ extern "C" int ch_cook_run(chx_ch_plan* p, double* c_now, double* c_prev, void* 
     if (rc) return rc;
   }
   p->hdr.last_stream = st;
-  return CHX_OK;
+  return launch_check("ch_cook_run");
 }
 
 extern "C" int ch_diagnostics(chx_ch_plan* p, const double* c, double* mass_out, double* energy_out, void* stream) {

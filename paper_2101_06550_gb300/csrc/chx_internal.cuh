@@ -76,8 +76,9 @@ const double* tri_plan_factors(const chx_tri_plan* p);
 // the step index comes from *d_step when d_step is not null.
 int launch_noise_normals(double* rho, int nx, int ny, int G, uint64_t seed, uint64_t sim0, uint64_t step,
                          const uint64_t* d_step, cudaStream_t st);
-// *d_step += 1 on the stream.
+// *d_step += 1, and *d_step = v, on the stream.
 int launch_step_advance(uint64_t* d_step, cudaStream_t st);
+int launch_step_set(uint64_t* d_step, uint64_t v, cudaStream_t st);
 
 // Plain non-cyclic pentadiagonal LU (paper factor steps) of the m x m Toeplitz
 // band (a, b, c, d, e); ralpha, beta, gam, del of length m.

@@ -78,10 +78,16 @@ __global__ void __launch_bounds__(kThreads) noise_normals_kernel(double* __restr
 }
 
 __global__ void step_advance_kernel(uint64_t* d_step) { *d_step += 1; }
+__global__ void step_set_kernel(uint64_t* d_step, uint64_t v) { *d_step = v; }
 
 }  // namespace
 
 namespace chx {
+int launch_step_set(uint64_t* d_step, uint64_t v, cudaStream_t st) {
+  step_set_kernel<<<1, 1, 0, st>>>(d_step, v);
+  return launch_check("noise step counter");
+}
+
 int launch_step_advance(uint64_t* d_step, cudaStream_t st) {
   step_advance_kernel<<<1, 1, 0, st>>>(d_step);
   return launch_check("noise step counter");
