@@ -243,8 +243,8 @@ def run_chx(args, rank, world, local_rank):
     ms32, ms32_prof, prof32, plan32, _, _, _ = measure(chx.PREC_F32_REFINE)
     launches_per_step = sum(n for _, n in prof64.values()) / max(1, args.steps)
 
-    # end to end through the public API with host buffers: H2D of both fields
-    # from pinned memory, one step, D2H of the new field, every step.  Two plans
+    # end to end through the C ABI with host buffers (ch_step_host): H2D of both
+    # fields from pinned memory, one step, D2H of the new field, every step.  Two plans
     # with their own device fields alternate on two streams, so one step's copies
     # overlap the other's kernels (the copy engines run beside the SMs).
     h_cn = c0.cpu().pin_memory()
@@ -260,11 +260,7 @@ def run_chx(args, rank, world, local_rank):
         for k in range(k_steps):
             plan, dn, dp, wk = lanes[k & 1]
             st = e2e_streams[k & 1]
-            with torch.cuda.stream(st):
-                dn.copy_(h_cn, non_blocking=True)
-                dp.copy_(h_cp, non_blocking=True)
-                plan.step(dn, dp, wk, 1, stream=st)
-                h_out[k & 1].copy_(dn, non_blocking=True)
+            plan.step_host(h_cn, h_cp, h_out[k & 1], dn, dp, wk, 1, stream=st)  # H2D, step, D2H in one call
 
     e2e_run(4)  # warm: captures each lane's step graph
     torch.cuda.synchronize()

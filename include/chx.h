@@ -177,6 +177,17 @@ int ch_plan_create(chx_ch_plan** plan, int nx, int ny, double lx, double ly, dou
                    int precision);
 size_t ch_work_bytes(const chx_ch_plan* plan);
 int ch_step(chx_ch_plan* plan, double* c_now, double* c_prev, void* work, int nsteps, void* stream);
+/*
+ * ch_step_host: ch_step on fields that live in HOST memory.  Enqueues on
+ *   `stream` the copies of h_now and h_prev (nx * ny doubles each) into the
+ *   caller's device fields d_now and d_prev, nsteps steps, and the copy of the
+ *   new C^n back into h_out; returns without waiting.  Host buffers should be
+ *   page-locked for the copies to run asynchronously; they must stay valid
+ *   until the stream reaches the copies.  Device-side arguments and errors as
+ *   for ch_step.
+ */
+int ch_step_host(chx_ch_plan* plan, const double* h_now, const double* h_prev, double* h_out, double* d_now,
+                 double* d_prev, void* work, int nsteps, void* stream);
 int ch_diagnostics(chx_ch_plan* plan, const double* c, double* mass_out, double* energy_out, void* stream);
 
 /*

@@ -26,7 +26,7 @@ STATUS = {0: "CHX_OK", -1: "CHX_EINVAL", -2: "CHX_ESINGULAR", -3: "CHX_ENONFINIT
 # every symbol include/chx.h declares
 EXPORTS = ("chx_status_string", "chx_last_error", "chx_version", "stencil_apply_2d", "penta_cyclic_factor",
            "penta_cyclic_refactor", "penta_cyclic_solve_batched", "tri_cyclic_factor", "tri_cyclic_refactor",
-           "tri_cyclic_solve_batched", "ch_plan_create", "ch_work_bytes", "ch_step", "ch_diagnostics",
+           "tri_cyclic_solve_batched", "ch_plan_create", "ch_work_bytes", "ch_step", "ch_step_host", "ch_diagnostics",
            "ch_diagnostics_noalloc", "ch1d_plan_create", "ch1d_step", "cn1d_plan_create", "cn1d_step", "ch_noise_normals", "ch_step_noise", "ch_cook_run", "ch_observables", "ens_group_observables", "chx_coarsening_rate", "ch_profile", "ch_profile_read", "ch_profile_slot_name", "ens_create",
            "ens_group_create", "ens_group_destroy", "ens_group_set_active", "ens_group_set_cook", "ens_slot_load", "ens_slot_read",
            "ens_slot_move", "ens_step", "ens_group_step", "ens_autotune", "ens_info", "ens_bytes_used",
@@ -67,6 +67,7 @@ def lib():
         "ch_plan_create": (i, [ctypes.POINTER(_P), i, i, d, d, d, d, i]),
         "ch_work_bytes": (sz, [_P]),
         "ch_step": (i, [_P, _P, _P, _P, i, _P]),
+        "ch_step_host": (i, [_P, _P, _P, _P, _P, _P, _P, i, _P]),
         "ch_diagnostics": (i, [_P, _P, _P, _P, _P]),
         "ch_diagnostics_noalloc": (i, [_P, i, i, d, d, d, _P, _P, _P]),
         "ch1d_plan_create": (i, [ctypes.POINTER(_P), i, i, d, d, d]),
@@ -273,6 +274,21 @@ class ChPlan(_Plan):
         _check(lib().ch_step(self._handle, _dev(c_now, torch.float64, n, "c_now"),
                              _dev(c_prev, torch.float64, n, "c_prev"), _dev(work, None, None, "work"), int(nsteps),
                              _stream(stream)))
+
+    def step_host(self, h_now, h_prev, h_out, d_now, d_prev, work, nsteps=1, stream=None):
+        """ch_step_host: host fields in (pinned CPU tensors), nsteps steps on the device fields,
+        the new C^n copied back into h_out; asynchronous on `stream`."""
+        import torch
+
+        n = self.nx * self.ny
+        for t, name in ((h_now, "h_now"), (h_prev, "h_prev"), (h_out, "h_out")):
+            if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous() \
+                    or t.numel() != n:
+                raise ValueError(f"{name} must be a contiguous float64 CPU tensor of {n} elements")
+        _check(lib().ch_step_host(self._handle, ctypes.c_void_p(h_now.data_ptr()), ctypes.c_void_p(h_prev.data_ptr()),
+                                  ctypes.c_void_p(h_out.data_ptr()), _dev(d_now, torch.float64, n, "d_now"),
+                                  _dev(d_prev, torch.float64, n, "d_prev"), _dev(work, None, None, "work"),
+                                  int(nsteps), _stream(stream)))
 
     def step_noise(self, c_now, c_prev, work, rho, sigma, stream=None):
         """One Cahn-Hilliard-Cook step with given deviates rho (2*nx*ny float64, device)."""

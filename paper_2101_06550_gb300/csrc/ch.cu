@@ -1312,6 +1312,20 @@ extern "C" int ch_cook_run(chx_ch_plan* p, double* c_now, double* c_prev, void* 
   return launch_check("ch_cook_run");
 }
 
+extern "C" int ch_step_host(chx_ch_plan* p, const double* h_now, const double* h_prev, double* h_out, double* d_now,
+                            double* d_prev, void* work, int nsteps, void* stream) {
+  if (!p || p->hdr.magic != kMagicCh) return fail(CHX_EINVAL, "ch_step_host: bad plan");
+  if (!h_now || !h_prev || !h_out) return fail(CHX_EINVAL, "ch_step_host: null host pointer");
+  const size_t fb = (size_t)p->g.nx * p->g.ny * sizeof(double);
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = cuda_check(cudaMemcpyAsync(d_now, h_now, fb, cudaMemcpyHostToDevice, st), "ch_step_host: C^n in");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(d_prev, h_prev, fb, cudaMemcpyHostToDevice, st), "ch_step_host: C^{n-1} in");
+  if (!rc) rc = ch_step(p, d_now, d_prev, work, nsteps, stream);
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(h_out, d_now, fb, cudaMemcpyDeviceToHost, st), "ch_step_host: result out");
+  p->hdr.last_stream = st;
+  return rc;
+}
+
 extern "C" int ch_diagnostics(chx_ch_plan* p, const double* c, double* mass_out, double* energy_out, void* stream) {
   if (!p || p->hdr.magic != kMagicCh) return fail(CHX_EINVAL, "ch_diagnostics: bad plan");
   if (!c || !mass_out || !energy_out) return fail(CHX_EINVAL, "ch_diagnostics: null pointer");

@@ -278,3 +278,30 @@ def test_ch_step_graph_pairs_match_single_steps(precision):
             g, h = eager(2 * nsteps)
             assert torch.equal(e, g) and torch.equal(f, h), nsteps
     plan.sync_status()
+
+
+def test_ch_step_host_matches_device_step():
+    # host fields in, steps on the device, result back in host memory
+    chx = _chx()
+    n, l, gamma, dt = 64, 2 * np.pi, 0.01, 1e-3
+    c0 = synth.field(40, n, n, -0.1, 0.1)
+    cm = c0 + 1e-3 * synth.field(41, n, n, -1, 1)
+    plan = chx.ChPlan(n, n, l, l, gamma, dt)
+    work = plan.alloc_work(DEV)
+    h_now = torch.from_numpy(c0.ravel()).pin_memory()
+    h_prev = torch.from_numpy(cm.ravel()).pin_memory()
+    h_out = torch.empty(n * n, dtype=torch.float64).pin_memory()
+    d_now = torch.empty(n * n, dtype=torch.float64, device=DEV)
+    d_prev = torch.empty_like(d_now)
+    for steps in (1, 1, 5):  # the second call repeats the pointers (graph path)
+        plan.step_host(h_now, h_prev, h_out, d_now, d_prev, work, steps)
+        torch.cuda.synchronize()
+        a = torch.from_numpy(c0.ravel()).to(DEV)
+        b = torch.from_numpy(cm.ravel()).to(DEV)
+        plan.profile(True)  # eager reference launches
+        plan.step(a, b, work, steps)
+        plan.profile(False)
+        plan.profile_read(reset=True)
+        torch.cuda.synchronize()
+        assert torch.equal(h_out, a.cpu()) and torch.equal(d_now, a), steps
+    plan.sync_status()
