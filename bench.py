@@ -449,8 +449,9 @@ def bench_cn1d(dev, steps=100, rewrite_steps=20):
     import paper_2101_06550_gb300 as chx
 
     n, batch = 1024, 1 << 16
-    # FP64 operations per unknown and step: explicit half + forward + backward sweep
-    ops = {4: 5 + 5 + 4, 2: 3 + 3 + 2}
+    # FP64 operations per unknown and step as implemented (C^{n+1} = 2 A^{-1} C^n - C^n):
+    # forward sweep + backward sweep + the final 2u - C
+    ops = {4: 5 + 4 + 1, 2: 3 + 2 + 1}
     out = {"n": n, "systems": batch, "unit": "unknown-steps/s"}
     for order, name, dt in ((4, "hyperdiffusion_penta", 1e-8), (2, "diffusion_tri", 1e-5)):
         x = np.arange(n) / n

@@ -288,19 +288,21 @@ int ch1d_step(chx_ch1d_plan* plan, double* c, int nsteps, void* stream);
  *  order 2, diffusion C_t = kappa C_xx (Sec. 5.3.2, eq5:1ddiffscheme),
  *    sigma = kappa dt / (2 dx^2):
  *    (-sigma, 1 + 2 sigma, -sigma) C^{n+1} = (sigma, 1 - 2 sigma, sigma) C^n.
- * The right-hand side is formed inside the forward sweep of the cyclic
- * pentadiagonal (Navon bordering + LU) or tridiagonal (Thomas + Sherman-Morrison)
- * solve.  cn1d_plan_create: order 2 or 4; n >= 6 (order 4) or >= 3 (order 2);
- * batch >= 1; l, dt > 0; kappa >= 0.  rewrite selects the paper's benchmark
- * variant (Sec. 4.3):
+ * In both the explicit row is twice the identity minus the implicit one
+ * (B = 2I - A), so a step is C^{n+1} = 2 A^{-1} C^n - C^n: one cyclic
+ * pentadiagonal (Navon bordering + LU) or tridiagonal (Thomas + Sherman-
+ * Morrison) solve with right-hand side C^n and no explicit half to form.
+ * cn1d_plan_create: order 2 or 4; n >= 6 (order 4) or >= 3 (order 2);
+ * batch >= 1; l, dt > 0; kappa >= 0.  Every plan owns n * batch doubles of
+ * sweep scratch.  rewrite selects the paper's benchmark variant (Sec. 4.3):
  *   0 (Constant)  the matrix is factorised once on the host in FP64; the plan
- *                 owns about 9 n doubles of device memory;
+ *                 also owns about 9 n doubles of factors;
  *   1 (Rewrite)   the plan owns (order + 1) * n * batch doubles of per-system
  *                 matrix entries plus a PER_SYSTEM solver plan (about 9 n batch
  *                 doubles of factors), and every step resets the entries and
  *                 refactorises every system on the device before the sweep.
  * cn1d_step advances nsteps >= 0 steps in place on the caller-owned device
- * array c (n * batch doubles); it needs no scratch.  Errors: CHX_EINVAL,
+ * array c (n * batch doubles).  Errors: CHX_EINVAL,
  * CHX_ESINGULAR (host factorisation; a Rewrite plan's device factorisation
  * reports it through chx_sync_status), CHX_ENOMEM, CHX_ECUDA.
  */

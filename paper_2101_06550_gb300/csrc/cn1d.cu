@@ -6,10 +6,9 @@
 //    (-sigma, 1 + 2 sigma, -sigma) C^{n+1} = (sigma, 1 - 2 sigma, sigma) C^n,
 // for a batch of systems in the interleaved layout c[i * batch + s].
 //
-// One thread per system.  The explicit half is formed inside the forward sweep
-// of the cyclic solve from a register window of C (as in ch1d.cu), so a step is
-// one in-place forward + backward pass.  Two ways to hold the matrix, the
-// paper's benchmark variants (Sec. 4.3):
+// One thread per system, one forward + backward pass per step (see below for
+// the form of the step).  Two ways to hold the matrix, the paper's benchmark
+// variants (Sec. 4.3):
 //  Constant  factors formed once on the host and shared by every system;
 //  Rewrite   every step resets each system's matrix entries in device memory
 //            and refactorises them per system (penta_cyclic_refactor /
@@ -30,6 +29,7 @@ struct chx_cn1d_plan {
   double sigma;
   double* d_fac;  // Constant: penta 9*(n-2), tri 5*n doubles
   double sinv[4];
+  double* d_g;    // forward-sweep scratch, n * batch doubles
   // Rewrite: per-system matrix entries (order + 1 diagonals of n * batch) and a
   // PER_SYSTEM solver plan holding the per-system factors
   double* d_coef;
@@ -42,11 +42,18 @@ namespace {
 constexpr int kThreads = 128;
 constexpr int kU = 8;
 
+// Both schemes have the form A C^{n+1} = B C^n with B = 2I - A (the explicit
+// row is twice the identity minus the implicit one), so C^{n+1} = 2 A^{-1} C^n
+// - C^n: one solve with right-hand side C^n and a final 2u - C^n, with no
+// explicit half to form (penta: 10 FP64 operations per unknown instead of 14,
+// tri: 6 instead of 8).  The forward sweep's intermediate goes to the plan's
+// scratch g (n * batch doubles, interleaved), the result overwrites c.
+
 // Pentadiagonal (order 4).  Factor rows [ralpha, beta, eps, gam, del, q0, q1,
 // G0, G1] over the m = n - 2 rows of the bordered block, then (PER) the 2x2
 // tail inverse of each system.
 template <bool PER>
-__global__ void __launch_bounds__(kThreads) cn_penta_kernel(double* c, int n, int batch, double sg,
+__global__ void __launch_bounds__(kThreads) cn_penta_kernel(double* c, double* __restrict__ gs, int n, int batch,
                                                             const double* __restrict__ fac, double s00, double s01,
                                                             double s10, double s11) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -55,46 +62,35 @@ __global__ void __launch_bounds__(kThreads) cn_penta_kernel(double* c, int n, in
   const size_t B = (size_t)batch;
   const size_t fst = PER ? B : 1, fofs = PER ? (size_t)s : 0;
 #define FAC(k, r) __ldg(&fac[((size_t)(k) * m + (r)) * fst + fofs])
-  const double w0 = fma(-6.0, sg, 1.0), w1 = 4.0 * sg, w2 = -sg;
   double* pc = c + s;
-  const double c0 = pc[0], c1 = pc[B];
-  // window c_{r-2}, c_{r-1}, c_r, c_{r+1}; row r + 2 comes from the prefetch
-  double a2 = pc[(size_t)(n - 2) * B], a1 = pc[(size_t)(n - 1) * B], a0 = c0, b1 = c1;
+  double* pg = gs + s;
   double g1 = 0, g2 = 0, t0 = 0, t1 = 0;
   double buf[kU];
 #pragma unroll
-  for (int u = 0; u < kU; ++u) buf[u] = (u < m) ? pc[(size_t)(u + 2) * B] : 0.0;
+  for (int u = 0; u < kU; ++u) buf[u] = (u < m) ? pc[(size_t)u * B] : 0.0;
   for (int r0 = 0; r0 < m; r0 += kU) {
     double nxt[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int r = r0 + kU + u;
-      nxt[u] = (r < m) ? pc[(size_t)(r + 2) * B] : 0.0;
+      nxt[u] = (r < m) ? pc[(size_t)r * B] : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int r = r0 + u;
       if (r < m) {
-        const double b2 = buf[u];
-        const double f = fma(w2, a2 + b2, fma(w1, a1 + b1, w0 * a0));
+        const double f = buf[u];
         const double g = (f - FAC(2, r) * g2 - FAC(1, r) * g1) * FAC(0, r);
         t0 = fma(FAC(5, r), f, t0);
         t1 = fma(FAC(6, r), f, t1);
-        pc[(size_t)r * B] = g;  // rows >= r + 1 of C are still unwritten
+        pg[(size_t)r * B] = g;
         g2 = g1;
         g1 = g;
-        a2 = a1;
-        a1 = a0;
-        a0 = b1;
-        b1 = b2;
       }
     }
 #pragma unroll
     for (int u = 0; u < kU; ++u) buf[u] = nxt[u];
   }
-  // tail rows m = n-2 (a0) and m+1 = n-1 (b1), wrapping onto c_0, c_1
-  const double fm = fma(w2, a2 + c0, fma(w1, a1 + b1, w0 * a0));
-  const double fl = fma(w2, a1 + c1, fma(w1, a0 + c0, w0 * b1));
   if (PER) {
     const size_t base = (size_t)9 * m * B + (size_t)s;
     s00 = __ldg(&fac[base]);
@@ -102,38 +98,45 @@ __global__ void __launch_bounds__(kThreads) cn_penta_kernel(double* c, int n, in
     s10 = __ldg(&fac[base + 2 * B]);
     s11 = __ldg(&fac[base + 3 * B]);
   }
+  const double fm = pc[(size_t)m * B], fl = pc[(size_t)(m + 1) * B];
   const double r0v = fm - t0, r1v = fl - t1;
   const double xt0 = s00 * r0v + s01 * r1v, xt1 = s10 * r0v + s11 * r1v;
-  pc[(size_t)m * B] = xt0;
-  pc[(size_t)(m + 1) * B] = xt1;
-  double x1 = 0, x2 = 0;
+  pc[(size_t)m * B] = fma(2.0, xt0, -fm);
+  pc[(size_t)(m + 1) * B] = fma(2.0, xt1, -fl);
+  double x1 = 0, x2 = 0;  // u of rows r+1, r+2
+  double gb[kU], cb[kU];
 #pragma unroll
   for (int u = 0; u < kU; ++u) {
     const int r = m - 1 - u;
-    buf[u] = (r >= 0) ? pc[(size_t)r * B] : 0.0;
+    gb[u] = (r >= 0) ? pg[(size_t)r * B] : 0.0;
+    cb[u] = (r >= 0) ? pc[(size_t)r * B] : 0.0;
   }
   for (int r0 = m - 1; r0 >= 0; r0 -= kU) {
-    double nxt[kU];
+    double gn[kU], cn[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int r = r0 - kU - u;
-      nxt[u] = (r >= 0) ? pc[(size_t)r * B] : 0.0;
+      gn[u] = (r >= 0) ? pg[(size_t)r * B] : 0.0;
+      cn[u] = (r >= 0) ? pc[(size_t)r * B] : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int r = r0 - u;
       if (r >= 0) {
-        double v = fma(-FAC(7, r), xt0, buf[u]);
+        double v = fma(-FAC(7, r), xt0, gb[u]);
         v = fma(-FAC(8, r), xt1, v);
-        v = fma(-FAC(3, r), x1, v);
         v = fma(-FAC(4, r), x2, v);
-        pc[(size_t)r * B] = v;
+        v = fma(-FAC(3, r), x1, v);
+        pc[(size_t)r * B] = fma(2.0, v, -cb[u]);
         x2 = x1;
         x1 = v;
       }
     }
 #pragma unroll
-    for (int u = 0; u < kU; ++u) buf[u] = nxt[u];
+    for (int u = 0; u < kU; ++u) {
+      gb[u] = gn[u];
+      cb[u] = cn[u];
+    }
   }
 #undef FAC
 }
@@ -141,76 +144,70 @@ __global__ void __launch_bounds__(kThreads) cn_penta_kernel(double* c, int n, in
 // Tridiagonal (order 2), Thomas with the Sherman-Morrison correction folded
 // into the sweeps as in tri.cu.  Factor rows [rden, a, chat, z, omega].
 template <bool PER>
-__global__ void __launch_bounds__(kThreads) cn_tri_kernel(double* c, int n, int batch, double sg,
+__global__ void __launch_bounds__(kThreads) cn_tri_kernel(double* c, double* __restrict__ gs, int n, int batch,
                                                           const double* __restrict__ fac) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= batch) return;
   const size_t B = (size_t)batch;
   const size_t fst = PER ? B : 1, fofs = PER ? (size_t)s : 0;
 #define FAC(k, r) __ldg(&fac[((size_t)(k) * n + (r)) * fst + fofs])
-  const double w0 = fma(-2.0, sg, 1.0);
   double* pc = c + s;
-  const double c0 = pc[0];
-  double a1 = pc[(size_t)(n - 1) * B], a0 = c0;  // window c_{r-1}, c_r
+  double* pg = gs + s;
   double d1 = 0, phi = 0;
-  const int last = n - 1;  // rows 0..n-2 read c_{r+1} from memory, row n-1 wraps to c_0
   double buf[kU];
 #pragma unroll
-  for (int u = 0; u < kU; ++u) buf[u] = (u < last) ? pc[(size_t)(u + 1) * B] : 0.0;
-  for (int r0 = 0; r0 < last; r0 += kU) {
+  for (int u = 0; u < kU; ++u) buf[u] = (u < n) ? pc[(size_t)u * B] : 0.0;
+  for (int r0 = 0; r0 < n; r0 += kU) {
     double nxt[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int r = r0 + kU + u;
-      nxt[u] = (r < last) ? pc[(size_t)(r + 1) * B] : 0.0;
+      nxt[u] = (r < n) ? pc[(size_t)r * B] : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int r = r0 + u;
-      if (r < last) {
-        const double b1 = buf[u];
-        const double f = fma(sg, a1 + b1, w0 * a0);
-        const double dh = fma(-FAC(1, r), d1, f) * FAC(0, r);
+      if (r < n) {
+        const double dh = fma(-FAC(1, r), d1, buf[u]) * FAC(0, r);
         phi = fma(FAC(4, r), dh, phi);
-        pc[(size_t)r * B] = dh;
+        pg[(size_t)r * B] = dh;
         d1 = dh;
-        a1 = a0;
-        a0 = b1;
       }
     }
 #pragma unroll
     for (int u = 0; u < kU; ++u) buf[u] = nxt[u];
   }
-  {
-    const double f = fma(sg, a1 + c0, w0 * a0);
-    const double dh = fma(-FAC(1, last), d1, f) * FAC(0, last);
-    phi = fma(FAC(4, last), dh, phi);
-    pc[(size_t)last * B] = dh;
-  }
   double y1 = 0;
+  double gb[kU], cb[kU];
 #pragma unroll
   for (int u = 0; u < kU; ++u) {
     const int r = n - 1 - u;
-    buf[u] = (r >= 0) ? pc[(size_t)r * B] : 0.0;
+    gb[u] = (r >= 0) ? pg[(size_t)r * B] : 0.0;
+    cb[u] = (r >= 0) ? pc[(size_t)r * B] : 0.0;
   }
   for (int r0 = n - 1; r0 >= 0; r0 -= kU) {
-    double nxt[kU];
+    double gn[kU], cn[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int r = r0 - kU - u;
-      nxt[u] = (r >= 0) ? pc[(size_t)r * B] : 0.0;
+      gn[u] = (r >= 0) ? pg[(size_t)r * B] : 0.0;
+      cn[u] = (r >= 0) ? pc[(size_t)r * B] : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int r = r0 - u;
       if (r >= 0) {
-        const double y = fma(-FAC(2, r), y1, buf[u]);
-        pc[(size_t)r * B] = fma(-phi, FAC(3, r), y);
+        const double y = fma(-FAC(2, r), y1, gb[u]);
+        const double x = fma(-phi, FAC(3, r), y);  // u = A^{-1} C^n
+        pc[(size_t)r * B] = fma(2.0, x, -cb[u]);
         y1 = y;
       }
     }
 #pragma unroll
-    for (int u = 0; u < kU; ++u) buf[u] = nxt[u];
+    for (int u = 0; u < kU; ++u) {
+      gb[u] = gn[u];
+      cb[u] = cn[u];
+    }
   }
 #undef FAC
 }
@@ -247,6 +244,7 @@ void* cn1d_inner_plan(chx_cn1d_plan* p) {
 void cn1d_plan_free(chx_cn1d_plan* p) {
   if (!p) return;
   if (p->d_fac) cudaFree(p->d_fac);
+  if (p->d_g) cudaFree(p->d_g);
   if (p->d_coef) cudaFree(p->d_coef);
   if (p->penta) penta_plan_free(p->penta);
   if (p->tri) tri_plan_free(p->tri);
@@ -294,6 +292,12 @@ extern "C" int cn1d_plan_create(chx_cn1d_plan** plan, int order, int n, int batc
   p->batch = batch;
   p->rewrite = rewrite;
   p->sigma = order == 4 ? kappa * dt / (2.0 * dx * dx * dx * dx) : kappa * dt / (2.0 * dx * dx);
+  if (cudaMalloc(&p->d_g, (size_t)n * batch * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    p->d_g = nullptr;
+    cn1d_plan_free(p);
+    return fail(CHX_ENOMEM, "cn1d_plan_create: sweep scratch");
+  }
   double v[5];
   implicit_coefs(order, p->sigma, v);
   if (rewrite) {
@@ -365,15 +369,15 @@ extern "C" int cn1d_step(chx_cn1d_plan* p, double* c, int nsteps, void* stream) 
       if (rc) return rc;
       // the refactor records the inner plan's stream; the sweep follows on `st`
       if (p->order == 4)
-        cn_penta_kernel<true><<<grid, blk, 0, st>>>(c, p->n, p->batch, p->sigma, penta_plan_factors(p->penta), 0,
-                                                         0, 0, 0);
+        cn_penta_kernel<true><<<grid, blk, 0, st>>>(c, p->d_g, p->n, p->batch, penta_plan_factors(p->penta), 0, 0, 0,
+                                                    0);
       else
-        cn_tri_kernel<true><<<grid, blk, 0, st>>>(c, p->n, p->batch, p->sigma, tri_plan_factors(p->tri));
+        cn_tri_kernel<true><<<grid, blk, 0, st>>>(c, p->d_g, p->n, p->batch, tri_plan_factors(p->tri));
     } else if (p->order == 4) {
-      cn_penta_kernel<false><<<grid, blk, 0, st>>>(c, p->n, p->batch, p->sigma, p->d_fac, p->sinv[0],
-                                                        p->sinv[1], p->sinv[2], p->sinv[3]);
+      cn_penta_kernel<false><<<grid, blk, 0, st>>>(c, p->d_g, p->n, p->batch, p->d_fac, p->sinv[0], p->sinv[1],
+                                                   p->sinv[2], p->sinv[3]);
     } else {
-      cn_tri_kernel<false><<<grid, blk, 0, st>>>(c, p->n, p->batch, p->sigma, p->d_fac);
+      cn_tri_kernel<false><<<grid, blk, 0, st>>>(c, p->d_g, p->n, p->batch, p->d_fac);
     }
   }
   p->hdr.last_stream = st;
