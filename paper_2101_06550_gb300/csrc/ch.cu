@@ -1002,8 +1002,10 @@ static void launch_local(const TIn* f, TC* y, int ld, int nsys, const DirView<TC
   }
 }
 
-// Reduced solves: four rows per thread, in single-warp blocks when the grid is
-// small (the balance rule of the one-thread-per-system kernels).
+// FP64 reduced solves: four rows per thread, in single-warp blocks when the
+// grid is small (the balance rule of the one-thread-per-system kernels).  The
+// FP32 path keeps one row per thread: its arithmetic is cheap, and four times
+// the threads hide more load latency (measured 10.4 us against 14 us at 2048^2).
 template <typename TC>
 static void launch_reduced(const TC* yb, const DirView<TC>& D, TC* tau, int nsys, size_t ybz, int Z, cudaStream_t st) {
   const unsigned blk = balanced_block((size_t)nsys * D.P * Z);
