@@ -510,7 +510,8 @@ __global__ void __launch_bounds__(kT* kBY) ch_xfinish_kernel(const TC* __restric
   for (int k = 0; k < kT / kBY; ++k) {
     const int li = threadIdx.y + k * kBY, i = i0 + li;
     if (i < nx && j < ny) {
-      const int s = i / m, r = i - s * m;
+      int s, r;
+      seg_row(i, m, D.rm, s, r);
       s_t[li][threadIdx.x] = (TO)spike_apply(y1[(size_t)i * ld + sys], vw, t1, m, P, G * ny, s, r, sys);
     }
   }
@@ -770,11 +771,11 @@ template <typename T>
 DirView<T> view(const SpikeDir& D, int spp);
 template <>
 DirView<double> view<double>(const SpikeDir& D, int spp) {
-  return DirView<double>{D.d_a, D.d_lu, D.d_vw, D.d_rinv, D.m, D.P, spp, D.band};
+  return DirView<double>{D.d_a, D.d_lu, D.d_vw, D.d_rinv, D.m, D.P, spp, D.band, 1.0f / (float)D.m};
 }
 template <>
 DirView<float> view<float>(const SpikeDir& D, int spp) {
-  return DirView<float>{D.d_a32, D.d_lu32, D.d_vw32, D.d_rinv32, D.m, D.P, spp, D.band};
+  return DirView<float>{D.d_a32, D.d_lu32, D.d_vw32, D.d_rinv32, D.m, D.P, spp, D.band, 1.0f / (float)D.m};
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }

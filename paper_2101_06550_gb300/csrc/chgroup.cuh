@@ -38,7 +38,23 @@ struct DirView {
   const T* vw;
   const T* rinv;
   int m, P, spp, band;
+  float rm;  // 1 / m, for seg_row
 };
+
+// Segment s and row r of global row i for segments of m rows, without an
+// integer division: a float reciprocal estimate, then one correction step
+// (the estimate is off by at most one for i < 2^22).
+__device__ __forceinline__ void seg_row(int i, int m, float rm, int& s, int& r) {
+  s = (int)((float)i * rm);
+  r = i - s * m;
+  if (r < 0) {
+    --s;
+    r += m;
+  } else if (r >= m) {
+    ++s;
+    r -= m;
+  }
+}
 
 // Per-kernel CUDA-event timing (ch_profile).
 enum ProfSlot { kRhs, kLocX, kRedX, kRefX, kLoc2X, kRed2X, kFinX, kLocY, kRedY, kRefY, kLoc2Y, kRed2Y, kUpd, kSlots };

@@ -134,15 +134,6 @@ __device__ __forceinline__ float corr32(const float* __restrict__ vw, const floa
   return c;
 }
 
-// First FP32 solution at global row i (wrapped) of system j.
-__device__ __forceinline__ float x0_at(const float* __restrict__ y1, const float* __restrict__ t1,
-                                       const float* __restrict__ vw, int n, int m, int P, int ld, int nsys, int i,
-                                       int j) {
-  i = wrapi(i, n);
-  const int s = i / m, r = i - s * m;
-  return y1[(size_t)i * ld + j] - corr32(vw, t1, m, P, nsys, s, r, j);
-}
-
 // A x0 for the ADI row (a, -4a, 1 + 6a, -4a, a): x0 + a * delta^4 x0, the fourth
 // difference formed with error-free sums.
 __device__ __forceinline__ ff adi_apply_ff(float w0, float w1, float w2, float w3, float w4, ff a) {
@@ -183,7 +174,8 @@ __global__ void __launch_bounds__(kT* kBY) ch_resid_ff_kernel(
     if (live) {
       int i = i0 - 2 + ly;
       i = i < 0 ? i + n : (i >= n ? i - n : i);
-      const int s = i / m, r = i - s * m;
+      int s, r;
+      seg_row(i, m, D.rm, s, r);
       const int sn = s + 1 == P ? 0 : s + 1, sp = s == 0 ? P - 1 : s - 1;
       float c = __ldg(&vw[r]) * t1[(size_t)(4 * sn) * S + j];
       c = fmaf(__ldg(&vw[m + r]), t1[(size_t)(4 * sn + 1) * S + j], c);
@@ -227,7 +219,8 @@ __global__ void __launch_bounds__(kT* kBY) ch_xfinish_ff_kernel(const float* __r
   for (int k = 0; k < kT / kBY; ++k) {
     const int li = threadIdx.y + k * kBY, i = i0 + li;
     if (i < nx && j < ny) {
-      const int s = i / m, r = i - s * m;
+      int s, r;
+      seg_row(i, m, D.rm, s, r);
       const float x0 = y1[(size_t)i * ld + sys];  // corrected first solution
       const float dl = y2[(size_t)i * ld + sys] - corr32(vw, t2, m, P, G * ny, s, r, sys);
       s_t[li][threadIdx.x] = two_sum(x0, dl);
