@@ -169,6 +169,10 @@ __global__ void __launch_bounds__(kT* kBY) ch_resid_ff_kernel(
   const int slot = blockIdx.z + (live ? j : 0) / D.spp;
   const float* vw = D.vw + (size_t)slot * 4 * m;
   const size_t S = (size_t)nsys;
+  // a warp's rows share threadIdx.y, so the segment (and its four reduced
+  // unknowns) changes warp-uniformly and rarely: load them once per segment
+  int cs = -1;
+  float ta = 0.f, tb = 0.f, tc = 0.f, td = 0.f;
   for (int ly = threadIdx.y; ly < kT + 4; ly += kBY) {
     float v = 0.f;
     if (live) {
@@ -176,11 +180,18 @@ __global__ void __launch_bounds__(kT* kBY) ch_resid_ff_kernel(
       i = i < 0 ? i + n : (i >= n ? i - n : i);
       int s, r;
       seg_row(i, m, D.rm, s, r);
-      const int sn = s + 1 == P ? 0 : s + 1, sp = s == 0 ? P - 1 : s - 1;
-      float c = __ldg(&vw[r]) * t1[(size_t)(4 * sn) * S + j];
-      c = fmaf(__ldg(&vw[m + r]), t1[(size_t)(4 * sn + 1) * S + j], c);
-      c = fmaf(__ldg(&vw[2 * m + r]), t1[(size_t)(4 * sp + 2) * S + j], c);
-      c = fmaf(__ldg(&vw[3 * m + r]), t1[(size_t)(4 * sp + 3) * S + j], c);
+      if (s != cs) {
+        cs = s;
+        const int sn = s + 1 == P ? 0 : s + 1, sp = s == 0 ? P - 1 : s - 1;
+        ta = t1[(size_t)(4 * sn) * S + j];
+        tb = t1[(size_t)(4 * sn + 1) * S + j];
+        tc = t1[(size_t)(4 * sp + 2) * S + j];
+        td = t1[(size_t)(4 * sp + 3) * S + j];
+      }
+      float c = __ldg(&vw[r]) * ta;
+      c = fmaf(__ldg(&vw[m + r]), tb, c);
+      c = fmaf(__ldg(&vw[2 * m + r]), tc, c);
+      c = fmaf(__ldg(&vw[3 * m + r]), td, c);
       v = y1[(size_t)i * ld + j] - c;
     }
     sx[ly][threadIdx.x] = v;
@@ -215,14 +226,29 @@ __global__ void __launch_bounds__(kT* kBY) ch_xfinish_ff_kernel(const float* __r
   const int j = j0 + threadIdx.x;
   const size_t ld = (size_t)G * ny;
   const int sys = z * ny + j;
+  const size_t S = (size_t)G * ny;
+  int cs = -1;  // the correction's reduced unknowns, loaded once per segment (warp-uniform)
+  float ta = 0.f, tb = 0.f, tc = 0.f, td = 0.f;
 #pragma unroll
   for (int k = 0; k < kT / kBY; ++k) {
     const int li = threadIdx.y + k * kBY, i = i0 + li;
     if (i < nx && j < ny) {
       int s, r;
       seg_row(i, m, D.rm, s, r);
+      if (s != cs) {
+        cs = s;
+        const int sn = s + 1 == P ? 0 : s + 1, sp = s == 0 ? P - 1 : s - 1;
+        ta = t2[(size_t)(4 * sn) * S + sys];
+        tb = t2[(size_t)(4 * sn + 1) * S + sys];
+        tc = t2[(size_t)(4 * sp + 2) * S + sys];
+        td = t2[(size_t)(4 * sp + 3) * S + sys];
+      }
+      float c = __ldg(&vw[r]) * ta;
+      c = fmaf(__ldg(&vw[m + r]), tb, c);
+      c = fmaf(__ldg(&vw[2 * m + r]), tc, c);
+      c = fmaf(__ldg(&vw[3 * m + r]), td, c);
       const float x0 = y1[(size_t)i * ld + sys];  // corrected first solution
-      const float dl = y2[(size_t)i * ld + sys] - corr32(vw, t2, m, P, G * ny, s, r, sys);
+      const float dl = y2[(size_t)i * ld + sys] - c;
       s_t[li][threadIdx.x] = two_sum(x0, dl);
     }
   }
