@@ -57,8 +57,9 @@ enum { CHX_COEF_UNIFORM = 0, CHX_COEF_SHARED = 1, CHX_COEF_PER_SYSTEM = 2 };
 
 enum { CHX_PREMAP_NONE = 0, CHX_PREMAP_CUBIC_MINUS_C = 1 };
 
-/* ch_step precision: plain FP64, or FP32 sweeps with one FP64-residual
- * refinement per pentadiagonal solve (FP64 state and update). */
+/* ch_step precision: plain FP64, or FP32 sweeps with one refinement pass per
+ * pentadiagonal solve whose residual, like the right-hand side, is formed in
+ * double-float arithmetic (FP64 state and update). */
 enum { CHX_PREC_F64 = 0, CHX_PREC_F32_REFINE = 1 };
 
 typedef struct chx_penta_plan chx_penta_plan;
@@ -164,7 +165,11 @@ int tri_cyclic_solve_batched(chx_tri_plan* plan, void* rhs_inout, int batch, voi
  *   nx * ny doubles (row-major, ld = nx) that keep their roles: on return
  *   c_now = C^{n+nsteps} and c_prev = C^{n+nsteps-1}.  work must hold at
  *   least ch_work_bytes(plan) bytes, 256-byte aligned, and must not overlap
- *   the fields.  Errors: CHX_EINVAL, CHX_ECUDA.
+ *   the fields.  A call that repeats the previous call's three pointers, or
+ *   runs four or more steps, replays CUDA graphs captured for those pointers
+ *   (two steps, and one role-keeping step); the first such call captures them.
+ *   While per-kernel profiling is on (ch_profile) the kernels launch one by
+ *   one instead.  Errors: CHX_EINVAL, CHX_ECUDA.
  * ch_diagnostics: mass = sum c dx dy and free energy
  *   F_h = sum [ (1/4)(c^2-1)^2 + (gamma/2)(|D+x c|^2 + |D+y c|^2) ] dx dy
  *   (forward differences, periodic; Sec. 2.5 with the bulk density read as
