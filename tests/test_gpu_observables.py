@@ -135,3 +135,34 @@ def test_coarsening_run_on_device():
     beta = chx.coarsening_rate(np.array(t), rows[:, 1])
     assert np.all(beta[late] > 0)
     assert np.allclose(beta, oracle.coarsening_rate(np.array(t), rows[:, 1]), rtol=1e-9)
+
+
+def test_coarsening_follows_the_one_third_law():
+    # Sec. 3.6 (fig3:scaling): after a deep quench s(t) and 1/k1(t) grow as
+    # t^(1/3) and F(t) decays as t^(-1/3).  On an 8 pi x 8 pi domain (2048^2,
+    # gamma = 0.01, dt = 0.1 dx, C(x, 0) uniform in [-0.1, 0.1]) the domains
+    # stay far from the box size up to t = 40; the fitted exponents over
+    # t in [10, 40] are within 0.03 of 1/3 (a full run to t = 80 gives 0.335,
+    # 0.330 and -0.338).
+    chx = _chx()
+    n, l, gamma = 2048, 8 * np.pi, 0.01
+    dt = 0.1 * l / n
+    plan = chx.ChPlan(n, n, l, l, gamma, dt)
+    cn = torch.from_numpy(synth.field(1, n, n, -0.1, 0.1)).to(DEV).reshape(-1)
+    cp = cn.clone()
+    work = plan.alloc_work(DEV)
+    out = torch.empty(4, dtype=torch.float64, device=DEV)
+    every = int(round(2.0 / dt))
+    t, rows = 0.0, []
+    while t < 40.0:
+        plan.step(cn, cp, work, every)
+        t += every * dt
+        plan.observables(cn, out)
+        rows.append([t] + out.cpu().tolist())
+    plan.sync_status()
+    rows = np.array(rows)
+    m = rows[:, 0] >= 10.0
+    lt = np.log(rows[m, 0])
+    assert abs(np.polyfit(lt, np.log(rows[m, 3]), 1)[0] - 1 / 3) < 0.03      # s
+    assert abs(np.polyfit(lt, -np.log(rows[m, 4]), 1)[0] - 1 / 3) < 0.03     # 1/k1
+    assert abs(np.polyfit(lt, np.log(rows[m, 2]), 1)[0] + 1 / 3) < 0.03      # F
