@@ -305,3 +305,42 @@ def test_ch_step_host_matches_device_step():
         torch.cuda.synchronize()
         assert torch.equal(h_out, a.cpu()) and torch.equal(d_now, a), steps
     plan.sync_status()
+
+
+def test_self_convergence_order_matches_the_paper_table():
+    # Sec. 3.5.3, Table table:converge2D: the 2D scheme's self-convergence with
+    # IC eps tanh(r - pi) (eps = 1e-6, r the distance from the domain centre),
+    # gamma = 0.01, T = 10, dt = 0.1 dx.  E_N = RMS of C_N minus the 2x2 cell
+    # averages of C_2N; the observed order log2(E_N / E_2N) at N = 256 and 512
+    # must match the table's within 0.1 (the absolute E_N depend on conventions
+    # the text leaves open; ours are within 25% of the printed ones).
+    import os
+
+    chx = _chx()
+    rows = {}
+    for ln in open(os.path.join(os.path.dirname(__file__), "golden", "table_converge2d.txt")):
+        if ln.strip() and not ln.startswith("#"):
+            nn, en, order = ln.split()
+            rows[int(nn)] = (float(en), float(order))
+    l, gamma, t_end, eps = 2 * np.pi, 0.01, 10.0, 1e-6
+    fields = {}
+    for n in (256, 512, 1024):
+        x = np.arange(n) * l / n
+        xx, yy = np.meshgrid(x, x)
+        c0 = eps * np.tanh(np.sqrt((xx - np.pi) ** 2 + (yy - np.pi) ** 2) - np.pi)
+        dt = 0.1 * l / n
+        plan = chx.ChPlan(n, n, l, l, gamma, dt)
+        cn = torch.from_numpy(c0).to(DEV).reshape(-1)
+        cp = cn.clone()
+        plan.step(cn, cp, plan.alloc_work(DEV), int(round(t_end / dt)))
+        plan.sync_status()
+        fields[n] = cn.cpu().numpy().reshape(n, n)
+
+    def err(n):
+        f = fields[2 * n]
+        avg = 0.25 * (f[0::2, 0::2] + f[1::2, 0::2] + f[0::2, 1::2] + f[1::2, 1::2])
+        return float(np.sqrt(np.mean((fields[n] - avg) ** 2)))
+
+    order = np.log2(err(256) / err(512))
+    assert abs(order - rows[256][1]) < 0.1, order
+    assert 0.75 < err(256) / rows[256][0] < 1.25
