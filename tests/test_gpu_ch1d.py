@@ -56,3 +56,27 @@ def test_ch1d_rejects_bad_arguments():
         chx.Ch1DPlan(4, 10, 1.0, 0.01, 1e-3)
     with pytest.raises(chx.ChxError):
         chx.Ch1DPlan(16, 10, 1.0, 0.01, 0.0)
+
+
+def test_ch1d_convergence_study_on_device():
+    # Table table5:converge1D rerun on the device (the oracle pin fixes the
+    # reading: t = 2, max-norm against the 2N grid's common points)
+    import os
+
+    import paper_2101_06550_gb300 as chx
+
+    rows = {}
+    for ln in open(os.path.join(os.path.dirname(__file__), "golden", "table_converge1d.txt")):
+        if ln.strip() and not ln.startswith("#"):
+            n, e, o = ln.split()
+            rows[int(n)] = (float(e), float(o))
+    l, gamma, t_end, eps = 2 * np.pi, 0.01, 2.0, 1e-6
+    res = {}
+    for n in (256, 512, 1024):
+        x = np.arange(n) * l / n
+        dt = 0.1 * l / n
+        c = torch.from_numpy(eps * np.cos(5 * x)).to("cuda")
+        chx.Ch1DPlan(n, 1, l, gamma, dt).step(c, int(round(t_end / dt)))
+        res[n] = c.cpu().numpy()
+    e = {n: float(np.max(np.abs(res[n] - res[2 * n][0::2]))) for n in (256, 512)}
+    assert abs(np.log2(e[256] / e[512]) - rows[256][1]) < 0.05
