@@ -258,3 +258,26 @@ def coarsening_rate(t, F):
     three-point central differences inside, three-point one-sided at the ends."""
     t, F = _f64(t), _f64(F)
     return -(t / F) * np.gradient(F, t, edge_order=2)
+
+
+# --------------------------------------------------------------------------- grid-refinement error
+def refinement_error_1d(fine, coarse):
+    """E_N of Eq. eq2:converge1D (Sec. 2.1.3): the mean absolute difference between
+    a periodic solution on N points and the one on N/2 points, taken at the
+    coarse grid's points (fine points 0, 2, 4, ... in 0-based indexing)."""
+    fine, coarse = _f64(fine), _f64(coarse)
+    if fine.shape[-1] != 2 * coarse.shape[-1]:
+        raise OracleError("fine grid must have twice the coarse grid's points")
+    return float(np.mean(np.abs(fine[..., 0::2] - coarse)))
+
+
+def refinement_error_2d(fine, coarse):
+    """E_N of Eq. eq2:converge2D (Sec. 2.1.3): the mean absolute difference between
+    each coarse point's value and the average of the 2x2 block of fine points
+    whose first corner it shares (fine rows and columns 2i, 2i + 1 in 0-based
+    indexing), over the (N/2)^2 coarse points."""
+    fine, coarse = _f64(fine), _f64(coarse)
+    if fine.shape != (2 * coarse.shape[0], 2 * coarse.shape[1]):
+        raise OracleError("fine grid must have twice the coarse grid's points in each direction")
+    block = 0.25 * (fine[0::2, 0::2] + fine[1::2, 0::2] + fine[0::2, 1::2] + fine[1::2, 1::2])
+    return float(np.mean(np.abs(block - coarse)))
