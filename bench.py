@@ -433,7 +433,7 @@ def bench_solvers(dev, reps=5):
 
 
 def bench_ch1d(dev, steps=20):
-    """Batched 1D Cahn-Hilliard (Sec. 6.2.4): 2^20 simulations of N = 256, dt = 0.1 dx, FP64."""
+    """Batched 1D Cahn-Hilliard (Sec. 6.2.3): 2^20 simulations of N = 256, dt = 0.1 dx, FP64."""
     import torch
 
     import paper_2101_06550_gb300 as chx
@@ -500,7 +500,7 @@ def bench_cn1d(dev, steps=100, rewrite_steps=20):
 
 
 def bench_cook(dev, steps=50):
-    """Cahn-Hilliard-Cook runs (Sec. 7.6) on the 2048^2 workload: C = 0 initially,
+    """Cahn-Hilliard-Cook runs (Sec. 7.7) on the 2048^2 workload: C = 0 initially,
     sigma = 1e-14, fresh Philox + Box-Muller deviates every step, FP64 step."""
     import torch
 
@@ -579,7 +579,7 @@ def bench_ensemble(dev, precision, steps, warmup, count=512):
 
 
 def bench_coarsening_stats(dev, sims=1024, samples=20, every=10):
-    """The statistics workload of Sec. 7.2: a batch of 1024 simulations on the
+    """The statistics workload of Sec. 7.3.2: a batch of 1024 simulations on the
     2 pi x 2 pi domain (256^2, gamma = 0.01, dt = 0.1 dx, symmetric U[-0.1, 0.1]
     mixtures, FP64), the observables (mass, F, s, k1) of every simulation sampled
     every `every` steps on the device and beta = -(t/F) dF/dt formed per

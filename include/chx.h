@@ -172,7 +172,7 @@ int tri_cyclic_solve_batched(chx_tri_plan* plan, void* rhs_inout, int batch, voi
  *   one instead.  Errors: CHX_EINVAL, CHX_ECUDA.
  * ch_diagnostics: mass = sum c dx dy and free energy
  *   F_h = sum [ (1/4)(c^2-1)^2 + (gamma/2)(|D+x c|^2 + |D+y c|^2) ] dx dy
- *   (forward differences, periodic; Sec. 2.5 with the bulk density read as
+ *   (forward differences, periodic; Sec. 2.4 with the bulk density read as
  *   (1/4)(c^2-1)^2, the one whose derivative is c^3 - c).  mass_out and
  *   energy_out are DEVICE pointers to one double each, written asynchronously
  *   in a fixed summation order (bit-reproducible).  If c holds NaN or Inf, the
@@ -196,7 +196,7 @@ int ch_step_host(chx_ch_plan* plan, const double* h_now, const double* h_prev, d
 int ch_diagnostics(chx_ch_plan* plan, const double* c, double* mass_out, double* energy_out, void* stream);
 
 /*
- * Cahn-Hilliard-Cook equation (Sec. 7.6): the Cahn-Hilliard equation with the
+ * Cahn-Hilliard-Cook equation (Sec. 7.7): the Cahn-Hilliard equation with the
  * conserved thermal forcing eta, C_t = Lap(C^3 - C - gamma Lap C) + eta, with
  *   eta_ij = sqrt(sigma / (dx dy dt)) div_h rho_ij,
  *   div_h rho_ij = (rho^x_ij - rho^x_{i-1,j}) / dx + (rho^y_ij - rho^y_{i,j-1}) / dy
@@ -256,7 +256,7 @@ int ch_cook_run(chx_ch_plan* plan, double* c_now, double* c_prev, void* work, do
  * Errors: CHX_EINVAL, CHX_ENOMEM, CHX_ECUDA.
  *
  * chx_coarsening_rate: HOST arrays.  beta_k = -(t_k / F_k) dF/dt(t_k) (Eq.
- *   eq7:betaN; the thesis extracts dF/dt numerically, Sec. 7.2) for a sampled
+ *   eq7:betaN; the thesis extracts dF/dt numerically, Sec. 7.3.2) for a sampled
  *   series, dF/dt from the derivative of the quadratic through three
  *   neighbouring samples: centred inside, one-sided at the ends (second order
  *   on uneven spacing).  count >= 3, t strictly increasing, F finite and
@@ -267,7 +267,7 @@ int ens_group_observables(chx_ens* ens, int group_id, int with_k1, double* out, 
 int chx_coarsening_rate(const double* t, const double* F, int count, double* beta);
 
 /*
- * Batched 1D Cahn-Hilliard (Sec. 6.2.2, eq6:1Dnumerical): for every simulation s
+ * Batched 1D Cahn-Hilliard (Sec. 6.2.1, eq6:1Dnumerical): for every simulation s
  * of an interleaved batch c[i * batch + s] (i = 0..n-1, periodic on [0, l)),
  *   (I + sigma delta^4) C^{n+1} = C^n + alpha delta^2 (C^3 - C)^n,
  *   sigma = gamma dt / dx^4, alpha = dt / dx^2, dx = l / n
@@ -318,8 +318,8 @@ int cn1d_step(chx_cn1d_plan* plan, double* c, int nsteps, void* stream);
 /*
  * Ensemble runtime: many simulations of uneven sizes advanced together (the
  * batches of 2D simulations per domain size behind the thesis's statistics,
- * Sec. 7.2, and its note that batches of different sizes want one LHS per
- * distinct matrix, Sec. 9).  Every simulation is the ADI step of ch_step with
+ * Sec. 7.3.2, and its note that batches of different sizes want one LHS per
+ * distinct matrix, Sec. 8).  Every simulation is the ADI step of ch_step with
  * the ensemble's dt and precision on an n x n grid of side l.
  *  - A group holds simulations with the same (n, l): packed device-resident
  *    state (C^n, C^{n-1}) for `capacity` slots, per-slot LHS factors (so the
@@ -342,7 +342,7 @@ int cn1d_step(chx_cn1d_plan* plan, double* c, int nsteps, void* stream);
  *    partitioned sweeps and keeps the fastest; the simulations' state is saved
  *    and restored, so the call changes no result other than by rounding order.
  *  - ens_group_set_cook turns on the Cahn-Hilliard-Cook forcing of ch_cook_run
- *    (Sec. 7.6) for every slot of a group (either precision): each later step
+ *    (Sec. 7.7) for every slot of a group (either precision): each later step
  *    of the group first draws the deviates of slot s with simulation id s, key
  *    seed, at the group's step counter
  *    (starting at step0 and advanced on the device, so graph replays draw

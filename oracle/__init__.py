@@ -149,7 +149,7 @@ def ch_diagnostics(c, lx, ly, gamma):
 
 
 def ch1d_run(c, l, gamma, dt, nsteps=1, batch=1):
-    """Batched 1D Cahn-Hilliard steps (Sec. 6.2.2) on an interleaved (n * batch) array; returns a new array."""
+    """Batched 1D Cahn-Hilliard steps (Sec. 6.2.1) on an interleaved (n * batch) array; returns a new array."""
     c = _f64(c).ravel().copy()
     n = c.size // batch
     _check(lib().oracle_ch1d_run(n, batch, float(l), float(gamma), float(dt), int(nsteps), _p(c)))
@@ -180,7 +180,7 @@ def noise_normals(nx, ny, seed, sim, step):
 
 
 def cook_forcing(rho, lx, ly, dt, sigma):
-    """eta = sqrt(sigma / (dx dy dt)) div_h rho for rho of shape (2, ny, nx) (Sec. 7.6)."""
+    """eta = sqrt(sigma / (dx dy dt)) div_h rho for rho of shape (2, ny, nx) (Sec. 7.7)."""
     rho = _f64(rho)
     _, ny, nx = rho.shape
     eta = np.empty((ny, nx))
@@ -209,7 +209,7 @@ def ch_cook_run(c_now, c_prev, lx, ly, gamma, dt, sigma, seed, sim, step0, nstep
 # --------------------------------------------------------------------------- coarsening observables
 def simpson_mean(v):
     """Spatial average of a periodic (ny, nx) field by the composite Simpson rule
-    (Sec. 3.6) in each direction.  Closing the periodic interval [0, L] with
+    (Sec. 3.5.4) in each direction.  Closing the periodic interval [0, L] with
     f(L) = f(0), the rule's weights h/3 (1, 4, 2, ..., 4, 1) fold onto the grid as
     h/3 (2, 4, 2, 4, ...).  Reading: it needs an even number of intervals; for an
     odd count the trapezoid rule (all weights h) is used in that direction."""
@@ -227,12 +227,12 @@ def simpson_mean(v):
 
 
 def s_of_t(c):
-    """s = 1 / (1 - <C^2>) with <.> the Simpson average (Sec. 3.6)."""
+    """s = 1 / (1 - <C^2>) with <.> the Simpson average (Sec. 3.5.4)."""
     return 1.0 / (1.0 - simpson_mean(_f64(c) ** 2))
 
 
 def k1_of_t(c, lx, ly):
-    """k1 = sum |C^(k)|^2 / sum |k|^-1 |C^(k)|^2 over the discrete Fourier modes (Sec. 3.6),
+    """k1 = sum |C^(k)|^2 / sum |k|^-1 |C^(k)|^2 over the discrete Fourier modes (Sec. 3.5.4),
     k = (2 pi mx / lx, 2 pi my / ly).  Reading: the k = 0 mode (the mean, with no
     length scale and an infinite weight |k|^-1) is left out of both sums."""
     c = _f64(c)
@@ -253,7 +253,7 @@ def observables(c, lx, ly, gamma):
 
 
 def coarsening_rate(t, F):
-    """beta = -(t / F) dF/dt along a sampled series (Eq. eq7:betaN, Sec. 7.2), dF/dt
+    """beta = -(t / F) dF/dt along a sampled series (Eq. eq7:betaN, Sec. 7.2.3), dF/dt
     from second-order finite differences on the (possibly uneven) sample times:
     three-point central differences inside, three-point one-sided at the ends."""
     t, F = _f64(t), _f64(F)

@@ -18,7 +18,7 @@
  *     (Sec. 3.3, weights indexed from the top-left, i fastest, row by row in j);
  *   - the ADI step of Eq. 3.1 (eq3:ch_adi) with C-bar = 2C^n - C^{n-1},
  *     the 13-point biharmonic and the 5-point Laplacian (Sec. 3.5.1-3.5.2);
- *   - mass and free energy of a field (Sec. 2.5, eq2:dFdt_ch).
+ *   - mass and free energy of a field (Sec. 2.4, eq2:dFdt_ch).
  * Readings of garbled or silent passages are listed where they are used.
  */
 #include <math.h>
@@ -400,7 +400,7 @@ int oracle_ch_run(int nx, int ny, double lx, double ly, double gamma, double dt,
 }
 
 /* ---------------------------------------------------------------------------
- * Mass and discrete free energy (Sec. 2.5).  mass = sum c dx dy.
+ * Mass and discrete free energy (Sec. 2.4).  mass = sum c dx dy.
  * F_h = sum [ (1/4)(c^2 - 1)^2 + (gamma/2)(|D+x c|^2 + |D+y c|^2) ] dx dy with
  * forward differences and periodic wrap.  Reading: the printed bulk density
  * (1/2)(C^2-1)^2 does not have C^3 - C as its derivative, which the chemical
@@ -425,7 +425,7 @@ int oracle_ch_diagnostics(int nx, int ny, double lx, double ly, double gamma, co
 }
 
 /* ---------------------------------------------------------------------------
- * Batched 1D Cahn-Hilliard step (Sec. 6.2.2, eq6:1Dnumerical): on [0, l) with
+ * Batched 1D Cahn-Hilliard step (Sec. 6.2.1, eq6:1Dnumerical): on [0, l) with
  * dx = l/n, for every system s of the interleaved batch c[i*batch + s],
  *   (I + sigma delta^4) C^{n+1} = C^n + alpha delta^2 (C^3 - C)^n,
  *   sigma = gamma dt / dx^4, alpha = dt / dx^2, periodic in i.
@@ -517,7 +517,7 @@ done2:
 }
 
 /* ---------------------------------------------------------------------------
- * Cahn-Hilliard-Cook forcing (Sec. 7.6): C_t = D Lap(C^3 - C - gamma Lap C) + eta,
+ * Cahn-Hilliard-Cook forcing (Sec. 7.7): C_t = D Lap(C^3 - C - gamma Lap C) + eta,
  * eta_ij = sqrt(sigma / (dx dy dt)) div_h rho_ij, rho a 2-vector field of N(0,1)
  * deviates drawn afresh every step by the Box-Muller transform of uniforms.
  * Readings: div_h is the backward difference

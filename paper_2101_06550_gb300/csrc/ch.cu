@@ -92,7 +92,7 @@ __device__ __forceinline__ int wrap_near(int i, int n) {
 // coalesced, so the output needs no staging tile (31 KB of shared memory per
 // block: 7 blocks per SM).
 //
-// NOISE (Cahn-Hilliard-Cook, Sec. 7.6): adds (2/3) dt eta with
+// NOISE (Cahn-Hilliard-Cook, Sec. 7.7): adds (2/3) dt eta with
 // eta = sqrt(sigma / (dx dy dt)) div_h rho, the backward-difference divergence
 // of the deviates rho (planes rho^x, rho^y of nx*ny per simulation):
 // nkx (rho^x_ij - rho^x_{i-1,j}) + nky (rho^y_ij - rho^y_{i,j-1}), formed with

@@ -1,8 +1,8 @@
-// Batched 1D Cahn-Hilliard (Sec. 6.2.2, eq6:1Dnumerical):
+// Batched 1D Cahn-Hilliard (Sec. 6.2.1, eq6:1Dnumerical):
 //   (I + sigma delta^4) C^{n+1} = C^n + alpha delta^2 (C^3 - C)^n,
 //   sigma = gamma dt / dx^4, alpha = dt / dx^2, periodic,
 // for a batch of independent simulations in the interleaved layout
-// c[i * batch + s] (the thesis runs 2^20 of them at N = 256, Sec. 6.2.4).
+// c[i * batch + s] (the thesis runs 2^20 of them at N = 256, Sec. 6.2.3).
 //
 // One thread per simulation.  The right-hand side is formed inside the forward
 // sweep of the cyclic pentadiagonal solve (Navon bordering folded in, as in

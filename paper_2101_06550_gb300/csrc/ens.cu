@@ -1,5 +1,5 @@
 // Ensemble runtime: many Cahn-Hilliard simulations of uneven sizes advanced
-// together (the batched pattern the thesis's 2D statistics rest on, Sec. 7.2:
+// together (the batched pattern the thesis's 2D statistics rest on, Sec. 7.3.2:
 // batches of simulations per domain size, run concurrently).
 //
 // Simulations that share (n, L) form a group: one ChGroup (one set of batched

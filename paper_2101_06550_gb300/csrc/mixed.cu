@@ -51,7 +51,7 @@ __device__ __forceinline__ ff lap_ff(const ff (*t)[LD], int y, int x, ff rho, ff
 // rows per warp while staging, j along the warp for the output, whose
 // transposed stores are then coalesced without a staging tile.
 //
-// NOISE (Cahn-Hilliard-Cook, Sec. 7.6): the forcing term (2/3) dt eta is
+// NOISE (Cahn-Hilliard-Cook, Sec. 7.7): the forcing term (2/3) dt eta is
 // formed in FP64 on the otherwise idle FP64 unit (one subtraction and one FMA
 // per direction), as in the FP64 kernel, and added as a double-float pair.
 template <bool kIso, bool NOISE = false>

@@ -1,4 +1,4 @@
-// Normal deviates for the Cahn-Hilliard-Cook forcing (Sec. 7.6): a 2-vector
+// Normal deviates for the Cahn-Hilliard-Cook forcing (Sec. 7.7): a 2-vector
 // field rho of N(0, 1) numbers per grid point, drawn afresh every step by the
 // Box-Muller transform of uniforms.
 //

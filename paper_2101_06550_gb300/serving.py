@@ -8,7 +8,7 @@ arrive while others run join the running batch instead of waiting for it to
 drain.  A tick advances every active simulation by the smallest remaining step
 count (capped at ``chunk``), after which finished simulations are copied out
 and their slots compacted.  The thesis motivates the workload (batches of 2D
-simulations for growth-rate statistics, Sec. 7.2); it has no serving layer.
+simulations for growth-rate statistics, Sec. 7.3.2); it has no serving layer.
 
 This module is host-side scheduling only: all arithmetic runs in ``libchx.so``.
 """

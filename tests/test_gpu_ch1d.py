@@ -1,4 +1,4 @@
-"""GPU parity of the batched 1D Cahn-Hilliard step (Sec. 6.2.2) against the CPU oracle."""
+"""GPU parity of the batched 1D Cahn-Hilliard step (Sec. 6.2.1) against the CPU oracle."""
 import numpy as np
 import pytest
 
@@ -30,7 +30,7 @@ def test_ch1d_matches_oracle(n, batch):
 
 
 def test_ch1d_full_batch_sampled_and_mass():
-    # 2^20 simulations of N = 256 (Sec. 6.2.4): sampled systems against the
+    # 2^20 simulations of N = 256 (Sec. 6.2.3): sampled systems against the
     # oracle, and every system's mass conserved
     import paper_2101_06550_gb300 as chx
 

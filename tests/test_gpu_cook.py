@@ -1,4 +1,4 @@
-"""GPU parity of the Cahn-Hilliard-Cook forcing (Sec. 7.6): the Philox4x64-10 +
+"""GPU parity of the Cahn-Hilliard-Cook forcing (Sec. 7.7): the Philox4x64-10 +
 Box-Muller deviates, the forced ADI step with given deviates, and whole runs."""
 import numpy as np
 import pytest

@@ -107,7 +107,7 @@ def test_observables_flag_nonfinite():
 
 
 def test_coarsening_run_on_device():
-    # Sec. 3.6's run: 512^2, L = 2 pi, gamma = 0.01, dt = 0.1 dx, deep quench
+    # Sec. 3.5.4's run: 512^2, L = 2 pi, gamma = 0.01, dt = 0.1 dx, deep quench
     # C(x, 0) uniform in [-0.1, 0.1].  After the spinodal stage the domains
     # coarsen: s grows, k1 falls, F decreases and beta is positive.
     chx = _chx()
@@ -138,7 +138,7 @@ def test_coarsening_run_on_device():
 
 
 def test_coarsening_follows_the_one_third_law():
-    # Sec. 3.6 (fig3:scaling): after a deep quench s(t) and 1/k1(t) grow as
+    # Sec. 3.5.4 (fig3:scaling): after a deep quench s(t) and 1/k1(t) grow as
     # t^(1/3) and F(t) decays as t^(-1/3).  On an 8 pi x 8 pi domain (2048^2,
     # gamma = 0.01, dt = 0.1 dx, C(x, 0) uniform in [-0.1, 0.1]) the domains
     # stay far from the box size up to t = 40; the fitted exponents over

@@ -320,7 +320,7 @@ def test_synth_torch_matches_numpy():
     assert np.array_equal(a, b)
 
 
-# --------------------------------------------------------------------------- 1D Cahn-Hilliard (Sec. 6.2.2)
+# --------------------------------------------------------------------------- 1D Cahn-Hilliard (Sec. 6.2.1)
 def test_ch1d_linear_mode_closed_form():
     # small single mode: N(c) ~ -c, so each step multiplies the mode by
     # G = (1 + dt p) / (1 + gamma dt p^2), p = 4 sin^2(k dx / 2) / dx^2
@@ -413,7 +413,7 @@ def test_cn_mode_amplification_closed_form(order):
     assert np.max(np.abs(got - G**10 * np.cos(2 * np.pi * kk * x))) <= 1e-12
 
 
-# --------------------------------------------------------------------------- Cahn-Hilliard-Cook (Sec. 7.6)
+# --------------------------------------------------------------------------- Cahn-Hilliard-Cook (Sec. 7.7)
 @pytest.mark.parametrize("key,ctr", [((5, 7), (0, 0, 0, 0)), ((0, 0), (41, 3, 0, 0)),
                                      ((2**64 - 1, 12345), (2**64 - 1, 5, 9, 0))])
 def test_philox4x64_matches_numpy(key, ctr):
@@ -592,7 +592,7 @@ def _steps_to(t_end, dt):
 
 
 def test_ch1d_convergence_reproduces_the_paper_table():
-    # Table table5:converge1D: the oracle's 1D scheme (Sec. 6.2.2) on the printed
+    # Table table5:converge1D: the oracle's 1D scheme (Sec. 6.2.1) on the printed
     # study, measured by Eq. eq2:converge1D.  The final time is not printed; t = 20
     # reproduces every printed E_N from N = 128 to 512 to its last digit and the
     # observed orders to four decimals.
