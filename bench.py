@@ -36,8 +36,9 @@ SEED = 3
 WORKLOAD = "ch2d_periodic_2048sq_gamma0.005_dt5e-4"
 # DRAM bytes (read + write) per launch of the FP64 right-hand-side kernel on this
 # workload, from an ncu capture of the current kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum, mean of 3 launches; the written field partly stays in L2)
-RHS_TRAFFIC_BYTES = 67.21e6 + 4.01e6  # ncu: dram__bytes_read + write per ch_rhs launch (mean of 3)
+# dram__bytes_write.sum, mean of 3 launches; the two written fields, r / k2 and
+# Cbar, partly stay in L2 for the kernels that read them next)
+RHS_TRAFFIC_BYTES = 67.27e6 + 20.00e6  # ncu: dram__bytes_read + write per ch_rhs launch (mean of 3)
 
 
 def _peaks():
@@ -284,25 +285,27 @@ def run_chx(args, rank, world, local_rank):
     launches_per_step = sum(n for _, n in prof64.values()) / max(1, args.steps)
 
     # end to end through the C ABI with host buffers (ch_step_host): H2D of both
-    # fields from pinned memory, one step, D2H of the new field, every step.  Two plans
-    # with their own device fields alternate on two streams, so one step's copies
-    # overlap the other's kernels (the copy engines run beside the SMs).
+    # fields from pinned memory, one step, D2H of the new field, every step.  Three
+    # plans with their own device fields rotate over three streams, so the copy
+    # engines (the host link, not the SMs, bounds this number) stay busy while
+    # the kernels of the other lanes run.
+    lanes_n = 3
     h_cn = c0.cpu().pin_memory()
     h_cp = h_cn.clone().pin_memory()
-    h_out = [torch.empty_like(h_cn).pin_memory() for _ in range(2)]
-    plan_b = chx.ChPlan(N, N, LX, LX, GAMMA, DT, chx.PREC_F64)
-    lanes = [(plan64, cn64, cp64, work64), (plan_b, torch.empty_like(cn64), torch.empty_like(cp64),
-                                            plan_b.alloc_work(dev))]
-    e2e_streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+    h_out = [torch.empty_like(h_cn).pin_memory() for _ in range(lanes_n)]
+    extra_plans = [chx.ChPlan(N, N, LX, LX, GAMMA, DT, chx.PREC_F64) for _ in range(lanes_n - 1)]
+    lanes = [(plan64, cn64, cp64, work64)] + [(p, torch.empty_like(cn64), torch.empty_like(cp64), p.alloc_work(dev))
+                                              for p in extra_plans]
+    e2e_streams = [torch.cuda.Stream(device=dev) for _ in range(lanes_n)]
     e2e_steps = max(1, args.steps)
 
     def e2e_run(k_steps):
         for k in range(k_steps):
-            plan, dn, dp, wk = lanes[k & 1]
-            st = e2e_streams[k & 1]
-            plan.step_host(h_cn, h_cp, h_out[k & 1], dn, dp, wk, 1, stream=st)  # H2D, step, D2H in one call
+            plan, dn, dp, wk = lanes[k % lanes_n]
+            st = e2e_streams[k % lanes_n]
+            plan.step_host(h_cn, h_cp, h_out[k % lanes_n], dn, dp, wk, 1, stream=st)  # H2D, step, D2H in one call
 
-    e2e_run(4)  # warm: captures each lane's step graph
+    e2e_run(2 * lanes_n)  # warm: captures each lane's step graph
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -314,7 +317,8 @@ def run_chx(args, rank, world, local_rank):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    plan_b.sync_status()
+    for p in extra_plans:
+        p.sync_status()
 
     ms64, ms32, e2e_ms = max_over_ranks([ms64, ms32, e2e_ms], dist, dev)
     if rank != 0:
@@ -328,14 +332,14 @@ def run_chx(args, rank, world, local_rank):
     peaks = _peaks()
     # dominant kernel of the FP64 step and its roofline (FP64-pipe bound)
     dom, (dom_ms, dom_n) = max(prof64.items(), key=lambda kv: kv[1][0])
-    dp_ops = {"ch_rhs": 15.0, "spike_local_x": 5.0, "spike_local_y": 5.0, "ch_xfinish": 4.0, "ch_update": 6.0}
+    dp_ops = {"ch_rhs": 14.0, "spike_local_x": 5.0, "spike_local_y": 5.0, "ch_xfinish": 4.0, "ch_update": 5.0}
     per_launch_ms = dom_ms / max(1, dom_n)
     fp64_peak_gops = 1.90 * 152 * 2.070  # measured DFMA issue rate x SMs x max clock (G DP-ops/s)
     if dom in dp_ops:
         ach = dp_ops[dom] * pts / (per_launch_ms * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp64_peak_gops, "unit": "G fp64-op/s",
                 "frac": ach / fp64_peak_gops, "traffic": RHS_TRAFFIC_BYTES if dom == "ch_rhs" else None,
-                "traffic_unit": "bytes per launch", "algorithmic_bytes": 24 * pts, "ms_per_launch": per_launch_ms,
+                "traffic_unit": "bytes per launch", "algorithmic_bytes": 32 * pts, "ms_per_launch": per_launch_ms,
                 "peak_source": "measured DFMA microbenchmark 1.90/clk/SM x 152 SMs x 2070 MHz"}
     else:
         roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": fp64_peak_gops, "unit": "G fp64-op/s",

@@ -90,17 +90,22 @@ __device__ __forceinline__ int wrap_near(int i, int n) {
 // The last phase maps j along the warp: its column reads of the shared tiles
 // (odd row pitches) are free of bank conflicts and its transposed stores are
 // coalesced, so the output needs no staging tile (31 KB of shared memory per
-// block: 7 blocks per SM).
+// block: 7 blocks per SM; 39 KB and 5 blocks with the noise tile).
+//
+// The pass writes r / k2 with k2 = (2/3) dt / dx^2, i.e. Lap_h M - kd (C^n - C^{n-1})
+// with kd = dx^2 / dt: one FMA where r itself takes a multiply and an FMA.  The
+// solves are linear, so the update restores the scale (C^{n+1} = Cbar + k2 v').
 //
 // NOISE (Cahn-Hilliard-Cook, Sec. 7.7): adds (2/3) dt eta with
 // eta = sqrt(sigma / (dx dy dt)) div_h rho, the backward-difference divergence
 // of the deviates rho (planes rho^x, rho^y of nx*ny per simulation):
-// nkx (rho^x_ij - rho^x_{i-1,j}) + nky (rho^y_ij - rho^y_{i,j-1}), formed with
-// coalesced row reads into a shared tile first.
+// nkx (rho^x_ij - rho^x_{i-1,j}) + nky (rho^y_ij - rho^y_{i,j-1}) (nkx, nky
+// divided by k2 like the rest of the output), formed with coalesced row reads
+// into a shared tile first.
 template <typename TC, typename TO, bool NOISE = false>
-__global__ void __launch_bounds__(kT* kBY, 7) ch_rhs_kernel(const double* __restrict__ cn, const double* __restrict__ cp,
+__global__ void __launch_bounds__(kT* kBY, NOISE ? 5 : 7) ch_rhs_kernel(const double* __restrict__ cn, const double* __restrict__ cp,
                                                          TO* __restrict__ rT, int nx, int ny, int G, TC rho, TC kap,
-                                                         const TC* __restrict__ gls, TC k1, TC k2,
+                                                         const TC* __restrict__ gls, TC kd,
                                                          double* __restrict__ cbar,
                                                          const double* __restrict__ dev = nullptr, double nkx = 0,
                                                          double nky = 0) {
@@ -168,7 +173,7 @@ __global__ void __launch_bounds__(kT* kBY, 7) ch_rhs_kernel(const double* __rest
     l = fma(rho, s_m[ly - 1][lx] + s_m[ly + 1][lx], l);
     l = fma(kap, s_m[ly][lx], l);
     const TC diff = s_cb[ly + 1][lx + 1] - s_cn[ly + 1][lx + 1];  // C^n - C^{n-1}
-    TC o = fma(k2, l, -(k1 * diff));
+    TC o = fma(-kd, diff, l);
     if (NOISE) o += s_nz[lj][li];
     const int gi = i0 + li, gj = j0 + lj;
     if (gi < nx && gj < ny) rT[(size_t)gi * ldo + (size_t)z * ny + gj] = (TO)o;
@@ -451,9 +456,11 @@ __global__ void __launch_bounds__(kSolveThreads) spike_reduced_kernel(const TC* 
 // The same reduced solve with the four rows of one segment block per thread:
 // each boundary value loaded (from L2) serves four dot products instead of
 // one, which cuts the kernel's L2 traffic fourfold.  Grid (systems / blk, P, Z).
+// The outputs are multiplied by `scale` (the update's k2 for the y sweep).
 template <typename TC>
 __global__ void __launch_bounds__(kSolveThreads) spike_reduced4_kernel(const TC* __restrict__ yb, DirView<TC> D,
-                                                                       TC* __restrict__ tau, int nsys, size_t ybz) {
+                                                                       TC* __restrict__ tau, int nsys, size_t ybz,
+                                                                       TC scale) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nsys) return;
   const int P = D.P, k = 4 * P;
@@ -465,20 +472,30 @@ __global__ void __launch_bounds__(kSolveThreads) spike_reduced4_kernel(const TC*
   const int nb = 2 * D.band + 1 < P ? 2 * D.band + 1 : P;
   const int s0 = nb == P ? 0 : sq - D.band;
   TC acc[4] = {0, 0, 0, 0};
-  for (int bb = 0; bb < nb; ++bb) {
-    int sb = s0 + bb;
-    sb = sb < 0 ? sb + P : (sb >= P ? sb - P : sb);
-    const int pc = 4 * sb;
-    TC v[4];
+  // block bb + 1's boundary values are loaded while block bb's 16 FMAs issue
+  auto col = [&](int bb) {
+    const int sb = s0 + bb;
+    return 4 * (sb < 0 ? sb + P : (sb >= P ? sb - P : sb));
+  };
+  int pc = col(0);
+  TC v[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = yb[(size_t)(pc + u) * nsys + j];
+  for (int u = 0; u < 4; ++u) v[u] = yb[(size_t)(pc + u) * nsys + j];
+  for (int bb = 0; bb < nb; ++bb) {
+    const int pn = bb + 1 < nb ? col(bb + 1) : pc;
+    TC nv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) nv[u] = yb[(size_t)(pn + u) * nsys + j];
 #pragma unroll
     for (int o = 0; o < 4; ++o)
 #pragma unroll
       for (int u = 0; u < 4; ++u) acc[o] = fma(__ldg(&row[(size_t)o * k + pc + u]), v[u], acc[o]);
+    pc = pn;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = nv[u];
   }
 #pragma unroll
-  for (int o = 0; o < 4; ++o) tau[(size_t)(4 * sq + o) * nsys + j] = acc[o];
+  for (int o = 0; o < 4; ++o) tau[(size_t)(4 * sq + o) * nsys + j] = acc[o] * scale;
 }
 
 // Spike correction of element (row r of segment s) of system j, applied to y
@@ -525,13 +542,14 @@ __global__ void __launch_bounds__(kT* kBY) ch_xfinish_kernel(const TC* __restric
   }
 }
 
-// y-sweep correction + update C^{n+1} = 2C^n - C^{n-1} + v for simulation z.
+// y-sweep correction + update C^{n+1} = Cbar + k2 v' for simulation z, where
+// v' solves the scaled right-hand side (the reduced values t1 carry k2 already).
 // keep_roles = 1 writes C^n into c_prev and C^{n+1} into c_now; otherwise
 // C^{n+1} goes into c_prev (the caller swaps the pointers).
 template <typename TC>
 __global__ void __launch_bounds__(kSolveThreads) ch_update_kernel(const TC* __restrict__ y1, const TC* __restrict__ t1,
                                                                   DirView<TC> D, const double* __restrict__ cbar,
-                                                                  double* cn, double* cp, int nx, int ny,
+                                                                  double* cn, double* cp, int nx, int ny, double k2,
                                                                   int keep_roles) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y, z = blockIdx.z, m = D.m, P = D.P;
@@ -539,9 +557,9 @@ __global__ void __launch_bounds__(kSolveThreads) ch_update_kernel(const TC* __re
   const int s = j / m, r = j - s * m;
   const size_t p = (size_t)z * nx * ny + (size_t)j * nx + i;
   t1 += (size_t)z * 4 * P * nx;
-  // C^{n+1} = Cbar + y - corr: one add, then the four spike terms
-  const double nxt = (double)spike_apply((TC)(cbar[p] + (double)y1[p]), D.vw + (size_t)z * 4 * m, t1, m, P, nx, s, r,
-                                         i);
+  // C^{n+1} = Cbar + k2 y - corr: one FMA, then the four spike terms
+  const double nxt = (double)spike_apply((TC)fma(k2, (double)y1[p], cbar[p]), D.vw + (size_t)z * 4 * m, t1, m, P, nx,
+                                         s, r, i);
   if (keep_roles) {
     cp[p] = cn[p];
     cn[p] = nxt;
@@ -1008,9 +1026,10 @@ static void launch_local(const TIn* f, TC* y, int ld, int nsys, const DirView<TC
 // FP32 path keeps one row per thread: its arithmetic is cheap, and four times
 // the threads hide more load latency (measured 10.4 us against 14 us at 2048^2).
 template <typename TC>
-static void launch_reduced(const TC* yb, const DirView<TC>& D, TC* tau, int nsys, size_t ybz, int Z, cudaStream_t st) {
+static void launch_reduced(const TC* yb, const DirView<TC>& D, TC* tau, int nsys, size_t ybz, int Z, TC scale,
+                           cudaStream_t st) {
   const unsigned blk = balanced_block((size_t)nsys * D.P * Z);
-  spike_reduced4_kernel<TC><<<dim3(ceil_div(nsys, blk), D.P, Z), blk, 0, st>>>(yb, D, tau, nsys, ybz);
+  spike_reduced4_kernel<TC><<<dim3(ceil_div(nsys, blk), D.P, Z), blk, 0, st>>>(yb, D, tau, nsys, ybz, scale);
 }
 
 static void step_f64(ChGroup* g, int G, double* cur, double* prev, void* work, int keep_roles, cudaStream_t st,
@@ -1029,19 +1048,20 @@ static void step_f64(ChGroup* g, int G, double* cur, double* prev, void* work, i
   if (g->noise) {
     PROF(kRhs);
     ch_rhs_kernel<double, double, true><<<tgrid, tblock, 0, st>>>(cur, prev, f, nx, ny, G, g->rho, g->kap, g->d_gl,
-                                                                  g->k1, g->k2, cbar, g->noise, g->nkx, g->nky);
+                                                                  g->k1 / g->k2, cbar, g->noise, g->nkx / g->k2,
+                                                                  g->nky / g->k2);
   } else {
     PROF(kRhs);
-    ch_rhs_kernel<double, double><<<tgrid, tblock, 0, st>>>(cur, prev, f, nx, ny, G, g->rho, g->kap, g->d_gl, g->k1,
-                                                            g->k2, cbar);
+    ch_rhs_kernel<double, double><<<tgrid, tblock, 0, st>>>(cur, prev, f, nx, ny, G, g->rho, g->kap, g->d_gl,
+                                                            g->k1 / g->k2, cbar);
   }
   { PROF(kLocX); launch_local<double, double>(f, f, nsx, nsx, X, ybx, 0, 0, 1, status, st); }
-  { PROF(kRedX); launch_reduced<double>(ybx, X, tx, nsx, 0, 1, st); }
+  { PROF(kRedX); launch_reduced<double>(ybx, X, tx, nsx, 0, 1, 1.0, st); }
   { PROF(kFinX); ch_xfinish_kernel<double, double><<<tgrid, tblock, 0, st>>>(f, tx, X, w, nx, ny, G); }
   { PROF(kLocY); launch_local<double, double>(w, w, nx, nx, Y, yby, N, kyz, G, status, st); }
-  { PROF(kRedY); launch_reduced<double>(yby, Y, ty, nx, kyz, G, st); }
+  { PROF(kRedY); launch_reduced<double>(yby, Y, ty, nx, kyz, G, g->k2, st); }
   { PROF(kUpd); ch_update_kernel<double><<<dim3(ceil_div(nx, kSolveThreads), ny, G), kSolveThreads, 0, st>>>(
-        w, ty, Y, cbar, cur, prev, nx, ny, keep_roles); }
+        w, ty, Y, cbar, cur, prev, nx, ny, g->k2, keep_roles); }
 }
 
 static void step_f32r(ChGroup* g, int G, double* cur, double* prev, void* work, int keep_roles, cudaStream_t st,
