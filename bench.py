@@ -543,7 +543,9 @@ def bench_cn1d(dev, steps=100, rewrite_steps=20):
 
 def bench_cook(dev, steps=50):
     """Cahn-Hilliard-Cook runs (Sec. 7.7) on the 2048^2 workload: C = 0 initially,
-    sigma = 1e-14, fresh Philox + Box-Muller deviates every step, FP64 step."""
+    sigma = 1e-14, fresh Philox + Box-Muller deviates every step (drawn inside the FP64
+    right-hand-side pass), FP64 step.  deviates_ms_per_step times the standalone
+    deviate kernel for comparison."""
     import torch
 
     import paper_2101_06550_gb300 as chx

@@ -217,7 +217,9 @@ int ch_diagnostics(chx_ch_plan* plan, const double* c, double* mass_out, double*
  * ch_step_noise: one step with caller-given deviates rho (device, 2 nx ny
  *   doubles, layout as above); c_now/c_prev keep their roles as in ch_step.
  * ch_cook_run: nsteps steps, step k drawing the deviates of step step0 + k into
- *   the caller's device scratch rho (2 nx ny doubles) before stepping.  Pairs
+ *   the caller's device scratch rho (2 nx ny doubles; FP64 plans with even nx
+ *   draw them inside the right-hand-side pass, the others first with the
+ *   deviate kernel: rho ends up with the same values either way).  Pairs
  *   of steps replay a captured graph whose deviates read their step index
  *   from a device counter; the first such call allocates that 8-byte counter
  *   and captures the graph (again when the pointers, sigma, seed or sim change).
@@ -231,7 +233,7 @@ int ch_cook_run(chx_ch_plan* plan, double* c_now, double* c_prev, void* work, do
                 double sigma, uint64_t seed, uint64_t sim, uint64_t step0, void* stream);
 
 /*
- * Coarsening observables (Secs. 2.5, 3.6, 7.2).  For a field C:
+ * Coarsening observables (Secs. 2.4, 3.5.4, 7.2.3).  For a field C:
  *   out[0] mass = sum C dx dy,
  *   out[1] F_h  (as ch_diagnostics),
  *   out[2] s    = 1 / (1 - <C^2>), <.> the composite Simpson average with the

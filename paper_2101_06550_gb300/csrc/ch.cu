@@ -32,6 +32,8 @@
 
 #include "bulk.cuh"
 #include "chgroup.cuh"
+#include "ff.cuh"
+#include "noise.cuh"
 
 using namespace chx;
 
@@ -100,19 +102,34 @@ __device__ __forceinline__ int wrap_near(int i, int n) {
 // eta = sqrt(sigma / (dx dy dt)) div_h rho, the backward-difference divergence
 // of the deviates rho (planes rho^x, rho^y of nx*ny per simulation):
 // nkx (rho^x_ij - rho^x_{i-1,j}) + nky (rho^y_ij - rho^y_{i,j-1}) (nkx, nky
-// divided by k2 like the rest of the output), formed with coalesced row reads
-// into a shared tile first.
-template <typename TC, typename TO, bool NOISE = false>
+// divided by k2 like the rest of the output), formed into a shared tile first.
+// kNoiseRead reads rho with coalesced row reads.  kNoiseDraw draws the tile's
+// deviates in place (noise.cuh; even nx, so that a Philox pair never straddles
+// rows): the 16 pairs of each tile row, the pair holding the west halo point,
+// and the row above, all with key (seed, sim0 + z) at the step *d_step (or
+// `step`), into float tiles that share memory with the M tile; the tile's own
+// deviates are also stored to rho.  The divergence of these FP32 deviates is
+// then formed in double-float on the FP32 pipes (exact differences, products
+// with nkx and nky as float pairs, bit-exact float -> double conversions), so
+// the forcing costs two FP64 additions per point instead of nine FP64-pipe
+// operations.
+constexpr int kNoiseNone = 0, kNoiseRead = 1, kNoiseDraw = 2;
+
+template <typename TC, typename TO, int NOISE = kNoiseNone>
 __global__ void __launch_bounds__(kT* kBY, NOISE ? 5 : 7) ch_rhs_kernel(const double* __restrict__ cn, const double* __restrict__ cp,
                                                          TO* __restrict__ rT, int nx, int ny, int G, TC rho, TC kap,
                                                          const TC* __restrict__ gls, TC kd,
-                                                         double* __restrict__ cbar,
-                                                         const double* __restrict__ dev = nullptr, double nkx = 0,
-                                                         double nky = 0) {
+                                                         double* __restrict__ cbar, double* dev = nullptr,
+                                                         double nkx = 0, double nky = 0, uint64_t seed = 0,
+                                                         uint64_t sim0 = 0, uint64_t step = 0,
+                                                         const uint64_t* __restrict__ d_step = nullptr) {
   __shared__ TC s_cn[kT + 4][kT + 5];
   __shared__ TC s_cb[kT + 4][kT + 5];
   __shared__ TC s_m[kT + 2][kT + 3];
-  __shared__ TC s_nz[NOISE ? kT : 1][kT + 1];
+  using NzT = typename std::conditional<NOISE == kNoiseDraw, ff, TC>::type;
+  __shared__ NzT s_nz[NOISE ? kT : 1][kT + 1];
+  static_assert(2 * (kT + 1) * (kT + 2) * sizeof(float) <= sizeof(TC) * (kT + 2) * (kT + 3),
+                "deviate tiles must fit in the M tile");
   const int z = blockIdx.z;
   const TC gl = gls[z];
   cn += (size_t)z * nx * ny;
@@ -130,7 +147,7 @@ __global__ void __launch_bounds__(kT* kBY, NOISE ? 5 : 7) ch_rhs_kernel(const do
   };
   for (int ly = threadIdx.y; ly < kT + 4; ly += kBY) stage(ly, threadIdx.x);
   if (tid < 4 * (kT + 4)) stage(tid >> 2, kT + (tid & 3));
-  if (NOISE) {
+  if constexpr (NOISE == kNoiseRead) {
     const size_t N = (size_t)nx * ny;
     const double* rx = dev + (size_t)z * 2 * N;
     const double* ry = rx + N;
@@ -147,7 +164,52 @@ __global__ void __launch_bounds__(kT* kBY, NOISE ? 5 : 7) ch_rhs_kernel(const do
       s_nz[lj][li] = v;
     }
   }
+  // deviate tiles (kNoiseDraw): entry [a][b] is grid point (i0 - 1 + b, j0 - 1 + a), wrapped
+  float(*s_dx)[kT + 2] = reinterpret_cast<float(*)[kT + 2]>(&s_m[0][0]);
+  float(*s_dy)[kT + 2] = s_dx + (kT + 1);
+  if constexpr (NOISE == kNoiseDraw) {
+    if (d_step) step = *d_step;
+    const uint64_t key1 = sim0 + (uint64_t)z;
+    constexpr int kPairs = kT / 2 + 1;  // per staged row: the west halo's pair, then the tile's
+    for (int q = tid; q < (kT + 1) * kPairs; q += kT * kBY) {
+      const int a = q / kPairs, h = q - a * kPairs;
+      const int gj = wrap_near(j0 - 1 + a, ny);
+      const int gi = h == 0 ? (i0 == 0 ? nx : i0) - 2 : i0 + 2 * (h - 1);  // even: first point of the pair
+      if (gi >= nx) continue;                                               // ragged last tile
+      float x0, y0, x1, y1;
+      deviate_pair(((size_t)gj * nx + gi) >> 1, step, seed, key1, &x0, &y0, &x1, &y1);
+      if (h == 0) {
+        s_dx[a][0] = x1;
+        s_dy[a][0] = y1;
+      } else {
+        s_dx[a][2 * h - 1] = x0;
+        s_dy[a][2 * h - 1] = y0;
+        s_dx[a][2 * h] = x1;
+        s_dy[a][2 * h] = y1;
+      }
+    }
+  }
   __syncthreads();
+  if constexpr (NOISE == kNoiseDraw) {
+    const size_t N = (size_t)nx * ny;
+    double* rx = dev + (size_t)z * 2 * N;
+    double* ry = rx + N;
+    const ff wx = d2ff(nkx), wy = d2ff(nky);
+    for (int idx = tid; idx < kT * kT; idx += kT * kBY) {
+      const int lj = idx / kT, li = idx % kT;
+      const int gi = i0 + li, gj = j0 + lj;
+      ff v{0.f, 0.f};
+      if (gi < nx && gj < ny) {
+        const float ax = s_dx[lj + 1][li + 1], ay = s_dy[lj + 1][li + 1];
+        v = ff_add(ff_mul(wx, two_sum(ax, -s_dx[lj + 1][li])), ff_mul(wy, two_sum(ay, -s_dy[lj][li + 1])));
+        const size_t q = (size_t)gj * nx + gi;
+        rx[q] = f2d_exact(ax);
+        ry[q] = f2d_exact(ay);
+      }
+      s_nz[lj][li] = v;
+    }
+    __syncthreads();  // the deviate tiles share memory with the M tile
+  }
   double* cbz = cbar + (size_t)z * nx * ny;
   auto mstage = [&](int ly, int lx) {  // M = C^3 - C - gamma Lap Cbar on the tile plus one halo ring
     TC l = s_cb[ly][lx - 1] + s_cb[ly][lx + 1];
@@ -174,7 +236,8 @@ __global__ void __launch_bounds__(kT* kBY, NOISE ? 5 : 7) ch_rhs_kernel(const do
     l = fma(kap, s_m[ly][lx], l);
     const TC diff = s_cb[ly + 1][lx + 1] - s_cn[ly + 1][lx + 1];  // C^n - C^{n-1}
     TC o = fma(-kd, diff, l);
-    if (NOISE) o += s_nz[lj][li];
+    if constexpr (NOISE == kNoiseRead) o += s_nz[lj][li];
+    if constexpr (NOISE == kNoiseDraw) o = (o + f2d_exact(s_nz[lj][li].hi)) + f2d_exact(s_nz[lj][li].lo);
     const int gi = i0 + li, gj = j0 + lj;
     if (gi < nx && gj < ny) rT[(size_t)gi * ldo + (size_t)z * ny + gj] = (TO)o;
   }
@@ -1045,11 +1108,16 @@ static void step_f64(ChGroup* g, int G, double* cur, double* prev, void* work, i
   const int nsx = G * ny;  // the x sweep: all row systems of the group, interleaved
   const DirView<double> X = view<double>(g->X, ny), Y = view<double>(g->Y, nx);
   const size_t kyz = 4 * (size_t)Y.P * nx;
-  if (g->noise) {
+  if (g->noise_w) {
     PROF(kRhs);
-    ch_rhs_kernel<double, double, true><<<tgrid, tblock, 0, st>>>(cur, prev, f, nx, ny, G, g->rho, g->kap, g->d_gl,
-                                                                  g->k1 / g->k2, cbar, g->noise, g->nkx / g->k2,
-                                                                  g->nky / g->k2);
+    ch_rhs_kernel<double, double, kNoiseDraw><<<tgrid, tblock, 0, st>>>(
+        cur, prev, f, nx, ny, G, g->rho, g->kap, g->d_gl, g->k1 / g->k2, cbar, g->noise_w, g->nkx / g->k2,
+        g->nky / g->k2, g->noise_seed, g->noise_sim0, g->noise_step, g->noise_dstep);
+  } else if (g->noise) {
+    PROF(kRhs);
+    ch_rhs_kernel<double, double, kNoiseRead><<<tgrid, tblock, 0, st>>>(
+        cur, prev, f, nx, ny, G, g->rho, g->kap, g->d_gl, g->k1 / g->k2, cbar, const_cast<double*>(g->noise),
+        g->nkx / g->k2, g->nky / g->k2);
   } else {
     PROF(kRhs);
     ch_rhs_kernel<double, double><<<tgrid, tblock, 0, st>>>(cur, prev, f, nx, ny, G, g->rho, g->kap, g->d_gl,
@@ -1097,6 +1165,28 @@ static void step_f32r(ChGroup* g, int G, double* cur, double* prev, void* work, 
   { PROF(kLoc2Y); launch_local<float, float>(y2, y2, nx, nx, Y, yby2, N, kyz, G, status, st); }
   { PROF(kRed2Y); spike_reduced_kernel<float><<<dim3(gy.x, 4 * Y.P, G), kSolveThreads, 0, st>>>(yby2, Y, ty2, nx, kyz); }
   { PROF(kUpd); launch_ch_update_ff(x0, ty, y2, ty2, Y, cur, prev, nx, ny, G, keep_roles, st); }
+}
+
+int group_cook_deviates(ChGroup* g, int gact, double* rho, uint64_t seed, uint64_t sim0, uint64_t step,
+                        const uint64_t* d_step, cudaStream_t st) {
+  if (g->precision == CHX_PREC_F64 && g->nx % 2 == 0) {
+    g->noise = nullptr;
+    g->noise_w = rho;
+    g->noise_seed = seed;
+    g->noise_sim0 = sim0;
+    g->noise_step = step;
+    g->noise_dstep = d_step;
+    return CHX_OK;
+  }
+  g->noise = rho;
+  g->noise_w = nullptr;
+  return launch_noise_normals(rho, g->nx, g->ny, gact, seed, sim0, step, d_step, st);
+}
+
+void group_cook_clear(ChGroup* g) {
+  g->noise = nullptr;
+  g->noise_w = nullptr;
+  g->noise_dstep = nullptr;
 }
 
 void group_step(ChGroup* g, int gact, double* cur, double* prev, void* work, int keep_roles, cudaStream_t st,
@@ -1286,13 +1376,12 @@ extern "C" int ch_cook_run(chx_ch_plan* p, double* c_now, double* c_prev, void* 
       cudaGraph_t graph = nullptr;
       if (!rc) rc = cuda_check(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal), "ch_cook_run: capture");
       if (!rc) {
-        p->g.noise = rho;
         for (int h = 0; h < 2; ++h) {
-          launch_noise_normals(rho, p->g.nx, p->g.ny, 1, seed, sim, 0, p->d_cook_step, p->cap);
+          group_cook_deviates(&p->g, 1, rho, seed, sim, 0, p->d_cook_step, p->cap);
           group_step(&p->g, 1, h ? c_prev : c_now, h ? c_now : c_prev, work, 0, p->cap, nullptr, p->hdr.d_status);
           launch_step_advance(p->d_cook_step, p->cap);
         }
-        p->g.noise = nullptr;
+        group_cook_clear(&p->g);
         rc = cuda_check(cudaStreamEndCapture(p->cap, &graph), "ch_cook_run: end capture");
       }
       if (!rc) rc = cuda_check(cudaGraphInstantiate(&p->cook_pair, graph, 0), "ch_cook_run: instantiate");
@@ -1318,11 +1407,10 @@ extern "C" int ch_cook_run(chx_ch_plan* p, double* c_now, double* c_prev, void* 
   double *cur = c_now, *prev = c_prev;
   for (int s = done; s < nsteps; ++s) {
     const int keep = s == nsteps - 1 && cur == c_now;
-    rc = launch_noise_normals(rho, p->g.nx, p->g.ny, 1, seed, sim, step0 + (uint64_t)s, nullptr, st);
+    rc = group_cook_deviates(&p->g, 1, rho, seed, sim, step0 + (uint64_t)s, nullptr, st);
     if (rc) return rc;
-    p->g.noise = rho;
     group_step(&p->g, 1, cur, prev, work, keep, st, p->prof, p->hdr.d_status);
-    p->g.noise = nullptr;
+    group_cook_clear(&p->g);
     if (!keep) {
       double* t = cur;
       cur = prev;

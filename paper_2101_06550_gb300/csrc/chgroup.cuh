@@ -93,6 +93,11 @@ struct ChGroup {
   // 2 nx ny doubles per slot, and the forcing weights (2/3) dt amp / dx, / dy
   const double* noise = nullptr;
   double nkx = 0, nky = 0;
+  // ... or drawn by the FP64 right-hand side itself (group_cook_deviates): into
+  // noise_w, key (noise_seed, noise_sim0 + slot), step *noise_dstep (or noise_step)
+  double* noise_w = nullptr;
+  uint64_t noise_seed = 0, noise_sim0 = 0, noise_step = 0;
+  const uint64_t* noise_dstep = nullptr;
   struct ObsState* obs = nullptr;  // observables scratch, made on first use (obs.cu)
   float2* d_glff = nullptr;
   SpikeDir X, Y;
@@ -109,6 +114,14 @@ int group_init(ChGroup* g, int nx, int ny, double lx, double ly, double gamma, d
                int px = 0, int py = 0);
 // Refactorises slot z of the group for a new gamma (host FP64, synchronous upload).
 int group_set_gamma(ChGroup* g, int z, double gamma);
+// Sets up the Cahn-Hilliard-Cook deviates of the group's next step for its
+// first gact slots (slot z: key (seed, sim0 + z)), into rho (2 nx ny doubles
+// per slot): drawn in place by the FP64 right-hand side when nx is even,
+// otherwise by the standalone deviate kernel on st first.  d_step, when given,
+// holds the step index on the device.  group_cook_clear undoes it.
+int group_cook_deviates(ChGroup* g, int gact, double* rho, uint64_t seed, uint64_t sim0, uint64_t step,
+                        const uint64_t* d_step, cudaStream_t st);
+void group_cook_clear(ChGroup* g);
 // Copies slot `from`'s parameters onto slot `to` (device to device, on st).
 int group_move_params(ChGroup* g, int from, int to, cudaStream_t st);
 void group_free(ChGroup* g);

@@ -91,9 +91,12 @@ void drop_graph(chx_ens* e) {
 
 void step_group(EnsGroup* G, cudaStream_t st) {
   if (G->active < 1) return;
-  if (G->sigma > 0) launch_noise_normals(G->d_rho, G->n, G->n, G->active, G->seed, 0, 0, G->d_step, st);
+  if (G->sigma > 0) group_cook_deviates(&G->g, G->active, G->d_rho, G->seed, 0, 0, G->d_step, st);
   group_step(&G->g, G->active, G->d_state[G->cur], G->d_state[1 - G->cur], G->d_work, 0, st, nullptr, G->status);
-  if (G->sigma > 0) launch_step_advance(G->d_step, st);
+  if (G->sigma > 0) {
+    launch_step_advance(G->d_step, st);
+    group_cook_clear(&G->g);
+  }
   G->cur = 1 - G->cur;
 }
 
@@ -321,7 +324,6 @@ extern "C" int ens_group_set_cook(chx_ens* e, int group_id, double sigma, uint64
   G->sigma = sigma;
   G->seed = seed;
   const double amp = sqrt(sigma / (G->g.dx * G->g.dy * G->g.dt));
-  G->g.noise = G->d_rho;
   G->g.nkx = (2.0 / 3.0) * G->g.dt * amp / G->g.dx;
   G->g.nky = (2.0 / 3.0) * G->g.dt * amp / G->g.dy;
   drop_graph(e);
@@ -436,12 +438,10 @@ extern "C" int ens_autotune(chx_ens* e, int group_id, int trial, int* px_out, in
       group_free(&ng);
       return rc;
     }
-    const double* noise = G->g.noise;
     const double nkx = G->g.nkx, nky = G->g.nky;
     group_free(&G->g);
     G->g = ng;
-    G->g.noise = noise;  // the group's forcing carries over to the new factors
-    G->g.nkx = nkx;
+    G->g.nkx = nkx;  // the group's forcing weights carry over to the new factors
     G->g.nky = nky;
     drop_graph(e);
   }

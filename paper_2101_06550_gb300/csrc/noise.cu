@@ -14,42 +14,13 @@
 #include <stdint.h>
 
 #include "chx_internal.cuh"
+#include "noise.cuh"
 
 using namespace chx;
 
 namespace {
 
 constexpr int kThreads = 256;
-
-__device__ __forceinline__ void philox4x64_10(uint64_t& x0, uint64_t& x1, uint64_t& x2, uint64_t& x3, uint64_t k0,
-                                              uint64_t k1) {
-  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
-  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
-#pragma unroll
-  for (int round = 0; round < 10; ++round) {
-    if (round > 0) {
-      k0 += W0;
-      k1 += W1;
-    }
-    const uint64_t hi0 = __umul64hi(M0, x0), lo0 = M0 * x0;
-    const uint64_t hi1 = __umul64hi(M1, x2), lo1 = M1 * x2;
-    const uint64_t y0 = hi1 ^ x1 ^ k0, y2 = hi0 ^ x3 ^ k1;
-    x0 = y0;
-    x1 = lo1;
-    x2 = y2;
-    x3 = lo0;
-  }
-}
-
-__device__ __forceinline__ float unit_open(uint64_t w) { return ((float)(w >> 41) + 0.5f) * 0x1p-23f; }
-
-__device__ __forceinline__ void box_muller(uint64_t wa, uint64_t wb, double* zx, double* zy) {
-  const float rad = sqrtf(-2.0f * logf(unit_open(wa)));
-  float s, c;
-  sincospif(2.0f * unit_open(wb), &s, &c);
-  *zx = (double)(rad * c);
-  *zy = (double)(rad * s);
-}
 
 // rho: G fields of [rho^x (nx*ny), rho^y (nx*ny)]; field z uses key (seed, sim0 + z).
 // The step index is `step`, or *d_step when d_step is given (a device counter
@@ -63,16 +34,13 @@ __global__ void __launch_bounds__(kThreads) noise_normals_kernel(double* __restr
   double* rx = rho + (size_t)z * 2 * np;
   double* ry = rx + np;
   for (size_t b = blockIdx.x * (size_t)blockDim.x + threadIdx.x; b < pairs; b += (size_t)gridDim.x * blockDim.x) {
-    uint64_t x0 = b, x1 = step, x2 = 0, x3 = 0;
-    philox4x64_10(x0, x1, x2, x3, seed, sim0 + (uint64_t)z);
-    double zx, zy;
-    box_muller(x0, x1, &zx, &zy);
-    rx[2 * b] = zx;
-    ry[2 * b] = zy;
+    float x0, y0, x1, y1;
+    deviate_pair(b, step, seed, sim0 + (uint64_t)z, &x0, &y0, &x1, &y1);
+    rx[2 * b] = x0;
+    ry[2 * b] = y0;
     if (2 * b + 1 < np) {
-      box_muller(x2, x3, &zx, &zy);
-      rx[2 * b + 1] = zx;
-      ry[2 * b + 1] = zy;
+      rx[2 * b + 1] = x1;
+      ry[2 * b + 1] = y1;
     }
   }
 }

@@ -1,4 +1,4 @@
-// Coarsening observables of Cahn-Hilliard fields (Secs. 2.5, 3.6, 7.2):
+// Coarsening observables of Cahn-Hilliard fields (Secs. 2.4, 3.5.4, 7.2.3):
 //   mass = sum C dx dy,
 //   F_h  = sum [ (1/4)(C^2 - 1)^2 + (gamma/2)(|D+x C|^2 + |D+y C|^2) ] dx dy,
 //   s    = 1 / (1 - <C^2>), <.> the composite Simpson average (periodic closure:

@@ -106,6 +106,38 @@ def test_cook_run_matches_oracle_from_rest(nsteps):
     assert np.all(np.abs(rho.cpu().numpy().reshape(2, n, n) - last) <= 5e-7 * np.sqrt(last[0]**2 + last[1]**2))
 
 
+@pytest.mark.parametrize("nx,ny", [(64, 64), (70, 40), (96, 33), (63, 48)])
+def test_cook_run_in_place_draw_matches_the_deviate_kernel(nx, ny):
+    # For even nx the FP64 right-hand side draws each step's deviates itself
+    # (tile by tile, with the west and south halo pairs); for odd nx the
+    # standalone kernel draws them first.  Either way rho ends up bit-identical
+    # to ch_noise_normals of the last step, and every step matches the oracle
+    # driven by the standalone kernel's deviates.  70 and 40 leave ragged
+    # tiles; 33 rows wrap the halo row of the last tile row.
+    chx = _chx()
+    lx, gamma, dt, sigma, seed, sim, step0, nsteps = 2 * np.pi, 0.01, 1e-3, 1e-6, 5, 2, 4, 3
+    ly = lx * ny / nx
+    c0 = synth.field(81, ny, nx, -0.1, 0.1)
+    plan = chx.ChPlan(nx, ny, lx, ly, gamma, dt)
+    cn = torch.from_numpy(c0).to(DEV).reshape(-1)
+    cp = cn.clone()
+    rho = torch.empty(2 * nx * ny, dtype=torch.float64, device=DEV)
+    plan.cook_run(cn, cp, plan.alloc_work(DEV), rho, nsteps, sigma, seed=seed, sim=sim, step0=step0)
+    plan.sync_status()
+    last = torch.empty_like(rho)
+    chx.noise_normals(last, nx, ny, seed, sim, step0 + nsteps - 1)
+    assert torch.equal(rho, last)
+    c, p = c0, c0
+    for k in range(nsteps):
+        r = torch.empty_like(rho)
+        chx.noise_normals(r, nx, ny, seed, sim, step0 + k)
+        rk = r.cpu().numpy().reshape(2, ny, nx)
+        tol_rhs = _forced_rhs_norm(c, p, rk, lx, ly, gamma, dt, sigma)
+        c, p = oracle.ch_cook_step(c, p, rk, lx, ly, gamma, dt, sigma)
+    tol = 1e-11 * float(np.max(np.abs(c))) * nsteps + 4 * 2.220446049250313e-16 * tol_rhs * nsteps
+    assert np.max(np.abs(cn.cpu().numpy().reshape(ny, nx) - c)) <= tol
+
+
 def test_cook_rejects_bad_arguments():
     chx = _chx()
     n = 32

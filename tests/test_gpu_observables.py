@@ -1,4 +1,4 @@
-"""GPU parity of the coarsening observables (mass, F_h, s, k1; Secs. 2.5, 3.6)
+"""GPU parity of the coarsening observables (mass, F_h, s, k1; Secs. 2.4, 3.5.4)
 for single fields and whole ensemble groups."""
 import numpy as np
 import pytest

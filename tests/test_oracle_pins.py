@@ -512,7 +512,7 @@ def test_cook_step_without_noise_is_the_plain_step_and_conserves_mass():
     assert np.max(np.abs(c - c0)) > 1e-6  # the forcing acted
 
 
-# --------------------------------------------------------------------------- coarsening observables (Secs. 3.6, 7.2)
+# --------------------------------------------------------------------------- coarsening observables (Secs. 3.5.4, 7.2.3)
 def test_simpson_mean_is_scipy_simpson_on_the_closed_interval():
     from scipy.integrate import simpson
 
