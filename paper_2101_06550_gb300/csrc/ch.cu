@@ -70,6 +70,12 @@ namespace {
 constexpr int kT = 32;      // tile edge of the transposing kernels
 constexpr int kBY = 8;      // tile threads in y
 constexpr int kSolveThreads = 128;
+// Rows of the FP64 reduced solve per thread.  Measured at 2048^2 (2048 systems x
+// 16 segments per direction): 4 rows 18.0 us, 2 rows 16.6 us, 1 row 16.3 us.
+// Fewer rows per thread mean more, shorter single-warp blocks, so the SMs
+// finish closer together (with 4 rows they sat idle a quarter of the time).
+// Two rows halve the boundary-value loads of one row per thread for nearly the same time.
+constexpr int kReducedRows = 2;
 
 __device__ __forceinline__ int wrapi(int i, int n) {
   int r = i % n;
@@ -516,26 +522,29 @@ __global__ void __launch_bounds__(kSolveThreads) spike_reduced_kernel(const TC* 
   tau[(size_t)q * nsys + j] = acc0 + acc1;
 }
 
-// The same reduced solve with the four rows of one segment block per thread:
-// each boundary value loaded (from L2) serves four dot products instead of
-// one, which cuts the kernel's L2 traffic fourfold.  Grid (systems / blk, P, Z).
-// The outputs are multiplied by `scale` (the update's k2 for the y sweep).
-template <typename TC>
-__global__ void __launch_bounds__(kSolveThreads) spike_reduced4_kernel(const TC* __restrict__ yb, DirView<TC> D,
+// The same reduced solve with R (1, 2 or 4) rows of one segment block per
+// thread: each boundary value loaded (from L2) serves R dot products instead of
+// one.  Grid (systems / blk, P * 4 / R, Z).  The outputs are multiplied by
+// `scale` (the update's k2 for the y sweep).
+template <typename TC, int R>
+__global__ void __launch_bounds__(kSolveThreads) spike_reducedR_kernel(const TC* __restrict__ yb, DirView<TC> D,
                                                                        TC* __restrict__ tau, int nsys, size_t ybz,
                                                                        TC scale) {
+  static_assert(R == 1 || R == 2 || R == 4, "rows per thread");
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nsys) return;
   const int P = D.P, k = 4 * P;
   const int slot = blockIdx.z + j / D.spp;
   yb += blockIdx.z * ybz;
   tau += blockIdx.z * ybz;
-  const int sq = blockIdx.y;
-  const TC* row = D.rinv + (size_t)slot * k * k + (size_t)(4 * sq) * k;
+  const int sq = blockIdx.y / (4 / R), q0 = 4 * sq + (blockIdx.y % (4 / R)) * R;  // first output row
+  const TC* row = D.rinv + (size_t)slot * k * k + (size_t)q0 * k;
   const int nb = 2 * D.band + 1 < P ? 2 * D.band + 1 : P;
   const int s0 = nb == P ? 0 : sq - D.band;
-  TC acc[4] = {0, 0, 0, 0};
-  // block bb + 1's boundary values are loaded while block bb's 16 FMAs issue
+  TC acc[R];
+#pragma unroll
+  for (int o = 0; o < R; ++o) acc[o] = 0;
+  // block bb + 1's boundary values are loaded while block bb's FMAs issue
   auto col = [&](int bb) {
     const int sb = s0 + bb;
     return 4 * (sb < 0 ? sb + P : (sb >= P ? sb - P : sb));
@@ -550,7 +559,7 @@ __global__ void __launch_bounds__(kSolveThreads) spike_reduced4_kernel(const TC*
 #pragma unroll
     for (int u = 0; u < 4; ++u) nv[u] = yb[(size_t)(pn + u) * nsys + j];
 #pragma unroll
-    for (int o = 0; o < 4; ++o)
+    for (int o = 0; o < R; ++o)
 #pragma unroll
       for (int u = 0; u < 4; ++u) acc[o] = fma(__ldg(&row[(size_t)o * k + pc + u]), v[u], acc[o]);
     pc = pn;
@@ -558,7 +567,7 @@ __global__ void __launch_bounds__(kSolveThreads) spike_reduced4_kernel(const TC*
     for (int u = 0; u < 4; ++u) v[u] = nv[u];
   }
 #pragma unroll
-  for (int o = 0; o < 4; ++o) tau[(size_t)(4 * sq + o) * nsys + j] = acc[o] * scale;
+  for (int o = 0; o < R; ++o) tau[(size_t)(q0 + o) * nsys + j] = acc[o] * scale;
 }
 
 // Spike correction of element (row r of segment s) of system j, applied to y
@@ -1087,15 +1096,17 @@ static void launch_local(const TIn* f, TC* y, int ld, int nsys, const DirView<TC
   }
 }
 
-// FP64 reduced solves: four rows per thread, in single-warp blocks when the
-// grid is small (the balance rule of the one-thread-per-system kernels).  The
-// FP32 path keeps one row per thread: its arithmetic is cheap, and four times
-// the threads hide more load latency (measured 10.4 us against 14 us at 2048^2).
+// FP64 reduced solves: kReducedRows rows per thread, in single-warp blocks when
+// the grid is small (the balance rule of the one-thread-per-system kernels).
+// The FP32 path keeps one row per thread: its arithmetic is cheap, and more
+// threads hide more load latency (measured 10.4 us against 14 us at 2048^2).
 template <typename TC>
 static void launch_reduced(const TC* yb, const DirView<TC>& D, TC* tau, int nsys, size_t ybz, int Z, TC scale,
                            cudaStream_t st) {
-  const unsigned blk = balanced_block((size_t)nsys * D.P * Z);
-  spike_reduced4_kernel<TC><<<dim3(ceil_div(nsys, blk), D.P, Z), blk, 0, st>>>(yb, D, tau, nsys, ybz, scale);
+  const int R = kReducedRows;
+  const unsigned blk = balanced_block((size_t)nsys * D.P * (4 / R) * Z);
+  spike_reducedR_kernel<TC, kReducedRows><<<dim3(ceil_div(nsys, blk), D.P * (4 / R), Z), blk, 0, st>>>(
+      yb, D, tau, nsys, ybz, scale);
 }
 
 static void step_f64(ChGroup* g, int G, double* cur, double* prev, void* work, int keep_roles, cudaStream_t st,
