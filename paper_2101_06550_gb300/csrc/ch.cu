@@ -69,6 +69,9 @@ namespace {
 
 constexpr int kT = 32;      // tile edge of the transposing kernels
 constexpr int kBY = 8;      // tile threads in y
+constexpr int kRBY = 8;     // the RHS kernel's threads in y
+constexpr int kRMinBlocks = 7, kRMinBlocksNoise = 5;  // its resident blocks per SM (shared memory bound)
+static_assert(kT * kRBY >= 4 * (kT + 4) && kT % kRBY == 0, "RHS staging assumes one pass over the extra columns");
 constexpr int kSolveThreads = 128;
 // Rows of the FP64 reduced solve per thread.  Measured at 2048^2 (2048 systems x
 // 16 segments per direction): 4 rows 18.0 us, 2 rows 16.6 us, 1 row 16.3 us.
@@ -122,7 +125,7 @@ __device__ __forceinline__ int wrap_near(int i, int n) {
 constexpr int kNoiseNone = 0, kNoiseRead = 1, kNoiseDraw = 2;
 
 template <typename TC, typename TO, int NOISE = kNoiseNone>
-__global__ void __launch_bounds__(kT* kBY, NOISE ? 5 : 7) ch_rhs_kernel(const double* __restrict__ cn, const double* __restrict__ cp,
+__global__ void __launch_bounds__(kT* kRBY, NOISE ? kRMinBlocksNoise : kRMinBlocks) ch_rhs_kernel(const double* __restrict__ cn, const double* __restrict__ cp,
                                                          TO* __restrict__ rT, int nx, int ny, int G, TC rho, TC kap,
                                                          const TC* __restrict__ gls, TC kd,
                                                          double* __restrict__ cbar, double* dev = nullptr,
@@ -151,13 +154,13 @@ __global__ void __launch_bounds__(kT* kBY, NOISE ? 5 : 7) ch_rhs_kernel(const do
     s_cn[ly][lx] = a;
     s_cb[ly][lx] = fma(TC(2), a, -b);
   };
-  for (int ly = threadIdx.y; ly < kT + 4; ly += kBY) stage(ly, threadIdx.x);
+  for (int ly = threadIdx.y; ly < kT + 4; ly += kRBY) stage(ly, threadIdx.x);
   if (tid < 4 * (kT + 4)) stage(tid >> 2, kT + (tid & 3));
   if constexpr (NOISE == kNoiseRead) {
     const size_t N = (size_t)nx * ny;
     const double* rx = dev + (size_t)z * 2 * N;
     const double* ry = rx + N;
-    for (int idx = tid; idx < kT * kT; idx += kT * kBY) {
+    for (int idx = tid; idx < kT * kT; idx += kT * kRBY) {
       const int lj = idx / kT, li = idx % kT;
       const int gi = i0 + li, gj = j0 + lj;
       TC v = 0;
@@ -177,7 +180,7 @@ __global__ void __launch_bounds__(kT* kBY, NOISE ? 5 : 7) ch_rhs_kernel(const do
     if (d_step) step = *d_step;
     const uint64_t key1 = sim0 + (uint64_t)z;
     constexpr int kPairs = kT / 2 + 1;  // per staged row: the west halo's pair, then the tile's
-    for (int q = tid; q < (kT + 1) * kPairs; q += kT * kBY) {
+    for (int q = tid; q < (kT + 1) * kPairs; q += kT * kRBY) {
       const int a = q / kPairs, h = q - a * kPairs;
       const int gj = wrap_near(j0 - 1 + a, ny);
       const int gi = h == 0 ? (i0 == 0 ? nx : i0) - 2 : i0 + 2 * (h - 1);  // even: first point of the pair
@@ -201,7 +204,7 @@ __global__ void __launch_bounds__(kT* kBY, NOISE ? 5 : 7) ch_rhs_kernel(const do
     double* rx = dev + (size_t)z * 2 * N;
     double* ry = rx + N;
     const ff wx = d2ff(nkx), wy = d2ff(nky);
-    for (int idx = tid; idx < kT * kT; idx += kT * kBY) {
+    for (int idx = tid; idx < kT * kT; idx += kT * kRBY) {
       const int lj = idx / kT, li = idx % kT;
       const int gi = i0 + li, gj = j0 + lj;
       ff v{0.f, 0.f};
@@ -229,13 +232,13 @@ __global__ void __launch_bounds__(kT* kBY, NOISE ? 5 : 7) ch_rhs_kernel(const do
     if (ly >= 2 && ly < kT + 2 && lx >= 2 && lx < kT + 2 && gi < nx && gj < ny)
       cbz[(size_t)gj * nx + gi] = (double)s_cb[ly][lx];
   };
-  for (int ly = 1 + threadIdx.y; ly <= kT + 2; ly += kBY) mstage(ly, 1 + threadIdx.x);
+  for (int ly = 1 + threadIdx.y; ly <= kT + 2; ly += kRBY) mstage(ly, 1 + threadIdx.x);
   if (tid < 2 * (kT + 2)) mstage(1 + (tid >> 1), kT + 1 + (tid & 1));
   __syncthreads();
   const size_t ldo = (size_t)G * ny;
 #pragma unroll
-  for (int k = 0; k < kT / kBY; ++k) {
-    const int li = threadIdx.y + k * kBY, lj = threadIdx.x;  // output (i0 + li, j0 + lj)
+  for (int k = 0; k < kT / kRBY; ++k) {
+    const int li = threadIdx.y + k * kRBY, lj = threadIdx.x;  // output (i0 + li, j0 + lj)
     const int ly = lj + 1, lx = li + 1;
     TC l = s_m[ly][lx - 1] + s_m[ly][lx + 1];
     l = fma(rho, s_m[ly - 1][lx] + s_m[ly + 1][lx], l);
@@ -1118,23 +1121,23 @@ static void step_f64(ChGroup* g, int G, double* cur, double* prev, void* work, i
   double *ybx = wptr<double>(work, g->off_ybx), *tx = wptr<double>(work, g->off_tx);
   double *yby = wptr<double>(work, g->off_yby), *ty = wptr<double>(work, g->off_ty);
   double* cbar = wptr<double>(work, g->off_cb);
-  const dim3 tgrid(ceil_div(nx, kT), ceil_div(ny, kT), G), tblock(kT, kBY);
+  const dim3 tgrid(ceil_div(nx, kT), ceil_div(ny, kT), G), tblock(kT, kBY), rblock(kT, kRBY);
   const int nsx = G * ny;  // the x sweep: all row systems of the group, interleaved
   const DirView<double> X = view<double>(g->X, ny), Y = view<double>(g->Y, nx);
   const size_t kyz = 4 * (size_t)Y.P * nx;
   if (g->noise_w) {
     PROF(kRhs);
-    ch_rhs_kernel<double, double, kNoiseDraw><<<tgrid, tblock, 0, st>>>(
+    ch_rhs_kernel<double, double, kNoiseDraw><<<tgrid, rblock, 0, st>>>(
         cur, prev, f, nx, ny, G, g->rho, g->kap, g->d_gl, g->k1 / g->k2, cbar, g->noise_w, g->nkx / g->k2,
         g->nky / g->k2, g->noise_seed, g->noise_sim0, g->noise_step, g->noise_dstep);
   } else if (g->noise) {
     PROF(kRhs);
-    ch_rhs_kernel<double, double, kNoiseRead><<<tgrid, tblock, 0, st>>>(
+    ch_rhs_kernel<double, double, kNoiseRead><<<tgrid, rblock, 0, st>>>(
         cur, prev, f, nx, ny, G, g->rho, g->kap, g->d_gl, g->k1 / g->k2, cbar, const_cast<double*>(g->noise),
         g->nkx / g->k2, g->nky / g->k2);
   } else {
     PROF(kRhs);
-    ch_rhs_kernel<double, double><<<tgrid, tblock, 0, st>>>(cur, prev, f, nx, ny, G, g->rho, g->kap, g->d_gl,
+    ch_rhs_kernel<double, double><<<tgrid, rblock, 0, st>>>(cur, prev, f, nx, ny, G, g->rho, g->kap, g->d_gl,
                                                             g->k1 / g->k2, cbar);
   }
   { PROF(kLocX); launch_local<double, double>(f, f, nsx, nsx, X, ybx, 0, 0, 1, status, st); }
