@@ -332,7 +332,7 @@ def run_chx(args, rank, world, local_rank):
     peaks = _peaks()
     # dominant kernel of the FP64 step and its roofline (FP64-pipe bound)
     dom, (dom_ms, dom_n) = max(prof64.items(), key=lambda kv: kv[1][0])
-    dp_ops = {"ch_rhs": 14.0, "spike_local_x": 5.0, "spike_local_y": 5.0, "ch_xfinish": 4.0, "ch_update": 5.0}
+    dp_ops = {"ch_rhs": 14.0, "spike_local_x": 5.0, "spike_local_y": 5.0, "ch_xfinish": 4.0, "ch_update": 6.375}
     per_launch_ms = dom_ms / max(1, dom_n)
     fp64_peak_gops = 1.90 * 152 * 2.070  # measured DFMA issue rate x SMs x max clock (G DP-ops/s)
     if dom in dp_ops:
