@@ -38,6 +38,7 @@ WORKLOAD = "ch2d_periodic_2048sq_gamma0.005_dt5e-4"
 # workload, from an ncu capture of the current kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum, mean of 3 launches; the two written fields, r / k2 and
 # Cbar, partly stay in L2 for the kernels that read them next)
+PREWARM_S = 1.5  # untimed steps before the first measurement (see measure())
 RHS_TRAFFIC_BYTES = 67.27e6 + 20.00e6  # ncu: dram__bytes_read + write per ch_rhs launch (mean of 3)
 
 
@@ -242,11 +243,18 @@ def run_chx(args, rank, world, local_rank):
     c0 = torch.from_numpy(synth.field(SEED, N, N, -0.05, 0.05)).to(dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # 512 MiB > L2 (129 MB)
 
-    def measure(precision):
+    def measure(precision, prewarm_s=0.0):
         plan = chx.ChPlan(N, N, LX, LX, GAMMA, DT, precision)
         cn = c0.clone()
         cp = c0.clone()
         work = plan.alloc_work(dev)
+        # a GPU fresh from idle runs the first second or so of work about 4% slow
+        # (measured: the first process on a box, at the same reported SM clock),
+        # so the first measurement is preceded by that long a run of steps
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < prewarm_s:
+            plan.step(cn, cp, work, 8)
+            torch.cuda.synchronize()
         for _ in range(args.warmup):
             plan.step(cn, cp, work, 1)
         torch.cuda.synchronize()
@@ -280,7 +288,7 @@ def run_chx(args, rank, world, local_rank):
         return ms, ms_profiled, prof, plan, cn, cp, work
 
     clk = ClockSampler(local_rank).__enter__()
-    ms64, ms64_prof, prof64, plan64, cn64, cp64, work64 = measure(chx.PREC_F64)
+    ms64, ms64_prof, prof64, plan64, cn64, cp64, work64 = measure(chx.PREC_F64, prewarm_s=PREWARM_S)
     ms32, ms32_prof, prof32, plan32, _, _, _ = measure(chx.PREC_F32_REFINE)
     launches_per_step = sum(n for _, n in prof64.values()) / max(1, args.steps)
 
@@ -332,7 +340,7 @@ def run_chx(args, rank, world, local_rank):
     peaks = _peaks()
     # dominant kernel of the FP64 step and its roofline (FP64-pipe bound)
     dom, (dom_ms, dom_n) = max(prof64.items(), key=lambda kv: kv[1][0])
-    dp_ops = {"ch_rhs": 14.0, "spike_local_x": 5.0, "spike_local_y": 5.0, "ch_xfinish": 4.0, "ch_update": 6.375}
+    dp_ops = {"ch_rhs": 14.0, "spike_local_x": 5.0, "spike_local_y": 5.0, "ch_xfinish": 4.0, "ch_update": 5.0}
     per_launch_ms = dom_ms / max(1, dom_n)
     fp64_peak_gops = 1.90 * 152 * 2.070  # measured DFMA issue rate x SMs x max clock (G DP-ops/s)
     if dom in dp_ops:
@@ -379,7 +387,7 @@ def run_chx(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms64 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": [N, N], "precision": "fp64", "l2": "flushed between timed steps",
-                   "replicas": world},
+                   "replicas": world, "prewarm_s": PREWARM_S},
         "fp32_refine": {"value": world * pts * args.steps / (ms32 * 1e-3), "ms_per_step": ms32 / args.steps,
                         "ms_per_step_profiled": ms32_prof / args.steps, "dtype": "f32+f64-residual"},
         "ms_per_step_profiled": ms64_prof / args.steps,

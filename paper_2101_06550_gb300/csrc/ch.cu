@@ -74,10 +74,11 @@ constexpr int kRMinBlocks = 7, kRMinBlocksNoise = 5;  // its resident blocks per
 static_assert(kT * kRBY >= 4 * (kT + 4) && kT % kRBY == 0, "RHS staging assumes one pass over the extra columns");
 constexpr int kSolveThreads = 128;
 // Rows of the FP64 reduced solve per thread.  Measured at 2048^2 (2048 systems x
-// 16 segments per direction): 4 rows 18.0 us, 2 rows 16.6 us, 1 row 16.3 us.
-// Fewer rows per thread mean more, shorter single-warp blocks, so the SMs
-// finish closer together (with 4 rows they sat idle a quarter of the time).
-// Two rows halve the boundary-value loads of one row per thread for nearly the same time.
+// 16 segments per direction), whole graph-replayed step, same box, three rounds:
+// 4 rows 0.3082 ms, 2 rows 0.3060 ms, 1 row 0.3068 ms.  Fewer rows per thread
+// mean more, shorter single-warp blocks, so the SMs finish closer together
+// (with 4 rows ncu showed them idle a quarter of the kernel's time); one row
+// per thread loads every boundary value four times.
 constexpr int kReducedRows = 2;
 
 __device__ __forceinline__ int wrapi(int i, int n) {
@@ -643,68 +644,6 @@ __global__ void __launch_bounds__(kSolveThreads) ch_update_kernel(const TC* __re
   }
 }
 
-// The reduced solve and the update in one pass, for the y sweep of the FP64
-// step.  Block (32 columns, segment s, simulation z): the segment's rows need
-// only four reduced values per column, t(4 sn + 0, 1) of the next segment and
-// t(4 sp + 2, 3) of the previous one, and no other segment needs them, so each
-// is a dot product of one Rinv row with the boundary values of the segments
-// within the band, formed once by thread row q (in the order of
-// spike_reducedR_kernel, so the results are bit-identical), times k2.  Then
-// every thread updates its column: C^{n+1} = Cbar + k2 y - V t (spike_apply's
-// order).  This saves the reduced kernel's launch and its ragged tail.
-constexpr int kUY = 4;  // rows of threads per block: thread row q forms the q-th reduced value
-static_assert(kUY == 4, "one thread row per reduced value");
-template <typename TC>
-__global__ void __launch_bounds__(kT* kUY) ch_update_reduced_kernel(const TC* __restrict__ y1,
-                                                                    const TC* __restrict__ yb, DirView<TC> D,
-                                                                    const double* __restrict__ cbar, double* cn,
-                                                                    double* cp, int nx, int ny, double k2,
-                                                                    int keep_roles) {
-  __shared__ TC s_tau[4][kT];
-  const int z = blockIdx.z, s = blockIdx.y, m = D.m, P = D.P, k = 4 * P;
-  const int i = blockIdx.x * kT + threadIdx.x;
-  const size_t S = (size_t)nx;
-  if (i < nx) {
-    const int q = threadIdx.y;
-    const int sq = q < 2 ? (s + 1 == P ? 0 : s + 1) : (s == 0 ? P - 1 : s - 1);
-    const TC* row = D.rinv + (size_t)z * k * k + (size_t)(4 * sq + q) * k;
-    const TC* ybz = yb + (size_t)z * 4 * P * S;
-    const int nb = 2 * D.band + 1 < P ? 2 * D.band + 1 : P;
-    const int s0 = nb == P ? 0 : sq - D.band;
-    TC acc = 0;
-    for (int bb = 0; bb < nb; ++bb) {
-      int sb = s0 + bb;
-      sb = sb < 0 ? sb + P : (sb >= P ? sb - P : sb);
-      const TC* v = ybz + (size_t)(4 * sb) * S + i;
-      const TC* w = row + 4 * sb;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) acc = fma(__ldg(&w[u]), v[(size_t)u * S], acc);
-    }
-    s_tau[q][threadIdx.x] = acc * (TC)k2;
-  }
-  __syncthreads();
-  if (i >= nx) return;
-  const TC t0 = s_tau[0][threadIdx.x], t1 = s_tau[1][threadIdx.x], t2 = s_tau[2][threadIdx.x],
-           t3 = s_tau[3][threadIdx.x];
-  const TC* vw = D.vw + (size_t)z * 4 * m;
-  const size_t base = (size_t)z * nx * ny + (size_t)s * m * nx + i;
-#pragma unroll 4
-  for (int r = threadIdx.y; r < m; r += kUY) {
-    const size_t p = base + (size_t)r * nx;
-    TC y = (TC)fma(k2, (double)y1[p], cbar[p]);
-    y = fma(-__ldg(&vw[r]), t0, y);
-    y = fma(-__ldg(&vw[m + r]), t1, y);
-    y = fma(-__ldg(&vw[2 * m + r]), t2, y);
-    const double nxt = (double)fma(-__ldg(&vw[3 * m + r]), t3, y);
-    if (keep_roles) {
-      cp[p] = cn[p];
-      cn[p] = nxt;
-    } else {
-      cp[p] = nxt;
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Diagnostics: per-block partial sums (fixed order), then one block.
 constexpr int kDiagBlocks = 304, kDiagThreads = 256;
@@ -1206,8 +1145,9 @@ static void step_f64(ChGroup* g, int G, double* cur, double* prev, void* work, i
   { PROF(kRedX); launch_reduced<double>(ybx, X, tx, nsx, 0, 1, 1.0, st); }
   { PROF(kFinX); ch_xfinish_kernel<double, double><<<tgrid, tblock, 0, st>>>(f, tx, X, w, nx, ny, G); }
   { PROF(kLocY); launch_local<double, double>(w, w, nx, nx, Y, yby, N, kyz, G, status, st); }
-  { PROF(kUpd); ch_update_reduced_kernel<double><<<dim3(ceil_div(nx, kT), Y.P, G), dim3(kT, kUY), 0, st>>>(
-        w, yby, Y, cbar, cur, prev, nx, ny, g->k2, keep_roles); }
+  { PROF(kRedY); launch_reduced<double>(yby, Y, ty, nx, kyz, G, g->k2, st); }
+  { PROF(kUpd); ch_update_kernel<double><<<dim3(ceil_div(nx, kSolveThreads), ny, G), kSolveThreads, 0, st>>>(
+        w, ty, Y, cbar, cur, prev, nx, ny, g->k2, keep_roles); }
 }
 
 static void step_f32r(ChGroup* g, int G, double* cur, double* prev, void* work, int keep_roles, cudaStream_t st,
