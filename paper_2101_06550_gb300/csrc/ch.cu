@@ -70,7 +70,7 @@ namespace {
 constexpr int kT = 32;      // tile edge of the transposing kernels
 constexpr int kBY = 8;      // tile threads in y
 constexpr int kRBY = 8;     // the RHS kernel's threads in y
-constexpr int kRMinBlocks = 7, kRMinBlocksNoise = 5;  // its resident blocks per SM (shared memory bound)
+constexpr int kRMinBlocks = 6, kRMinBlocksNoise = 5;  // its occupancy bound (38 registers; 7 fit by shared memory)
 static_assert(kT * kRBY >= 4 * (kT + 4) && kT % kRBY == 0, "RHS staging assumes one pass over the extra columns");
 constexpr int kSolveThreads = 128;
 // Rows of the FP64 reduced solve per thread.  Measured at 2048^2 (2048 systems x
@@ -102,7 +102,8 @@ __device__ __forceinline__ int wrap_near(int i, int n) {
 // The last phase maps j along the warp: its column reads of the shared tiles
 // (odd row pitches) are free of bank conflicts and its transposed stores are
 // coalesced, so the output needs no staging tile (31 KB of shared memory per
-// block: 7 blocks per SM; 39 KB and 5 blocks with the noise tile).
+// block; 39 KB with the noise tile).  Six blocks per SM with 38 registers
+// measured 129.5 us at 2048^2 against 131 us for seven with 32 registers.
 //
 // The pass writes r / k2 with k2 = (2/3) dt / dx^2, i.e. Lap_h M - kd (C^n - C^{n-1})
 // with kd = dx^2 / dt: one FMA where r itself takes a multiply and an FMA.  The
@@ -155,7 +156,12 @@ __global__ void __launch_bounds__(kT* kRBY, NOISE ? kRMinBlocksNoise : kRMinBloc
     s_cn[ly][lx] = a;
     s_cb[ly][lx] = fma(TC(2), a, -b);
   };
-  for (int ly = threadIdx.y; ly < kT + 4; ly += kRBY) stage(ly, threadIdx.x);
+  // unrolled, so that each thread's loads are all in flight before the first use
+#pragma unroll
+  for (int k = 0; k < (kT + 4 + kRBY - 1) / kRBY; ++k) {
+    const int ly = threadIdx.y + k * kRBY;
+    if (ly < kT + 4) stage(ly, threadIdx.x);
+  }
   if (tid < 4 * (kT + 4)) stage(tid >> 2, kT + (tid & 3));
   if constexpr (NOISE == kNoiseRead) {
     const size_t N = (size_t)nx * ny;
@@ -233,7 +239,12 @@ __global__ void __launch_bounds__(kT* kRBY, NOISE ? kRMinBlocksNoise : kRMinBloc
     if (ly >= 2 && ly < kT + 2 && lx >= 2 && lx < kT + 2 && gi < nx && gj < ny)
       cbz[(size_t)gj * nx + gi] = (double)s_cb[ly][lx];
   };
-  for (int ly = 1 + threadIdx.y; ly <= kT + 2; ly += kRBY) mstage(ly, 1 + threadIdx.x);
+  // unrolled: independent points interleave their dependent FP64 chains
+#pragma unroll
+  for (int k = 0; k < (kT + 2 + kRBY - 1) / kRBY; ++k) {
+    const int ly = 1 + threadIdx.y + k * kRBY;
+    if (ly <= kT + 2) mstage(ly, 1 + threadIdx.x);
+  }
   if (tid < 2 * (kT + 2)) mstage(1 + (tid >> 1), kT + 1 + (tid & 1));
   __syncthreads();
   const size_t ldo = (size_t)G * ny;
