@@ -5,8 +5,6 @@ its scratch in a fixed device array.  It must give the same mass and energy as
 the plan-based ch_diagnostics, on two calls in a row (the second call reuses the
 array the first one left behind).  This file is collected last on purpose.
 """
-import ctypes
-
 import numpy as np
 import pytest
 
