@@ -39,6 +39,12 @@ WORKLOAD = "ch2d_periodic_2048sq_gamma0.005_dt5e-4"
 # dram__bytes_write.sum, mean of 3 launches; the two written fields, r / k2 and
 # Cbar, partly stay in L2 for the kernels that read them next)
 PREWARM_S = 1.5  # untimed steps before the first measurement (see measure())
+# DRAM bytes (read + write) of one whole step on this workload, summed over its
+# kernels from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum).
+# ncu flushes the caches before each kernel it measures, so these are cold-cache
+# figures: intermediates that a live step finds in L2 are counted as DRAM reads.
+STEP_DRAM_BYTES_F64 = 272.94e6 + 43.99e6
+STEP_DRAM_BYTES_F32R = 373.69e6 + 19.73e6
 RHS_TRAFFIC_BYTES = 67.27e6 + 20.49e6  # ncu: dram__bytes_read + write per ch_rhs launch (mean of 3)
 
 
@@ -148,6 +154,23 @@ def fp32_accuracy(dev, checkpoints=(100, 1000, 5000)):
     return {"checkpoints": out,
             "note": "per-step error: one FP32+refine step from the FP64 state against the oracle; the "
                     "trajectory error grows with the spinodal instability (growth rate up to 1/(4 gamma))"}
+
+
+def hbm_fraction(pts, ms64, ms32, peak_gbs):
+    """The step's HBM traffic against the measured copy bandwidth.  The minimum a
+    step must move is 24 B per point (Cn and Cn-1 in, Cn+1 out); the ncu figure
+    is every kernel's DRAM bytes, cold-cache.  Both fall far below the peak: the
+    step is bound by the FP64 pipe (the roofline object), not by HBM."""
+    def one(ms, dram):
+        d = {"ms_per_step": ms, "algorithmic_bytes_per_step": 24 * pts, "dram_bytes_per_step_ncu_cold": dram,
+             "gbs_algorithmic": 24 * pts / (ms * 1e-3) / 1e9, "gbs_dram_ncu_cold": dram / (ms * 1e-3) / 1e9}
+        if peak_gbs:
+            d["frac_algorithmic"] = d["gbs_algorithmic"] / peak_gbs
+            d["frac_dram_ncu_cold"] = d["gbs_dram_ncu_cold"] / peak_gbs
+        return d
+
+    return {"peak_gbs": peak_gbs, "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
+            "fp64": one(ms64, STEP_DRAM_BYTES_F64), "fp32_refine": one(ms32, STEP_DRAM_BYTES_F32R)}
 
 
 def cpu_baseline_oracle(steps: int):
@@ -406,6 +429,7 @@ def run_chx(args, rank, world, local_rank):
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "clocks": clk.summary(),
         "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
+        "hbm": hbm_fraction(pts, ms64 / args.steps, ms32 / args.steps, peaks.get("hbm_gbs")),
     }
     line.update(extras)
     print(json.dumps(line), flush=True)
