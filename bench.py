@@ -651,6 +651,27 @@ def bench_ensemble(dev, precision, steps, warmup, count=512):
            "value": pts * steps / (ms * 1e-3), "unit": "grid-pt-steps/s", "segments": tuned,
            "hbm_bytes": ens.bytes_used}
     ens.close()
+    # the plain per-simulation FP64 step on the same GPU: each simulation advanced
+    # by its own ch_step plan, one after another (measured step time per size)
+    t_step = {}
+    for n in sorted(by_n):
+        plan = chx.ChPlan(n, n, n * dx, n * dx, 0.01, dt)
+        c = synth.uniform_torch(1, n * n, -0.1, 0.1, device=dev)
+        pc = c.clone()
+        w = plan.alloc_work(dev)
+        plan.step(c, pc, w, 3)
+        torch.cuda.synchronize()
+        a.record()
+        plan.step(c, pc, w, 20)
+        b.record()
+        torch.cuda.synchronize()
+        t_step[n] = a.elapsed_time(b) / 20
+        plan.close()
+    serial_ms = sum(len(lst) * t_step[n] for n, lst in by_n.items())
+    res["per_simulation_fp64_baseline"] = {"ms_per_ensemble_step": serial_ms, "value": pts / (serial_ms * 1e-3),
+                                           "step_ms_by_n": t_step,
+                                           "kind": "one FP64 ch_step plan per simulation, run in turn"}
+    res["speedup_vs_per_simulation_fp64"] = serial_ms / (ms / steps)
     return res
 
 
