@@ -34,18 +34,24 @@ LX = 2 * np.pi
 GAMMA, DT = 0.005, 5e-4
 SEED = 3
 WORKLOAD = "ch2d_periodic_2048sq_gamma0.005_dt5e-4"
-# DRAM bytes (read + write) per launch of the FP64 right-hand-side kernel on this
-# workload, from an ncu capture of the current kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum, mean of 3 launches; the two written fields, r / k2 and
-# Cbar, partly stay in L2 for the kernels that read them next)
 PREWARM_S = 1.5  # untimed steps before the first measurement (see measure())
 # DRAM bytes (read + write) of one whole step on this workload, summed over its
 # kernels from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum).
 # ncu flushes the caches before each kernel it measures, so these are cold-cache
 # figures: intermediates that a live step finds in L2 are counted as DRAM reads.
-STEP_DRAM_BYTES_F64 = 272.94e6 + 43.99e6
+STEP_DRAM_BYTES_F64 = 373.58e6 + 53.25e6
 STEP_DRAM_BYTES_F32R = 373.69e6 + 19.73e6
-RHS_TRAFFIC_BYTES = 67.27e6 + 20.49e6  # ncu: dram__bytes_read + write per ch_rhs launch (mean of 3)
+# DRAM bytes (read + write) per launch of the FP64 step's kernels on this
+# workload, from one ncu capture of the current kernels (dram__bytes_read.sum +
+# dram__bytes_write.sum, mean of 3 launches).  The first right-hand-side pass
+# (ch_rhs: Cbar and M) writes two fields that partly stay in L2 for the
+# kernels that read them next.  None: not captured for the current kernel.
+KERNEL_TRAFFIC_BYTES = {"ch_rhs": 67.20e6 + 22.67e6, "ch_rhs_lap": 100.72e6 + 6.54e6}
+# Algorithmic FP64 operations and bytes per grid point of each FP64 kernel.
+KERNEL_FP64_OPS = {"ch_rhs": 8.0, "ch_rhs_lap": 6.0, "spike_local_x": 5.0, "spike_local_y": 5.0, "ch_xfinish": 4.0,
+                   "ch_update": 5.0}
+KERNEL_BYTES = {"ch_rhs": 32, "ch_rhs_lap": 32, "spike_local_x": 16, "spike_local_y": 16, "ch_xfinish": 16,
+                "ch_update": 24}
 
 
 def _peaks():
@@ -163,10 +169,11 @@ def hbm_fraction(pts, ms64, ms32, peak_gbs):
     step is bound by the FP64 pipe (the roofline object), not by HBM."""
     def one(ms, dram):
         d = {"ms_per_step": ms, "algorithmic_bytes_per_step": 24 * pts, "dram_bytes_per_step_ncu_cold": dram,
-             "gbs_algorithmic": 24 * pts / (ms * 1e-3) / 1e9, "gbs_dram_ncu_cold": dram / (ms * 1e-3) / 1e9}
+             "gbs_algorithmic": 24 * pts / (ms * 1e-3) / 1e9,
+             "gbs_dram_ncu_cold": dram / (ms * 1e-3) / 1e9 if dram else None}
         if peak_gbs:
             d["frac_algorithmic"] = d["gbs_algorithmic"] / peak_gbs
-            d["frac_dram_ncu_cold"] = d["gbs_dram_ncu_cold"] / peak_gbs
+            d["frac_dram_ncu_cold"] = d["gbs_dram_ncu_cold"] / peak_gbs if dram else None
         return d
 
     return {"peak_gbs": peak_gbs, "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
@@ -363,14 +370,14 @@ def run_chx(args, rank, world, local_rank):
     peaks = _peaks()
     # dominant kernel of the FP64 step and its roofline (FP64-pipe bound)
     dom, (dom_ms, dom_n) = max(prof64.items(), key=lambda kv: kv[1][0])
-    dp_ops = {"ch_rhs": 14.0, "spike_local_x": 5.0, "spike_local_y": 5.0, "ch_xfinish": 4.0, "ch_update": 5.0}
     per_launch_ms = dom_ms / max(1, dom_n)
     fp64_peak_gops = 1.90 * 152 * 2.070  # measured DFMA issue rate x SMs x max clock (G DP-ops/s)
-    if dom in dp_ops:
-        ach = dp_ops[dom] * pts / (per_launch_ms * 1e-3) / 1e9
+    if dom in KERNEL_FP64_OPS:
+        ach = KERNEL_FP64_OPS[dom] * pts / (per_launch_ms * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp64_peak_gops, "unit": "G fp64-op/s",
-                "frac": ach / fp64_peak_gops, "traffic": RHS_TRAFFIC_BYTES if dom == "ch_rhs" else None,
-                "traffic_unit": "bytes per launch", "algorithmic_bytes": 32 * pts, "ms_per_launch": per_launch_ms,
+                "frac": ach / fp64_peak_gops, "fp64_ops_per_point": KERNEL_FP64_OPS[dom],
+                "traffic": KERNEL_TRAFFIC_BYTES.get(dom), "traffic_unit": "bytes per launch",
+                "algorithmic_bytes": KERNEL_BYTES[dom] * pts, "ms_per_launch": per_launch_ms,
                 "peak_source": "measured DFMA microbenchmark 1.90/clk/SM x 152 SMs x 2070 MHz"}
     else:
         roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": fp64_peak_gops, "unit": "G fp64-op/s",

@@ -41,7 +41,7 @@ namespace chx {
 const char* const kSlotName[kSlots] = {"ch_rhs",           "spike_local_x",   "spike_reduced_x",  "ch_resid_x",
                                        "spike_local2_x",   "spike_reduced2_x", "ch_xfinish",       "spike_local_y",
                                        "spike_reduced_y",  "ch_resid_y",       "spike_local2_y",   "spike_reduced2_y",
-                                       "ch_update"};
+                                       "ch_update",        "ch_rhs_lap"};
 }  // namespace chx
 
 struct chx_ch_plan {
@@ -70,6 +70,9 @@ namespace {
 constexpr int kT = 32;      // tile edge of the transposing kernels
 constexpr int kBY = 8;      // tile threads in y
 constexpr int kRBY = 8;     // the RHS kernel's threads in y
+// The unforced FP64 RHS as two passes (ch_rhs_m_kernel, ch_rhs_r_kernel): measured
+// same-box at 2048^2, 0.2997 ms per step against 0.3038 ms with the one-pass kernel.
+constexpr bool kRhsTwoPass = true;
 constexpr int kRMinBlocks = 6, kRMinBlocksNoise = 5;  // its occupancy bound (38 registers; 7 fit by shared memory)
 static_assert(kT * kRBY >= 4 * (kT + 4) && kT % kRBY == 0, "RHS staging assumes one pass over the extra columns");
 constexpr int kSolveThreads = 128;
@@ -259,6 +262,108 @@ __global__ void __launch_bounds__(kT* kRBY, NOISE ? kRMinBlocksNoise : kRMinBloc
     TC o = fma(-kd, diff, l);
     if constexpr (NOISE == kNoiseRead) o += s_nz[lj][li];
     if constexpr (NOISE == kNoiseDraw) o = (o + f2d_exact(s_nz[lj][li].hi)) + f2d_exact(s_nz[lj][li].lo);
+    const int gi = i0 + li, gj = j0 + lj;
+    if (gi < nx && gj < ny) rT[(size_t)gi * ldo + (size_t)z * ny + gj] = (TO)o;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The same right-hand side in two passes (the unforced FP64 step), so that M is
+// formed once per point instead of again on every tile's halo ring: 14.1 FP64
+// operations per point instead of 15.2, for one more launch and 32 more bytes
+// per point (M out and back in), which the FP64-bound passes have room for.
+// Pass 1: Cbar = 2 C^n - C^{n-1} on 32 x 32 tiles with a 1-point halo, then
+// M = C^3 - C - gamma Lap_h Cbar on the tile; M and Cbar are stored row-major.
+template <typename TC>
+__global__ void __launch_bounds__(kT* kRBY) ch_rhs_m_kernel(const double* __restrict__ cn,
+                                                            const double* __restrict__ cp, double* __restrict__ m,
+                                                            double* __restrict__ cbar, int nx, int ny, TC rho,
+                                                            TC kap, const TC* __restrict__ gls) {
+  __shared__ TC s_cb[kT + 2][kT + 3];
+  const int z = blockIdx.z;
+  const TC gl = gls[z];
+  const size_t off = (size_t)z * nx * ny;
+  cn += off;
+  cp += off;
+  const int i0 = blockIdx.x * kT, j0 = blockIdx.y * kT;
+  const int tid = threadIdx.y * kT + threadIdx.x;
+  auto stage = [&](int ly, int lx) {
+    const int gi = wrap_near(i0 - 1 + lx, nx), gj = wrap_near(j0 - 1 + ly, ny);
+    const size_t p = (size_t)gj * nx + gi;
+    s_cb[ly][lx] = fma(TC(2), (TC)cn[p], -(TC)cp[p]);
+  };
+#pragma unroll
+  for (int k = 0; k < (kT + 2 + kRBY - 1) / kRBY; ++k) {
+    const int ly = threadIdx.y + k * kRBY;
+    if (ly < kT + 2) stage(ly, threadIdx.x);
+  }
+  if (tid < 2 * (kT + 2)) stage(tid >> 1, kT + (tid & 1));
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kT / kRBY; ++k) {
+    const int ly = 1 + threadIdx.y + k * kRBY, lx = 1 + threadIdx.x;
+    const int gi = i0 + threadIdx.x, gj = j0 + ly - 1;
+    if (gi < nx && gj < ny) {
+      TC l = s_cb[ly][lx - 1] + s_cb[ly][lx + 1];
+      l = fma(rho, s_cb[ly - 1][lx] + s_cb[ly + 1][lx], l);
+      l = fma(kap, s_cb[ly][lx], l);
+      const size_t p = (size_t)gj * nx + gi;
+      const TC c = (TC)__ldg(&cn[p]);
+      const TC nl = c * fma(c, c, TC(-1));
+      m[off + p] = (double)fma(-gl, l, nl);
+      cbar[off + p] = (double)s_cb[ly][lx];
+    }
+  }
+}
+
+// Pass 2: r / k2 = Lap_h M - kd (Cbar - C^n) on 32 x 32 tiles, M staged with a
+// 1-point halo and the difference on the tile, written transposed for the x
+// sweep as ch_rhs_kernel does.
+template <typename TC, typename TO>
+__global__ void __launch_bounds__(kT* kRBY) ch_rhs_r_kernel(const double* __restrict__ m,
+                                                            const double* __restrict__ cn,
+                                                            const double* __restrict__ cbar, TO* __restrict__ rT,
+                                                            int nx, int ny, int G, TC rho, TC kap, TC kd) {
+  __shared__ TC s_m[kT + 2][kT + 3];
+  __shared__ TC s_d[kT][kT + 1];
+  const int z = blockIdx.z;
+  const size_t off = (size_t)z * nx * ny;
+  m += off;
+  cn += off;
+  cbar += off;
+  const int i0 = blockIdx.x * kT, j0 = blockIdx.y * kT;
+  const int tid = threadIdx.y * kT + threadIdx.x;
+  auto stage = [&](int ly, int lx) {
+    const int gi = wrap_near(i0 - 1 + lx, nx), gj = wrap_near(j0 - 1 + ly, ny);
+    s_m[ly][lx] = (TC)m[(size_t)gj * nx + gi];
+  };
+#pragma unroll
+  for (int k = 0; k < (kT + 2 + kRBY - 1) / kRBY; ++k) {
+    const int ly = threadIdx.y + k * kRBY;
+    if (ly < kT + 2) stage(ly, threadIdx.x);
+  }
+  if (tid < 2 * (kT + 2)) stage(tid >> 1, kT + (tid & 1));
+#pragma unroll
+  for (int k = 0; k < kT / kRBY; ++k) {
+    const int lj = threadIdx.y + k * kRBY, li = threadIdx.x;
+    const int gi = i0 + li, gj = j0 + lj;
+    TC d = 0;
+    if (gi < nx && gj < ny) {
+      const size_t p = (size_t)gj * nx + gi;
+      d = (TC)cbar[p] - (TC)cn[p];  // C^n - C^{n-1}
+    }
+    s_d[lj][li] = d;
+  }
+  __syncthreads();
+  const size_t ldo = (size_t)G * ny;
+#pragma unroll
+  for (int k = 0; k < kT / kRBY; ++k) {
+    const int li = threadIdx.y + k * kRBY, lj = threadIdx.x;  // output (i0 + li, j0 + lj)
+    const int ly = lj + 1, lx = li + 1;
+    TC l = s_m[ly][lx - 1] + s_m[ly][lx + 1];
+    l = fma(rho, s_m[ly - 1][lx] + s_m[ly + 1][lx], l);
+    l = fma(kap, s_m[ly][lx], l);
+    const TC o = fma(-kd, s_d[lj][li], l);
     const int gi = i0 + li, gj = j0 + lj;
     if (gi < nx && gj < ny) rT[(size_t)gi * ldo + (size_t)z * ny + gj] = (TO)o;
   }
@@ -1039,6 +1144,7 @@ int group_init(ChGroup* g, int nx, int ny, double lx, double ly, double gamma, d
   g->off_y2 = off; off = align256(off + mix);
   g->off_x0 = off; off = align256(off + mix);
   g->off_cb = off; off = align256(off + (f64 ? N * esz : 0));  // Cbar, formed by the RHS pass for the update
+  g->off_m = off; off = align256(off + (f64 && kRhsTwoPass ? N * esz : 0));  // M of the two-pass RHS
   const size_t kx = 4 * (size_t)g->X.P * ny * G, ky = 4 * (size_t)g->Y.P * nx * G;
   g->off_ybx = off; off = align256(off + kx * esz);
   g->off_tx = off; off = align256(off + kx * esz);
@@ -1147,6 +1253,12 @@ static void step_f64(ChGroup* g, int G, double* cur, double* prev, void* work, i
     ch_rhs_kernel<double, double, kNoiseRead><<<tgrid, rblock, 0, st>>>(
         cur, prev, f, nx, ny, G, g->rho, g->kap, g->d_gl, g->k1 / g->k2, cbar, const_cast<double*>(g->noise),
         g->nkx / g->k2, g->nky / g->k2);
+  } else if (kRhsTwoPass) {
+    double* mf = wptr<double>(work, g->off_m);
+    { PROF(kRhs); ch_rhs_m_kernel<double><<<tgrid, rblock, 0, st>>>(cur, prev, mf, cbar, nx, ny, g->rho, g->kap,
+                                                                    g->d_gl); }
+    { PROF(kRhsLap); ch_rhs_r_kernel<double, double><<<tgrid, rblock, 0, st>>>(mf, cur, cbar, f, nx, ny, G, g->rho,
+                                                                               g->kap, g->k1 / g->k2); }
   } else {
     PROF(kRhs);
     ch_rhs_kernel<double, double><<<tgrid, rblock, 0, st>>>(cur, prev, f, nx, ny, G, g->rho, g->kap, g->d_gl,

@@ -57,7 +57,8 @@ __device__ __forceinline__ void seg_row(int i, int m, float rm, int& s, int& r) 
 }
 
 // Per-kernel CUDA-event timing (ch_profile).
-enum ProfSlot { kRhs, kLocX, kRedX, kRefX, kLoc2X, kRed2X, kFinX, kLocY, kRedY, kRefY, kLoc2Y, kRed2Y, kUpd, kSlots };
+enum ProfSlot { kRhs, kLocX, kRedX, kRefX, kLoc2X, kRed2X, kFinX, kLocY, kRedY, kRefY, kLoc2Y, kRed2Y, kUpd, kRhsLap,
+                kSlots };
 extern const char* const kSlotName[kSlots];
 
 struct Prof {
@@ -102,7 +103,7 @@ struct ChGroup {
   float2* d_glff = nullptr;
   SpikeDir X, Y;
   // work layout (byte offsets), for G fields
-  size_t off_f = 0, off_flo = 0, off_w = 0, off_wlo = 0, off_y1 = 0, off_y2 = 0, off_x0 = 0, off_cb = 0;
+  size_t off_f = 0, off_flo = 0, off_w = 0, off_wlo = 0, off_y1 = 0, off_y2 = 0, off_x0 = 0, off_cb = 0, off_m = 0;
   size_t off_ybx = 0, off_tx = 0, off_ybx2 = 0, off_tx2 = 0, off_yby = 0, off_ty = 0, off_yby2 = 0, off_ty2 = 0;
   size_t work_bytes = 0;
 };

@@ -25,3 +25,27 @@ def test_reference_arm_prints_one_contract_line():
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"].startswith("ch2d_periodic_2048sq")
+
+
+def test_bench_refers_to_no_undefined_name():
+    # the GPU arm cannot run here, so a missing module-level name would only show
+    # on the GPU machine: every name the script loads must be a builtin, a module
+    # global, or bound somewhere in it
+    import ast
+    import builtins
+
+    tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
+    known = set(dir(builtins)) | {"__file__", "__name__"}
+    for n in ast.walk(tree):
+        if isinstance(n, ast.Name) and isinstance(n.ctx, (ast.Store, ast.Del)):
+            known.add(n.id)
+        elif isinstance(n, ast.arg):
+            known.add(n.arg)
+        elif isinstance(n, (ast.FunctionDef, ast.ClassDef)):
+            known.add(n.name)
+        elif isinstance(n, (ast.Import, ast.ImportFrom)):
+            known.update((a.asname or a.name).split(".")[0] for a in n.names)
+        elif isinstance(n, ast.ExceptHandler) and n.name:
+            known.add(n.name)
+    used = {n.id for n in ast.walk(tree) if isinstance(n, ast.Name) and isinstance(n.ctx, ast.Load)}
+    assert not used - known, sorted(used - known)
