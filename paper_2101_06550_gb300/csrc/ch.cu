@@ -69,12 +69,8 @@ namespace {
 
 constexpr int kT = 32;      // tile edge of the transposing kernels
 constexpr int kBY = 8;      // tile threads in y
-constexpr int kRBY = 8;     // the RHS kernel's threads in y
-// The unforced FP64 RHS as two passes (ch_rhs_m_kernel, ch_rhs_r_kernel): measured
-// same-box at 2048^2, 0.2997 ms per step against 0.3038 ms with the one-pass kernel.
-constexpr bool kRhsTwoPass = true;
-constexpr int kRMinBlocks = 6, kRMinBlocksNoise = 5;  // its occupancy bound (38 registers; 7 fit by shared memory)
-static_assert(kT * kRBY >= 4 * (kT + 4) && kT % kRBY == 0, "RHS staging assumes one pass over the extra columns");
+constexpr int kRBY = 8;     // the RHS passes' threads in y
+static_assert(kT * kRBY >= 2 * (kT + 2) && kT % kRBY == 0, "RHS staging assumes one pass over the extra columns");
 constexpr int kSolveThreads = 128;
 // Rows of the FP64 reduced solve per thread.  Measured at 2048^2 (2048 systems x
 // 16 segments per direction), whole graph-replayed step, same box, three rounds:
@@ -99,181 +95,20 @@ __device__ __forceinline__ int wrap_near(int i, int n) {
 }
 
 // ---------------------------------------------------------------------------
-// RHS stencil pass.  Tile of 32 (i) x 32 (j) outputs of simulation blockIdx.z,
-// Cn/Cbar staged with a 2-point halo, M with a 1-point halo.  Output element
-// (i, j) of simulation z goes to rT[i * (G*ny) + z*ny + j].  gls[z] = gamma/dx^2.
-// The last phase maps j along the warp: its column reads of the shared tiles
-// (odd row pitches) are free of bank conflicts and its transposed stores are
-// coalesced, so the output needs no staging tile (31 KB of shared memory per
-// block; 39 KB with the noise tile).  Six blocks per SM with 38 registers
-// measured 129.5 us at 2048^2 against 131 us for seven with 32 registers.
-//
-// The pass writes r / k2 with k2 = (2/3) dt / dx^2, i.e. Lap_h M - kd (C^n - C^{n-1})
-// with kd = dx^2 / dt: one FMA where r itself takes a multiply and an FMA.  The
-// solves are linear, so the update restores the scale (C^{n+1} = Cbar + k2 v').
-//
-// NOISE (Cahn-Hilliard-Cook, Sec. 7.7): adds (2/3) dt eta with
-// eta = sqrt(sigma / (dx dy dt)) div_h rho, the backward-difference divergence
-// of the deviates rho (planes rho^x, rho^y of nx*ny per simulation):
-// nkx (rho^x_ij - rho^x_{i-1,j}) + nky (rho^y_ij - rho^y_{i,j-1}) (nkx, nky
-// divided by k2 like the rest of the output), formed into a shared tile first.
-// kNoiseRead reads rho with coalesced row reads.  kNoiseDraw draws the tile's
-// deviates in place (noise.cuh; even nx, so that a Philox pair never straddles
-// rows): the 16 pairs of each tile row, the pair holding the west halo point,
-// and the row above, all with key (seed, sim0 + z) at the step *d_step (or
-// `step`), into float tiles that share memory with the M tile; the tile's own
-// deviates are also stored to rho.  The divergence of these FP32 deviates is
-// then formed in double-float on the FP32 pipes (exact differences, products
-// with nkx and nky as float pairs, bit-exact float -> double conversions), so
-// the forcing costs two FP64 additions per point instead of nine FP64-pipe
-// operations.
-constexpr int kNoiseNone = 0, kNoiseRead = 1, kNoiseDraw = 2;
-
-template <typename TC, typename TO, int NOISE = kNoiseNone>
-__global__ void __launch_bounds__(kT* kRBY, NOISE ? kRMinBlocksNoise : kRMinBlocks) ch_rhs_kernel(const double* __restrict__ cn, const double* __restrict__ cp,
-                                                         TO* __restrict__ rT, int nx, int ny, int G, TC rho, TC kap,
-                                                         const TC* __restrict__ gls, TC kd,
-                                                         double* __restrict__ cbar, double* dev = nullptr,
-                                                         double nkx = 0, double nky = 0, uint64_t seed = 0,
-                                                         uint64_t sim0 = 0, uint64_t step = 0,
-                                                         const uint64_t* __restrict__ d_step = nullptr) {
-  __shared__ TC s_cn[kT + 4][kT + 5];
-  __shared__ TC s_cb[kT + 4][kT + 5];
-  __shared__ TC s_m[kT + 2][kT + 3];
-  using NzT = typename std::conditional<NOISE == kNoiseDraw, ff, TC>::type;
-  __shared__ NzT s_nz[NOISE ? kT : 1][kT + 1];
-  static_assert(2 * (kT + 1) * (kT + 2) * sizeof(float) <= sizeof(TC) * (kT + 2) * (kT + 3),
-                "deviate tiles must fit in the M tile");
-  const int z = blockIdx.z;
-  const TC gl = gls[z];
-  cn += (size_t)z * nx * ny;
-  cp += (size_t)z * nx * ny;
-  const int i0 = blockIdx.x * kT, j0 = blockIdx.y * kT;
-  const int tid = threadIdx.y * kT + threadIdx.x;
-  // Phases 1 and 2 give each warp whole 32-column rows (bank-conflict free),
-  // then sweep the few columns past 32 with the first threads.
-  auto stage = [&](int ly, int lx) {
-    const int gi = wrap_near(i0 - 2 + lx, nx), gj = wrap_near(j0 - 2 + ly, ny);
-    const size_t p = (size_t)gj * nx + gi;
-    const TC a = (TC)cn[p], b = (TC)cp[p];
-    s_cn[ly][lx] = a;
-    s_cb[ly][lx] = fma(TC(2), a, -b);
-  };
-  // unrolled, so that each thread's loads are all in flight before the first use
-#pragma unroll
-  for (int k = 0; k < (kT + 4 + kRBY - 1) / kRBY; ++k) {
-    const int ly = threadIdx.y + k * kRBY;
-    if (ly < kT + 4) stage(ly, threadIdx.x);
-  }
-  if (tid < 4 * (kT + 4)) stage(tid >> 2, kT + (tid & 3));
-  if constexpr (NOISE == kNoiseRead) {
-    const size_t N = (size_t)nx * ny;
-    const double* rx = dev + (size_t)z * 2 * N;
-    const double* ry = rx + N;
-    for (int idx = tid; idx < kT * kT; idx += kT * kRBY) {
-      const int lj = idx / kT, li = idx % kT;
-      const int gi = i0 + li, gj = j0 + lj;
-      TC v = 0;
-      if (gi < nx && gj < ny) {
-        const size_t q = (size_t)gj * nx + gi;
-        const size_t qw = (size_t)gj * nx + (gi == 0 ? nx - 1 : gi - 1);
-        const size_t qs = (size_t)(gj == 0 ? ny - 1 : gj - 1) * nx + gi;
-        v = (TC)fma(nkx, rx[q] - rx[qw], nky * (ry[q] - ry[qs]));
-      }
-      s_nz[lj][li] = v;
-    }
-  }
-  // deviate tiles (kNoiseDraw): entry [a][b] is grid point (i0 - 1 + b, j0 - 1 + a), wrapped
-  float(*s_dx)[kT + 2] = reinterpret_cast<float(*)[kT + 2]>(&s_m[0][0]);
-  float(*s_dy)[kT + 2] = s_dx + (kT + 1);
-  if constexpr (NOISE == kNoiseDraw) {
-    if (d_step) step = *d_step;
-    const uint64_t key1 = sim0 + (uint64_t)z;
-    constexpr int kPairs = kT / 2 + 1;  // per staged row: the west halo's pair, then the tile's
-    for (int q = tid; q < (kT + 1) * kPairs; q += kT * kRBY) {
-      const int a = q / kPairs, h = q - a * kPairs;
-      const int gj = wrap_near(j0 - 1 + a, ny);
-      const int gi = h == 0 ? (i0 == 0 ? nx : i0) - 2 : i0 + 2 * (h - 1);  // even: first point of the pair
-      if (gi >= nx) continue;                                               // ragged last tile
-      float x0, y0, x1, y1;
-      deviate_pair(((size_t)gj * nx + gi) >> 1, step, seed, key1, &x0, &y0, &x1, &y1);
-      if (h == 0) {
-        s_dx[a][0] = x1;
-        s_dy[a][0] = y1;
-      } else {
-        s_dx[a][2 * h - 1] = x0;
-        s_dy[a][2 * h - 1] = y0;
-        s_dx[a][2 * h] = x1;
-        s_dy[a][2 * h] = y1;
-      }
-    }
-  }
-  __syncthreads();
-  if constexpr (NOISE == kNoiseDraw) {
-    const size_t N = (size_t)nx * ny;
-    double* rx = dev + (size_t)z * 2 * N;
-    double* ry = rx + N;
-    const ff wx = d2ff(nkx), wy = d2ff(nky);
-    for (int idx = tid; idx < kT * kT; idx += kT * kRBY) {
-      const int lj = idx / kT, li = idx % kT;
-      const int gi = i0 + li, gj = j0 + lj;
-      ff v{0.f, 0.f};
-      if (gi < nx && gj < ny) {
-        const float ax = s_dx[lj + 1][li + 1], ay = s_dy[lj + 1][li + 1];
-        v = ff_add(ff_mul(wx, two_sum(ax, -s_dx[lj + 1][li])), ff_mul(wy, two_sum(ay, -s_dy[lj][li + 1])));
-        const size_t q = (size_t)gj * nx + gi;
-        rx[q] = f2d_exact(ax);
-        ry[q] = f2d_exact(ay);
-      }
-      s_nz[lj][li] = v;
-    }
-    __syncthreads();  // the deviate tiles share memory with the M tile
-  }
-  double* cbz = cbar + (size_t)z * nx * ny;
-  auto mstage = [&](int ly, int lx) {  // M = C^3 - C - gamma Lap Cbar on the tile plus one halo ring
-    TC l = s_cb[ly][lx - 1] + s_cb[ly][lx + 1];
-    l = fma(rho, s_cb[ly - 1][lx] + s_cb[ly + 1][lx], l);
-    l = fma(kap, s_cb[ly][lx], l);
-    const TC c = s_cn[ly][lx];
-    const TC nl = c * fma(c, c, TC(-1));
-    s_m[ly - 1][lx - 1] = fma(-gl, l, nl);
-    // the tile's own Cbar goes out for the update (C^{n+1} = Cbar + v)
-    const int gi = i0 - 2 + lx, gj = j0 - 2 + ly;
-    if (ly >= 2 && ly < kT + 2 && lx >= 2 && lx < kT + 2 && gi < nx && gj < ny)
-      cbz[(size_t)gj * nx + gi] = (double)s_cb[ly][lx];
-  };
-  // unrolled: independent points interleave their dependent FP64 chains
-#pragma unroll
-  for (int k = 0; k < (kT + 2 + kRBY - 1) / kRBY; ++k) {
-    const int ly = 1 + threadIdx.y + k * kRBY;
-    if (ly <= kT + 2) mstage(ly, 1 + threadIdx.x);
-  }
-  if (tid < 2 * (kT + 2)) mstage(1 + (tid >> 1), kT + 1 + (tid & 1));
-  __syncthreads();
-  const size_t ldo = (size_t)G * ny;
-#pragma unroll
-  for (int k = 0; k < kT / kRBY; ++k) {
-    const int li = threadIdx.y + k * kRBY, lj = threadIdx.x;  // output (i0 + li, j0 + lj)
-    const int ly = lj + 1, lx = li + 1;
-    TC l = s_m[ly][lx - 1] + s_m[ly][lx + 1];
-    l = fma(rho, s_m[ly - 1][lx] + s_m[ly + 1][lx], l);
-    l = fma(kap, s_m[ly][lx], l);
-    const TC diff = s_cb[ly + 1][lx + 1] - s_cn[ly + 1][lx + 1];  // C^n - C^{n-1}
-    TC o = fma(-kd, diff, l);
-    if constexpr (NOISE == kNoiseRead) o += s_nz[lj][li];
-    if constexpr (NOISE == kNoiseDraw) o = (o + f2d_exact(s_nz[lj][li].hi)) + f2d_exact(s_nz[lj][li].lo);
-    const int gi = i0 + li, gj = j0 + lj;
-    if (gi < nx && gj < ny) rT[(size_t)gi * ldo + (size_t)z * ny + gj] = (TO)o;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// The same right-hand side in two passes (the unforced FP64 step), so that M is
-// formed once per point instead of again on every tile's halo ring: 14.1 FP64
-// operations per point instead of 15.2, for one more launch and 32 more bytes
-// per point (M out and back in), which the FP64-bound passes have room for.
-// Pass 1: Cbar = 2 C^n - C^{n-1} on 32 x 32 tiles with a 1-point halo, then
-// M = C^3 - C - gamma Lap_h Cbar on the tile; M and Cbar are stored row-major.
+// The FP64 right-hand side, in two passes over 32 (i) x 32 (j) tiles of
+// simulation blockIdx.z (gls[z] = gamma / dx^2):
+//   pass 1 (ch_rhs_m_kernel): Cbar = 2 C^n - C^{n-1} with a 1-point halo, then
+//     M = C^3 - C - gamma Lap_h Cbar on the tile; M and Cbar are stored (the
+//     update reads Cbar: C^{n+1} = Cbar + v);
+//   pass 2 (ch_rhs_r_kernel): r / k2 = Lap_h M - kd (Cbar - C^n), M staged with
+//     a 1-point halo, written transposed for the x sweep:
+//     rT[i * (G*ny) + z*ny + j].
+// A single pass would recompute M on every tile's halo ring (34^2 / 32^2 of
+// the points): 15.2 FP64 operations per point against 14.1 here, for one more
+// launch and 32 more bytes per point, which these FP64-bound passes absorb.
+// r / k2 with k2 = (2/3) dt / dx^2 and kd = dx^2 / dt takes one FMA where r
+// itself takes a multiply and an FMA; the solves are linear, so the update
+// restores the scale (C^{n+1} = Cbar + k2 v').
 template <typename TC>
 __global__ void __launch_bounds__(kT* kRBY) ch_rhs_m_kernel(const double* __restrict__ cn,
                                                             const double* __restrict__ cp, double* __restrict__ m,
@@ -287,6 +122,7 @@ __global__ void __launch_bounds__(kT* kRBY) ch_rhs_m_kernel(const double* __rest
   cp += off;
   const int i0 = blockIdx.x * kT, j0 = blockIdx.y * kT;
   const int tid = threadIdx.y * kT + threadIdx.x;
+  // whole 32-column rows per warp (bank-conflict free), then the two columns past 32
   auto stage = [&](int ly, int lx) {
     const int gi = wrap_near(i0 - 1 + lx, nx), gj = wrap_near(j0 - 1 + ly, ny);
     const size_t p = (size_t)gj * nx + gi;
@@ -316,18 +152,45 @@ __global__ void __launch_bounds__(kT* kRBY) ch_rhs_m_kernel(const double* __rest
   }
 }
 
-// Pass 2: r / k2 = Lap_h M - kd (Cbar - C^n) on 32 x 32 tiles, M staged with a
-// 1-point halo and the difference on the tile, written transposed for the x
-// sweep as ch_rhs_kernel does.
-template <typename TC, typename TO>
-__global__ void __launch_bounds__(kT* kRBY) ch_rhs_r_kernel(const double* __restrict__ m,
+// NOISE (Cahn-Hilliard-Cook, Sec. 7.7) adds, in pass 2, (2/3) dt eta / k2 with
+// eta = sqrt(sigma / (dx dy dt)) div_h rho, the backward-difference divergence
+// of the deviates rho (planes rho^x, rho^y of nx*ny per simulation):
+// nkx (rho^x_ij - rho^x_{i-1,j}) + nky (rho^y_ij - rho^y_{i,j-1}), nkx and nky
+// divided by k2 like the rest of the output.
+//   kNoiseRead: caller-given FP64 deviates, read with coalesced row reads and
+//     differenced in FP64 into a shared tile.
+//   kNoiseDraw: the tile's deviates drawn in place (noise.cuh; even nx, so that
+//     a Philox pair never straddles rows): the 16 pairs of each tile row, the
+//     pair holding the west halo point, and the row above, with key
+//     (seed, sim0 + z) at step *d_step (or `step`), into float tiles; the tile's
+//     own deviates are stored to rho as they are drawn.  The divergence of
+//     these FP32 values is formed in double-float on the FP32 pipes (exact
+//     differences, products with nkx and nky as float pairs, bit-exact float to
+//     double conversions): two FP64 additions per point instead of the nine
+//     FP64-pipe operations (conversions included) of forming it in FP64.
+constexpr int kNoiseNone = 0, kNoiseRead = 1, kNoiseDraw = 2;
+// Pass 2's occupancy bound.  Unbounded, its deviate-drawing form takes 54
+// registers and 4 blocks per SM: the Cook step measured 0.401 ms against 0.335 ms
+// with 6 blocks (40 registers) and 0.339 ms with 8 (same box); the plain step is
+// the same 0.2997 ms under all three.
+constexpr int kRLapMinBlocks = 6;
+
+template <typename TC, typename TO, int NOISE = kNoiseNone>
+__global__ void __launch_bounds__(kT* kRBY, kRLapMinBlocks) ch_rhs_r_kernel(const double* __restrict__ m,
                                                             const double* __restrict__ cn,
                                                             const double* __restrict__ cbar, TO* __restrict__ rT,
-                                                            int nx, int ny, int G, TC rho, TC kap, TC kd) {
+                                                            int nx, int ny, int G, TC rho, TC kap, TC kd,
+                                                            double* dev = nullptr, double nkx = 0, double nky = 0,
+                                                            uint64_t seed = 0, uint64_t sim0 = 0, uint64_t step = 0,
+                                                            const uint64_t* __restrict__ d_step = nullptr) {
   __shared__ TC s_m[kT + 2][kT + 3];
   __shared__ TC s_d[kT][kT + 1];
+  __shared__ TC s_nz[NOISE == kNoiseRead ? kT : 1][kT + 1];
+  // deviate tiles: [a][b] is grid point (i0 - 1 + b, j0 - 1 + a), wrapped; odd pitch for the transposed reads
+  __shared__ float s_dx[NOISE == kNoiseDraw ? kT + 1 : 1][kT + 1];
+  __shared__ float s_dy[NOISE == kNoiseDraw ? kT + 1 : 1][kT + 1];
   const int z = blockIdx.z;
-  const size_t off = (size_t)z * nx * ny;
+  const size_t N = (size_t)nx * ny, off = (size_t)z * N;
   m += off;
   cn += off;
   cbar += off;
@@ -354,8 +217,61 @@ __global__ void __launch_bounds__(kT* kRBY) ch_rhs_r_kernel(const double* __rest
     }
     s_d[lj][li] = d;
   }
+  if constexpr (NOISE == kNoiseRead) {
+    const double* rx = dev + (size_t)z * 2 * N;
+    const double* ry = rx + N;
+#pragma unroll
+    for (int k = 0; k < kT / kRBY; ++k) {
+      const int lj = threadIdx.y + k * kRBY, li = threadIdx.x;
+      const int gi = i0 + li, gj = j0 + lj;
+      TC v = 0;
+      if (gi < nx && gj < ny) {
+        const size_t q = (size_t)gj * nx + gi;
+        const size_t qw = (size_t)gj * nx + (gi == 0 ? nx - 1 : gi - 1);
+        const size_t qs = (size_t)(gj == 0 ? ny - 1 : gj - 1) * nx + gi;
+        v = (TC)fma(nkx, rx[q] - rx[qw], nky * (ry[q] - ry[qs]));
+      }
+      s_nz[lj][li] = v;
+    }
+  }
+  if constexpr (NOISE == kNoiseDraw) {
+    if (d_step) step = *d_step;
+    const uint64_t key1 = sim0 + (uint64_t)z;
+    double* rx = dev + (size_t)z * 2 * N;
+    double* ry = rx + N;
+    constexpr int kPairs = kT / 2 + 1;  // per staged row: the west halo's pair, then the tile's
+    for (int q = tid; q < (kT + 1) * kPairs; q += kT * kRBY) {
+      const int a = q / kPairs, h = q - a * kPairs;
+      const int gj = wrap_near(j0 - 1 + a, ny);
+      const int gi = h == 0 ? (i0 == 0 ? nx : i0) - 2 : i0 + 2 * (h - 1);  // even: first point of the pair
+      if (gi >= nx) continue;                                               // ragged last tile
+      float x0, y0, x1, y1;
+      const size_t p = (size_t)gj * nx + gi;
+      deviate_pair(p >> 1, step, seed, key1, &x0, &y0, &x1, &y1);
+      if (h == 0) {
+        s_dx[a][0] = x1;
+        s_dy[a][0] = y1;
+      } else {
+        s_dx[a][2 * h - 1] = x0;
+        s_dy[a][2 * h - 1] = y0;
+        s_dx[a][2 * h] = x1;
+        s_dy[a][2 * h] = y1;
+        if (a >= 1 && j0 + a - 1 < ny) {  // the tile's own points
+          rx[p] = f2d_exact(x0);
+          rx[p + 1] = f2d_exact(x1);
+          ry[p] = f2d_exact(y0);
+          ry[p + 1] = f2d_exact(y1);
+        }
+      }
+    }
+  }
   __syncthreads();
   const size_t ldo = (size_t)G * ny;
+  ff wx, wy;
+  if constexpr (NOISE == kNoiseDraw) {
+    wx = d2ff(nkx);
+    wy = d2ff(nky);
+  }
 #pragma unroll
   for (int k = 0; k < kT / kRBY; ++k) {
     const int li = threadIdx.y + k * kRBY, lj = threadIdx.x;  // output (i0 + li, j0 + lj)
@@ -363,7 +279,13 @@ __global__ void __launch_bounds__(kT* kRBY) ch_rhs_r_kernel(const double* __rest
     TC l = s_m[ly][lx - 1] + s_m[ly][lx + 1];
     l = fma(rho, s_m[ly - 1][lx] + s_m[ly + 1][lx], l);
     l = fma(kap, s_m[ly][lx], l);
-    const TC o = fma(-kd, s_d[lj][li], l);
+    TC o = fma(-kd, s_d[lj][li], l);
+    if constexpr (NOISE == kNoiseRead) o += s_nz[lj][li];
+    if constexpr (NOISE == kNoiseDraw) {
+      const ff v = ff_add(ff_mul(wx, two_sum(s_dx[lj + 1][li + 1], -s_dx[lj + 1][li])),
+                          ff_mul(wy, two_sum(s_dy[lj + 1][li + 1], -s_dy[lj][li + 1])));
+      o = (o + f2d_exact(v.hi)) + f2d_exact(v.lo);
+    }
     const int gi = i0 + li, gj = j0 + lj;
     if (gi < nx && gj < ny) rT[(size_t)gi * ldo + (size_t)z * ny + gj] = (TO)o;
   }
@@ -1144,7 +1066,7 @@ int group_init(ChGroup* g, int nx, int ny, double lx, double ly, double gamma, d
   g->off_y2 = off; off = align256(off + mix);
   g->off_x0 = off; off = align256(off + mix);
   g->off_cb = off; off = align256(off + (f64 ? N * esz : 0));  // Cbar, formed by the RHS pass for the update
-  g->off_m = off; off = align256(off + (f64 && kRhsTwoPass ? N * esz : 0));  // M of the two-pass RHS
+  g->off_m = off; off = align256(off + (f64 ? N * esz : 0));  // M, between the two RHS passes
   const size_t kx = 4 * (size_t)g->X.P * ny * G, ky = 4 * (size_t)g->Y.P * nx * G;
   g->off_ybx = off; off = align256(off + kx * esz);
   g->off_tx = off; off = align256(off + kx * esz);
@@ -1243,26 +1165,22 @@ static void step_f64(ChGroup* g, int G, double* cur, double* prev, void* work, i
   const int nsx = G * ny;  // the x sweep: all row systems of the group, interleaved
   const DirView<double> X = view<double>(g->X, ny), Y = view<double>(g->Y, nx);
   const size_t kyz = 4 * (size_t)Y.P * nx;
-  if (g->noise_w) {
-    PROF(kRhs);
-    ch_rhs_kernel<double, double, kNoiseDraw><<<tgrid, rblock, 0, st>>>(
-        cur, prev, f, nx, ny, G, g->rho, g->kap, g->d_gl, g->k1 / g->k2, cbar, g->noise_w, g->nkx / g->k2,
-        g->nky / g->k2, g->noise_seed, g->noise_sim0, g->noise_step, g->noise_dstep);
-  } else if (g->noise) {
-    PROF(kRhs);
-    ch_rhs_kernel<double, double, kNoiseRead><<<tgrid, rblock, 0, st>>>(
-        cur, prev, f, nx, ny, G, g->rho, g->kap, g->d_gl, g->k1 / g->k2, cbar, const_cast<double*>(g->noise),
-        g->nkx / g->k2, g->nky / g->k2);
-  } else if (kRhsTwoPass) {
-    double* mf = wptr<double>(work, g->off_m);
-    { PROF(kRhs); ch_rhs_m_kernel<double><<<tgrid, rblock, 0, st>>>(cur, prev, mf, cbar, nx, ny, g->rho, g->kap,
-                                                                    g->d_gl); }
-    { PROF(kRhsLap); ch_rhs_r_kernel<double, double><<<tgrid, rblock, 0, st>>>(mf, cur, cbar, f, nx, ny, G, g->rho,
-                                                                               g->kap, g->k1 / g->k2); }
-  } else {
-    PROF(kRhs);
-    ch_rhs_kernel<double, double><<<tgrid, rblock, 0, st>>>(cur, prev, f, nx, ny, G, g->rho, g->kap, g->d_gl,
-                                                            g->k1 / g->k2, cbar);
+  double* mf = wptr<double>(work, g->off_m);
+  { PROF(kRhs); ch_rhs_m_kernel<double><<<tgrid, rblock, 0, st>>>(cur, prev, mf, cbar, nx, ny, g->rho, g->kap,
+                                                                  g->d_gl); }
+  {
+    PROF(kRhsLap);
+    const double kd = g->k1 / g->k2;
+    if (g->noise_w)
+      ch_rhs_r_kernel<double, double, kNoiseDraw><<<tgrid, rblock, 0, st>>>(
+          mf, cur, cbar, f, nx, ny, G, g->rho, g->kap, kd, g->noise_w, g->nkx / g->k2, g->nky / g->k2,
+          g->noise_seed, g->noise_sim0, g->noise_step, g->noise_dstep);
+    else if (g->noise)
+      ch_rhs_r_kernel<double, double, kNoiseRead><<<tgrid, rblock, 0, st>>>(
+          mf, cur, cbar, f, nx, ny, G, g->rho, g->kap, kd, const_cast<double*>(g->noise), g->nkx / g->k2,
+          g->nky / g->k2);
+    else
+      ch_rhs_r_kernel<double, double><<<tgrid, rblock, 0, st>>>(mf, cur, cbar, f, nx, ny, G, g->rho, g->kap, kd);
   }
   { PROF(kLocX); launch_local<double, double>(f, f, nsx, nsx, X, ybx, 0, 0, 1, status, st); }
   { PROF(kRedX); launch_reduced<double>(ybx, X, tx, nsx, 0, 1, 1.0, st); }
