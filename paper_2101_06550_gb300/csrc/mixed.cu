@@ -47,13 +47,16 @@ __device__ __forceinline__ ff lap_ff(const ff (*t)[LD], int y, int x, ff rho, ff
 }
 
 // Right-hand side of Eq. 3.1 in double-float: r = k2 L'(M) - k1 (C^n - C^{n-1}),
-// M = C^3 - C - gl L'(Cbar).  Same tiling as the FP64 kernel: whole 32-column
-// rows per warp while staging, j along the warp for the output, whose
-// transposed stores are then coalesced without a staging tile.
+// M = C^3 - C - gl L'(Cbar), in one pass over 32 x 32 tiles (M formed on the
+// tile and a 1-point halo ring): whole 32-column rows per warp while staging,
+// j along the warp for the output, whose transposed stores are then coalesced
+// without a staging tile.  (The FP64 step splits this into two passes to save
+// the ring's FP64 work; here the ring costs issue slots on the FP32 pipes.)
 //
 // NOISE (Cahn-Hilliard-Cook, Sec. 7.7): the forcing term (2/3) dt eta is
 // formed in FP64 on the otherwise idle FP64 unit (one subtraction and one FMA
-// per direction), as in the FP64 kernel, and added as a double-float pair.
+// per direction) from caller-given or pre-drawn deviates, and added as a
+// double-float pair.
 template <bool kIso, bool NOISE = false>
 __global__ void __launch_bounds__(kT* kBY) ch_rhs_ff_kernel(const double* __restrict__ cn,
                                                             const double* __restrict__ cp, float* __restrict__ rhi,
