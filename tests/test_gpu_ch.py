@@ -150,6 +150,22 @@ def test_ch_step_256_500_steps_per_step_parity_and_mass():
     assert e1 < e0
 
 
+@pytest.mark.parametrize("ny,nx,lx,ly", [(64, 48, 2 * np.pi, np.pi), (40, 96, 3.0, 7.0), (33, 47, 2 * np.pi, 2.5)])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 1e-6)])
+def test_ch_step_unequal_spacing_matches_oracle(ny, nx, lx, ly, precision, tol):
+    # dx != dy: the Laplacians weight the y neighbours by (dx/dy)^2 (the
+    # anisotropic forms of both right-hand sides) and the two sweeps carry
+    # different a' = (2/3) gamma dt / dx^4 and / dy^4; 33 x 47 takes single
+    # segments of odd length
+    gamma, dt = 0.01, 1e-3
+    c0 = synth.field(21, ny, nx, -0.2, 0.2)
+    cm = c0 + 1e-3 * synth.field(22, ny, nx, -1, 1)
+    got, gprev = _run_gpu(c0, cm, lx, ly, gamma, dt, 3, precision=precision)
+    ref, rprev = oracle.ch_run(c0, cm, lx, ly, gamma, dt, 3)
+    assert _rel(got, ref) <= tol
+    assert _rel(gprev, rprev) <= tol
+
+
 @pytest.mark.parametrize("n,bound", [(512, 1e-6), (2048, 1e-4)])
 def test_ch_step_f32_refine_from_random_state(n, bound):
     # one step from the rough random initial state.  At 2048^2 (a' = 1.9e4) the

@@ -106,17 +106,18 @@ def test_cook_run_matches_oracle_from_rest(nsteps):
     assert np.all(np.abs(rho.cpu().numpy().reshape(2, n, n) - last) <= 5e-7 * np.sqrt(last[0]**2 + last[1]**2))
 
 
-@pytest.mark.parametrize("nx,ny", [(64, 64), (70, 40), (96, 33), (63, 48)])
-def test_cook_run_in_place_draw_matches_the_deviate_kernel(nx, ny):
+@pytest.mark.parametrize("nx,ny,aspect", [(64, 64, 1.0), (70, 40, 1.0), (96, 33, 1.0), (63, 48, 1.0), (64, 48, 0.5)])
+def test_cook_run_in_place_draw_matches_the_deviate_kernel(nx, ny, aspect):
     # For even nx the FP64 right-hand side draws each step's deviates itself
     # (tile by tile, with the west and south halo pairs); for odd nx the
     # standalone kernel draws them first.  Either way rho ends up bit-identical
     # to ch_noise_normals of the last step, and every step matches the oracle
     # driven by the standalone kernel's deviates.  70 and 40 leave ragged
-    # tiles; 33 rows wrap the halo row of the last tile row.
+    # tiles; 33 rows wrap the halo row of the last tile row; aspect != 1 makes
+    # dy != dx (different forcing weights in x and y).
     chx = _chx()
     lx, gamma, dt, sigma, seed, sim, step0, nsteps = 2 * np.pi, 0.01, 1e-3, 1e-6, 5, 2, 4, 3
-    ly = lx * ny / nx
+    ly = lx * ny / nx * aspect
     c0 = synth.field(81, ny, nx, -0.1, 0.1)
     plan = chx.ChPlan(nx, ny, lx, ly, gamma, dt)
     cn = torch.from_numpy(c0).to(DEV).reshape(-1)
