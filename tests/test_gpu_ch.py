@@ -124,6 +124,22 @@ def test_ch_step_stiff_large_grid_one_step():
     assert np.max(np.abs(got - sp)) <= max(tol, 1.5 * np.max(np.abs(ref - sp)))
 
 
+def test_ch_step_4096sq_beyond_the_workloads():
+    # twice the largest workload's grid (16.8 M points; 8 segments of 512 per
+    # direction, against 16 of 128 at 2048^2): one step against the oracle and
+    # its mass
+    n, lx, gamma, dt = 4096, 2 * np.pi, 0.005, 5e-4
+    c0 = synth.field(5, n, n, -0.05, 0.05)
+    cm = c0 + 1e-4 * synth.field(6, n, n, -1, 1)
+    got, gprev = _run_gpu(c0, cm, lx, lx, gamma, dt, 1)
+    assert np.array_equal(gprev, c0)
+    ref, _ = oracle.ch_run(c0, cm, lx, lx, gamma, dt, 1)
+    assert np.max(np.abs(got - ref)) <= step_tolerance(ref, c0, cm, lx, lx, gamma, dt)
+    # Lap_h sums to zero and the solves keep sums, so the mean follows the
+    # scheme's k = 0 mode: M^{n+1} = (4 M^n - M^{n-1}) / 3
+    assert abs(got.sum() - (4 * c0.sum() - cm.sum()) / 3) <= 1e-12 * np.abs(c0).sum()
+
+
 def test_ch_step_256_500_steps_per_step_parity_and_mass():
     # the 256^2, 500-step workload: per-step parity from the same input state at
     # sampled steps, and mass conservation along the GPU trajectory
