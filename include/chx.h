@@ -160,7 +160,9 @@ int tri_cyclic_solve_batched(chx_tri_plan* plan, void* rhs_inout, int batch, voi
  * ch_plan_create: nx, ny in [8, 16384]; lx, ly, dt > 0; gamma >= 0;
  *   precision CHX_PREC_F64 or CHX_PREC_F32_REFINE.  Factors the two implicit
  *   operators on the host in FP64 and uploads them (plan-owned).
- * ch_work_bytes: size of the caller-provided device scratch `work` for ch_step.
+ * ch_work_bytes: size of the caller-provided device scratch `work` for ch_step
+ *   (FP64: about 32 B per grid point, for r, w, Cbar and M; FP32+refine: about
+ *   28 B per point; plus the reduced systems' few values per segment).
  * ch_step: advances nsteps >= 0 steps.  c_now and c_prev are device arrays of
  *   nx * ny doubles (row-major, ld = nx) that keep their roles: on return
  *   c_now = C^{n+nsteps} and c_prev = C^{n+nsteps-1}.  work must hold at
