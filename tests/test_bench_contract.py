@@ -49,3 +49,19 @@ def test_bench_refers_to_no_undefined_name():
             known.add(n.name)
     used = {n.id for n in ast.walk(tree) if isinstance(n, ast.Name) and isinstance(n.ctx, ast.Load)}
     assert not used - known, sorted(used - known)
+
+
+def test_bench_kernel_tables_name_profile_slots():
+    # the roofline tables are keyed by the library's profile slot names
+    import re
+    import sys as _sys
+
+    _sys.path.insert(0, ROOT)
+    import bench
+
+    src = open(os.path.join(ROOT, "paper_2101_06550_gb300", "csrc", "ch.cu")).read()
+    table = src[src.index("kSlotName[kSlots] = {"):]
+    slots = set(re.findall(r'"([a-z0-9_]+)"', table[:table.index("};")]))
+    for name in list(bench.KERNEL_FP64_OPS) + list(bench.KERNEL_BYTES) + list(bench.KERNEL_TRAFFIC_BYTES):
+        assert name in slots, name
+    assert set(bench.KERNEL_FP64_OPS) == set(bench.KERNEL_BYTES)
