@@ -20,8 +20,6 @@ struct ff {
   float hi, lo;
 };
 
-__device__ __forceinline__ ff ff_make(float h, float l) { return ff{h, l}; }
-
 // |a| >= |b| (or a == 0)
 __device__ __forceinline__ ff fast_two_sum(float a, float b) {
   const float s = a + b;
