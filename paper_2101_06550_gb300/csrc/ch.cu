@@ -109,8 +109,11 @@ __device__ __forceinline__ int wrap_near(int i, int n) {
 // r / k2 with k2 = (2/3) dt / dx^2 and kd = dx^2 / dt takes one FMA where r
 // itself takes a multiply and an FMA; the solves are linear, so the update
 // restores the scale (C^{n+1} = Cbar + k2 v').
+// Pass 1's occupancy bound: 8 blocks per SM (32 registers).  Same-box A/B at
+// 2048^2: 0.0725 ms per launch, against 0.0727-0.0728 ms with 6 or 4 blocks.
+constexpr int kRMMinBlocks = 8;
 template <typename TC>
-__global__ void __launch_bounds__(kT* kRBY) ch_rhs_m_kernel(const double* __restrict__ cn,
+__global__ void __launch_bounds__(kT* kRBY, kRMMinBlocks) ch_rhs_m_kernel(const double* __restrict__ cn,
                                                             const double* __restrict__ cp, double* __restrict__ m,
                                                             double* __restrict__ cbar, int nx, int ny, TC rho,
                                                             TC kap, const TC* __restrict__ gls) {
