@@ -41,7 +41,7 @@ namespace chx {
 const char* const kSlotName[kSlots] = {"ch_rhs",           "spike_local_x",   "spike_reduced_x",  "ch_resid_x",
                                        "spike_local2_x",   "spike_reduced2_x", "ch_xfinish",       "spike_local_y",
                                        "spike_reduced_y",  "ch_resid_y",       "spike_local2_y",   "spike_reduced2_y",
-                                       "ch_update",        "ch_rhs_lap"};
+                                       "ch_update",        "ch_rhs_lap",       "x_solve_ff",       "y_solve_ff"};
 }  // namespace chx
 
 struct chx_ch_plan {
@@ -835,6 +835,14 @@ int put(T* dst, const std::vector<double>& src) {
   return cuda_check(cudaMemcpy(dst, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice), "ch: upload");
 }
 
+// Uploads v - (float)v for every entry: the low float of the double-float pair
+// whose high float put<float> stores.
+int put_lo(float* dst, const std::vector<double>& src) {
+  std::vector<float> h(src.size());
+  for (size_t i = 0; i < src.size(); ++i) h[i] = (float)(src[i] - (double)(float)src[i]);
+  return cuda_check(cudaMemcpy(dst, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice), "ch: upload");
+}
+
 int dir_alloc(SpikeDir* D, int n, int P, int slots) {
   D->n = n;
   D->P = P;
@@ -844,7 +852,9 @@ int dir_alloc(SpikeDir* D, int n, int P, int slots) {
   int rc;
   if ((rc = dev_alloc(&D->d_a, slots)) || (rc = dev_alloc(&D->d_lu, m4)) || (rc = dev_alloc(&D->d_vw, m4)) ||
       (rc = dev_alloc(&D->d_rinv, kk)) || (rc = dev_alloc(&D->d_a32, slots)) || (rc = dev_alloc(&D->d_aff, slots)) ||
-      (rc = dev_alloc(&D->d_lu32, m4)) || (rc = dev_alloc(&D->d_vw32, m4)) || (rc = dev_alloc(&D->d_rinv32, kk)))
+      (rc = dev_alloc(&D->d_lu32, m4)) || (rc = dev_alloc(&D->d_vw32, m4)) || (rc = dev_alloc(&D->d_rinv32, kk)) ||
+      (rc = dev_alloc(&D->d_vwlo, m4)) || (rc = dev_alloc(&D->d_rinvlo, kk)) || (rc = dev_alloc(&D->d_rb32, kk)) ||
+      (rc = dev_alloc(&D->d_rblo, kk)))
     return rc;
   return CHX_OK;
 }
@@ -858,11 +868,18 @@ int dir_set(SpikeDir* D, int z, double a) {
   const int band = rinv_band(rinv, D->P);
   if (band > D->band) D->band = band;
   const size_t m4 = 4 * (size_t)D->m, kk = (size_t)16 * D->P * D->P;
+  const int P = D->P, K = 4 * P;
+  std::vector<double> rb(kk);
+  for (int d = 0; d < P; ++d)
+    for (int u = 0; u < 4; ++u)
+      for (int q = 0; q < K; ++q) rb[(size_t)(d * 4 + u) * K + q] = rinv[(size_t)q * K + 4 * ((q / 4 + d) % P) + u];
   const std::vector<double> av(1, a);
   const float2 aff = split_ff(a);
   if ((rc = put(D->d_a + z, av)) || (rc = put(D->d_lu + z * m4, lu)) || (rc = put(D->d_vw + z * m4, vw)) ||
       (rc = put(D->d_rinv + z * kk, rinv)) || (rc = put(D->d_a32 + z, av)) || (rc = put(D->d_lu32 + z * m4, lu)) ||
-      (rc = put(D->d_vw32 + z * m4, vw)) || (rc = put(D->d_rinv32 + z * kk, rinv)))
+      (rc = put(D->d_vw32 + z * m4, vw)) || (rc = put(D->d_rinv32 + z * kk, rinv)) ||
+      (rc = put_lo(D->d_vwlo + z * m4, vw)) || (rc = put_lo(D->d_rinvlo + z * kk, rinv)) ||
+      (rc = put(D->d_rb32 + z * kk, rb)) || (rc = put_lo(D->d_rblo + z * kk, rb)))
     return rc;
   return cuda_check(cudaMemcpy(D->d_aff + z, &aff, sizeof(float2), cudaMemcpyHostToDevice), "ch: upload");
 }
@@ -881,15 +898,20 @@ int dir_replicate(SpikeDir* D) {
     if (!rc) rc = cuda_check(cudaMemcpy(D->d_lu32 + z * m4, D->d_lu32, m4 * 4, cudaMemcpyDeviceToDevice), "ch: replicate");
     if (!rc) rc = cuda_check(cudaMemcpy(D->d_vw32 + z * m4, D->d_vw32, m4 * 4, cudaMemcpyDeviceToDevice), "ch: replicate");
     if (!rc) rc = cuda_check(cudaMemcpy(D->d_rinv32 + z * kk, D->d_rinv32, kk * 4, cudaMemcpyDeviceToDevice), "ch: replicate");
+    if (!rc) rc = cuda_check(cudaMemcpy(D->d_vwlo + z * m4, D->d_vwlo, m4 * 4, cudaMemcpyDeviceToDevice), "ch: replicate");
+    if (!rc) rc = cuda_check(cudaMemcpy(D->d_rinvlo + z * kk, D->d_rinvlo, kk * 4, cudaMemcpyDeviceToDevice), "ch: replicate");
+    if (!rc) rc = cuda_check(cudaMemcpy(D->d_rb32 + z * kk, D->d_rb32, kk * 4, cudaMemcpyDeviceToDevice), "ch: replicate");
+    if (!rc) rc = cuda_check(cudaMemcpy(D->d_rblo + z * kk, D->d_rblo, kk * 4, cudaMemcpyDeviceToDevice), "ch: replicate");
   }
   return rc;
 }
 
 int dir_move(SpikeDir* D, int from, int to, cudaStream_t st) {
   const size_t m4 = 4 * (size_t)D->m, kk = (size_t)16 * D->P * D->P;
-  struct { void* base; size_t esz, per; } a[9] = {
+  struct { void* base; size_t esz, per; } a[13] = {
       {D->d_a, 8, 1}, {D->d_lu, 8, m4}, {D->d_vw, 8, m4}, {D->d_rinv, 8, kk}, {D->d_a32, 4, 1},
-      {D->d_aff, 8, 1}, {D->d_lu32, 4, m4}, {D->d_vw32, 4, m4}, {D->d_rinv32, 4, kk}};
+      {D->d_aff, 8, 1}, {D->d_lu32, 4, m4}, {D->d_vw32, 4, m4}, {D->d_rinv32, 4, kk}, {D->d_vwlo, 4, m4},
+      {D->d_rinvlo, 4, kk}, {D->d_rb32, 4, kk}, {D->d_rblo, 4, kk}};
   for (auto& x : a) {
     const size_t b = x.esz * x.per;
     int rc = cuda_check(cudaMemcpyAsync((char*)x.base + to * b, (char*)x.base + from * b, b, cudaMemcpyDeviceToDevice, st),
@@ -902,6 +924,7 @@ int dir_move(SpikeDir* D, int from, int to, cudaStream_t st) {
 void free_dir(SpikeDir* D) {
   cudaFree(D->d_a); cudaFree(D->d_lu); cudaFree(D->d_vw); cudaFree(D->d_rinv);
   cudaFree(D->d_a32); cudaFree(D->d_aff); cudaFree(D->d_lu32); cudaFree(D->d_vw32); cudaFree(D->d_rinv32);
+  cudaFree(D->d_vwlo); cudaFree(D->d_rinvlo); cudaFree(D->d_rb32); cudaFree(D->d_rblo);
   *D = SpikeDir();
 }
 
@@ -909,11 +932,13 @@ template <typename T>
 DirView<T> view(const SpikeDir& D, int spp);
 template <>
 DirView<double> view<double>(const SpikeDir& D, int spp) {
-  return DirView<double>{D.d_a, D.d_lu, D.d_vw, D.d_rinv, D.m, D.P, spp, D.band, 1.0f / (float)D.m};
+  return DirView<double>{D.d_a,  D.d_lu,  D.d_vw,  D.d_rinv, D.m,    D.P,   spp,
+                         D.band, 1.0f / (float)D.m, nullptr, nullptr,  nullptr, nullptr};
 }
 template <>
 DirView<float> view<float>(const SpikeDir& D, int spp) {
-  return DirView<float>{D.d_a32, D.d_lu32, D.d_vw32, D.d_rinv32, D.m, D.P, spp, D.band, 1.0f / (float)D.m};
+  return DirView<float>{D.d_a32, D.d_lu32, D.d_vw32, D.d_rinv32, D.m,     D.P,    spp,
+                        D.band,  1.0f / (float)D.m, D.d_vwlo, D.d_rinvlo, D.d_rb32, D.d_rblo};
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -1013,6 +1038,7 @@ static int prepare_kernels() {
   rc = cuda_check(cudaFuncSetAttribute(spike_local_staged_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024),
                   "ch: shared-memory opt-in");
+  if (!rc) rc = prepare_solve_ff();
   if (!rc) done[dev] = true;
   return rc;
 }
@@ -1051,6 +1077,10 @@ int group_init(ChGroup* g, int nx, int ny, double lx, double ly, double gamma, d
     group_free(g);
     return rc;
   }
+  if (precision == CHX_PREC_F32_REFINE && !solve_ff_fits(nx, ny, g->X.P, g->Y.P)) {
+    group_free(g);
+    return fail(CHX_EUNSUPPORTED, "ch: FP32+refine strips of %d x %d do not fit in shared memory", nx, ny);
+  }
   for (int z = 1; z < G && !rc; ++z) rc = group_move_params_gl(g, 0, z);
   if (rc) {
     group_free(g);
@@ -1065,20 +1095,20 @@ int group_init(ChGroup* g, int nx, int ny, double lx, double ly, double gamma, d
   g->off_flo = off; off = align256(off + mix);
   g->off_w = off; off = align256(off + N * esz);
   g->off_wlo = off; off = align256(off + mix);
-  g->off_y1 = off; off = align256(off + mix);
-  g->off_y2 = off; off = align256(off + mix);
-  g->off_x0 = off; off = align256(off + mix);
-  g->off_cb = off; off = align256(off + (f64 ? N * esz : 0));  // Cbar, formed by the RHS pass for the update
+  g->off_y1 = off;
+  g->off_y2 = off;
+  g->off_x0 = off; off = align256(off + mix);  // the fused solves' x0 scratch
+  g->off_cb = off; off = align256(off + N * sizeof(double));  // Cbar (FP64), formed by the RHS pass for the update
   g->off_m = off; off = align256(off + (f64 ? N * esz : 0));  // M, between the two RHS passes
-  const size_t kx = 4 * (size_t)g->X.P * ny * G, ky = 4 * (size_t)g->Y.P * nx * G;
+  // the FP64 step's boundary values and reduced solutions (the fused FP32
+  // solves keep theirs in shared memory)
+  const size_t kx = f64 ? 4 * (size_t)g->X.P * ny * G : 0, ky = f64 ? 4 * (size_t)g->Y.P * nx * G : 0;
   g->off_ybx = off; off = align256(off + kx * esz);
   g->off_tx = off; off = align256(off + kx * esz);
-  g->off_ybx2 = off; off = align256(off + (f64 ? 0 : kx * esz));
-  g->off_tx2 = off; off = align256(off + (f64 ? 0 : kx * esz));
+  g->off_ybx2 = g->off_tx2 = off;
   g->off_yby = off; off = align256(off + ky * esz);
   g->off_ty = off; off = align256(off + ky * esz);
-  g->off_yby2 = off; off = align256(off + (f64 ? 0 : ky * esz));
-  g->off_ty2 = off; off = align256(off + (f64 ? 0 : ky * esz));
+  g->off_yby2 = g->off_ty2 = off;
   g->work_bytes = off;
   return CHX_OK;
 }
@@ -1194,39 +1224,20 @@ static void step_f64(ChGroup* g, int G, double* cur, double* prev, void* work, i
         w, ty, Y, cbar, cur, prev, nx, ny, g->k2, keep_roles); }
 }
 
+// FP32 + one refinement pass (Sec. 8's float types): the double-float
+// right-hand side, then one fused launch per direction (mixed.cu), the last of
+// which forms the update.
 static void step_f32r(ChGroup* g, int G, double* cur, double* prev, void* work, int keep_roles, cudaStream_t st,
-                      Prof* prof, int* status) {
+                      Prof* prof) {
   const int nx = g->nx, ny = g->ny;
-  const size_t N = (size_t)nx * ny;
   float *fhi = wptr<float>(work, g->off_f), *flo = wptr<float>(work, g->off_flo);
   float *whi = wptr<float>(work, g->off_w), *wlo = wptr<float>(work, g->off_wlo);
-  float* y1 = wptr<float>(work, g->off_y1);
-  float* y2 = wptr<float>(work, g->off_y2);
-  float* x0 = wptr<float>(work, g->off_x0);
-  float *ybx = wptr<float>(work, g->off_ybx), *tx = wptr<float>(work, g->off_tx);
-  float *ybx2 = wptr<float>(work, g->off_ybx2), *tx2 = wptr<float>(work, g->off_tx2);
-  float *yby = wptr<float>(work, g->off_yby), *ty = wptr<float>(work, g->off_ty);
-  float *yby2 = wptr<float>(work, g->off_yby2), *ty2 = wptr<float>(work, g->off_ty2);
-  const int nsx = G * ny;
+  float* x0s = wptr<float>(work, g->off_x0);
+  double* cbar = wptr<double>(work, g->off_cb);
   const DirView<float> X = view<float>(g->X, ny), Y = view<float>(g->Y, nx);
-  const dim3 gx(ceil_div(nsx, kSolveThreads), X.P), gy(ceil_div(nx, kSolveThreads), Y.P, G);
-  const size_t kyz = 4 * (size_t)Y.P * nx;
-  // right-hand side in double-float
-  { PROF(kRhs); launch_ch_rhs_ff(cur, prev, fhi, flo, nx, ny, G, g->kff, g->d_glff, g->noise, g->nkx, g->nky, st); }
-  // x: FP32 solve of the high part, double-float residual, FP32 correction solve
-  { PROF(kLocX); launch_local<float, float>(fhi, y1, nsx, nsx, X, ybx, 0, 0, 1, status, st); }
-  { PROF(kRedX); spike_reduced_kernel<float><<<dim3(gx.x, 4 * X.P), kSolveThreads, 0, st>>>(ybx, X, tx, nsx, 0); }
-  { PROF(kRefX); launch_resid_ff(fhi, flo, y1, tx, x0, y2, nsx, nsx, nx, X, g->X.d_aff, 1, 0, 0, st); }
-  { PROF(kLoc2X); launch_local<float, float>(y2, y2, nsx, nsx, X, ybx2, 0, 0, 1, status, st); }
-  { PROF(kRed2X); spike_reduced_kernel<float><<<dim3(gx.x, 4 * X.P), kSolveThreads, 0, st>>>(ybx2, X, tx2, nsx, 0); }
-  { PROF(kFinX); launch_ch_xfinish_ff(x0, tx, y2, tx2, X, whi, wlo, nx, ny, G, st); }
-  // y
-  { PROF(kLocY); launch_local<float, float>(whi, y1, nx, nx, Y, yby, N, kyz, G, status, st); }
-  { PROF(kRedY); spike_reduced_kernel<float><<<dim3(gy.x, 4 * Y.P, G), kSolveThreads, 0, st>>>(yby, Y, ty, nx, kyz); }
-  { PROF(kRefY); launch_resid_ff(whi, wlo, y1, ty, x0, y2, nx, nx, ny, Y, g->Y.d_aff, G, N, kyz, st); }
-  { PROF(kLoc2Y); launch_local<float, float>(y2, y2, nx, nx, Y, yby2, N, kyz, G, status, st); }
-  { PROF(kRed2Y); spike_reduced_kernel<float><<<dim3(gy.x, 4 * Y.P, G), kSolveThreads, 0, st>>>(yby2, Y, ty2, nx, kyz); }
-  { PROF(kUpd); launch_ch_update_ff(x0, ty, y2, ty2, Y, cur, prev, nx, ny, G, keep_roles, st); }
+  { PROF(kRhs); launch_ch_rhs_ff(cur, prev, fhi, flo, cbar, nx, ny, G, g->kff, g->d_glff, g->noise, g->nkx, g->nky, st); }
+  { PROF(kXSolve); launch_x_solve_ff(fhi, flo, x0s, whi, wlo, nx, G * ny, ny, X, g->X.d_aff, st); }
+  { PROF(kYSolve); launch_y_solve_ff(whi, wlo, x0s, cbar, cur, prev, nx, ny, G, Y, g->Y.d_aff, keep_roles, st); }
 }
 
 int group_cook_deviates(ChGroup* g, int gact, double* rho, uint64_t seed, uint64_t sim0, uint64_t step,
@@ -1254,7 +1265,7 @@ void group_cook_clear(ChGroup* g) {
 void group_step(ChGroup* g, int gact, double* cur, double* prev, void* work, int keep_roles, cudaStream_t st,
                 Prof* prof, int* status) {
   if (g->precision == CHX_PREC_F64) step_f64(g, gact, cur, prev, work, keep_roles, st, prof, status);
-  else step_f32r(g, gact, cur, prev, work, keep_roles, st, prof, status);
+  else step_f32r(g, gact, cur, prev, work, keep_roles, st, prof);
 }
 
 void ch_plan_free(chx_ch_plan* p) {

@@ -28,6 +28,16 @@ struct SpikeDir {
   float* d_lu32 = nullptr;
   float* d_vw32 = nullptr;
   float* d_rinv32 = nullptr;
+  // the FP64 spikes and reduced inverse less their FP32 roundings (v - (float)v):
+  // with d_vw32 / d_rinv32 they form the double-float pairs of the first
+  // mixed-precision solve's cyclic coupling
+  float* d_vwlo = nullptr;
+  float* d_rinvlo = nullptr;
+  // the reduced inverse by block offset, for the fused mixed-precision solves:
+  // rb[(d*4 + u)*4P + q] = rinv[q][4*((q/4 + d) mod P) + u], d in [0, P), so
+  // that consecutive output rows q read consecutive words; high and low floats
+  float* d_rb32 = nullptr;
+  float* d_rblo = nullptr;
 };
 
 // Per-direction view handed to the kernels: slot of system j = blockIdx.z + j / spp.
@@ -39,6 +49,10 @@ struct DirView {
   const T* rinv;
   int m, P, spp, band;
   float rm;  // 1 / m, for seg_row
+  const float* vwlo;    // FP32 views: low parts of vw and rinv (nullptr for FP64)
+  const float* rinvlo;
+  const float* rb;      // FP32 views: rinv by block offset, high and low floats
+  const float* rblo;
 };
 
 // Segment s and row r of global row i for segments of m rows, without an
@@ -58,7 +72,7 @@ __device__ __forceinline__ void seg_row(int i, int m, float rm, int& s, int& r) 
 
 // Per-kernel CUDA-event timing (ch_profile).
 enum ProfSlot { kRhs, kLocX, kRedX, kRefX, kLoc2X, kRed2X, kFinX, kLocY, kRedY, kRefY, kLoc2Y, kRed2Y, kUpd, kRhsLap,
-                kSlots };
+                kXSolve, kYSolve, kSlots };
 extern const char* const kSlotName[kSlots];
 
 struct Prof {

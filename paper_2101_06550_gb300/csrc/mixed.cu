@@ -48,10 +48,11 @@ __device__ __forceinline__ ff lap_ff(const ff (*t)[LD], int y, int x, ff rho, ff
 
 // Right-hand side of Eq. 3.1 in double-float: r = k2 L'(M) - k1 (C^n - C^{n-1}),
 // M = C^3 - C - gl L'(Cbar), in one pass over 32 x 32 tiles (M formed on the
-// tile and a 1-point halo ring): whole 32-column rows per warp while staging,
-// j along the warp for the output, whose transposed stores are then coalesced
-// without a staging tile.  (The FP64 step splits this into two passes to save
-// the ring's FP64 work; here the ring costs issue slots on the FP32 pipes.)
+// tile and a 1-point halo ring): whole 32-column rows per warp, r written
+// row-major (rhi, rlo: [z][j][i]) for the fused x solve, and Cbar = 2 C^n -
+// C^{n-1} in FP64 (cbo) for the update.  (The FP64 step
+// splits this into two passes to save the ring's FP64 work; here the ring
+// costs issue slots on the FP32 pipes.)
 //
 // NOISE (Cahn-Hilliard-Cook, Sec. 7.7): the forcing term (2/3) dt eta is
 // formed in FP64 on the otherwise idle FP64 unit (one subtraction and one FMA
@@ -62,8 +63,9 @@ __global__ void __launch_bounds__(kT* kBY) ch_rhs_ff_kernel(const double* __rest
                                                             const double* __restrict__ cp, float* __restrict__ rhi,
                                                             float* __restrict__ rlo, int nx, int ny, int G, float2 rho2,
                                                             float2 kap2, const float2* __restrict__ glff, float2 k12,
-                                                            float2 k22, const double* __restrict__ dev = nullptr,
-                                                            double nkx = 0, double nky = 0) {
+                                                            float2 k22, double* __restrict__ cbo,
+                                                            const double* __restrict__ dev = nullptr, double nkx = 0,
+                                                            double nky = 0) {
   __shared__ ff s_cn[kT + 4][kT + 5];
   __shared__ ff s_cb[kT + 4][kT + 5];
   __shared__ ff s_m[kT + 2][kT + 3];
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(kT* kBY) ch_rhs_ff_kernel(const double* __rest
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < kT / kBY; ++k) {
-    const int li = threadIdx.y + k * kBY, lj = threadIdx.x;  // output (i0 + li, j0 + lj)
+    const int li = threadIdx.x, lj = threadIdx.y + k * kBY;  // output (i0 + li, j0 + lj)
     const int ly = lj + 1, lx = li + 1;
     const ff l = lap_ff<kT + 3, kIso>(s_m, ly, lx, rho, kap);
     const ff diff = ff_sub(s_cb[ly + 1][lx + 1], s_cn[ly + 1][lx + 1]);  // C^n - C^{n-1}
@@ -119,9 +121,11 @@ __global__ void __launch_bounds__(kT* kBY) ch_rhs_ff_kernel(const double* __rest
     if (NOISE) v = ff_add(v, s_nz[lj][li]);
     const int gi = i0 + li, gj = j0 + lj;
     if (gi < nx && gj < ny) {
-      const size_t q = (size_t)gi * G * ny + (size_t)z * ny + gj;
+      const size_t q = ((size_t)z * ny + gj) * nx + gi;
       rhi[q] = v.hi;
       rlo[q] = v.lo;
+      const size_t pq = (size_t)gj * nx + gi;
+      cbo[q] = fma(2.0, cn[pq], -cp[pq]);  // Cbar for the update, on the otherwise idle FP64 unit
     }
   }
 }
@@ -137,6 +141,70 @@ __device__ __forceinline__ float corr32(const float* __restrict__ vw, const floa
   return c;
 }
 
+// x0 = y - (V0 ta + V1 tb + W0 tc + W1 td) for row r of a segment, rounded once
+// to float.  Near the segment ends the four spike terms are several times
+// larger than x0 (|V| up to ~6 at a' = 1.9e4) and cancel, so a plain FP32
+// chain would leave several ulps of the terms in x0.  Here every spike is a
+// double-float pair (vw + vwlo), the high products are exact (TwoProd), the
+// running sum is carried as an unevaluated pair (TwoSum), and only the
+// low-part products (~2^-24 of the terms) are rounded in FP32.
+__device__ __forceinline__ float corr_exact(float y, const float* __restrict__ vw, const float* __restrict__ vwlo,
+                                            int m, int r, float ta, float tb, float tc, float td) {
+  const float t[4] = {ta, tb, tc, td};
+  float s = y, e = 0.f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float vh = __ldg(&vw[k * m + r]), vl = __ldg(&vwlo[k * m + r]);
+    const ff p = two_prod(vh, t[k]);
+    const ff q = two_sum(s, -p.hi);
+    s = q.hi;
+    e = e + (q.lo - fmaf(vl, t[k], p.lo));
+  }
+  return s + e;
+}
+
+// Reduced system of the first (full right-hand side) solve in double-float:
+// tau = Rinv * yb with Rinv as pairs (rinv + rinvlo) against the FP32
+// boundary values, each term's product exact (TwoProd) and the sum carried as
+// an unevaluated pair; tau is rounded once to float.  The reduced system
+// inherits the conditioning of the stiff operator (cond ~2e4 at a' = 1.9e4),
+// so an FP32 evaluation would leave ~1e-3 relative error in the boundary
+// values that a single refinement pass cannot remove.  One output per thread;
+// grid (systems / 128, 4P, Z); rows as in the FP32 reduced kernel (band).
+__global__ void __launch_bounds__(kSolveThreads) spike_reduced_ff_kernel(const float* __restrict__ yb,
+                                                                         DirView<float> D, float* __restrict__ tau,
+                                                                         int nsys, size_t ybz) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nsys) return;
+  const int P = D.P, k = 4 * P;
+  const int slot = blockIdx.z + j / D.spp;
+  yb += blockIdx.z * ybz;
+  tau += blockIdx.z * ybz;
+  const int q = blockIdx.y;
+  const size_t ro = (size_t)slot * k * k + (size_t)q * k;
+  const float* rh = D.rinv + ro;
+  const float* rl = D.rinvlo + ro;
+  const int sq = q >> 2, nb = 2 * D.band + 1 < P ? 2 * D.band + 1 : P;
+  const int s0 = nb == P ? 0 : sq - D.band;
+  float s = 0.f, e = 0.f;
+  for (int bb = 0; bb < nb; ++bb) {
+    int sb = s0 + bb;
+    sb = sb < 0 ? sb + P : (sb >= P ? sb - P : sb);
+    const int pc = 4 * sb;
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = yb[(size_t)(pc + u) * nsys + j];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const ff p = two_prod(__ldg(&rh[pc + u]), v[u]);
+      const ff t = two_sum(s, p.hi);
+      s = t.hi;
+      e = e + (t.lo + fmaf(__ldg(&rl[pc + u]), v[u], p.lo));
+    }
+  }
+  tau[(size_t)q * nsys + j] = s + e;
+}
+
 // A x0 for the ADI row (a, -4a, 1 + 6a, -4a, a): x0 + a * delta^4 x0, the fourth
 // difference formed with error-free sums.
 __device__ __forceinline__ ff adi_apply_ff(float w0, float w1, float w2, float w3, float w4, ff a) {
@@ -148,8 +216,9 @@ __device__ __forceinline__ ff adi_apply_ff(float w0, float w1, float w2, float w
 }
 
 // Refinement residual on tiles of 32 rows x 32 systems: the first FP32
-// solution x0 = y1 - spike correction is formed once per element of the tile
-// and its 2-row halo and staged in shared memory; then rho = f - A x0 in
+// solution x0 = y1 - spike correction (corr_exact: double-float spikes, exact
+// accumulation) is formed once per element of the tile and its 2-row halo and
+// staged in shared memory; then rho = f - A x0 in
 // double-float for the tile's points.  Writes rho's high part (the right-hand
 // side of the FP32 correction solve) and x0.  Element (row i, system j) at
 // [i*ld + j] (+ blockIdx.z * fz); grid (systems / 32, n / 32, Z), block 32 x 8.
@@ -171,6 +240,7 @@ __global__ void __launch_bounds__(kT* kBY) ch_resid_ff_kernel(
   const bool live = j < nsys;
   const int slot = blockIdx.z + (live ? j : 0) / D.spp;
   const float* vw = D.vw + (size_t)slot * 4 * m;
+  const float* vwlo = D.vwlo + (size_t)slot * 4 * m;
   const size_t S = (size_t)nsys;
   // a warp's rows share threadIdx.y, so the segment (and its four reduced
   // unknowns) changes warp-uniformly and rarely: load them once per segment
@@ -191,11 +261,7 @@ __global__ void __launch_bounds__(kT* kBY) ch_resid_ff_kernel(
         tc = t1[(size_t)(4 * sp + 2) * S + j];
         td = t1[(size_t)(4 * sp + 3) * S + j];
       }
-      float c = __ldg(&vw[r]) * ta;
-      c = fmaf(__ldg(&vw[m + r]), tb, c);
-      c = fmaf(__ldg(&vw[2 * m + r]), tc, c);
-      c = fmaf(__ldg(&vw[3 * m + r]), td, c);
-      v = y1[(size_t)i * ld + j] - c;
+      v = corr_exact(y1[(size_t)i * ld + j], vw, vwlo, m, r, ta, tb, tc, td);
     }
     sx[ly][threadIdx.x] = v;
   }
@@ -491,23 +557,473 @@ __global__ void __launch_bounds__(kSolveThreads) penta_solve_f32_from_f64_kernel
 #undef FAC
 }
 
+// ---------------------------------------------------------------------------
+// Fused FP32 + refinement solves of the ADI step, one launch per direction.
+//
+// A block owns S whole systems (x: S rows, y: S columns of one simulation) in
+// shared memory and runs the refinement of (I + a delta^4) w = f on them:
+//   1. FP32 segment sweeps on f_hi (partitioned solve, segments of m rows);
+//   2. the reduced (cyclic-coupling) system in double-float;
+//   3. x0 = y - spike correction with exact accumulation (corr_exact), to a
+//      global scratch x0s (L2-resident: the block rereads it shortly);
+//   4. rho = f - A x0 in double-float, back into shared memory;
+//   5. FP32 segment sweeps and FP32 reduced system on rho, then the FP32
+//      correction: delta;
+//   6. w = x0 + delta as an exact double-float pair (x), or the update
+//      C^{n+1} = 2 C^n - C^{n-1} + w in FP64 (y).
+// Between the phases the data stays on chip; the only global traffic is f,
+// the output and the x0 scratch.  Sweep phases use S * P threads (one per
+// segment of each system); the others use the whole block.
+
+// In-place sweeps of one segment on shared memory (rows ST apart):
+// y = E^{-1} f with the FP32 LU factors of the segment block; boundary values
+// y_0, y_1, y_{m-2}, y_{m-1} to yb4.  Rows are taken in blocks of B: the
+// block's values and factors are loaded first, so the serial recurrence
+// waits on one load latency per block instead of one per row.
+template <int ST>
+__device__ __forceinline__ void seg_sweep32(float* x, int m, float a, const float* __restrict__ lu, float* yb4) {
+  constexpr int B = 8;
+  const float *ra = lu, *be = lu + m, *ga = lu + 2 * m, *de = lu + 3 * m;
+  const int mb = m - m % B;
+  float g1 = 0.f, g2 = 0.f;
+  for (int r0 = 0; r0 < mb; r0 += B) {
+    float v[B], cb[B], cr[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      v[u] = x[(r0 + u) * ST];
+      cb[u] = __ldg(&be[r0 + u]);
+      cr[u] = __ldg(&ra[r0 + u]);
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      float g = fmaf(-a, g2, v[u]);
+      g = fmaf(-cb[u], g1, g) * cr[u];
+      v[u] = g;
+      g2 = g1;
+      g1 = g;
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u) x[(r0 + u) * ST] = v[u];
+  }
+  for (int r = mb; r < m; ++r) {
+    float g = fmaf(-a, g2, x[r * ST]);
+    g = fmaf(-__ldg(&be[r]), g1, g) * __ldg(&ra[r]);
+    x[r * ST] = g;
+    g2 = g1;
+    g1 = g;
+  }
+  float x1 = 0.f, x2 = 0.f;
+  for (int r = m - 1; r >= mb; --r) {
+    float v = fmaf(-__ldg(&ga[r]), x1, x[r * ST]);
+    v = fmaf(-__ldg(&de[r]), x2, v);
+    x[r * ST] = v;
+    x2 = x1;
+    x1 = v;
+  }
+  for (int r0 = mb - B; r0 >= 0; r0 -= B) {
+    float v[B], cg[B], cd[B];
+#pragma unroll
+    for (int u = B - 1; u >= 0; --u) {
+      v[u] = x[(r0 + u) * ST];
+      cg[u] = __ldg(&ga[r0 + u]);
+      cd[u] = __ldg(&de[r0 + u]);
+    }
+#pragma unroll
+    for (int u = B - 1; u >= 0; --u) {
+      float t = fmaf(-cg[u], x1, v[u]);
+      t = fmaf(-cd[u], x2, t);
+      v[u] = t;
+      x2 = x1;
+      x1 = t;
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u) x[(r0 + u) * ST] = v[u];
+  }
+  yb4[0] = x1;
+  yb4[1] = x2;
+  yb4[2] = x[(m - 2) * ST];
+  yb4[3] = x[(m - 1) * ST];
+}
+
+// Block offset of step t of the banded reduced product (t in [0, nb)):
+// offsets -band..band around the row's own segment, or all P when nb == P.
+__device__ __forceinline__ int red_offset(int t, int nb, int band, int P) {
+  if (nb == P) return t;
+  const int d = t - band;
+  return d < 0 ? d + P : d;
+}
+
+// Row q of tau = Rinv yb for one system (yb: its 4P boundary values in shared
+// memory), with Rinv by block offset (rb, rbl: see SpikeDir::d_rb32).  FF:
+// double-float (exact products, pair-carried sum, one final rounding);
+// otherwise plain FP32 FMAs.
+template <bool FF>
+__device__ __forceinline__ float reduced_row(const float* yb, int q, const float* __restrict__ rb,
+                                             const float* __restrict__ rbl, int P, int band) {
+  const int K = 4 * P, sq = q >> 2;
+  const int nb = 2 * band + 1 < P ? 2 * band + 1 : P;
+  float s = 0.f, e = 0.f;
+  for (int t = 0; t < nb; ++t) {
+    const int d = red_offset(t, nb, band, P);
+    int sb = sq + d;
+    sb = sb >= P ? sb - P : sb;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float v = yb[4 * sb + u];
+      const size_t w = (size_t)(d * 4 + u) * K + q;
+      if (FF) {
+        const ff p = two_prod(__ldg(&rb[w]), v);
+        const ff c = two_sum(s, p.hi);
+        s = c.hi;
+        e = e + (c.lo + fmaf(__ldg(&rbl[w]), v, p.lo));
+      } else {
+        s = fmaf(__ldg(&rb[w]), v, s);
+      }
+    }
+  }
+  return s + e;
+}
+
+// Plain FP32 spike correction of row r of a segment: V0 ta + V1 tb + W0 tc + W1 td.
+__device__ __forceinline__ float spikes32(const float* __restrict__ vw, int m, int r, float ta, float tb, float tc,
+                                          float td) {
+  float c = __ldg(&vw[r]) * ta;
+  c = fmaf(__ldg(&vw[m + r]), tb, c);
+  c = fmaf(__ldg(&vw[2 * m + r]), tc, c);
+  return fmaf(__ldg(&vw[3 * m + r]), td, c);
+}
+
+constexpr int kXS = 2, kXThreads = 128;  // x: rows per block, threads
+constexpr int kYThreads = 256;           // y: threads (columns per block: template)
+
+// Row e of a system -> (segment p, row r in the segment) for segments of m
+// rows: shifts when m is a power of two (lg = log2 m), else seg_row.
+struct SegMap {
+  int m, lg;
+  float rm;
+  __device__ __forceinline__ void map(int e, int& p, int& r) const {
+    if (lg >= 0) {
+      p = e >> lg;
+      r = e & (m - 1);
+    } else {
+      seg_row(e, m, rm, p, r);
+    }
+  }
+};
+
+__device__ __forceinline__ int wrap2(int j, int n) { return j < 0 ? j + n : (j >= n ? j - n : j); }
+
+// x direction.  Rows row0 .. row0 + S - 1 of the group (row = z * ny + j,
+// slot z), n = nx points each, row-major f, w and x0s.  Shared memory: the
+// rows as [s][segment][m + 1] (the pad makes the segment sweeps of a warp
+// bank-conflict free), then the boundary values and reduced solutions, then
+// the residual's round edges.
+//
+// The residual rho = f - A x0 overwrites x0 in shared memory in rounds of one
+// element per thread: a round reads x0 at its elements' neighbours, then (after
+// a barrier) writes rho.  The two elements before a round were overwritten by
+// the previous round, which saved their x0 (double-buffered edge slots), and
+// the periodic wrap reads x0 at rows 0 and 1 from slots saved by round 0.
+// f for the next round is loaded while the current one computes.
+__global__ void __launch_bounds__(kXThreads, 7) x_solve_ff_kernel(const float* __restrict__ fhi,
+                                                                  const float* __restrict__ flo,
+                                                                  float* __restrict__ x0s, float* __restrict__ whi,
+                                                                  float* __restrict__ wlo, int n, int rows, int ny,
+                                                                  DirView<float> D, const float2* __restrict__ aff,
+                                                                  int lgm) {
+  extern __shared__ float sm[];
+  const int m = D.m, P = D.P, K = 4 * P, Ls = n + P;
+  float* X = sm;
+  float* yb = X + kXS * Ls;
+  float* tau = yb + kXS * K;
+  float* eb = tau + kXS * K;  // [s][2 buffers][2]
+  float* wr = eb + kXS * 4;   // [s][2]
+  const SegMap sg{m, lgm, D.rm};
+  const int row0 = blockIdx.x * kXS;
+  const int ns = rows - row0 < kXS ? rows - row0 : kXS;
+  const int tid = threadIdx.x;
+  for (int s = 0; s < ns; ++s) {
+    const float* src = fhi + (size_t)(row0 + s) * n;
+    float* xs = X + s * Ls;
+#pragma unroll 4
+    for (int e = tid; e < n; e += kXThreads) {
+      int p, r;
+      sg.map(e, p, r);
+      xs[e + p] = src[e];
+    }
+  }
+  __syncthreads();
+  auto sweeps = [&]() {
+    for (int w = tid; w < ns * P; w += kXThreads) {
+      const int s = w / P, p = w - s * P, slot = (row0 + s) / ny;
+      seg_sweep32<1>(X + s * Ls + p * (m + 1), m, D.a[slot], D.lu + (size_t)slot * 4 * m, yb + s * K + 4 * p);
+    }
+  };
+  sweeps();
+  __syncthreads();
+  for (int o = tid; o < ns * K; o += kXThreads) {
+    const int s = o / K, q = o - s * K, slot = (row0 + s) / ny;
+    const size_t ko = (size_t)slot * K * K;
+    tau[o] = reduced_row<true>(yb + s * K, q, D.rb + ko, D.rblo + ko, P, D.band);
+  }
+  __syncthreads();
+  for (int s = 0; s < ns; ++s) {
+    const int slot = (row0 + s) / ny;
+    const float* vw = D.vw + (size_t)slot * 4 * m;
+    const float* vwl = D.vwlo + (size_t)slot * 4 * m;
+    const float* ts = tau + s * K;
+    float* xs = X + s * Ls;
+    float* dst = x0s + (size_t)(row0 + s) * n;
+#pragma unroll 2
+    for (int e = tid; e < n; e += kXThreads) {
+      int p, r;
+      sg.map(e, p, r);
+      const int pn = p + 1 == P ? 0 : p + 1, pp = p == 0 ? P - 1 : p - 1;
+      const float v = corr_exact(xs[e + p], vw, vwl, m, r, ts[4 * pn], ts[4 * pn + 1], ts[4 * pp + 2], ts[4 * pp + 3]);
+      xs[e + p] = v;
+      dst[e] = v;
+    }
+  }
+  __syncthreads();
+  const int R = (n + kXThreads - 1) / kXThreads;
+  for (int s = 0; s < ns; ++s) {
+    const int slot = (row0 + s) / ny;
+    const ff a = ffc(aff[slot]);
+    const size_t ro = (size_t)(row0 + s) * n;
+    float* xs = X + s * Ls;
+    float* ebs = eb + s * 4;
+    float* wrs = wr + s * 2;
+    float nfh = 0.f, nfl = 0.f;
+    if (tid < n) {
+      nfh = fhi[ro + tid];
+      nfl = flo[ro + tid];
+    }
+    for (int k = 0; k < R; ++k) {
+      const int k0 = k * kXThreads, e = k0 + tid;
+      const float fh = nfh, fl = nfl;
+      if (e + kXThreads < n) {
+        nfh = fhi[ro + e + kXThreads];
+        nfl = flo[ro + e + kXThreads];
+      }
+      float rho = 0.f;
+      if (e < n) {
+        float w[5];
+#pragma unroll
+        for (int d = 0; d < 5; ++d) {
+          const int j = wrap2(e + d - 2, n);
+          if (j >= k0) {
+            int p, r;
+            sg.map(j, p, r);
+            w[d] = xs[j + p];
+          } else if (j >= k0 - 2) {
+            w[d] = ebs[((k - 1) & 1) * 2 + j - (k0 - 2)];
+          } else {
+            w[d] = wrs[j];
+          }
+        }
+        if (k == 0 && e < 2) wrs[e] = w[2];
+        if (e >= k0 + kXThreads - 2) ebs[(k & 1) * 2 + e - (k0 + kXThreads - 2)] = w[2];
+        rho = ff_sub(ff{fh, fl}, adi_apply_ff(w[0], w[1], w[2], w[3], w[4], a)).hi;
+      }
+      __syncthreads();
+      if (e < n) {
+        int p, r;
+        sg.map(e, p, r);
+        xs[e + p] = rho;
+      }
+    }
+  }
+  __syncthreads();
+  sweeps();
+  __syncthreads();
+  for (int o = tid; o < ns * K; o += kXThreads) {
+    const int s = o / K, q = o - s * K, slot = (row0 + s) / ny;
+    tau[o] = reduced_row<false>(yb + s * K, q, D.rb + (size_t)slot * K * K, nullptr, P, D.band);
+  }
+  __syncthreads();
+  for (int s = 0; s < ns; ++s) {
+    const int slot = (row0 + s) / ny;
+    const float* vw = D.vw + (size_t)slot * 4 * m;
+    const float* ts = tau + s * K;
+    const float* xs = X + s * Ls;
+    const size_t ro = (size_t)(row0 + s) * n;
+#pragma unroll 4
+    for (int e = tid; e < n; e += kXThreads) {
+      int p, r;
+      sg.map(e, p, r);
+      const int pn = p + 1 == P ? 0 : p + 1, pp = p == 0 ? P - 1 : p - 1;
+      const float dl = xs[e + p] - spikes32(vw, m, r, ts[4 * pn], ts[4 * pn + 1], ts[4 * pp + 2], ts[4 * pp + 3]);
+      const ff w = two_sum(x0s[ro + e], dl);
+      whi[ro + e] = w.hi;
+      wlo[ro + e] = w.lo;
+    }
+  }
+}
+
+// y direction.  Columns col0 .. col0 + S - 1 of simulation z (blockIdx.y),
+// n = ny points each; w (the right-hand side), x0s and the fields are
+// row-major [z][j][i].  Shared memory: [segment][m rows][S columns] with a
+// segment pitch of m S + pad, pad = S - m S (mod 32): the 32 / S segments a
+// warp sweeps start S banks apart; then the boundary values and reduced
+// solutions ([s][4P + 1]: the pad spreads a warp's columns over banks) and
+// the residual's round edges.  Thread t handles column t % S and rows
+// t / S + k T / S; the residual runs in rounds of T / S rows as in the x
+// solve.  The update C^{n+1} = Cbar + v (v = x0 + delta, an exact pair; Cbar =
+// 2 C^n - C^{n-1} in FP64 from the right-hand side pass) is formed in FP64;
+// keep_roles as in ch_update_kernel.
+template <int S>
+__global__ void __launch_bounds__(kYThreads, 2) y_solve_ff_kernel(const float* __restrict__ fhi,
+                                                                  const float* __restrict__ flo,
+                                                                  float* __restrict__ x0s,
+                                                                  const double* __restrict__ cbar, double* __restrict__ cn,
+                                                                  double* __restrict__ cp, int nx, int n, DirView<float> D,
+                                                                  const float2* __restrict__ aff, int pad,
+                                                                  int keep_roles, int lgm) {
+  static_assert(kYThreads % S == 0, "threads per column");
+  constexpr int RR = kYThreads / S;  // rows per round
+  extern __shared__ float sm[];
+  const int m = D.m, P = D.P, K = 4 * P, K1 = K + 1, pitch = m * S + pad;
+  float* X = sm;
+  float* yb = X + P * pitch;
+  float* tau = yb + S * K1;
+  float* eb = tau + S * K1;  // [2 buffers][2][S]
+  float* wr = eb + 4 * S;    // [2][S]
+  const SegMap sg{m, lgm, D.rm};
+  const int z = blockIdx.y, slot = z, col0 = blockIdx.x * S;
+  const int ns = nx - col0 < S ? nx - col0 : S;
+  const size_t zo = (size_t)z * nx * n;
+  fhi += zo;
+  flo += zo;
+  x0s += zo;
+  cbar += zo;
+  cn += zo;
+  cp += zo;
+  const int tid = threadIdx.x, s = tid % S, e0 = tid / S;
+  const bool live = s < ns;
+  const int c = col0 + s;
+  auto at = [&](int e) {
+    int p, r;
+    sg.map(e, p, r);
+    return p * pad + e * S + s;
+  };
+  if (live) {
+#pragma unroll 4
+    for (int e = e0; e < n; e += RR) X[at(e)] = fhi[(size_t)e * nx + c];
+  }
+  __syncthreads();
+  const float a32 = D.a[slot];
+  const float* lu = D.lu + (size_t)slot * 4 * m;
+  auto sweeps = [&]() {
+    for (int w = tid; w < S * P; w += kYThreads) {
+      const int sw = w % S, p = w / S;
+      if (sw < ns) seg_sweep32<S>(X + p * pitch + sw, m, a32, lu, yb + sw * K1 + 4 * p);
+    }
+  };
+  sweeps();
+  __syncthreads();
+  const size_t ko = (size_t)slot * K * K;
+  for (int o = tid; o < S * K; o += kYThreads) {
+    const int so = o / K, q = o - so * K;
+    if (so < ns) tau[so * K1 + q] = reduced_row<true>(yb + so * K1, q, D.rb + ko, D.rblo + ko, P, D.band);
+  }
+  __syncthreads();
+  const float* vw = D.vw + (size_t)slot * 4 * m;
+  const float* vwl = D.vwlo + (size_t)slot * 4 * m;
+  const float* ts = tau + s * K1;
+  if (live) {
+#pragma unroll 2
+    for (int e = e0; e < n; e += RR) {
+      int p, r;
+      sg.map(e, p, r);
+      const int pn = p + 1 == P ? 0 : p + 1, pp = p == 0 ? P - 1 : p - 1;
+      const int ix = p * pad + e * S + s;
+      const float v = corr_exact(X[ix], vw, vwl, m, r, ts[4 * pn], ts[4 * pn + 1], ts[4 * pp + 2], ts[4 * pp + 3]);
+      X[ix] = v;
+      x0s[(size_t)e * nx + c] = v;
+    }
+  }
+  __syncthreads();
+  {
+    const ff a = ffc(aff[slot]);
+    const int R = (n + RR - 1) / RR;
+    float nfh = 0.f, nfl = 0.f;
+    if (live && e0 < n) {
+      nfh = fhi[(size_t)e0 * nx + c];
+      nfl = flo[(size_t)e0 * nx + c];
+    }
+    for (int k = 0; k < R; ++k) {
+      const int k0 = k * RR, e = k0 + e0;
+      const float fh = nfh, fl = nfl;
+      if (live && e + RR < n) {
+        nfh = fhi[(size_t)(e + RR) * nx + c];
+        nfl = flo[(size_t)(e + RR) * nx + c];
+      }
+      float rho = 0.f;
+      if (live && e < n) {
+        float w[5];
+#pragma unroll
+        for (int d = 0; d < 5; ++d) {
+          const int j = wrap2(e + d - 2, n);
+          if (j >= k0)
+            w[d] = X[at(j)];
+          else if (j >= k0 - 2)
+            w[d] = eb[(((k - 1) & 1) * 2 + j - (k0 - 2)) * S + s];
+          else
+            w[d] = wr[j * S + s];
+        }
+        if (k == 0 && e < 2) wr[e * S + s] = w[2];
+        if (e >= k0 + RR - 2) eb[((k & 1) * 2 + e - (k0 + RR - 2)) * S + s] = w[2];
+        rho = ff_sub(ff{fh, fl}, adi_apply_ff(w[0], w[1], w[2], w[3], w[4], a)).hi;
+      }
+      __syncthreads();
+      if (live && e < n) X[at(e)] = rho;
+    }
+  }
+  __syncthreads();
+  sweeps();
+  __syncthreads();
+  for (int o = tid; o < S * K; o += kYThreads) {
+    const int so = o / K, q = o - so * K;
+    if (so < ns) tau[so * K1 + q] = reduced_row<false>(yb + so * K1, q, D.rb + ko, nullptr, P, D.band);
+  }
+  __syncthreads();
+  if (live) {
+#pragma unroll 8
+    for (int e = e0; e < n; e += RR) {
+      int p, r;
+      sg.map(e, p, r);
+      const int pn = p + 1 == P ? 0 : p + 1, pp = p == 0 ? P - 1 : p - 1;
+      const size_t q = (size_t)e * nx + c;
+      const float dl = X[p * pad + e * S + s] - spikes32(vw, m, r, ts[4 * pn], ts[4 * pn + 1], ts[4 * pp + 2], ts[4 * pp + 3]);
+      const ff v = two_sum(x0s[q], dl);
+      const double nxt = cbar[q] + ff2d(v);
+      if (keep_roles) {
+        cp[q] = cn[q];
+        cn[q] = nxt;
+      } else {
+        cp[q] = nxt;
+      }
+    }
+  }
+}
+
 }  // namespace
 
-void launch_ch_rhs_ff(const double* cn, const double* cp, float* rhi, float* rlo, int nx, int ny, int G,
+void launch_ch_rhs_ff(const double* cn, const double* cp, float* rhi, float* rlo, double* cbar, int nx, int ny, int G,
                       const FFConst& k, const float2* glff, const double* noise, double nkx, double nky,
                       cudaStream_t st) {
   const dim3 grid(ceil_div(nx, kT), ceil_div(ny, kT), G), block(kT, kBY);
   const bool iso = k.rho.x == 1.f && k.rho.y == 0.f;
   if (noise && iso)
     ch_rhs_ff_kernel<true, true><<<grid, block, 0, st>>>(cn, cp, rhi, rlo, nx, ny, G, k.rho, k.kap, glff, k.k1, k.k2,
-                                                         noise, nkx, nky);
+                                                         cbar, noise, nkx, nky);
   else if (noise)
     ch_rhs_ff_kernel<false, true><<<grid, block, 0, st>>>(cn, cp, rhi, rlo, nx, ny, G, k.rho, k.kap, glff, k.k1, k.k2,
-                                                          noise, nkx, nky);
+                                                          cbar, noise, nkx, nky);
   else if (iso)
-    ch_rhs_ff_kernel<true><<<grid, block, 0, st>>>(cn, cp, rhi, rlo, nx, ny, G, k.rho, k.kap, glff, k.k1, k.k2);
+    ch_rhs_ff_kernel<true><<<grid, block, 0, st>>>(cn, cp, rhi, rlo, nx, ny, G, k.rho, k.kap, glff, k.k1, k.k2, cbar);
   else
-    ch_rhs_ff_kernel<false><<<grid, block, 0, st>>>(cn, cp, rhi, rlo, nx, ny, G, k.rho, k.kap, glff, k.k1, k.k2);
+    ch_rhs_ff_kernel<false><<<grid, block, 0, st>>>(cn, cp, rhi, rlo, nx, ny, G, k.rho, k.kap, glff, k.k1, k.k2, cbar);
 }
 
 void launch_resid_ff(const float* fhi, const float* flo, const float* y1, const float* t1, float* x0, float* rho,
@@ -515,6 +1031,12 @@ void launch_resid_ff(const float* fhi, const float* flo, const float* y1, const 
                      cudaStream_t st) {
   ch_resid_ff_kernel<<<dim3(ceil_div(nsys, kT), ceil_div(n, kT), Z), dim3(kT, kBY), 0, st>>>(fhi, flo, y1, t1, x0, rho,
                                                                                            ld, nsys, n, D, aff, fz, ybz);
+}
+
+void launch_reduced_ff(const float* yb, const DirView<float>& D, float* tau, int nsys, size_t ybz, int Z,
+                       cudaStream_t st) {
+  spike_reduced_ff_kernel<<<dim3(ceil_div(nsys, kSolveThreads), 4 * D.P, Z), kSolveThreads, 0, st>>>(yb, D, tau, nsys,
+                                                                                                     ybz);
 }
 
 void launch_ch_xfinish_ff(const float* y1, const float* t1, const float* y2, const float* t2, const DirView<float>& D,
@@ -536,6 +1058,69 @@ void launch_penta_refine_ff(double* x, float* work, int n, int batch, const floa
                                                                    s32[3]);
   penta_refine_ff_kernel<<<grid, blk, 0, st>>>(x, work, n, batch, fac32, coef_ff, s32[0], s32[1], s32[2],
                                                          s32[3]);
+}
+
+
+// ---------------------------------------------------------------------------
+// Fused solves: shared-memory sizes, column counts and launches.
+namespace {
+size_t x_solve_smem(int n, int P) {
+  return sizeof(float) * ((size_t)kXS * (n + P) + 2 * (size_t)kXS * 4 * P + 6 * kXS);
+}
+int y_pad(int m, int S) { return (((S - m * S) % 32) + 32) % 32; }
+size_t y_solve_smem(int n, int P, int S) {
+  const int m = n / P;
+  return sizeof(float) * ((size_t)P * (m * S + y_pad(m, S)) + 2 * (size_t)S * (4 * P + 1) + 6 * S);
+}
+int log2_exact(int m) {
+  int lg = 0;
+  while ((1 << lg) < m) ++lg;
+  return (1 << lg) == m ? lg : -1;
+}
+constexpr size_t kSmemMax = 227 * 1024;
+}  // namespace
+
+// Columns per block of the y solve: the widest strip that leaves room for two
+// blocks per SM, else the widest that fits at all.
+int y_solve_cols(int n, int P) {
+  for (int S = 8; S >= 1; S /= 2)
+    if (y_solve_smem(n, P, S) <= 100 * 1024) return S;
+  for (int S = 8; S >= 1; S /= 2)
+    if (y_solve_smem(n, P, S) <= kSmemMax) return S;
+  return 0;
+}
+
+int prepare_solve_ff() {
+  int rc = cuda_check(cudaFuncSetAttribute(x_solve_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax),
+                      "mixed: shared-memory opt-in");
+  if (!rc) rc = cuda_check(cudaFuncSetAttribute(y_solve_ff_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax), "mixed: shared-memory opt-in");
+  if (!rc) rc = cuda_check(cudaFuncSetAttribute(y_solve_ff_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax), "mixed: shared-memory opt-in");
+  if (!rc) rc = cuda_check(cudaFuncSetAttribute(y_solve_ff_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax), "mixed: shared-memory opt-in");
+  if (!rc) rc = cuda_check(cudaFuncSetAttribute(y_solve_ff_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax), "mixed: shared-memory opt-in");
+  return rc;
+}
+
+bool solve_ff_fits(int nx, int ny, int px, int py) {
+  return x_solve_smem(nx, px) <= kSmemMax && y_solve_cols(ny, py) > 0;
+}
+
+void launch_x_solve_ff(const float* fhi, const float* flo, float* x0s, float* whi, float* wlo, int nx, int rows, int ny,
+                       const DirView<float>& D, const float2* aff, cudaStream_t st) {
+  x_solve_ff_kernel<<<ceil_div(rows, kXS), kXThreads, x_solve_smem(nx, D.P), st>>>(fhi, flo, x0s, whi, wlo, nx, rows,
+                                                                                   ny, D, aff, log2_exact(D.m));
+}
+
+void launch_y_solve_ff(const float* fhi, const float* flo, float* x0s, const double* cbar, double* cn, double* cp, int nx,
+                       int ny, int G, const DirView<float>& D, const float2* aff, int keep_roles, cudaStream_t st) {
+  const int S = y_solve_cols(ny, D.P), pad = y_pad(D.m, S), lg = log2_exact(D.m);
+  const dim3 grid(ceil_div(nx, S), G);
+  const size_t sh = y_solve_smem(ny, D.P, S);
+  switch (S) {
+    case 8: y_solve_ff_kernel<8><<<grid, kYThreads, sh, st>>>(fhi, flo, x0s, cbar, cn, cp, nx, ny, D, aff, pad, keep_roles, lg); break;
+    case 4: y_solve_ff_kernel<4><<<grid, kYThreads, sh, st>>>(fhi, flo, x0s, cbar, cn, cp, nx, ny, D, aff, pad, keep_roles, lg); break;
+    case 2: y_solve_ff_kernel<2><<<grid, kYThreads, sh, st>>>(fhi, flo, x0s, cbar, cn, cp, nx, ny, D, aff, pad, keep_roles, lg); break;
+    default: y_solve_ff_kernel<1><<<grid, kYThreads, sh, st>>>(fhi, flo, x0s, cbar, cn, cp, nx, ny, D, aff, pad, keep_roles, lg); break;
+  }
 }
 
 }  // namespace chx

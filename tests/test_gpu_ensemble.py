@@ -62,6 +62,28 @@ def test_ensemble_matches_single_plans(precision, steps):
     ens.sync_status()
 
 
+def test_ensemble_f32_refine_odd_rows_straddle_slots():
+    # odd n: the fused x solve's two-row blocks straddle simulations (row 32 of
+    # slot 0 with row 0 of slot 1 at n = 33), each row solved with its own
+    # slot's operator; single segments of odd length in both directions
+    chx = _chx()
+    n, dt = 33, 1e-3
+    gammas = [0.01, 0.02, 0.005]
+    ens = chx.Ensemble(dt, chx.PREC_F32_REFINE)
+    gid = ens.group_create(n, n * DX, 0.01, 3)
+    for s, g in enumerate(gammas):
+        ens.load(gid, s, torch.from_numpy(_ic(60 + s, n)).to(DEV), None, g)
+    ens.set_active(gid, 3)
+    ens.step(4)
+    ens.sync_status()
+    for s, g in enumerate(gammas):
+        out = torch.empty(n * n, dtype=torch.float64, device=DEV)
+        ens.read(gid, s, out)
+        c0 = _ic(60 + s, n)
+        ref, _ = oracle.ch_run(c0, c0, n * DX, n * DX, g, dt, 4)
+        assert _rel(out.cpu().numpy().reshape(n, n), ref) <= 1e-6, (s, g)
+
+
 def test_ensemble_result_independent_of_the_mix_bit_exact():
     chx = _chx()
     n, dt, steps = 64, 1e-3, 9

@@ -47,3 +47,23 @@ def test_noalloc_rejects_too_many_rows_and_flags_nonfinite():
     c[2, 3] = float("nan")
     _chx.ch_diagnostics_noalloc(c, 1.0, 1.0, 0.01, out)
     assert np.all(np.isnan(out.cpu().numpy()))
+
+
+@pytest.mark.gpu
+def test_noalloc_call_takes_no_device_memory():
+    # the property the entry point exists for: after a first call (which loads
+    # its kernels and looks up the array's address), a call at another shape
+    # leaves the device's free memory unchanged
+    from paper_2101_06550_gb300 import _chx
+
+    a = torch.from_numpy(synth.field(45, 96, 160, -1, 1)).to("cuda")
+    b = torch.from_numpy(synth.field(46, 1024, 40, -1, 1)).to("cuda")
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    _chx.ch_diagnostics_noalloc(a, 1.0, 1.0, 0.01, out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    _chx.ch_diagnostics_noalloc(b, 2.0, 1.5, 0.02, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0
+    assert np.all(np.isfinite(out.cpu().numpy()))
