@@ -30,7 +30,7 @@ EXPORTS = ("chx_status_string", "chx_last_error", "chx_version", "stencil_apply_
            "ch_diagnostics_noalloc", "ch1d_plan_create", "ch1d_step", "cn1d_plan_create", "cn1d_step", "ch_noise_normals", "ch_step_noise", "ch_cook_run", "ch_observables", "ens_group_observables", "chx_coarsening_rate", "ch_profile", "ch_profile_read", "ch_profile_slot_name", "ens_create",
            "ens_group_create", "ens_group_destroy", "ens_group_set_active", "ens_group_set_cook", "ens_slot_load", "ens_slot_read",
            "ens_slot_move", "ens_step", "ens_group_step", "ens_autotune", "ens_info", "ens_bytes_used",
-           "chx_sync_status", "chx_plan_destroy")
+           "chx_fp64_fma_rate", "chx_sync_status", "chx_plan_destroy")
 
 
 class ChxError(RuntimeError):
@@ -97,6 +97,7 @@ def lib():
         "ens_info": (i, [_P, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                          ctypes.POINTER(i), ctypes.POINTER(sz)]),
         "ens_bytes_used": (sz, [_P]),
+        "chx_fp64_fma_rate": (i, [_D, _P]),
         "chx_sync_status": (i, [_P]),
         "chx_plan_destroy": (None, [_P]),
     }
@@ -362,6 +363,13 @@ def coarsening_rate(t, F):
     P = ctypes.POINTER(ctypes.c_double)
     _check(lib().chx_coarsening_rate(t.ctypes.data_as(P), F.ctypes.data_as(P), int(t.size), beta.ctypes.data_as(P)))
     return beta
+
+
+def fp64_fma_rate(stream=None) -> float:
+    """The device's FP64 fused multiply-add rate in 1e9 per second (chx_fp64_fma_rate)."""
+    v = ctypes.c_double(0.0)
+    _check(lib().chx_fp64_fma_rate(ctypes.byref(v), _stream(stream)))
+    return v.value
 
 
 def ch_diagnostics_noalloc(c, lx, ly, gamma, out, stream=None):

@@ -379,3 +379,58 @@ extern "C" void chx_plan_destroy(void* plan) {
     default: break;
   }
 }
+
+// ---------------------------------------------------------------------------
+// FP64 FMA throughput: eight independent chains per thread, so the FP64 pipe
+// rather than the FMA latency sets the rate; the result feeds a sink only if
+// it takes an impossible value, which keeps the chains live.
+namespace {
+constexpr int kRateChains = 8, kRateIters = 4096, kRateThreads = 256, kRateBlocksPerSM = 8;
+__global__ void __launch_bounds__(kRateThreads) fp64_fma_rate_kernel(double* sink, double mul, double add) {
+  double v[kRateChains];
+#pragma unroll
+  for (int k = 0; k < kRateChains; ++k) v[k] = 1e-3 * (threadIdx.x + k);
+  for (int i = 0; i < kRateIters; ++i) {
+#pragma unroll
+    for (int k = 0; k < kRateChains; ++k) v[k] = fma(v[k], mul, add);
+  }
+  double t = 0;
+#pragma unroll
+  for (int k = 0; k < kRateChains; ++k) t += v[k];
+  if (t == -1.0) *sink = t;
+}
+}  // namespace
+
+extern "C" int chx_fp64_fma_rate(double* gops_out, void* stream) {
+  if (!gops_out) return fail(CHX_EINVAL, "chx_fp64_fma_rate: null pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  int rc = cuda_check(cudaGetDevice(&dev), "chx_fp64_fma_rate: device");
+  if (!rc) rc = cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "chx_fp64_fma_rate: SMs");
+  if (rc) return rc;
+  double* sink = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if ((rc = cuda_check(cudaMalloc(&sink, sizeof(double)), "chx_fp64_fma_rate: sink")) ||
+      (rc = cuda_check(cudaEventCreate(&a), "chx_fp64_fma_rate: event")) ||
+      (rc = cuda_check(cudaEventCreate(&b), "chx_fp64_fma_rate: event"))) {
+    cudaFree(sink);
+    if (a) cudaEventDestroy(a);
+    return rc;
+  }
+  const unsigned blocks = (unsigned)sms * kRateBlocksPerSM;
+  fp64_fma_rate_kernel<<<blocks, kRateThreads, 0, st>>>(sink, 0.999999999, 1e-12);
+  cudaEventRecord(a, st);
+  fp64_fma_rate_kernel<<<blocks, kRateThreads, 0, st>>>(sink, 0.999999999, 1e-12);
+  cudaEventRecord(b, st);
+  rc = cuda_check(cudaEventSynchronize(b), "chx_fp64_fma_rate: run");
+  float ms = 0.f;
+  if (!rc) rc = cuda_check(cudaEventElapsedTime(&ms, a, b), "chx_fp64_fma_rate: timing");
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(sink);
+  if (rc) return rc;
+  const double fmas = (double)blocks * kRateThreads * kRateChains * kRateIters;
+  *gops_out = ms > 0.f ? fmas / (ms * 1e-3) / 1e9 : 0.0;
+  return CHX_OK;
+}
+

@@ -867,6 +867,39 @@ int dir_set(SpikeDir* D, int z, double a) {
   // the band is shared by the slots: keep the widest any slot has needed
   const int band = rinv_band(rinv, D->P);
   if (band > D->band) D->band = band;
+  // rows where the spikes are small enough for a plain FP32 correction: the
+  // middle interval where sum_k |vw_k(r)| <= 1, narrowed to what every slot
+  // factorised so far allows
+  {
+    const int m = D->m;
+    int lo = 0, hi = m;
+    while (lo < m) {
+      double t = 0;
+      for (int k = 0; k < 4; ++k) t += fabs(vw[(size_t)k * m + lo]);
+      if (t <= 1.0) break;
+      ++lo;
+    }
+    while (hi > lo) {
+      double t = 0;
+      for (int k = 0; k < 4; ++k) t += fabs(vw[(size_t)k * m + hi - 1]);
+      if (t <= 1.0) break;
+      --hi;
+    }
+    for (int r = lo; r < hi; ++r) {  // keep the interval contiguous
+      double t = 0;
+      for (int k = 0; k < 4; ++k) t += fabs(vw[(size_t)k * m + r]);
+      if (t > 1.0) { hi = lo; break; }
+    }
+    if (!D->pset) {
+      D->plo = lo;
+      D->phi = hi;
+      D->pset = true;
+    } else {
+      D->plo = lo > D->plo ? lo : D->plo;
+      D->phi = hi < D->phi ? hi : D->phi;
+    }
+    if (D->phi < D->plo) D->phi = D->plo;
+  }
   const size_t m4 = 4 * (size_t)D->m, kk = (size_t)16 * D->P * D->P;
   const int P = D->P, K = 4 * P;
   std::vector<double> rb(kk);
@@ -933,12 +966,12 @@ DirView<T> view(const SpikeDir& D, int spp);
 template <>
 DirView<double> view<double>(const SpikeDir& D, int spp) {
   return DirView<double>{D.d_a,  D.d_lu,  D.d_vw,  D.d_rinv, D.m,    D.P,   spp,
-                         D.band, 1.0f / (float)D.m, nullptr, nullptr,  nullptr, nullptr};
+                         D.band, 1.0f / (float)D.m, nullptr, nullptr,  nullptr, nullptr, 0, 0};
 }
 template <>
 DirView<float> view<float>(const SpikeDir& D, int spp) {
-  return DirView<float>{D.d_a32, D.d_lu32, D.d_vw32, D.d_rinv32, D.m,     D.P,    spp,
-                        D.band,  1.0f / (float)D.m, D.d_vwlo, D.d_rinvlo, D.d_rb32, D.d_rblo};
+  return DirView<float>{D.d_a32, D.d_lu32, D.d_vw32, D.d_rinv32, D.m,     D.P,    spp,     D.band,
+                        1.0f / (float)D.m, D.d_vwlo, D.d_rinvlo, D.d_rb32, D.d_rblo, D.plo, D.phi};
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }

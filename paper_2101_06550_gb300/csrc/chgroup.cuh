@@ -38,6 +38,11 @@ struct SpikeDir {
   // that consecutive output rows q read consecutive words; high and low floats
   float* d_rb32 = nullptr;
   float* d_rblo = nullptr;
+  // rows [plo, phi) of every slot's segment block where the four spikes'
+  // magnitudes sum to at most 1: the first mixed-precision solve forms x0 there
+  // with plain FP32 arithmetic (exact accumulation elsewhere)
+  int plo = 0, phi = 0;
+  bool pset = false;
 };
 
 // Per-direction view handed to the kernels: slot of system j = blockIdx.z + j / spp.
@@ -53,6 +58,7 @@ struct DirView {
   const float* rinvlo;
   const float* rb;      // FP32 views: rinv by block offset, high and low floats
   const float* rblo;
+  int plo, phi;         // FP32 views: rows of plain FP32 spike correction (SpikeDir)
 };
 
 // Segment s and row r of global row i for segments of m rows, without an

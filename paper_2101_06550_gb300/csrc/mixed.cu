@@ -163,6 +163,22 @@ __device__ __forceinline__ float corr_exact(float y, const float* __restrict__ v
   return s + e;
 }
 
+// x0 for row r of a segment: the exact form near the segment ends, where the
+// spike terms are large and cancel, and the plain FP32 chain in the rows
+// [plo, phi) where the spikes' magnitudes sum to at most 1 (there the rounding
+// of the terms is no larger than that of x0 itself).
+__device__ __forceinline__ float corr_first(float y, const float* __restrict__ vw, const float* __restrict__ vwlo,
+                                            int m, int r, int plo, int phi, float ta, float tb, float tc, float td) {
+  if (r >= plo && r < phi) {
+    float c = __ldg(&vw[r]) * ta;
+    c = fmaf(__ldg(&vw[m + r]), tb, c);
+    c = fmaf(__ldg(&vw[2 * m + r]), tc, c);
+    c = fmaf(__ldg(&vw[3 * m + r]), td, c);
+    return y - c;
+  }
+  return corr_exact(y, vw, vwlo, m, r, ta, tb, tc, td);
+}
+
 // Reduced system of the first (full right-hand side) solve in double-float:
 // tau = Rinv * yb with Rinv as pairs (rinv + rinvlo) against the FP32
 // boundary values, each term's product exact (TwoProd) and the sum carried as
@@ -694,7 +710,7 @@ __device__ __forceinline__ float spikes32(const float* __restrict__ vw, int m, i
 }
 
 constexpr int kXS = 2, kXThreads = 128;  // x: rows per block, threads
-constexpr int kYThreads = 256;           // y: threads (columns per block: template)
+constexpr int kYThreads = 512;           // y: threads (columns per block: template)
 
 // Row e of a system -> (segment p, row r in the segment) for segments of m
 // rows: shifts when m is a power of two (lg = log2 m), else seg_row.
@@ -716,15 +732,10 @@ __device__ __forceinline__ int wrap2(int j, int n) { return j < 0 ? j + n : (j >
 // x direction.  Rows row0 .. row0 + S - 1 of the group (row = z * ny + j,
 // slot z), n = nx points each, row-major f, w and x0s.  Shared memory: the
 // rows as [s][segment][m + 1] (the pad makes the segment sweeps of a warp
-// bank-conflict free), then the boundary values and reduced solutions, then
-// the residual's round edges.
-//
-// The residual rho = f - A x0 overwrites x0 in shared memory in rounds of one
-// element per thread: a round reads x0 at its elements' neighbours, then (after
-// a barrier) writes rho.  The two elements before a round were overwritten by
-// the previous round, which saved their x0 (double-buffered edge slots), and
-// the periodic wrap reads x0 at rows 0 and 1 from slots saved by round 0.
-// f for the next round is loaded while the current one computes.
+// bank-conflict free), then the boundary values and reduced solutions.  x0
+// goes to the scratch (the residual reads its neighbours there, L2-resident)
+// and the residual rho = f - A x0 replaces y in shared memory.  The memory
+// phases load a batch of elements before computing on them.
 __global__ void __launch_bounds__(kXThreads, 7) x_solve_ff_kernel(const float* __restrict__ fhi,
                                                                   const float* __restrict__ flo,
                                                                   float* __restrict__ x0s, float* __restrict__ whi,
@@ -736,8 +747,6 @@ __global__ void __launch_bounds__(kXThreads, 7) x_solve_ff_kernel(const float* _
   float* X = sm;
   float* yb = X + kXS * Ls;
   float* tau = yb + kXS * K;
-  float* eb = tau + kXS * K;  // [s][2 buffers][2]
-  float* wr = eb + kXS * 4;   // [s][2]
   const SegMap sg{m, lgm, D.rm};
   const int row0 = blockIdx.x * kXS;
   const int ns = rows - row0 < kXS ? rows - row0 : kXS;
@@ -745,21 +754,26 @@ __global__ void __launch_bounds__(kXThreads, 7) x_solve_ff_kernel(const float* _
   for (int s = 0; s < ns; ++s) {
     const float* src = fhi + (size_t)(row0 + s) * n;
     float* xs = X + s * Ls;
-#pragma unroll 4
-    for (int e = tid; e < n; e += kXThreads) {
-      int p, r;
-      sg.map(e, p, r);
-      xs[e + p] = src[e];
+    for (int e1 = tid; e1 < n; e1 += 4 * kXThreads) {
+      float v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = e1 + u * kXThreads < n ? src[e1 + u * kXThreads] : 0.f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e1 + u * kXThreads;
+        if (e < n) {
+          int p, r;
+          sg.map(e, p, r);
+          xs[e + p] = v[u];
+        }
+      }
     }
   }
   __syncthreads();
-  auto sweeps = [&]() {
-    for (int w = tid; w < ns * P; w += kXThreads) {
-      const int s = w / P, p = w - s * P, slot = (row0 + s) / ny;
-      seg_sweep32<1>(X + s * Ls + p * (m + 1), m, D.a[slot], D.lu + (size_t)slot * 4 * m, yb + s * K + 4 * p);
-    }
-  };
-  sweeps();
+  for (int w = tid; w < ns * P; w += kXThreads) {
+    const int s = w / P, p = w - s * P, slot = (row0 + s) / ny;
+    seg_sweep32<1>(X + s * Ls + p * (m + 1), m, D.a[slot], D.lu + (size_t)slot * 4 * m, yb + s * K + 4 * p);
+  }
   __syncthreads();
   for (int o = tid; o < ns * K; o += kXThreads) {
     const int s = o / K, q = o - s * K, slot = (row0 + s) / ny;
@@ -779,62 +793,49 @@ __global__ void __launch_bounds__(kXThreads, 7) x_solve_ff_kernel(const float* _
       int p, r;
       sg.map(e, p, r);
       const int pn = p + 1 == P ? 0 : p + 1, pp = p == 0 ? P - 1 : p - 1;
-      const float v = corr_exact(xs[e + p], vw, vwl, m, r, ts[4 * pn], ts[4 * pn + 1], ts[4 * pp + 2], ts[4 * pp + 3]);
-      xs[e + p] = v;
-      dst[e] = v;
+      dst[e] = corr_first(xs[e + p], vw, vwl, m, r, D.plo, D.phi, ts[4 * pn], ts[4 * pn + 1], ts[4 * pp + 2],
+                          ts[4 * pp + 3]);
     }
   }
   __syncthreads();
-  const int R = (n + kXThreads - 1) / kXThreads;
+  // rho = f - A x0 into shared memory (x0 and its neighbours from the scratch)
   for (int s = 0; s < ns; ++s) {
     const int slot = (row0 + s) / ny;
     const ff a = ffc(aff[slot]);
     const size_t ro = (size_t)(row0 + s) * n;
+    const float* x0 = x0s + ro;
     float* xs = X + s * Ls;
-    float* ebs = eb + s * 4;
-    float* wrs = wr + s * 2;
-    float nfh = 0.f, nfl = 0.f;
-    if (tid < n) {
-      nfh = fhi[ro + tid];
-      nfl = flo[ro + tid];
-    }
-    for (int k = 0; k < R; ++k) {
-      const int k0 = k * kXThreads, e = k0 + tid;
-      const float fh = nfh, fl = nfl;
-      if (e + kXThreads < n) {
-        nfh = fhi[ro + e + kXThreads];
-        nfl = flo[ro + e + kXThreads];
-      }
-      float rho = 0.f;
-      if (e < n) {
-        float w[5];
+    for (int e1 = tid; e1 < n; e1 += 2 * kXThreads) {
+      float fh[2], fl[2], w[2][5];
 #pragma unroll
-        for (int d = 0; d < 5; ++d) {
-          const int j = wrap2(e + d - 2, n);
-          if (j >= k0) {
-            int p, r;
-            sg.map(j, p, r);
-            w[d] = xs[j + p];
-          } else if (j >= k0 - 2) {
-            w[d] = ebs[((k - 1) & 1) * 2 + j - (k0 - 2)];
-          } else {
-            w[d] = wrs[j];
-          }
+      for (int u = 0; u < 2; ++u) {
+        const int e = e1 + u * kXThreads;
+        fh[u] = fl[u] = 0.f;
+#pragma unroll
+        for (int d = 0; d < 5; ++d) w[u][d] = 0.f;
+        if (e < n) {
+          fh[u] = fhi[ro + e];
+          fl[u] = flo[ro + e];
+#pragma unroll
+          for (int d = 0; d < 5; ++d) w[u][d] = x0[wrap2(e + d - 2, n)];
         }
-        if (k == 0 && e < 2) wrs[e] = w[2];
-        if (e >= k0 + kXThreads - 2) ebs[(k & 1) * 2 + e - (k0 + kXThreads - 2)] = w[2];
-        rho = ff_sub(ff{fh, fl}, adi_apply_ff(w[0], w[1], w[2], w[3], w[4], a)).hi;
       }
-      __syncthreads();
-      if (e < n) {
-        int p, r;
-        sg.map(e, p, r);
-        xs[e + p] = rho;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int e = e1 + u * kXThreads;
+        if (e < n) {
+          int p, r;
+          sg.map(e, p, r);
+          xs[e + p] = ff_sub(ff{fh[u], fl[u]}, adi_apply_ff(w[u][0], w[u][1], w[u][2], w[u][3], w[u][4], a)).hi;
+        }
       }
     }
   }
   __syncthreads();
-  sweeps();
+  for (int w = tid; w < ns * P; w += kXThreads) {
+    const int s = w / P, p = w - s * P, slot = (row0 + s) / ny;
+    seg_sweep32<1>(X + s * Ls + p * (m + 1), m, D.a[slot], D.lu + (size_t)slot * 4 * m, yb + s * K + 4 * p);
+  }
   __syncthreads();
   for (int o = tid; o < ns * K; o += kXThreads) {
     const int s = o / K, q = o - s * K, slot = (row0 + s) / ny;
@@ -847,15 +848,22 @@ __global__ void __launch_bounds__(kXThreads, 7) x_solve_ff_kernel(const float* _
     const float* ts = tau + s * K;
     const float* xs = X + s * Ls;
     const size_t ro = (size_t)(row0 + s) * n;
-#pragma unroll 4
-    for (int e = tid; e < n; e += kXThreads) {
-      int p, r;
-      sg.map(e, p, r);
-      const int pn = p + 1 == P ? 0 : p + 1, pp = p == 0 ? P - 1 : p - 1;
-      const float dl = xs[e + p] - spikes32(vw, m, r, ts[4 * pn], ts[4 * pn + 1], ts[4 * pp + 2], ts[4 * pp + 3]);
-      const ff w = two_sum(x0s[ro + e], dl);
-      whi[ro + e] = w.hi;
-      wlo[ro + e] = w.lo;
+    for (int e1 = tid; e1 < n; e1 += 4 * kXThreads) {
+      float xv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) xv[u] = e1 + u * kXThreads < n ? x0s[ro + e1 + u * kXThreads] : 0.f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e1 + u * kXThreads;
+        if (e >= n) break;
+        int p, r;
+        sg.map(e, p, r);
+        const int pn = p + 1 == P ? 0 : p + 1, pp = p == 0 ? P - 1 : p - 1;
+        const float dl = xs[e + p] - spikes32(vw, m, r, ts[4 * pn], ts[4 * pn + 1], ts[4 * pp + 2], ts[4 * pp + 3]);
+        const ff w = two_sum(xv[u], dl);
+        whi[ro + e] = w.hi;
+        wlo[ro + e] = w.lo;
+      }
     }
   }
 }
@@ -866,9 +874,8 @@ __global__ void __launch_bounds__(kXThreads, 7) x_solve_ff_kernel(const float* _
 // segment pitch of m S + pad, pad = S - m S (mod 32): the 32 / S segments a
 // warp sweeps start S banks apart; then the boundary values and reduced
 // solutions ([s][4P + 1]: the pad spreads a warp's columns over banks) and
-// the residual's round edges.  Thread t handles column t % S and rows
-// t / S + k T / S; the residual runs in rounds of T / S rows as in the x
-// solve.  The update C^{n+1} = Cbar + v (v = x0 + delta, an exact pair; Cbar =
+// Thread t handles column t % S and rows t / S + k T / S; x0 and the
+// residual as in the x solve.  The update C^{n+1} = Cbar + v (v = x0 + delta, an exact pair; Cbar =
 // 2 C^n - C^{n-1} in FP64 from the right-hand side pass) is formed in FP64;
 // keep_roles as in ch_update_kernel.
 template <int S>
@@ -880,14 +887,12 @@ __global__ void __launch_bounds__(kYThreads, 2) y_solve_ff_kernel(const float* _
                                                                   const float2* __restrict__ aff, int pad,
                                                                   int keep_roles, int lgm) {
   static_assert(kYThreads % S == 0, "threads per column");
-  constexpr int RR = kYThreads / S;  // rows per round
+  constexpr int RR = kYThreads / S;  // rows a pass of the block covers
   extern __shared__ float sm[];
   const int m = D.m, P = D.P, K = 4 * P, K1 = K + 1, pitch = m * S + pad;
   float* X = sm;
   float* yb = X + P * pitch;
   float* tau = yb + S * K1;
-  float* eb = tau + S * K1;  // [2 buffers][2][S]
-  float* wr = eb + 4 * S;    // [2][S]
   const SegMap sg{m, lgm, D.rm};
   const int z = blockIdx.y, slot = z, col0 = blockIdx.x * S;
   const int ns = nx - col0 < S ? nx - col0 : S;
@@ -906,20 +911,24 @@ __global__ void __launch_bounds__(kYThreads, 2) y_solve_ff_kernel(const float* _
     sg.map(e, p, r);
     return p * pad + e * S + s;
   };
+  constexpr int B = 4;  // elements per batch of hoisted global loads
   if (live) {
-#pragma unroll 4
-    for (int e = e0; e < n; e += RR) X[at(e)] = fhi[(size_t)e * nx + c];
+    for (int e1 = e0; e1 < n; e1 += B * RR) {
+      float v[B];
+#pragma unroll
+      for (int u = 0; u < B; ++u) v[u] = e1 + u * RR < n ? fhi[(size_t)(e1 + u * RR) * nx + c] : 0.f;
+#pragma unroll
+      for (int u = 0; u < B; ++u)
+        if (e1 + u * RR < n) X[at(e1 + u * RR)] = v[u];
+    }
   }
   __syncthreads();
   const float a32 = D.a[slot];
   const float* lu = D.lu + (size_t)slot * 4 * m;
-  auto sweeps = [&]() {
-    for (int w = tid; w < S * P; w += kYThreads) {
-      const int sw = w % S, p = w / S;
-      if (sw < ns) seg_sweep32<S>(X + p * pitch + sw, m, a32, lu, yb + sw * K1 + 4 * p);
-    }
-  };
-  sweeps();
+  for (int w = tid; w < S * P; w += kYThreads) {
+    const int sw = w % S, p = w / S;
+    if (sw < ns) seg_sweep32<S>(X + p * pitch + sw, m, a32, lu, yb + sw * K1 + 4 * p);
+  }
   __syncthreads();
   const size_t ko = (size_t)slot * K * K;
   for (int o = tid; o < S * K; o += kYThreads) {
@@ -936,51 +945,40 @@ __global__ void __launch_bounds__(kYThreads, 2) y_solve_ff_kernel(const float* _
       int p, r;
       sg.map(e, p, r);
       const int pn = p + 1 == P ? 0 : p + 1, pp = p == 0 ? P - 1 : p - 1;
-      const int ix = p * pad + e * S + s;
-      const float v = corr_exact(X[ix], vw, vwl, m, r, ts[4 * pn], ts[4 * pn + 1], ts[4 * pp + 2], ts[4 * pp + 3]);
-      X[ix] = v;
-      x0s[(size_t)e * nx + c] = v;
+      x0s[(size_t)e * nx + c] = corr_first(X[p * pad + e * S + s], vw, vwl, m, r, D.plo, D.phi, ts[4 * pn],
+                                           ts[4 * pn + 1], ts[4 * pp + 2], ts[4 * pp + 3]);
     }
   }
   __syncthreads();
-  {
+  if (live) {  // rho = f - A x0 into shared memory (x0 and its neighbours from the scratch)
     const ff a = ffc(aff[slot]);
-    const int R = (n + RR - 1) / RR;
-    float nfh = 0.f, nfl = 0.f;
-    if (live && e0 < n) {
-      nfh = fhi[(size_t)e0 * nx + c];
-      nfl = flo[(size_t)e0 * nx + c];
-    }
-    for (int k = 0; k < R; ++k) {
-      const int k0 = k * RR, e = k0 + e0;
-      const float fh = nfh, fl = nfl;
-      if (live && e + RR < n) {
-        nfh = fhi[(size_t)(e + RR) * nx + c];
-        nfl = flo[(size_t)(e + RR) * nx + c];
-      }
-      float rho = 0.f;
-      if (live && e < n) {
-        float w[5];
+    for (int e1 = e0; e1 < n; e1 += 2 * RR) {
+      float fh[2], fl[2], w[2][5];
 #pragma unroll
-        for (int d = 0; d < 5; ++d) {
-          const int j = wrap2(e + d - 2, n);
-          if (j >= k0)
-            w[d] = X[at(j)];
-          else if (j >= k0 - 2)
-            w[d] = eb[(((k - 1) & 1) * 2 + j - (k0 - 2)) * S + s];
-          else
-            w[d] = wr[j * S + s];
+      for (int u = 0; u < 2; ++u) {
+        const int e = e1 + u * RR;
+        fh[u] = fl[u] = 0.f;
+#pragma unroll
+        for (int d = 0; d < 5; ++d) w[u][d] = 0.f;
+        if (e < n) {
+          fh[u] = fhi[(size_t)e * nx + c];
+          fl[u] = flo[(size_t)e * nx + c];
+#pragma unroll
+          for (int d = 0; d < 5; ++d) w[u][d] = x0s[(size_t)wrap2(e + d - 2, n) * nx + c];
         }
-        if (k == 0 && e < 2) wr[e * S + s] = w[2];
-        if (e >= k0 + RR - 2) eb[((k & 1) * 2 + e - (k0 + RR - 2)) * S + s] = w[2];
-        rho = ff_sub(ff{fh, fl}, adi_apply_ff(w[0], w[1], w[2], w[3], w[4], a)).hi;
       }
-      __syncthreads();
-      if (live && e < n) X[at(e)] = rho;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int e = e1 + u * RR;
+        if (e < n) X[at(e)] = ff_sub(ff{fh[u], fl[u]}, adi_apply_ff(w[u][0], w[u][1], w[u][2], w[u][3], w[u][4], a)).hi;
+      }
     }
   }
   __syncthreads();
-  sweeps();
+  for (int w = tid; w < S * P; w += kYThreads) {
+    const int sw = w % S, p = w / S;
+    if (sw < ns) seg_sweep32<S>(X + p * pitch + sw, m, a32, lu, yb + sw * K1 + 4 * p);
+  }
   __syncthreads();
   for (int o = tid; o < S * K; o += kYThreads) {
     const int so = o / K, q = o - so * K;
@@ -988,20 +986,35 @@ __global__ void __launch_bounds__(kYThreads, 2) y_solve_ff_kernel(const float* _
   }
   __syncthreads();
   if (live) {
-#pragma unroll 8
-    for (int e = e0; e < n; e += RR) {
-      int p, r;
-      sg.map(e, p, r);
-      const int pn = p + 1 == P ? 0 : p + 1, pp = p == 0 ? P - 1 : p - 1;
-      const size_t q = (size_t)e * nx + c;
-      const float dl = X[p * pad + e * S + s] - spikes32(vw, m, r, ts[4 * pn], ts[4 * pn + 1], ts[4 * pp + 2], ts[4 * pp + 3]);
-      const ff v = two_sum(x0s[q], dl);
-      const double nxt = cbar[q] + ff2d(v);
-      if (keep_roles) {
-        cp[q] = cn[q];
-        cn[q] = nxt;
-      } else {
-        cp[q] = nxt;
+    for (int e1 = e0; e1 < n; e1 += B * RR) {
+      float xv[B];
+      double cv[B];
+#pragma unroll
+      for (int u = 0; u < B; ++u) {
+        const int e = e1 + u * RR;
+        xv[u] = 0.f;
+        cv[u] = 0.0;
+        if (e < n) {
+          xv[u] = x0s[(size_t)e * nx + c];
+          cv[u] = cbar[(size_t)e * nx + c];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < B; ++u) {
+        const int e = e1 + u * RR;
+        if (e >= n) break;
+        int p, r;
+        sg.map(e, p, r);
+        const int pn = p + 1 == P ? 0 : p + 1, pp = p == 0 ? P - 1 : p - 1;
+        const size_t q = (size_t)e * nx + c;
+        const float dl = X[p * pad + e * S + s] - spikes32(vw, m, r, ts[4 * pn], ts[4 * pn + 1], ts[4 * pp + 2], ts[4 * pp + 3]);
+        const double nxt = cv[u] + ff2d(two_sum(xv[u], dl));
+        if (keep_roles) {
+          cp[q] = cn[q];
+          cn[q] = nxt;
+        } else {
+          cp[q] = nxt;
+        }
       }
     }
   }
@@ -1065,12 +1078,12 @@ void launch_penta_refine_ff(double* x, float* work, int n, int batch, const floa
 // Fused solves: shared-memory sizes, column counts and launches.
 namespace {
 size_t x_solve_smem(int n, int P) {
-  return sizeof(float) * ((size_t)kXS * (n + P) + 2 * (size_t)kXS * 4 * P + 6 * kXS);
+  return sizeof(float) * ((size_t)kXS * (n + P) + 2 * (size_t)kXS * 4 * P);
 }
 int y_pad(int m, int S) { return (((S - m * S) % 32) + 32) % 32; }
 size_t y_solve_smem(int n, int P, int S) {
   const int m = n / P;
-  return sizeof(float) * ((size_t)P * (m * S + y_pad(m, S)) + 2 * (size_t)S * (4 * P + 1) + 6 * S);
+  return sizeof(float) * ((size_t)P * (m * S + y_pad(m, S)) + 2 * (size_t)S * (4 * P + 1));
 }
 int log2_exact(int m) {
   int lg = 0;
