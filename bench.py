@@ -162,6 +162,28 @@ def fp32_accuracy(dev, checkpoints=(100, 1000, 5000)):
                     "trajectory error grows with the spinodal instability (growth rate up to 1/(4 gamma))"}
 
 
+# Algorithmic bytes per grid point of one FP32 + refinement step: the scope
+# table's lower figure (48 B per point-step: the FP64 fields C^n and C^{n-1}
+# read, C^{n+1} written, and the FP32 / double-float intermediates of the two
+# sweeps).  The fused kernels move 72 B per point as designed (right-hand side
+# 16 B in + 16 B out, x solve 8 + 8, y solve 16 in + 8 out).
+FP32R_BYTES_PER_POINT = 48
+FP32R_DESIGN_BYTES_PER_POINT = 72
+
+
+def fp32_roofline(pts, ms_step, peaks):
+    """The FP32+refine step against the measured HBM copy bandwidth, on the
+    algorithmic bytes per point (the step is bound by instruction issue of its
+    double-float arithmetic; this is the fraction of the memory roofline)."""
+    peak = peaks.get("hbm_gbs") or 6800.0
+    ach = FP32R_BYTES_PER_POINT * pts / (ms_step * 1e-3) / 1e9
+    return {"kernel": "step (ch_rhs + x_solve_ff + y_solve_ff)", "bound": "hbm", "achieved": ach, "peak": peak,
+            "unit": "GB/s", "frac": ach / peak, "traffic": None,
+            "algorithmic_bytes_per_point": FP32R_BYTES_PER_POINT,
+            "design_bytes_per_point": FP32R_DESIGN_BYTES_PER_POINT,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)" if peaks.get("hbm_gbs") else "fallback"}
+
+
 def hbm_fraction(pts, ms64, ms32, peak_gbs):
     """The step's HBM traffic against the measured copy bandwidth.  The minimum a
     step must move is 24 B per point (Cn and Cn-1 in, Cn+1 out); the ncu figure
@@ -371,14 +393,15 @@ def run_chx(args, rank, world, local_rank):
     # dominant kernel of the FP64 step and its roofline (FP64-pipe bound)
     dom, (dom_ms, dom_n) = max(prof64.items(), key=lambda kv: kv[1][0])
     per_launch_ms = dom_ms / max(1, dom_n)
-    fp64_peak_gops = 1.90 * 152 * 2.070  # measured DFMA issue rate x SMs x max clock (G DP-ops/s)
+    # the FP64 pipe's rate measured in this process (DFMA throughput kernel, G DP-ops/s)
+    fp64_peak_gops = chx.fp64_fma_rate()
     if dom in KERNEL_FP64_OPS:
         ach = KERNEL_FP64_OPS[dom] * pts / (per_launch_ms * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp64_peak_gops, "unit": "G fp64-op/s",
                 "frac": ach / fp64_peak_gops, "fp64_ops_per_point": KERNEL_FP64_OPS[dom],
                 "traffic": KERNEL_TRAFFIC_BYTES.get(dom), "traffic_unit": "bytes per launch",
                 "algorithmic_bytes": KERNEL_BYTES[dom] * pts, "ms_per_launch": per_launch_ms,
-                "peak_source": "measured DFMA microbenchmark 1.90/clk/SM x 152 SMs x 2070 MHz"}
+                "peak_source": "in-run chx_fp64_fma_rate (DFMA throughput kernel, same process)"}
     else:
         roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": fp64_peak_gops, "unit": "G fp64-op/s",
                 "frac": None, "traffic": None, "ms_per_launch": per_launch_ms}
@@ -397,18 +420,7 @@ def run_chx(args, rank, world, local_rank):
         torch.cuda.empty_cache()
         extras["coarsening_stats"] = bench_coarsening_stats(dev)
         torch.cuda.empty_cache()
-        extras["serving"] = bench_serving(dev, args.serve_requests, args.serve_rate, chx.PREC_F32_REFINE)
-        torch.cuda.empty_cache()
-        # the same request mix at a sustainable arrival rate: 60% of the throughput the
-        # burst run achieved, so latency reflects service rather than queueing
-        from paper_2101_06550_gb300 import serving
-
-        mix = serving.poisson_requests(args.serve_requests, 1.0, seed=7)
-        work = np.mean([r.n * r.n * r.steps for r in mix])
-        steady = 0.6 * extras["serving"]["grid_pt_steps_per_s"] / work
-        extras["serving_steady"] = bench_serving(dev, args.serve_requests, steady, chx.PREC_F32_REFINE)
-        extras["serving_steady"]["arrival_rate_per_s"] = steady
-        torch.cuda.empty_cache()
+        extras.update(serving_suite(dev, args.serve_requests, args.serve_rate))
     clk.__exit__(None, None, None)
     cb_v, cb_t = cpu_baseline_oracle(max(1, args.cpu_steps))
     cba_v, cba_t, cba_cores = cpu_baseline_oracle_all_cores(max(1, args.cpu_steps // 4))
@@ -419,7 +431,8 @@ def run_chx(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD, "grid": [N, N], "precision": "fp64", "l2": "flushed between timed steps",
                    "replicas": world, "prewarm_s": PREWARM_S},
         "fp32_refine": {"value": world * pts * args.steps / (ms32 * 1e-3), "ms_per_step": ms32 / args.steps,
-                        "ms_per_step_profiled": ms32_prof / args.steps, "dtype": "f32+f64-residual"},
+                        "ms_per_step_profiled": ms32_prof / args.steps, "dtype": "f32+f64-residual",
+                        "roofline": fp32_roofline(pts, ms32 / args.steps, peaks)},
         "ms_per_step_profiled": ms64_prof / args.steps,
         "timing": "headline steps carry no per-kernel events; kernels_ms_per_step and the roofline come from a "
                   "second pass of the same steps with an event pair around every kernel (ms_per_step_profiled)",
@@ -623,8 +636,14 @@ def ensemble_sims(count=512, seed=11):
     return [(int(sizes[k]), float(gammas[k]), 1000 + k) for k in range(count)]
 
 
-def bench_ensemble(dev, precision, steps, warmup, count=512):
-    """One ensemble step advances all simulations; grid-pt-steps/s over `steps` steps."""
+def bench_ensemble(dev, precision, steps, warmup, count=512, long_steps=2000):
+    """The uneven ensemble (512 simulations, n in {128, ..., 1024}, FP32+refine): one
+    ensemble step advances every simulation with the packed phase launches; the
+    schedule and the segment counts are autotuned first.  Grid-pt-steps/s over
+    `steps` steps, then the run continued to `long_steps` steps with its accuracy
+    (per grid size: one FP32+refine step from the FP64 state of two simulations
+    against the FP64 step, the ensemble trajectories against FP64 single plans,
+    and mass drift), and the plain per-simulation FP64 step as the baseline."""
     import torch
 
     import paper_2101_06550_gb300 as chx
@@ -643,7 +662,14 @@ def bench_ensemble(dev, precision, steps, warmup, count=512):
             c0 = synth.uniform_torch(sd, n * n, -0.1, 0.1, device=dev)
             ens.load(gid, slot, c0, None, g)
         ens.set_active(gid, len(lst))
+    mass0 = {}
+    for n, gid in gids.items():
+        for slot in (0, 1):
+            x = torch.empty(n * n, dtype=torch.float64, device=dev)
+            ens.read(gid, slot, x)
+            mass0[(n, slot)] = (float(x.sum()), float(x.abs().sum()))
     tuned = {n: ens.autotune(gid, 2) for n, gid in gids.items()}
+    sched = ens.tune_schedule(2) if precision == chx.PREC_F32_REFINE else None
     ens.step(max(2, warmup))
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -657,26 +683,63 @@ def bench_ensemble(dev, precision, steps, warmup, count=512):
     res = {"sims": count, "grid_pts": pts, "steps": steps, "ms_per_ensemble_step": ms / steps,
            "value": pts * steps / (ms * 1e-3), "unit": "grid-pt-steps/s", "segments": tuned,
            "hbm_bytes": ens.bytes_used}
+    if sched is not None:
+        res["schedule"] = dict(ens.schedule_info(), tuned=sched,
+                               launches_per_step="3 persistent phase launches (rhs, x, y) over all groups")
+    # continue to long_steps steps, then the accuracy at that length
+    done = max(2, warmup) + steps
+    t0 = time.perf_counter()
+    ens.step(max(0, long_steps - done))
+    torch.cuda.synchronize()
+    res["long_run"] = {"steps": long_steps, "wall_s": time.perf_counter() - t0 + ms * 1e-3}
+    acc = {}
+    for n, lst in sorted(by_n.items()):
+        rows = []
+        for slot in (0, 1):
+            g, sd = lst[slot]
+            x = torch.empty(n * n, dtype=torch.float64, device=dev)
+            ens.read(gids[n], slot, x)
+            m, sa = mass0[(n, slot)]
+            p64 = chx.ChPlan(n, n, n * dx, n * dx, g, dt)
+            c = synth.uniform_torch(sd, n * n, -0.1, 0.1, device=dev)
+            pc = c.clone()
+            w = p64.alloc_work(dev)
+            p64.step(c, pc, w, long_steps)
+            # one step of each precision from the FP64 state
+            p32 = chx.ChPlan(n, n, n * dx, n * dx, g, dt, chx.PREC_F32_REFINE)
+            e, f = c.clone(), pc.clone()
+            p32.step(e, f, p32.alloc_work(dev), 1)
+            p64.step(c, pc, w, 1)
+            torch.cuda.synchronize()
+            rows.append({"slot": slot, "gamma": g,
+                         "per_step_rel_err_vs_fp64": float((e - c).abs().max() / c.abs().max()),
+                         "trajectory_rel_err_vs_fp64": float((x - pc).abs().max() / pc.abs().max()),
+                         "mass_drift_rel_to_sum_abs_c": abs(float(x.sum()) - m) / sa})
+            p64.close()
+            p32.close()
+        acc[n] = rows
+    res["accuracy_at_long_steps"] = acc
     ens.close()
     # the plain per-simulation FP64 step on the same GPU: each simulation advanced
-    # by its own ch_step plan, one after another (measured step time per size)
+    # by its own ch_step plan, one after another (measured step time per size and gamma)
     t_step = {}
     for n in sorted(by_n):
-        plan = chx.ChPlan(n, n, n * dx, n * dx, 0.01, dt)
-        c = synth.uniform_torch(1, n * n, -0.1, 0.1, device=dev)
-        pc = c.clone()
-        w = plan.alloc_work(dev)
-        plan.step(c, pc, w, 3)
-        torch.cuda.synchronize()
-        a.record()
-        plan.step(c, pc, w, 20)
-        b.record()
-        torch.cuda.synchronize()
-        t_step[n] = a.elapsed_time(b) / 20
-        plan.close()
-    serial_ms = sum(len(lst) * t_step[n] for n, lst in by_n.items())
+        for g in sorted({gg for gg, _ in by_n[n]}):
+            plan = chx.ChPlan(n, n, n * dx, n * dx, g, dt)
+            c = synth.uniform_torch(1, n * n, -0.1, 0.1, device=dev)
+            pc = c.clone()
+            w = plan.alloc_work(dev)
+            plan.step(c, pc, w, 3)
+            torch.cuda.synchronize()
+            a.record()
+            plan.step(c, pc, w, 20)
+            b.record()
+            torch.cuda.synchronize()
+            t_step[(n, g)] = a.elapsed_time(b) / 20
+            plan.close()
+    serial_ms = sum(t_step[(n, g)] for n, lst in by_n.items() for g, _ in lst)
     res["per_simulation_fp64_baseline"] = {"ms_per_ensemble_step": serial_ms, "value": pts / (serial_ms * 1e-3),
-                                           "step_ms_by_n": t_step,
+                                           "step_ms_by_n_gamma": {f"{n}/{g}": v for (n, g), v in t_step.items()},
                                            "kind": "one FP64 ch_step plan per simulation, run in turn"}
     res["speedup_vs_per_simulation_fp64"] = serial_ms / (ms / steps)
     return res
@@ -728,47 +791,83 @@ def bench_coarsening_stats(dev, sims=1024, samples=20, every=10):
     return res
 
 
-def bench_serving(dev, count, rate, precision):
+def serial_fp64_serving(dev, reqs, dx, dt, time_limit=900.0):
+    """The serial per-request FP64 baseline, run for real on the same GPU: requests
+    in arrival order, each starting at its arrival or when the previous one is
+    done, advanced alone by its own FP64 ch_step plan; latency from arrival to its
+    result on the host (host clock)."""
     import torch
 
+    import paper_2101_06550_gb300 as chx
+
+    t0 = time.perf_counter()
+    lat, work, done = [], 0, 0
+    for r in sorted(reqs, key=lambda r: r.arrival):
+        now = time.perf_counter() - t0
+        if now > time_limit:
+            break
+        if now < r.arrival:
+            time.sleep(r.arrival - now)
+        plan = chx.ChPlan(r.n, r.n, r.n * dx, r.n * dx, r.gamma, dt)
+        c = synth.uniform_torch(r.seed, r.n * r.n, -0.1, 0.1, device=dev)
+        pc = c.clone()
+        plan.step(c, pc, plan.alloc_work(dev), r.steps)
+        c.cpu()
+        lat.append(time.perf_counter() - t0 - r.arrival)
+        work += r.n * r.n * r.steps
+        done += 1
+        plan.close()
+    makespan = time.perf_counter() - t0
+    lat = np.array(lat)
+    return {"completed": done, "submitted": len(reqs), "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()), "makespan_s": makespan,
+            "grid_pt_steps_per_s": work / makespan,
+            "kind": "measured: one FP64 ch_step plan per request, FIFO over the same arrivals, host-clock latency"}
+
+
+SERVE_FILL_POINTS = 2 * 2048 * 2048  # admitted grid points that fill the GPU
+SERVE_TICK_MS = 20.0
+
+
+def bench_serving(dev, count, rate, precision, serial=True):
+    """Poisson arrivals of the request mix (n log-uniform in [128, 2048], 500-5000
+    steps, gamma in [0.005, 0.02]) served by continuous batching; latency
+    percentiles, throughput, and the serial FP64 baseline on the same arrivals."""
     import paper_2101_06550_gb300 as chx
     from paper_2101_06550_gb300 import serving
 
     dx, dt = 2 * np.pi / 256, 1e-3
     reqs = serving.poisson_requests(count, rate, seed=7)
     srv = serving.Server(dt, dx, precision=precision, hbm_budget=96 << 30, capacity=16, chunk=100,
-                         keep_results=False)
+                         keep_results=False, fill_points=SERVE_FILL_POINTS, tick_ms=SERVE_TICK_MS)
     stats = serving.serve(reqs, srv, time_limit=900)
     offered = sum(r.n * r.n * r.steps for r in reqs) / max(reqs[-1].arrival, 1e-9)
     stats["offered_grid_pt_steps_per_s"] = offered
+    stats["arrival_rate_per_s"] = rate
     stats["precision"] = "f32+f64-residual" if precision == chx.PREC_F32_REFINE else "f64"
-    # serial per-request FP64 baseline on the same GPU: measured FP64 step time per
-    # grid size, a FIFO single-server queue over the same arrivals
-    t_step = {}
-    for n in sorted({r.n for r in reqs}):
-        plan = chx.ChPlan(n, n, n * dx, n * dx, 0.01, dt)
-        c = synth.uniform_torch(1, n * n, -0.1, 0.1, device=dev)
-        pc = c.clone()
-        w = plan.alloc_work(dev)
-        plan.step(c, pc, w, 3)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        plan.step(c, pc, w, 20)
-        b.record()
-        torch.cuda.synchronize()
-        t_step[n] = a.elapsed_time(b) / 20e3
-        plan.close()
-    t, lat = 0.0, []
-    for r in sorted(reqs, key=lambda r: r.arrival):
-        t = max(t, r.arrival) + r.steps * t_step[r.n]
-        lat.append(t - r.arrival)
-    lat = np.array(lat)
-    stats["serial_fp64_baseline"] = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-                                     "makespan_s": t,
-                                     "grid_pt_steps_per_s": sum(r.n * r.n * r.steps for r in reqs) / t,
-                                     "kind": "FIFO queue over measured per-size FP64 ch_step times"}
+    stats["admission"] = {"fill_points": SERVE_FILL_POINTS, "tick_ms": SERVE_TICK_MS, "capacity_per_size": 16}
+    srv.ens.close()
+    if serial:
+        stats["serial_fp64_baseline"] = serial_fp64_serving(dev, reqs, dx, dt)
     return stats
+
+
+def serving_suite(dev, count, rate):
+    """The burst at the given arrival rate, then the same mix at a sustainable rate
+    (60% of the throughput the burst achieved), each beside the serial baseline."""
+    import paper_2101_06550_gb300 as chx
+    from paper_2101_06550_gb300 import serving
+
+    import torch
+
+    out = {"serving": bench_serving(dev, count, rate, chx.PREC_F32_REFINE)}
+    torch.cuda.empty_cache()
+    mix = serving.poisson_requests(count, 1.0, seed=7)
+    work = np.mean([r.n * r.n * r.steps for r in mix])
+    steady = 0.6 * out["serving"]["grid_pt_steps_per_s"] / work
+    out["serving_steady"] = bench_serving(dev, count, steady, chx.PREC_F32_REFINE)
+    torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -780,7 +879,9 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=12)
     ap.add_argument("--no-extras", action="store_true", help="skip the solver / ensemble / serving sub-benchmarks")
     ap.add_argument("--ens-steps", type=int, default=20)
-    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-requests", type=int, default=120)
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run only the serving benchmarks (burst and sustainable rate) and print their JSON")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -788,6 +889,14 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.serve_only:
+        import torch
+
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        out = serving_suite(dev, args.serve_requests, args.serve_rate)
+        if rank == 0:
+            print(json.dumps({"serving_only": True, "requests": args.serve_requests, **out}))
     else:
         run_chx(args, rank, world, local_rank)
 

@@ -370,6 +370,24 @@ int ens_step(chx_ens* ens, int nsteps, void* stream);
 int ens_group_step(chx_ens* ens, int group_id, int nsteps, void* stream);
 int ens_autotune(chx_ens* ens, int group_id, int trial, int* px_out, int* py_out, void* stream);
 int ens_info(chx_ens* ens, int group_id, int* n, int* capacity, int* active, int* px, int* py, size_t* bytes);
+/* FP32 + refinement ensembles step every group with three launches per step,
+ * one per phase (right-hand side, x solves, y solves with the update): each a
+ * persistent grid whose blocks stride over the work items of all groups, packed
+ * group after group (the thesis's batches of uneven 2D simulations, Sec. 7.3.2,
+ * with one LHS per distinct matrix, Sec. 8); every group keeps tiles of its own
+ * shape.  ens_tune_schedule times `trial` steps for each candidate schedule --
+ * group order (0: most work per item first, 1: least first), points per work
+ * item of the solves (2048, 4096 or 8192; each group's x rows and y columns per
+ * item follow) and the y phase's blocks per SM -- keeps the fastest, and
+ * reports the order, the points per item and the blocks of the three phases
+ * (blocks_out: 3 ints; any output may be NULL).
+ * It saves C^{n-1} of the active slots and puts it back, so no simulation
+ * changes; the saved copy counts against the HBM budget (CHX_ENOMEM).
+ * ens_schedule_info reports the current layout (items_out, blocks_out: 3 ints).
+ * Both return CHX_EUNSUPPORTED for FP64 ensembles and, for the tuner, when no
+ * group is active or more than 256 groups are. */
+int ens_tune_schedule(chx_ens* ens, int trial, int* order_out, int* target_out, int* blocks_out, void* stream);
+int ens_schedule_info(chx_ens* ens, int* items_out, int* blocks_out, int* target_out, int* order_out);
 size_t ens_bytes_used(const chx_ens* ens);
 
 /*

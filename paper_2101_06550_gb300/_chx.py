@@ -29,7 +29,8 @@ EXPORTS = ("chx_status_string", "chx_last_error", "chx_version", "stencil_apply_
            "tri_cyclic_solve_batched", "ch_plan_create", "ch_work_bytes", "ch_step", "ch_step_host", "ch_diagnostics",
            "ch_diagnostics_noalloc", "ch1d_plan_create", "ch1d_step", "cn1d_plan_create", "cn1d_step", "ch_noise_normals", "ch_step_noise", "ch_cook_run", "ch_observables", "ens_group_observables", "chx_coarsening_rate", "ch_profile", "ch_profile_read", "ch_profile_slot_name", "ens_create",
            "ens_group_create", "ens_group_destroy", "ens_group_set_active", "ens_group_set_cook", "ens_slot_load", "ens_slot_read",
-           "ens_slot_move", "ens_step", "ens_group_step", "ens_autotune", "ens_info", "ens_bytes_used",
+           "ens_slot_move", "ens_step", "ens_group_step", "ens_autotune", "ens_info", "ens_tune_schedule",
+           "ens_schedule_info", "ens_bytes_used",
            "chx_fp64_fma_rate", "chx_sync_status", "chx_plan_destroy")
 
 
@@ -94,6 +95,8 @@ def lib():
         "ens_step": (i, [_P, i, _P]),
         "ens_group_step": (i, [_P, i, i, _P]),
         "ens_autotune": (i, [_P, i, i, ctypes.POINTER(i), ctypes.POINTER(i), _P]),
+        "ens_tune_schedule": (i, [_P, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), _P]),
+        "ens_schedule_info": (i, [_P, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
         "ens_info": (i, [_P, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                          ctypes.POINTER(i), ctypes.POINTER(sz)]),
         "ens_bytes_used": (sz, [_P]),
@@ -492,6 +495,21 @@ class Ensemble(_Plan):
         px, py = ctypes.c_int(), ctypes.c_int()
         _check(lib().ens_autotune(self._handle, gid, int(trial), ctypes.byref(px), ctypes.byref(py), _stream(stream)))
         return px.value, py.value
+
+    def tune_schedule(self, trial=3, stream=None):
+        """Pick the packed FP32 schedule (group order, points per work item, y blocks per SM) by timing."""
+        order, target = ctypes.c_int(), ctypes.c_int()
+        blocks = (ctypes.c_int * 3)()
+        _check(lib().ens_tune_schedule(self._handle, int(trial), ctypes.byref(order), ctypes.byref(target), blocks,
+                                       _stream(stream)))
+        return {"order": order.value, "points_per_item": target.value, "blocks": list(blocks)}
+
+    def schedule_info(self):
+        """Work items and blocks of the packed FP32 step's three phases, points per item and group order."""
+        items, blocks = (ctypes.c_int * 3)(), (ctypes.c_int * 3)()
+        target, order = ctypes.c_int(), ctypes.c_int()
+        _check(lib().ens_schedule_info(self._handle, items, blocks, ctypes.byref(target), ctypes.byref(order)))
+        return {"items": list(items), "blocks": list(blocks), "points_per_item": target.value, "order": order.value}
 
     def info(self, gid):
         v = [ctypes.c_int() for _ in range(5)]

@@ -30,7 +30,6 @@
 #include <utility>
 #include <vector>
 
-#include "bulk.cuh"
 #include "chgroup.cuh"
 #include "ff.cuh"
 #include "noise.cuh"
@@ -470,103 +469,6 @@ __global__ void __launch_bounds__(kSolveThreads) spike_local_even_kernel(const T
   yb[(size_t)(4 * s + 3) * S + j] = ylast;
 }
 
-// The same sweeps with the segment tile staged in shared memory: one thread
-// issues bulk asynchronous copies of the m rows (32 systems each) onto an
-// mbarrier, so the whole tile is in flight at once, and the forward
-// intermediate stays on chip instead of making a round trip through HBM.
-// Requires nsys % 32 == 0 and 16-byte aligned rows (checked by the host).
-template <typename TC>
-__global__ void __launch_bounds__(32) spike_local_staged_kernel(const TC* f, TC* y, int ld, int nsys, DirView<TC> D,
-                                                                TC* __restrict__ yb, size_t fz, size_t ybz,
-                                                                int* status) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ uint64_t bar;
-  TC* tile = reinterpret_cast<TC*>(smem_raw);
-  const int t = threadIdx.x, s = blockIdx.y, m = D.m;
-  const int j0 = blockIdx.x * 32, j = j0 + t;
-  f += blockIdx.z * fz;
-  y += blockIdx.z * fz;
-  yb += blockIdx.z * ybz;
-  const size_t L = (size_t)ld;
-  if (t == 0) mbar_init(&bar, 1);
-  __syncthreads();
-  if (t == 0) bulk_tile_load(tile, (const char*)(f + (size_t)s * m * L + j0), L * sizeof(TC), 32 * sizeof(TC), m, &bar);
-  if (!mbar_wait_bounded(&bar, 0, status)) {
-    mbar_wait_bounded(&bar, 0, status);  // let copies still in flight land before the CTA exits
-    return;
-  }
-  const int slot = blockIdx.z + j / D.spp;
-  const TC a = D.a[slot];
-  const TC* lu = D.lu + (size_t)slot * 4 * m;
-  const TC *ra = lu, *be = lu + m, *ga = lu + 2 * m, *de = lu + 3 * m;
-  TC g1 = 0, g2 = 0;
-#pragma unroll 8
-  for (int r = 0; r < m; ++r) {
-    TC g = fma(-a, g2, tile[r * 32 + t]);
-    g = fma(-__ldg(&be[r]), g1, g) * __ldg(&ra[r]);
-    tile[r * 32 + t] = g;
-    g2 = g1;
-    g1 = g;
-  }
-  TC x1 = 0, x2 = 0, ylast = 0, ylast2 = 0;
-  TC* py = y + (size_t)s * m * L + j;
-#pragma unroll 8
-  for (int r = m - 1; r >= 0; --r) {
-    TC v = fma(-__ldg(&ga[r]), x1, tile[r * 32 + t]);
-    v = fma(-__ldg(&de[r]), x2, v);
-    py[(size_t)r * L] = v;
-    if (r == m - 1) ylast = v;
-    if (r == m - 2) ylast2 = v;
-    x2 = x1;
-    x1 = v;
-  }
-  const size_t S = (size_t)nsys;
-  yb[(size_t)(4 * s + 0) * S + j] = x1;
-  yb[(size_t)(4 * s + 1) * S + j] = x2;
-  yb[(size_t)(4 * s + 2) * S + j] = ylast2;
-  yb[(size_t)(4 * s + 3) * S + j] = ylast;
-}
-
-// Reduced system: tau = Rinv * yb for every system (4P unknowns each), one
-// output per thread.  Rinv's 4x4 blocks decay with the circular distance
-// between segments; only distances <= D.band are kept (the dropped blocks are
-// below half an FP64 ulp of the largest, set at plan time), so output q reads the boundary
-// values of segments s_q - band .. s_q + band, 8 loads at a time.
-template <typename TC>
-__global__ void __launch_bounds__(kSolveThreads) spike_reduced_kernel(const TC* __restrict__ yb, DirView<TC> D,
-                                                                      TC* __restrict__ tau, int nsys, size_t ybz) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= nsys) return;
-  const int P = D.P, k = 4 * P;
-  const int slot = blockIdx.z + j / D.spp;
-  yb += blockIdx.z * ybz;
-  tau += blockIdx.z * ybz;
-  const int q = blockIdx.y;
-  const TC* row = D.rinv + (size_t)slot * k * k + (size_t)q * k;
-  const int sq = q >> 2, nb = 2 * D.band + 1 < P ? 2 * D.band + 1 : P;
-  const int s0 = nb == P ? 0 : sq - D.band;
-  TC acc0 = 0, acc1 = 0;
-  for (int bb = 0; bb < nb; bb += 2) {
-    TC v[8];
-    int pc[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      int sb = s0 + bb + h;
-      sb = sb < 0 ? sb + P : (sb >= P ? sb - P : sb);
-      pc[h] = 4 * sb;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) v[4 * h + u] = (bb + h < nb) ? yb[(size_t)(pc[h] + u) * nsys + j] : TC(0);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) acc0 = fma(__ldg(&row[pc[0] + u]), v[u], acc0);
-    if (bb + 1 < nb) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) acc1 = fma(__ldg(&row[pc[1] + u]), v[4 + u], acc1);
-    }
-  }
-  tau[(size_t)q * nsys + j] = acc0 + acc1;
-}
-
 // The same reduced solve with R (1, 2 or 4) rows of one segment block per
 // thread: each boundary value loaded (from L2) serves R dot products instead of
 // one.  Grid (systems / blk, P * 4 / R, Z).  The outputs are multiplied by
@@ -739,14 +641,18 @@ __global__ void ch_diag_final_kernel(const double* __restrict__ part, int nb, do
 
 // ---------------------------------------------------------------------------
 // Host helpers.
-int default_segments(int n, int nsys) {
+int default_segments(int n, int nsys, int precision) {
   // The dense reduced solve costs 16 P^2 / n operations per point, so P stays
-  // near sqrt(n / 8) while aiming at about 32k independent sweeps.
+  // near sqrt(n / 8).  FP64 (one thread per segment of every system, streamed
+  // from HBM) aims at about 32k independent sweeps and takes fewer segments
+  // when there are many systems.  The fused FP32 solves sweep the segments of
+  // a block's few systems in shared memory, so their parallelism is x rows (or
+  // y columns) per block times P: they keep P near sqrt(n / 8) for any batch.
   int pmax = (int)floor(sqrt(n / 8.0));
   if (pmax < 1) pmax = 1;
   int want = (32768 + nsys - 1) / nsys;
   if (want < 1) want = 1;
-  int lim = pmax < want ? pmax : want;
+  int lim = (pmax < want || precision == CHX_PREC_F32_REFINE) ? pmax : want;
   for (int P = lim; P >= 1; --P)
     if (n % P == 0 && n / P >= 8) return P;
   return 1;
@@ -986,6 +892,42 @@ T* wptr(void* work, size_t off) {
 // ---------------------------------------------------------------------------
 namespace chx {
 
+FFStep ff_step_params(const ChGroup* g, int G, double* cur, double* prev, void* work, int target) {
+  FFStep P{};
+  P.nx = g->nx;
+  P.ny = g->ny;
+  P.G = G;
+  P.iso = g->kff.rho.x == 1.f && g->kff.rho.y == 0.f;
+  P.tx = (int)ceil_div(g->nx, kT);
+  P.ty = (int)ceil_div(g->ny, kT);
+  P.X = view<float>(g->X, g->ny);
+  P.Y = view<float>(g->Y, g->nx);
+  P.xs = x_solve_rows(g->nx, g->X.P, target);
+  P.ysc = y_solve_cols(g->ny, g->Y.P, target);
+  P.lgys = log2_exact(P.ysc);
+  P.ypad = y_solve_pad(g->Y.m, P.ysc);
+  P.lgx = log2_exact(g->X.m);
+  P.lgy = log2_exact(g->Y.m);
+  P.k = g->kff;
+  P.glff = g->d_glff;
+  P.noise = g->noise;
+  P.nkx = g->nkx;
+  P.nky = g->nky;
+  P.affX = g->X.d_aff;
+  P.affY = g->Y.d_aff;
+  P.st[0] = cur;
+  P.st[1] = prev;
+  P.cur0 = 0;
+  P.fhi = wptr<float>(work, g->off_f);
+  P.flo = wptr<float>(work, g->off_flo);
+  P.whi = wptr<float>(work, g->off_w);
+  P.wlo = wptr<float>(work, g->off_wlo);
+  P.x0s = wptr<float>(work, g->off_x0);
+  P.cbar = wptr<double>(work, g->off_cb);
+  return P;
+}
+
+
 cudaEvent_t Prof::get() {
   if (!pool.empty()) {
     cudaEvent_t e = pool.back();
@@ -1045,9 +987,8 @@ ProfScope::~ProfScope() {
 #define PROF(slot) ProfScope prof_scope_##slot(prof, slot, st)
 
 std::vector<int> segment_candidates(int n, int nsys, int precision) {
-  (void)precision;
   std::vector<int> out;
-  const int d = default_segments(n, nsys);
+  const int d = default_segments(n, nsys, precision);
   out.push_back(d);
   for (int P = 1; P <= n / 8 && P <= 64; ++P)
     if (n % P == 0 && P != d && (P == d / 2 || P == 2 * d || P == d / 4 || P == 4 * d)) out.push_back(P);
@@ -1068,10 +1009,7 @@ static int prepare_kernels() {
   int rc = cuda_check(cudaGetDevice(&dev), "ch: cudaGetDevice");
   if (rc || dev < 0 || dev >= 64 || done[dev]) return rc;
   balanced_block(0);  // reads the SM count now, outside any stream capture
-  rc = cuda_check(cudaFuncSetAttribute(spike_local_staged_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       200 * 1024),
-                  "ch: shared-memory opt-in");
-  if (!rc) rc = prepare_solve_ff();
+  rc = prepare_solve_ff();
   if (!rc) done[dev] = true;
   return rc;
 }
@@ -1103,8 +1041,8 @@ int group_init(ChGroup* g, int nx, int ny, double lx, double ly, double gamma, d
   g->kff.k1 = split_ff(g->k1);
   g->kff.k2 = split_ff(g->k2);
   int rc;
-  if ((rc = dir_alloc(&g->X, nx, px ? px : default_segments(nx, G * ny), G)) ||
-      (rc = dir_alloc(&g->Y, ny, py ? py : default_segments(ny, nx * G), G)) || (rc = dev_alloc(&g->d_gl, G)) ||
+  if ((rc = dir_alloc(&g->X, nx, px ? px : default_segments(nx, G * ny, precision), G)) ||
+      (rc = dir_alloc(&g->Y, ny, py ? py : default_segments(ny, nx * G, precision), G)) || (rc = dev_alloc(&g->d_gl, G)) ||
       (rc = dev_alloc(&g->d_glff, G)) || (rc = group_set_gamma(g, 0, gamma)) || (rc = dir_replicate(&g->X)) ||
       (rc = dir_replicate(&g->Y))) {
     group_free(g);
@@ -1113,6 +1051,13 @@ int group_init(ChGroup* g, int nx, int ny, double lx, double ly, double gamma, d
   if (precision == CHX_PREC_F32_REFINE && !solve_ff_fits(nx, ny, g->X.P, g->Y.P)) {
     group_free(g);
     return fail(CHX_EUNSUPPORTED, "ch: FP32+refine strips of %d x %d do not fit in shared memory", nx, ny);
+  }
+  {
+    auto dir_bytes = [&](const SpikeDir& D) {
+      const size_t m4 = 4 * (size_t)D.m, kk = (size_t)16 * D.P * D.P;
+      return (size_t)G * (8 + 4 + 8 + m4 * (8 + 8 + 4 + 4 + 4) + kk * (8 + 4 + 4 + 4 + 4));
+    };
+    g->factor_bytes = dir_bytes(g->X) + dir_bytes(g->Y) + (size_t)G * (sizeof(double) + sizeof(float2));
   }
   for (int z = 1; z < G && !rc; ++z) rc = group_move_params_gl(g, 0, z);
   if (rc) {
@@ -1180,29 +1125,17 @@ void group_free(ChGroup* g) {
   g->d_glff = nullptr;
 }
 
-// Segment-local sweeps.  FP32: the shared-memory staged kernel when the tile
-// rows are 16-byte aligned and the systems fill whole warps (measured 20 us vs
-// 24 us at 2048^2).  FP64: the register-prefetch kernel, which keeps the FP64
-// pipe busier (51 us vs 82 us staged: the serial chain per system, not load
-// latency, limits these sweeps).
-template <typename TIn, typename TC>
-static void launch_local(const TIn* f, TC* y, int ld, int nsys, const DirView<TC>& D, TC* yb, size_t fz, size_t ybz,
-                         int Z, int* status, cudaStream_t st) {
-  const size_t tile = (size_t)D.m * 32 * sizeof(TC);
-  const bool aligned = std::is_same<TIn, TC>::value && sizeof(TC) == 4 && nsys % 32 == 0 &&
-                       ((size_t)ld * sizeof(TC)) % 16 == 0 &&
-                       (fz * sizeof(TC)) % 16 == 0 && ((uintptr_t)f & 15) == 0 && tile <= 200 * 1024;
-  if (aligned) {
-    spike_local_staged_kernel<TC><<<dim3(nsys / 32, D.P, Z), 32, tile, st>>>((const TC*)f, y, ld, nsys, D, yb, fz, ybz,
-                                                                           status);
-  } else {
-    const unsigned blk = balanced_block((size_t)nsys * D.P * Z);
-    const dim3 grid(ceil_div(nsys, blk), D.P, Z);
-    if (std::is_same<TIn, TC>::value && sizeof(TC) == 8 && D.m % 16 == 0)
-      spike_local_even_kernel<TC><<<grid, blk, 0, st>>>((const TC*)f, y, ld, nsys, D, yb, fz, ybz);
-    else
-      spike_local_kernel<TIn, TC><<<grid, blk, 0, st>>>(f, y, ld, nsys, D, yb, fz, ybz);
-  }
+// Segment-local FP64 sweeps: the register-prefetch kernel (the serial chain
+// per system, not load latency, limits these sweeps; a shared-memory staged
+// variant measured 82 us against 51 us at 2048^2).
+static void launch_local(const double* f, double* y, int ld, int nsys, const DirView<double>& D, double* yb, size_t fz,
+                         size_t ybz, int Z, cudaStream_t st) {
+  const unsigned blk = balanced_block((size_t)nsys * D.P * Z);
+  const dim3 grid(ceil_div(nsys, blk), D.P, Z);
+  if (D.m % 16 == 0)
+    spike_local_even_kernel<double><<<grid, blk, 0, st>>>(f, y, ld, nsys, D, yb, fz, ybz);
+  else
+    spike_local_kernel<double, double><<<grid, blk, 0, st>>>(f, y, ld, nsys, D, yb, fz, ybz);
 }
 
 // FP64 reduced solves: kReducedRows rows per thread, in single-warp blocks when
@@ -1248,10 +1181,10 @@ static void step_f64(ChGroup* g, int G, double* cur, double* prev, void* work, i
     else
       ch_rhs_r_kernel<double, double><<<tgrid, rblock, 0, st>>>(mf, cur, cbar, f, nx, ny, G, g->rho, g->kap, kd);
   }
-  { PROF(kLocX); launch_local<double, double>(f, f, nsx, nsx, X, ybx, 0, 0, 1, status, st); }
+  { PROF(kLocX); launch_local(f, f, nsx, nsx, X, ybx, 0, 0, 1, st); }
   { PROF(kRedX); launch_reduced<double>(ybx, X, tx, nsx, 0, 1, 1.0, st); }
   { PROF(kFinX); ch_xfinish_kernel<double, double><<<tgrid, tblock, 0, st>>>(f, tx, X, w, nx, ny, G); }
-  { PROF(kLocY); launch_local<double, double>(w, w, nx, nx, Y, yby, N, kyz, G, status, st); }
+  { PROF(kLocY); launch_local(w, w, nx, nx, Y, yby, N, kyz, G, st); }
   { PROF(kRedY); launch_reduced<double>(yby, Y, ty, nx, kyz, G, g->k2, st); }
   { PROF(kUpd); ch_update_kernel<double><<<dim3(ceil_div(nx, kSolveThreads), ny, G), kSolveThreads, 0, st>>>(
         w, ty, Y, cbar, cur, prev, nx, ny, g->k2, keep_roles); }
@@ -1262,15 +1195,7 @@ static void step_f64(ChGroup* g, int G, double* cur, double* prev, void* work, i
 // which forms the update.
 static void step_f32r(ChGroup* g, int G, double* cur, double* prev, void* work, int keep_roles, cudaStream_t st,
                       Prof* prof) {
-  const int nx = g->nx, ny = g->ny;
-  float *fhi = wptr<float>(work, g->off_f), *flo = wptr<float>(work, g->off_flo);
-  float *whi = wptr<float>(work, g->off_w), *wlo = wptr<float>(work, g->off_wlo);
-  float* x0s = wptr<float>(work, g->off_x0);
-  double* cbar = wptr<double>(work, g->off_cb);
-  const DirView<float> X = view<float>(g->X, ny), Y = view<float>(g->Y, nx);
-  { PROF(kRhs); launch_ch_rhs_ff(cur, prev, fhi, flo, cbar, nx, ny, G, g->kff, g->d_glff, g->noise, g->nkx, g->nky, st); }
-  { PROF(kXSolve); launch_x_solve_ff(fhi, flo, x0s, whi, wlo, nx, G * ny, ny, X, g->X.d_aff, st); }
-  { PROF(kYSolve); launch_y_solve_ff(whi, wlo, x0s, cbar, cur, prev, nx, ny, G, Y, g->Y.d_aff, keep_roles, st); }
+  launch_step_ff(ff_step_params(g, G, cur, prev, work), keep_roles, prof, st);
 }
 
 int group_cook_deviates(ChGroup* g, int gact, double* rho, uint64_t seed, uint64_t sim0, uint64_t step,

@@ -76,6 +76,63 @@ __device__ __forceinline__ void seg_row(int i, int m, float rm, int& s, int& r) 
   }
 }
 
+struct ChGroup;
+
+// One group's fused FP32 + refinement step (mixed.cu): everything its three
+// launches need, passed by value to a single plan's kernels and as a device
+// array to the ensemble's phase kernels.  The fields of slot z are at
+// st[b] + z * nx * ny; at step parity q, C^n is in st[cur0 ^ q] and C^{n-1}
+// (overwritten by C^{n+1}) in the other buffer.
+struct FFStep {
+  int nx, ny, G;       // grid and simulations stepped
+  int iso;             // square cells (rho = 1): the exact-scaling Laplacian
+  int tx, ty;          // right-hand-side tiles per simulation along x and y
+  int xs;             // x solve: rows per block
+  int ysc, lgys, ypad; // y solve: columns per block (a power of two), its log2, the shared-memory pad
+  int lgx, lgy;        // log2 of the segment lengths (-1 if not a power of two)
+  FFConst k;
+  const float2* glff;  // per slot gamma / dx^2 (double-float)
+  const double* noise; // Cahn-Hilliard-Cook deviates (nullptr: none)
+  double nkx, nky;
+  DirView<float> X, Y;
+  const float2* affX;  // per slot a' along x and y (double-float)
+  const float2* affY;
+  double* st[2];
+  int cur0;
+  float *fhi, *flo, *whi, *wlo, *x0s;  // work: right-hand side, x result, x0 scratch
+  double* cbar;                        // work: Cbar in FP64
+};
+
+// Builds the parameters of the group's fused step for its first G slots, with
+// cur / prev as C^n / C^{n-1} (st = {cur, prev}, cur0 = 0); the solves' blocks
+// take about `target` points each.
+FFStep ff_step_params(const ChGroup* g, int G, double* cur, double* prev, void* work, int target = kFFTarget);
+// The three launches of one fused step (keep_roles as in group_step).
+// Shared-memory bytes of the fused x / y solves for an n-point system with P
+// segments (xs rows / S columns per block), and the tile shapes for about
+// `target` points per block (0: does not fit).
+size_t x_solve_smem(int n, int P, int xs);
+size_t y_solve_smem(int n, int P, int S);
+int x_solve_rows(int n, int P, int target);
+int y_solve_cols(int n, int P, int target);
+int y_solve_pad(int m, int S);
+int log2_exact(int m);
+
+// The ensemble's phase kernels: one launch per phase (0: right-hand side,
+// 1: x solves, 2: y solves and updates) covers the work items of every group.
+// Items are numbered group after group in the order `order` (device array of
+// ngroups group indices into steps); start[k] is the first item of the k-th
+// group of the order (ngroups + 1 entries, start[ngroups] = nitems).  Block b
+// takes items b, b + blocks, ...; every group keeps its own tile shape.  smem:
+// the largest of the groups' blocks (for the right-hand side phase, 0 or 1:
+// whether any group has Cook forcing).
+void launch_ens_phase_ff(int phase, const FFStep* steps, const int* order, const int* start, int ngroups, int nitems,
+                         int blocks, int parity, size_t smem, cudaStream_t st);
+// Items of one phase of a group, and the most blocks per SM its kernel can keep
+// resident with `smem` bytes of dynamic shared memory.
+int ens_phase_items(int phase, const FFStep& P);
+int ens_phase_occupancy(int phase, size_t smem);
+
 // Per-kernel CUDA-event timing (ch_profile).
 enum ProfSlot { kRhs, kLocX, kRedX, kRefX, kLoc2X, kRed2X, kFinX, kLocY, kRedY, kRefY, kLoc2Y, kRed2Y, kUpd, kRhsLap,
                 kXSolve, kYSolve, kSlots };
@@ -104,6 +161,9 @@ struct ProfScope {
 
 struct ObsState;
 
+// The three launches of one fused FP32 step (keep_roles as in group_step).
+void launch_step_ff(const FFStep& P, int keep_roles, Prof* prof, cudaStream_t st);
+
 struct ChGroup {
   int nx = 0, ny = 0, G = 0, precision = 0;
   double lx = 0, ly = 0, gamma = 0, dt = 0, dx = 0, dy = 0;
@@ -126,6 +186,7 @@ struct ChGroup {
   size_t off_f = 0, off_flo = 0, off_w = 0, off_wlo = 0, off_y1 = 0, off_y2 = 0, off_x0 = 0, off_cb = 0, off_m = 0;
   size_t off_ybx = 0, off_tx = 0, off_ybx2 = 0, off_tx2 = 0, off_yby = 0, off_ty = 0, off_yby2 = 0, off_ty2 = 0;
   size_t work_bytes = 0;
+  size_t factor_bytes = 0;  // device bytes of the per-slot factors and parameters (group_init)
 };
 
 // Validates, factorises both directions on the host (FP64) for `gamma` and

@@ -2,18 +2,26 @@
 // together (the batched pattern the thesis's 2D statistics rest on, Sec. 7.3.2:
 // batches of simulations per domain size, run concurrently).
 //
-// Simulations that share (n, L) form a group: one ChGroup (one set of batched
-// launches per step) with packed device-resident state, C^n and C^{n-1} for
-// `capacity` slots, and per-slot LHS factors, so a group mixes any gammas
-// (one LHS per distinct matrix, as the thesis proposes for uneven batches).  Slots [0, active) of a group
-// are stepped; the host keeps them packed (ens_slot_move).  ens_step replays a
-// CUDA graph holding two steps of every group, each group on its own branch so
-// small groups overlap large ones; an odd leftover step runs eagerly.  The two
-// state buffers of a group swap roles each step (no copy).
+// Simulations that share (n, L) form a group: one ChGroup with packed
+// device-resident state, C^n and C^{n-1} for `capacity` slots, and per-slot LHS
+// factors, so a group mixes any gammas (one LHS per distinct matrix, as the
+// thesis proposes for uneven batches).  Slots [0, active) of a group are
+// stepped; the host keeps them packed (ens_slot_move).  The two state buffers
+// of a group swap roles each step (no copy).
+//
+// FP32 + refinement ensembles advance every group with three launches per
+// step, one per phase (right-hand side, x solves, y solves with the update):
+// each launch is a persistent grid whose blocks stride over the work items of
+// all groups, packed group after group in a tuned order (ens_tune_schedule
+// picks the order, the blocks per SM of each phase and the y strips' width).
+// FP64 ensembles launch each group's kernels on a branch of their own.
+// ens_step replays a CUDA graph of two steps; an odd leftover step runs
+// eagerly.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -48,6 +56,23 @@ struct EnsGroup {
 
 }  // namespace
 
+// The FP32 ensemble's packed schedule (see the file comment).
+constexpr int kEnsMaxGroups = 256;  // groups the phase launches cover (more: per-group branches)
+struct EnsSchedule {
+  // tuned choices: order 0 = most work per item first, 1 = least first;
+  // blocks per SM per phase (0 = as many as fit); points per work item of the
+  // solves (the x rows / y columns of every group's tiles follow from it)
+  int order_mode = 0, bps[3] = {0, 0, 0}, target = kFFTarget;
+  // derived for the current groups and active counts
+  int ngroups = 0, nitems[3] = {0, 0, 0}, blocks[3] = {0, 0, 0};
+  size_t smem[3] = {0, 0, 0};
+  bool valid = false;
+  FFStep* d_steps = nullptr;  // kEnsMaxGroups
+  int* d_order = nullptr;     // kEnsMaxGroups
+  int* d_start = nullptr;     // 3 x (kEnsMaxGroups + 1)
+  std::vector<EnsGroup*> members;  // groups in schedule order
+};
+
 struct chx_ens {
   PlanHdr hdr;
   int precision;
@@ -58,6 +83,7 @@ struct chx_ens {
   bool dirty;  // active counts or groups changed since the graph was built
   cudaEvent_t fork;
   cudaStream_t cap;  // private stream the graph is captured on (never the legacy stream)
+  EnsSchedule* sched;  // FP32 + refinement ensembles only
 };
 
 namespace {
@@ -87,6 +113,88 @@ void drop_graph(chx_ens* e) {
   if (e->exec) cudaGraphExecDestroy(e->exec);
   e->exec = nullptr;
   e->dirty = true;
+  if (e->sched) e->sched->valid = false;
+}
+
+bool packed(const chx_ens* e) { return e->precision == CHX_PREC_F32_REFINE && e->sched; }
+
+// Lays out the packed FP32 schedule for the current groups and active counts
+// and uploads it (synchronous; outside any capture).  Returns CHX_OK with
+// valid = false when the groups do not fit the schedule (the per-group branches
+// then step them).
+int build_schedule(chx_ens* e) {
+  EnsSchedule& S = *e->sched;
+  S.valid = false;
+  S.members.clear();
+  for (EnsGroup* G : *e->groups)
+    if (G && G->live && G->active > 0) S.members.push_back(G);
+  S.ngroups = (int)S.members.size();
+  if (S.ngroups == 0 || S.ngroups > kEnsMaxGroups) return CHX_OK;
+  std::vector<FFStep> steps(S.ngroups);
+  for (int k = 0; k < S.ngroups; ++k) {
+    EnsGroup* G = S.members[k];
+    G->g.noise = G->sigma > 0 ? G->d_rho : nullptr;
+    steps[k] = ff_step_params(&G->g, G->active, G->d_state[0], G->d_state[1], G->d_work, S.target);
+    steps[k].cur0 = G->cur;
+    G->g.noise = nullptr;
+    if (steps[k].xs < 1 || steps[k].ysc < 1) return CHX_OK;  // a tile does not fit: per-group launches
+  }
+  // order: most work per item first (largest grids), or least first
+  std::vector<int> order(S.ngroups);
+  for (int k = 0; k < S.ngroups; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return S.order_mode == 0 ? S.members[a]->n > S.members[b]->n : S.members[a]->n < S.members[b]->n;
+  });
+  std::vector<int> start(3 * (kEnsMaxGroups + 1), 0);
+  bool noise = false;
+  size_t sx = 0, sy = 0;
+  for (int k = 0; k < S.ngroups; ++k) {
+    const FFStep& P = steps[order[k]];
+    for (int ph = 0; ph < 3; ++ph)
+      start[ph * (kEnsMaxGroups + 1) + k + 1] = start[ph * (kEnsMaxGroups + 1) + k] + ens_phase_items(ph, P);
+    noise = noise || P.noise;
+    sx = std::max(sx, x_solve_smem(P.nx, P.X.P, P.xs));
+    sy = std::max(sy, y_solve_smem(P.ny, P.Y.P, P.ysc));
+  }
+  int dev = 0, sms = 0;
+  int rc = cuda_check(cudaGetDevice(&dev), "ens: device");
+  if (!rc) rc = cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "ens: SM count");
+  if (rc) return rc;
+  S.smem[0] = noise ? 1 : 0;
+  S.smem[1] = sx;
+  S.smem[2] = sy;
+  for (int ph = 0; ph < 3; ++ph) {
+    S.nitems[ph] = start[ph * (kEnsMaxGroups + 1) + S.ngroups];
+    const int occ = ens_phase_occupancy(ph, ph == 0 ? 0 : S.smem[ph]);
+    const int bps = S.bps[ph] > 0 && S.bps[ph] < occ ? S.bps[ph] : occ;
+    S.blocks[ph] = std::min(S.nitems[ph], sms * bps);
+  }
+  std::vector<FFStep> packed_steps(S.ngroups);
+  for (int k = 0; k < S.ngroups; ++k) packed_steps[k] = steps[k];
+  if ((rc = cuda_check(cudaMemcpy(S.d_steps, packed_steps.data(), S.ngroups * sizeof(FFStep), cudaMemcpyHostToDevice),
+                       "ens: schedule upload")) ||
+      (rc = cuda_check(cudaMemcpy(S.d_order, order.data(), S.ngroups * sizeof(int), cudaMemcpyHostToDevice),
+                       "ens: schedule upload")) ||
+      (rc = cuda_check(cudaMemcpy(S.d_start, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice),
+                       "ens: schedule upload")))
+    return rc;
+  S.valid = true;
+  return CHX_OK;
+}
+
+// One packed FP32 step of every scheduled group at step parity q (C^n of a
+// group in its buffer cur ^ q); Cook groups draw their deviates first.
+void step_packed(chx_ens* e, int q, cudaStream_t st) {
+  EnsSchedule& S = *e->sched;
+  for (EnsGroup* G : S.members)
+    if (G->sigma > 0) {
+      launch_noise_normals(G->d_rho, G->n, G->n, G->active, G->seed, 0, 0, G->d_step, st);
+    }
+  for (int ph = 0; ph < 3; ++ph)
+    launch_ens_phase_ff(ph, S.d_steps, S.d_order, S.d_start + ph * (kEnsMaxGroups + 1), S.ngroups, S.nitems[ph],
+                        S.blocks[ph], q, S.smem[ph], st);
+  for (EnsGroup* G : S.members)
+    if (G->sigma > 0) launch_step_advance(G->d_step, st);
 }
 
 void step_group(EnsGroup* G, cudaStream_t st) {
@@ -100,29 +208,41 @@ void step_group(EnsGroup* G, cudaStream_t st) {
   G->cur = 1 - G->cur;
 }
 
-// Two steps of every active group, each group on its own branch.  Captured on
-// the ensemble's private stream; the instantiated graph can launch on any stream.
+// Two steps of every active group: the packed phase launches (FP32 +
+// refinement), or each group on its own branch.  Captured on the ensemble's
+// private stream; the instantiated graph can launch on any stream.
 int build_graph(chx_ens* e) {
   drop_graph(e);
+  if (packed(e)) {
+    int rc0 = build_schedule(e);
+    if (rc0) return rc0;
+  }
+  const bool use_packed = packed(e) && e->sched->valid;
   cudaGraph_t graph = nullptr;
   cudaStream_t st = e->cap;
   int rc = cuda_check(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "ens: begin capture");
   if (rc) return rc;
-  cudaEventRecord(e->fork, st);
   std::vector<int> saved;
-  for (EnsGroup* G : *e->groups) {
-    saved.push_back(G && G->live ? G->cur : 0);
-    if (!G || !G->live || G->active < 1) continue;
-    cudaStreamWaitEvent(G->stream, e->fork, 0);
-    step_group(G, G->stream);
-    step_group(G, G->stream);
-    cudaEventRecord(G->done, G->stream);
-    cudaStreamWaitEvent(st, G->done, 0);
+  if (use_packed) {
+    step_packed(e, 0, st);
+    step_packed(e, 1, st);
+  } else {
+    cudaEventRecord(e->fork, st);
+    for (EnsGroup* G : *e->groups) {
+      saved.push_back(G && G->live ? G->cur : 0);
+      if (!G || !G->live || G->active < 1) continue;
+      cudaStreamWaitEvent(G->stream, e->fork, 0);
+      step_group(G, G->stream);
+      step_group(G, G->stream);
+      cudaEventRecord(G->done, G->stream);
+      cudaStreamWaitEvent(st, G->done, 0);
+    }
   }
   cudaError_t ce = cudaStreamEndCapture(st, &graph);
   // capture does not execute: put the role flags back (two flips cancel anyway)
-  for (size_t k = 0; k < e->groups->size(); ++k)
-    if ((*e->groups)[k] && (*e->groups)[k]->live) (*e->groups)[k]->cur = saved[k];
+  if (!use_packed)
+    for (size_t k = 0; k < e->groups->size(); ++k)
+      if ((*e->groups)[k] && (*e->groups)[k]->live) (*e->groups)[k]->cur = saved[k];
   rc = cuda_check(ce, "ens: end capture");
   if (!rc) rc = cuda_check(cudaGraphInstantiate(&e->exec, graph, 0), "ens: graph instantiate");
   if (graph) cudaGraphDestroy(graph);
@@ -146,6 +266,12 @@ void ens_free(chx_ens* e) {
   }
   if (e->fork) cudaEventDestroy(e->fork);
   if (e->cap) cudaStreamDestroy(e->cap);
+  if (e->sched) {
+    cudaFree(e->sched->d_steps);
+    cudaFree(e->sched->d_order);
+    cudaFree(e->sched->d_start);
+    delete e->sched;
+  }
   hdr_free(&e->hdr);
   free(e);
 }
@@ -167,6 +293,16 @@ extern "C" int ens_create(chx_ens** out, int precision, double dt, size_t hbm_bu
   e->dirty = true;
   if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming), "ens_create: event");
   if (!rc) rc = cuda_check(cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking), "ens_create: stream");
+  if (!rc && precision == CHX_PREC_F32_REFINE) {
+    e->sched = new (std::nothrow) EnsSchedule();
+    if (!e->sched) rc = fail(CHX_ENOMEM, "ens_create: host allocation");
+    if (!rc && (cudaMalloc(&e->sched->d_steps, kEnsMaxGroups * sizeof(FFStep)) != cudaSuccess ||
+                cudaMalloc(&e->sched->d_order, kEnsMaxGroups * sizeof(int)) != cudaSuccess ||
+                cudaMalloc(&e->sched->d_start, 3 * (kEnsMaxGroups + 1) * sizeof(int)) != cudaSuccess)) {
+      cudaGetLastError();
+      rc = fail(CHX_ENOMEM, "ens_create: schedule tables");
+    }
+  }
   if (rc) { ens_free(e); return rc; }
   *out = e;
   return CHX_OK;
@@ -183,7 +319,7 @@ extern "C" int ens_group_create(chx_ens* e, int n, double l, double gamma, int c
   G->slot_gamma.assign(capacity, gamma);
   // room for the autotuner's larger segment counts (their boundary arrays grow with P)
   G->work_bytes = G->g.work_bytes + G->g.work_bytes / 4 + (1 << 20);
-  G->bytes = state_bytes(n, capacity) + G->work_bytes;
+  G->bytes = state_bytes(n, capacity) + G->work_bytes + G->g.factor_bytes;
   if (e->budget && e->used + G->bytes > e->budget) {
     free_group(G);
     return fail(CHX_ENOMEM, "ens_group_create: %zu bytes over the HBM budget (%zu of %zu used)", G->bytes, e->used,
@@ -234,7 +370,7 @@ extern "C" int ens_slot_load(chx_ens* e, int group_id, int slot, const double* c
     if (!rc) rc = group_set_gamma(&G->g, slot, gamma);
     if (rc) return rc;
     G->slot_gamma[slot] = gamma;
-    e->dirty = true;  // the reduced-solve band captured in the graph may have grown
+    drop_graph(e);  // the reduced-solve band and spike rows captured in the graph may have changed
   }
   rc = cuda_check(cudaMemcpyAsync((char*)G->d_state[G->cur] + slot * nb, c0, nb, cudaMemcpyDefault, st),
                       "ens_slot_load: C^n");
@@ -335,7 +471,7 @@ extern "C" int ens_group_set_active(chx_ens* e, int group_id, int active) {
   if (!G || active < 0 || active > G->capacity) return fail(CHX_EINVAL, "ens_group_set_active: bad argument");
   if (G->active != active) {
     G->active = active;
-    e->dirty = true;
+    drop_graph(e);
   }
   return CHX_OK;
 }
@@ -353,9 +489,18 @@ extern "C" int ens_step(chx_ens* e, int nsteps, void* stream) {
     if (rc) return rc;
   }
   if (nsteps & 1) {
-    for (EnsGroup* G : *e->groups)
-      if (G && G->live) step_group(G, st);
-    e->dirty = true;  // the captured pair starts from the other buffer now
+    if (packed(e) && !e->sched->valid) {
+      rc = build_schedule(e);
+      if (rc) return rc;
+    }
+    if (packed(e) && e->sched->valid) {
+      step_packed(e, 0, st);
+      for (EnsGroup* G : e->sched->members) G->cur = 1 - G->cur;
+    } else {
+      for (EnsGroup* G : *e->groups)
+        if (G && G->live) step_group(G, st);
+    }
+    drop_graph(e);  // the captured pair and the schedule start from the other buffer now
   }
   e->hdr.last_stream = st;
   return launch_check("ens_step");
@@ -366,7 +511,7 @@ extern "C" int ens_group_step(chx_ens* e, int group_id, int nsteps, void* stream
   if (!G || nsteps < 0) return fail(CHX_EINVAL, "ens_group_step: bad argument");
   cudaStream_t st = (cudaStream_t)stream;
   for (int k = 0; k < nsteps; ++k) step_group(G, st);
-  if (nsteps & 1) e->dirty = true;
+  if (nsteps & 1) drop_graph(e);
   e->hdr.last_stream = st;
   return launch_check("ens_group_step");
 }
@@ -385,6 +530,8 @@ extern "C" int ens_autotune(chx_ens* e, int group_id, int trial, int* px_out, in
   double best = 1e300;
   int bx = G->g.X.P, by = G->g.Y.P;
   void* save = nullptr;
+  if (e->budget && e->used + 2 * sb > e->budget)
+    return fail(CHX_ENOMEM, "ens_autotune: %zu bytes of saved state over the HBM budget", 2 * sb);
   if (cudaMalloc(&save, 2 * sb) != cudaSuccess) {
     cudaGetLastError();
     return fail(CHX_ENOMEM, "ens_autotune: scratch for the saved state");
@@ -399,9 +546,13 @@ extern "C" int ens_autotune(chx_ens* e, int group_id, int trial, int* px_out, in
   for (int P : cx) {
     ChGroup trialg;
     rc = group_init(&trialg, n, n, G->l, G->l, G->gamma, e->dt, e->precision, G->capacity, P, P);
+    if (rc) break;  // group_init frees its own partial allocations
     for (int z = 0; z < G->active && !rc; ++z)
       if (G->slot_gamma[z] != G->gamma) rc = group_set_gamma(&trialg, z, G->slot_gamma[z]);
-    if (rc) break;
+    if (rc) {
+      group_free(&trialg);
+      break;
+    }
     if (trialg.work_bytes > G->work_bytes) {  // candidate needs more scratch than the group holds
       group_free(&trialg);
       continue;
@@ -441,6 +592,9 @@ extern "C" int ens_autotune(chx_ens* e, int group_id, int trial, int* px_out, in
     const double nkx = G->g.nkx, nky = G->g.nky;
     group_free(&G->g);
     G->g = ng;
+    e->used -= G->bytes;  // the new segment counts change the factor arrays' size
+    G->bytes = state_bytes(n, G->capacity) + G->work_bytes + G->g.factor_bytes;
+    e->used += G->bytes;
     G->g.nkx = nkx;  // the group's forcing weights carry over to the new factors
     G->g.nky = nky;
     drop_graph(e);
@@ -464,3 +618,112 @@ extern "C" int ens_info(chx_ens* e, int group_id, int* n, int* capacity, int* ac
 }
 
 extern "C" size_t ens_bytes_used(const chx_ens* e) { return (e && e->hdr.magic == kMagicEns) ? e->used : 0; }
+
+// Times `trial` packed steps for each candidate schedule of an FP32 +
+// refinement ensemble and keeps the fastest: the group order (most or least
+// work per item first), the points per work item of the solves (2048, 4096 or
+// 8192: every group's x rows and y columns per block follow from it) and the y
+// phase's blocks per SM (as many as fit, or one).  The trials overwrite
+// C^{n-1} of the active slots, which is saved first and put back, so the call
+// changes no simulation; the save counts against the HBM budget.
+extern "C" int ens_tune_schedule(chx_ens* e, int trial, int* order_out, int* target_out, int* blocks_out,
+                                 void* stream) {
+  if (!e || e->hdr.magic != kMagicEns || trial < 1) return fail(CHX_EINVAL, "ens_tune_schedule: bad argument");
+  if (!packed(e)) return fail(CHX_EUNSUPPORTED, "ens_tune_schedule: FP32 + refinement ensembles only");
+  cudaStream_t st = (cudaStream_t)stream;
+  EnsSchedule& S = *e->sched;
+  int rc = build_schedule(e);
+  if (rc) return rc;
+  if (!S.valid) return fail(CHX_EUNSUPPORTED, "ens_tune_schedule: no active groups, or more than %d", kEnsMaxGroups);
+  // save C^{n-1} of every active slot
+  size_t save_bytes = 0;
+  for (EnsGroup* G : S.members) save_bytes += (size_t)G->active * G->n * G->n * sizeof(double);
+  if (e->budget && e->used + save_bytes > e->budget)
+    return fail(CHX_ENOMEM, "ens_tune_schedule: %zu bytes of saved state over the HBM budget", save_bytes);
+  char* save = nullptr;
+  if (cudaMalloc(&save, save_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(CHX_ENOMEM, "ens_tune_schedule: %zu bytes for the saved state", save_bytes);
+  }
+  {
+    size_t off = 0;
+    for (EnsGroup* G : S.members) {
+      const size_t b = (size_t)G->active * G->n * G->n * sizeof(double);
+      cudaMemcpyAsync(save + off, G->d_state[1 - G->cur], b, cudaMemcpyDeviceToDevice, st);
+      off += b;
+    }
+  }
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  const int order0 = S.order_mode, target0 = S.target, bps0 = S.bps[2];
+  double best = 1e300;
+  int bo = order0, bt = target0, bb = bps0;
+  for (int om = 0; om < 2 && !rc; ++om)
+    for (int tg : {2048, 4096, 8192}) {
+      if (rc) break;
+      for (int yb : {0, 1}) {
+        S.order_mode = om;
+        S.target = tg;
+        S.bps[2] = yb;
+        if ((rc = build_schedule(e))) break;
+        if (!S.valid) continue;
+        step_packed(e, 0, st);  // warm-up
+        cudaEventRecord(a, st);
+        for (int k = 0; k < trial; ++k) step_packed(e, 0, st);
+        cudaEventRecord(b, st);
+        if ((rc = cuda_check(cudaEventSynchronize(b), "ens_tune_schedule: trial"))) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < best) {
+          best = ms;
+          bo = om;
+          bt = tg;
+          bb = yb;
+        }
+      }
+    }
+  {
+    size_t off = 0;
+    for (EnsGroup* G : S.members) {
+      const size_t bs = (size_t)G->active * G->n * G->n * sizeof(double);
+      cudaMemcpyAsync(G->d_state[1 - G->cur], save + off, bs, cudaMemcpyDeviceToDevice, st);
+      off += bs;
+    }
+  }
+  cudaStreamSynchronize(st);
+  cudaFree(save);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  S.order_mode = rc ? order0 : bo;
+  S.target = rc ? target0 : bt;
+  S.bps[2] = rc ? bps0 : bb;
+  drop_graph(e);
+  if (rc) return rc;
+  rc = build_schedule(e);
+  if (rc) return rc;
+  if (order_out) *order_out = S.order_mode;
+  if (target_out) *target_out = S.target;
+  if (blocks_out)
+    for (int ph = 0; ph < 3; ++ph) blocks_out[ph] = S.blocks[ph];
+  return CHX_OK;
+}
+
+// The packed schedule's layout for the current groups (FP32 + refinement
+// ensembles): work items and blocks of each phase, points per item, order.
+extern "C" int ens_schedule_info(chx_ens* e, int* items_out, int* blocks_out, int* target_out, int* order_out) {
+  if (!e || e->hdr.magic != kMagicEns) return fail(CHX_EINVAL, "ens_schedule_info: bad argument");
+  if (!packed(e)) return fail(CHX_EUNSUPPORTED, "ens_schedule_info: FP32 + refinement ensembles only");
+  EnsSchedule& S = *e->sched;
+  if (!S.valid) {
+    int rc = build_schedule(e);
+    if (rc) return rc;
+  }
+  for (int ph = 0; ph < 3; ++ph) {
+    if (items_out) items_out[ph] = S.valid ? S.nitems[ph] : 0;
+    if (blocks_out) blocks_out[ph] = S.valid ? S.blocks[ph] : 0;
+  }
+  if (target_out) *target_out = S.target;
+  if (order_out) *order_out = S.order_mode;
+  return CHX_OK;
+}

@@ -11,6 +11,8 @@
 // residual plus the FP64<->FP32 conversions around it would cost as much as the
 // FP64 sweeps it is meant to replace.  The double-float residual is accurate to
 // ~2^-46 of its terms, which is what one refinement step of an FP32 solve needs.
+#include <algorithm>
+
 #include "chgroup.cuh"
 #include "ff.cuh"
 
@@ -58,23 +60,33 @@ __device__ __forceinline__ ff lap_ff(const ff (*t)[LD], int y, int x, ff rho, ff
 // formed in FP64 on the otherwise idle FP64 unit (one subtraction and one FMA
 // per direction) from caller-given or pre-drawn deviates, and added as a
 // double-float pair.
-template <bool kIso, bool NOISE = false>
-__global__ void __launch_bounds__(kT* kBY) ch_rhs_ff_kernel(const double* __restrict__ cn,
-                                                            const double* __restrict__ cp, float* __restrict__ rhi,
-                                                            float* __restrict__ rlo, int nx, int ny, int G, float2 rho2,
-                                                            float2 kap2, const float2* __restrict__ glff, float2 k12,
-                                                            float2 k22, double* __restrict__ cbo,
-                                                            const double* __restrict__ dev = nullptr, double nkx = 0,
-                                                            double nky = 0) {
-  __shared__ ff s_cn[kT + 4][kT + 5];
-  __shared__ ff s_cb[kT + 4][kT + 5];
-  __shared__ ff s_m[kT + 2][kT + 3];
-  __shared__ ff s_nz[NOISE ? kT : 1][kT + 1];
-  const int z = blockIdx.z;
-  const ff rho = ffc(rho2), kap = ffc(kap2), gl = ffc(glff[z]), k1 = ffc(k12), k2 = ffc(k22);
+template <bool NOISE>
+struct RhsSmem {
+  ff cn[kT + 4][kT + 5];
+  ff cb[kT + 4][kT + 5];
+  ff m[kT + 2][kT + 3];
+  ff nz[NOISE ? kT : 1][kT + 1];
+};
+
+// One 32 x 32 tile (bx, by) of simulation z, by a 32 x 8 thread block; cn / cp
+// are the group's C^n / C^{n-1} buffers.
+template <bool kIso, bool NOISE>
+__device__ __forceinline__ void rhs_ff_tile(RhsSmem<NOISE>& sh, const FFStep& P, const double* __restrict__ cn,
+                                            const double* __restrict__ cp, int z, int bx, int by) {
+  auto& s_cn = sh.cn;
+  auto& s_cb = sh.cb;
+  auto& s_m = sh.m;
+  auto& s_nz = sh.nz;
+  const int nx = P.nx, ny = P.ny;
+  float* __restrict__ rhi = P.fhi;
+  float* __restrict__ rlo = P.flo;
+  double* __restrict__ cbo = P.cbar;
+  const double* __restrict__ dev = P.noise;
+  const double nkx = P.nkx, nky = P.nky;
+  const ff rho = ffc(P.k.rho), kap = ffc(P.k.kap), gl = ffc(P.glff[z]), k1 = ffc(P.k.k1), k2 = ffc(P.k.k2);
   cn += (size_t)z * nx * ny;
   cp += (size_t)z * nx * ny;
-  const int i0 = blockIdx.x * kT, j0 = blockIdx.y * kT;
+  const int i0 = bx * kT, j0 = by * kT;
   const int tid = threadIdx.y * kT + threadIdx.x;
   auto stage = [&](int ly, int lx) {
     const int gi = wrap_near(i0 - 2 + lx, nx), gj = wrap_near(j0 - 2 + ly, ny);
@@ -130,15 +142,11 @@ __global__ void __launch_bounds__(kT* kBY) ch_rhs_ff_kernel(const double* __rest
   }
 }
 
-__device__ __forceinline__ float corr32(const float* __restrict__ vw, const float* __restrict__ tau, int m, int P,
-                                        int nsys, int s, int r, int j) {
-  const int sn = s + 1 == P ? 0 : s + 1, sp = s == 0 ? P - 1 : s - 1;
-  const size_t S = (size_t)nsys;
-  float c = __ldg(&vw[r]) * tau[(size_t)(4 * sn + 0) * S + j];
-  c = fmaf(__ldg(&vw[m + r]), tau[(size_t)(4 * sn + 1) * S + j], c);
-  c = fmaf(__ldg(&vw[2 * m + r]), tau[(size_t)(4 * sp + 2) * S + j], c);
-  c = fmaf(__ldg(&vw[3 * m + r]), tau[(size_t)(4 * sp + 3) * S + j], c);
-  return c;
+template <bool kIso, bool NOISE>
+__global__ void __launch_bounds__(kT* kBY) ch_rhs_ff_kernel(FFStep P, const double* __restrict__ cn,
+                                                            const double* __restrict__ cp) {
+  __shared__ RhsSmem<NOISE> sh;
+  rhs_ff_tile<kIso, NOISE>(sh, P, cn, cp, blockIdx.z, blockIdx.x, blockIdx.y);
 }
 
 // x0 = y - (V0 ta + V1 tb + W0 tc + W1 td) for row r of a segment, rounded once
@@ -179,48 +187,6 @@ __device__ __forceinline__ float corr_first(float y, const float* __restrict__ v
   return corr_exact(y, vw, vwlo, m, r, ta, tb, tc, td);
 }
 
-// Reduced system of the first (full right-hand side) solve in double-float:
-// tau = Rinv * yb with Rinv as pairs (rinv + rinvlo) against the FP32
-// boundary values, each term's product exact (TwoProd) and the sum carried as
-// an unevaluated pair; tau is rounded once to float.  The reduced system
-// inherits the conditioning of the stiff operator (cond ~2e4 at a' = 1.9e4),
-// so an FP32 evaluation would leave ~1e-3 relative error in the boundary
-// values that a single refinement pass cannot remove.  One output per thread;
-// grid (systems / 128, 4P, Z); rows as in the FP32 reduced kernel (band).
-__global__ void __launch_bounds__(kSolveThreads) spike_reduced_ff_kernel(const float* __restrict__ yb,
-                                                                         DirView<float> D, float* __restrict__ tau,
-                                                                         int nsys, size_t ybz) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= nsys) return;
-  const int P = D.P, k = 4 * P;
-  const int slot = blockIdx.z + j / D.spp;
-  yb += blockIdx.z * ybz;
-  tau += blockIdx.z * ybz;
-  const int q = blockIdx.y;
-  const size_t ro = (size_t)slot * k * k + (size_t)q * k;
-  const float* rh = D.rinv + ro;
-  const float* rl = D.rinvlo + ro;
-  const int sq = q >> 2, nb = 2 * D.band + 1 < P ? 2 * D.band + 1 : P;
-  const int s0 = nb == P ? 0 : sq - D.band;
-  float s = 0.f, e = 0.f;
-  for (int bb = 0; bb < nb; ++bb) {
-    int sb = s0 + bb;
-    sb = sb < 0 ? sb + P : (sb >= P ? sb - P : sb);
-    const int pc = 4 * sb;
-    float v[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = yb[(size_t)(pc + u) * nsys + j];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const ff p = two_prod(__ldg(&rh[pc + u]), v[u]);
-      const ff t = two_sum(s, p.hi);
-      s = t.hi;
-      e = e + (t.lo + fmaf(__ldg(&rl[pc + u]), v[u], p.lo));
-    }
-  }
-  tau[(size_t)q * nsys + j] = s + e;
-}
-
 // A x0 for the ADI row (a, -4a, 1 + 6a, -4a, a): x0 + a * delta^4 x0, the fourth
 // difference formed with error-free sums.
 __device__ __forceinline__ ff adi_apply_ff(float w0, float w1, float w2, float w3, float w4, ff a) {
@@ -229,155 +195,6 @@ __device__ __forceinline__ ff adi_apply_ff(float w0, float w1, float w2, float w
   ff d = ff_sub(s2, ff_scale2(s1, 4.f));
   d = ff_add(d, two_prod(6.f, w2));
   return ff_add_f(ff_mul(a, d), w2);
-}
-
-// Refinement residual on tiles of 32 rows x 32 systems: the first FP32
-// solution x0 = y1 - spike correction (corr_exact: double-float spikes, exact
-// accumulation) is formed once per element of the tile and its 2-row halo and
-// staged in shared memory; then rho = f - A x0 in
-// double-float for the tile's points.  Writes rho's high part (the right-hand
-// side of the FP32 correction solve) and x0.  Element (row i, system j) at
-// [i*ld + j] (+ blockIdx.z * fz); grid (systems / 32, n / 32, Z), block 32 x 8.
-__global__ void __launch_bounds__(kT* kBY) ch_resid_ff_kernel(
-    const float* __restrict__ fhi, const float* __restrict__ flo, const float* __restrict__ y1,
-    const float* __restrict__ t1, float* __restrict__ x0out, float* __restrict__ rho, int ld, int nsys, int n,
-    DirView<float> D, const float2* __restrict__ aff, size_t fz, size_t ybz) {
-  __shared__ float sx[kT + 4][kT + 1];
-  const int m = D.m, P = D.P;
-  const int j = blockIdx.x * kT + threadIdx.x;
-  const int i0 = blockIdx.y * kT;
-  const size_t off = blockIdx.z * fz;
-  fhi += off;
-  flo += off;
-  y1 += off;
-  x0out += off;
-  rho += off;
-  t1 += blockIdx.z * ybz;
-  const bool live = j < nsys;
-  const int slot = blockIdx.z + (live ? j : 0) / D.spp;
-  const float* vw = D.vw + (size_t)slot * 4 * m;
-  const float* vwlo = D.vwlo + (size_t)slot * 4 * m;
-  const size_t S = (size_t)nsys;
-  // a warp's rows share threadIdx.y, so the segment (and its four reduced
-  // unknowns) changes warp-uniformly and rarely: load them once per segment
-  int cs = -1;
-  float ta = 0.f, tb = 0.f, tc = 0.f, td = 0.f;
-  for (int ly = threadIdx.y; ly < kT + 4; ly += kBY) {
-    float v = 0.f;
-    if (live) {
-      int i = i0 - 2 + ly;
-      i = i < 0 ? i + n : (i >= n ? i - n : i);
-      int s, r;
-      seg_row(i, m, D.rm, s, r);
-      if (s != cs) {
-        cs = s;
-        const int sn = s + 1 == P ? 0 : s + 1, sp = s == 0 ? P - 1 : s - 1;
-        ta = t1[(size_t)(4 * sn) * S + j];
-        tb = t1[(size_t)(4 * sn + 1) * S + j];
-        tc = t1[(size_t)(4 * sp + 2) * S + j];
-        td = t1[(size_t)(4 * sp + 3) * S + j];
-      }
-      v = corr_exact(y1[(size_t)i * ld + j], vw, vwlo, m, r, ta, tb, tc, td);
-    }
-    sx[ly][threadIdx.x] = v;
-  }
-  __syncthreads();
-  if (!live) return;
-  const ff a = ffc(aff[slot]);
-#pragma unroll
-  for (int k = 0; k < kT / kBY; ++k) {
-    const int ly = threadIdx.y + k * kBY, i = i0 + ly;
-    if (i >= n) break;
-    const float* col = &sx[ly][threadIdx.x];
-    const ff ax = adi_apply_ff(col[0], col[kT + 1], col[2 * (kT + 1)], col[3 * (kT + 1)], col[4 * (kT + 1)], a);
-    const size_t p = (size_t)i * ld + j;
-    rho[p] = ff_sub(ff{fhi[p], flo[p]}, ax).hi;
-    x0out[p] = col[2 * (kT + 1)];
-  }
-}
-
-// x sweep result w = x0 + delta as an exact double-float pair, transposed back
-// to row-major (w[j*nx + i]).
-__global__ void __launch_bounds__(kT* kBY) ch_xfinish_ff_kernel(const float* __restrict__ y1,
-                                                                const float* __restrict__ t1,
-                                                                const float* __restrict__ y2,
-                                                                const float* __restrict__ t2, DirView<float> D,
-                                                                float* __restrict__ whi, float* __restrict__ wlo,
-                                                                int nx, int ny, int G) {
-  __shared__ ff s_t[kT][kT + 1];
-  const int z = blockIdx.z, m = D.m, P = D.P;
-  const float* vw = D.vw + (size_t)z * 4 * m;
-  const int i0 = blockIdx.x * kT, j0 = blockIdx.y * kT;
-  const int j = j0 + threadIdx.x;
-  const size_t ld = (size_t)G * ny;
-  const int sys = z * ny + j;
-  const size_t S = (size_t)G * ny;
-  int cs = -1;  // the correction's reduced unknowns, loaded once per segment (warp-uniform)
-  float ta = 0.f, tb = 0.f, tc = 0.f, td = 0.f;
-#pragma unroll
-  for (int k = 0; k < kT / kBY; ++k) {
-    const int li = threadIdx.y + k * kBY, i = i0 + li;
-    if (i < nx && j < ny) {
-      int s, r;
-      seg_row(i, m, D.rm, s, r);
-      if (s != cs) {
-        cs = s;
-        const int sn = s + 1 == P ? 0 : s + 1, sp = s == 0 ? P - 1 : s - 1;
-        ta = t2[(size_t)(4 * sn) * S + sys];
-        tb = t2[(size_t)(4 * sn + 1) * S + sys];
-        tc = t2[(size_t)(4 * sp + 2) * S + sys];
-        td = t2[(size_t)(4 * sp + 3) * S + sys];
-      }
-      float c = __ldg(&vw[r]) * ta;
-      c = fmaf(__ldg(&vw[m + r]), tb, c);
-      c = fmaf(__ldg(&vw[2 * m + r]), tc, c);
-      c = fmaf(__ldg(&vw[3 * m + r]), td, c);
-      const float x0 = y1[(size_t)i * ld + sys];  // corrected first solution
-      const float dl = y2[(size_t)i * ld + sys] - c;
-      s_t[li][threadIdx.x] = two_sum(x0, dl);
-    }
-  }
-  __syncthreads();
-  whi += (size_t)z * nx * ny;
-  wlo += (size_t)z * nx * ny;
-#pragma unroll
-  for (int k = 0; k < kT / kBY; ++k) {
-    const int lj = threadIdx.y + k * kBY, li = threadIdx.x;
-    const int gi = i0 + li, gj = j0 + lj;
-    if (gi < nx && gj < ny) {
-      const ff v = s_t[li][lj];
-      whi[(size_t)gj * nx + gi] = v.hi;
-      wlo[(size_t)gj * nx + gi] = v.lo;
-    }
-  }
-}
-
-// C^{n+1} = 2 C^n - C^{n-1} + v with v = x0 + delta (exact pair, added in FP64).
-__global__ void __launch_bounds__(kSolveThreads) ch_update_ff_kernel(const float* __restrict__ y1,
-                                                                     const float* __restrict__ t1,
-                                                                     const float* __restrict__ y2,
-                                                                     const float* __restrict__ t2, DirView<float> D,
-                                                                     double* cn, double* cp, int nx, int ny,
-                                                                     int keep_roles) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y, z = blockIdx.z, m = D.m, P = D.P;
-  const float* vw = D.vw + (size_t)z * 4 * m;
-  if (i >= nx) return;
-  const int s = j / m, r = j - s * m;
-  const size_t p = (size_t)z * nx * ny + (size_t)j * nx + i;
-  t1 += (size_t)z * 4 * P * nx;
-  t2 += (size_t)z * 4 * P * nx;
-  const float x0 = y1[p];  // corrected first solution
-  const float dl = y2[p] - corr32(vw, t2, m, P, nx, s, r, i);
-  const ff v = two_sum(x0, dl);
-  const double a = cn[p], b = cp[p];
-  const double nxt = fma(2.0, a, -b) + ff2d(v);
-  if (keep_roles) {
-    cp[p] = a;
-    cn[p] = nxt;
-  } else {
-    cp[p] = nxt;
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -597,8 +414,10 @@ __global__ void __launch_bounds__(kSolveThreads) penta_solve_f32_from_f64_kernel
 // block's values and factors are loaded first, so the serial recurrence
 // waits on one load latency per block instead of one per row.
 template <int ST>
-__device__ __forceinline__ void seg_sweep32(float* x, int m, float a, const float* __restrict__ lu, float* yb4) {
+__device__ __forceinline__ void seg_sweep32(float* x, int m, float a, const float* __restrict__ lu, float* yb4,
+                                            int st = ST) {
   constexpr int B = 8;
+  const int STR = ST > 0 ? ST : st;  // ST = 0: the stride st given at run time
   const float *ra = lu, *be = lu + m, *ga = lu + 2 * m, *de = lu + 3 * m;
   const int mb = m - m % B;
   float g1 = 0.f, g2 = 0.f;
@@ -606,7 +425,7 @@ __device__ __forceinline__ void seg_sweep32(float* x, int m, float a, const floa
     float v[B], cb[B], cr[B];
 #pragma unroll
     for (int u = 0; u < B; ++u) {
-      v[u] = x[(r0 + u) * ST];
+      v[u] = x[(r0 + u) * STR];
       cb[u] = __ldg(&be[r0 + u]);
       cr[u] = __ldg(&ra[r0 + u]);
     }
@@ -619,20 +438,20 @@ __device__ __forceinline__ void seg_sweep32(float* x, int m, float a, const floa
       g1 = g;
     }
 #pragma unroll
-    for (int u = 0; u < B; ++u) x[(r0 + u) * ST] = v[u];
+    for (int u = 0; u < B; ++u) x[(r0 + u) * STR] = v[u];
   }
   for (int r = mb; r < m; ++r) {
-    float g = fmaf(-a, g2, x[r * ST]);
+    float g = fmaf(-a, g2, x[r * STR]);
     g = fmaf(-__ldg(&be[r]), g1, g) * __ldg(&ra[r]);
-    x[r * ST] = g;
+    x[r * STR] = g;
     g2 = g1;
     g1 = g;
   }
   float x1 = 0.f, x2 = 0.f;
   for (int r = m - 1; r >= mb; --r) {
-    float v = fmaf(-__ldg(&ga[r]), x1, x[r * ST]);
+    float v = fmaf(-__ldg(&ga[r]), x1, x[r * STR]);
     v = fmaf(-__ldg(&de[r]), x2, v);
-    x[r * ST] = v;
+    x[r * STR] = v;
     x2 = x1;
     x1 = v;
   }
@@ -640,7 +459,7 @@ __device__ __forceinline__ void seg_sweep32(float* x, int m, float a, const floa
     float v[B], cg[B], cd[B];
 #pragma unroll
     for (int u = B - 1; u >= 0; --u) {
-      v[u] = x[(r0 + u) * ST];
+      v[u] = x[(r0 + u) * STR];
       cg[u] = __ldg(&ga[r0 + u]);
       cd[u] = __ldg(&de[r0 + u]);
     }
@@ -653,12 +472,12 @@ __device__ __forceinline__ void seg_sweep32(float* x, int m, float a, const floa
       x1 = t;
     }
 #pragma unroll
-    for (int u = 0; u < B; ++u) x[(r0 + u) * ST] = v[u];
+    for (int u = 0; u < B; ++u) x[(r0 + u) * STR] = v[u];
   }
   yb4[0] = x1;
   yb4[1] = x2;
-  yb4[2] = x[(m - 2) * ST];
-  yb4[3] = x[(m - 1) * ST];
+  yb4[2] = x[(m - 2) * STR];
+  yb4[3] = x[(m - 1) * STR];
 }
 
 // Block offset of step t of the banded reduced product (t in [0, nb)):
@@ -709,8 +528,8 @@ __device__ __forceinline__ float spikes32(const float* __restrict__ vw, int m, i
   return fmaf(__ldg(&vw[3 * m + r]), td, c);
 }
 
-constexpr int kXS = 2, kXThreads = 128;  // x: rows per block, threads
-constexpr int kYThreads = 512;           // y: threads (columns per block: template)
+constexpr int kXThreads = 128;  // x solve: threads per block (rows per block: FFStep::xs)
+constexpr int kYThreads = 512;  // y solve: threads per block (columns per block: FFStep::ysc)
 
 // Row e of a system -> (segment p, row r in the segment) for segments of m
 // rows: shifts when m is a power of two (lg = log2 m), else seg_row.
@@ -736,20 +555,22 @@ __device__ __forceinline__ int wrap2(int j, int n) { return j < 0 ? j + n : (j >
 // goes to the scratch (the residual reads its neighbours there, L2-resident)
 // and the residual rho = f - A x0 replaces y in shared memory.  The memory
 // phases load a batch of elements before computing on them.
-__global__ void __launch_bounds__(kXThreads, 7) x_solve_ff_kernel(const float* __restrict__ fhi,
-                                                                  const float* __restrict__ flo,
-                                                                  float* __restrict__ x0s, float* __restrict__ whi,
-                                                                  float* __restrict__ wlo, int n, int rows, int ny,
-                                                                  DirView<float> D, const float2* __restrict__ aff,
-                                                                  int lgm) {
-  extern __shared__ float sm[];
+__device__ __forceinline__ void x_solve_rows(float* sm, const FFStep& PS, int row0) {
+  const float* __restrict__ fhi = PS.fhi;
+  const float* __restrict__ flo = PS.flo;
+  float* __restrict__ x0s = PS.x0s;
+  float* __restrict__ whi = PS.whi;
+  float* __restrict__ wlo = PS.wlo;
+  const int n = PS.nx, ny = PS.ny, rows = PS.G * PS.ny, lgm = PS.lgx;
+  const DirView<float>& D = PS.X;
+  const float2* __restrict__ aff = PS.affX;
   const int m = D.m, P = D.P, K = 4 * P, Ls = n + P;
   float* X = sm;
-  float* yb = X + kXS * Ls;
-  float* tau = yb + kXS * K;
+  const int XS = PS.xs;
+  float* yb = X + XS * Ls;
+  float* tau = yb + XS * K;
   const SegMap sg{m, lgm, D.rm};
-  const int row0 = blockIdx.x * kXS;
-  const int ns = rows - row0 < kXS ? rows - row0 : kXS;
+  const int ns = rows - row0 < XS ? rows - row0 : XS;
   const int tid = threadIdx.x;
   for (int s = 0; s < ns; ++s) {
     const float* src = fhi + (size_t)(row0 + s) * n;
@@ -868,6 +689,11 @@ __global__ void __launch_bounds__(kXThreads, 7) x_solve_ff_kernel(const float* _
   }
 }
 
+__global__ void __launch_bounds__(kXThreads, 7) x_solve_ff_kernel(FFStep P) {
+  extern __shared__ float sm[];
+  x_solve_rows(sm, P, blockIdx.x * P.xs);
+}
+
 // y direction.  Columns col0 .. col0 + S - 1 of simulation z (blockIdx.y),
 // n = ny points each; w (the right-hand side), x0s and the fields are
 // row-major [z][j][i].  Shared memory: [segment][m rows][S columns] with a
@@ -878,32 +704,28 @@ __global__ void __launch_bounds__(kXThreads, 7) x_solve_ff_kernel(const float* _
 // residual as in the x solve.  The update C^{n+1} = Cbar + v (v = x0 + delta, an exact pair; Cbar =
 // 2 C^n - C^{n-1} in FP64 from the right-hand side pass) is formed in FP64;
 // keep_roles as in ch_update_kernel.
-template <int S>
-__global__ void __launch_bounds__(kYThreads, 2) y_solve_ff_kernel(const float* __restrict__ fhi,
-                                                                  const float* __restrict__ flo,
-                                                                  float* __restrict__ x0s,
-                                                                  const double* __restrict__ cbar, double* __restrict__ cn,
-                                                                  double* __restrict__ cp, int nx, int n, DirView<float> D,
-                                                                  const float2* __restrict__ aff, int pad,
-                                                                  int keep_roles, int lgm) {
-  static_assert(kYThreads % S == 0, "threads per column");
-  constexpr int RR = kYThreads / S;  // rows a pass of the block covers
-  extern __shared__ float sm[];
+__device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double* __restrict__ cn,
+                                             double* __restrict__ cp, int keep_roles, int z, int col0) {
+  const int nx = PS.nx, n = PS.ny, pad = PS.ypad, lgm = PS.lgy;
+  const DirView<float>& D = PS.Y;
+  const float2* __restrict__ aff = PS.affY;
+  const int S = PS.ysc, lgs = PS.lgys;  // columns per block (a power of two <= 32)
+  const int RR = kYThreads >> lgs;      // rows a pass of the block covers
   const int m = D.m, P = D.P, K = 4 * P, K1 = K + 1, pitch = m * S + pad;
   float* X = sm;
   float* yb = X + P * pitch;
   float* tau = yb + S * K1;
   const SegMap sg{m, lgm, D.rm};
-  const int z = blockIdx.y, slot = z, col0 = blockIdx.x * S;
+  const int slot = z;
   const int ns = nx - col0 < S ? nx - col0 : S;
   const size_t zo = (size_t)z * nx * n;
-  fhi += zo;
-  flo += zo;
-  x0s += zo;
-  cbar += zo;
+  const float* __restrict__ fhi = PS.whi + zo;  // the y solve's right-hand side is the x result
+  const float* __restrict__ flo = PS.wlo + zo;
+  float* __restrict__ x0s = PS.x0s + zo;
+  const double* __restrict__ cbar = PS.cbar + zo;
   cn += zo;
   cp += zo;
-  const int tid = threadIdx.x, s = tid % S, e0 = tid / S;
+  const int tid = threadIdx.x, s = tid & (S - 1), e0 = tid >> lgs;
   const bool live = s < ns;
   const int c = col0 + s;
   auto at = [&](int e) {
@@ -926,8 +748,8 @@ __global__ void __launch_bounds__(kYThreads, 2) y_solve_ff_kernel(const float* _
   const float a32 = D.a[slot];
   const float* lu = D.lu + (size_t)slot * 4 * m;
   for (int w = tid; w < S * P; w += kYThreads) {
-    const int sw = w % S, p = w / S;
-    if (sw < ns) seg_sweep32<S>(X + p * pitch + sw, m, a32, lu, yb + sw * K1 + 4 * p);
+    const int sw = w & (S - 1), p = w >> lgs;
+    if (sw < ns) seg_sweep32<0>(X + p * pitch + sw, m, a32, lu, yb + sw * K1 + 4 * p, S);
   }
   __syncthreads();
   const size_t ko = (size_t)slot * K * K;
@@ -976,8 +798,8 @@ __global__ void __launch_bounds__(kYThreads, 2) y_solve_ff_kernel(const float* _
   }
   __syncthreads();
   for (int w = tid; w < S * P; w += kYThreads) {
-    const int sw = w % S, p = w / S;
-    if (sw < ns) seg_sweep32<S>(X + p * pitch + sw, m, a32, lu, yb + sw * K1 + 4 * p);
+    const int sw = w & (S - 1), p = w >> lgs;
+    if (sw < ns) seg_sweep32<0>(X + p * pitch + sw, m, a32, lu, yb + sw * K1 + 4 * p, S);
   }
   __syncthreads();
   for (int o = tid; o < S * K; o += kYThreads) {
@@ -1020,49 +842,72 @@ __global__ void __launch_bounds__(kYThreads, 2) y_solve_ff_kernel(const float* _
   }
 }
 
+__global__ void __launch_bounds__(kYThreads, 2) y_solve_ff_kernel(FFStep P, double* cn, double* cp, int keep_roles) {
+  extern __shared__ float sm[];
+  y_solve_cols(sm, P, cn, cp, keep_roles, blockIdx.y, blockIdx.x * P.ysc);
+}
+
+// ---------------------------------------------------------------------------
+// Ensemble phase kernels: block b takes items b, b + gridDim.x, ... of the
+// packed order (every group's items, group after group); see chgroup.cuh.
+__device__ __forceinline__ int item_group(const int* __restrict__ start, int ng, int item) {
+  int k = 0;
+  while (k + 1 < ng && start[k + 1] <= item) ++k;
+  return k;
+}
+
+template <bool NOISE>
+__global__ void __launch_bounds__(kT* kBY) ens_rhs_ff_kernel(const FFStep* __restrict__ steps,
+                                                             const int* __restrict__ order,
+                                                             const int* __restrict__ start, int ng, int nitems,
+                                                             int parity) {
+  __shared__ RhsSmem<NOISE> sh;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int k = item_group(start, ng, it);
+    const FFStep P = steps[order[k]];
+    const int idx = it - start[k], tpz = P.tx * P.ty;
+    const int z = idx / tpz, rem = idx - z * tpz, by = rem / P.tx, bx = rem - by * P.tx;
+    const int c = P.cur0 ^ parity;
+    if (NOISE && P.noise) {
+      if (P.iso) rhs_ff_tile<true, NOISE>(sh, P, P.st[c], P.st[1 - c], z, bx, by);
+      else rhs_ff_tile<false, NOISE>(sh, P, P.st[c], P.st[1 - c], z, bx, by);
+    } else {
+      // tiles without forcing: the NOISE branch of the tile is compiled out
+      if (P.iso) rhs_ff_tile<true, false>(*reinterpret_cast<RhsSmem<false>*>(&sh), P, P.st[c], P.st[1 - c], z, bx, by);
+      else rhs_ff_tile<false, false>(*reinterpret_cast<RhsSmem<false>*>(&sh), P, P.st[c], P.st[1 - c], z, bx, by);
+    }
+    __syncthreads();  // the next item reuses the shared tiles
+  }
+}
+
+__global__ void __launch_bounds__(kXThreads, 7) ens_x_ff_kernel(const FFStep* __restrict__ steps,
+                                                                const int* __restrict__ order,
+                                                                const int* __restrict__ start, int ng, int nitems) {
+  extern __shared__ float sm[];
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int k = item_group(start, ng, it);
+    const FFStep P = steps[order[k]];
+    x_solve_rows(sm, P, (it - start[k]) * P.xs);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kYThreads, 2) ens_y_ff_kernel(const FFStep* __restrict__ steps,
+                                                                const int* __restrict__ order,
+                                                                const int* __restrict__ start, int ng, int nitems,
+                                                                int parity) {
+  extern __shared__ float sm[];
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int k = item_group(start, ng, it);
+    const FFStep P = steps[order[k]];
+    const int idx = it - start[k], nstrip = (P.nx + P.ysc - 1) / P.ysc;
+    const int z = idx / nstrip, col0 = (idx - z * nstrip) * P.ysc, c = P.cur0 ^ parity;
+    y_solve_cols(sm, P, P.st[c], P.st[1 - c], 0, z, col0);
+    __syncthreads();
+  }
+}
+
 }  // namespace
-
-void launch_ch_rhs_ff(const double* cn, const double* cp, float* rhi, float* rlo, double* cbar, int nx, int ny, int G,
-                      const FFConst& k, const float2* glff, const double* noise, double nkx, double nky,
-                      cudaStream_t st) {
-  const dim3 grid(ceil_div(nx, kT), ceil_div(ny, kT), G), block(kT, kBY);
-  const bool iso = k.rho.x == 1.f && k.rho.y == 0.f;
-  if (noise && iso)
-    ch_rhs_ff_kernel<true, true><<<grid, block, 0, st>>>(cn, cp, rhi, rlo, nx, ny, G, k.rho, k.kap, glff, k.k1, k.k2,
-                                                         cbar, noise, nkx, nky);
-  else if (noise)
-    ch_rhs_ff_kernel<false, true><<<grid, block, 0, st>>>(cn, cp, rhi, rlo, nx, ny, G, k.rho, k.kap, glff, k.k1, k.k2,
-                                                          cbar, noise, nkx, nky);
-  else if (iso)
-    ch_rhs_ff_kernel<true><<<grid, block, 0, st>>>(cn, cp, rhi, rlo, nx, ny, G, k.rho, k.kap, glff, k.k1, k.k2, cbar);
-  else
-    ch_rhs_ff_kernel<false><<<grid, block, 0, st>>>(cn, cp, rhi, rlo, nx, ny, G, k.rho, k.kap, glff, k.k1, k.k2, cbar);
-}
-
-void launch_resid_ff(const float* fhi, const float* flo, const float* y1, const float* t1, float* x0, float* rho,
-                     int ld, int nsys, int n, const DirView<float>& D, const float2* aff, int Z, size_t fz, size_t ybz,
-                     cudaStream_t st) {
-  ch_resid_ff_kernel<<<dim3(ceil_div(nsys, kT), ceil_div(n, kT), Z), dim3(kT, kBY), 0, st>>>(fhi, flo, y1, t1, x0, rho,
-                                                                                           ld, nsys, n, D, aff, fz, ybz);
-}
-
-void launch_reduced_ff(const float* yb, const DirView<float>& D, float* tau, int nsys, size_t ybz, int Z,
-                       cudaStream_t st) {
-  spike_reduced_ff_kernel<<<dim3(ceil_div(nsys, kSolveThreads), 4 * D.P, Z), kSolveThreads, 0, st>>>(yb, D, tau, nsys,
-                                                                                                     ybz);
-}
-
-void launch_ch_xfinish_ff(const float* y1, const float* t1, const float* y2, const float* t2, const DirView<float>& D,
-                          float* whi, float* wlo, int nx, int ny, int G, cudaStream_t st) {
-  const dim3 grid(ceil_div(nx, kT), ceil_div(ny, kT), G), block(kT, kBY);
-  ch_xfinish_ff_kernel<<<grid, block, 0, st>>>(y1, t1, y2, t2, D, whi, wlo, nx, ny, G);
-}
-
-void launch_ch_update_ff(const float* y1, const float* t1, const float* y2, const float* t2, const DirView<float>& D,
-                         double* cn, double* cp, int nx, int ny, int G, int keep_roles, cudaStream_t st) {
-  ch_update_ff_kernel<<<dim3(ceil_div(nx, kSolveThreads), ny, G), kSolveThreads, 0, st>>>(y1, t1, y2, t2, D, cn, cp,
-                                                                                         nx, ny, keep_roles);
-}
 
 void launch_penta_refine_ff(double* x, float* work, int n, int batch, const float* fac32, const float2* coef_ff,
                             const float* s32, cudaStream_t st) {
@@ -1076,63 +921,102 @@ void launch_penta_refine_ff(double* x, float* work, int n, int batch, const floa
 
 // ---------------------------------------------------------------------------
 // Fused solves: shared-memory sizes, column counts and launches.
-namespace {
-size_t x_solve_smem(int n, int P) {
-  return sizeof(float) * ((size_t)kXS * (n + P) + 2 * (size_t)kXS * 4 * P);
+size_t x_solve_smem(int n, int P, int xs) {
+  return sizeof(float) * ((size_t)xs * (n + P) + 2 * (size_t)xs * 4 * P);
 }
-int y_pad(int m, int S) { return (((S - m * S) % 32) + 32) % 32; }
+int y_solve_pad(int m, int S) { return (((S - m * S) % 32) + 32) % 32; }
 size_t y_solve_smem(int n, int P, int S) {
   const int m = n / P;
-  return sizeof(float) * ((size_t)P * (m * S + y_pad(m, S)) + 2 * (size_t)S * (4 * P + 1));
+  return sizeof(float) * ((size_t)P * (m * S + y_solve_pad(m, S)) + 2 * (size_t)S * (4 * P + 1));
 }
 int log2_exact(int m) {
   int lg = 0;
   while ((1 << lg) < m) ++lg;
   return (1 << lg) == m ? lg : -1;
 }
+namespace {
 constexpr size_t kSmemMax = 227 * 1024;
 }  // namespace
 
-// Columns per block of the y solve: the widest strip that leaves room for two
-// blocks per SM, else the widest that fits at all.
-int y_solve_cols(int n, int P) {
-  for (int S = 8; S >= 1; S /= 2)
-    if (y_solve_smem(n, P, S) <= 100 * 1024) return S;
-  for (int S = 8; S >= 1; S /= 2)
-    if (y_solve_smem(n, P, S) <= kSmemMax) return S;
-  return 0;
+// Tile shapes of the fused solves: about `target` points per block (so that a
+// block's phases amortise their barriers on small grids), as a power of two;
+// the y solve takes at least 8 columns (32-byte row segments) and at most 32,
+// the x solve at most 32 rows; both shrink until two blocks fit on an SM (or,
+// failing that, one).  0: nothing fits.
+static int pow2_floor(int v) {
+  int p = 1;
+  while (2 * p <= v) p *= 2;
+  return p;
+}
+int x_solve_rows(int n, int P, int target) {
+  int xs = pow2_floor(std::min(32, std::max(2, target / n)));
+  while (xs > 1 && x_solve_smem(n, P, xs) > 100 * 1024) xs /= 2;
+  return x_solve_smem(n, P, xs) <= kSmemMax ? xs : 0;
+}
+int y_solve_cols(int n, int P, int target) {
+  int S = pow2_floor(std::min(32, std::max(8, target / n)));
+  while (S > 1 && y_solve_smem(n, P, S) > 100 * 1024) S /= 2;
+  return y_solve_smem(n, P, S) <= kSmemMax ? S : 0;
 }
 
 int prepare_solve_ff() {
   int rc = cuda_check(cudaFuncSetAttribute(x_solve_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax),
                       "mixed: shared-memory opt-in");
-  if (!rc) rc = cuda_check(cudaFuncSetAttribute(y_solve_ff_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax), "mixed: shared-memory opt-in");
-  if (!rc) rc = cuda_check(cudaFuncSetAttribute(y_solve_ff_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax), "mixed: shared-memory opt-in");
-  if (!rc) rc = cuda_check(cudaFuncSetAttribute(y_solve_ff_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax), "mixed: shared-memory opt-in");
-  if (!rc) rc = cuda_check(cudaFuncSetAttribute(y_solve_ff_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax), "mixed: shared-memory opt-in");
+  if (!rc) rc = cuda_check(cudaFuncSetAttribute(y_solve_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax), "mixed: shared-memory opt-in");
+  if (!rc) rc = cuda_check(cudaFuncSetAttribute(ens_x_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax), "mixed: shared-memory opt-in");
+  if (!rc) rc = cuda_check(cudaFuncSetAttribute(ens_y_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax), "mixed: shared-memory opt-in");
   return rc;
 }
 
 bool solve_ff_fits(int nx, int ny, int px, int py) {
-  return x_solve_smem(nx, px) <= kSmemMax && y_solve_cols(ny, py) > 0;
+  return x_solve_rows(nx, px, kFFTarget) > 0 && y_solve_cols(ny, py, kFFTarget) > 0;
 }
 
-void launch_x_solve_ff(const float* fhi, const float* flo, float* x0s, float* whi, float* wlo, int nx, int rows, int ny,
-                       const DirView<float>& D, const float2* aff, cudaStream_t st) {
-  x_solve_ff_kernel<<<ceil_div(rows, kXS), kXThreads, x_solve_smem(nx, D.P), st>>>(fhi, flo, x0s, whi, wlo, nx, rows,
-                                                                                   ny, D, aff, log2_exact(D.m));
+void launch_step_ff(const FFStep& P, int keep_roles, Prof* prof, cudaStream_t st) {
+  {
+    ProfScope ps(prof, kRhs, st);
+    const dim3 grid(P.tx, P.ty, P.G), block(kT, kBY);
+    if (P.noise && P.iso) ch_rhs_ff_kernel<true, true><<<grid, block, 0, st>>>(P, P.st[0], P.st[1]);
+    else if (P.noise) ch_rhs_ff_kernel<false, true><<<grid, block, 0, st>>>(P, P.st[0], P.st[1]);
+    else if (P.iso) ch_rhs_ff_kernel<true, false><<<grid, block, 0, st>>>(P, P.st[0], P.st[1]);
+    else ch_rhs_ff_kernel<false, false><<<grid, block, 0, st>>>(P, P.st[0], P.st[1]);
+  }
+  {
+    ProfScope ps(prof, kXSolve, st);
+    x_solve_ff_kernel<<<ceil_div((size_t)P.G * P.ny, P.xs), kXThreads, x_solve_smem(P.nx, P.X.P, P.xs), st>>>(P);
+  }
+  {
+    ProfScope ps(prof, kYSolve, st);
+    const dim3 grid(ceil_div(P.nx, P.ysc), P.G);
+    y_solve_ff_kernel<<<grid, kYThreads, y_solve_smem(P.ny, P.Y.P, P.ysc), st>>>(P, P.st[0], P.st[1], keep_roles);
+  }
 }
 
-void launch_y_solve_ff(const float* fhi, const float* flo, float* x0s, const double* cbar, double* cn, double* cp, int nx,
-                       int ny, int G, const DirView<float>& D, const float2* aff, int keep_roles, cudaStream_t st) {
-  const int S = y_solve_cols(ny, D.P), pad = y_pad(D.m, S), lg = log2_exact(D.m);
-  const dim3 grid(ceil_div(nx, S), G);
-  const size_t sh = y_solve_smem(ny, D.P, S);
-  switch (S) {
-    case 8: y_solve_ff_kernel<8><<<grid, kYThreads, sh, st>>>(fhi, flo, x0s, cbar, cn, cp, nx, ny, D, aff, pad, keep_roles, lg); break;
-    case 4: y_solve_ff_kernel<4><<<grid, kYThreads, sh, st>>>(fhi, flo, x0s, cbar, cn, cp, nx, ny, D, aff, pad, keep_roles, lg); break;
-    case 2: y_solve_ff_kernel<2><<<grid, kYThreads, sh, st>>>(fhi, flo, x0s, cbar, cn, cp, nx, ny, D, aff, pad, keep_roles, lg); break;
-    default: y_solve_ff_kernel<1><<<grid, kYThreads, sh, st>>>(fhi, flo, x0s, cbar, cn, cp, nx, ny, D, aff, pad, keep_roles, lg); break;
+int ens_phase_items(int phase, const FFStep& P) {
+  if (phase == 0) return P.tx * P.ty * P.G;
+  if (phase == 1) return (int)ceil_div((size_t)P.G * P.ny, P.xs);
+  return (int)ceil_div(P.nx, P.ysc) * P.G;
+}
+
+int ens_phase_occupancy(int phase, size_t smem) {
+  int b = 0;
+  if (phase == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ens_rhs_ff_kernel<true>, kT * kBY, 0);
+  else if (phase == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ens_x_ff_kernel, kXThreads, smem);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ens_y_ff_kernel, kYThreads, smem);
+  cudaGetLastError();
+  return b > 0 ? b : 1;
+}
+
+void launch_ens_phase_ff(int phase, const FFStep* steps, const int* order, const int* start, int ngroups, int nitems,
+                         int blocks, int parity, size_t smem, cudaStream_t st) {
+  if (nitems < 1 || blocks < 1) return;
+  if (phase == 0) {
+    if (smem) ens_rhs_ff_kernel<true><<<blocks, dim3(kT, kBY), 0, st>>>(steps, order, start, ngroups, nitems, parity);
+    else ens_rhs_ff_kernel<false><<<blocks, dim3(kT, kBY), 0, st>>>(steps, order, start, ngroups, nitems, parity);
+  } else if (phase == 1) {
+    ens_x_ff_kernel<<<blocks, kXThreads, smem, st>>>(steps, order, start, ngroups, nitems);
+  } else {
+    ens_y_ff_kernel<<<blocks, kYThreads, smem, st>>>(steps, order, start, ngroups, nitems, parity);
   }
 }
 

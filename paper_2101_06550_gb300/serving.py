@@ -3,12 +3,20 @@
 Requests (grid n, step count, gamma, seed) arrive over time.  Each is admitted
 into a slot of the ensemble group for its grid size as soon as a slot and HBM
 budget are free; all admitted simulations advance together (one graph-captured
-``ens_step`` per tick, every group on its own graph branch), so requests that
-arrive while others run join the running batch instead of waiting for it to
-drain.  A tick advances every active simulation by the smallest remaining step
-count (capped at ``chunk``), after which finished simulations are copied out
-and their slots compacted.  The thesis motivates the workload (batches of 2D
-simulations for growth-rate statistics, Sec. 7.3.2); it has no serving layer.
+``ens_step`` per tick: the packed phase launches of an FP32 + refinement
+ensemble, or one graph branch per group in FP64), so requests that arrive while
+others run join the running batch instead of waiting for it to drain.
+
+Two limits keep the tail short.  Admission stops while the admitted grid
+points already fill the GPU (``fill_points``; a request is always admitted when
+nothing runs), so a large request keeps most of the GPU instead of being
+shared among everything that arrived -- requests that would not speed up the
+batch wait in FIFO order.  A tick advances every active simulation by the
+smallest remaining step count, capped so that a tick lasts about
+``tick_ms`` by the measured per-point step time, so arrivals are admitted and
+finished results harvested promptly.  The thesis motivates the workload
+(batches of 2D simulations for growth-rate statistics, Sec. 7.3.2); it has no
+serving layer.
 
 This module is host-side scheduling only: all arithmetic runs in ``libchx.so``.
 """
@@ -47,12 +55,16 @@ class Server:
 
     def __init__(self, dt: float, dx: float, precision: int = PREC_F64, hbm_budget: int = 0, capacity: int = 16,
                  chunk: int = 100, keep_results: bool = True, device: str = "cuda",
-                 make_ic: Optional[Callable[[Request], object]] = None, autotune: bool = False):
+                 make_ic: Optional[Callable[[Request], object]] = None, autotune: bool = False,
+                 fill_points: int = 0, tick_ms: float = 0.0):
         import torch
 
         self.torch = torch
         self.dt, self.dx = dt, dx
         self.capacity, self.chunk = capacity, chunk
+        self.fill_points = fill_points  # 0: no limit on admitted grid points
+        self.tick_ms = tick_ms          # 0: ticks of up to `chunk` steps
+        self.ns_per_point = None        # measured step time per grid point (tick_ms)
         self.keep_results = keep_results
         self.device = device
         self.autotune = autotune
@@ -97,7 +109,12 @@ class Server:
             self.active.pop(g, None)
         return bool(idle)
 
+    def active_points(self) -> int:
+        return sum(r.n * r.n for reqs in self.active.values() for r in reqs)
+
     def try_admit(self, req: Request, now: float) -> bool:
+        if self.fill_points and self.busy() and self.active_points() + req.n * req.n > self.fill_points:
+            return False
         gid = self._group(req.n)
         if gid is None or len(self.active[gid]) >= self.capacity:
             return False
@@ -121,8 +138,19 @@ class Server:
         if not live:
             return []
         k = min(min(r.remaining for r in live), self.chunk)
+        if self.tick_ms and self.ns_per_point:
+            per_step_ms = self.ns_per_point * sum(r.n * r.n for r in live) * 1e-6
+            k = max(1, min(k, int(self.tick_ms / max(per_step_ms, 1e-6))))
+            if k > 1 and k % 2:
+                k -= 1  # whole captured step pairs
+        t_tick = time.perf_counter()
         self.ens.step(k, stream=self.stream)
         self.ticks += 1
+        if self.tick_ms:
+            self.stream.synchronize()
+            pts = sum(r.n * r.n for r in live) * k
+            est = (time.perf_counter() - t_tick) * 1e9 / max(pts, 1)
+            self.ns_per_point = est if self.ns_per_point is None else 0.7 * self.ns_per_point + 0.3 * est
         finished = []
         for gid, reqs in self.active.items():
             for r in reqs:

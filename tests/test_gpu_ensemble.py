@@ -84,29 +84,79 @@ def test_ensemble_f32_refine_odd_rows_straddle_slots():
         assert _rel(out.cpu().numpy().reshape(n, n), ref) <= 1e-6, (s, g)
 
 
-def test_ensemble_result_independent_of_the_mix_bit_exact():
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ensemble_result_independent_of_the_mix(precision):
+    # the same simulation alone and among others of other sizes and gammas gives
+    # the same bits: FP32 + refinement ensembles step all groups with shared
+    # persistent phase launches, whose work items never mix simulations
     chx = _chx()
     n, dt, steps = 64, 1e-3, 9
     target = torch.from_numpy(_ic(11, n)).to(DEV)
-    ens1 = chx.Ensemble(dt)
+    ens1 = chx.Ensemble(dt, precision)
     g1 = ens1.group_create(n, n * DX, 0.01, 8)
     ens1.load(g1, 0, target, None, 0.013)
     ens1.set_active(g1, 1)
     ens1.step(steps)
     a = torch.empty(n * n, dtype=torch.float64, device=DEV)
     ens1.read(g1, 0, a)
-    ens2 = chx.Ensemble(dt)
+    ens2 = chx.Ensemble(dt, precision)
     g2 = ens2.group_create(n, n * DX, 0.01, 8)
+    g3 = ens2.group_create(96, 96 * DX, 0.01, 3)
     for s in range(6):
         if s == 3:
             ens2.load(g2, s, target, None, 0.013)
         else:
             ens2.load(g2, s, torch.from_numpy(_ic(50 + s, n)).to(DEV), None, 0.005 + 0.003 * s)
+    for s in range(3):
+        ens2.load(g3, s, torch.from_numpy(_ic(70 + s, 96)).to(DEV), None, 0.02)
     ens2.set_active(g2, 6)
+    ens2.set_active(g3, 3)
     ens2.step(steps)
     b = torch.empty(n * n, dtype=torch.float64, device=DEV)
     ens2.read(g2, 3, b)
+    ens1.sync_status()
+    ens2.sync_status()
     assert torch.equal(a, b)
+
+
+def test_ensemble_schedule_tuning_changes_no_result():
+    # the packed schedule (group order, y strip width, blocks per SM) only moves
+    # work items between blocks: a tuned ensemble and an untuned one agree bit
+    # for bit, and the tuner leaves every simulation where it was
+    chx = _chx()
+    dt = 1e-3
+    sizes = [(64, 4), (128, 2), (96, 3)]
+
+    def make():
+        ens = chx.Ensemble(dt, chx.PREC_F32_REFINE)
+        gids = []
+        for k, (n, cnt) in enumerate(sizes):
+            g = ens.group_create(n, n * DX, 0.01, cnt)
+            for s in range(cnt):
+                ens.load(g, s, torch.from_numpy(_ic(100 + 10 * k + s, n)).to(DEV), None, 0.005 + 0.005 * s)
+            ens.set_active(g, cnt)
+            gids.append(g)
+        return ens, gids
+
+    e1, g1 = make()
+    e2, g2 = make()
+    e1.step(3)
+    e2.step(3)
+    sched = e2.tune_schedule(2)
+    assert sched["order"] in (0, 1) and sched["points_per_item"] in (2048, 4096, 8192) and min(sched["blocks"]) >= 1
+    info = e2.schedule_info()
+    assert info["items"][0] == sum(cnt * ((n + 31) // 32) ** 2 for n, cnt in sizes)
+    e1.step(5)
+    e2.step(5)
+    for (n, cnt), a, b in zip(sizes, g1, g2):
+        for s in range(cnt):
+            x = torch.empty(n * n, dtype=torch.float64, device=DEV)
+            y = torch.empty(n * n, dtype=torch.float64, device=DEV)
+            e1.read(a, s, x)
+            e2.read(b, s, y)
+            assert torch.equal(x, y), (n, s)
+    e1.sync_status()
+    e2.sync_status()
 
 
 def test_ensemble_matches_oracle_and_slot_move():
@@ -149,23 +199,56 @@ def test_ensemble_autotune_keeps_state_and_budget_admission():
     assert ens.bytes_used <= 64 << 20
 
 
-def test_server_continuous_batching_results_match_alone():
+@pytest.mark.parametrize("precision", [0, 1])
+def test_server_continuous_batching_results_match_alone(precision):
+    # FP64 and FP32 + refinement servers: requests overlap on the device, each
+    # result matches the request run alone (single plan: 1e-11 in FP64, the
+    # FP32 path's 1e-6 target), and a request served alone gives the same bits
+    # as in the mix
     from paper_2101_06550_gb300 import serving
 
     dt = 1e-3
     reqs = serving.poisson_requests(12, rate=400.0, seed=3, n_min=32, n_max=128, steps_lo=10, steps_hi=60)
-    srv = serving.Server(dt, DX, capacity=4, chunk=16, make_ic=lambda r: torch.from_numpy(_ic(r.seed, r.n)).to(DEV))
+    mk = lambda r: torch.from_numpy(_ic(r.seed, r.n)).to(DEV)  # noqa: E731
+    srv = serving.Server(dt, DX, precision=precision, capacity=4, chunk=16, make_ic=mk)
     stats = serving.serve(reqs, srv, time_limit=120)
     assert stats["completed"] == len(reqs)
     assert stats["p50_s"] <= stats["p99_s"]
     # requests overlapped on the device: more requests than ticks would allow one at a time
     assert srv.ticks < sum(-(-r.steps // 16) for r in reqs)
+    tol = 1e-11 if precision == 0 else 1e-6
     for r in reqs:
         got = r.result.numpy().reshape(r.n, r.n)
-        assert _rel(got, _alone(r.n, r.gamma, dt, r.seed, r.steps)) <= 1e-11, r
-    # the same request alone in a fresh server gives the same bits as in the mix
+        assert _rel(got, _alone(r.n, r.gamma, dt, r.seed, r.steps, precision)) <= tol, r
     r0 = reqs[5]
     solo = serving.Request(rid=0, n=r0.n, steps=r0.steps, gamma=r0.gamma, seed=r0.seed, arrival=0.0)
-    srv2 = serving.Server(dt, DX, capacity=4, chunk=16, make_ic=lambda r: torch.from_numpy(_ic(r.seed, r.n)).to(DEV))
+    srv2 = serving.Server(dt, DX, precision=precision, capacity=4, chunk=16, make_ic=mk)
     serving.serve([solo], srv2)
     assert torch.equal(solo.result, r0.result)
+
+
+def test_server_fill_admission_and_time_bounded_ticks():
+    # admission stops while the admitted grid points fill the GPU (a request is
+    # still admitted when nothing runs), ticks are cut to about tick_ms, and
+    # every result still matches its request run alone
+    from paper_2101_06550_gb300 import serving
+
+    dt = 1e-3
+    reqs = serving.poisson_requests(10, rate=1000.0, seed=5, n_min=64, n_max=128, steps_lo=20, steps_hi=40)
+    mk = lambda r: torch.from_numpy(_ic(r.seed, r.n)).to(DEV)  # noqa: E731
+    fill = 2 * 128 * 128
+    srv = serving.Server(dt, DX, precision=1, capacity=8, chunk=16, make_ic=mk, fill_points=fill, tick_ms=0.05)
+    peak = [0]
+    tick = srv.tick
+
+    def watched(clock):
+        peak[0] = max(peak[0], srv.active_points())
+        return tick(clock)
+
+    srv.tick = watched
+    stats = serving.serve(reqs, srv, time_limit=120)
+    assert stats["completed"] == len(reqs)
+    assert 0 < peak[0] <= fill
+    for r in reqs:
+        got = r.result.numpy().reshape(r.n, r.n)
+        assert _rel(got, _alone(r.n, r.gamma, dt, r.seed, r.steps, 1)) <= 1e-6, r
