@@ -381,18 +381,21 @@ extern "C" void chx_plan_destroy(void* plan) {
 }
 
 // ---------------------------------------------------------------------------
-// FP64 FMA throughput: eight independent chains per thread, so the FP64 pipe
-// rather than the FMA latency sets the rate; the result feeds a sink only if
-// it takes an impossible value, which keeps the chains live.
+// FP64 FMA throughput: sixteen independent chains per thread and a loop body
+// of 64 FMAs, so the FP64 pipe rather than the FMA latency or the loop's own
+// instructions sets the rate; the result feeds a sink only if it takes an
+// impossible value, which keeps the chains live.
 namespace {
-constexpr int kRateChains = 8, kRateIters = 4096, kRateThreads = 256, kRateBlocksPerSM = 8;
+constexpr int kRateChains = 16, kRateUnroll = 4, kRateIters = 1024, kRateThreads = 256, kRateBlocksPerSM = 8;
 __global__ void __launch_bounds__(kRateThreads) fp64_fma_rate_kernel(double* sink, double mul, double add) {
   double v[kRateChains];
 #pragma unroll
   for (int k = 0; k < kRateChains; ++k) v[k] = 1e-3 * (threadIdx.x + k);
   for (int i = 0; i < kRateIters; ++i) {
 #pragma unroll
-    for (int k = 0; k < kRateChains; ++k) v[k] = fma(v[k], mul, add);
+    for (int j = 0; j < kRateUnroll; ++j)
+#pragma unroll
+      for (int k = 0; k < kRateChains; ++k) v[k] = fma(v[k], mul, add);
   }
   double t = 0;
 #pragma unroll
@@ -429,7 +432,7 @@ extern "C" int chx_fp64_fma_rate(double* gops_out, void* stream) {
   cudaEventDestroy(b);
   cudaFree(sink);
   if (rc) return rc;
-  const double fmas = (double)blocks * kRateThreads * kRateChains * kRateIters;
+  const double fmas = (double)blocks * kRateThreads * kRateChains * kRateUnroll * kRateIters;
   *gops_out = ms > 0.f ? fmas / (ms * 1e-3) / 1e9 : 0.0;
   return CHX_OK;
 }

@@ -760,7 +760,7 @@ int dir_alloc(SpikeDir* D, int n, int P, int slots) {
       (rc = dev_alloc(&D->d_rinv, kk)) || (rc = dev_alloc(&D->d_a32, slots)) || (rc = dev_alloc(&D->d_aff, slots)) ||
       (rc = dev_alloc(&D->d_lu32, m4)) || (rc = dev_alloc(&D->d_vw32, m4)) || (rc = dev_alloc(&D->d_rinv32, kk)) ||
       (rc = dev_alloc(&D->d_vwlo, m4)) || (rc = dev_alloc(&D->d_rinvlo, kk)) || (rc = dev_alloc(&D->d_rb32, kk)) ||
-      (rc = dev_alloc(&D->d_rblo, kk)))
+      (rc = dev_alloc(&D->d_rblo, kk)) || (rc = dev_alloc(&D->d_vw4, m4 / 4)) || (rc = dev_alloc(&D->d_vw4lo, m4 / 4)))
     return rc;
   return CHX_OK;
 }
@@ -820,6 +820,14 @@ int dir_set(SpikeDir* D, int z, double a) {
       (rc = put_lo(D->d_vwlo + z * m4, vw)) || (rc = put_lo(D->d_rinvlo + z * kk, rinv)) ||
       (rc = put(D->d_rb32 + z * kk, rb)) || (rc = put_lo(D->d_rblo + z * kk, rb)))
     return rc;
+  {
+    const int m = D->m;
+    std::vector<double> v4(m4);  // [r][k] = spike k at row r
+    for (int r = 0; r < m; ++r)
+      for (int k = 0; k < 4; ++k) v4[(size_t)r * 4 + k] = vw[(size_t)k * m + r];
+    if ((rc = put((float*)(D->d_vw4 + z * (m4 / 4)), v4)) || (rc = put_lo((float*)(D->d_vw4lo + z * (m4 / 4)), v4)))
+      return rc;
+  }
   return cuda_check(cudaMemcpy(D->d_aff + z, &aff, sizeof(float2), cudaMemcpyHostToDevice), "ch: upload");
 }
 
@@ -841,16 +849,18 @@ int dir_replicate(SpikeDir* D) {
     if (!rc) rc = cuda_check(cudaMemcpy(D->d_rinvlo + z * kk, D->d_rinvlo, kk * 4, cudaMemcpyDeviceToDevice), "ch: replicate");
     if (!rc) rc = cuda_check(cudaMemcpy(D->d_rb32 + z * kk, D->d_rb32, kk * 4, cudaMemcpyDeviceToDevice), "ch: replicate");
     if (!rc) rc = cuda_check(cudaMemcpy(D->d_rblo + z * kk, D->d_rblo, kk * 4, cudaMemcpyDeviceToDevice), "ch: replicate");
+    if (!rc) rc = cuda_check(cudaMemcpy(D->d_vw4 + z * (m4 / 4), D->d_vw4, m4 * 4, cudaMemcpyDeviceToDevice), "ch: replicate");
+    if (!rc) rc = cuda_check(cudaMemcpy(D->d_vw4lo + z * (m4 / 4), D->d_vw4lo, m4 * 4, cudaMemcpyDeviceToDevice), "ch: replicate");
   }
   return rc;
 }
 
 int dir_move(SpikeDir* D, int from, int to, cudaStream_t st) {
   const size_t m4 = 4 * (size_t)D->m, kk = (size_t)16 * D->P * D->P;
-  struct { void* base; size_t esz, per; } a[13] = {
+  struct { void* base; size_t esz, per; } a[15] = {
       {D->d_a, 8, 1}, {D->d_lu, 8, m4}, {D->d_vw, 8, m4}, {D->d_rinv, 8, kk}, {D->d_a32, 4, 1},
       {D->d_aff, 8, 1}, {D->d_lu32, 4, m4}, {D->d_vw32, 4, m4}, {D->d_rinv32, 4, kk}, {D->d_vwlo, 4, m4},
-      {D->d_rinvlo, 4, kk}, {D->d_rb32, 4, kk}, {D->d_rblo, 4, kk}};
+      {D->d_rinvlo, 4, kk}, {D->d_rb32, 4, kk}, {D->d_rblo, 4, kk}, {D->d_vw4, 4, m4}, {D->d_vw4lo, 4, m4}};
   for (auto& x : a) {
     const size_t b = x.esz * x.per;
     int rc = cuda_check(cudaMemcpyAsync((char*)x.base + to * b, (char*)x.base + from * b, b, cudaMemcpyDeviceToDevice, st),
@@ -864,6 +874,7 @@ void free_dir(SpikeDir* D) {
   cudaFree(D->d_a); cudaFree(D->d_lu); cudaFree(D->d_vw); cudaFree(D->d_rinv);
   cudaFree(D->d_a32); cudaFree(D->d_aff); cudaFree(D->d_lu32); cudaFree(D->d_vw32); cudaFree(D->d_rinv32);
   cudaFree(D->d_vwlo); cudaFree(D->d_rinvlo); cudaFree(D->d_rb32); cudaFree(D->d_rblo);
+  cudaFree(D->d_vw4); cudaFree(D->d_vw4lo);
   *D = SpikeDir();
 }
 
@@ -872,12 +883,12 @@ DirView<T> view(const SpikeDir& D, int spp);
 template <>
 DirView<double> view<double>(const SpikeDir& D, int spp) {
   return DirView<double>{D.d_a,  D.d_lu,  D.d_vw,  D.d_rinv, D.m,    D.P,   spp,
-                         D.band, 1.0f / (float)D.m, nullptr, nullptr,  nullptr, nullptr, 0, 0};
+                         D.band, 1.0f / (float)D.m, nullptr, nullptr,  nullptr, nullptr, nullptr, nullptr, 0, 0};
 }
 template <>
 DirView<float> view<float>(const SpikeDir& D, int spp) {
   return DirView<float>{D.d_a32, D.d_lu32, D.d_vw32, D.d_rinv32, D.m,     D.P,    spp,     D.band,
-                        1.0f / (float)D.m, D.d_vwlo, D.d_rinvlo, D.d_rb32, D.d_rblo, D.plo, D.phi};
+                        1.0f / (float)D.m, D.d_vwlo, D.d_rinvlo, D.d_rb32, D.d_rblo, D.d_vw4, D.d_vw4lo, D.plo, D.phi};
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -1055,7 +1066,7 @@ int group_init(ChGroup* g, int nx, int ny, double lx, double ly, double gamma, d
   {
     auto dir_bytes = [&](const SpikeDir& D) {
       const size_t m4 = 4 * (size_t)D.m, kk = (size_t)16 * D.P * D.P;
-      return (size_t)G * (8 + 4 + 8 + m4 * (8 + 8 + 4 + 4 + 4) + kk * (8 + 4 + 4 + 4 + 4));
+      return (size_t)G * (8 + 4 + 8 + m4 * (8 + 8 + 4 + 4 + 4 + 4 + 4) + kk * (8 + 4 + 4 + 4 + 4));
     };
     g->factor_bytes = dir_bytes(g->X) + dir_bytes(g->Y) + (size_t)G * (sizeof(double) + sizeof(float2));
   }

@@ -38,6 +38,10 @@ struct SpikeDir {
   // that consecutive output rows q read consecutive words; high and low floats
   float* d_rb32 = nullptr;
   float* d_rblo = nullptr;
+  // the four spikes of each row packed (V0, V1, W0, W1), high and low floats,
+  // so the fused solves fetch a row's spikes with one 128-bit load
+  float4* d_vw4 = nullptr;
+  float4* d_vw4lo = nullptr;
   // rows [plo, phi) of every slot's segment block where the four spikes'
   // magnitudes sum to at most 1: the first mixed-precision solve forms x0 there
   // with plain FP32 arithmetic (exact accumulation elsewhere)
@@ -58,6 +62,8 @@ struct DirView {
   const float* rinvlo;
   const float* rb;      // FP32 views: rinv by block offset, high and low floats
   const float* rblo;
+  const float4* vw4;    // FP32 views: packed spikes per row, high and low floats
+  const float4* vw4lo;
   int plo, phi;         // FP32 views: rows of plain FP32 spike correction (SpikeDir)
 };
 

@@ -149,24 +149,26 @@ __global__ void __launch_bounds__(kT* kBY) ch_rhs_ff_kernel(FFStep P, const doub
   rhs_ff_tile<kIso, NOISE>(sh, P, cn, cp, blockIdx.z, blockIdx.x, blockIdx.y);
 }
 
-// x0 = y - (V0 ta + V1 tb + W0 tc + W1 td) for row r of a segment, rounded once
-// to float.  Near the segment ends the four spike terms are several times
+// x0 = y - (V0 ta + V1 tb + W0 tc + W1 td) for one row of a segment, rounded once
+// to float: vh / vl are the row's packed spikes (V0, V1, W0, W1) as high and
+// low floats, tn = (ta, tb) the next segment's first two reduced unknowns and
+// tp = (tc, td) the previous segment's last two.  Near the segment ends the four spike terms are several times
 // larger than x0 (|V| up to ~6 at a' = 1.9e4) and cancel, so a plain FP32
 // chain would leave several ulps of the terms in x0.  Here every spike is a
 // double-float pair (vw + vwlo), the high products are exact (TwoProd), the
 // running sum is carried as an unevaluated pair (TwoSum), and only the
 // low-part products (~2^-24 of the terms) are rounded in FP32.
-__device__ __forceinline__ float corr_exact(float y, const float* __restrict__ vw, const float* __restrict__ vwlo,
-                                            int m, int r, float ta, float tb, float tc, float td) {
-  const float t[4] = {ta, tb, tc, td};
+__device__ __forceinline__ float corr_exact(float y, float4 vh, float4 vl, float2 tn, float2 tp) {
+  const float t[4] = {tn.x, tn.y, tp.x, tp.y};
+  const float h[4] = {vh.x, vh.y, vh.z, vh.w};
+  const float l[4] = {vl.x, vl.y, vl.z, vl.w};
   float s = y, e = 0.f;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const float vh = __ldg(&vw[k * m + r]), vl = __ldg(&vwlo[k * m + r]);
-    const ff p = two_prod(vh, t[k]);
+    const ff p = two_prod(h[k], t[k]);
     const ff q = two_sum(s, -p.hi);
     s = q.hi;
-    e = e + (q.lo - fmaf(vl, t[k], p.lo));
+    e = e + (q.lo - fmaf(l[k], t[k], p.lo));
   }
   return s + e;
 }
@@ -175,16 +177,17 @@ __device__ __forceinline__ float corr_exact(float y, const float* __restrict__ v
 // spike terms are large and cancel, and the plain FP32 chain in the rows
 // [plo, phi) where the spikes' magnitudes sum to at most 1 (there the rounding
 // of the terms is no larger than that of x0 itself).
-__device__ __forceinline__ float corr_first(float y, const float* __restrict__ vw, const float* __restrict__ vwlo,
-                                            int m, int r, int plo, int phi, float ta, float tb, float tc, float td) {
+__device__ __forceinline__ float corr_first(float y, const float4* __restrict__ vw4, const float4* __restrict__ vw4lo,
+                                            int r, int plo, int phi, float2 tn, float2 tp) {
+  const float4 v = __ldg(&vw4[r]);
   if (r >= plo && r < phi) {
-    float c = __ldg(&vw[r]) * ta;
-    c = fmaf(__ldg(&vw[m + r]), tb, c);
-    c = fmaf(__ldg(&vw[2 * m + r]), tc, c);
-    c = fmaf(__ldg(&vw[3 * m + r]), td, c);
+    float c = v.x * tn.x;
+    c = fmaf(v.y, tn.y, c);
+    c = fmaf(v.z, tp.x, c);
+    c = fmaf(v.w, tp.y, c);
     return y - c;
   }
-  return corr_exact(y, vw, vwlo, m, r, ta, tb, tc, td);
+  return corr_exact(y, v, __ldg(&vw4lo[r]), tn, tp);
 }
 
 // A x0 for the ADI row (a, -4a, 1 + 6a, -4a, a): x0 + a * delta^4 x0, the fourth
@@ -480,52 +483,59 @@ __device__ __forceinline__ void seg_sweep32(float* x, int m, float a, const floa
   yb4[3] = x[(m - 1) * STR];
 }
 
-// Block offset of step t of the banded reduced product (t in [0, nb)):
-// offsets -band..band around the row's own segment, or all P when nb == P.
-__device__ __forceinline__ int red_offset(int t, int nb, int band, int P) {
-  if (nb == P) return t;
-  const int d = t - band;
-  return d < 0 ? d + P : d;
-}
-
 // Row q of tau = Rinv yb for one system (yb: its 4P boundary values in shared
-// memory), with Rinv by block offset (rb, rbl: see SpikeDir::d_rb32).  FF:
+// memory, 16-byte aligned), with Rinv by block offset (rb, rbl: see
+// SpikeDir::d_rb32), over the band's block offsets -band..band (or all P) with
+// pointers advanced per block.  FF:
 // double-float (exact products, pair-carried sum, one final rounding);
 // otherwise plain FP32 FMAs.
 template <bool FF>
 __device__ __forceinline__ float reduced_row(const float* yb, int q, const float* __restrict__ rb,
                                              const float* __restrict__ rbl, int P, int band) {
-  const int K = 4 * P, sq = q >> 2;
+  const int K = 4 * P;
   const int nb = 2 * band + 1 < P ? 2 * band + 1 : P;
+  int d = nb == P ? 0 : P - band;  // block offset of the first step (mod P)
+  int sb = (q >> 2) + d;
+  if (sb >= P) sb -= P;
+  const size_t stepw = 4 * (size_t)K;
+  const float* rp = rb + d * stepw + q;
+  const float* rl = FF ? rbl + d * stepw + q : nullptr;
   float s = 0.f, e = 0.f;
   for (int t = 0; t < nb; ++t) {
-    const int d = red_offset(t, nb, band, P);
-    int sb = sq + d;
-    sb = sb >= P ? sb - P : sb;
+    const float4 v = *reinterpret_cast<const float4*>(yb + 4 * sb);
+    const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const float v = yb[4 * sb + u];
-      const size_t w = (size_t)(d * 4 + u) * K + q;
       if (FF) {
-        const ff p = two_prod(__ldg(&rb[w]), v);
+        const ff p = two_prod(__ldg(rp + u * K), vv[u]);
         const ff c = two_sum(s, p.hi);
         s = c.hi;
-        e = e + (c.lo + fmaf(__ldg(&rbl[w]), v, p.lo));
+        e = e + (c.lo + fmaf(__ldg(rl + u * K), vv[u], p.lo));
       } else {
-        s = fmaf(__ldg(&rb[w]), v, s);
+        s = fmaf(__ldg(rp + u * K), vv[u], s);
       }
     }
+    if (++d == P) {
+      d = 0;
+      rp -= (P - 1) * stepw;
+      if (FF) rl -= (P - 1) * stepw;
+    } else {
+      rp += stepw;
+      if (FF) rl += stepw;
+    }
+    if (++sb == P) sb = 0;
   }
   return s + e;
 }
 
-// Plain FP32 spike correction of row r of a segment: V0 ta + V1 tb + W0 tc + W1 td.
-__device__ __forceinline__ float spikes32(const float* __restrict__ vw, int m, int r, float ta, float tb, float tc,
-                                          float td) {
-  float c = __ldg(&vw[r]) * ta;
-  c = fmaf(__ldg(&vw[m + r]), tb, c);
-  c = fmaf(__ldg(&vw[2 * m + r]), tc, c);
-  return fmaf(__ldg(&vw[3 * m + r]), td, c);
+// Plain FP32 spike correction of one row of a segment: V0 ta + V1 tb + W0 tc + W1 td
+// (packed spikes as in corr_exact).
+__device__ __forceinline__ float spikes32(const float4* __restrict__ vw4, int r, float2 tn, float2 tp) {
+  const float4 v = __ldg(&vw4[r]);
+  float c = v.x * tn.x;
+  c = fmaf(v.y, tn.y, c);
+  c = fmaf(v.z, tp.x, c);
+  return fmaf(v.w, tp.y, c);
 }
 
 constexpr int kXThreads = 128;  // x solve: threads per block (rows per block: FFStep::xs)
@@ -567,7 +577,7 @@ __device__ __forceinline__ void x_solve_rows(float* sm, const FFStep& PS, int ro
   const int m = D.m, P = D.P, K = 4 * P, Ls = n + P;
   float* X = sm;
   const int XS = PS.xs;
-  float* yb = X + XS * Ls;
+  float* yb = X + ((XS * Ls + 3) & ~3);  // 16-byte aligned: boundary values by float4
   float* tau = yb + XS * K;
   const SegMap sg{m, lgm, D.rm};
   const int ns = rows - row0 < XS ? rows - row0 : XS;
@@ -604,27 +614,31 @@ __device__ __forceinline__ void x_solve_rows(float* sm, const FFStep& PS, int ro
   __syncthreads();
   for (int s = 0; s < ns; ++s) {
     const int slot = (row0 + s) / ny;
-    const float* vw = D.vw + (size_t)slot * 4 * m;
-    const float* vwl = D.vwlo + (size_t)slot * 4 * m;
+    const float4* vw4 = D.vw4 + (size_t)slot * m;
+    const float4* vw4l = D.vw4lo + (size_t)slot * m;
     const float* ts = tau + s * K;
-    float* xs = X + s * Ls;
+    const float* xs = X + s * Ls;
     float* dst = x0s + (size_t)(row0 + s) * n;
 #pragma unroll 2
     for (int e = tid; e < n; e += kXThreads) {
       int p, r;
       sg.map(e, p, r);
       const int pn = p + 1 == P ? 0 : p + 1, pp = p == 0 ? P - 1 : p - 1;
-      dst[e] = corr_first(xs[e + p], vw, vwl, m, r, D.plo, D.phi, ts[4 * pn], ts[4 * pn + 1], ts[4 * pp + 2],
-                          ts[4 * pp + 3]);
+      const float2 tn = *reinterpret_cast<const float2*>(ts + 4 * pn);
+      const float2 tp = *reinterpret_cast<const float2*>(ts + 4 * pp + 2);
+      dst[e] = corr_first(xs[e + p], vw4, vw4l, r, D.plo, D.phi, tn, tp);
     }
   }
   __syncthreads();
-  // rho = f - A x0 into shared memory (x0 and its neighbours from the scratch)
+  // rho = f - A x0 into shared memory (x0 and its neighbours from the scratch;
+  // the periodic wrap only at a row's first and last two points)
   for (int s = 0; s < ns; ++s) {
     const int slot = (row0 + s) / ny;
     const ff a = ffc(aff[slot]);
     const size_t ro = (size_t)(row0 + s) * n;
     const float* x0 = x0s + ro;
+    const float* fh0 = fhi + ro;
+    const float* fl0 = flo + ro;
     float* xs = X + s * Ls;
     for (int e1 = tid; e1 < n; e1 += 2 * kXThreads) {
       float fh[2], fl[2], w[2][5];
@@ -635,10 +649,16 @@ __device__ __forceinline__ void x_solve_rows(float* sm, const FFStep& PS, int ro
 #pragma unroll
         for (int d = 0; d < 5; ++d) w[u][d] = 0.f;
         if (e < n) {
-          fh[u] = fhi[ro + e];
-          fl[u] = flo[ro + e];
+          fh[u] = fh0[e];
+          fl[u] = fl0[e];
+          if (e >= 2 && e < n - 2) {
+            const float* q = x0 + e;
 #pragma unroll
-          for (int d = 0; d < 5; ++d) w[u][d] = x0[wrap2(e + d - 2, n)];
+            for (int d = 0; d < 5; ++d) w[u][d] = q[d - 2];
+          } else {
+#pragma unroll
+            for (int d = 0; d < 5; ++d) w[u][d] = x0[wrap2(e + d - 2, n)];
+          }
         }
       }
 #pragma unroll
@@ -665,14 +685,17 @@ __device__ __forceinline__ void x_solve_rows(float* sm, const FFStep& PS, int ro
   __syncthreads();
   for (int s = 0; s < ns; ++s) {
     const int slot = (row0 + s) / ny;
-    const float* vw = D.vw + (size_t)slot * 4 * m;
+    const float4* vw4 = D.vw4 + (size_t)slot * m;
     const float* ts = tau + s * K;
     const float* xs = X + s * Ls;
     const size_t ro = (size_t)(row0 + s) * n;
+    const float* x0 = x0s + ro;
+    float* wh = whi + ro;
+    float* wl = wlo + ro;
     for (int e1 = tid; e1 < n; e1 += 4 * kXThreads) {
       float xv[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) xv[u] = e1 + u * kXThreads < n ? x0s[ro + e1 + u * kXThreads] : 0.f;
+      for (int u = 0; u < 4; ++u) xv[u] = e1 + u * kXThreads < n ? x0[e1 + u * kXThreads] : 0.f;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int e = e1 + u * kXThreads;
@@ -680,17 +703,18 @@ __device__ __forceinline__ void x_solve_rows(float* sm, const FFStep& PS, int ro
         int p, r;
         sg.map(e, p, r);
         const int pn = p + 1 == P ? 0 : p + 1, pp = p == 0 ? P - 1 : p - 1;
-        const float dl = xs[e + p] - spikes32(vw, m, r, ts[4 * pn], ts[4 * pn + 1], ts[4 * pp + 2], ts[4 * pp + 3]);
-        const ff w = two_sum(xv[u], dl);
-        whi[ro + e] = w.hi;
-        wlo[ro + e] = w.lo;
+        const float2 tn = *reinterpret_cast<const float2*>(ts + 4 * pn);
+        const float2 tp = *reinterpret_cast<const float2*>(ts + 4 * pp + 2);
+        const ff w = two_sum(xv[u], xs[e + p] - spikes32(vw4, r, tn, tp));
+        wh[e] = w.hi;
+        wl[e] = w.lo;
       }
     }
   }
 }
 
 __global__ void __launch_bounds__(kXThreads, 7) x_solve_ff_kernel(FFStep P) {
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   x_solve_rows(sm, P, blockIdx.x * P.xs);
 }
 
@@ -711,23 +735,27 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
   const float2* __restrict__ aff = PS.affY;
   const int S = PS.ysc, lgs = PS.lgys;  // columns per block (a power of two <= 32)
   const int RR = kYThreads >> lgs;      // rows a pass of the block covers
-  const int m = D.m, P = D.P, K = 4 * P, K1 = K + 1, pitch = m * S + pad;
+  // per-column boundary values and reduced unknowns at a pitch of 4P + 4 floats:
+  // 16-byte aligned rows whose starts fall on different banks for a warp's columns
+  const int m = D.m, P = D.P, K = 4 * P, K1 = K + 4, pitch = m * S + pad;
   float* X = sm;
-  float* yb = X + P * pitch;
+  float* yb = X + ((P * pitch + 3) & ~3);
   float* tau = yb + S * K1;
   const SegMap sg{m, lgm, D.rm};
   const int slot = z;
   const int ns = nx - col0 < S ? nx - col0 : S;
   const size_t zo = (size_t)z * nx * n;
-  const float* __restrict__ fhi = PS.whi + zo;  // the y solve's right-hand side is the x result
-  const float* __restrict__ flo = PS.wlo + zo;
-  float* __restrict__ x0s = PS.x0s + zo;
-  const double* __restrict__ cbar = PS.cbar + zo;
-  cn += zo;
-  cp += zo;
   const int tid = threadIdx.x, s = tid & (S - 1), e0 = tid >> lgs;
   const bool live = s < ns;
   const int c = col0 + s;
+  // column c of the simulation's fields (row e at + e * nx)
+  const float* __restrict__ fhi = PS.whi + zo + c;  // the y solve's right-hand side is the x result
+  const float* __restrict__ flo = PS.wlo + zo + c;
+  float* __restrict__ x0s = PS.x0s + zo + c;
+  const double* __restrict__ cbar = PS.cbar + zo + c;
+  cn += zo + c;
+  cp += zo + c;
+  const size_t ldr = (size_t)RR * nx;  // a pass of the block in elements
   auto at = [&](int e) {
     int p, r;
     sg.map(e, p, r);
@@ -736,9 +764,10 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
   constexpr int B = 4;  // elements per batch of hoisted global loads
   if (live) {
     for (int e1 = e0; e1 < n; e1 += B * RR) {
+      const float* src = fhi + (size_t)e1 * nx;
       float v[B];
 #pragma unroll
-      for (int u = 0; u < B; ++u) v[u] = e1 + u * RR < n ? fhi[(size_t)(e1 + u * RR) * nx + c] : 0.f;
+      for (int u = 0; u < B; ++u) v[u] = e1 + u * RR < n ? src[u * ldr] : 0.f;
 #pragma unroll
       for (int u = 0; u < B; ++u)
         if (e1 + u * RR < n) X[at(e1 + u * RR)] = v[u];
@@ -758,8 +787,8 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
     if (so < ns) tau[so * K1 + q] = reduced_row<true>(yb + so * K1, q, D.rb + ko, D.rblo + ko, P, D.band);
   }
   __syncthreads();
-  const float* vw = D.vw + (size_t)slot * 4 * m;
-  const float* vwl = D.vwlo + (size_t)slot * 4 * m;
+  const float4* vw4 = D.vw4 + (size_t)slot * m;
+  const float4* vw4l = D.vw4lo + (size_t)slot * m;
   const float* ts = tau + s * K1;
   if (live) {
 #pragma unroll 2
@@ -767,13 +796,15 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
       int p, r;
       sg.map(e, p, r);
       const int pn = p + 1 == P ? 0 : p + 1, pp = p == 0 ? P - 1 : p - 1;
-      x0s[(size_t)e * nx + c] = corr_first(X[p * pad + e * S + s], vw, vwl, m, r, D.plo, D.phi, ts[4 * pn],
-                                           ts[4 * pn + 1], ts[4 * pp + 2], ts[4 * pp + 3]);
+      const float2 tn = *reinterpret_cast<const float2*>(ts + 4 * pn);
+      const float2 tp = *reinterpret_cast<const float2*>(ts + 4 * pp + 2);
+      x0s[(size_t)e * nx] = corr_first(X[p * pad + e * S + s], vw4, vw4l, r, D.plo, D.phi, tn, tp);
     }
   }
   __syncthreads();
   if (live) {  // rho = f - A x0 into shared memory (x0 and its neighbours from the scratch)
     const ff a = ffc(aff[slot]);
+    const size_t nx1 = nx, nx2 = 2 * (size_t)nx;
     for (int e1 = e0; e1 < n; e1 += 2 * RR) {
       float fh[2], fl[2], w[2][5];
 #pragma unroll
@@ -783,10 +814,20 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
 #pragma unroll
         for (int d = 0; d < 5; ++d) w[u][d] = 0.f;
         if (e < n) {
-          fh[u] = fhi[(size_t)e * nx + c];
-          fl[u] = flo[(size_t)e * nx + c];
+          const size_t eo = (size_t)e * nx;
+          fh[u] = fhi[eo];
+          fl[u] = flo[eo];
+          if (e >= 2 && e < n - 2) {
+            const float* q = x0s + eo;
+            w[u][0] = q[-(ptrdiff_t)nx2];
+            w[u][1] = q[-(ptrdiff_t)nx1];
+            w[u][2] = q[0];
+            w[u][3] = q[nx1];
+            w[u][4] = q[nx2];
+          } else {
 #pragma unroll
-          for (int d = 0; d < 5; ++d) w[u][d] = x0s[(size_t)wrap2(e + d - 2, n) * nx + c];
+            for (int d = 0; d < 5; ++d) w[u][d] = x0s[(size_t)wrap2(e + d - 2, n) * nx];
+          }
         }
       }
 #pragma unroll
@@ -809,16 +850,16 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
   __syncthreads();
   if (live) {
     for (int e1 = e0; e1 < n; e1 += B * RR) {
+      const size_t eo1 = (size_t)e1 * nx;
       float xv[B];
       double cv[B];
 #pragma unroll
       for (int u = 0; u < B; ++u) {
-        const int e = e1 + u * RR;
         xv[u] = 0.f;
         cv[u] = 0.0;
-        if (e < n) {
-          xv[u] = x0s[(size_t)e * nx + c];
-          cv[u] = cbar[(size_t)e * nx + c];
+        if (e1 + u * RR < n) {
+          xv[u] = x0s[eo1 + u * ldr];
+          cv[u] = cbar[eo1 + u * ldr];
         }
       }
 #pragma unroll
@@ -828,8 +869,10 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
         int p, r;
         sg.map(e, p, r);
         const int pn = p + 1 == P ? 0 : p + 1, pp = p == 0 ? P - 1 : p - 1;
-        const size_t q = (size_t)e * nx + c;
-        const float dl = X[p * pad + e * S + s] - spikes32(vw, m, r, ts[4 * pn], ts[4 * pn + 1], ts[4 * pp + 2], ts[4 * pp + 3]);
+        const float2 tn = *reinterpret_cast<const float2*>(ts + 4 * pn);
+        const float2 tp = *reinterpret_cast<const float2*>(ts + 4 * pp + 2);
+        const size_t q = eo1 + u * ldr;
+        const float dl = X[p * pad + e * S + s] - spikes32(vw4, r, tn, tp);
         const double nxt = cv[u] + ff2d(two_sum(xv[u], dl));
         if (keep_roles) {
           cp[q] = cn[q];
@@ -843,7 +886,7 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
 }
 
 __global__ void __launch_bounds__(kYThreads, 2) y_solve_ff_kernel(FFStep P, double* cn, double* cp, int keep_roles) {
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   y_solve_cols(sm, P, cn, cp, keep_roles, blockIdx.y, blockIdx.x * P.ysc);
 }
 
@@ -883,7 +926,7 @@ __global__ void __launch_bounds__(kT* kBY) ens_rhs_ff_kernel(const FFStep* __res
 __global__ void __launch_bounds__(kXThreads, 7) ens_x_ff_kernel(const FFStep* __restrict__ steps,
                                                                 const int* __restrict__ order,
                                                                 const int* __restrict__ start, int ng, int nitems) {
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int k = item_group(start, ng, it);
     const FFStep P = steps[order[k]];
@@ -896,7 +939,7 @@ __global__ void __launch_bounds__(kYThreads, 2) ens_y_ff_kernel(const FFStep* __
                                                                 const int* __restrict__ order,
                                                                 const int* __restrict__ start, int ng, int nitems,
                                                                 int parity) {
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int k = item_group(start, ng, it);
     const FFStep P = steps[order[k]];
@@ -922,12 +965,12 @@ void launch_penta_refine_ff(double* x, float* work, int n, int batch, const floa
 // ---------------------------------------------------------------------------
 // Fused solves: shared-memory sizes, column counts and launches.
 size_t x_solve_smem(int n, int P, int xs) {
-  return sizeof(float) * ((size_t)xs * (n + P) + 2 * (size_t)xs * 4 * P);
+  return sizeof(float) * ((((size_t)xs * (n + P) + 3) & ~(size_t)3) + 2 * (size_t)xs * 4 * P);
 }
 int y_solve_pad(int m, int S) { return (((S - m * S) % 32) + 32) % 32; }
 size_t y_solve_smem(int n, int P, int S) {
   const int m = n / P;
-  return sizeof(float) * ((size_t)P * (m * S + y_solve_pad(m, S)) + 2 * (size_t)S * (4 * P + 1));
+  return sizeof(float) * ((((size_t)P * (m * S + y_solve_pad(m, S)) + 3) & ~(size_t)3) + 2 * (size_t)S * (4 * P + 4));
 }
 int log2_exact(int m) {
   int lg = 0;

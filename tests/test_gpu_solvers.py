@@ -127,6 +127,35 @@ def test_penta_full_size_sampled_and_residual():
     assert _rel(X[:, idx].cpu().numpy(), ref) <= 1e-11
 
 
+def test_penta_per_system_full_size_sampled_and_residual():
+    # the variable-coefficient ("Rewrite") workload at full size: N = 1024,
+    # batch 65536, every system its own diagonally dominant random rows
+    # (synth.diag_dominant_penta drawn on the device, seed 2): the residual of
+    # every system, and 64 sampled systems against the oracle
+    chx = _chx()
+    n, batch = 1024, 65536
+    cnt = n * batch
+    a, b, d, e = (synth.uniform_torch(2, cnt, -1.0, 1.0, device=DEV, offset=k * cnt) for k in range(4))
+    u = synth.uniform_torch(2, cnt, 0.0, 1.0, device=DEV, offset=4 * cnt)
+    c = (1.5 + 0.5 * u) * (a.abs() + b.abs() + d.abs() + e.abs())
+    del u
+    f = synth.uniform_torch(9, cnt, -1.0, 1.0, device=DEV)
+    plan = chx.PentaPlan(n, [a, b, c, d, e], batch, mode=chx.COEF_PER_SYSTEM)
+    x = f.clone()
+    plan.solve(x)
+    plan.sync_status()
+    A, B, C, D, E, X, F = (v.view(n, batch) for v in (a, b, c, d, e, x, f))
+    # row i: a_i x_{i-2} + b_i x_{i-1} + c_i x_i + d_i x_{i+1} + e_i x_{i+2} = f_i (indices mod n)
+    res = A * torch.roll(X, 2, 0) + B * torch.roll(X, 1, 0) + C * X + D * torch.roll(X, -1, 0) + E * torch.roll(X, -2, 0) - F
+    scale = (A.abs() + B.abs() + C.abs() + D.abs() + E.abs()) * X.abs().max()
+    assert float((res.abs() / scale).max()) <= 64 * 2.220446049250313e-16
+    idx = np.array(synth.splitmix64(6, 64) % batch, dtype=np.int64)
+    it = torch.from_numpy(idx).to(DEV)
+    cols = [v.view(n, batch)[:, it].cpu().numpy().ravel() for v in (a, b, c, d, e, f)]
+    ref = oracle.penta_cyclic_batch(*cols[:5], cols[5], len(idx)).reshape(n, -1)
+    assert _rel(X[:, it].cpu().numpy(), ref) <= 1e-12
+
+
 def test_penta_errors():
     chx = _chx()
     with pytest.raises(chx.ChxError) as e:
