@@ -758,7 +758,7 @@ int dir_alloc(SpikeDir* D, int n, int P, int slots) {
   int rc;
   if ((rc = dev_alloc(&D->d_a, slots)) || (rc = dev_alloc(&D->d_lu, m4)) || (rc = dev_alloc(&D->d_vw, m4)) ||
       (rc = dev_alloc(&D->d_rinv, kk)) || (rc = dev_alloc(&D->d_a32, slots)) || (rc = dev_alloc(&D->d_aff, slots)) ||
-      (rc = dev_alloc(&D->d_lu32, m4)) || (rc = dev_alloc(&D->d_vw32, m4)) || (rc = dev_alloc(&D->d_rinv32, kk)) ||
+      (rc = dev_alloc(&D->d_lu4, m4 / 4)) || (rc = dev_alloc(&D->d_vw32, m4)) || (rc = dev_alloc(&D->d_rinv32, kk)) ||
       (rc = dev_alloc(&D->d_vwlo, m4)) || (rc = dev_alloc(&D->d_rinvlo, kk)) || (rc = dev_alloc(&D->d_rb32, kk)) ||
       (rc = dev_alloc(&D->d_rblo, kk)) || (rc = dev_alloc(&D->d_vw4, m4 / 4)) || (rc = dev_alloc(&D->d_vw4lo, m4 / 4)))
     return rc;
@@ -815,7 +815,7 @@ int dir_set(SpikeDir* D, int z, double a) {
   const std::vector<double> av(1, a);
   const float2 aff = split_ff(a);
   if ((rc = put(D->d_a + z, av)) || (rc = put(D->d_lu + z * m4, lu)) || (rc = put(D->d_vw + z * m4, vw)) ||
-      (rc = put(D->d_rinv + z * kk, rinv)) || (rc = put(D->d_a32 + z, av)) || (rc = put(D->d_lu32 + z * m4, lu)) ||
+      (rc = put(D->d_rinv + z * kk, rinv)) || (rc = put(D->d_a32 + z, av)) ||
       (rc = put(D->d_vw32 + z * m4, vw)) || (rc = put(D->d_rinv32 + z * kk, rinv)) ||
       (rc = put_lo(D->d_vwlo + z * m4, vw)) || (rc = put_lo(D->d_rinvlo + z * kk, rinv)) ||
       (rc = put(D->d_rb32 + z * kk, rb)) || (rc = put_lo(D->d_rblo + z * kk, rb)))
@@ -827,6 +827,9 @@ int dir_set(SpikeDir* D, int z, double a) {
       for (int k = 0; k < 4; ++k) v4[(size_t)r * 4 + k] = vw[(size_t)k * m + r];
     if ((rc = put((float*)(D->d_vw4 + z * (m4 / 4)), v4)) || (rc = put_lo((float*)(D->d_vw4lo + z * (m4 / 4)), v4)))
       return rc;
+    for (int r = 0; r < m; ++r)  // the LU factors the same way: [r][k] = factor k at row r
+      for (int k = 0; k < 4; ++k) v4[(size_t)r * 4 + k] = lu[(size_t)k * m + r];
+    if ((rc = put((float*)(D->d_lu4 + z * (m4 / 4)), v4))) return rc;
   }
   return cuda_check(cudaMemcpy(D->d_aff + z, &aff, sizeof(float2), cudaMemcpyHostToDevice), "ch: upload");
 }
@@ -842,7 +845,7 @@ int dir_replicate(SpikeDir* D) {
     if (!rc) rc = cuda_check(cudaMemcpy(D->d_rinv + z * kk, D->d_rinv, kk * 8, cudaMemcpyDeviceToDevice), "ch: replicate");
     if (!rc) rc = cuda_check(cudaMemcpy(D->d_a32 + z, D->d_a32, 4, cudaMemcpyDeviceToDevice), "ch: replicate");
     if (!rc) rc = cuda_check(cudaMemcpy(D->d_aff + z, D->d_aff, 8, cudaMemcpyDeviceToDevice), "ch: replicate");
-    if (!rc) rc = cuda_check(cudaMemcpy(D->d_lu32 + z * m4, D->d_lu32, m4 * 4, cudaMemcpyDeviceToDevice), "ch: replicate");
+    if (!rc) rc = cuda_check(cudaMemcpy(D->d_lu4 + z * (m4 / 4), D->d_lu4, m4 * 4, cudaMemcpyDeviceToDevice), "ch: replicate");
     if (!rc) rc = cuda_check(cudaMemcpy(D->d_vw32 + z * m4, D->d_vw32, m4 * 4, cudaMemcpyDeviceToDevice), "ch: replicate");
     if (!rc) rc = cuda_check(cudaMemcpy(D->d_rinv32 + z * kk, D->d_rinv32, kk * 4, cudaMemcpyDeviceToDevice), "ch: replicate");
     if (!rc) rc = cuda_check(cudaMemcpy(D->d_vwlo + z * m4, D->d_vwlo, m4 * 4, cudaMemcpyDeviceToDevice), "ch: replicate");
@@ -859,7 +862,7 @@ int dir_move(SpikeDir* D, int from, int to, cudaStream_t st) {
   const size_t m4 = 4 * (size_t)D->m, kk = (size_t)16 * D->P * D->P;
   struct { void* base; size_t esz, per; } a[15] = {
       {D->d_a, 8, 1}, {D->d_lu, 8, m4}, {D->d_vw, 8, m4}, {D->d_rinv, 8, kk}, {D->d_a32, 4, 1},
-      {D->d_aff, 8, 1}, {D->d_lu32, 4, m4}, {D->d_vw32, 4, m4}, {D->d_rinv32, 4, kk}, {D->d_vwlo, 4, m4},
+      {D->d_aff, 8, 1}, {D->d_lu4, 4, m4}, {D->d_vw32, 4, m4}, {D->d_rinv32, 4, kk}, {D->d_vwlo, 4, m4},
       {D->d_rinvlo, 4, kk}, {D->d_rb32, 4, kk}, {D->d_rblo, 4, kk}, {D->d_vw4, 4, m4}, {D->d_vw4lo, 4, m4}};
   for (auto& x : a) {
     const size_t b = x.esz * x.per;
@@ -872,7 +875,7 @@ int dir_move(SpikeDir* D, int from, int to, cudaStream_t st) {
 
 void free_dir(SpikeDir* D) {
   cudaFree(D->d_a); cudaFree(D->d_lu); cudaFree(D->d_vw); cudaFree(D->d_rinv);
-  cudaFree(D->d_a32); cudaFree(D->d_aff); cudaFree(D->d_lu32); cudaFree(D->d_vw32); cudaFree(D->d_rinv32);
+  cudaFree(D->d_a32); cudaFree(D->d_aff); cudaFree(D->d_lu4); cudaFree(D->d_vw32); cudaFree(D->d_rinv32);
   cudaFree(D->d_vwlo); cudaFree(D->d_rinvlo); cudaFree(D->d_rb32); cudaFree(D->d_rblo);
   cudaFree(D->d_vw4); cudaFree(D->d_vw4lo);
   *D = SpikeDir();
@@ -883,12 +886,13 @@ DirView<T> view(const SpikeDir& D, int spp);
 template <>
 DirView<double> view<double>(const SpikeDir& D, int spp) {
   return DirView<double>{D.d_a,  D.d_lu,  D.d_vw,  D.d_rinv, D.m,    D.P,   spp,
-                         D.band, 1.0f / (float)D.m, nullptr, nullptr,  nullptr, nullptr, nullptr, nullptr, 0, 0};
+                         D.band, 1.0f / (float)D.m, nullptr, nullptr,  nullptr, nullptr, nullptr, nullptr, 0, 0, nullptr};
 }
 template <>
 DirView<float> view<float>(const SpikeDir& D, int spp) {
-  return DirView<float>{D.d_a32, D.d_lu32, D.d_vw32, D.d_rinv32, D.m,     D.P,    spp,     D.band,
-                        1.0f / (float)D.m, D.d_vwlo, D.d_rinvlo, D.d_rb32, D.d_rblo, D.d_vw4, D.d_vw4lo, D.plo, D.phi};
+  return DirView<float>{D.d_a32, nullptr, D.d_vw32, D.d_rinv32, D.m,     D.P,    spp,     D.band,
+                        1.0f / (float)D.m, D.d_vwlo, D.d_rinvlo, D.d_rb32, D.d_rblo, D.d_vw4, D.d_vw4lo, D.plo, D.phi,
+                        D.d_lu4};
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -913,7 +917,7 @@ FFStep ff_step_params(const ChGroup* g, int G, double* cur, double* prev, void* 
   P.ty = (int)ceil_div(g->ny, kT);
   P.X = view<float>(g->X, g->ny);
   P.Y = view<float>(g->Y, g->nx);
-  P.xs = x_solve_rows(g->nx, g->X.P, target);
+  P.xs = x_solve_rows(g->nx, g->ny, g->X.P, target);
   P.ysc = y_solve_cols(g->ny, g->Y.P, target);
   P.lgys = log2_exact(P.ysc);
   P.ypad = y_solve_pad(g->Y.m, P.ysc);
@@ -934,7 +938,7 @@ FFStep ff_step_params(const ChGroup* g, int G, double* cur, double* prev, void* 
   P.whi = wptr<float>(work, g->off_w);
   P.wlo = wptr<float>(work, g->off_wlo);
   P.x0s = wptr<float>(work, g->off_x0);
-  P.cbar = wptr<double>(work, g->off_cb);
+  P.cbar = wptr<float2>(work, g->off_cb);
   return P;
 }
 
@@ -1087,7 +1091,7 @@ int group_init(ChGroup* g, int nx, int ny, double lx, double ly, double gamma, d
   g->off_y1 = off;
   g->off_y2 = off;
   g->off_x0 = off; off = align256(off + mix);  // the fused solves' x0 scratch
-  g->off_cb = off; off = align256(off + N * sizeof(double));  // Cbar (FP64), formed by the RHS pass for the update
+  g->off_cb = off; off = align256(off + N * sizeof(double));  // Cbar (FP64, or a double-float pair), formed by the RHS pass
   g->off_m = off; off = align256(off + (f64 ? N * esz : 0));  // M, between the two RHS passes
   // the FP64 step's boundary values and reduced solutions (the fused FP32
   // solves keep theirs in shared memory)

@@ -25,7 +25,7 @@ struct SpikeDir {
   double* d_rinv = nullptr;     // slots x (4P)^2 reduced-system inverse
   float* d_a32 = nullptr;
   float2* d_aff = nullptr;      // a as a double-float pair
-  float* d_lu32 = nullptr;
+  float4* d_lu4 = nullptr;      // slots x m: the FP32 factors of each row (ralpha, beta, gam, del)
   float* d_vw32 = nullptr;
   float* d_rinv32 = nullptr;
   // the FP64 spikes and reduced inverse less their FP32 roundings (v - (float)v):
@@ -65,6 +65,7 @@ struct DirView {
   const float4* vw4;    // FP32 views: packed spikes per row, high and low floats
   const float4* vw4lo;
   int plo, phi;         // FP32 views: rows of plain FP32 spike correction (SpikeDir)
+  const float4* lu4;    // FP32 views: factors packed per row (SpikeDir::d_lu4; lu is unused)
 };
 
 // Segment s and row r of global row i for segments of m rows, without an
@@ -106,7 +107,7 @@ struct FFStep {
   double* st[2];
   int cur0;
   float *fhi, *flo, *whi, *wlo, *x0s;  // work: right-hand side, x result, x0 scratch
-  double* cbar;                        // work: Cbar in FP64
+  float2* cbar;                        // work: Cbar as a double-float pair
 };
 
 // Builds the parameters of the group's fused step for its first G slots, with
@@ -117,9 +118,9 @@ FFStep ff_step_params(const ChGroup* g, int G, double* cur, double* prev, void* 
 // Shared-memory bytes of the fused x / y solves for an n-point system with P
 // segments (xs rows / S columns per block), and the tile shapes for about
 // `target` points per block (0: does not fit).
-size_t x_solve_smem(int n, int P, int xs);
+size_t x_solve_smem(int n, int ny, int P, int xs);
 size_t y_solve_smem(int n, int P, int S);
-int x_solve_rows(int n, int P, int target);
+int x_solve_rows(int n, int ny, int P, int target);
 int y_solve_cols(int n, int P, int target);
 int y_solve_pad(int m, int S);
 int log2_exact(int m);

@@ -153,7 +153,7 @@ int build_schedule(chx_ens* e) {
     for (int ph = 0; ph < 3; ++ph)
       start[ph * (kEnsMaxGroups + 1) + k + 1] = start[ph * (kEnsMaxGroups + 1) + k] + ens_phase_items(ph, P);
     noise = noise || P.noise;
-    sx = std::max(sx, x_solve_smem(P.nx, P.X.P, P.xs));
+    sx = std::max(sx, x_solve_smem(P.nx, P.ny, P.X.P, P.xs));
     sy = std::max(sy, y_solve_smem(P.ny, P.Y.P, P.ysc));
   }
   int dev = 0, sms = 0;

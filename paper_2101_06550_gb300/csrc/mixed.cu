@@ -48,11 +48,23 @@ __device__ __forceinline__ ff lap_ff(const ff (*t)[LD], int y, int x, ff rho, ff
   return ff_add(a, ff_mul(kap, t[y][x]));
 }
 
+// The same at two points (y0, x0), (y1, x1) with packed arithmetic.
+template <int LD, bool kIso>
+__device__ __forceinline__ ff2 lap_ff2(const ff (*t)[LD], int y0, int x0, int y1, int x1, ff2 rho, ff2 kap) {
+  ff2 a = ff2_add(ff2_pack(t[y0][x0 - 1], t[y1][x1 - 1]), ff2_pack(t[y0][x0 + 1], t[y1][x1 + 1]));
+  const ff2 b = ff2_add(ff2_pack(t[y0 - 1][x0], t[y1 - 1][x1]), ff2_pack(t[y0 + 1][x0], t[y1 + 1][x1]));
+  const ff2 c = ff2_pack(t[y0][x0], t[y1][x1]);
+  if (kIso) return ff2_add(ff2_add(a, b), ff2_scale2(c, -4.f));
+  a = ff2_add(a, ff2_mul(rho, b));
+  return ff2_add(a, ff2_mul(kap, c));
+}
+
+
 // Right-hand side of Eq. 3.1 in double-float: r = k2 L'(M) - k1 (C^n - C^{n-1}),
 // M = C^3 - C - gl L'(Cbar), in one pass over 32 x 32 tiles (M formed on the
 // tile and a 1-point halo ring): whole 32-column rows per warp, r written
 // row-major (rhi, rlo: [z][j][i]) for the fused x solve, and Cbar = 2 C^n -
-// C^{n-1} in FP64 (cbo) for the update.  (The FP64 step
+// C^{n-1} as a double-float pair (cbo) for the update.  (The FP64 step
 // splits this into two passes to save the ring's FP64 work; here the ring
 // costs issue slots on the FP32 pipes.)
 //
@@ -80,7 +92,7 @@ __device__ __forceinline__ void rhs_ff_tile(RhsSmem<NOISE>& sh, const FFStep& P,
   const int nx = P.nx, ny = P.ny;
   float* __restrict__ rhi = P.fhi;
   float* __restrict__ rlo = P.flo;
-  double* __restrict__ cbo = P.cbar;
+  float2* __restrict__ cbo = P.cbar;
   const double* __restrict__ dev = P.noise;
   const double nkx = P.nkx, nky = P.nky;
   const ff rho = ffc(P.k.rho), kap = ffc(P.k.kap), gl = ffc(P.glff[z]), k1 = ffc(P.k.k1), k2 = ffc(P.k.k2);
@@ -95,7 +107,23 @@ __device__ __forceinline__ void rhs_ff_tile(RhsSmem<NOISE>& sh, const FFStep& P,
     s_cn[ly][lx] = a;
     s_cb[ly][lx] = ff_sub(ff_scale2(a, 2.f), b);
   };
-  for (int ly = threadIdx.y; ly < kT + 4; ly += kBY) stage(ly, threadIdx.x);
+  {
+    // two staged points per packed pass: Cbar = 2 C^n - C^{n-1} on both at once
+    auto stage2 = [&](int ly0, int lx0, int ly1, int lx1) {
+      const int gi0 = wrap_near(i0 - 2 + lx0, nx), gj0 = wrap_near(j0 - 2 + ly0, ny);
+      const int gi1 = wrap_near(i0 - 2 + lx1, nx), gj1 = wrap_near(j0 - 2 + ly1, ny);
+      const size_t p0 = (size_t)gj0 * nx + gi0, p1 = (size_t)gj1 * nx + gi1;
+      const ff a0 = d2ff(cn[p0]), b0 = d2ff(cp[p0]), a1 = d2ff(cn[p1]), b1 = d2ff(cp[p1]);
+      s_cn[ly0][lx0] = a0;
+      s_cn[ly1][lx1] = a1;
+      const ff2 cb = ff2_sub(ff2_scale2(ff2_pack(a0, a1), 2.f), ff2_pack(b0, b1));
+      s_cb[ly0][lx0] = ff2_first(cb);
+      s_cb[ly1][lx1] = ff2_second(cb);
+    };
+    int ly = threadIdx.y;
+    for (; ly + kBY < kT + 4; ly += 2 * kBY) stage2(ly, threadIdx.x, ly + kBY, threadIdx.x);
+    if (ly < kT + 4) stage(ly, threadIdx.x);
+  }
   if (tid < 4 * (kT + 4)) stage(tid >> 2, kT + (tid & 3));
   if (NOISE) {
     const size_t N = (size_t)nx * ny;
@@ -120,24 +148,44 @@ __device__ __forceinline__ void rhs_ff_tile(RhsSmem<NOISE>& sh, const FFStep& P,
     const ff nl = ff_mul(c, ff_add_f(ff_mul(c, c), -1.f));
     s_m[ly - 1][lx - 1] = ff_sub(nl, ff_mul(gl, l));
   };
-  for (int ly = 1 + threadIdx.y; ly <= kT + 2; ly += kBY) mstage(ly, 1 + threadIdx.x);
+  {
+    const ff2 rho2 = ff2_splat(rho), kap2 = ff2_splat(kap), gl2 = ff2_splat(gl);
+    auto mstage2 = [&](int ly0, int ly1, int lx) {
+      const ff2 l = lap_ff2<kT + 5, kIso>(s_cb, ly0, lx, ly1, lx, rho2, kap2);
+      const ff2 c = ff2_pack(s_cn[ly0][lx], s_cn[ly1][lx]);
+      const ff2 nl = ff2_mul(c, ff2_add_f(ff2_mul(c, c), make_float2(-1.f, -1.f)));
+      const ff2 v = ff2_sub(nl, ff2_mul(gl2, l));
+      s_m[ly0 - 1][lx - 1] = ff2_first(v);
+      s_m[ly1 - 1][lx - 1] = ff2_second(v);
+    };
+    int ly = 1 + threadIdx.y;
+    for (; ly + kBY <= kT + 2; ly += 2 * kBY) mstage2(ly, ly + kBY, 1 + threadIdx.x);
+    if (ly <= kT + 2) mstage(ly, 1 + threadIdx.x);
+  }
   if (tid < 2 * (kT + 2)) mstage(1 + (tid >> 1), kT + 1 + (tid & 1));
   __syncthreads();
+  const ff2 rho2 = ff2_splat(rho), kap2 = ff2_splat(kap), k12 = ff2_splat(k1), k22 = ff2_splat(k2);
 #pragma unroll
-  for (int k = 0; k < kT / kBY; ++k) {
-    const int li = threadIdx.x, lj = threadIdx.y + k * kBY;  // output (i0 + li, j0 + lj)
-    const int ly = lj + 1, lx = li + 1;
-    const ff l = lap_ff<kT + 3, kIso>(s_m, ly, lx, rho, kap);
-    const ff diff = ff_sub(s_cb[ly + 1][lx + 1], s_cn[ly + 1][lx + 1]);  // C^n - C^{n-1}
-    ff v = ff_sub(ff_mul(k2, l), ff_mul(k1, diff));
-    if (NOISE) v = ff_add(v, s_nz[lj][li]);
-    const int gi = i0 + li, gj = j0 + lj;
-    if (gi < nx && gj < ny) {
-      const size_t q = ((size_t)z * ny + gj) * nx + gi;
-      rhi[q] = v.hi;
-      rlo[q] = v.lo;
-      const size_t pq = (size_t)gj * nx + gi;
-      cbo[q] = fma(2.0, cn[pq], -cp[pq]);  // Cbar for the update, on the otherwise idle FP64 unit
+  for (int k = 0; k < kT / kBY; k += 2) {  // output (i0 + li, j0 + lj) for two rows lj at once
+    const int li = threadIdx.x, lj0 = threadIdx.y + k * kBY, lj1 = lj0 + kBY;
+    const int lx = li + 1;
+    const ff2 l = lap_ff2<kT + 3, kIso>(s_m, lj0 + 1, lx, lj1 + 1, lx, rho2, kap2);
+    const ff2 diff = ff2_sub(ff2_pack(s_cb[lj0 + 2][lx + 1], s_cb[lj1 + 2][lx + 1]),
+                             ff2_pack(s_cn[lj0 + 2][lx + 1], s_cn[lj1 + 2][lx + 1]));  // C^n - C^{n-1}
+    ff2 v = ff2_sub(ff2_mul(k22, l), ff2_mul(k12, diff));
+    if (NOISE) v = ff2_add(v, ff2_pack(s_nz[lj0][li], s_nz[lj1][li]));
+    const int gi = i0 + li;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int gj = j0 + (h ? lj1 : lj0);
+      if (gi < nx && gj < ny) {
+        const ff o = h ? ff2_second(v) : ff2_first(v);
+        const size_t q = ((size_t)z * ny + gj) * nx + gi;
+        rhi[q] = o.hi;
+        rlo[q] = o.lo;
+        const ff b = s_cb[(h ? lj1 : lj0) + 2][lx + 1];
+        cbo[q] = make_float2(b.hi, b.lo);  // Cbar for the update
+      }
     }
   }
 }
@@ -151,15 +199,15 @@ __global__ void __launch_bounds__(kT* kBY) ch_rhs_ff_kernel(FFStep P, const doub
 
 // x0 = y - (V0 ta + V1 tb + W0 tc + W1 td) for one row of a segment, rounded once
 // to float: vh / vl are the row's packed spikes (V0, V1, W0, W1) as high and
-// low floats, tn = (ta, tb) the next segment's first two reduced unknowns and
-// tp = (tc, td) the previous segment's last two.  Near the segment ends the four spike terms are several times
+// low floats, tt = (ta, tb, tc, td) the next segment's first two reduced
+// unknowns and the previous segment's last two.  Near the segment ends the four spike terms are several times
 // larger than x0 (|V| up to ~6 at a' = 1.9e4) and cancel, so a plain FP32
 // chain would leave several ulps of the terms in x0.  Here every spike is a
 // double-float pair (vw + vwlo), the high products are exact (TwoProd), the
 // running sum is carried as an unevaluated pair (TwoSum), and only the
 // low-part products (~2^-24 of the terms) are rounded in FP32.
-__device__ __forceinline__ float corr_exact(float y, float4 vh, float4 vl, float2 tn, float2 tp) {
-  const float t[4] = {tn.x, tn.y, tp.x, tp.y};
+__device__ __forceinline__ float corr_exact(float y, float4 vh, float4 vl, float4 tt) {
+  const float t[4] = {tt.x, tt.y, tt.z, tt.w};
   const float h[4] = {vh.x, vh.y, vh.z, vh.w};
   const float l[4] = {vl.x, vl.y, vl.z, vl.w};
   float s = y, e = 0.f;
@@ -178,26 +226,37 @@ __device__ __forceinline__ float corr_exact(float y, float4 vh, float4 vl, float
 // [plo, phi) where the spikes' magnitudes sum to at most 1 (there the rounding
 // of the terms is no larger than that of x0 itself).
 __device__ __forceinline__ float corr_first(float y, const float4* __restrict__ vw4, const float4* __restrict__ vw4lo,
-                                            int r, int plo, int phi, float2 tn, float2 tp) {
+                                            int r, int plo, int phi, float4 t) {
   const float4 v = __ldg(&vw4[r]);
   if (r >= plo && r < phi) {
-    float c = v.x * tn.x;
-    c = fmaf(v.y, tn.y, c);
-    c = fmaf(v.z, tp.x, c);
-    c = fmaf(v.w, tp.y, c);
+    float c = v.x * t.x;
+    c = fmaf(v.y, t.y, c);
+    c = fmaf(v.z, t.z, c);
+    c = fmaf(v.w, t.w, c);
     return y - c;
   }
-  return corr_exact(y, v, __ldg(&vw4lo[r]), tn, tp);
+  return corr_exact(y, v, __ldg(&vw4lo[r]), t);
 }
 
-// A x0 for the ADI row (a, -4a, 1 + 6a, -4a, a): x0 + a * delta^4 x0, the fourth
+// A x0 for the ADI row (a, -4a, 1 + 6a, -4a, a) at two rows at once (packed
+// arithmetic; lane k from w[.].{x,y}): x0 + a * delta^4 x0, the fourth
 // difference formed with error-free sums.
-__device__ __forceinline__ ff adi_apply_ff(float w0, float w1, float w2, float w3, float w4, ff a) {
-  const ff s2 = two_sum(w0, w4);
-  const ff s1 = two_sum(w1, w3);
-  ff d = ff_sub(s2, ff_scale2(s1, 4.f));
-  d = ff_add(d, two_prod(6.f, w2));
-  return ff_add_f(ff_mul(a, d), w2);
+__device__ __forceinline__ ff2 adi_apply_ff2(const float2 (&w)[5], ff2 a) {
+  const ff2 s2 = two_sum2(w[0], w[4]);
+  const ff2 s1 = two_sum2(w[1], w[3]);
+  ff2 d = ff2_sub(s2, ff2_scale2(s1, 4.f));
+  d = ff2_add(d, two_prod2(make_float2(6.f, 6.f), w[2]));
+  return ff2_add_f(ff2_mul(a, d), w[2]);
+}
+
+// rho = f - A x0 (high float) for the two rows of a residual pass: f as
+// (high, low) floats per row, w[u][d] the five neighbours x0_{e-2..e+2} of row u.
+__device__ __forceinline__ float2 resid_pair(const float (&fh)[2], const float (&fl)[2], const float (&w)[2][5],
+                                             ff2 a) {
+  float2 wv[5];
+#pragma unroll
+  for (int d = 0; d < 5; ++d) wv[d] = make_float2(w[0][d], w[1][d]);
+  return ff2_sub(ff2{make_float2(fh[0], fh[1]), make_float2(fl[0], fl[1])}, adi_apply_ff2(wv, a)).hi;
 }
 
 // ---------------------------------------------------------------------------
@@ -412,30 +471,30 @@ __global__ void __launch_bounds__(kSolveThreads) penta_solve_f32_from_f64_kernel
 // segment of each system); the others use the whole block.
 
 // In-place sweeps of one segment on shared memory (rows ST apart):
-// y = E^{-1} f with the FP32 LU factors of the segment block; boundary values
-// y_0, y_1, y_{m-2}, y_{m-1} to yb4.  Rows are taken in blocks of B: the
-// block's values and factors are loaded first, so the serial recurrence
-// waits on one load latency per block instead of one per row.
+// y = E^{-1} f with the FP32 LU factors of the segment block, f[r] = (ralpha,
+// beta, gam, del) of row r (staged in shared memory: one 128-bit load per row,
+// at shared-memory rather than L1 latency); boundary values y_0, y_1,
+// y_{m-2}, y_{m-1} to yb4.  Rows are taken in blocks of B: the block's values
+// and factors are loaded first, so the serial recurrence waits on one load
+// latency per block instead of one per row.
 template <int ST>
-__device__ __forceinline__ void seg_sweep32(float* x, int m, float a, const float* __restrict__ lu, float* yb4,
-                                            int st = ST) {
+__device__ __forceinline__ void seg_sweep32(float* x, int m, float a, const float4* f, float* yb4, int st = ST) {
   constexpr int B = 8;
   const int STR = ST > 0 ? ST : st;  // ST = 0: the stride st given at run time
-  const float *ra = lu, *be = lu + m, *ga = lu + 2 * m, *de = lu + 3 * m;
   const int mb = m - m % B;
   float g1 = 0.f, g2 = 0.f;
   for (int r0 = 0; r0 < mb; r0 += B) {
-    float v[B], cb[B], cr[B];
+    float v[B];
+    float4 c[B];
 #pragma unroll
     for (int u = 0; u < B; ++u) {
       v[u] = x[(r0 + u) * STR];
-      cb[u] = __ldg(&be[r0 + u]);
-      cr[u] = __ldg(&ra[r0 + u]);
+      c[u] = f[r0 + u];
     }
 #pragma unroll
     for (int u = 0; u < B; ++u) {
       float g = fmaf(-a, g2, v[u]);
-      g = fmaf(-cb[u], g1, g) * cr[u];
+      g = fmaf(-c[u].y, g1, g) * c[u].x;
       v[u] = g;
       g2 = g1;
       g1 = g;
@@ -444,32 +503,34 @@ __device__ __forceinline__ void seg_sweep32(float* x, int m, float a, const floa
     for (int u = 0; u < B; ++u) x[(r0 + u) * STR] = v[u];
   }
   for (int r = mb; r < m; ++r) {
+    const float4 c = f[r];
     float g = fmaf(-a, g2, x[r * STR]);
-    g = fmaf(-__ldg(&be[r]), g1, g) * __ldg(&ra[r]);
+    g = fmaf(-c.y, g1, g) * c.x;
     x[r * STR] = g;
     g2 = g1;
     g1 = g;
   }
   float x1 = 0.f, x2 = 0.f;
   for (int r = m - 1; r >= mb; --r) {
-    float v = fmaf(-__ldg(&ga[r]), x1, x[r * STR]);
-    v = fmaf(-__ldg(&de[r]), x2, v);
+    const float4 c = f[r];
+    float v = fmaf(-c.z, x1, x[r * STR]);
+    v = fmaf(-c.w, x2, v);
     x[r * STR] = v;
     x2 = x1;
     x1 = v;
   }
   for (int r0 = mb - B; r0 >= 0; r0 -= B) {
-    float v[B], cg[B], cd[B];
+    float v[B];
+    float4 c[B];
 #pragma unroll
     for (int u = B - 1; u >= 0; --u) {
       v[u] = x[(r0 + u) * STR];
-      cg[u] = __ldg(&ga[r0 + u]);
-      cd[u] = __ldg(&de[r0 + u]);
+      c[u] = f[r0 + u];
     }
 #pragma unroll
     for (int u = B - 1; u >= 0; --u) {
-      float t = fmaf(-cg[u], x1, v[u]);
-      t = fmaf(-cd[u], x2, t);
+      float t = fmaf(-c[u].z, x1, v[u]);
+      t = fmaf(-c[u].w, x2, t);
       v[u] = t;
       x2 = x1;
       x1 = t;
@@ -530,12 +591,23 @@ __device__ __forceinline__ float reduced_row(const float* yb, int q, const float
 
 // Plain FP32 spike correction of one row of a segment: V0 ta + V1 tb + W0 tc + W1 td
 // (packed spikes as in corr_exact).
-__device__ __forceinline__ float spikes32(const float4* __restrict__ vw4, int r, float2 tn, float2 tp) {
+__device__ __forceinline__ float spikes32(const float4* __restrict__ vw4, int r, float4 t) {
   const float4 v = __ldg(&vw4[r]);
-  float c = v.x * tn.x;
-  c = fmaf(v.y, tn.y, c);
-  c = fmaf(v.z, tp.x, c);
-  return fmaf(v.w, tp.y, c);
+  float c = v.x * t.x;
+  c = fmaf(v.y, t.y, c);
+  c = fmaf(v.z, t.z, c);
+  return fmaf(v.w, t.w, c);
+}
+
+// The reduced unknowns are stored by the segment that uses them: segment p's
+// four words are (tau_{4(p+1)}, tau_{4(p+1)+1}, tau_{4(p-1)+2}, tau_{4(p-1)+3})
+// (segment indices mod P), the next segment's first two and the previous
+// segment's last two, so a row's correction reads them with one 128-bit load.
+// Word of reduced unknown q = 4 p + u in that layout:
+__device__ __forceinline__ int tau_word(int q, int P) {
+  int p = (q >> 2) + ((q & 2) ? 1 : P - 1);
+  if (p >= P) p -= P;
+  return 4 * p + (q & 3);
 }
 
 constexpr int kXThreads = 128;  // x solve: threads per block (rows per block: FFStep::xs)
@@ -564,8 +636,11 @@ __device__ __forceinline__ int wrap2(int j, int n) { return j < 0 ? j + n : (j >
 // bank-conflict free), then the boundary values and reduced solutions.  x0
 // goes to the scratch (the residual reads its neighbours there, L2-resident)
 // and the residual rho = f - A x0 replaces y in shared memory.  The memory
-// phases load a batch of elements before computing on them.
-__device__ __forceinline__ void x_solve_rows(float* sm, const FFStep& PS, int row0) {
+// phases load a batch of elements before computing on them.  keep_roles: the
+// threads the first sweeps leave idle also copy the rows of C^n into the
+// C^{n-1} buffer (the kept-roles update then only writes C^{n+1}); the right-
+// hand side pass, the last reader of C^{n-1}, has completed.
+__device__ __forceinline__ void x_solve_rows(float* sm, const FFStep& PS, int row0, int keep_roles) {
   const float* __restrict__ fhi = PS.fhi;
   const float* __restrict__ flo = PS.flo;
   float* __restrict__ x0s = PS.x0s;
@@ -579,9 +654,12 @@ __device__ __forceinline__ void x_solve_rows(float* sm, const FFStep& PS, int ro
   const int XS = PS.xs;
   float* yb = X + ((XS * Ls + 3) & ~3);  // 16-byte aligned: boundary values by float4
   float* tau = yb + XS * K;
+  float4* fs = reinterpret_cast<float4*>(tau + XS * K);  // LU factors of the block's slots
   const SegMap sg{m, lgm, D.rm};
   const int ns = rows - row0 < XS ? rows - row0 : XS;
   const int tid = threadIdx.x;
+  const int slot0 = row0 / ny;
+  for (int i = tid; i < ((row0 + ns - 1) / ny - slot0 + 1) * m; i += kXThreads) fs[i] = __ldg(&D.lu4[(size_t)slot0 * m + i]);
   for (int s = 0; s < ns; ++s) {
     const float* src = fhi + (size_t)(row0 + s) * n;
     float* xs = X + s * Ls;
@@ -603,13 +681,31 @@ __device__ __forceinline__ void x_solve_rows(float* sm, const FFStep& PS, int ro
   __syncthreads();
   for (int w = tid; w < ns * P; w += kXThreads) {
     const int s = w / P, p = w - s * P, slot = (row0 + s) / ny;
-    seg_sweep32<1>(X + s * Ls + p * (m + 1), m, D.a[slot], D.lu + (size_t)slot * 4 * m, yb + s * K + 4 * p);
+    seg_sweep32<1>(X + s * Ls + p * (m + 1), m, D.a[slot], fs + (slot - slot0) * m, yb + s * K + 4 * p);
+  }
+  if (keep_roles) {
+    // warps without sweeps copy (all threads, after their sweeps, when every warp has some)
+    const int busy = ns * P >= kXThreads - 32 ? 0 : (ns * P + 31) & ~31;
+    if (tid >= busy) {
+      const double* __restrict__ src = PS.st[PS.cur0] + (size_t)row0 * n;
+      double* __restrict__ dst = PS.st[1 - PS.cur0] + (size_t)row0 * n;
+      const int len = ns * n, nt = kXThreads - busy;
+      constexpr int U = 8;
+      for (int i1 = tid - busy; i1 < len; i1 += U * nt) {
+        double v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = i1 + u * nt < len ? src[i1 + u * nt] : 0.0;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (i1 + u * nt < len) dst[i1 + u * nt] = v[u];
+      }
+    }
   }
   __syncthreads();
   for (int o = tid; o < ns * K; o += kXThreads) {
     const int s = o / K, q = o - s * K, slot = (row0 + s) / ny;
     const size_t ko = (size_t)slot * K * K;
-    tau[o] = reduced_row<true>(yb + s * K, q, D.rb + ko, D.rblo + ko, P, D.band);
+    tau[s * K + tau_word(q, P)] = reduced_row<true>(yb + s * K, q, D.rb + ko, D.rblo + ko, P, D.band);
   }
   __syncthreads();
   for (int s = 0; s < ns; ++s) {
@@ -623,10 +719,8 @@ __device__ __forceinline__ void x_solve_rows(float* sm, const FFStep& PS, int ro
     for (int e = tid; e < n; e += kXThreads) {
       int p, r;
       sg.map(e, p, r);
-      const int pn = p + 1 == P ? 0 : p + 1, pp = p == 0 ? P - 1 : p - 1;
-      const float2 tn = *reinterpret_cast<const float2*>(ts + 4 * pn);
-      const float2 tp = *reinterpret_cast<const float2*>(ts + 4 * pp + 2);
-      dst[e] = corr_first(xs[e + p], vw4, vw4l, r, D.plo, D.phi, tn, tp);
+      const float4 t = *reinterpret_cast<const float4*>(ts + 4 * p);
+      dst[e] = corr_first(xs[e + p], vw4, vw4l, r, D.plo, D.phi, t);
     }
   }
   __syncthreads();
@@ -634,7 +728,7 @@ __device__ __forceinline__ void x_solve_rows(float* sm, const FFStep& PS, int ro
   // the periodic wrap only at a row's first and last two points)
   for (int s = 0; s < ns; ++s) {
     const int slot = (row0 + s) / ny;
-    const ff a = ffc(aff[slot]);
+    const ff2 a = ff2_splat(ffc(aff[slot]));
     const size_t ro = (size_t)(row0 + s) * n;
     const float* x0 = x0s + ro;
     const float* fh0 = fhi + ro;
@@ -661,13 +755,14 @@ __device__ __forceinline__ void x_solve_rows(float* sm, const FFStep& PS, int ro
           }
         }
       }
+      const float2 rv = resid_pair(fh, fl, w, a);
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int e = e1 + u * kXThreads;
         if (e < n) {
           int p, r;
           sg.map(e, p, r);
-          xs[e + p] = ff_sub(ff{fh[u], fl[u]}, adi_apply_ff(w[u][0], w[u][1], w[u][2], w[u][3], w[u][4], a)).hi;
+          xs[e + p] = u ? rv.y : rv.x;
         }
       }
     }
@@ -675,12 +770,12 @@ __device__ __forceinline__ void x_solve_rows(float* sm, const FFStep& PS, int ro
   __syncthreads();
   for (int w = tid; w < ns * P; w += kXThreads) {
     const int s = w / P, p = w - s * P, slot = (row0 + s) / ny;
-    seg_sweep32<1>(X + s * Ls + p * (m + 1), m, D.a[slot], D.lu + (size_t)slot * 4 * m, yb + s * K + 4 * p);
+    seg_sweep32<1>(X + s * Ls + p * (m + 1), m, D.a[slot], fs + (slot - slot0) * m, yb + s * K + 4 * p);
   }
   __syncthreads();
   for (int o = tid; o < ns * K; o += kXThreads) {
     const int s = o / K, q = o - s * K, slot = (row0 + s) / ny;
-    tau[o] = reduced_row<false>(yb + s * K, q, D.rb + (size_t)slot * K * K, nullptr, P, D.band);
+    tau[s * K + tau_word(q, P)] = reduced_row<false>(yb + s * K, q, D.rb + (size_t)slot * K * K, nullptr, P, D.band);
   }
   __syncthreads();
   for (int s = 0; s < ns; ++s) {
@@ -696,26 +791,36 @@ __device__ __forceinline__ void x_solve_rows(float* sm, const FFStep& PS, int ro
       float xv[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) xv[u] = e1 + u * kXThreads < n ? x0[e1 + u * kXThreads] : 0.f;
+      float dl[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int e = e1 + u * kXThreads;
-        if (e >= n) break;
-        int p, r;
-        sg.map(e, p, r);
-        const int pn = p + 1 == P ? 0 : p + 1, pp = p == 0 ? P - 1 : p - 1;
-        const float2 tn = *reinterpret_cast<const float2*>(ts + 4 * pn);
-        const float2 tp = *reinterpret_cast<const float2*>(ts + 4 * pp + 2);
-        const ff w = two_sum(xv[u], xs[e + p] - spikes32(vw4, r, tn, tp));
-        wh[e] = w.hi;
-        wl[e] = w.lo;
+        dl[u] = 0.f;
+        if (e < n) {
+          int p, r;
+          sg.map(e, p, r);
+          const float4 t = *reinterpret_cast<const float4*>(ts + 4 * p);
+          dl[u] = xs[e + p] - spikes32(vw4, r, t);
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < 4; h += 2) {  // w = x0 + delta as an exact pair, two rows at once
+        const ff2 w = two_sum2(make_float2(xv[h], xv[h + 1]), make_float2(dl[h], dl[h + 1]));
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int e = e1 + (h + k) * kXThreads;
+          if (e >= n) break;
+          wh[e] = k ? w.hi.y : w.hi.x;
+          wl[e] = k ? w.lo.y : w.lo.x;
+        }
       }
     }
   }
 }
 
-__global__ void __launch_bounds__(kXThreads, 7) x_solve_ff_kernel(FFStep P) {
+__global__ void __launch_bounds__(kXThreads, 7) x_solve_ff_kernel(FFStep P, int keep_roles) {
   extern __shared__ __align__(16) float sm[];
-  x_solve_rows(sm, P, blockIdx.x * P.xs);
+  x_solve_rows(sm, P, blockIdx.x * P.xs, keep_roles);
 }
 
 // y direction.  Columns col0 .. col0 + S - 1 of simulation z (blockIdx.y),
@@ -723,11 +828,12 @@ __global__ void __launch_bounds__(kXThreads, 7) x_solve_ff_kernel(FFStep P) {
 // row-major [z][j][i].  Shared memory: [segment][m rows][S columns] with a
 // segment pitch of m S + pad, pad = S - m S (mod 32): the 32 / S segments a
 // warp sweeps start S banks apart; then the boundary values and reduced
-// solutions ([s][4P + 1]: the pad spreads a warp's columns over banks) and
-// Thread t handles column t % S and rows t / S + k T / S; x0 and the
-// residual as in the x solve.  The update C^{n+1} = Cbar + v (v = x0 + delta, an exact pair; Cbar =
-// 2 C^n - C^{n-1} in FP64 from the right-hand side pass) is formed in FP64;
-// keep_roles as in ch_update_kernel.
+// solutions (per column at a pitch of 4P + 4 floats).  Thread t handles
+// column t % S and rows t / S + k T / S; x0 and the residual as in the x
+// solve.  The update C^{n+1} = Cbar + v (v = x0 + delta, an exact pair; Cbar =
+// 2 C^n - C^{n-1} as the right-hand side pass's double-float pair) is summed
+// in double-float and rounded once to FP64 into cp, or with keep_roles (C^n
+// then already copied into cp by the x solve) into cn.
 __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double* __restrict__ cn,
                                              double* __restrict__ cp, int keep_roles, int z, int col0) {
   const int nx = PS.nx, n = PS.ny, pad = PS.ypad, lgm = PS.lgy;
@@ -741,6 +847,7 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
   float* X = sm;
   float* yb = X + ((P * pitch + 3) & ~3);
   float* tau = yb + S * K1;
+  float4* fs = reinterpret_cast<float4*>(tau + S * K1);  // LU factors of the slot
   const SegMap sg{m, lgm, D.rm};
   const int slot = z;
   const int ns = nx - col0 < S ? nx - col0 : S;
@@ -752,60 +859,63 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
   const float* __restrict__ fhi = PS.whi + zo + c;  // the y solve's right-hand side is the x result
   const float* __restrict__ flo = PS.wlo + zo + c;
   float* __restrict__ x0s = PS.x0s + zo + c;
-  const double* __restrict__ cbar = PS.cbar + zo + c;
+  const float2* __restrict__ cbar = PS.cbar + zo + c;
   cn += zo + c;
   cp += zo + c;
   const size_t ldr = (size_t)RR * nx;  // a pass of the block in elements
-  auto at = [&](int e) {
+  // row e = e0 + k RR of the thread's column is at X[p * pad + tid + k * kYThreads]
+  // (e S + s = tid + k kYThreads), p its segment; the global loop pointers
+  // advance by a pass of the block
+  auto seg = [&](int e) {
     int p, r;
     sg.map(e, p, r);
-    return p * pad + e * S + s;
+    return p;
   };
   constexpr int B = 4;  // elements per batch of hoisted global loads
+  for (int i = tid; i < m; i += kYThreads) fs[i] = __ldg(&D.lu4[(size_t)slot * m + i]);
   if (live) {
-    for (int e1 = e0; e1 < n; e1 += B * RR) {
-      const float* src = fhi + (size_t)e1 * nx;
+    const float* src = fhi + (size_t)e0 * nx;
+    for (int e1 = e0, xi = tid; e1 < n; e1 += B * RR, xi += B * kYThreads, src += B * ldr) {
       float v[B];
 #pragma unroll
       for (int u = 0; u < B; ++u) v[u] = e1 + u * RR < n ? src[u * ldr] : 0.f;
 #pragma unroll
       for (int u = 0; u < B; ++u)
-        if (e1 + u * RR < n) X[at(e1 + u * RR)] = v[u];
+        if (e1 + u * RR < n) X[seg(e1 + u * RR) * pad + xi + u * kYThreads] = v[u];
     }
   }
   __syncthreads();
   const float a32 = D.a[slot];
-  const float* lu = D.lu + (size_t)slot * 4 * m;
   for (int w = tid; w < S * P; w += kYThreads) {
     const int sw = w & (S - 1), p = w >> lgs;
-    if (sw < ns) seg_sweep32<0>(X + p * pitch + sw, m, a32, lu, yb + sw * K1 + 4 * p, S);
+    if (sw < ns) seg_sweep32<0>(X + p * pitch + sw, m, a32, fs, yb + sw * K1 + 4 * p, S);
   }
   __syncthreads();
   const size_t ko = (size_t)slot * K * K;
   for (int o = tid; o < S * K; o += kYThreads) {
     const int so = o / K, q = o - so * K;
-    if (so < ns) tau[so * K1 + q] = reduced_row<true>(yb + so * K1, q, D.rb + ko, D.rblo + ko, P, D.band);
+    if (so < ns) tau[so * K1 + tau_word(q, P)] = reduced_row<true>(yb + so * K1, q, D.rb + ko, D.rblo + ko, P, D.band);
   }
   __syncthreads();
   const float4* vw4 = D.vw4 + (size_t)slot * m;
   const float4* vw4l = D.vw4lo + (size_t)slot * m;
   const float* ts = tau + s * K1;
   if (live) {
+    float* dst = x0s + (size_t)e0 * nx;
 #pragma unroll 2
-    for (int e = e0; e < n; e += RR) {
+    for (int e = e0, xi = tid; e < n; e += RR, xi += kYThreads, dst += ldr) {
       int p, r;
       sg.map(e, p, r);
-      const int pn = p + 1 == P ? 0 : p + 1, pp = p == 0 ? P - 1 : p - 1;
-      const float2 tn = *reinterpret_cast<const float2*>(ts + 4 * pn);
-      const float2 tp = *reinterpret_cast<const float2*>(ts + 4 * pp + 2);
-      x0s[(size_t)e * nx] = corr_first(X[p * pad + e * S + s], vw4, vw4l, r, D.plo, D.phi, tn, tp);
+      const float4 t = *reinterpret_cast<const float4*>(ts + 4 * p);
+      *dst = corr_first(X[p * pad + xi], vw4, vw4l, r, D.plo, D.phi, t);
     }
   }
   __syncthreads();
   if (live) {  // rho = f - A x0 into shared memory (x0 and its neighbours from the scratch)
-    const ff a = ffc(aff[slot]);
+    const ff2 a = ff2_splat(ffc(aff[slot]));
     const size_t nx1 = nx, nx2 = 2 * (size_t)nx;
-    for (int e1 = e0; e1 < n; e1 += 2 * RR) {
+    size_t eo1 = (size_t)e0 * nx;
+    for (int e1 = e0, xi = tid; e1 < n; e1 += 2 * RR, xi += 2 * kYThreads, eo1 += 2 * ldr) {
       float fh[2], fl[2], w[2][5];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
@@ -814,7 +924,7 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
 #pragma unroll
         for (int d = 0; d < 5; ++d) w[u][d] = 0.f;
         if (e < n) {
-          const size_t eo = (size_t)e * nx;
+          const size_t eo = eo1 + u * ldr;
           fh[u] = fhi[eo];
           fl[u] = flo[eo];
           if (e >= 2 && e < n - 2) {
@@ -830,55 +940,61 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
           }
         }
       }
+      const float2 rv = resid_pair(fh, fl, w, a);
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int e = e1 + u * RR;
-        if (e < n) X[at(e)] = ff_sub(ff{fh[u], fl[u]}, adi_apply_ff(w[u][0], w[u][1], w[u][2], w[u][3], w[u][4], a)).hi;
+        if (e < n) X[seg(e) * pad + xi + u * kYThreads] = u ? rv.y : rv.x;
       }
     }
   }
   __syncthreads();
   for (int w = tid; w < S * P; w += kYThreads) {
     const int sw = w & (S - 1), p = w >> lgs;
-    if (sw < ns) seg_sweep32<0>(X + p * pitch + sw, m, a32, lu, yb + sw * K1 + 4 * p, S);
+    if (sw < ns) seg_sweep32<0>(X + p * pitch + sw, m, a32, fs, yb + sw * K1 + 4 * p, S);
   }
   __syncthreads();
   for (int o = tid; o < S * K; o += kYThreads) {
     const int so = o / K, q = o - so * K;
-    if (so < ns) tau[so * K1 + q] = reduced_row<false>(yb + so * K1, q, D.rb + ko, nullptr, P, D.band);
+    if (so < ns) tau[so * K1 + tau_word(q, P)] = reduced_row<false>(yb + so * K1, q, D.rb + ko, nullptr, P, D.band);
   }
   __syncthreads();
   if (live) {
-    for (int e1 = e0; e1 < n; e1 += B * RR) {
-      const size_t eo1 = (size_t)e1 * nx;
+    size_t eo1 = (size_t)e0 * nx;
+    for (int e1 = e0, xi = tid; e1 < n; e1 += B * RR, xi += B * kYThreads, eo1 += B * ldr) {
       float xv[B];
-      double cv[B];
+      float2 cv[B];
 #pragma unroll
       for (int u = 0; u < B; ++u) {
         xv[u] = 0.f;
-        cv[u] = 0.0;
+        cv[u] = make_float2(0.f, 0.f);
         if (e1 + u * RR < n) {
           xv[u] = x0s[eo1 + u * ldr];
           cv[u] = cbar[eo1 + u * ldr];
         }
       }
+      float dl[B];
 #pragma unroll
       for (int u = 0; u < B; ++u) {
         const int e = e1 + u * RR;
-        if (e >= n) break;
-        int p, r;
-        sg.map(e, p, r);
-        const int pn = p + 1 == P ? 0 : p + 1, pp = p == 0 ? P - 1 : p - 1;
-        const float2 tn = *reinterpret_cast<const float2*>(ts + 4 * pn);
-        const float2 tp = *reinterpret_cast<const float2*>(ts + 4 * pp + 2);
-        const size_t q = eo1 + u * ldr;
-        const float dl = X[p * pad + e * S + s] - spikes32(vw4, r, tn, tp);
-        const double nxt = cv[u] + ff2d(two_sum(xv[u], dl));
-        if (keep_roles) {
-          cp[q] = cn[q];
-          cn[q] = nxt;
-        } else {
-          cp[q] = nxt;
+        dl[u] = 0.f;
+        if (e < n) {
+          int p, r;
+          sg.map(e, p, r);
+          const float4 t = *reinterpret_cast<const float4*>(ts + 4 * p);
+          dl[u] = X[p * pad + xi + u * kYThreads] - spikes32(vw4, r, t);
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < B; h += 2) {  // Cbar + (x0 + delta) for two rows at once
+        const ff2 cb{make_float2(cv[h].x, cv[h + 1].x), make_float2(cv[h].y, cv[h + 1].y)};
+        const ff2 v = ff2_add(cb, two_sum2(make_float2(xv[h], xv[h + 1]), make_float2(dl[h], dl[h + 1])));
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          if (e1 + (h + k) * RR >= n) break;
+          const size_t q = eo1 + (h + k) * ldr;
+          // kept roles: C^{n+1} over C^n (the x solve has moved C^n into cp)
+          (keep_roles ? cn : cp)[q] = ff2d(k ? ff2_second(v) : ff2_first(v));
         }
       }
     }
@@ -930,7 +1046,7 @@ __global__ void __launch_bounds__(kXThreads, 7) ens_x_ff_kernel(const FFStep* __
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int k = item_group(start, ng, it);
     const FFStep P = steps[order[k]];
-    x_solve_rows(sm, P, (it - start[k]) * P.xs);
+    x_solve_rows(sm, P, (it - start[k]) * P.xs, 0);
     __syncthreads();
   }
 }
@@ -964,13 +1080,14 @@ void launch_penta_refine_ff(double* x, float* work, int n, int batch, const floa
 
 // ---------------------------------------------------------------------------
 // Fused solves: shared-memory sizes, column counts and launches.
-size_t x_solve_smem(int n, int P, int xs) {
-  return sizeof(float) * ((((size_t)xs * (n + P) + 3) & ~(size_t)3) + 2 * (size_t)xs * 4 * P);
+size_t x_solve_smem(int n, int ny, int P, int xs) {
+  const int slots = std::min(xs, (xs - 1 + ny - 1) / ny + 1);  // most slots xs consecutive rows can touch
+  return sizeof(float) * ((((size_t)xs * (n + P) + 3) & ~(size_t)3) + 2 * (size_t)xs * 4 * P + 4 * (size_t)(n / P) * slots);
 }
 int y_solve_pad(int m, int S) { return (((S - m * S) % 32) + 32) % 32; }
 size_t y_solve_smem(int n, int P, int S) {
   const int m = n / P;
-  return sizeof(float) * ((((size_t)P * (m * S + y_solve_pad(m, S)) + 3) & ~(size_t)3) + 2 * (size_t)S * (4 * P + 4));
+  return sizeof(float) * ((((size_t)P * (m * S + y_solve_pad(m, S)) + 3) & ~(size_t)3) + 2 * (size_t)S * (4 * P + 4) + 4 * (size_t)m);
 }
 int log2_exact(int m) {
   int lg = 0;
@@ -991,10 +1108,10 @@ static int pow2_floor(int v) {
   while (2 * p <= v) p *= 2;
   return p;
 }
-int x_solve_rows(int n, int P, int target) {
+int x_solve_rows(int n, int ny, int P, int target) {
   int xs = pow2_floor(std::min(32, std::max(2, target / n)));
-  while (xs > 1 && x_solve_smem(n, P, xs) > 100 * 1024) xs /= 2;
-  return x_solve_smem(n, P, xs) <= kSmemMax ? xs : 0;
+  while (xs > 1 && x_solve_smem(n, ny, P, xs) > 100 * 1024) xs /= 2;
+  return x_solve_smem(n, ny, P, xs) <= kSmemMax ? xs : 0;
 }
 int y_solve_cols(int n, int P, int target) {
   int S = pow2_floor(std::min(32, std::max(8, target / n)));
@@ -1012,7 +1129,7 @@ int prepare_solve_ff() {
 }
 
 bool solve_ff_fits(int nx, int ny, int px, int py) {
-  return x_solve_rows(nx, px, kFFTarget) > 0 && y_solve_cols(ny, py, kFFTarget) > 0;
+  return x_solve_rows(nx, ny, px, kFFTarget) > 0 && y_solve_cols(ny, py, kFFTarget) > 0;
 }
 
 void launch_step_ff(const FFStep& P, int keep_roles, Prof* prof, cudaStream_t st) {
@@ -1026,7 +1143,7 @@ void launch_step_ff(const FFStep& P, int keep_roles, Prof* prof, cudaStream_t st
   }
   {
     ProfScope ps(prof, kXSolve, st);
-    x_solve_ff_kernel<<<ceil_div((size_t)P.G * P.ny, P.xs), kXThreads, x_solve_smem(P.nx, P.X.P, P.xs), st>>>(P);
+    x_solve_ff_kernel<<<ceil_div((size_t)P.G * P.ny, P.xs), kXThreads, x_solve_smem(P.nx, P.ny, P.X.P, P.xs), st>>>(P, keep_roles);
   }
   {
     ProfScope ps(prof, kYSolve, st);
