@@ -734,6 +734,36 @@ __device__ __forceinline__ void x_solve_rows(float* sm, const FFStep& PS, int ro
     const float* fh0 = fhi + ro;
     const float* fl0 = flo + ro;
     float* xs = X + s * Ls;
+    if ((n & 1) == 0 && ((reinterpret_cast<uintptr_t>(fhi) | reinterpret_cast<uintptr_t>(flo) |
+                          reinterpret_cast<uintptr_t>(x0s)) & 7) == 0) {
+      // a thread takes two adjacent points e, e + 1: f by 8-byte loads and
+      // the six values x0_{e-2..e+3} by three (rows start 8-byte aligned)
+#pragma unroll 2
+      for (int e = 2 * tid; e < n; e += 2 * kXThreads) {
+        const float2 fh2 = *reinterpret_cast<const float2*>(fh0 + e);
+        const float2 fl2 = *reinterpret_cast<const float2*>(fl0 + e);
+        float w[6];
+        if (e >= 2 && e + 4 <= n) {
+          const float2 a0 = *reinterpret_cast<const float2*>(x0 + e - 2);
+          const float2 a1 = *reinterpret_cast<const float2*>(x0 + e);
+          const float2 a2 = *reinterpret_cast<const float2*>(x0 + e + 2);
+          w[0] = a0.x, w[1] = a0.y, w[2] = a1.x, w[3] = a1.y, w[4] = a2.x, w[5] = a2.y;
+        } else {
+#pragma unroll
+          for (int d = 0; d < 6; ++d) w[d] = x0[wrap2(e + d - 2, n)];
+        }
+        float2 wv[5];
+#pragma unroll
+        for (int d = 0; d < 5; ++d) wv[d] = make_float2(w[d], w[d + 1]);
+        const float2 rv = ff2_sub(ff2{fh2, fl2}, adi_apply_ff2(wv, a)).hi;
+        int p, r;
+        sg.map(e, p, r);
+        xs[e + p] = rv.x;
+        sg.map(e + 1, p, r);
+        xs[e + 1 + p] = rv.y;
+      }
+      continue;
+    }
     for (int e1 = tid; e1 < n; e1 += 2 * kXThreads) {
       float fh[2], fl[2], w[2][5];
 #pragma unroll
@@ -860,6 +890,14 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
   const float* __restrict__ flo = PS.wlo + zo + c;
   float* __restrict__ x0s = PS.x0s + zo + c;
   const float2* __restrict__ cbar = PS.cbar + zo + c;
+  // full strips of an even-width grid take the corrections, residual and update
+  // two adjacent columns per thread (8- and 16-byte accesses, packed arithmetic)
+  double* const dst0 = keep_roles ? cn : cp;  // the update's destination
+  const bool pairs = ns == S && S >= 2 && (nx & 1) == 0 &&
+                     ((reinterpret_cast<uintptr_t>(PS.whi) | reinterpret_cast<uintptr_t>(PS.wlo) |
+                       reinterpret_cast<uintptr_t>(PS.x0s)) & 7) == 0 &&
+                     ((reinterpret_cast<uintptr_t>(PS.cbar) | reinterpret_cast<uintptr_t>(dst0)) & 15) == 0;
+  double* __restrict__ out2 = dst0 + zo + col0;  // strip base
   cn += zo + c;
   cp += zo + c;
   const size_t ldr = (size_t)RR * nx;  // a pass of the block in elements
@@ -900,7 +938,21 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
   const float4* vw4 = D.vw4 + (size_t)slot * m;
   const float4* vw4l = D.vw4lo + (size_t)slot * m;
   const float* ts = tau + s * K1;
-  if (live) {
+  if (pairs) {
+    const int cq = 2 * (tid & (S / 2 - 1)), RR2 = 2 * RR;
+    const float* t0 = tau + cq * K1;
+    float* __restrict__ x02 = PS.x0s + zo + col0 + cq;
+#pragma unroll 2
+    for (int e = tid >> (lgs - 1); e < n; e += RR2) {
+      int p, r;
+      sg.map(e, p, r);
+      const float2 yv = *reinterpret_cast<const float2*>(X + p * pad + e * S + cq);
+      const float4 ta = *reinterpret_cast<const float4*>(t0 + 4 * p);
+      const float4 tb = *reinterpret_cast<const float4*>(t0 + K1 + 4 * p);
+      *reinterpret_cast<float2*>(x02 + (size_t)e * nx) =
+          make_float2(corr_first(yv.x, vw4, vw4l, r, D.plo, D.phi, ta), corr_first(yv.y, vw4, vw4l, r, D.plo, D.phi, tb));
+    }
+  } else if (live) {
     float* dst = x0s + (size_t)e0 * nx;
 #pragma unroll 2
     for (int e = e0, xi = tid; e < n; e += RR, xi += kYThreads, dst += ldr) {
@@ -911,7 +963,45 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
     }
   }
   __syncthreads();
-  if (live) {  // rho = f - A x0 into shared memory (x0 and its neighbours from the scratch)
+  if (pairs) {
+    // rho = f - A x0 into shared memory, a thread taking two adjacent columns
+    // of a row (8-byte loads of f and of the five x0 neighbours, from the
+    // scratch; both lanes of the packed arithmetic) and rows 2 RR apart
+    const ff2 a = ff2_splat(ffc(aff[slot]));
+    const int cq = 2 * (tid & (S / 2 - 1)), r0 = tid >> (lgs - 1), RR2 = 2 * RR;
+    const size_t cz = zo + col0 + cq;
+    const float* __restrict__ fh2 = PS.whi + cz;
+    const float* __restrict__ fl2 = PS.wlo + cz;
+    const float* __restrict__ x02 = PS.x0s + cz;
+    const size_t nx1 = nx;
+    for (int e1 = r0; e1 < n; e1 += 2 * RR2) {  // two rows' loads in flight
+      float2 h[2], l[2], w[2][5];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int e = e1 + u * RR2;
+        h[u] = l[u] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int d = 0; d < 5; ++d) w[u][d] = make_float2(0.f, 0.f);
+        if (e < n) {
+          const size_t eo = (size_t)e * nx;
+          h[u] = *reinterpret_cast<const float2*>(fh2 + eo);
+          l[u] = *reinterpret_cast<const float2*>(fl2 + eo);
+          if (e >= 2 && e < n - 2) {
+#pragma unroll
+            for (int d = 0; d < 5; ++d) w[u][d] = *reinterpret_cast<const float2*>(x02 + eo + (d - 2) * (ptrdiff_t)nx1);
+          } else {
+#pragma unroll
+            for (int d = 0; d < 5; ++d) w[u][d] = *reinterpret_cast<const float2*>(x02 + (size_t)wrap2(e + d - 2, n) * nx);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int e = e1 + u * RR2;
+        if (e < n) *reinterpret_cast<float2*>(X + seg(e) * pad + e * S + cq) = ff2_sub(ff2{h[u], l[u]}, adi_apply_ff2(w[u], a)).hi;
+      }
+    }
+  } else if (live) {  // the same one column per thread (x0 and its neighbours from the scratch)
     const ff2 a = ff2_splat(ffc(aff[slot]));
     const size_t nx1 = nx, nx2 = 2 * (size_t)nx;
     size_t eo1 = (size_t)e0 * nx;
@@ -959,7 +1049,41 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
     if (so < ns) tau[so * K1 + tau_word(q, P)] = reduced_row<false>(yb + so * K1, q, D.rb + ko, nullptr, P, D.band);
   }
   __syncthreads();
-  if (live) {
+  if (pairs) {
+    const int cq = 2 * (tid & (S / 2 - 1)), RR2 = 2 * RR;
+    const float* t0 = tau + cq * K1;
+    const float* __restrict__ x02 = PS.x0s + zo + col0 + cq;
+    const float2* __restrict__ cb2 = PS.cbar + zo + col0 + cq;
+    double* __restrict__ o2 = out2 + cq;
+    for (int e1 = tid >> (lgs - 1); e1 < n; e1 += 2 * RR2) {  // two rows' loads in flight
+      float2 xv[2];
+      float4 cv[2];  // Cbar of the two columns: (hi, lo, hi, lo)
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int e = e1 + u * RR2;
+        xv[u] = make_float2(0.f, 0.f);
+        cv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e < n) {
+          xv[u] = *reinterpret_cast<const float2*>(x02 + (size_t)e * nx);
+          cv[u] = *reinterpret_cast<const float4*>(cb2 + (size_t)e * nx);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int e = e1 + u * RR2;
+        if (e >= n) break;
+        int p, r;
+        sg.map(e, p, r);
+        const float2 dv = *reinterpret_cast<const float2*>(X + p * pad + e * S + cq);
+        const float4 ta = *reinterpret_cast<const float4*>(t0 + 4 * p);
+        const float4 tb = *reinterpret_cast<const float4*>(t0 + K1 + 4 * p);
+        const float2 dl = make_float2(dv.x - spikes32(vw4, r, ta), dv.y - spikes32(vw4, r, tb));
+        const ff2 cb{make_float2(cv[u].x, cv[u].z), make_float2(cv[u].y, cv[u].w)};
+        const ff2 v = ff2_add(cb, two_sum2(xv[u], dl));
+        *reinterpret_cast<double2*>(o2 + (size_t)e * nx) = make_double2(ff2d(ff2_first(v)), ff2d(ff2_second(v)));
+      }
+    }
+  } else if (live) {
     size_t eo1 = (size_t)e0 * nx;
     for (int e1 = e0, xi = tid; e1 < n; e1 += B * RR, xi += B * kYThreads, eo1 += B * ldr) {
       float xv[B];

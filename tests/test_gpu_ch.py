@@ -182,6 +182,35 @@ def test_ch_step_unequal_spacing_matches_oracle(ny, nx, lx, ly, precision, tol):
     assert _rel(gprev, rprev) <= tol
 
 
+def test_ch_step_f32_refine_same_on_fields_off_16_byte_boundaries():
+    # C^n / C^{n-1} as views 8 bytes past a 16-byte boundary: the y solve's
+    # two-columns-per-thread passes (16-byte field stores) give way to the
+    # one-column passes, whose arithmetic is the same lane by lane, so every
+    # value matches the aligned run bit for bit, over single steps (kept
+    # roles) and step pairs
+    chx = _chx()
+    ny, nx, lx, ly, gamma, dt = 64, 96, 3.0, 2.0, 0.01, 1e-3
+    c0 = synth.field(23, ny, nx, -0.2, 0.2)
+    cm = c0 + 1e-3 * synth.field(24, ny, nx, -1, 1)
+    plan = chx.ChPlan(nx, ny, lx, ly, gamma, dt, 1)
+    work = plan.alloc_work(DEV)
+    n = ny * nx
+    a = torch.from_numpy(c0).to(DEV)
+    b = torch.from_numpy(cm).to(DEV)
+    buf = torch.zeros(2 * n + 2, dtype=torch.float64, device=DEV)
+    ua = buf[1:1 + n].view(ny, nx)
+    ub = buf[1 + n:1 + 2 * n].view(ny, nx)
+    assert ua.data_ptr() % 16 == 8 and ub.data_ptr() % 16 == 8
+    ua.copy_(a)
+    ub.copy_(b)
+    for k in (1, 2, 3):
+        plan.step(a, b, work, k)
+        plan.step(ua, ub, work, k)
+        torch.cuda.synchronize()
+        assert torch.equal(a, ua) and torch.equal(b, ub)
+    plan.sync_status()
+
+
 @pytest.mark.parametrize("n", [512, 2048])
 def test_ch_step_f32_refine_from_random_state(n):
     # one step from the rough random initial state, the hardest case for one
