@@ -139,6 +139,9 @@ void launch_ens_phase_ff(int phase, const FFStep* steps, const int* order, const
 // resident with `smem` bytes of dynamic shared memory.
 int ens_phase_items(int phase, const FFStep& P);
 int ens_phase_occupancy(int phase, size_t smem);
+// Most dynamic shared memory a block of the x / y phase kernels may take (they
+// keep the current group's parameters in static shared memory besides).
+size_t ens_phase_smem_max();
 
 // Per-kernel CUDA-event timing (ch_profile).
 enum ProfSlot { kRhs, kLocX, kRedX, kRefX, kLoc2X, kRed2X, kFinX, kLocY, kRedY, kRefY, kLoc2Y, kRed2Y, kUpd, kRhsLap,

@@ -156,6 +156,7 @@ int build_schedule(chx_ens* e) {
     sx = std::max(sx, x_solve_smem(P.nx, P.ny, P.X.P, P.xs));
     sy = std::max(sy, y_solve_smem(P.ny, P.Y.P, P.ysc));
   }
+  if (sx > ens_phase_smem_max() || sy > ens_phase_smem_max()) return CHX_OK;  // per-group launches
   int dev = 0, sms = 0;
   int rc = cuda_check(cudaGetDevice(&dev), "ens: device");
   if (!rc) rc = cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "ens: SM count");
@@ -165,7 +166,7 @@ int build_schedule(chx_ens* e) {
   S.smem[2] = sy;
   for (int ph = 0; ph < 3; ++ph) {
     S.nitems[ph] = start[ph * (kEnsMaxGroups + 1) + S.ngroups];
-    const int occ = ens_phase_occupancy(ph, ph == 0 ? 0 : S.smem[ph]);
+    const int occ = ens_phase_occupancy(ph, S.smem[ph]);
     const int bps = S.bps[ph] > 0 && S.bps[ph] < occ ? S.bps[ph] : occ;
     S.blocks[ph] = std::min(S.nitems[ph], sms * bps);
   }

@@ -1133,22 +1133,45 @@ __global__ void __launch_bounds__(kYThreads, 2) y_solve_ff_kernel(FFStep P, doub
 // ---------------------------------------------------------------------------
 // Ensemble phase kernels: block b takes items b, b + gridDim.x, ... of the
 // packed order (every group's items, group after group); see chgroup.cuh.
-__device__ __forceinline__ int item_group(const int* __restrict__ start, int ng, int item) {
-  int k = 0;
-  while (k + 1 < ng && start[k + 1] <= item) ++k;
-  return k;
-}
+// The group of a block's current item, with that group's step parameters
+// cached in shared memory.  A block's items increase, so its group only moves
+// forward; the parameters are copied (by all threads, then a barrier) when the
+// group changes, and the item numbers the group covers are kept in registers,
+// so an item of the same group starts with no global-memory round trip.  Every
+// thread of the block makes the same calls; the caller's barrier at the end of
+// each item keeps the copy from overwriting parameters still in use.
+struct EnsCursor {
+  int k = -1, first = 0, end = 0;
+  __device__ __forceinline__ const FFStep& at(FFStep& sP, const FFStep* __restrict__ steps,
+                                              const int* __restrict__ order, const int* __restrict__ start, int ng,
+                                              int it) {
+    if (it >= end) {
+      int kn = k + 1;
+      while (kn + 1 < ng && start[kn + 1] <= it) ++kn;
+      k = kn;
+      first = start[kn];
+      end = start[kn + 1];
+      const int* src = reinterpret_cast<const int*>(steps + order[kn]);
+      int* dst = reinterpret_cast<int*>(&sP);
+      const int nt = blockDim.x * blockDim.y, t = threadIdx.y * blockDim.x + threadIdx.x;
+      for (int w = t; w < (int)(sizeof(FFStep) / sizeof(int)); w += nt) dst[w] = src[w];
+      __syncthreads();
+    }
+    return sP;
+  }
+};
 
 template <bool NOISE>
-__global__ void __launch_bounds__(kT* kBY) ens_rhs_ff_kernel(const FFStep* __restrict__ steps,
+__global__ void __launch_bounds__(kT* kBY, 5) ens_rhs_ff_kernel(const FFStep* __restrict__ steps,
                                                              const int* __restrict__ order,
                                                              const int* __restrict__ start, int ng, int nitems,
                                                              int parity) {
   __shared__ RhsSmem<NOISE> sh;
+  __shared__ FFStep sP;
+  EnsCursor cur;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const int k = item_group(start, ng, it);
-    const FFStep P = steps[order[k]];
-    const int idx = it - start[k], tpz = P.tx * P.ty;
+    const FFStep& P = cur.at(sP, steps, order, start, ng, it);
+    const int idx = it - cur.first, tpz = P.tx * P.ty;
     const int z = idx / tpz, rem = idx - z * tpz, by = rem / P.tx, bx = rem - by * P.tx;
     const int c = P.cur0 ^ parity;
     if (NOISE && P.noise) {
@@ -1159,7 +1182,7 @@ __global__ void __launch_bounds__(kT* kBY) ens_rhs_ff_kernel(const FFStep* __res
       if (P.iso) rhs_ff_tile<true, false>(*reinterpret_cast<RhsSmem<false>*>(&sh), P, P.st[c], P.st[1 - c], z, bx, by);
       else rhs_ff_tile<false, false>(*reinterpret_cast<RhsSmem<false>*>(&sh), P, P.st[c], P.st[1 - c], z, bx, by);
     }
-    __syncthreads();  // the next item reuses the shared tiles
+    __syncthreads();  // the next item reuses the shared tiles and parameters
   }
 }
 
@@ -1167,10 +1190,11 @@ __global__ void __launch_bounds__(kXThreads, 7) ens_x_ff_kernel(const FFStep* __
                                                                 const int* __restrict__ order,
                                                                 const int* __restrict__ start, int ng, int nitems) {
   extern __shared__ __align__(16) float sm[];
+  __shared__ FFStep sP;
+  EnsCursor cur;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const int k = item_group(start, ng, it);
-    const FFStep P = steps[order[k]];
-    x_solve_rows(sm, P, (it - start[k]) * P.xs, 0);
+    const FFStep& P = cur.at(sP, steps, order, start, ng, it);
+    x_solve_rows(sm, P, (it - cur.first) * P.xs, 0);
     __syncthreads();
   }
 }
@@ -1180,10 +1204,11 @@ __global__ void __launch_bounds__(kYThreads, 2) ens_y_ff_kernel(const FFStep* __
                                                                 const int* __restrict__ start, int ng, int nitems,
                                                                 int parity) {
   extern __shared__ __align__(16) float sm[];
+  __shared__ FFStep sP;
+  EnsCursor cur;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const int k = item_group(start, ng, it);
-    const FFStep P = steps[order[k]];
-    const int idx = it - start[k], nstrip = (P.nx + P.ysc - 1) / P.ysc;
+    const FFStep& P = cur.at(sP, steps, order, start, ng, it);
+    const int idx = it - cur.first, nstrip = (P.nx + P.ysc - 1) / P.ysc;
     const int z = idx / nstrip, col0 = (idx - z * nstrip) * P.ysc, c = P.cur0 ^ parity;
     y_solve_cols(sm, P, P.st[c], P.st[1 - c], 0, z, col0);
     __syncthreads();
@@ -1243,12 +1268,16 @@ int y_solve_cols(int n, int P, int target) {
   return y_solve_smem(n, P, S) <= kSmemMax ? S : 0;
 }
 
+static_assert(sizeof(FFStep) <= 1024, "the ensemble kernels' static parameter copy must fit the reserved kilobyte");
+size_t ens_phase_smem_max() { return kSmemMax - 1024; }
+
 int prepare_solve_ff() {
   int rc = cuda_check(cudaFuncSetAttribute(x_solve_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax),
                       "mixed: shared-memory opt-in");
   if (!rc) rc = cuda_check(cudaFuncSetAttribute(y_solve_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax), "mixed: shared-memory opt-in");
-  if (!rc) rc = cuda_check(cudaFuncSetAttribute(ens_x_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax), "mixed: shared-memory opt-in");
-  if (!rc) rc = cuda_check(cudaFuncSetAttribute(ens_y_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax), "mixed: shared-memory opt-in");
+  // the ensemble kernels also hold a group's parameters in static shared memory
+  if (!rc) rc = cuda_check(cudaFuncSetAttribute(ens_x_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ens_phase_smem_max()), "mixed: shared-memory opt-in");
+  if (!rc) rc = cuda_check(cudaFuncSetAttribute(ens_y_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ens_phase_smem_max()), "mixed: shared-memory opt-in");
   return rc;
 }
 
@@ -1284,7 +1313,10 @@ int ens_phase_items(int phase, const FFStep& P) {
 
 int ens_phase_occupancy(int phase, size_t smem) {
   int b = 0;
-  if (phase == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ens_rhs_ff_kernel<true>, kT * kBY, 0);
+  if (phase == 0) {  // smem: whether the launch is the Cook-forcing variant (static shared memory only)
+    if (smem) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ens_rhs_ff_kernel<true>, kT * kBY, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ens_rhs_ff_kernel<false>, kT * kBY, 0);
+  }
   else if (phase == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ens_x_ff_kernel, kXThreads, smem);
   else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ens_y_ff_kernel, kYThreads, smem);
   cudaGetLastError();
