@@ -612,6 +612,7 @@ __device__ __forceinline__ int tau_word(int q, int P) {
 
 constexpr int kXThreads = 128;  // x solve: threads per block (rows per block: FFStep::xs)
 constexpr int kYThreads = 512;  // y solve: threads per block (columns per block: FFStep::ysc)
+constexpr int kYThreadsEns = 256;  // the ensemble's y phase: more, smaller blocks per SM overlap their phases
 
 // Row e of a system -> (segment p, row r in the segment) for segments of m
 // rows: shifts when m is a power of two (lg = log2 m), else seg_row.
@@ -859,18 +860,19 @@ __global__ void __launch_bounds__(kXThreads, 7) x_solve_ff_kernel(FFStep P, int 
 // segment pitch of m S + pad, pad = S - m S (mod 32): the 32 / S segments a
 // warp sweeps start S banks apart; then the boundary values and reduced
 // solutions (per column at a pitch of 4P + 4 floats).  Thread t handles
-// column t % S and rows t / S + k T / S; x0 and the residual as in the x
+// column t % S and rows t / S + k NT / S (NT threads); x0 and the residual as in the x
 // solve.  The update C^{n+1} = Cbar + v (v = x0 + delta, an exact pair; Cbar =
 // 2 C^n - C^{n-1} as the right-hand side pass's double-float pair) is summed
 // in double-float and rounded once to FP64 into cp, or with keep_roles (C^n
 // then already copied into cp by the x solve) into cn.
+template <int NT>
 __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double* __restrict__ cn,
                                              double* __restrict__ cp, int keep_roles, int z, int col0) {
   const int nx = PS.nx, n = PS.ny, pad = PS.ypad, lgm = PS.lgy;
   const DirView<float>& D = PS.Y;
   const float2* __restrict__ aff = PS.affY;
   const int S = PS.ysc, lgs = PS.lgys;  // columns per block (a power of two <= 32)
-  const int RR = kYThreads >> lgs;      // rows a pass of the block covers
+  const int RR = NT >> lgs;      // rows a pass of the block covers
   // per-column boundary values and reduced unknowns at a pitch of 4P + 4 floats:
   // 16-byte aligned rows whose starts fall on different banks for a warp's columns
   const int m = D.m, P = D.P, K = 4 * P, K1 = K + 4, pitch = m * S + pad;
@@ -901,8 +903,8 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
   cn += zo + c;
   cp += zo + c;
   const size_t ldr = (size_t)RR * nx;  // a pass of the block in elements
-  // row e = e0 + k RR of the thread's column is at X[p * pad + tid + k * kYThreads]
-  // (e S + s = tid + k kYThreads), p its segment; the global loop pointers
+  // row e = e0 + k RR of the thread's column is at X[p * pad + tid + k * NT]
+  // (e S + s = tid + k NT), p its segment; the global loop pointers
   // advance by a pass of the block
   auto seg = [&](int e) {
     int p, r;
@@ -910,27 +912,27 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
     return p;
   };
   constexpr int B = 4;  // elements per batch of hoisted global loads
-  for (int i = tid; i < m; i += kYThreads) fs[i] = __ldg(&D.lu4[(size_t)slot * m + i]);
+  for (int i = tid; i < m; i += NT) fs[i] = __ldg(&D.lu4[(size_t)slot * m + i]);
   if (live) {
     const float* src = fhi + (size_t)e0 * nx;
-    for (int e1 = e0, xi = tid; e1 < n; e1 += B * RR, xi += B * kYThreads, src += B * ldr) {
+    for (int e1 = e0, xi = tid; e1 < n; e1 += B * RR, xi += B * NT, src += B * ldr) {
       float v[B];
 #pragma unroll
       for (int u = 0; u < B; ++u) v[u] = e1 + u * RR < n ? src[u * ldr] : 0.f;
 #pragma unroll
       for (int u = 0; u < B; ++u)
-        if (e1 + u * RR < n) X[seg(e1 + u * RR) * pad + xi + u * kYThreads] = v[u];
+        if (e1 + u * RR < n) X[seg(e1 + u * RR) * pad + xi + u * NT] = v[u];
     }
   }
   __syncthreads();
   const float a32 = D.a[slot];
-  for (int w = tid; w < S * P; w += kYThreads) {
+  for (int w = tid; w < S * P; w += NT) {
     const int sw = w & (S - 1), p = w >> lgs;
     if (sw < ns) seg_sweep32<0>(X + p * pitch + sw, m, a32, fs, yb + sw * K1 + 4 * p, S);
   }
   __syncthreads();
   const size_t ko = (size_t)slot * K * K;
-  for (int o = tid; o < S * K; o += kYThreads) {
+  for (int o = tid; o < S * K; o += NT) {
     const int so = o / K, q = o - so * K;
     if (so < ns) tau[so * K1 + tau_word(q, P)] = reduced_row<true>(yb + so * K1, q, D.rb + ko, D.rblo + ko, P, D.band);
   }
@@ -955,7 +957,7 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
   } else if (live) {
     float* dst = x0s + (size_t)e0 * nx;
 #pragma unroll 2
-    for (int e = e0, xi = tid; e < n; e += RR, xi += kYThreads, dst += ldr) {
+    for (int e = e0, xi = tid; e < n; e += RR, xi += NT, dst += ldr) {
       int p, r;
       sg.map(e, p, r);
       const float4 t = *reinterpret_cast<const float4*>(ts + 4 * p);
@@ -1005,7 +1007,7 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
     const ff2 a = ff2_splat(ffc(aff[slot]));
     const size_t nx1 = nx, nx2 = 2 * (size_t)nx;
     size_t eo1 = (size_t)e0 * nx;
-    for (int e1 = e0, xi = tid; e1 < n; e1 += 2 * RR, xi += 2 * kYThreads, eo1 += 2 * ldr) {
+    for (int e1 = e0, xi = tid; e1 < n; e1 += 2 * RR, xi += 2 * NT, eo1 += 2 * ldr) {
       float fh[2], fl[2], w[2][5];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
@@ -1034,17 +1036,17 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int e = e1 + u * RR;
-        if (e < n) X[seg(e) * pad + xi + u * kYThreads] = u ? rv.y : rv.x;
+        if (e < n) X[seg(e) * pad + xi + u * NT] = u ? rv.y : rv.x;
       }
     }
   }
   __syncthreads();
-  for (int w = tid; w < S * P; w += kYThreads) {
+  for (int w = tid; w < S * P; w += NT) {
     const int sw = w & (S - 1), p = w >> lgs;
     if (sw < ns) seg_sweep32<0>(X + p * pitch + sw, m, a32, fs, yb + sw * K1 + 4 * p, S);
   }
   __syncthreads();
-  for (int o = tid; o < S * K; o += kYThreads) {
+  for (int o = tid; o < S * K; o += NT) {
     const int so = o / K, q = o - so * K;
     if (so < ns) tau[so * K1 + tau_word(q, P)] = reduced_row<false>(yb + so * K1, q, D.rb + ko, nullptr, P, D.band);
   }
@@ -1085,7 +1087,7 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
     }
   } else if (live) {
     size_t eo1 = (size_t)e0 * nx;
-    for (int e1 = e0, xi = tid; e1 < n; e1 += B * RR, xi += B * kYThreads, eo1 += B * ldr) {
+    for (int e1 = e0, xi = tid; e1 < n; e1 += B * RR, xi += B * NT, eo1 += B * ldr) {
       float xv[B];
       float2 cv[B];
 #pragma unroll
@@ -1106,7 +1108,7 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
           int p, r;
           sg.map(e, p, r);
           const float4 t = *reinterpret_cast<const float4*>(ts + 4 * p);
-          dl[u] = X[p * pad + xi + u * kYThreads] - spikes32(vw4, r, t);
+          dl[u] = X[p * pad + xi + u * NT] - spikes32(vw4, r, t);
         }
       }
 #pragma unroll
@@ -1127,7 +1129,7 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
 
 __global__ void __launch_bounds__(kYThreads, 2) y_solve_ff_kernel(FFStep P, double* cn, double* cp, int keep_roles) {
   extern __shared__ __align__(16) float sm[];
-  y_solve_cols(sm, P, cn, cp, keep_roles, blockIdx.y, blockIdx.x * P.ysc);
+  y_solve_cols<kYThreads>(sm, P, cn, cp, keep_roles, blockIdx.y, blockIdx.x * P.ysc);
 }
 
 // ---------------------------------------------------------------------------
@@ -1199,7 +1201,7 @@ __global__ void __launch_bounds__(kXThreads, 7) ens_x_ff_kernel(const FFStep* __
   }
 }
 
-__global__ void __launch_bounds__(kYThreads, 2) ens_y_ff_kernel(const FFStep* __restrict__ steps,
+__global__ void __launch_bounds__(kYThreadsEns, 4) ens_y_ff_kernel(const FFStep* __restrict__ steps,
                                                                 const int* __restrict__ order,
                                                                 const int* __restrict__ start, int ng, int nitems,
                                                                 int parity) {
@@ -1210,7 +1212,7 @@ __global__ void __launch_bounds__(kYThreads, 2) ens_y_ff_kernel(const FFStep* __
     const FFStep& P = cur.at(sP, steps, order, start, ng, it);
     const int idx = it - cur.first, nstrip = (P.nx + P.ysc - 1) / P.ysc;
     const int z = idx / nstrip, col0 = (idx - z * nstrip) * P.ysc, c = P.cur0 ^ parity;
-    y_solve_cols(sm, P, P.st[c], P.st[1 - c], 0, z, col0);
+    y_solve_cols<kYThreadsEns>(sm, P, P.st[c], P.st[1 - c], 0, z, col0);
     __syncthreads();
   }
 }
@@ -1318,7 +1320,7 @@ int ens_phase_occupancy(int phase, size_t smem) {
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ens_rhs_ff_kernel<false>, kT * kBY, 0);
   }
   else if (phase == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ens_x_ff_kernel, kXThreads, smem);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ens_y_ff_kernel, kYThreads, smem);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ens_y_ff_kernel, kYThreadsEns, smem);
   cudaGetLastError();
   return b > 0 ? b : 1;
 }
@@ -1332,7 +1334,7 @@ void launch_ens_phase_ff(int phase, const FFStep* steps, const int* order, const
   } else if (phase == 1) {
     ens_x_ff_kernel<<<blocks, kXThreads, smem, st>>>(steps, order, start, ngroups, nitems);
   } else {
-    ens_y_ff_kernel<<<blocks, kYThreads, smem, st>>>(steps, order, start, ngroups, nitems, parity);
+    ens_y_ff_kernel<<<blocks, kYThreadsEns, smem, st>>>(steps, order, start, ngroups, nitems, parity);
   }
 }
 
