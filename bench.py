@@ -40,7 +40,7 @@ PREWARM_S = 1.5  # untimed steps before the first measurement (see measure())
 # ncu flushes the caches before each kernel it measures, so these are cold-cache
 # figures: intermediates that a live step finds in L2 are counted as DRAM reads.
 STEP_DRAM_BYTES_F64 = 373.58e6 + 53.25e6
-STEP_DRAM_BYTES_F32R = 373.69e6 + 19.73e6
+STEP_DRAM_BYTES_F32R = 213.88e6 + 68.92e6  # the three fused kernels
 # DRAM bytes (read + write) per launch of the FP64 step's kernels on this
 # workload, from one ncu capture of the current kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum, mean of 3 launches).  The first right-hand-side pass
@@ -166,9 +166,10 @@ def fp32_accuracy(dev, checkpoints=(100, 1000, 5000)):
 # table's lower figure (48 B per point-step: the FP64 fields C^n and C^{n-1}
 # read, C^{n+1} written, and the FP32 / double-float intermediates of the two
 # sweeps).  The fused kernels move 72 B per point as designed (right-hand side
-# 16 B in + 16 B out, x solve 8 + 8, y solve 16 in + 8 out).
+# 16 B in + 16 B out, x solve 8 + 8, y solve 16 in + 8 out), and 88 B when a
+# one-step call keeps the roles (the x solve's 16 B copy of C^n into C^{n-1}).
 FP32R_BYTES_PER_POINT = 48
-FP32R_DESIGN_BYTES_PER_POINT = 72
+FP32R_DESIGN_BYTES_PER_POINT = 88
 
 
 def fp32_roofline(pts, ms_step, peaks):
@@ -870,6 +871,28 @@ def serving_suite(dev, count, rate):
     return out
 
 
+def kernel_case(args, local_rank):
+    """The headline workload's step at one precision, W + K one-step calls and
+    nothing else: the program ncu captures of single kernels run."""
+    import torch
+
+    import paper_2101_06550_gb300 as chx
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    prec = chx.PREC_F64 if args.kernel_case == "fp64" else chx.PREC_F32_REFINE
+    plan = chx.ChPlan(N, N, LX, LX, GAMMA, DT, prec)
+    cn = torch.from_numpy(synth.field(SEED, N, N, -0.05, 0.05)).to(dev)
+    cp = cn.clone()
+    work = plan.alloc_work(dev)
+    for _ in range(args.warmup + args.steps):
+        plan.step(cn, cp, work, 1)
+    torch.cuda.synchronize()
+    plan.sync_status()
+    print(json.dumps({"kernel_case": args.kernel_case, "steps": args.warmup + args.steps,
+                      "max_abs_c": float(cn.abs().max())}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -883,12 +906,17 @@ def main():
     ap.add_argument("--serve-only", action="store_true",
                     help="run only the serving benchmarks (burst and sustainable rate) and print their JSON")
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--kernel-case", choices=["fp64", "fp32"],
+                    help="untimed: run --warmup + --steps single steps of the headline workload at that precision "
+                         "and exit (the small case that ncu captures are taken on)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.kernel_case:
+        kernel_case(args, local_rank)
     elif args.serve_only:
         import torch
 
