@@ -224,7 +224,7 @@ std::vector<int> segment_candidates(int n, int nsys, int precision);
 // gact contiguous fields of nx*ny doubles (C^n, C^{n-1}).  keep_roles = 0
 // writes C^{n+1} over prev (caller swaps); 1 writes C^n into prev and C^{n+1}
 // into cur.
-// status: device word for bounded-wait timeouts (CHX_ETIMEOUT), may be null.
+// status: the plan's device status word (no step kernel writes it at present); may be null.
 // Coarsening observables [mass, F_h, s, k1] of the first gact fields into the
 // device array out (4 per field; k1 only with with_k1 and gact == 1, else NaN).
 int group_observables(ChGroup* g, int gact, const double* fields, double* out, int with_k1, int* status,
