@@ -126,10 +126,11 @@ def max_over_ranks(values, dist, device):
     return t.tolist()
 
 
-def fp32_accuracy(dev, checkpoints=(100, 1000, 5000)):
-    """Config-3 accuracy of the FP32+refine step at steps 100, 1000 and 5000: the
-    per-step error against the CPU oracle from the state the FP64 path has reached,
-    the FP32 trajectory's error against the FP64 trajectory, and its mass drift."""
+def fp32_accuracy(dev, checkpoints=(0, 1, 100, 1000, 5000)):
+    """Config-3 accuracy of the FP32+refine step at steps 0, 1, 100, 1000 and 5000:
+    the per-step error against the CPU oracle from the state the FP64 path has
+    reached (step 0: the first step, from the rough initial state), the FP32
+    trajectory's error against the FP64 trajectory, and its mass drift."""
     import torch
 
     import oracle

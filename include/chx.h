@@ -343,8 +343,11 @@ int cn1d_step(chx_cn1d_plan* plan, double* c, int nsteps, void* stream);
  *    optionally C^{n-1}) out.  ens_slot_move copies state and factors.  Pointers may
  *    be host or device memory (cudaMemcpyDefault); n*n doubles each.
  *  - ens_autotune times `trial` steps per candidate segment count of a group's
- *    partitioned sweeps and keeps the fastest; the simulations' state is saved
- *    and restored, so the call changes no result other than by rounding order.
+ *    partitioned sweeps and keeps the fastest: every candidate x count with the
+ *    y count held, then every y count with the chosen x count (the two are
+ *    independent; px_out / py_out receive them).  The simulations' state is
+ *    saved and restored, so the call changes no result other than by rounding
+ *    order.
  *  - ens_group_set_cook turns on the Cahn-Hilliard-Cook forcing of ch_cook_run
  *    (Sec. 7.7) for every slot of a group (either precision): each later step
  *    of the group first draws the deviates of slot s with simulation id s, key

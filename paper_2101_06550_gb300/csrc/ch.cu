@@ -907,7 +907,7 @@ T* wptr(void* work, size_t off) {
 // ---------------------------------------------------------------------------
 namespace chx {
 
-FFStep ff_step_params(const ChGroup* g, int G, double* cur, double* prev, void* work, int target) {
+FFStep ff_step_params(const ChGroup* g, int G, double* cur, double* prev, void* work, int target, bool balance) {
   FFStep P{};
   P.nx = g->nx;
   P.ny = g->ny;
@@ -918,8 +918,7 @@ FFStep ff_step_params(const ChGroup* g, int G, double* cur, double* prev, void* 
   P.X = view<float>(g->X, g->ny);
   P.Y = view<float>(g->Y, g->nx);
   P.xs = x_solve_rows(g->nx, g->ny, g->X.P, target);
-  P.ysc = y_solve_cols(g->ny, g->Y.P, target);
-  P.lgys = log2_exact(P.ysc);
+  y_solve_shape(g->nx, g->ny, G, g->Y.P, target, balance, &P.ysc, &P.ynt);
   P.ypad = y_solve_pad(g->Y.m, P.ysc);
   P.lgx = log2_exact(g->X.m);
   P.lgy = log2_exact(g->Y.m);
@@ -1210,7 +1209,7 @@ static void step_f64(ChGroup* g, int G, double* cur, double* prev, void* work, i
 // which forms the update.
 static void step_f32r(ChGroup* g, int G, double* cur, double* prev, void* work, int keep_roles, cudaStream_t st,
                       Prof* prof) {
-  launch_step_ff(ff_step_params(g, G, cur, prev, work), keep_roles, prof, st);
+  launch_step_ff(ff_step_params(g, G, cur, prev, work, kFFTarget, true), keep_roles, prof, st);
 }
 
 int group_cook_deviates(ChGroup* g, int gact, double* rho, uint64_t seed, uint64_t sim0, uint64_t step,

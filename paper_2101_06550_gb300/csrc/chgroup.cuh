@@ -95,7 +95,7 @@ struct FFStep {
   int iso;             // square cells (rho = 1): the exact-scaling Laplacian
   int tx, ty;          // right-hand-side tiles per simulation along x and y
   int xs;             // x solve: rows per block
-  int ysc, lgys, ypad; // y solve: columns per block (a power of two), its log2, the shared-memory pad
+  int ysc, ynt, ypad;  // y solve: columns per block (1 to 32), threads per block (512 or 1024), shared-memory pad
   int lgx, lgy;        // log2 of the segment lengths (-1 if not a power of two)
   FFConst k;
   const float2* glff;  // per slot gamma / dx^2 (double-float)
@@ -113,7 +113,8 @@ struct FFStep {
 // Builds the parameters of the group's fused step for its first G slots, with
 // cur / prev as C^n / C^{n-1} (st = {cur, prev}, cur0 = 0); the solves' blocks
 // take about `target` points each.
-FFStep ff_step_params(const ChGroup* g, int G, double* cur, double* prev, void* work, int target = kFFTarget);
+FFStep ff_step_params(const ChGroup* g, int G, double* cur, double* prev, void* work, int target = kFFTarget,
+                      bool balance = false);
 // The three launches of one fused step (keep_roles as in group_step).
 // Shared-memory bytes of the fused x / y solves for an n-point system with P
 // segments (xs rows / S columns per block), and the tile shapes for about
@@ -122,6 +123,11 @@ size_t x_solve_smem(int n, int ny, int P, int xs);
 size_t y_solve_smem(int n, int P, int S);
 int x_solve_rows(int n, int ny, int P, int target);
 int y_solve_cols(int n, int P, int target);
+// The y strips of a single plan's step: the width S (and 512 or 1024 threads)
+// that puts the fewest columns on the busiest SM, from the default width and
+// every even width up to 32 (a width that fits one block per SM takes 1024
+// threads).  Without balance: the default width, 512 threads.
+void y_solve_shape(int nx, int ny, int G, int P, int target, bool balance, int* S, int* nt);
 int y_solve_pad(int m, int S);
 int log2_exact(int m);
 

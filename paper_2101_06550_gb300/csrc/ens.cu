@@ -544,19 +544,18 @@ extern "C" int ens_autotune(chx_ens* e, int group_id, int trial, int* px_out, in
   cudaEventCreate(&a);
   cudaEventCreate(&b);
   int rc = CHX_OK;
-  for (int P : cx) {
+  // one trial: `trial` steps of the group with px / py segments (ms, or < 0 when
+  // the candidate does not fit the group's work buffer)
+  auto trial_ms = [&](int px, int py, float* ms) -> int {
+    *ms = -1.f;
     ChGroup trialg;
-    rc = group_init(&trialg, n, n, G->l, G->l, G->gamma, e->dt, e->precision, G->capacity, P, P);
-    if (rc) break;  // group_init frees its own partial allocations
-    for (int z = 0; z < G->active && !rc; ++z)
-      if (G->slot_gamma[z] != G->gamma) rc = group_set_gamma(&trialg, z, G->slot_gamma[z]);
-    if (rc) {
+    int r = group_init(&trialg, n, n, G->l, G->l, G->gamma, e->dt, e->precision, G->capacity, px, py);
+    if (r) return r;  // group_init frees its own partial allocations
+    for (int z = 0; z < G->active && !r; ++z)
+      if (G->slot_gamma[z] != G->gamma) r = group_set_gamma(&trialg, z, G->slot_gamma[z]);
+    if (r || trialg.work_bytes > G->work_bytes) {  // a candidate that needs more scratch is skipped
       group_free(&trialg);
-      break;
-    }
-    if (trialg.work_bytes > G->work_bytes) {  // candidate needs more scratch than the group holds
-      group_free(&trialg);
-      continue;
+      return r;
     }
     group_step(&trialg, G->active, G->d_state[G->cur], G->d_state[1 - G->cur], G->d_work, 0, st, nullptr, G->status);
     G->cur = 1 - G->cur;
@@ -566,12 +565,24 @@ extern "C" int ens_autotune(chx_ens* e, int group_id, int trial, int* px_out, in
       G->cur = 1 - G->cur;
     }
     cudaEventRecord(b, st);
-    rc = cuda_check(cudaEventSynchronize(b), "ens_autotune: trial");
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, a, b);
+    r = cuda_check(cudaEventSynchronize(b), "ens_autotune: trial");
+    if (!r) cudaEventElapsedTime(ms, a, b);
     group_free(&trialg);
-    if (rc) break;
-    if (ms < best) { best = ms; bx = P; by = P; }
+    return r;
+  };
+  // coordinate search: the x count with y's fixed, then the y count with x's chosen
+  for (int pass = 0; pass < 2 && !rc; ++pass) {
+    for (int P : cx) {
+      const int px = pass == 0 ? P : bx, py = pass == 0 ? by : P;
+      float ms = -1.f;
+      rc = trial_ms(px, py, &ms);
+      if (rc) break;
+      if (ms >= 0.f && ms < best) {
+        best = ms;
+        bx = px;
+        by = py;
+      }
+    }
   }
   cudaMemcpyAsync(G->d_state[0], save, sb, cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(G->d_state[1], (char*)save + sb, sb, cudaMemcpyDeviceToDevice, st);

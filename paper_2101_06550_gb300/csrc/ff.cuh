@@ -69,7 +69,7 @@ __device__ __forceinline__ ff ff_scale2(ff x, float p2) { return ff{x.hi * p2, x
 // FP64 -> ff by bit manipulation: hi is the double truncated to 24 significand
 // bits, lo the rest rounded to 24 bits (so ~2^-48 relative).  Magnitudes below
 // 2^-126 are flushed to zero; lo is dropped below 2^-100 relative reach.
-__device__ __forceinline__ ff d2ff(double x) {
+__device__ __forceinline__ ff d2ff_general(double x) {
   const uint64_t b = (uint64_t)__double_as_longlong(x);
   const uint32_t sgn = (uint32_t)(b >> 63) << 31;
   const int e = (int)((b >> 52) & 0x7ff);
@@ -90,9 +90,33 @@ __device__ __forceinline__ ff d2ff(double x) {
   return ff{hi, lo};
 }
 
+// The same split, with a short path for 2^-74 <= |x| < 2^128 (both parts are
+// then normal floats): hi's exponent and top 23 significand bits are one
+// funnel shift of the double's two words, rebiased by one subtraction (the
+// exponent field is taken mod 2^9, and e - 896 lies in [53, 254] there, so the
+// wrap-around restores it); lo is the low 29 significand bits converted and
+// scaled by 2^(e - 1075).  The bits equal d2ff_general's, zero lo included.
+__device__ __forceinline__ ff d2ff(double x) {
+  const uint32_t w1 = (uint32_t)__double2hiint(x), w0 = (uint32_t)__double2loint(x);
+  const uint32_t e = (w1 >> 20) & 0x7ffu;
+  if (e - 949u < 202u) {
+    const uint32_t sgn = w1 & 0x80000000u;
+    const float hi = __uint_as_float((__funnelshift_l(w0, w1, 3) - 0xC0000000u) | sgn);  // 896 << 23, mod 2^32
+    const uint32_t r = w0 & 0x1FFFFFFFu;
+    const float lo = __uint2float_rn(r) * __uint_as_float((e - 948u) << 23);
+    return ff{hi, r ? __uint_as_float(__float_as_uint(lo) | sgn) : 0.f};
+  }
+  return d2ff_general(x);
+}
+
 // Exact float -> double by bit manipulation (denormal floats flush to zero).
+// Normal floats take the short path: exponent rebiased by 896 in the high word,
+// the significand's low 3 bits at the top of the low word.
 __device__ __forceinline__ double f2d_exact(float f) {
   const uint32_t u = __float_as_uint(f);
+  const uint32_t a = u & 0x7fffffffu;
+  if (a - 0x00800000u < 0x7f000000u)
+    return __hiloint2double((int)(((a >> 3) + (896u << 20)) | (u & 0x80000000u)), (int)(u << 29));
   const uint32_t e = (u >> 23) & 0xff;
   const uint64_t sgn = (uint64_t)(u >> 31) << 63;
   if (e == 0) return __longlong_as_double((long long)sgn);

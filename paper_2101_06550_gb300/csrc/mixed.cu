@@ -226,15 +226,21 @@ __device__ __forceinline__ float corr_exact(float y, float4 vh, float4 vl, float
 // [plo, phi) where the spikes' magnitudes sum to at most 1 (there the rounding
 // of the terms is no larger than that of x0 itself).
 __device__ __forceinline__ float corr_first(float y, const float4* __restrict__ vw4, const float4* __restrict__ vw4lo,
+                                            int r, int plo, int phi, float4 t);
+
+// The plain FP32 form, for a row's spikes v already loaded.
+__device__ __forceinline__ float corr_plain(float y, float4 v, float4 t) {
+  float c = v.x * t.x;
+  c = fmaf(v.y, t.y, c);
+  c = fmaf(v.z, t.z, c);
+  c = fmaf(v.w, t.w, c);
+  return y - c;
+}
+
+__device__ __forceinline__ float corr_first(float y, const float4* __restrict__ vw4, const float4* __restrict__ vw4lo,
                                             int r, int plo, int phi, float4 t) {
   const float4 v = __ldg(&vw4[r]);
-  if (r >= plo && r < phi) {
-    float c = v.x * t.x;
-    c = fmaf(v.y, t.y, c);
-    c = fmaf(v.z, t.z, c);
-    c = fmaf(v.w, t.w, c);
-    return y - c;
-  }
+  if (r >= plo && r < phi) return corr_plain(y, v, t);
   return corr_exact(y, v, __ldg(&vw4lo[r]), t);
 }
 
@@ -591,12 +597,14 @@ __device__ __forceinline__ float reduced_row(const float* yb, int q, const float
 
 // Plain FP32 spike correction of one row of a segment: V0 ta + V1 tb + W0 tc + W1 td
 // (packed spikes as in corr_exact).
-__device__ __forceinline__ float spikes32(const float4* __restrict__ vw4, int r, float4 t) {
-  const float4 v = __ldg(&vw4[r]);
+__device__ __forceinline__ float spikes_v(float4 v, float4 t) {
   float c = v.x * t.x;
   c = fmaf(v.y, t.y, c);
   c = fmaf(v.z, t.z, c);
   return fmaf(v.w, t.w, c);
+}
+__device__ __forceinline__ float spikes32(const float4* __restrict__ vw4, int r, float4 t) {
+  return spikes_v(__ldg(&vw4[r]), t);
 }
 
 // The reduced unknowns are stored by the segment that uses them: segment p's
@@ -716,6 +724,23 @@ __device__ __forceinline__ void x_solve_rows(float* sm, const FFStep& PS, int ro
     const float* ts = tau + s * K;
     const float* xs = X + s * Ls;
     float* dst = x0s + (size_t)(row0 + s) * n;
+    if (kXThreads % m == 0) {
+      // m divides the block: the thread's points all sit at row r = tid % m of
+      // their segments, so its spikes (and the form of its correction) are fixed
+      const int r = tid % m;
+      const float4 v = __ldg(&vw4[r]);
+      const bool plain = r >= D.plo && r < D.phi;
+      const float4 vl = plain ? v : __ldg(&vw4l[r]);
+#pragma unroll 2
+      for (int e = tid; e < n; e += kXThreads) {
+        int p, rr;
+        sg.map(e, p, rr);  // rr == r
+        const float4 t = *reinterpret_cast<const float4*>(ts + 4 * p);
+        const float y = xs[e + p];
+        dst[e] = plain ? corr_plain(y, v, t) : corr_exact(y, v, vl, t);
+      }
+      continue;
+    }
 #pragma unroll 2
     for (int e = tid; e < n; e += kXThreads) {
       int p, r;
@@ -818,6 +843,8 @@ __device__ __forceinline__ void x_solve_rows(float* sm, const FFStep& PS, int ro
     const float* x0 = x0s + ro;
     float* wh = whi + ro;
     float* wl = wlo + ro;
+    const bool fixr = kXThreads % m == 0;  // as in the correction: one row of the segment block per thread
+    const float4 vr = fixr ? __ldg(&vw4[tid % m]) : make_float4(0.f, 0.f, 0.f, 0.f);
     for (int e1 = tid; e1 < n; e1 += 4 * kXThreads) {
       float xv[4];
 #pragma unroll
@@ -831,7 +858,7 @@ __device__ __forceinline__ void x_solve_rows(float* sm, const FFStep& PS, int ro
           int p, r;
           sg.map(e, p, r);
           const float4 t = *reinterpret_cast<const float4*>(ts + 4 * p);
-          dl[u] = xs[e + p] - spikes32(vw4, r, t);
+          dl[u] = xs[e + p] - (fixr ? spikes_v(vr, t) : spikes32(vw4, r, t));
         }
       }
 #pragma unroll
@@ -871,8 +898,9 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
   const int nx = PS.nx, n = PS.ny, pad = PS.ypad, lgm = PS.lgy;
   const DirView<float>& D = PS.Y;
   const float2* __restrict__ aff = PS.affY;
-  const int S = PS.ysc, lgs = PS.lgys;  // columns per block (a power of two <= 32)
-  const int RR = NT >> lgs;      // rows a pass of the block covers
+  const int S = PS.ysc;      // columns per block (1 to 32)
+  const int RR = NT / S;     // rows a pass of the block covers
+  const int used = RR * S;   // threads of the row passes (the rest idle there)
   // per-column boundary values and reduced unknowns at a pitch of 4P + 4 floats:
   // 16-byte aligned rows whose starts fall on different banks for a warp's columns
   const int m = D.m, P = D.P, K = 4 * P, K1 = K + 4, pitch = m * S + pad;
@@ -884,8 +912,8 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
   const int slot = z;
   const int ns = nx - col0 < S ? nx - col0 : S;
   const size_t zo = (size_t)z * nx * n;
-  const int tid = threadIdx.x, s = tid & (S - 1), e0 = tid >> lgs;
-  const bool live = s < ns;
+  const int tid = threadIdx.x, s = tid % S, e0 = tid / S;
+  const bool live = s < ns && tid < used;
   const int c = col0 + s;
   // column c of the simulation's fields (row e at + e * nx)
   const float* __restrict__ fhi = PS.whi + zo + c;  // the y solve's right-hand side is the x result
@@ -900,11 +928,14 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
                        reinterpret_cast<uintptr_t>(PS.x0s)) & 7) == 0 &&
                      ((reinterpret_cast<uintptr_t>(PS.cbar) | reinterpret_cast<uintptr_t>(dst0)) & 15) == 0;
   double* __restrict__ out2 = dst0 + zo + col0;  // strip base
+  // pair passes: column pair cq / 2 of hp, rows rq + k RRp (threads past RRp hp idle there)
+  const int hp = S > 1 ? S / 2 : 1, RRp = NT / hp, cq = 2 * (tid % hp), rq = tid / hp;
+  const bool plive = tid < RRp * hp;
   cn += zo + c;
   cp += zo + c;
   const size_t ldr = (size_t)RR * nx;  // a pass of the block in elements
-  // row e = e0 + k RR of the thread's column is at X[p * pad + tid + k * NT]
-  // (e S + s = tid + k NT), p its segment; the global loop pointers
+  // row e = e0 + k RR of the thread's column is at X[p * pad + tid + k * used]
+  // (e S + s = tid + k RR S), p its segment; the global loop pointers
   // advance by a pass of the block
   auto seg = [&](int e) {
     int p, r;
@@ -915,19 +946,19 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
   for (int i = tid; i < m; i += NT) fs[i] = __ldg(&D.lu4[(size_t)slot * m + i]);
   if (live) {
     const float* src = fhi + (size_t)e0 * nx;
-    for (int e1 = e0, xi = tid; e1 < n; e1 += B * RR, xi += B * NT, src += B * ldr) {
+    for (int e1 = e0, xi = tid; e1 < n; e1 += B * RR, xi += B * used, src += B * ldr) {
       float v[B];
 #pragma unroll
       for (int u = 0; u < B; ++u) v[u] = e1 + u * RR < n ? src[u * ldr] : 0.f;
 #pragma unroll
       for (int u = 0; u < B; ++u)
-        if (e1 + u * RR < n) X[seg(e1 + u * RR) * pad + xi + u * NT] = v[u];
+        if (e1 + u * RR < n) X[seg(e1 + u * RR) * pad + xi + u * used] = v[u];
     }
   }
   __syncthreads();
   const float a32 = D.a[slot];
   for (int w = tid; w < S * P; w += NT) {
-    const int sw = w & (S - 1), p = w >> lgs;
+    const int p = w / S, sw = w - p * S;
     if (sw < ns) seg_sweep32<0>(X + p * pitch + sw, m, a32, fs, yb + sw * K1 + 4 * p, S);
   }
   __syncthreads();
@@ -941,11 +972,10 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
   const float4* vw4l = D.vw4lo + (size_t)slot * m;
   const float* ts = tau + s * K1;
   if (pairs) {
-    const int cq = 2 * (tid & (S / 2 - 1)), RR2 = 2 * RR;
     const float* t0 = tau + cq * K1;
     float* __restrict__ x02 = PS.x0s + zo + col0 + cq;
 #pragma unroll 2
-    for (int e = tid >> (lgs - 1); e < n; e += RR2) {
+    for (int e = plive ? rq : n; e < n; e += RRp) {
       int p, r;
       sg.map(e, p, r);
       const float2 yv = *reinterpret_cast<const float2*>(X + p * pad + e * S + cq);
@@ -957,7 +987,7 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
   } else if (live) {
     float* dst = x0s + (size_t)e0 * nx;
 #pragma unroll 2
-    for (int e = e0, xi = tid; e < n; e += RR, xi += NT, dst += ldr) {
+    for (int e = e0, xi = tid; e < n; e += RR, xi += used, dst += ldr) {
       int p, r;
       sg.map(e, p, r);
       const float4 t = *reinterpret_cast<const float4*>(ts + 4 * p);
@@ -970,13 +1000,13 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
     // of a row (8-byte loads of f and of the five x0 neighbours, from the
     // scratch; both lanes of the packed arithmetic) and rows 2 RR apart
     const ff2 a = ff2_splat(ffc(aff[slot]));
-    const int cq = 2 * (tid & (S / 2 - 1)), r0 = tid >> (lgs - 1), RR2 = 2 * RR;
+    const int RR2 = RRp;
     const size_t cz = zo + col0 + cq;
     const float* __restrict__ fh2 = PS.whi + cz;
     const float* __restrict__ fl2 = PS.wlo + cz;
     const float* __restrict__ x02 = PS.x0s + cz;
     const size_t nx1 = nx;
-    for (int e1 = r0; e1 < n; e1 += 2 * RR2) {  // two rows' loads in flight
+    for (int e1 = plive ? rq : n; e1 < n; e1 += 2 * RR2) {  // two rows' loads in flight
       float2 h[2], l[2], w[2][5];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
@@ -1007,7 +1037,7 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
     const ff2 a = ff2_splat(ffc(aff[slot]));
     const size_t nx1 = nx, nx2 = 2 * (size_t)nx;
     size_t eo1 = (size_t)e0 * nx;
-    for (int e1 = e0, xi = tid; e1 < n; e1 += 2 * RR, xi += 2 * NT, eo1 += 2 * ldr) {
+    for (int e1 = e0, xi = tid; e1 < n; e1 += 2 * RR, xi += 2 * used, eo1 += 2 * ldr) {
       float fh[2], fl[2], w[2][5];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
@@ -1036,13 +1066,13 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int e = e1 + u * RR;
-        if (e < n) X[seg(e) * pad + xi + u * NT] = u ? rv.y : rv.x;
+        if (e < n) X[seg(e) * pad + xi + u * used] = u ? rv.y : rv.x;
       }
     }
   }
   __syncthreads();
   for (int w = tid; w < S * P; w += NT) {
-    const int sw = w & (S - 1), p = w >> lgs;
+    const int p = w / S, sw = w - p * S;
     if (sw < ns) seg_sweep32<0>(X + p * pitch + sw, m, a32, fs, yb + sw * K1 + 4 * p, S);
   }
   __syncthreads();
@@ -1052,12 +1082,12 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
   }
   __syncthreads();
   if (pairs) {
-    const int cq = 2 * (tid & (S / 2 - 1)), RR2 = 2 * RR;
+    const int RR2 = RRp;
     const float* t0 = tau + cq * K1;
     const float* __restrict__ x02 = PS.x0s + zo + col0 + cq;
     const float2* __restrict__ cb2 = PS.cbar + zo + col0 + cq;
     double* __restrict__ o2 = out2 + cq;
-    for (int e1 = tid >> (lgs - 1); e1 < n; e1 += 2 * RR2) {  // two rows' loads in flight
+    for (int e1 = plive ? rq : n; e1 < n; e1 += 2 * RR2) {  // two rows' loads in flight
       float2 xv[2];
       float4 cv[2];  // Cbar of the two columns: (hi, lo, hi, lo)
 #pragma unroll
@@ -1087,7 +1117,7 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
     }
   } else if (live) {
     size_t eo1 = (size_t)e0 * nx;
-    for (int e1 = e0, xi = tid; e1 < n; e1 += B * RR, xi += B * NT, eo1 += B * ldr) {
+    for (int e1 = e0, xi = tid; e1 < n; e1 += B * RR, xi += B * used, eo1 += B * ldr) {
       float xv[B];
       float2 cv[B];
 #pragma unroll
@@ -1108,7 +1138,7 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
           int p, r;
           sg.map(e, p, r);
           const float4 t = *reinterpret_cast<const float4*>(ts + 4 * p);
-          dl[u] = X[p * pad + xi + u * NT] - spikes32(vw4, r, t);
+          dl[u] = X[p * pad + xi + u * used] - spikes32(vw4, r, t);
         }
       }
 #pragma unroll
@@ -1127,9 +1157,11 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
   }
 }
 
-__global__ void __launch_bounds__(kYThreads, 2) y_solve_ff_kernel(FFStep P, double* cn, double* cp, int keep_roles) {
+template <int NT>
+__global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 2) y_solve_ff_kernel(FFStep P, double* cn, double* cp,
+                                                                            int keep_roles) {
   extern __shared__ __align__(16) float sm[];
-  y_solve_cols<kYThreads>(sm, P, cn, cp, keep_roles, blockIdx.y, blockIdx.x * P.ysc);
+  y_solve_cols<NT>(sm, P, cn, cp, keep_roles, blockIdx.y, blockIdx.x * P.ysc);
 }
 
 // ---------------------------------------------------------------------------
@@ -1270,13 +1302,42 @@ int y_solve_cols(int n, int P, int target) {
   return y_solve_smem(n, P, S) <= kSmemMax ? S : 0;
 }
 
+void y_solve_shape(int nx, int ny, int G, int P, int target, bool balance, int* S_out, int* nt_out) {
+  const int S0 = y_solve_cols(ny, P, target);
+  *S_out = S0;
+  *nt_out = 512;
+  if (!balance || S0 < 1) return;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 0;
+    cudaGetLastError();
+    if (sms < 1) return;
+  }
+  // columns on the busiest SM: strips are handed out one per SM in turn
+  auto cost = [&](int S) { return (long long)ceil_div((size_t)ceil_div((size_t)nx, (size_t)S) * G, (size_t)sms) * S; };
+  long long best = cost(S0);
+  for (int S = 4; S <= 32; S += 2) {
+    const size_t sm = y_solve_smem(ny, P, S);
+    if (sm > kSmemMax - 1024) continue;
+    const long long c = cost(S);
+    if (c * 20 < best * 19) {  // at least 5% fewer columns on the busiest SM
+      best = c;
+      *S_out = S;
+      *nt_out = sm <= 112 * 1024 ? 512 : 1024;  // two 512-thread blocks per SM, else one of 1024
+    }
+  }
+}
+
 static_assert(sizeof(FFStep) <= 1024, "the ensemble kernels' static parameter copy must fit the reserved kilobyte");
 size_t ens_phase_smem_max() { return kSmemMax - 1024; }
 
 int prepare_solve_ff() {
   int rc = cuda_check(cudaFuncSetAttribute(x_solve_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax),
                       "mixed: shared-memory opt-in");
-  if (!rc) rc = cuda_check(cudaFuncSetAttribute(y_solve_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax), "mixed: shared-memory opt-in");
+  if (!rc) rc = cuda_check(cudaFuncSetAttribute(y_solve_ff_kernel<kYThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax), "mixed: shared-memory opt-in");
+  if (!rc) rc = cuda_check(cudaFuncSetAttribute(y_solve_ff_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax), "mixed: shared-memory opt-in");
   // the ensemble kernels also hold a group's parameters in static shared memory
   if (!rc) rc = cuda_check(cudaFuncSetAttribute(ens_x_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ens_phase_smem_max()), "mixed: shared-memory opt-in");
   if (!rc) rc = cuda_check(cudaFuncSetAttribute(ens_y_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ens_phase_smem_max()), "mixed: shared-memory opt-in");
@@ -1303,7 +1364,9 @@ void launch_step_ff(const FFStep& P, int keep_roles, Prof* prof, cudaStream_t st
   {
     ProfScope ps(prof, kYSolve, st);
     const dim3 grid(ceil_div(P.nx, P.ysc), P.G);
-    y_solve_ff_kernel<<<grid, kYThreads, y_solve_smem(P.ny, P.Y.P, P.ysc), st>>>(P, P.st[0], P.st[1], keep_roles);
+    const size_t smem = y_solve_smem(P.ny, P.Y.P, P.ysc);
+    if (P.ynt == 1024) y_solve_ff_kernel<1024><<<grid, 1024, smem, st>>>(P, P.st[0], P.st[1], keep_roles);
+    else y_solve_ff_kernel<kYThreads><<<grid, kYThreads, smem, st>>>(P, P.st[0], P.st[1], keep_roles);
   }
 }
 
