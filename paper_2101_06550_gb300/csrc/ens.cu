@@ -520,6 +520,49 @@ extern "C" int ens_group_step(chx_ens* e, int group_id, int nsteps, void* stream
 // Times `trial` steps of the group for each candidate pair of segment counts
 // and keeps the fastest.  The state of the active slots is saved and restored
 // around the trials, so the call changes no simulation.
+// `trial` steps of group G's active slots with factors g by the packed phase
+// launches the FP32 ensemble schedule runs, on a one-group schedule held in
+// `dev` (room for one FFStep, then the order and the three phases' item
+// ranges).  ms < 0: the candidate's tiles do not fit.  Steps G's state (the
+// caller saves it) and flips G->cur per step.
+static int time_packed_group(chx_ens* e, EnsGroup* G, ChGroup* g, int trial, void* dev, cudaStream_t st,
+                             cudaEvent_t a, cudaEvent_t b, float* ms) {
+  *ms = -1.f;
+  FFStep P = ff_step_params(g, G->active, G->d_state[0], G->d_state[1], G->d_work, e->sched->target);
+  P.cur0 = G->cur;
+  if (P.xs < 1 || P.ysc < 1) return CHX_OK;
+  const size_t smem[3] = {0, x_solve_smem(P.nx, P.ny, P.X.P, P.xs), y_solve_smem(P.ny, P.Y.P, P.ysc)};
+  if (smem[1] > ens_phase_smem_max() || smem[2] > ens_phase_smem_max()) return CHX_OK;
+  int items[3], host_ints[1 + 3 * 2], blocks[3], sms = 0, dv = 0;
+  int rc = cuda_check(cudaGetDevice(&dv), "ens_autotune: device");
+  if (!rc) rc = cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dv), "ens_autotune: SMs");
+  if (rc) return rc;
+  host_ints[0] = 0;  // the order: the one group
+  for (int ph = 0; ph < 3; ++ph) {
+    items[ph] = ens_phase_items(ph, P);
+    host_ints[1 + 2 * ph] = 0;
+    host_ints[2 + 2 * ph] = items[ph];
+    blocks[ph] = std::min(items[ph], sms * ens_phase_occupancy(ph, smem[ph]));
+  }
+  FFStep* d_steps = (FFStep*)dev;
+  int* d_ints = (int*)((char*)dev + ((sizeof(FFStep) + 15) & ~(size_t)15));
+  if ((rc = cuda_check(cudaMemcpy(d_steps, &P, sizeof(FFStep), cudaMemcpyHostToDevice), "ens_autotune: upload")) ||
+      (rc = cuda_check(cudaMemcpy(d_ints, host_ints, sizeof(host_ints), cudaMemcpyHostToDevice), "ens_autotune: upload")))
+    return rc;
+  auto one = [&](int q) {
+    for (int ph = 0; ph < 3; ++ph)
+      launch_ens_phase_ff(ph, d_steps, d_ints, d_ints + 1 + 2 * ph, 1, items[ph], blocks[ph], q, smem[ph], st);
+  };
+  one(0);  // warm-up step
+  cudaEventRecord(a, st);
+  for (int k = 1; k <= trial; ++k) one(k & 1);
+  cudaEventRecord(b, st);
+  rc = cuda_check(cudaEventSynchronize(b), "ens_autotune: trial");
+  if (!rc) cudaEventElapsedTime(ms, a, b);
+  if ((1 + trial) & 1) G->cur = 1 - G->cur;
+  return rc;
+}
+
 extern "C" int ens_autotune(chx_ens* e, int group_id, int trial, int* px_out, int* py_out, void* stream) {
   EnsGroup* G = get_group(e, group_id);
   if (!G || trial < 1) return fail(CHX_EINVAL, "ens_autotune: bad argument");
@@ -540,6 +583,12 @@ extern "C" int ens_autotune(chx_ens* e, int group_id, int trial, int* px_out, in
   cudaMemcpyAsync(save, G->d_state[0], sb, cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync((char*)save + sb, G->d_state[1], sb, cudaMemcpyDeviceToDevice, st);
   const int cur0 = G->cur;
+  void* sched_scratch = nullptr;  // a one-group packed schedule (FP32 + refinement)
+  if (packed(e) && cudaMalloc(&sched_scratch, 1024 + 64) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(save);
+    return fail(CHX_ENOMEM, "ens_autotune: schedule scratch");
+  }
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
@@ -554,6 +603,11 @@ extern "C" int ens_autotune(chx_ens* e, int group_id, int trial, int* px_out, in
     for (int z = 0; z < G->active && !r; ++z)
       if (G->slot_gamma[z] != G->gamma) r = group_set_gamma(&trialg, z, G->slot_gamma[z]);
     if (r || trialg.work_bytes > G->work_bytes) {  // a candidate that needs more scratch is skipped
+      group_free(&trialg);
+      return r;
+    }
+    if (packed(e)) {  // FP32 + refinement: timed as the ensemble runs it, by the packed phase launches
+      r = time_packed_group(e, G, &trialg, trial, sched_scratch, st, a, b, ms);
       group_free(&trialg);
       return r;
     }
@@ -589,6 +643,7 @@ extern "C" int ens_autotune(chx_ens* e, int group_id, int trial, int* px_out, in
   G->cur = cur0;
   cudaStreamSynchronize(st);
   cudaFree(save);
+  cudaFree(sched_scratch);
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (rc) return rc;

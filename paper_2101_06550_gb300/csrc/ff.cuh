@@ -90,24 +90,27 @@ __device__ __forceinline__ ff d2ff_general(double x) {
   return ff{hi, lo};
 }
 
-// The same split, with a short path for 2^-74 <= |x| < 2^128 (both parts are
-// then normal floats): hi's exponent and top 23 significand bits are one
+// The same split by a short path, exact for 2^-74 <= |x| < 2^128 (both parts
+// are then normal floats): hi's exponent and top 23 significand bits are one
 // funnel shift of the double's two words, rebiased by one subtraction (the
 // exponent field is taken mod 2^9, and e - 896 lies in [53, 254] there, so the
 // wrap-around restores it); lo is the low 29 significand bits converted and
-// scaled by 2^(e - 1075).  The bits equal d2ff_general's, zero lo included.
-__device__ __forceinline__ ff d2ff(double x) {
+// scaled by 2^(e - 1075).  No branch: `bad` is set when x is outside that
+// range, and the caller then redoes its batch with d2ff_general (so a batch's
+// loads are all issued before any test of their values).  Where it applies the
+// bits equal d2ff_general's, zero lo included.
+__device__ __forceinline__ ff d2ff_fast(double x, bool& bad) {
   const uint32_t w1 = (uint32_t)__double2hiint(x), w0 = (uint32_t)__double2loint(x);
   const uint32_t e = (w1 >> 20) & 0x7ffu;
-  if (e - 949u < 202u) {
-    const uint32_t sgn = w1 & 0x80000000u;
-    const float hi = __uint_as_float((__funnelshift_l(w0, w1, 3) - 0xC0000000u) | sgn);  // 896 << 23, mod 2^32
-    const uint32_t r = w0 & 0x1FFFFFFFu;
-    const float lo = __uint2float_rn(r) * __uint_as_float((e - 948u) << 23);
-    return ff{hi, r ? __uint_as_float(__float_as_uint(lo) | sgn) : 0.f};
-  }
-  return d2ff_general(x);
+  bad = bad || e - 949u >= 202u;
+  const uint32_t sgn = w1 & 0x80000000u;
+  const float hi = __uint_as_float((__funnelshift_l(w0, w1, 3) - 0xC0000000u) | sgn);  // 896 << 23, mod 2^32
+  const uint32_t r = w0 & 0x1FFFFFFFu;
+  const float lo = __uint2float_rn(r) * __uint_as_float((e - 948u) << 23);
+  return ff{hi, r ? __uint_as_float(__float_as_uint(lo) | sgn) : 0.f};
 }
+
+__device__ __forceinline__ ff d2ff(double x) { return d2ff_general(x); }
 
 // Exact float -> double by bit manipulation (denormal floats flush to zero).
 // Normal floats take the short path: exponent rebiased by 896 in the high word,

@@ -103,7 +103,10 @@ __device__ __forceinline__ void rhs_ff_tile(RhsSmem<NOISE>& sh, const FFStep& P,
   auto stage = [&](int ly, int lx) {
     const int gi = wrap_near(i0 - 2 + lx, nx), gj = wrap_near(j0 - 2 + ly, ny);
     const size_t p = (size_t)gj * nx + gi;
-    const ff a = d2ff(cn[p]), b = d2ff(cp[p]);
+    const double xa = cn[p], xb = cp[p];
+    bool bad = false;
+    ff a = d2ff_fast(xa, bad), b = d2ff_fast(xb, bad);
+    if (bad) a = d2ff_general(xa), b = d2ff_general(xb);
     s_cn[ly][lx] = a;
     s_cb[ly][lx] = ff_sub(ff_scale2(a, 2.f), b);
   };
@@ -113,7 +116,10 @@ __device__ __forceinline__ void rhs_ff_tile(RhsSmem<NOISE>& sh, const FFStep& P,
       const int gi0 = wrap_near(i0 - 2 + lx0, nx), gj0 = wrap_near(j0 - 2 + ly0, ny);
       const int gi1 = wrap_near(i0 - 2 + lx1, nx), gj1 = wrap_near(j0 - 2 + ly1, ny);
       const size_t p0 = (size_t)gj0 * nx + gi0, p1 = (size_t)gj1 * nx + gi1;
-      const ff a0 = d2ff(cn[p0]), b0 = d2ff(cp[p0]), a1 = d2ff(cn[p1]), b1 = d2ff(cp[p1]);
+      const double xa0 = cn[p0], xb0 = cp[p0], xa1 = cn[p1], xb1 = cp[p1];
+      bool bad = false;
+      ff a0 = d2ff_fast(xa0, bad), b0 = d2ff_fast(xb0, bad), a1 = d2ff_fast(xa1, bad), b1 = d2ff_fast(xb1, bad);
+      if (bad) a0 = d2ff_general(xa0), b0 = d2ff_general(xb0), a1 = d2ff_general(xa1), b1 = d2ff_general(xb1);
       s_cn[ly0][lx0] = a0;
       s_cn[ly1][lx1] = a1;
       const ff2 cb = ff2_sub(ff2_scale2(ff2_pack(a0, a1), 2.f), ff2_pack(b0, b1));
