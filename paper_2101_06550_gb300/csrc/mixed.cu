@@ -37,28 +37,19 @@ __device__ __forceinline__ int wrap_near(int i, int n) {
 
 __device__ __forceinline__ ff ffc(float2 c) { return ff{c.x, c.y}; }
 
-// L'(u) = (E + W) + rho (N + S) + kap C on shared-memory ff tiles; for a
-// square cell (rho = 1, kap = -4) the scalings are exact and skipped.
+// L'(u) = (E + W) + rho (N + S) + kap C at (y, x) of a shared tile stored as
+// separate high and low arrays of float2 (one simulation tile per lane); for a
+// square cell (rho = 1, kap = -4) the scalings are exact and skipped.  Each
+// lane performs the scalar double-float operations in the same order.
 template <int LD, bool kIso>
-__device__ __forceinline__ ff lap_ff(const ff (*t)[LD], int y, int x, ff rho, ff kap) {
-  ff a = ff_add(t[y][x - 1], t[y][x + 1]);
-  const ff b = ff_add(t[y - 1][x], t[y + 1][x]);
-  if (kIso) return ff_add(ff_add(a, b), ff_scale2(t[y][x], -4.f));
-  a = ff_add(a, ff_mul(rho, b));
-  return ff_add(a, ff_mul(kap, t[y][x]));
-}
-
-// The same at two points (y0, x0), (y1, x1) with packed arithmetic.
-template <int LD, bool kIso>
-__device__ __forceinline__ ff2 lap_ff2(const ff (*t)[LD], int y0, int x0, int y1, int x1, ff2 rho, ff2 kap) {
-  ff2 a = ff2_add(ff2_pack(t[y0][x0 - 1], t[y1][x1 - 1]), ff2_pack(t[y0][x0 + 1], t[y1][x1 + 1]));
-  const ff2 b = ff2_add(ff2_pack(t[y0 - 1][x0], t[y1 - 1][x1]), ff2_pack(t[y0 + 1][x0], t[y1 + 1][x1]));
-  const ff2 c = ff2_pack(t[y0][x0], t[y1][x1]);
+__device__ __forceinline__ ff2 lap_soa(const float2 (*h)[LD], const float2 (*l)[LD], int y, int x, ff2 rho, ff2 kap) {
+  ff2 a = ff2_add(ff2{h[y][x - 1], l[y][x - 1]}, ff2{h[y][x + 1], l[y][x + 1]});
+  const ff2 b = ff2_add(ff2{h[y - 1][x], l[y - 1][x]}, ff2{h[y + 1][x], l[y + 1][x]});
+  const ff2 c{h[y][x], l[y][x]};
   if (kIso) return ff2_add(ff2_add(a, b), ff2_scale2(c, -4.f));
   a = ff2_add(a, ff2_mul(rho, b));
   return ff2_add(a, ff2_mul(kap, c));
 }
-
 
 // Right-hand side of Eq. 3.1 in double-float: r = k2 L'(M) - k1 (C^n - C^{n-1}),
 // M = C^3 - C - gl L'(Cbar), in one pass over 32 x 32 tiles (M formed on the
@@ -66,7 +57,11 @@ __device__ __forceinline__ ff2 lap_ff2(const ff (*t)[LD], int y0, int x0, int y1
 // row-major (rhi, rlo: [z][j][i]) for the fused x solve, and Cbar = 2 C^n -
 // C^{n-1} as a double-float pair (cbo) for the update.  (The FP64 step
 // splits this into two passes to save the ring's FP64 work; here the ring
-// costs issue slots on the FP32 pipes.)
+// costs issue slots on the FP32 pipes.)  A block takes two vertically
+// adjacent tiles, A (rows j0 .. j0 + 31) and B (the next 32 rows), one in
+// each lane of the packed FP32x2 arithmetic: its shared tiles hold float2
+// (lane A, lane B) in separate high and low arrays, so every operand of a
+// packed double-float operation is a single 64-bit shared-memory load.
 //
 // NOISE (Cahn-Hilliard-Cook, Sec. 7.7): the forcing term (2/3) dt eta is
 // formed in FP64 on the otherwise idle FP64 unit (one subtraction and one FMA
@@ -74,123 +69,102 @@ __device__ __forceinline__ ff2 lap_ff2(const ff (*t)[LD], int y0, int x0, int y1
 // double-float pair.
 template <bool NOISE>
 struct RhsSmem {
-  ff cn[kT + 4][kT + 5];
-  ff cb[kT + 4][kT + 5];
-  ff m[kT + 2][kT + 3];
-  ff nz[NOISE ? kT : 1][kT + 1];
+  float2 cnh[kT + 4][kT + 5], cnl[kT + 4][kT + 5];  // C^n
+  float2 cbh[kT + 4][kT + 5], cbl[kT + 4][kT + 5];  // Cbar
+  float2 mh[kT + 2][kT + 3], ml[kT + 2][kT + 3];    // M on the tile and its ring
+  float2 nzh[NOISE ? kT : 1][kT + 1], nzl[NOISE ? kT : 1][kT + 1];
 };
 
-// One 32 x 32 tile (bx, by) of simulation z, by a 32 x 8 thread block; cn / cp
-// are the group's C^n / C^{n-1} buffers.
+// Tiles (bx, by) and (bx, by + 1) of simulation z, by a 32 x 8 thread block;
+// cn / cp are the group's C^n / C^{n-1} buffers.  Tile B may lie past the
+// grid's last row: its loads wrap like the halo's and its stores are skipped.
 template <bool kIso, bool NOISE>
-__device__ __forceinline__ void rhs_ff_tile(RhsSmem<NOISE>& sh, const FFStep& P, const double* __restrict__ cn,
+__device__ __forceinline__ void rhs_ff_pair(RhsSmem<NOISE>& sh, const FFStep& P, const double* __restrict__ cn,
                                             const double* __restrict__ cp, int z, int bx, int by) {
-  auto& s_cn = sh.cn;
-  auto& s_cb = sh.cb;
-  auto& s_m = sh.m;
-  auto& s_nz = sh.nz;
   const int nx = P.nx, ny = P.ny;
   float* __restrict__ rhi = P.fhi;
   float* __restrict__ rlo = P.flo;
   float2* __restrict__ cbo = P.cbar;
   const double* __restrict__ dev = P.noise;
   const double nkx = P.nkx, nky = P.nky;
-  const ff rho = ffc(P.k.rho), kap = ffc(P.k.kap), gl = ffc(P.glff[z]), k1 = ffc(P.k.k1), k2 = ffc(P.k.k2);
+  const ff2 rho2 = ff2_splat(ffc(P.k.rho)), kap2 = ff2_splat(ffc(P.k.kap)), gl2 = ff2_splat(ffc(P.glff[z]));
+  const ff2 k12 = ff2_splat(ffc(P.k.k1)), k22 = ff2_splat(ffc(P.k.k2));
   cn += (size_t)z * nx * ny;
   cp += (size_t)z * nx * ny;
   const int i0 = bx * kT, j0 = by * kT;
   const int tid = threadIdx.y * kT + threadIdx.x;
+  // C^n and Cbar = 2 C^n - C^{n-1} at one staged point of both tiles; the four
+  // loads are issued before any test of their values
   auto stage = [&](int ly, int lx) {
-    const int gi = wrap_near(i0 - 2 + lx, nx), gj = wrap_near(j0 - 2 + ly, ny);
-    const size_t p = (size_t)gj * nx + gi;
-    const double xa = cn[p], xb = cp[p];
+    const int gi = wrap_near(i0 - 2 + lx, nx);
+    const size_t pa = (size_t)wrap_near(j0 - 2 + ly, ny) * nx + gi;
+    const size_t pb = (size_t)wrap_near(j0 + kT - 2 + ly, ny) * nx + gi;
+    const double xa = cn[pa], ya = cp[pa], xb = cn[pb], yb = cp[pb];
     bool bad = false;
-    ff a = d2ff_fast(xa, bad), b = d2ff_fast(xb, bad);
-    if (bad) a = d2ff_general(xa), b = d2ff_general(xb);
-    s_cn[ly][lx] = a;
-    s_cb[ly][lx] = ff_sub(ff_scale2(a, 2.f), b);
+    ff a0 = d2ff_fast(xa, bad), b0 = d2ff_fast(ya, bad), a1 = d2ff_fast(xb, bad), b1 = d2ff_fast(yb, bad);
+    if (bad) a0 = d2ff_general(xa), b0 = d2ff_general(ya), a1 = d2ff_general(xb), b1 = d2ff_general(yb);
+    const ff2 c = ff2_pack(a0, a1);
+    sh.cnh[ly][lx] = c.hi;
+    sh.cnl[ly][lx] = c.lo;
+    const ff2 cb = ff2_sub(ff2_scale2(c, 2.f), ff2_pack(b0, b1));
+    sh.cbh[ly][lx] = cb.hi;
+    sh.cbl[ly][lx] = cb.lo;
   };
-  {
-    // two staged points per packed pass: Cbar = 2 C^n - C^{n-1} on both at once
-    auto stage2 = [&](int ly0, int lx0, int ly1, int lx1) {
-      const int gi0 = wrap_near(i0 - 2 + lx0, nx), gj0 = wrap_near(j0 - 2 + ly0, ny);
-      const int gi1 = wrap_near(i0 - 2 + lx1, nx), gj1 = wrap_near(j0 - 2 + ly1, ny);
-      const size_t p0 = (size_t)gj0 * nx + gi0, p1 = (size_t)gj1 * nx + gi1;
-      const double xa0 = cn[p0], xb0 = cp[p0], xa1 = cn[p1], xb1 = cp[p1];
-      bool bad = false;
-      ff a0 = d2ff_fast(xa0, bad), b0 = d2ff_fast(xb0, bad), a1 = d2ff_fast(xa1, bad), b1 = d2ff_fast(xb1, bad);
-      if (bad) a0 = d2ff_general(xa0), b0 = d2ff_general(xb0), a1 = d2ff_general(xa1), b1 = d2ff_general(xb1);
-      s_cn[ly0][lx0] = a0;
-      s_cn[ly1][lx1] = a1;
-      const ff2 cb = ff2_sub(ff2_scale2(ff2_pack(a0, a1), 2.f), ff2_pack(b0, b1));
-      s_cb[ly0][lx0] = ff2_first(cb);
-      s_cb[ly1][lx1] = ff2_second(cb);
-    };
-    int ly = threadIdx.y;
-    for (; ly + kBY < kT + 4; ly += 2 * kBY) stage2(ly, threadIdx.x, ly + kBY, threadIdx.x);
-    if (ly < kT + 4) stage(ly, threadIdx.x);
-  }
+  for (int ly = threadIdx.y; ly < kT + 4; ly += kBY) stage(ly, threadIdx.x);
   if (tid < 4 * (kT + 4)) stage(tid >> 2, kT + (tid & 3));
   if (NOISE) {
     const size_t N = (size_t)nx * ny;
     const double* rx = dev + (size_t)z * 2 * N;
     const double* ry = rx + N;
     for (int lj = threadIdx.y; lj < kT; lj += kBY) {
-      const int li = threadIdx.x, gi = i0 + li, gj = j0 + lj;
-      double v = 0;
-      if (gi < nx && gj < ny) {
-        const size_t q = (size_t)gj * nx + gi;
-        const size_t qw = (size_t)gj * nx + (gi == 0 ? nx - 1 : gi - 1);
-        const size_t qs = (size_t)(gj == 0 ? ny - 1 : gj - 1) * nx + gi;
-        v = fma(nkx, rx[q] - rx[qw], nky * (ry[q] - ry[qs]));
+      const int li = threadIdx.x, gi = i0 + li;
+      ff nzv[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int gj = j0 + h * kT + lj;
+        double v = 0;
+        if (gi < nx && gj < ny) {
+          const size_t q = (size_t)gj * nx + gi;
+          const size_t qw = (size_t)gj * nx + (gi == 0 ? nx - 1 : gi - 1);
+          const size_t qs = (size_t)(gj == 0 ? ny - 1 : gj - 1) * nx + gi;
+          v = fma(nkx, rx[q] - rx[qw], nky * (ry[q] - ry[qs]));
+        }
+        nzv[h] = d2ff(v);
       }
-      s_nz[lj][li] = d2ff(v);
+      sh.nzh[lj][li] = make_float2(nzv[0].hi, nzv[1].hi);
+      sh.nzl[lj][li] = make_float2(nzv[0].lo, nzv[1].lo);
     }
   }
   __syncthreads();
+  // M on the tile and its 1-point ring (rows and columns 1 .. 34 of the staged grid)
   auto mstage = [&](int ly, int lx) {
-    const ff l = lap_ff<kT + 5, kIso>(s_cb, ly, lx, rho, kap);
-    const ff c = s_cn[ly][lx];
-    const ff nl = ff_mul(c, ff_add_f(ff_mul(c, c), -1.f));
-    s_m[ly - 1][lx - 1] = ff_sub(nl, ff_mul(gl, l));
+    const ff2 l = lap_soa<kT + 5, kIso>(sh.cbh, sh.cbl, ly, lx, rho2, kap2);
+    const ff2 c{sh.cnh[ly][lx], sh.cnl[ly][lx]};
+    const ff2 nl = ff2_mul(c, ff2_add_f(ff2_mul(c, c), make_float2(-1.f, -1.f)));
+    const ff2 v = ff2_sub(nl, ff2_mul(gl2, l));
+    sh.mh[ly - 1][lx - 1] = v.hi;
+    sh.ml[ly - 1][lx - 1] = v.lo;
   };
-  {
-    const ff2 rho2 = ff2_splat(rho), kap2 = ff2_splat(kap), gl2 = ff2_splat(gl);
-    auto mstage2 = [&](int ly0, int ly1, int lx) {
-      const ff2 l = lap_ff2<kT + 5, kIso>(s_cb, ly0, lx, ly1, lx, rho2, kap2);
-      const ff2 c = ff2_pack(s_cn[ly0][lx], s_cn[ly1][lx]);
-      const ff2 nl = ff2_mul(c, ff2_add_f(ff2_mul(c, c), make_float2(-1.f, -1.f)));
-      const ff2 v = ff2_sub(nl, ff2_mul(gl2, l));
-      s_m[ly0 - 1][lx - 1] = ff2_first(v);
-      s_m[ly1 - 1][lx - 1] = ff2_second(v);
-    };
-    int ly = 1 + threadIdx.y;
-    for (; ly + kBY <= kT + 2; ly += 2 * kBY) mstage2(ly, ly + kBY, 1 + threadIdx.x);
-    if (ly <= kT + 2) mstage(ly, 1 + threadIdx.x);
-  }
+  for (int ly = 1 + threadIdx.y; ly <= kT + 2; ly += kBY) mstage(ly, 1 + threadIdx.x);
   if (tid < 2 * (kT + 2)) mstage(1 + (tid >> 1), kT + 1 + (tid & 1));
   __syncthreads();
-  const ff2 rho2 = ff2_splat(rho), kap2 = ff2_splat(kap), k12 = ff2_splat(k1), k22 = ff2_splat(k2);
 #pragma unroll
-  for (int k = 0; k < kT / kBY; k += 2) {  // output (i0 + li, j0 + lj) for two rows lj at once
-    const int li = threadIdx.x, lj0 = threadIdx.y + k * kBY, lj1 = lj0 + kBY;
-    const int lx = li + 1;
-    const ff2 l = lap_ff2<kT + 3, kIso>(s_m, lj0 + 1, lx, lj1 + 1, lx, rho2, kap2);
-    const ff2 diff = ff2_sub(ff2_pack(s_cb[lj0 + 2][lx + 1], s_cb[lj1 + 2][lx + 1]),
-                             ff2_pack(s_cn[lj0 + 2][lx + 1], s_cn[lj1 + 2][lx + 1]));  // C^n - C^{n-1}
+  for (int k = 0; k < kT / kBY; ++k) {  // output (i0 + li, j0 + lj) of tile A and the same point of tile B
+    const int li = threadIdx.x, lj = threadIdx.y + k * kBY, lx = li + 1;
+    const ff2 l = lap_soa<kT + 3, kIso>(sh.mh, sh.ml, lj + 1, lx, rho2, kap2);
+    const float2 bh = sh.cbh[lj + 2][lx + 1], bl = sh.cbl[lj + 2][lx + 1];
+    const ff2 diff = ff2_sub(ff2{bh, bl}, ff2{sh.cnh[lj + 2][lx + 1], sh.cnl[lj + 2][lx + 1]});  // C^n - C^{n-1}
     ff2 v = ff2_sub(ff2_mul(k22, l), ff2_mul(k12, diff));
-    if (NOISE) v = ff2_add(v, ff2_pack(s_nz[lj0][li], s_nz[lj1][li]));
+    if (NOISE) v = ff2_add(v, ff2{sh.nzh[lj][li], sh.nzl[lj][li]});
     const int gi = i0 + li;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int gj = j0 + (h ? lj1 : lj0);
+      const int gj = j0 + h * kT + lj;
       if (gi < nx && gj < ny) {
-        const ff o = h ? ff2_second(v) : ff2_first(v);
         const size_t q = ((size_t)z * ny + gj) * nx + gi;
-        rhi[q] = o.hi;
-        rlo[q] = o.lo;
-        const ff b = s_cb[(h ? lj1 : lj0) + 2][lx + 1];
-        cbo[q] = make_float2(b.hi, b.lo);  // Cbar for the update
+        rhi[q] = h ? v.hi.y : v.hi.x;
+        rlo[q] = h ? v.lo.y : v.lo.x;
+        cbo[q] = h ? make_float2(bh.y, bl.y) : make_float2(bh.x, bl.x);  // Cbar for the update
       }
     }
   }
@@ -199,8 +173,9 @@ __device__ __forceinline__ void rhs_ff_tile(RhsSmem<NOISE>& sh, const FFStep& P,
 template <bool kIso, bool NOISE>
 __global__ void __launch_bounds__(kT* kBY) ch_rhs_ff_kernel(FFStep P, const double* __restrict__ cn,
                                                             const double* __restrict__ cp) {
-  __shared__ RhsSmem<NOISE> sh;
-  rhs_ff_tile<kIso, NOISE>(sh, P, cn, cp, blockIdx.z, blockIdx.x, blockIdx.y);
+  extern __shared__ __align__(16) unsigned char rhs_sm[];
+  rhs_ff_pair<kIso, NOISE>(*reinterpret_cast<RhsSmem<NOISE>*>(rhs_sm), P, cn, cp, blockIdx.z, blockIdx.x,
+                           2 * blockIdx.y);
 }
 
 // x0 = y - (V0 ta + V1 tb + W0 tc + W1 td) for one row of a segment, rounded once
@@ -1201,26 +1176,29 @@ struct EnsCursor {
   }
 };
 
+// An item is a pair of vertically adjacent tiles (rhs_ff_pair).
 template <bool NOISE>
-__global__ void __launch_bounds__(kT* kBY, 5) ens_rhs_ff_kernel(const FFStep* __restrict__ steps,
-                                                             const int* __restrict__ order,
-                                                             const int* __restrict__ start, int ng, int nitems,
-                                                             int parity) {
-  __shared__ RhsSmem<NOISE> sh;
+__global__ void __launch_bounds__(kT* kBY) ens_rhs_ff_kernel(const FFStep* __restrict__ steps,
+                                                          const int* __restrict__ order,
+                                                          const int* __restrict__ start, int ng, int nitems,
+                                                          int parity) {
+  extern __shared__ __align__(16) unsigned char rhs_sm[];
   __shared__ FFStep sP;
   EnsCursor cur;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const FFStep& P = cur.at(sP, steps, order, start, ng, it);
-    const int idx = it - cur.first, tpz = P.tx * P.ty;
-    const int z = idx / tpz, rem = idx - z * tpz, by = rem / P.tx, bx = rem - by * P.tx;
+    const int typ = (P.ty + 1) / 2, idx = it - cur.first, tpz = P.tx * typ;
+    const int z = idx / tpz, rem = idx - z * tpz, byp = rem / P.tx, bx = rem - byp * P.tx, by = 2 * byp;
     const int c = P.cur0 ^ parity;
     if (NOISE && P.noise) {
-      if (P.iso) rhs_ff_tile<true, NOISE>(sh, P, P.st[c], P.st[1 - c], z, bx, by);
-      else rhs_ff_tile<false, NOISE>(sh, P, P.st[c], P.st[1 - c], z, bx, by);
+      auto& sh = *reinterpret_cast<RhsSmem<NOISE>*>(rhs_sm);
+      if (P.iso) rhs_ff_pair<true, NOISE>(sh, P, P.st[c], P.st[1 - c], z, bx, by);
+      else rhs_ff_pair<false, NOISE>(sh, P, P.st[c], P.st[1 - c], z, bx, by);
     } else {
       // tiles without forcing: the NOISE branch of the tile is compiled out
-      if (P.iso) rhs_ff_tile<true, false>(*reinterpret_cast<RhsSmem<false>*>(&sh), P, P.st[c], P.st[1 - c], z, bx, by);
-      else rhs_ff_tile<false, false>(*reinterpret_cast<RhsSmem<false>*>(&sh), P, P.st[c], P.st[1 - c], z, bx, by);
+      auto& sh = *reinterpret_cast<RhsSmem<false>*>(rhs_sm);
+      if (P.iso) rhs_ff_pair<true, false>(sh, P, P.st[c], P.st[1 - c], z, bx, by);
+      else rhs_ff_pair<false, false>(sh, P, P.st[c], P.st[1 - c], z, bx, by);
     }
     __syncthreads();  // the next item reuses the shared tiles and parameters
   }
@@ -1344,6 +1322,14 @@ int prepare_solve_ff() {
                       "mixed: shared-memory opt-in");
   if (!rc) rc = cuda_check(cudaFuncSetAttribute(y_solve_ff_kernel<kYThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax), "mixed: shared-memory opt-in");
   if (!rc) rc = cuda_check(cudaFuncSetAttribute(y_solve_ff_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax), "mixed: shared-memory opt-in");
+  // the right-hand side's shared tiles (two tiles, high and low arrays) exceed the 48 KB default
+  const int r1 = (int)sizeof(RhsSmem<true>), r0 = (int)sizeof(RhsSmem<false>);
+  if (!rc) rc = cuda_check(cudaFuncSetAttribute(ch_rhs_ff_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, r1), "mixed: shared-memory opt-in");
+  if (!rc) rc = cuda_check(cudaFuncSetAttribute(ch_rhs_ff_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, r1), "mixed: shared-memory opt-in");
+  if (!rc) rc = cuda_check(cudaFuncSetAttribute(ch_rhs_ff_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, r0), "mixed: shared-memory opt-in");
+  if (!rc) rc = cuda_check(cudaFuncSetAttribute(ch_rhs_ff_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, r0), "mixed: shared-memory opt-in");
+  if (!rc) rc = cuda_check(cudaFuncSetAttribute(ens_rhs_ff_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, r1), "mixed: shared-memory opt-in");
+  if (!rc) rc = cuda_check(cudaFuncSetAttribute(ens_rhs_ff_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, r0), "mixed: shared-memory opt-in");
   // the ensemble kernels also hold a group's parameters in static shared memory
   if (!rc) rc = cuda_check(cudaFuncSetAttribute(ens_x_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ens_phase_smem_max()), "mixed: shared-memory opt-in");
   if (!rc) rc = cuda_check(cudaFuncSetAttribute(ens_y_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ens_phase_smem_max()), "mixed: shared-memory opt-in");
@@ -1357,11 +1343,12 @@ bool solve_ff_fits(int nx, int ny, int px, int py) {
 void launch_step_ff(const FFStep& P, int keep_roles, Prof* prof, cudaStream_t st) {
   {
     ProfScope ps(prof, kRhs, st);
-    const dim3 grid(P.tx, P.ty, P.G), block(kT, kBY);
-    if (P.noise && P.iso) ch_rhs_ff_kernel<true, true><<<grid, block, 0, st>>>(P, P.st[0], P.st[1]);
-    else if (P.noise) ch_rhs_ff_kernel<false, true><<<grid, block, 0, st>>>(P, P.st[0], P.st[1]);
-    else if (P.iso) ch_rhs_ff_kernel<true, false><<<grid, block, 0, st>>>(P, P.st[0], P.st[1]);
-    else ch_rhs_ff_kernel<false, false><<<grid, block, 0, st>>>(P, P.st[0], P.st[1]);
+    const dim3 grid(P.tx, (P.ty + 1) / 2, P.G), block(kT, kBY);  // a block per pair of tiles
+    const size_t s1 = sizeof(RhsSmem<true>), s0 = sizeof(RhsSmem<false>);
+    if (P.noise && P.iso) ch_rhs_ff_kernel<true, true><<<grid, block, s1, st>>>(P, P.st[0], P.st[1]);
+    else if (P.noise) ch_rhs_ff_kernel<false, true><<<grid, block, s1, st>>>(P, P.st[0], P.st[1]);
+    else if (P.iso) ch_rhs_ff_kernel<true, false><<<grid, block, s0, st>>>(P, P.st[0], P.st[1]);
+    else ch_rhs_ff_kernel<false, false><<<grid, block, s0, st>>>(P, P.st[0], P.st[1]);
   }
   {
     ProfScope ps(prof, kXSolve, st);
@@ -1377,16 +1364,16 @@ void launch_step_ff(const FFStep& P, int keep_roles, Prof* prof, cudaStream_t st
 }
 
 int ens_phase_items(int phase, const FFStep& P) {
-  if (phase == 0) return P.tx * P.ty * P.G;
+  if (phase == 0) return P.tx * ((P.ty + 1) / 2) * P.G;  // pairs of tiles
   if (phase == 1) return (int)ceil_div((size_t)P.G * P.ny, P.xs);
   return (int)ceil_div(P.nx, P.ysc) * P.G;
 }
 
 int ens_phase_occupancy(int phase, size_t smem) {
   int b = 0;
-  if (phase == 0) {  // smem: whether the launch is the Cook-forcing variant (static shared memory only)
-    if (smem) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ens_rhs_ff_kernel<true>, kT * kBY, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ens_rhs_ff_kernel<false>, kT * kBY, 0);
+  if (phase == 0) {  // smem: whether the launch is the Cook-forcing variant
+    if (smem) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ens_rhs_ff_kernel<true>, kT * kBY, sizeof(RhsSmem<true>));
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ens_rhs_ff_kernel<false>, kT * kBY, sizeof(RhsSmem<false>));
   }
   else if (phase == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ens_x_ff_kernel, kXThreads, smem);
   else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ens_y_ff_kernel, kYThreadsEns, smem);
@@ -1398,8 +1385,12 @@ void launch_ens_phase_ff(int phase, const FFStep* steps, const int* order, const
                          int blocks, int parity, size_t smem, cudaStream_t st) {
   if (nitems < 1 || blocks < 1) return;
   if (phase == 0) {
-    if (smem) ens_rhs_ff_kernel<true><<<blocks, dim3(kT, kBY), 0, st>>>(steps, order, start, ngroups, nitems, parity);
-    else ens_rhs_ff_kernel<false><<<blocks, dim3(kT, kBY), 0, st>>>(steps, order, start, ngroups, nitems, parity);
+    if (smem)
+      ens_rhs_ff_kernel<true><<<blocks, dim3(kT, kBY), sizeof(RhsSmem<true>), st>>>(steps, order, start, ngroups, nitems,
+                                                                                  parity);
+    else
+      ens_rhs_ff_kernel<false><<<blocks, dim3(kT, kBY), sizeof(RhsSmem<false>), st>>>(steps, order, start, ngroups,
+                                                                                    nitems, parity);
   } else if (phase == 1) {
     ens_x_ff_kernel<<<blocks, kXThreads, smem, st>>>(steps, order, start, ngroups, nitems);
   } else {

@@ -145,7 +145,8 @@ def test_ensemble_schedule_tuning_changes_no_result():
     sched = e2.tune_schedule(2)
     assert sched["order"] in (0, 1) and sched["points_per_item"] in (2048, 4096, 8192) and min(sched["blocks"]) >= 1
     info = e2.schedule_info()
-    assert info["items"][0] == sum(cnt * ((n + 31) // 32) ** 2 for n, cnt in sizes)
+    # right-hand-side items are pairs of vertically adjacent 32 x 32 tiles
+    assert info["items"][0] == sum(cnt * ((n + 31) // 32) * (((n + 31) // 32 + 1) // 2) for n, cnt in sizes)
     e1.step(5)
     e2.step(5)
     for (n, cnt), a, b in zip(sizes, g1, g2):
