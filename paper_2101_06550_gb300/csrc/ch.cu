@@ -918,7 +918,7 @@ FFStep ff_step_params(const ChGroup* g, int G, double* cur, double* prev, void* 
   P.X = view<float>(g->X, g->ny);
   P.Y = view<float>(g->Y, g->nx);
   P.xs = x_solve_rows(g->nx, g->ny, g->X.P, target);
-  y_solve_shape(g->nx, g->ny, G, g->Y.P, target, balance, &P.ysc, &P.ynt);
+  y_solve_shape(g->nx, g->ny, G, g->Y.P, target, balance, &P.ysc, &P.ynt, &P.yrb);
   P.ypad = y_solve_pad(g->Y.m, P.ysc);
   P.lgx = log2_exact(g->X.m);
   P.lgy = log2_exact(g->Y.m);

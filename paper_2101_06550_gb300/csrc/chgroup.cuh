@@ -96,6 +96,7 @@ struct FFStep {
   int tx, ty;          // right-hand-side tiles per simulation along x and y
   int xs;             // x solve: rows per block
   int ysc, ynt, ypad;  // y solve: columns per block (1 to 32), threads per block (512 or 1024), shared-memory pad
+  int yrb;             // y solve: the slot's reduced inverse staged in shared memory (single plans, when it fits)
   int lgx, lgy;        // log2 of the segment lengths (-1 if not a power of two)
   FFConst k;
   const float2* glff;  // per slot gamma / dx^2 (double-float)
@@ -120,14 +121,15 @@ FFStep ff_step_params(const ChGroup* g, int G, double* cur, double* prev, void* 
 // segments (xs rows / S columns per block), and the tile shapes for about
 // `target` points per block (0: does not fit).
 size_t x_solve_smem(int n, int ny, int P, int xs);
-size_t y_solve_smem(int n, int P, int S);
+size_t y_solve_smem(int n, int P, int S, int rbs = 0);
 int x_solve_rows(int n, int ny, int P, int target);
 int y_solve_cols(int n, int P, int target);
 // The y strips of a single plan's step: the width S (and 512 or 1024 threads)
 // that puts the fewest columns on the busiest SM, from the default width and
 // every even width up to 32 (a width that fits one block per SM takes 1024
-// threads).  Without balance: the default width, 512 threads.
-void y_solve_shape(int nx, int ny, int G, int P, int target, bool balance, int* S, int* nt);
+// threads); rbs: whether the reduced inverse also fits in shared memory at the
+// same blocks per SM.  Without balance: the default width, 512 threads, no staging.
+void y_solve_shape(int nx, int ny, int G, int P, int target, bool balance, int* S, int* nt, int* rbs);
 int y_solve_pad(int m, int S);
 int log2_exact(int m);
 

@@ -202,6 +202,34 @@ __device__ __forceinline__ float corr_exact(float y, float4 vh, float4 vl, float
   return s + e;
 }
 
+// The same for two points that share a row's spikes (two columns of a y strip,
+// or two segments of an x row), one per lane: ta and tb their reduced unknowns.
+// Each lane performs corr_exact's operations in the same order.
+__device__ __forceinline__ float2 corr_exact2(float2 y, float4 vh, float4 vl, float4 ta, float4 tb) {
+  const float2 t[4] = {make_float2(ta.x, tb.x), make_float2(ta.y, tb.y), make_float2(ta.z, tb.z),
+                       make_float2(ta.w, tb.w)};
+  const float h[4] = {vh.x, vh.y, vh.z, vh.w};
+  const float l[4] = {vl.x, vl.y, vl.z, vl.w};
+  float2 s = y, e = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const ff2 p = two_prod2(make_float2(h[k], h[k]), t[k]);
+    const ff2 q = two_sum2(s, f2neg(p.hi));
+    s = q.hi;
+    e = f2add(e, f2sub(q.lo, __ffma2_rn(make_float2(l[k], l[k]), t[k], p.lo)));
+  }
+  return f2add(s, e);
+}
+
+// Spike sum V0 ta + V1 tb + W0 tc + W1 td of one row for two points (lanes),
+// in corr_plain's order.
+__device__ __forceinline__ float2 spikes_v2(float4 v, float4 ta, float4 tb) {
+  float2 c = __fmul2_rn(make_float2(v.x, v.x), make_float2(ta.x, tb.x));
+  c = __ffma2_rn(make_float2(v.y, v.y), make_float2(ta.y, tb.y), c);
+  c = __ffma2_rn(make_float2(v.z, v.z), make_float2(ta.z, tb.z), c);
+  return __ffma2_rn(make_float2(v.w, v.w), make_float2(ta.w, tb.w), c);
+}
+
 // x0 for row r of a segment: the exact form near the segment ends, where the
 // spike terms are large and cancel, and the plain FP32 chain in the rows
 // [plo, phi) where the spikes' magnitudes sum to at most 1 (there the rounding
@@ -537,9 +565,10 @@ __device__ __forceinline__ void seg_sweep32(float* x, int m, float a, const floa
 // pointers advanced per block.  FF:
 // double-float (exact products, pair-carried sum, one final rounding);
 // otherwise plain FP32 FMAs.
-template <bool FF>
+template <bool FF, bool SH = false>  // SH: rb / rbl are in shared memory
 __device__ __forceinline__ float reduced_row(const float* yb, int q, const float* __restrict__ rb,
                                              const float* __restrict__ rbl, int P, int band) {
+  auto ld = [](const float* a) { return SH ? *a : __ldg(a); };
   const int K = 4 * P;
   const int nb = 2 * band + 1 < P ? 2 * band + 1 : P;
   int d = nb == P ? 0 : P - band;  // block offset of the first step (mod P)
@@ -555,12 +584,12 @@ __device__ __forceinline__ float reduced_row(const float* yb, int q, const float
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       if (FF) {
-        const ff p = two_prod(__ldg(rp + u * K), vv[u]);
+        const ff p = two_prod(ld(rp + u * K), vv[u]);
         const ff c = two_sum(s, p.hi);
         s = c.hi;
-        e = e + (c.lo + fmaf(__ldg(rl + u * K), vv[u], p.lo));
+        e = e + (c.lo + fmaf(ld(rl + u * K), vv[u], p.lo));
       } else {
-        s = fmaf(__ldg(rp + u * K), vv[u], s);
+        s = fmaf(ld(rp + u * K), vv[u], s);
       }
     }
     if (++d == P) {
@@ -712,13 +741,18 @@ __device__ __forceinline__ void x_solve_rows(float* sm, const FFStep& PS, int ro
       const float4 v = __ldg(&vw4[r]);
       const bool plain = r >= D.plo && r < D.phi;
       const float4 vl = plain ? v : __ldg(&vw4l[r]);
-#pragma unroll 2
-      for (int e = tid; e < n; e += kXThreads) {
-        int p, rr;
+      // points e and e + kXThreads (same row r, segments p and pb) in the two lanes
+      for (int e = tid; e < n; e += 2 * kXThreads) {
+        const int e2 = e + kXThreads, eb = e2 < n ? e2 : e;
+        int p, pb, rr;
         sg.map(e, p, rr);  // rr == r
-        const float4 t = *reinterpret_cast<const float4*>(ts + 4 * p);
-        const float y = xs[e + p];
-        dst[e] = plain ? corr_plain(y, v, t) : corr_exact(y, v, vl, t);
+        sg.map(eb, pb, rr);
+        const float4 ta = *reinterpret_cast<const float4*>(ts + 4 * p);
+        const float4 tb = *reinterpret_cast<const float4*>(ts + 4 * pb);
+        const float2 y = make_float2(xs[e + p], xs[eb + pb]);
+        const float2 x0 = plain ? f2sub(y, spikes_v2(v, ta, tb)) : corr_exact2(y, v, vl, ta, tb);
+        dst[e] = x0.x;
+        if (e2 < n) dst[e2] = x0.y;
       }
       continue;
     }
@@ -925,6 +959,17 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
   };
   constexpr int B = 4;  // elements per batch of hoisted global loads
   for (int i = tid; i < m; i += NT) fs[i] = __ldg(&D.lu4[(size_t)slot * m + i]);
+  // the slot's reduced inverse by block offset (high, then low floats), when staged
+  float* rbs = reinterpret_cast<float*>(fs + m);
+  const size_t ko = (size_t)slot * K * K;
+  if (PS.yrb) {
+    const float4* h4 = reinterpret_cast<const float4*>(D.rb + ko);
+    const float4* l4 = reinterpret_cast<const float4*>(D.rblo + ko);
+    for (int i = tid; i < K * K / 4; i += NT) {
+      reinterpret_cast<float4*>(rbs)[i] = __ldg(&h4[i]);
+      reinterpret_cast<float4*>(rbs + K * K)[i] = __ldg(&l4[i]);
+    }
+  }
   if (live) {
     const float* src = fhi + (size_t)e0 * nx;
     for (int e1 = e0, xi = tid; e1 < n; e1 += B * RR, xi += B * used, src += B * ldr) {
@@ -943,10 +988,12 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
     if (sw < ns) seg_sweep32<0>(X + p * pitch + sw, m, a32, fs, yb + sw * K1 + 4 * p, S);
   }
   __syncthreads();
-  const size_t ko = (size_t)slot * K * K;
   for (int o = tid; o < S * K; o += NT) {
     const int so = o / K, q = o - so * K;
-    if (so < ns) tau[so * K1 + tau_word(q, P)] = reduced_row<true>(yb + so * K1, q, D.rb + ko, D.rblo + ko, P, D.band);
+    if (so < ns)
+      tau[so * K1 + tau_word(q, P)] =
+          PS.yrb ? reduced_row<true, true>(yb + so * K1, q, rbs, rbs + K * K, P, D.band)
+                 : reduced_row<true>(yb + so * K1, q, D.rb + ko, D.rblo + ko, P, D.band);
   }
   __syncthreads();
   const float4* vw4 = D.vw4 + (size_t)slot * m;
@@ -962,8 +1009,9 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
       const float2 yv = *reinterpret_cast<const float2*>(X + p * pad + e * S + cq);
       const float4 ta = *reinterpret_cast<const float4*>(t0 + 4 * p);
       const float4 tb = *reinterpret_cast<const float4*>(t0 + K1 + 4 * p);
+      const float4 v = __ldg(&vw4[r]);  // both columns' row r: one spike row, both lanes
       *reinterpret_cast<float2*>(x02 + (size_t)e * nx) =
-          make_float2(corr_first(yv.x, vw4, vw4l, r, D.plo, D.phi, ta), corr_first(yv.y, vw4, vw4l, r, D.plo, D.phi, tb));
+          r >= D.plo && r < D.phi ? f2sub(yv, spikes_v2(v, ta, tb)) : corr_exact2(yv, v, __ldg(&vw4l[r]), ta, tb);
     }
   } else if (live) {
     float* dst = x0s + (size_t)e0 * nx;
@@ -1059,7 +1107,9 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
   __syncthreads();
   for (int o = tid; o < S * K; o += NT) {
     const int so = o / K, q = o - so * K;
-    if (so < ns) tau[so * K1 + tau_word(q, P)] = reduced_row<false>(yb + so * K1, q, D.rb + ko, nullptr, P, D.band);
+    if (so < ns)
+      tau[so * K1 + tau_word(q, P)] = PS.yrb ? reduced_row<false, true>(yb + so * K1, q, rbs, nullptr, P, D.band)
+                                             : reduced_row<false>(yb + so * K1, q, D.rb + ko, nullptr, P, D.band);
   }
   __syncthreads();
   if (pairs) {
@@ -1090,7 +1140,7 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
         const float2 dv = *reinterpret_cast<const float2*>(X + p * pad + e * S + cq);
         const float4 ta = *reinterpret_cast<const float4*>(t0 + 4 * p);
         const float4 tb = *reinterpret_cast<const float4*>(t0 + K1 + 4 * p);
-        const float2 dl = make_float2(dv.x - spikes32(vw4, r, ta), dv.y - spikes32(vw4, r, tb));
+        const float2 dl = f2sub(dv, spikes_v2(__ldg(&vw4[r]), ta, tb));
         const ff2 cb{make_float2(cv[u].x, cv[u].z), make_float2(cv[u].y, cv[u].w)};
         const ff2 v = ff2_add(cb, two_sum2(xv[u], dl));
         *reinterpret_cast<double2*>(o2 + (size_t)e * nx) = make_double2(ff2d(ff2_first(v)), ff2d(ff2_second(v)));
@@ -1252,9 +1302,10 @@ size_t x_solve_smem(int n, int ny, int P, int xs) {
   return sizeof(float) * ((((size_t)xs * (n + P) + 3) & ~(size_t)3) + 2 * (size_t)xs * 4 * P + 4 * (size_t)(n / P) * slots);
 }
 int y_solve_pad(int m, int S) { return (((S - m * S) % 32) + 32) % 32; }
-size_t y_solve_smem(int n, int P, int S) {
+size_t y_solve_smem(int n, int P, int S, int rbs) {
   const int m = n / P;
-  return sizeof(float) * ((((size_t)P * (m * S + y_solve_pad(m, S)) + 3) & ~(size_t)3) + 2 * (size_t)S * (4 * P + 4) + 4 * (size_t)m);
+  return sizeof(float) * ((((size_t)P * (m * S + y_solve_pad(m, S)) + 3) & ~(size_t)3) + 2 * (size_t)S * (4 * P + 4) +
+                          4 * (size_t)m + (rbs ? 2 * (size_t)16 * P * P : 0));
 }
 int log2_exact(int m) {
   int lg = 0;
@@ -1286,11 +1337,20 @@ int y_solve_cols(int n, int P, int target) {
   return y_solve_smem(n, P, S) <= kSmemMax ? S : 0;
 }
 
-void y_solve_shape(int nx, int ny, int G, int P, int target, bool balance, int* S_out, int* nt_out) {
+void y_solve_shape(int nx, int ny, int G, int P, int target, bool balance, int* S_out, int* nt_out, int* rbs_out) {
   const int S0 = y_solve_cols(ny, P, target);
   *S_out = S0;
   *nt_out = 512;
+  *rbs_out = 0;
   if (!balance || S0 < 1) return;
+  // stage the reduced inverse when it keeps the blocks per SM (two of 512 threads, or one of 1024)
+  struct Pick {
+    static void rbs(int ny_, int P_, int S_, int nt_, int* out) {
+      const size_t with = y_solve_smem(ny_, P_, S_, 1);
+      *out = nt_ == 512 ? with <= 112 * 1024 : with <= kSmemMax - 1024;
+    }
+  };
+  Pick::rbs(ny, P, S0, 512, rbs_out);
   static int sms = 0;
   if (!sms) {
     int dev = 0;
@@ -1310,6 +1370,7 @@ void y_solve_shape(int nx, int ny, int G, int P, int target, bool balance, int* 
       best = c;
       *S_out = S;
       *nt_out = sm <= 112 * 1024 ? 512 : 1024;  // two 512-thread blocks per SM, else one of 1024
+      Pick::rbs(ny, P, S, *nt_out, rbs_out);
     }
   }
 }
@@ -1357,7 +1418,7 @@ void launch_step_ff(const FFStep& P, int keep_roles, Prof* prof, cudaStream_t st
   {
     ProfScope ps(prof, kYSolve, st);
     const dim3 grid(ceil_div(P.nx, P.ysc), P.G);
-    const size_t smem = y_solve_smem(P.ny, P.Y.P, P.ysc);
+    const size_t smem = y_solve_smem(P.ny, P.Y.P, P.ysc, P.yrb);
     if (P.ynt == 1024) y_solve_ff_kernel<1024><<<grid, 1024, smem, st>>>(P, P.st[0], P.st[1], keep_roles);
     else y_solve_ff_kernel<kYThreads><<<grid, kYThreads, smem, st>>>(P, P.st[0], P.st[1], keep_roles);
   }
