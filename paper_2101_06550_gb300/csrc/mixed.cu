@@ -19,7 +19,8 @@
 namespace chx {
 namespace {
 
-constexpr int kT = 32, kBY = 8, kSolveThreads = 128;
+// right-hand side: 32 x 32 tiles, 32 x 16 threads (three 512-thread blocks per SM)
+constexpr int kT = 32, kBY = 16, kSolveThreads = 128;
 
 __device__ __forceinline__ int wrapi(int i, int n) {
   int r = i % n;
@@ -75,7 +76,7 @@ struct RhsSmem {
   float2 nzh[NOISE ? kT : 1][kT + 1], nzl[NOISE ? kT : 1][kT + 1];
 };
 
-// Tiles (bx, by) and (bx, by + 1) of simulation z, by a 32 x 8 thread block;
+// Tiles (bx, by) and (bx, by + 1) of simulation z, by a 32 x 16 thread block;
 // cn / cp are the group's C^n / C^{n-1} buffers.  Tile B may lie past the
 // grid's last row: its loads wrap like the halo's and its stores are skipped.
 template <bool kIso, bool NOISE>
@@ -171,7 +172,7 @@ __device__ __forceinline__ void rhs_ff_pair(RhsSmem<NOISE>& sh, const FFStep& P,
 }
 
 template <bool kIso, bool NOISE>
-__global__ void __launch_bounds__(kT* kBY) ch_rhs_ff_kernel(FFStep P, const double* __restrict__ cn,
+__global__ void __launch_bounds__(kT* kBY, NOISE ? 2 : 3) ch_rhs_ff_kernel(FFStep P, const double* __restrict__ cn,
                                                             const double* __restrict__ cp) {
   extern __shared__ __align__(16) unsigned char rhs_sm[];
   rhs_ff_pair<kIso, NOISE>(*reinterpret_cast<RhsSmem<NOISE>*>(rhs_sm), P, cn, cp, blockIdx.z, blockIdx.x,
@@ -1228,7 +1229,7 @@ struct EnsCursor {
 
 // An item is a pair of vertically adjacent tiles (rhs_ff_pair).
 template <bool NOISE>
-__global__ void __launch_bounds__(kT* kBY) ens_rhs_ff_kernel(const FFStep* __restrict__ steps,
+__global__ void __launch_bounds__(kT* kBY, NOISE ? 2 : 3) ens_rhs_ff_kernel(const FFStep* __restrict__ steps,
                                                           const int* __restrict__ order,
                                                           const int* __restrict__ start, int ng, int nitems,
                                                           int parity) {
