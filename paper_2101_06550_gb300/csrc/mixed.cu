@@ -632,6 +632,7 @@ __device__ __forceinline__ int tau_word(int q, int P) {
 constexpr int kXThreads = 128;  // x solve: threads per block (rows per block: FFStep::xs)
 constexpr int kYThreads = 512;  // y solve: threads per block (columns per block: FFStep::ysc)
 constexpr int kYThreadsEns = 256;  // the ensemble's y phase: more, smaller blocks per SM overlap their phases
+constexpr int kYUpdRows = 2;       // y update, column pairs: rows whose loads a thread keeps in flight
 
 // Row e of a system -> (segment p, row r in the segment) for segments of m
 // rows: shifts when m is a power of two (lg = log2 m), else seg_row.
@@ -1119,11 +1120,12 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
     const float* __restrict__ x02 = PS.x0s + zo + col0 + cq;
     const float2* __restrict__ cb2 = PS.cbar + zo + col0 + cq;
     double* __restrict__ o2 = out2 + cq;
-    for (int e1 = plive ? rq : n; e1 < n; e1 += 2 * RR2) {  // two rows' loads in flight
-      float2 xv[2];
-      float4 cv[2];  // Cbar of the two columns: (hi, lo, hi, lo)
+    constexpr int UB = kYUpdRows;
+    for (int e1 = plive ? rq : n; e1 < n; e1 += UB * RR2) {  // UB rows' loads in flight
+      float2 xv[UB];
+      float4 cv[UB];  // Cbar of the two columns: (hi, lo, hi, lo)
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < UB; ++u) {
         const int e = e1 + u * RR2;
         xv[u] = make_float2(0.f, 0.f);
         cv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1133,7 +1135,7 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
         }
       }
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < UB; ++u) {
         const int e = e1 + u * RR2;
         if (e >= n) break;
         int p, r;
