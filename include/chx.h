@@ -61,8 +61,9 @@ enum { CHX_PREMAP_NONE = 0, CHX_PREMAP_CUBIC_MINUS_C = 1 };
  * pentadiagonal solve whose residual, like the right-hand side, is formed in
  * double-float arithmetic (FP64 state and update).  FP32+refine keeps a step
  * within 1e-6 of max|c| of the FP64 step up to a' = (2/3) gamma dt / dx^4 of
- * about 2e4 (the 2048^2, gamma 0.005, dt 5e-4 workload); at a' = 3e5 a step from
- * a rough random state is off by about 5e-5 (smooth states stay within 1e-6).
+ * about 2e4 (the 2048^2, gamma 0.005, dt 5e-4 workload).  Above a' = 5e4 the
+ * solves take a second refinement pass: at a' = 3e5 a step from a rough random
+ * state is then off by about 5e-6 (smooth states stay within 1e-6).
  * Its fused solves keep whole rows and column strips in shared memory: grids
  * whose rows or columns do not fit are rejected at ch_plan_create with
  * CHX_EUNSUPPORTED. */

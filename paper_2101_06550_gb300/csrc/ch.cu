@@ -773,6 +773,7 @@ int dir_set(SpikeDir* D, int z, double a) {
   // the band is shared by the slots: keep the widest any slot has needed
   const int band = rinv_band(rinv, D->P);
   if (band > D->band) D->band = band;
+  if (refine_passes(a) > D->passes) D->passes = refine_passes(a);  // likewise the refinement passes
   // rows where the spikes are small enough for a plain FP32 correction: the
   // middle interval where sum_k |vw_k(r)| <= 1, narrowed to what every slot
   // factorised so far allows
@@ -919,6 +920,8 @@ FFStep ff_step_params(const ChGroup* g, int G, double* cur, double* prev, void* 
   P.Y = view<float>(g->Y, g->nx);
   P.xs = x_solve_rows(g->nx, g->ny, g->X.P, target);
   y_solve_shape(g->nx, g->ny, G, g->Y.P, target, balance, &P.ysc, &P.ynt, &P.yrb);
+  P.xpass = g->X.passes;
+  P.ypass = g->Y.passes;
   P.ypad = y_solve_pad(g->Y.m, P.ysc);
   P.lgx = log2_exact(g->X.m);
   P.lgy = log2_exact(g->Y.m);

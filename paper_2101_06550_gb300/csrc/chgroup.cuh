@@ -47,7 +47,16 @@ struct SpikeDir {
   // with plain FP32 arithmetic (exact accumulation elsewhere)
   int plo = 0, phi = 0;
   bool pset = false;
+  // refinement passes of the mixed-precision solves, for the stiffest slot
+  int passes = 1;
 };
+// Refinement passes for the operator I + a delta^4: one up to a = 5e4 (the
+// 2048^2 workload's a = 1.9e4 meets 1e-6 with one), two above.  Measured at
+// a = 3e5 from a rough state: 5.5e-5 of max|c| after one pass, 4.5e-6 after
+// two; a third pass makes it worse (2.3e-5): the partitioned FP32 solve's
+// own error on the ever smaller correction sets a floor, which a numpy model
+// of the same solve reproduces.
+inline int refine_passes(double a) { return a <= 5e4 ? 1 : 2; }
 
 // Per-direction view handed to the kernels: slot of system j = blockIdx.z + j / spp.
 template <typename T>
@@ -97,6 +106,7 @@ struct FFStep {
   int xs;             // x solve: rows per block
   int ysc, ynt, ypad;  // y solve: columns per block (1 to 32), threads per block (512 or 1024), shared-memory pad
   int yrb;             // y solve: the slot's reduced inverse staged in shared memory (single plans, when it fits)
+  int xpass, ypass;    // refinement passes of the x / y solve (SpikeDir::passes)
   int lgx, lgy;        // log2 of the segment lengths (-1 if not a power of two)
   FFConst k;
   const float2* glff;  // per slot gamma / dx^2 (double-float)

@@ -275,6 +275,17 @@ __device__ __forceinline__ float2 resid_pair(const float (&fh)[2], const float (
   return ff2_sub(ff2{make_float2(fh[0], fh[1]), make_float2(fl[0], fl[1])}, adi_apply_ff2(wv, a)).hi;
 }
 
+// A w for the ADI row with w itself a double-float pair at each of the five
+// points (the second refinement pass, whose iterate is x0 + delta), two
+// points per call in the two lanes.
+__device__ __forceinline__ ff2 adi_apply_pair2(const ff2 (&w)[5], ff2 a) {
+  const ff2 s2 = ff2_add(w[0], w[4]);
+  const ff2 s1 = ff2_add(w[1], w[3]);
+  ff2 d = ff2_sub(s2, ff2_scale2(s1, 4.f));
+  d = ff2_add(d, ff2_mul(ff2{make_float2(6.f, 6.f), make_float2(0.f, 0.f)}, w[2]));
+  return ff2_add(w[2], ff2_mul(a, d));
+}
+
 // ---------------------------------------------------------------------------
 // Batched pentadiagonal refinement (SHARED / UNIFORM coefficients): residual
 // r = f - A x0 in double-float (rows of A as double-float constants, f split
@@ -891,6 +902,72 @@ __device__ __forceinline__ void x_solve_rows(float* sm, const FFStep& PS, int ro
       }
     }
   }
+  // Further refinement passes (stiff operators): rho = f - A w in double-float
+  // with the current result w = (whi, wlo) itself a pair (its neighbours from
+  // global memory, this block's own rows), delta by the FP32 solve with the
+  // coupling in double-float, and w += delta.  Two points per thread per
+  // step, e and e + kXThreads.
+  for (int pass = 1; pass < PS.xpass; ++pass) {
+    __syncthreads();
+    for (int s = 0; s < ns; ++s) {
+      const int slot = (row0 + s) / ny;
+      const ff2 a = ff2_splat(ffc(aff[slot]));
+      const size_t ro = (size_t)(row0 + s) * n;
+      const float* wh0 = whi + ro;
+      const float* wl0 = wlo + ro;
+      const float* fh0 = fhi + ro;
+      const float* fl0 = flo + ro;
+      float* xs = X + s * Ls;
+      for (int e1 = tid; e1 < n; e1 += 2 * kXThreads) {
+        const int e2 = e1 + kXThreads, eb = e2 < n ? e2 : e1;
+        ff2 w[5];
+  #pragma unroll
+        for (int d = 0; d < 5; ++d) {
+          const int qa = wrap2(e1 + d - 2, n), qb = wrap2(eb + d - 2, n);
+          w[d] = ff2{make_float2(wh0[qa], wh0[qb]), make_float2(wl0[qa], wl0[qb])};
+        }
+        const ff2 f{make_float2(fh0[e1], fh0[eb]), make_float2(fl0[e1], fl0[eb])};
+        const float2 rv = ff2_sub(f, adi_apply_pair2(w, a)).hi;
+        int p, r;
+        sg.map(e1, p, r);
+        xs[e1 + p] = rv.x;
+        if (e2 < n) {
+          sg.map(e2, p, r);
+          xs[e2 + p] = rv.y;
+        }
+      }
+    }
+    __syncthreads();
+    for (int w = tid; w < ns * P; w += kXThreads) {
+      const int s = w / P, p = w - s * P, slot = (row0 + s) / ny;
+      seg_sweep32<1>(X + s * Ls + p * (m + 1), m, D.a[slot], fs + (slot - slot0) * m, yb + s * K + 4 * p);
+    }
+    __syncthreads();
+    for (int o = tid; o < ns * K; o += kXThreads) {  // the coupling in double-float, as in the first solve
+      const int s = o / K, q = o - s * K, slot = (row0 + s) / ny;
+      const size_t ko = (size_t)slot * K * K;
+      tau[s * K + tau_word(q, P)] = reduced_row<true>(yb + s * K, q, D.rb + ko, D.rblo + ko, P, D.band);
+    }
+    __syncthreads();
+    for (int s = 0; s < ns; ++s) {
+      const int slot = (row0 + s) / ny;
+      const float4* vw4 = D.vw4 + (size_t)slot * m;
+      const float4* vw4l = D.vw4lo + (size_t)slot * m;
+      const float* ts = tau + s * K;
+      const float* xs = X + s * Ls;
+      const size_t ro = (size_t)(row0 + s) * n;
+      float* wh = whi + ro;
+      float* wl = wlo + ro;
+      for (int e = tid; e < n; e += kXThreads) {
+        int p, r;
+        sg.map(e, p, r);
+        const float4 t = *reinterpret_cast<const float4*>(ts + 4 * p);
+        const ff w = ff_add_f(ff{wh[e], wl[e]}, corr_first(xs[e + p], vw4, vw4l, r, D.plo, D.phi, t));
+        wh[e] = w.hi;
+        wl[e] = w.lo;
+      }
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kXThreads, 7) x_solve_ff_kernel(FFStep P, int keep_roles) {
@@ -1144,8 +1221,14 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
         const float4 ta = *reinterpret_cast<const float4*>(t0 + 4 * p);
         const float4 tb = *reinterpret_cast<const float4*>(t0 + K1 + 4 * p);
         const float2 dl = f2sub(dv, spikes_v2(__ldg(&vw4[r]), ta, tb));
+        const ff2 v1 = two_sum2(xv[u], dl);  // x0 + delta as an exact pair
+        if (PS.ypass > 1) {  // kept for the further passes
+          *reinterpret_cast<float2*>(PS.fhi + zo + col0 + cq + (size_t)e * nx) = v1.hi;
+          *reinterpret_cast<float2*>(PS.flo + zo + col0 + cq + (size_t)e * nx) = v1.lo;
+          continue;
+        }
         const ff2 cb{make_float2(cv[u].x, cv[u].z), make_float2(cv[u].y, cv[u].w)};
-        const ff2 v = ff2_add(cb, two_sum2(xv[u], dl));
+        const ff2 v = ff2_add(cb, v1);
         *reinterpret_cast<double2*>(o2 + (size_t)e * nx) = make_double2(ff2d(ff2_first(v)), ff2d(ff2_second(v)));
       }
     }
@@ -1178,14 +1261,79 @@ __device__ __forceinline__ void y_solve_cols(float* sm, const FFStep& PS, double
 #pragma unroll
       for (int h = 0; h < B; h += 2) {  // Cbar + (x0 + delta) for two rows at once
         const ff2 cb{make_float2(cv[h].x, cv[h + 1].x), make_float2(cv[h].y, cv[h + 1].y)};
-        const ff2 v = ff2_add(cb, two_sum2(make_float2(xv[h], xv[h + 1]), make_float2(dl[h], dl[h + 1])));
+        const ff2 v1 = two_sum2(make_float2(xv[h], xv[h + 1]), make_float2(dl[h], dl[h + 1]));
+        const ff2 v = ff2_add(cb, v1);
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
           if (e1 + (h + k) * RR >= n) break;
           const size_t q = eo1 + (h + k) * ldr;
+          if (PS.ypass > 1) {  // x0 + delta kept for the further passes
+            PS.fhi[zo + c + q] = k ? v1.hi.y : v1.hi.x;
+            PS.flo[zo + c + q] = k ? v1.lo.y : v1.lo.x;
+            continue;
+          }
           // kept roles: C^{n+1} over C^n (the x solve has moved C^n into cp)
           (keep_roles ? cn : cp)[q] = ff2d(k ? ff2_second(v) : ff2_first(v));
         }
+      }
+    }
+  }
+  // Further refinement passes (stiff operators), one column per thread: rho =
+  // f - A v in double-float with v = x0 + delta the pair kept in the right-hand
+  // side's buffers (free during the y solve; this block's own columns), delta
+  // by the FP32 solve with the coupling in double-float, v += delta, and after
+  // the last pass C^{n+1} = Cbar + v.
+  float* __restrict__ vh = PS.fhi + zo + c;
+  float* __restrict__ vl = PS.flo + zo + c;
+  for (int pass = 1; pass < PS.ypass; ++pass) {
+    const bool last = pass + 1 == PS.ypass;
+    __syncthreads();
+    if (live) {
+      const ff2 a = ff2_splat(ffc(aff[slot]));
+      for (int e1 = e0, xi = tid; e1 < n; e1 += 2 * RR, xi += 2 * used) {
+        const int e2 = e1 + RR, eb = e2 < n ? e2 : e1;
+        ff2 w[5];
+  #pragma unroll
+        for (int d = 0; d < 5; ++d) {
+          const size_t qa = (size_t)wrap2(e1 + d - 2, n) * nx, qb = (size_t)wrap2(eb + d - 2, n) * nx;
+          w[d] = ff2{make_float2(vh[qa], vh[qb]), make_float2(vl[qa], vl[qb])};
+        }
+        const size_t fa = (size_t)e1 * nx, fb = (size_t)eb * nx;
+        const ff2 f{make_float2(fhi[fa], fhi[fb]), make_float2(flo[fa], flo[fb])};
+        const float2 rv = ff2_sub(f, adi_apply_pair2(w, a)).hi;
+        X[seg(e1) * pad + xi] = rv.x;
+        if (e2 < n) X[seg(e2) * pad + xi + used] = rv.y;
+      }
+    }
+    __syncthreads();
+    for (int w = tid; w < S * P; w += NT) {
+      const int p = w / S, sw = w - p * S;
+      if (sw < ns) seg_sweep32<0>(X + p * pitch + sw, m, a32, fs, yb + sw * K1 + 4 * p, S);
+    }
+    __syncthreads();
+    for (int o = tid; o < S * K; o += NT) {  // the coupling in double-float, as in the first solve
+      const int so = o / K, q = o - so * K;
+      if (so < ns)
+        tau[so * K1 + tau_word(q, P)] =
+            PS.yrb ? reduced_row<true, true>(yb + so * K1, q, rbs, rbs + K * K, P, D.band)
+                   : reduced_row<true>(yb + so * K1, q, D.rb + ko, D.rblo + ko, P, D.band);
+    }
+    __syncthreads();
+    if (live) {
+      double* __restrict__ dst = keep_roles ? cn : cp;  // this thread's column
+      for (int e = e0, xi = tid; e < n; e += RR, xi += used) {
+        int p, r;
+        sg.map(e, p, r);
+        const float4 t = *reinterpret_cast<const float4*>(ts + 4 * p);
+        const size_t q = (size_t)e * nx;
+        const ff v = ff_add_f(ff{vh[q], vl[q]}, corr_first(X[p * pad + xi], vw4, vw4l, r, D.plo, D.phi, t));
+        if (!last) {
+          vh[q] = v.hi;
+          vl[q] = v.lo;
+          continue;
+        }
+        const float2 cb = cbar[q];
+        dst[q] = ff2d(ff_add(ff{cb.x, cb.y}, v));
       }
     }
   }
