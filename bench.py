@@ -40,7 +40,7 @@ PREWARM_S = 1.5  # untimed steps before the first measurement (see measure())
 # ncu flushes the caches before each kernel it measures, so these are cold-cache
 # figures: intermediates that a live step finds in L2 are counted as DRAM reads.
 STEP_DRAM_BYTES_F64 = 373.58e6 + 53.25e6
-STEP_DRAM_BYTES_F32R = 213.22e6 + 62.47e6  # the three fused kernels
+STEP_DRAM_BYTES_F32R = 213.10e6 + 63.37e6  # the three fused kernels
 # DRAM bytes (read + write) per launch of the FP64 step's kernels on this
 # workload, from one ncu capture of the current kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum, mean of 3 launches).  The first right-hand-side pass
