@@ -881,6 +881,23 @@ def kernel_case(args, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
+    if args.kernel_case == "ens":
+        dx, dt = 2 * np.pi / 256, 1e-3
+        ens = chx.Ensemble(dt, chx.PREC_F32_REFINE)
+        by_n = {}
+        for n, g, sd in ensemble_sims(512):
+            by_n.setdefault(n, []).append((g, sd))
+        for n, lst in sorted(by_n.items()):
+            gid = ens.group_create(n, n * dx, lst[0][0], len(lst))
+            for slot, (g, sd) in enumerate(lst):
+                ens.load(gid, slot, synth.uniform_torch(sd, n * n, -0.1, 0.1, device=dev), None, g)
+            ens.set_active(gid, len(lst))
+        ens.step(args.warmup + args.steps)
+        torch.cuda.synchronize()
+        ens.sync_status()
+        print(json.dumps({"kernel_case": "ens", "steps": args.warmup + args.steps, "info": ens.schedule_info()}))
+        ens.close()
+        return
     prec = chx.PREC_F64 if args.kernel_case == "fp64" else chx.PREC_F32_REFINE
     plan = chx.ChPlan(N, N, LX, LX, GAMMA, DT, prec)
     cn = torch.from_numpy(synth.field(SEED, N, N, -0.05, 0.05)).to(dev)
@@ -907,9 +924,10 @@ def main():
     ap.add_argument("--serve-only", action="store_true",
                     help="run only the serving benchmarks (burst and sustainable rate) and print their JSON")
     ap.add_argument("--serve-rate", type=float, default=200.0)
-    ap.add_argument("--kernel-case", choices=["fp64", "fp32"],
+    ap.add_argument("--kernel-case", choices=["fp64", "fp32", "ens"],
                     help="untimed: run --warmup + --steps single steps of the headline workload at that precision "
-                         "and exit (the small case that ncu captures are taken on)")
+                         "(ens: ensemble steps of the 512-simulation FP32+refine ensemble, untuned) and exit; "
+                         "the programs ncu captures are taken on")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
