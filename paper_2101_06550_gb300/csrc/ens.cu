@@ -154,7 +154,7 @@ int build_schedule(chx_ens* e) {
       start[ph * (kEnsMaxGroups + 1) + k + 1] = start[ph * (kEnsMaxGroups + 1) + k] + ens_phase_items(ph, P);
     noise = noise || P.noise;
     sx = std::max(sx, x_solve_smem(P.nx, P.ny, P.X.P, P.xs));
-    sy = std::max(sy, y_solve_smem(P.ny, P.Y.P, P.ysc));
+    sy = std::max(sy, y_solve_smem(P.ny, P.Y.P, P.ysc, P.yrb));
   }
   if (sx > ens_phase_smem_max() || sy > ens_phase_smem_max()) return CHX_OK;  // per-group launches
   int dev = 0, sms = 0;
@@ -531,7 +531,7 @@ static int time_packed_group(chx_ens* e, EnsGroup* G, ChGroup* g, int trial, voi
   FFStep P = ff_step_params(g, G->active, G->d_state[0], G->d_state[1], G->d_work, e->sched->target);
   P.cur0 = G->cur;
   if (P.xs < 1 || P.ysc < 1) return CHX_OK;
-  const size_t smem[3] = {0, x_solve_smem(P.nx, P.ny, P.X.P, P.xs), y_solve_smem(P.ny, P.Y.P, P.ysc)};
+  const size_t smem[3] = {0, x_solve_smem(P.nx, P.ny, P.X.P, P.xs), y_solve_smem(P.ny, P.Y.P, P.ysc, P.yrb)};
   if (smem[1] > ens_phase_smem_max() || smem[2] > ens_phase_smem_max()) return CHX_OK;
   int items[3], host_ints[1 + 3 * 2], blocks[3], sms = 0, dv = 0;
   int rc = cuda_check(cudaGetDevice(&dv), "ens_autotune: device");
@@ -580,8 +580,14 @@ extern "C" int ens_autotune(chx_ens* e, int group_id, int trial, int* px_out, in
     cudaGetLastError();
     return fail(CHX_ENOMEM, "ens_autotune: scratch for the saved state");
   }
-  cudaMemcpyAsync(save, G->d_state[0], sb, cudaMemcpyDeviceToDevice, st);
-  cudaMemcpyAsync((char*)save + sb, G->d_state[1], sb, cudaMemcpyDeviceToDevice, st);
+  {
+    cudaError_t ce = cudaMemcpyAsync(save, G->d_state[0], sb, cudaMemcpyDeviceToDevice, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync((char*)save + sb, G->d_state[1], sb, cudaMemcpyDeviceToDevice, st);
+    if (ce != cudaSuccess) {
+      cudaFree(save);
+      return cuda_check(ce, "ens_autotune: saving the state");
+    }
+  }
   const int cur0 = G->cur;
   void* sched_scratch = nullptr;  // a one-group packed schedule (FP32 + refinement)
   if (packed(e) && cudaMalloc(&sched_scratch, 1024 + 64) != cudaSuccess) {
@@ -589,10 +595,9 @@ extern "C" int ens_autotune(chx_ens* e, int group_id, int trial, int* px_out, in
     cudaFree(save);
     return fail(CHX_ENOMEM, "ens_autotune: schedule scratch");
   }
-  cudaEvent_t a, b;
-  cudaEventCreate(&a);
-  cudaEventCreate(&b);
-  int rc = CHX_OK;
+  cudaEvent_t a = nullptr, b = nullptr;
+  int rc = cuda_check(cudaEventCreate(&a), "ens_autotune: event");
+  if (!rc) rc = cuda_check(cudaEventCreate(&b), "ens_autotune: event");
   // one trial: `trial` steps of the group with px / py segments (ms, or < 0 when
   // the candidate does not fit the group's work buffer)
   auto trial_ms = [&](int px, int py, float* ms) -> int {
@@ -638,20 +643,27 @@ extern "C" int ens_autotune(chx_ens* e, int group_id, int trial, int* px_out, in
       }
     }
   }
-  cudaMemcpyAsync(G->d_state[0], save, sb, cudaMemcpyDeviceToDevice, st);
-  cudaMemcpyAsync(G->d_state[1], (char*)save + sb, sb, cudaMemcpyDeviceToDevice, st);
+  // put the state back (whatever the trials returned)
+  int rs = cuda_check(cudaMemcpyAsync(G->d_state[0], save, sb, cudaMemcpyDeviceToDevice, st), "ens_autotune: restore");
+  if (!rs) rs = cuda_check(cudaMemcpyAsync(G->d_state[1], (char*)save + sb, sb, cudaMemcpyDeviceToDevice, st),
+                           "ens_autotune: restore");
+  if (!rs) rs = cuda_check(cudaStreamSynchronize(st), "ens_autotune: restore");
+  if (!rc) rc = rs;
   G->cur = cur0;
-  cudaStreamSynchronize(st);
   cudaFree(save);
   cudaFree(sched_scratch);
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
   if (rc) return rc;
   if (bx != G->g.X.P || by != G->g.Y.P) {
     ChGroup ng;
     rc = group_init(&ng, n, n, G->l, G->l, G->gamma, e->dt, e->precision, G->capacity, bx, by);
     for (int z = 0; z < G->capacity && !rc; ++z)
       if (G->slot_gamma[z] != G->gamma) rc = group_set_gamma(&ng, z, G->slot_gamma[z]);
+    // the new segment counts change the factor arrays' size
+    const size_t nbytes = state_bytes(n, G->capacity) + G->work_bytes + ng.factor_bytes;
+    if (!rc && e->budget && e->used - G->bytes + nbytes > e->budget)
+      rc = fail(CHX_ENOMEM, "ens_autotune: factors for %d x %d segments over the HBM budget", bx, by);
     if (rc) {
       group_free(&ng);
       return rc;
@@ -659,9 +671,8 @@ extern "C" int ens_autotune(chx_ens* e, int group_id, int trial, int* px_out, in
     const double nkx = G->g.nkx, nky = G->g.nky;
     group_free(&G->g);
     G->g = ng;
-    e->used -= G->bytes;  // the new segment counts change the factor arrays' size
-    G->bytes = state_bytes(n, G->capacity) + G->work_bytes + G->g.factor_bytes;
-    e->used += G->bytes;
+    e->used = e->used - G->bytes + nbytes;
+    G->bytes = nbytes;
     G->g.nkx = nkx;  // the group's forcing weights carry over to the new factors
     G->g.nky = nky;
     drop_graph(e);
@@ -716,13 +727,17 @@ extern "C" int ens_tune_schedule(chx_ens* e, int trial, int* order_out, int* tar
     size_t off = 0;
     for (EnsGroup* G : S.members) {
       const size_t b = (size_t)G->active * G->n * G->n * sizeof(double);
-      cudaMemcpyAsync(save + off, G->d_state[1 - G->cur], b, cudaMemcpyDeviceToDevice, st);
+      const cudaError_t ce = cudaMemcpyAsync(save + off, G->d_state[1 - G->cur], b, cudaMemcpyDeviceToDevice, st);
+      if (ce != cudaSuccess) {
+        cudaFree(save);
+        return cuda_check(ce, "ens_tune_schedule: saving the state");
+      }
       off += b;
     }
   }
   cudaEvent_t a = nullptr, b = nullptr;
-  cudaEventCreate(&a);
-  cudaEventCreate(&b);
+  rc = cuda_check(cudaEventCreate(&a), "ens_tune_schedule: event");
+  if (!rc) rc = cuda_check(cudaEventCreate(&b), "ens_tune_schedule: event");
   const int order0 = S.order_mode, target0 = S.target, bps0 = S.bps[2];
   double best = 1e300;
   int bo = order0, bt = target0, bb = bps0;
@@ -751,17 +766,22 @@ extern "C" int ens_tune_schedule(chx_ens* e, int trial, int* order_out, int* tar
       }
     }
   {
+    // put C^{n-1} back (whatever the trials returned)
     size_t off = 0;
+    int rs = CHX_OK;
     for (EnsGroup* G : S.members) {
       const size_t bs = (size_t)G->active * G->n * G->n * sizeof(double);
-      cudaMemcpyAsync(G->d_state[1 - G->cur], save + off, bs, cudaMemcpyDeviceToDevice, st);
+      if (!rs)
+        rs = cuda_check(cudaMemcpyAsync(G->d_state[1 - G->cur], save + off, bs, cudaMemcpyDeviceToDevice, st),
+                        "ens_tune_schedule: restore");
       off += bs;
     }
+    if (!rs) rs = cuda_check(cudaStreamSynchronize(st), "ens_tune_schedule: restore");
+    if (!rc) rc = rs;
   }
-  cudaStreamSynchronize(st);
   cudaFree(save);
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
   S.order_mode = rc ? order0 : bo;
   S.target = rc ? target0 : bt;
   S.bps[2] = rc ? bps0 : bb;
