@@ -440,10 +440,12 @@ const char* ch_profile_slot_name(int slot);
 /* Measurement aid (no counterpart in the paper): the device's sustained FP64
  * fused multiply-add rate, for the roofline of the FP64 kernels, which are
  * bound by the FP64 pipe rather than by HBM.  Runs a throughput kernel of
- * independent DFMA chains (one warm-up launch, then a timed one, CUDA events on
- * `stream`) over every SM and writes the rate in 1e9 DFMA per second to
- * *gops_out (host pointer).  Synchronous; allocates and frees an 8-byte device
- * sink.  Returns CHX_EINVAL for a NULL pointer, CHX_ECUDA on a CUDA error. */
+ * independent DFMA chains over every SM in two operand forms (constants as
+ * kernel parameters, and loaded into registers; each one warm-up launch, then
+ * two timed ones, CUDA events on `stream`) and writes the larger rate, in 1e9
+ * DFMA per second, to *gops_out (host pointer): some forms of the same chains
+ * issue at a lower rate.  Synchronous; allocates and frees a 24-byte device
+ * scratch.  Returns CHX_EINVAL for a NULL pointer, CHX_ECUDA on a CUDA error. */
 int chx_fp64_fma_rate(double* gops_out, void* stream);
 
 /* Waits for the plan's last stream and returns (and clears) the first error the

@@ -428,3 +428,15 @@ def test_self_convergence_reproduces_the_paper_table():
         assert abs(e[n] - rows[n][0]) <= rows[n][2], (n, e[n], rows[n][0])
     for n in (128, 256, 512):
         assert abs(np.log2(e[n] / e[2 * n]) - rows[n][1]) <= 2e-4, (n, np.log2(e[n] / e[2 * n]), rows[n][1])
+
+
+# --------------------------------------------------------------------------- FP64 rate (roofline denominator)
+def test_fp64_fma_rate_is_a_physical_rate():
+    """chx_fp64_fma_rate: positive, reproducible within 5%, and at most two DFMA per clock per SM
+    at a 2.2 GHz ceiling (GB300: 2070 MHz maximum SM clock)."""
+    chx = _chx()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    r = [chx.fp64_fma_rate() for _ in range(3)]
+    assert min(r) > 0
+    assert max(r) <= 2 * sms * 2.2
+    assert max(r) <= 1.05 * min(r)
